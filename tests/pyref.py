@@ -1,0 +1,170 @@
+"""Second, pure-Python statements of a few oracle parts, written independently of
+oracle/labs_oracle.c, used only to pin the oracle in the CPU tests.
+
+* ISL through numpy's correlate (a library routine) instead of Eq. 1 loops.
+* Philox4x32-10 in Python integers (Salmon et al., SC'11).
+* The walk of Algorithm 1 (self-avoiding form) with dISL by flip-and-recompute, not
+  by the two-position formula the oracle uses.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+MASK32 = 0xFFFFFFFF
+
+
+def isl_np(s) -> int:
+    s = np.asarray(s, dtype=np.int64)
+    L = s.size
+    full = np.correlate(s, s, mode="full")  # index L-1+k holds C_k
+    side = full[L:]
+    return int(np.dot(side, side))
+
+
+def philox(ctr, key):
+    x = [int(v) & MASK32 for v in ctr]
+    k = [int(v) & MASK32 for v in key]
+    for r in range(10):
+        if r:
+            k = [(k[0] + 0x9E3779B9) & MASK32, (k[1] + 0xBB67AE85) & MASK32]
+        p0 = 0xD2511F53 * x[0]
+        p1 = 0xCD9E8D57 * x[2]
+        x = [((p1 >> 32) ^ x[1] ^ k[0]) & MASK32, p1 & MASK32,
+             ((p0 >> 32) ^ x[3] ^ k[1]) & MASK32, p0 & MASK32]
+    return x
+
+
+def skew(x, L):
+    n = (L + 1) // 2
+    c = n - 1
+    s = np.zeros(L, dtype=np.int64)
+    s[:n] = x
+    for j in range(1, n):
+        s[c + j] = -s[c - j] if j % 2 else s[c - j]
+    return s
+
+
+def start_vars(seed, g, r, L):
+    n = (L + 1) // 2
+    x = np.zeros(n, dtype=np.int64)
+    for i in range(n):
+        blk = philox([g, r, i // 128, 0], [seed & MASK32, seed >> 32])
+        w = blk[(i // 32) % 4]
+        x[i] = -1 if (w >> (i % 32)) & 1 else 1
+    return x
+
+
+def zkey(L, i):
+    o = philox([i, L, 0, 2], [0x1BADB002, 0x2011A068])
+    return o[0] | (o[1] << 32)
+
+
+GEN = 0xFFFFF
+
+
+class HT:
+    def __init__(self, log2, cap):
+        self.size = 1 << log2
+        self.slot = [0] * self.size
+        self.cap = min(cap, self.size)
+        self.gen = 1
+
+    def contains(self, fp):
+        tag = (fp & ~GEN & 0xFFFFFFFFFFFFFFFF) | self.gen
+        for p in range(self.cap):
+            e = self.slot[(fp + p) % self.size]
+            if e & GEN != self.gen:
+                return False
+            if e == tag:
+                return True
+        return False
+
+    def insert(self, fp):
+        tag = (fp & ~GEN & 0xFFFFFFFFFFFFFFFF) | self.gen
+        for p in range(self.cap):
+            j = (fp + p) % self.size
+            e = self.slot[j]
+            if e & GEN != self.gen:
+                self.slot[j] = tag
+                return True
+            if e == tag:
+                return True
+        return False
+
+    def new_generation(self):
+        self.gen += 1
+        if self.gen > GEN:
+            self.slot = [0] * self.size
+            self.gen = 1
+
+
+def walk(L, seed, g, steps, tabu_log2=16, cap=32, patience=0):
+    """Returns (trace_code, trace_isl, best_isl, restarts) for walker g."""
+    n = (L + 1) // 2
+    patience = patience or 2 * n
+    keys = [zkey(L, i) for i in range(n)]
+    ht = HT(tabu_log2, cap)
+    st = {"r": 0, "best": None, "restarts": 0}
+
+    def fp_of(s):
+        f = 0
+        for i in range(n):
+            if s[i] < 0:
+                f ^= keys[i]
+        return f
+
+    def begin():
+        s = skew(start_vars(seed, g, st["r"], L), L)
+        e = isl_np(s)
+        f = fp_of(s)
+        ht.insert(f)
+        if st["best"] is None or e < st["best"]:
+            st["best"] = e
+        return s, e, f, e, 0
+
+    s, e, f, since, stag = begin()
+    codes, isls = [], []
+    for _ in range(steps):
+        deltas = []
+        for i in range(n):
+            t = s.copy()
+            t[i] = -t[i]
+            if L - 1 - i != i:
+                t[L - 1 - i] = -t[L - 1 - i]
+            deltas.append(isl_np(t) - e)
+        order = sorted(range(n), key=lambda i: (deltas[i], i))
+        chosen = None
+        for i in order:
+            if not ht.contains(f ^ keys[i]):
+                chosen = i
+                break
+        if chosen is None:
+            st["r"] += 1
+            st["restarts"] += 1
+            ht.new_generation()
+            s, e, f, since, stag = begin()
+            codes.append(-1)
+            isls.append(e)
+            continue
+        s[chosen] = -s[chosen]
+        if L - 1 - chosen != chosen:
+            s[L - 1 - chosen] = -s[L - 1 - chosen]
+        e += deltas[chosen]
+        f ^= keys[chosen]
+        stored = ht.insert(f)
+        if e < st["best"]:
+            st["best"] = e
+        if e < since:
+            since, stag = e, 0
+        else:
+            stag += 1
+        code = chosen
+        if stag >= patience or not stored:
+            st["r"] += 1
+            st["restarts"] += 1
+            ht.new_generation()
+            s, e, f, since, stag = begin()
+            code |= 0x10000
+        codes.append(code)
+        isls.append(e)
+    return codes, isls, st["best"], st["restarts"]
