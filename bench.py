@@ -1,0 +1,297 @@
+"""Throughput of the skew-symmetric LABS walk on GB300: exact flip evaluations per second.
+
+One bench step = one full run of the L=201 workload: every walker restarts from its
+Philox start (labs_reset) and takes 10^4 walk steps (labs_walk), each step evaluating
+all n = 101 free-variable flips exactly (int32 ISL).  Default: 16384 walkers, HT of 2^16
+slots per walker (8.6 GB of tables, far larger than the 129 MB L2), seed 7.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (oracle/, plain C, all host cores) on a bounded
+sample of the same workload.  Under torchrun every rank runs its own walkers (seed
+offset by rank, no collective on the data path) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact flip evaluations/sec"
+UNIT = "flip evaluations/s"
+# Derived int32 peak: 152 SMs x 128 INT32 lanes x 2070 MHz (maximum SM clock).
+INT32_LANES_PER_SM = 128
+ALGO_OPS_PER_LAG_TERM = 4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--L", type=int, default=201)
+    ap.add_argument("--walkers", type=int, default=16384)
+    ap.add_argument("--walk-steps", type=int, default=10000)
+    ap.add_argument("--tabu-log2", type=int, default=16)
+    ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--cpu-walkers", type=int, default=64)
+    ap.add_argument("--cpu-steps", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(args):
+    """The oracle as it stands, all host cores, on a bounded sample of the workload."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.walk(args.L, args.seed, args.cpu_walkers, args.cpu_steps, tabu_log2=args.tabu_log2, nthreads=cores)
+    dt = time.perf_counter() - t0
+    n = (args.L + 1) // 2
+    flips = args.cpu_walkers * args.cpu_steps * n
+    return {"value": flips / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "L=%d, %d walkers x %d steps (walkers 0..%d of the workload), %.2f s" %
+                      (args.L, args.cpu_walkers, args.cpu_steps, args.cpu_walkers - 1, dt)}
+
+
+def config_of(args, world):
+    return {"workload": "L=%d skew-symmetric self-avoiding walk, %d walkers/GPU x %d steps, HT 2^%d slots/walker, "
+                        "uniform random +-1 Philox starts, seed %d" % (args.L, args.walkers, args.walk_steps,
+                                                                      args.tabu_log2, args.seed),
+            "L": args.L, "walkers_per_gpu": args.walkers, "walk_steps": args.walk_steps,
+            "tabu_slots_per_walker": 1 << args.tabu_log2,
+            "l2": "inputs larger than L2: %.1f GB of HT tables per GPU" %
+                  ((args.walkers << args.tabu_log2) * 8 / 1e9),
+            "parallelism": "independent walkers, %d rank(s)" % world}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    n = (args.L + 1) // 2
+    steps = args.cpu_steps
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.walk(args.L, args.seed, args.cpu_walkers, steps, tabu_log2=args.tabu_log2, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    tmax = sum(times) / len(times)
+    flips = args.cpu_walkers * steps * n
+    value = flips / tmax
+    sample = "L=%d, %d walkers x %d steps per step (a bounded sample of the workload)" % (args.L, args.cpu_walkers, steps)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": config_of(args, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2011_00068_gb300 as labs
+
+    rank, world, local = dist_env()
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        pg = dist
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(dev)
+    n = (args.L + 1) // 2
+    seed = args.seed + 1000003 * rank
+    s = labs.Search(args.L, args.walkers, seed, device=dev, stream=stream, tabu_log2=args.tabu_log2)
+    chunk = int(s.cfg.chunk_steps) or 1024
+    nchunks = -(-args.walk_steps // chunk)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if pg:
+            pg.barrier()
+
+    def one_step():
+        s.reset()
+        s.walk(args.walk_steps)
+
+    for _ in range(args.warmup):
+        one_step()
+    s.sync()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    wall = []
+    with ClockSampler(local) as clk:
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            # walk-kernel time: events on the library's stream around labs_walk
+            s.reset()
+            ev[i][0].record(stream)
+            s.walk(args.walk_steps)
+            ev[i][1].record(stream)
+        s.sync()
+        barrier()
+        t1 = time.perf_counter()
+    walk_ms = [a.elapsed_time(b) for a, b in ev]
+    elapsed = t1 - t0
+    if pg:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed = float(t.item())
+    flips_per_step = args.walkers * args.walk_steps * n
+    value = world * flips_per_step * args.steps / elapsed
+    st = s.stats()
+    assert st["steps"] == args.walkers * args.walk_steps, st
+
+    # roofline of the walk kernel: lag terms n(n-1) per walker step, 4 int32 ops each
+    avg_launch_s = statistics.mean(walk_ms) / 1e3 / nchunks
+    ops_per_launch = ALGO_OPS_PER_LAG_TERM * n * (n - 1) * args.walkers * args.walk_steps / nchunks
+    peaks = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = INT32_LANES_PER_SM * sms * sm_mhz * 1e6
+    achieved = ops_per_launch / avg_launch_s
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s (int32)",
+                "frac": achieved / peak, "traffic": None, "kernel": "walk_chunk_kernel",
+                "peak_source": "derived: %d SMs x %d INT32 lanes x %.0f MHz" % (sms, INT32_LANES_PER_SM, sm_mhz)}
+
+    e2e = None
+    if not args.no_e2e:
+        # the user's whole call: fresh start, walk, and the per-walker results read back
+        e2e_times = []
+        d2h = 0
+        for _ in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            s.reset()
+            s.walk(args.walk_steps)
+            r = s.results()
+            b = s.best()
+            e2e_times.append(time.perf_counter() - t0)
+            d2h = sum(v.nbytes for v in r.values()) + b["seq"].nbytes + 16
+        e2e = {"value": world * flips_per_step / statistics.mean(e2e_times), "unit": UNIT,
+               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": config_of(args, world), "roofline": roofline,
+                "clocks": clk.summary(), "e2e": e2e,
+                "gpu_launches": args.steps * (2 + nchunks),
+                "walk_ms_per_step": statistics.mean(walk_ms),
+                "best": {"isl": st["best_isl"], "F": args.L ** 2 / (2 * st["best_isl"]), "L": st["best_L"]},
+                "restarts": st["restarts"]}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(line))
+    s.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

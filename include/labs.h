@@ -1,0 +1,203 @@
+/*
+ * labs.h -- C ABI of liblabs, a single-GPU (GB300, sm_103a) search for skew-symmetric
+ * binary sequences with a high merit factor, after Brest & Boskovic, "Computational
+ * Search of Long Skew-symmetric Binary Sequences with High Merit Factors"
+ * (arXiv 2011.00068).
+ *
+ * Terms (Section 1 of the paper):
+ *   S = (s_0 .. s_{L-1}), s_i in {+1, -1}, stored as int8 rows of length L.
+ *   C_k = sum_i s_i s_{i+k}                                   (Eq. 1)
+ *   ISL = sum_{k=1}^{L-1} C_k^2                               (Eq. 2)
+ *   F   = L^2 / (2 ISL)                                       (Eq. 3)
+ *   skew symmetry, L = 2n-1, centre c = n-1:
+ *         s_{c+j} = (-1)^j s_{c-j}, j = 1..n-1                 (Eq. 4, 0-based)
+ *   The n free variables are s_0 .. s_c; flipping free variable i negates s_i and
+ *   its mirror s_{L-1-i} (only s_c for i = c), which keeps Eq. 4 (Algorithm 1,
+ *   neighbourhood loop).
+ *
+ * Conventions for every call:
+ *   - Returns LABS_OK (0) or a negative LABS_E* code; labs_last_error() gives text.
+ *   - "dev" pointers are device memory owned by the caller; "host" pointers are
+ *     host memory owned by the caller.  The library allocates no device memory for
+ *     its searches: a context's state lives in one caller-allocated workspace
+ *     (labs_workspace_bytes / labs_bind_workspace).
+ *   - Calls that launch work are asynchronous on the CUDA stream given to labs_init
+ *     (a cudaStream_t passed as void*; NULL = the legacy default stream).  Errors
+ *     detected on the device are reported by the next synchronising call
+ *     (labs_sync, labs_best, labs_walker_results, labs_stats, labs_checkpoint).
+ *   - Lengths: odd L with 3 <= L <= LABS_MAX_L.
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef LABS_H
+#define LABS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LABS_OK 0
+#define LABS_EINVAL (-1)     /* bad argument, or invalid input rows seen on the device */
+#define LABS_ENOMEM (-2)     /* workspace missing or too small, host allocation failed */
+#define LABS_ECUDA (-3)      /* a CUDA runtime call failed */
+#define LABS_ETIMEOUT (-4)   /* the deadline set by labs_set_deadline passed */
+#define LABS_ECANCELLED (-5) /* labs_cancel was called */
+#define LABS_ESTATE (-6)     /* a walker's stored state failed its consistency check */
+
+#define LABS_MAX_L 511       /* n = (L+1)/2 <= 256 free variables */
+#define LABS_MAX_GROUPS 64   /* distinct lengths in one context */
+
+/* Step trace codes written by labs_trace (one int32 per walker step). */
+#define LABS_TRACE_RESTART 0x10000 /* OR-ed into the flipped index: the step ended in a restart */
+#define LABS_TRACE_BLOCKED (-1)    /* every neighbour was already visited: restart, no move */
+
+typedef struct labs_ctx labs_ctx;
+
+/* Walk parameters.  The paper fixes none of these (Algorithm 1 names a visited-set
+ * hash table HT and a stopping rule only); the defaults are the library's reading. */
+typedef struct labs_config {
+    int32_t tabu_log2;       /* HT slots per walker = 2^tabu_log2, 1..20; default 16 */
+    int32_t probe_cap;       /* linear-probe limit of HT, 1..32; default 32 */
+    int32_t patience;        /* restart after this many steps without a new best since
+                                the last restart; 0 (default) = 2n */
+    int32_t target_num;      /* time-to-target threshold F >= target_num/target_den; */
+    int32_t target_den;      /* default 17/2 (F >= 8.5); 0/0 disables it */
+    int32_t chunk_steps;     /* steps per kernel launch inside labs_walk; 0 = auto */
+    int32_t warps_per_cta;   /* walkers resident per CTA (one warp each); 0 = tuned */
+    int32_t flags;           /* LABS_FLAG_* */
+} labs_config;
+
+#define LABS_FLAG_NO_GRAPH 1     /* launch chunks one by one instead of a CUDA graph */
+#define LABS_FLAG_CHECK_STATE 2  /* re-derive ISL from scratch at each chunk end */
+
+/* Counters of a context, summed over its walkers (labs_stats). */
+typedef struct labs_counters {
+    int64_t steps;             /* walker steps taken */
+    int64_t flip_evaluations;  /* n per step: every free-variable flip is evaluated */
+    int64_t restarts;          /* restarts after the first start */
+    int64_t overflows;         /* HT insertions that found no free slot within probe_cap */
+    int64_t blocked;           /* steps whose whole neighbourhood was in HT */
+    int32_t best_isl;          /* lowest ISL seen by any walker of the selected length */
+    int32_t best_L;            /* its length */
+    int64_t best_walker;       /* lowest walker id reaching it */
+    int64_t target_step;       /* fewest steps after which some walker met the target,
+                                  -1 if none did */
+    int64_t walkers_at_target; /* walkers that met the target */
+} labs_counters;
+
+/* Fills *cfg with the defaults above. */
+void labs_default_config(labs_config *cfg);
+
+/* Creates a context for `walkers` independent walkers of one odd length L
+ * (Algorithm 1: input L; every walker is one run of the search).  Walker w starts
+ * from the random skew-symmetric sequence drawn by Philox4x32-10 under key `seed`
+ * (Algorithm 1, "initialize a starting skew-symmetric sequence").  cfg may be NULL
+ * (defaults).  No device work happens until a workspace is bound. */
+int labs_init(labs_ctx **ctx, int32_t L, int64_t walkers, uint64_t seed,
+              const labs_config *cfg, void *cuda_stream);
+
+/* As labs_init for nL lengths at once (Table 1 covers L = 201..303): walkers_per_L[j]
+ * walkers of length Ls[j].  Walker ids run group by group in the order given. */
+int labs_init_multi(labs_ctx **ctx, const int32_t *Ls, const int64_t *walkers_per_L,
+                    int32_t nL, uint64_t seed, const labs_config *cfg, void *cuda_stream);
+
+/* Device bytes the caller must allocate for the context's workspace (state of all
+ * walkers, their HT tables, counters).  Alignment 256 bytes. */
+int labs_workspace_bytes(const labs_ctx *ctx, size_t *bytes);
+
+/* Hands the workspace to the context (the caller keeps ownership and must keep it
+ * alive until labs_destroy) and starts every walker at step 0 (see labs_reset). */
+int labs_bind_workspace(labs_ctx *ctx, void *dev_workspace, size_t bytes);
+
+/* Puts every walker back to its first random start, step 0, empty HT. */
+int labs_reset(labs_ctx *ctx);
+
+/* Eq. 2 for a batch of arbitrary +-1 rows: dev_seqs is int8 [batch][L] (row-major,
+ * L = the context's single length), dev_isl_out is int32 [batch].  A row holding a
+ * value other than +-1 gets ISL -1 (and labs_sync then reports LABS_EINVAL when a
+ * workspace is bound).  batch may be 0. */
+int labs_isl(labs_ctx *ctx, const int8_t *dev_seqs, int64_t batch, int32_t *dev_isl_out);
+
+/* The neighbourhood of Algorithm 1 ("fast calculate merit factor of S_f") for a
+ * batch of skew-symmetric rows: dev_delta_out is int32 [batch][n], entry i = ISL after
+ * flipping free variable i (and its mirror) minus ISL before, i = 0..n-1.  A row that
+ * is not +-1 or breaks Eq. 4 gets INT32_MIN in every entry (and labs_sync reports
+ * LABS_EINVAL when a workspace is bound). */
+int labs_neighbor_delta(labs_ctx *ctx, const int8_t *dev_seqs, int64_t batch,
+                        int32_t *dev_delta_out);
+
+/* Advances every walker by `steps` steps of the walk (Algorithm 1, self-avoiding
+ * form; the step rule is stated here and implemented in csrc/labs_kernels.cu):
+ *   evaluate all n flips; take the flip with the lowest dISL whose result is not in
+ *   the walker's HT (ties to the lowest i); move there and insert it into HT; keep
+ *   the best sequence (strictly lower ISL); restart from a new random sequence with
+ *   an empty HT after `patience` steps without a new best since the last restart,
+ *   when every neighbour is in HT, or when HT has no free slot for the new state.
+ * The trajectory of a walker depends only on (seed, walker id, L, cfg), never on
+ * chunking, launch shape or the other walkers. */
+int labs_walk(labs_ctx *ctx, int64_t steps);
+
+/* Waits for the context's stream; returns the first device-side error, if any. */
+int labs_sync(labs_ctx *ctx);
+
+/* Best sequence found so far among walkers of length L (L = 0: all lengths):
+ * lowest ISL, ties to the lowest walker id.  Synchronising.  host_seq_out: int8 [L]
+ * (nullable; sized for the winning length, which *L_out gives), isl/F/L_out nullable,
+ * hex_out: ceil(L/4)+1 chars in the encoding described below Table 1 (nullable). */
+int labs_best(labs_ctx *ctx, int32_t L, int8_t *host_seq_out, int32_t *isl, double *F,
+              int32_t *L_out, char *hex_out);
+
+/* Per-walker results for walkers [first, first+count): current and best ISL (int32),
+ * and optionally their sequences (int8 [count][Lw], all walkers in the range must have
+ * the same length Lw).  Any pointer may be NULL.  Synchronising. */
+int labs_walker_results(labs_ctx *ctx, int64_t first, int64_t count, int32_t *host_isl,
+                        int32_t *host_best_isl, int8_t *host_seq, int8_t *host_best_seq,
+                        int64_t *host_target_step);
+
+/* Counters summed over the walkers of length L (0 = all).  Synchronising. */
+int labs_stats(labs_ctx *ctx, int32_t L, labs_counters *out);
+
+/* Arms per-step tracing of k walkers (host_walker_ids, host array) for the following
+ * labs_walk calls: step t (counted from this call) of walker host_walker_ids[j] writes
+ * its trace code to dev_code_log[j*capacity + t] and its ISL at the end of the step to
+ * dev_isl_log[j*capacity + t], for t < capacity.  k = 0 disarms.  The logs are caller
+ * device buffers of k*capacity int32 each. */
+int labs_trace(labs_ctx *ctx, const int64_t *host_walker_ids, int32_t k, int64_t capacity,
+               int32_t *dev_code_log, int32_t *dev_isl_log);
+
+/* Exhaustive search over all skew-symmetric sequences of odd length L (3 <= L <= 63)
+ * with the centre s_c = +1 (negation keeps Eq. 4 and ISL): returns the minimum ISL,
+ * the number of minimising assignments, and the lowest minimising assignment a, where
+ * bit i of a set means s_i = -1 (i < c).  Needs caller device scratch of
+ * labs_enumerate_scratch_bytes(L) bytes.  Synchronises `cuda_stream`. */
+int labs_enumerate_scratch_bytes(int32_t L, size_t *bytes);
+int labs_enumerate(int32_t L, void *dev_scratch, size_t scratch_bytes, int64_t *min_isl,
+                   uint64_t *count, uint64_t *first_assignment, void *cuda_stream);
+
+/* Checkpoint of every walker's state (sequence, ISL, best, counters, random-stream
+ * position) and, with with_tabu != 0, its HT.  With the HT included a restored run
+ * continues bit-identically; without it the HT restarts empty.  host_buf NULL queries
+ * the size.  Synchronising. */
+int labs_checkpoint(labs_ctx *ctx, int with_tabu, void *host_buf, size_t *bytes);
+int labs_restore(labs_ctx *ctx, const void *host_buf, size_t bytes);
+
+/* Deadline, in nanoseconds of the GPU's global timer from now (0 = already passed,
+ * UINT64_MAX = none): walkers stop at the next check and labs_sync reports
+ * LABS_ETIMEOUT.  labs_cancel stops them the same way with LABS_ECANCELLED.  Walkers
+ * stop between steps, with their state saved; labs_clear_stop resumes. */
+int labs_set_deadline(labs_ctx *ctx, uint64_t ns_from_now);
+int labs_cancel(labs_ctx *ctx);
+int labs_clear_stop(labs_ctx *ctx);
+
+/* Text of the last error on this context (never NULL). */
+const char *labs_last_error(const labs_ctx *ctx);
+
+void labs_destroy(labs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LABS_H */

@@ -1,0 +1,721 @@
+// labs_api.cu -- host side of the liblabs C ABI (include/labs.h): contexts, workspace
+// layout, chunked and graph-captured walk launches, reductions, checkpoints.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <ctime>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "labs_internal.cuh"
+
+using namespace labsgpu;
+
+struct labs_ctx {
+    labs_config cfg;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;  // private stream used only to record CUDA graphs
+    uint64_t seed = 0;
+    int device = 0;
+    int sms = 0;
+    int nG = 0;
+    DevGroup groups[LABS_MAX_GROUPS];
+    int64_t W = 0;
+    int n_max = 0;
+    // workspace layout (byte offsets)
+    size_t off_status = 0, off_groups = 0, off_zkeys = 0, off_states = 0, off_trace_start = 0,
+           off_trace_ids = 0, off_queue = 0, off_tabu = 0, total = 0;
+    char* ws = nullptr;
+    Control* ctrl_host = nullptr;
+    Control* ctrl_dev = nullptr;
+    long long gpu_minus_host_ns = 0;
+    int warps_per_cta = 0, ctas_per_sm = 0, grid = 0, chunk = 0;
+    size_t smem_bytes = 0;
+    bool catch_up = false;
+    int64_t planned = 0;
+    std::map<int, cudaGraphExec_t> graphs;
+    std::string err;
+};
+
+namespace {
+
+constexpr uint64_t kCkptMagic = 0x4C41425343503031ull;  // "LABSCP01"
+
+int fail(labs_ctx* c, int code, const char* fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(labs_ctx* c, cudaError_t e, const char* what)
+{
+    return fail(c, LABS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t align_up(size_t x, size_t a)
+{
+    return (x + a - 1) / a * a;
+}
+
+long long host_ns()
+{
+    timespec ts;
+    clock_gettime(CLOCK_REALTIME, &ts);
+    return (long long)ts.tv_sec * 1000000000ll + ts.tv_nsec;
+}
+
+template <class T>
+T* at(labs_ctx* c, size_t off)
+{
+    return reinterpret_cast<T*>(c->ws + off);
+}
+
+KParams params(labs_ctx* c)
+{
+    KParams p;
+    p.status = at<DevStatus>(c, c->off_status);
+    p.groups = at<DevGroup>(c, c->off_groups);
+    p.zkeys = at<uint64_t>(c, c->off_zkeys);
+    p.states = at<WalkerState>(c, c->off_states);
+    p.tabu = at<uint64_t>(c, c->off_tabu);
+    p.trace_start = at<int64_t>(c, c->off_trace_start);
+    p.queue = at<uint32_t>(c, c->off_queue);
+    p.ctrl = c->ctrl_dev;
+    p.W = c->W;
+    p.nG = c->nG;
+    p.n_max = c->n_max;
+    p.tabu_log2 = c->cfg.tabu_log2;
+    p.probe_cap = c->cfg.probe_cap;
+    p.patience = c->cfg.patience;
+    p.target_num = c->cfg.target_num;
+    p.target_den = c->cfg.target_den;
+    p.chunk_steps = c->chunk;
+    p.seed = c->seed;
+    return p;
+}
+
+bool valid_L(int32_t L)
+{
+    return L >= 3 && L <= LABS_MAX_L && (L & 1) == 1;
+}
+
+int need_ws(labs_ctx* c)
+{
+    if (!c) return LABS_EINVAL;
+    if (!c->ws) return fail(c, LABS_ENOMEM, "no workspace bound (labs_bind_workspace)");
+    return LABS_OK;
+}
+
+// Sequence (+-1) of free-variable bits by Eq. 4.
+void expand_bits(const uint32_t* bits, int L, int8_t* out)
+{
+    const int n = (L + 1) / 2, c = n - 1;
+    for (int j = 0; j < L; ++j) {
+        const int f = j <= c ? j : 2 * c - j;
+        int x = ((bits[f >> 5] >> (f & 31)) & 1u) ? -1 : 1;
+        if (j > c && ((j - c) & 1)) x = -x;
+        out[j] = (int8_t)x;
+    }
+}
+
+// Encoding described below Table 1: first symbol most significant, 0 <-> +1,
+// 1 <-> -1, leading zero bits up to whole hex digits.
+void hex_of(const int8_t* s, int L, char* out)
+{
+    static const char digits[] = "0123456789ABCDEF";
+    const int nd = (L + 3) / 4, pad = 4 * nd - L;
+    for (int d = 0; d < nd; ++d) {
+        int v = 0;
+        for (int t = 0; t < 4; ++t) {
+            const int b = 4 * d + t - pad;
+            v = (v << 1) | (b >= 0 && s[b] < 0 ? 1 : 0);
+        }
+        out[d] = digits[v];
+    }
+    out[nd] = 0;
+}
+
+int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uint64_t seed,
+          const labs_config* cfg, void* stream)
+{
+    labs_default_config(&c->cfg);
+    if (cfg) c->cfg = *cfg;
+    labs_config& k = c->cfg;
+    if (k.tabu_log2 < 1 || k.tabu_log2 > 20) return fail(c, LABS_EINVAL, "tabu_log2 must be 1..20");
+    if (k.probe_cap < 1 || k.probe_cap > 32) return fail(c, LABS_EINVAL, "probe_cap must be 1..32");
+    if (k.patience < 0 || k.chunk_steps < 0 || k.warps_per_cta < 0 || k.warps_per_cta > 16)
+        return fail(c, LABS_EINVAL, "bad patience / chunk_steps / warps_per_cta");
+    if (nL < 1 || nL > LABS_MAX_GROUPS) return fail(c, LABS_EINVAL, "need 1..%d lengths", LABS_MAX_GROUPS);
+    c->seed = seed;
+    c->stream = (cudaStream_t)stream;
+    c->nG = nL;
+    int64_t first = 0, zoff = 0;
+    for (int g = 0; g < nL; ++g) {
+        if (!valid_L(Ls[g])) return fail(c, LABS_EINVAL, "L=%d: need odd 3 <= L <= %d", Ls[g], LABS_MAX_L);
+        if (counts[g] < 0) return fail(c, LABS_EINVAL, "negative walker count");
+        DevGroup& G = c->groups[g];
+        G.L = Ls[g];
+        G.n = (Ls[g] + 1) / 2;
+        G.first = first;
+        G.count = counts[g];
+        G.zkey_off = zoff;
+        first += counts[g];
+        zoff += G.n;
+        c->n_max = std::max(c->n_max, G.n);
+    }
+    c->W = first;
+    if (c->W > (int64_t)UINT32_MAX - 1) return fail(c, LABS_EINVAL, "too many walkers");
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetDevice");
+    e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaDeviceGetAttribute");
+    // workspace layout
+    size_t off = 0;
+    c->off_status = off;
+    off = align_up(off + sizeof(DevStatus), 256);
+    c->off_groups = off;
+    off = align_up(off + sizeof(DevGroup) * LABS_MAX_GROUPS, 256);
+    c->off_zkeys = off;
+    off = align_up(off + sizeof(uint64_t) * (size_t)zoff, 256);
+    c->off_states = off;
+    off = align_up(off + sizeof(WalkerState) * (size_t)c->W, 256);
+    c->off_trace_start = off;
+    off = align_up(off + sizeof(int64_t) * kMaxTrace, 256);
+    c->off_trace_ids = off;
+    off = align_up(off + sizeof(int64_t) * kMaxTrace, 256);
+    c->off_queue = off;
+    off = align_up(off + sizeof(uint32_t) * kMaxChunksPerCall, 256);
+    c->off_tabu = off;
+    off = align_up(off + sizeof(uint64_t) * ((size_t)c->W << k.tabu_log2), 256);
+    c->total = off;
+    // launch shape of the walk kernel
+    const size_t per_warp = (size_t)warp_smem(c->n_max).words * sizeof(int);
+    int warps = k.warps_per_cta ? k.warps_per_cta : 8;
+    for (;;) {
+        c->smem_bytes = per_warp * (size_t)warps;
+        int occ = 0;
+        if (walk_kernel_config(warps, c->smem_bytes, &occ) == LABS_OK && occ > 0) {
+            c->ctas_per_sm = occ;
+            break;
+        }
+        if (warps == 1) return fail(c, LABS_ECUDA, "walk kernel does not fit on an SM");
+        warps /= 2;
+    }
+    c->warps_per_cta = warps;
+    c->grid = c->sms * c->ctas_per_sm;
+    c->chunk = k.chunk_steps ? k.chunk_steps : 1024;
+    e = cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamCreate");
+    e = cudaHostAlloc((void**)&c->ctrl_host, sizeof(Control), cudaHostAllocMapped);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaHostAlloc");
+    c->ctrl_host->stop = 0;
+    c->ctrl_host->deadline_ns = UINT64_MAX;
+    e = cudaHostGetDevicePointer((void**)&c->ctrl_dev, c->ctrl_host, 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaHostGetDevicePointer");
+    return LABS_OK;
+}
+
+int create(labs_ctx** out, const int32_t* Ls, const int64_t* counts, int32_t nL, uint64_t seed,
+           const labs_config* cfg, void* stream)
+{
+    if (!out || !Ls || !counts) return LABS_EINVAL;
+    *out = nullptr;
+    labs_ctx* c = new (std::nothrow) labs_ctx();
+    if (!c) return LABS_ENOMEM;
+    const int rc = setup(c, Ls, counts, nL, seed, cfg, stream);
+    *out = c;  // returned even on failure so that labs_last_error can explain; caller destroys
+    return rc;
+}
+
+int sync_status(labs_ctx* c)
+{
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
+    DevStatus st;
+    e = cudaMemcpy(&st, at<DevStatus>(c, c->off_status), sizeof(DevStatus), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+    if (st.error) {
+        const char* what = st.error == LABS_ETIMEOUT     ? "deadline passed"
+                           : st.error == LABS_ECANCELLED ? "cancelled"
+                           : st.error == LABS_ESTATE     ? "walker state failed its consistency check"
+                                                         : "device error";
+        return fail(c, st.error, "%s (walker %d)", what, st.error_detail);
+    }
+    if (st.invalid_rows) {
+        const int32_t zero = 0;
+        cudaMemcpy(&at<DevStatus>(c, c->off_status)->invalid_rows, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+        return fail(c, LABS_EINVAL, "%d input rows were not +-1 / not skew-symmetric", st.invalid_rows);
+    }
+    return LABS_OK;
+}
+
+int graph_for(labs_ctx* c, int nchunks, cudaGraphExec_t* exec)
+{
+    auto it = c->graphs.find(nchunks);
+    if (it != c->graphs.end()) {
+        *exec = it->second;
+        return LABS_OK;
+    }
+    const KParams p = params(c);
+    cudaError_t e = cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
+    int rc = LABS_OK;
+    for (int j = 0; j < nchunks && rc == LABS_OK; ++j)
+        rc = launch_walk_chunk(p, j, c->grid, c->warps_per_cta, c->smem_bytes, c->capture);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->capture, &g);
+    if (rc != LABS_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, e != cudaSuccess ? e : cudaGetLastError(), "graph capture");
+    }
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    c->graphs[nchunks] = *exec;
+    return LABS_OK;
+}
+
+void drop_graphs(labs_ctx* c)
+{
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+void labs_default_config(labs_config* cfg)
+{
+    if (!cfg) return;
+    cfg->tabu_log2 = 16;
+    cfg->probe_cap = 32;
+    cfg->patience = 0;
+    cfg->target_num = 17;
+    cfg->target_den = 2;
+    cfg->chunk_steps = 0;
+    cfg->warps_per_cta = 0;
+    cfg->flags = 0;
+}
+
+int labs_init(labs_ctx** ctx, int32_t L, int64_t walkers, uint64_t seed, const labs_config* cfg,
+              void* cuda_stream)
+{
+    return create(ctx, &L, &walkers, 1, seed, cfg, cuda_stream);
+}
+
+int labs_init_multi(labs_ctx** ctx, const int32_t* Ls, const int64_t* walkers_per_L, int32_t nL,
+                    uint64_t seed, const labs_config* cfg, void* cuda_stream)
+{
+    return create(ctx, Ls, walkers_per_L, nL, seed, cfg, cuda_stream);
+}
+
+int labs_workspace_bytes(const labs_ctx* ctx, size_t* bytes)
+{
+    if (!ctx || !bytes) return LABS_EINVAL;
+    *bytes = ctx->total;
+    return LABS_OK;
+}
+
+int labs_reset(labs_ctx* c)
+{
+    int rc = need_ws(c);
+    if (rc) return rc;
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaMemsetAsync(c->ws + c->off_status, 0, sizeof(DevStatus), c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->ws + c->off_states, 0, sizeof(WalkerState) * (size_t)c->W, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->ws + c->off_tabu, 0, c->total - c->off_tabu, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "workspace clear");
+    const KParams p = params(c);
+    if (c->W > 0) {
+        const int block = 8 * kWarp;
+        const int64_t need = (c->W + 7) / 8;
+        const int grid = (int)std::min<int64_t>(need, (int64_t)c->sms * 4);
+        rc = launch_reset(p, grid, block, c->stream);
+        if (rc) return fail(c, rc, "reset launch: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    c->planned = 0;
+    c->catch_up = false;
+    return LABS_OK;
+}
+
+int labs_bind_workspace(labs_ctx* c, void* dev_workspace, size_t bytes)
+{
+    if (!c || !dev_workspace) return LABS_EINVAL;
+    if (bytes < c->total) return fail(c, LABS_ENOMEM, "workspace has %zu bytes, needs %zu", bytes, c->total);
+    if (((uintptr_t)dev_workspace & 255) != 0) return fail(c, LABS_EINVAL, "workspace must be 256-byte aligned");
+    cudaSetDevice(c->device);
+    c->ws = (char*)dev_workspace;
+    cudaError_t e = cudaMemcpy(c->ws + c->off_groups, c->groups, sizeof(DevGroup) * c->nG, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "group table upload");
+    const KParams p = params(c);
+    int rc = launch_zobrist(p, at<uint64_t>(c, c->off_zkeys), c->groups, c->nG, c->stream);
+    if (rc) return fail(c, rc, "fingerprint keys");
+    // align the host clock with the GPU global timer for deadlines
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
+    unsigned long long* probe = &at<DevStatus>(c, c->off_status)->probe_ns;
+    const long long t0 = host_ns();
+    launch_time_probe(probe, c->stream);
+    e = cudaStreamSynchronize(c->stream);
+    const long long t1 = host_ns();
+    if (e != cudaSuccess) return cuda_fail(c, e, "clock probe");
+    uint64_t g = 0;
+    cudaMemcpy(&g, probe, sizeof(g), cudaMemcpyDeviceToHost);
+    c->gpu_minus_host_ns = (long long)g - (t0 + (t1 - t0) / 2);
+    return labs_reset(c);
+}
+
+int labs_isl(labs_ctx* c, const int8_t* dev_seqs, int64_t batch, int32_t* dev_isl_out)
+{
+    if (!c) return LABS_EINVAL;
+    if (c->nG != 1) return fail(c, LABS_EINVAL, "labs_isl needs a single-length context");
+    if (batch < 0 || (batch > 0 && (!dev_seqs || !dev_isl_out))) return fail(c, LABS_EINVAL, "bad batch");
+    cudaSetDevice(c->device);
+    DevStatus* st = c->ws ? at<DevStatus>(c, c->off_status) : nullptr;
+    const int rc = launch_isl(dev_seqs, batch, c->groups[0].L, dev_isl_out, st, c->stream);
+    return rc ? fail(c, rc, "labs_isl launch: %s", cudaGetErrorString(cudaGetLastError())) : LABS_OK;
+}
+
+int labs_neighbor_delta(labs_ctx* c, const int8_t* dev_seqs, int64_t batch, int32_t* dev_delta_out)
+{
+    if (!c) return LABS_EINVAL;
+    if (c->nG != 1) return fail(c, LABS_EINVAL, "labs_neighbor_delta needs a single-length context");
+    if (batch < 0 || (batch > 0 && (!dev_seqs || !dev_delta_out))) return fail(c, LABS_EINVAL, "bad batch");
+    cudaSetDevice(c->device);
+    DevStatus* st = c->ws ? at<DevStatus>(c, c->off_status) : nullptr;
+    const int rc = launch_delta(dev_seqs, batch, c->groups[0].L, dev_delta_out, st, c->stream);
+    return rc ? fail(c, rc, "labs_neighbor_delta launch: %s", cudaGetErrorString(cudaGetLastError())) : LABS_OK;
+}
+
+int labs_walk(labs_ctx* c, int64_t steps)
+{
+    int rc = need_ws(c);
+    if (rc) return rc;
+    if (steps < 0) return fail(c, LABS_EINVAL, "negative steps");
+    if ((steps == 0 && !c->catch_up) || c->W == 0) return LABS_OK;
+    cudaSetDevice(c->device);
+    const KParams p = params(c);
+    while (steps > 0 || c->catch_up) {
+        int64_t take = std::min<int64_t>(steps, (int64_t)c->chunk * (kMaxChunksPerCall - 1));
+        int64_t span = take;
+        if (c->catch_up) {
+            span = c->planned + take;  // walkers stopped early may be anywhere behind
+            c->catch_up = false;
+        }
+        const int nchunks = (int)std::min<int64_t>((span + c->chunk - 1) / c->chunk, kMaxChunksPerCall);
+        rc = launch_prep_walk(p, take, nchunks, c->stream);
+        if (rc) return fail(c, rc, "walk preparation launch");
+        if (c->cfg.flags & LABS_FLAG_NO_GRAPH) {
+            for (int j = 0; j < nchunks; ++j) {
+                rc = launch_walk_chunk(p, j, c->grid, c->warps_per_cta, c->smem_bytes, c->stream);
+                if (rc) return fail(c, rc, "walk launch: %s", cudaGetErrorString(cudaGetLastError()));
+            }
+        } else {
+            cudaGraphExec_t exec = nullptr;
+            rc = graph_for(c, nchunks, &exec);
+            if (rc) return rc;
+            cudaError_t e = cudaGraphLaunch(exec, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+        }
+        c->planned += take;
+        steps -= take;
+    }
+    return LABS_OK;
+}
+
+int labs_sync(labs_ctx* c)
+{
+    int rc = need_ws(c);
+    if (rc) {
+        if (!c) return rc;
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        return e == cudaSuccess ? LABS_OK : cuda_fail(c, e, "stream synchronise");
+    }
+    cudaSetDevice(c->device);
+    return sync_status(c);
+}
+
+int labs_best(labs_ctx* c, int32_t L, int8_t* host_seq_out, int32_t* isl, double* F, int32_t* L_out,
+              char* hex_out)
+{
+    int rc = need_ws(c);
+    if (rc) return rc;
+    cudaSetDevice(c->device);
+    DevStatus* st = at<DevStatus>(c, c->off_status);
+    cudaError_t e = cudaMemsetAsync(&st->best_key, 0xFF, sizeof(st->best_key), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "best reset");
+    rc = launch_best(params(c), L, c->stream);
+    if (rc) return fail(c, rc, "best launch");
+    rc = sync_status(c);
+    if (rc) return rc;
+    unsigned long long key = 0;
+    e = cudaMemcpy(&key, &st->best_key, sizeof(key), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "best read");
+    if (key == ~0ull) return fail(c, LABS_EINVAL, "no walker of length %d", L);
+    const int64_t w = (int64_t)(key & 0xFFFFFFFFull);
+    WalkerState ws;
+    e = cudaMemcpy(&ws, at<WalkerState>(c, c->off_states) + w, sizeof(ws), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "best state read");
+    const int Lw = c->groups[ws.group].L;
+    std::vector<int8_t> seq((size_t)Lw);
+    expand_bits(ws.best, Lw, seq.data());
+    if (host_seq_out) memcpy(host_seq_out, seq.data(), (size_t)Lw);
+    if (isl) *isl = ws.best_isl;
+    if (F) *F = (double)Lw * Lw / (2.0 * ws.best_isl);
+    if (L_out) *L_out = Lw;
+    if (hex_out) hex_of(seq.data(), Lw, hex_out);
+    return LABS_OK;
+}
+
+int labs_walker_results(labs_ctx* c, int64_t first, int64_t count, int32_t* host_isl, int32_t* host_best_isl,
+                        int8_t* host_seq, int8_t* host_best_seq, int64_t* host_target_step)
+{
+    int rc = need_ws(c);
+    if (rc) return rc;
+    if (first < 0 || count < 0 || first + count > c->W) return fail(c, LABS_EINVAL, "walker range out of bounds");
+    cudaSetDevice(c->device);
+    rc = sync_status(c);
+    if (rc) return rc;
+    std::vector<WalkerState> v((size_t)count);
+    if (count) {
+        cudaError_t e = cudaMemcpy(v.data(), at<WalkerState>(c, c->off_states) + first, sizeof(WalkerState) * count,
+                                   cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "walker state read");
+    }
+    int Lw = count ? c->groups[v[0].group].L : 0;
+    if ((host_seq || host_best_seq))
+        for (auto& s : v)
+            if (c->groups[s.group].L != Lw) return fail(c, LABS_EINVAL, "walkers in the range differ in length");
+    for (int64_t j = 0; j < count; ++j) {
+        if (host_isl) host_isl[j] = v[j].isl;
+        if (host_best_isl) host_best_isl[j] = v[j].best_isl;
+        if (host_target_step) host_target_step[j] = v[j].target_step;
+        if (host_seq) expand_bits(v[j].cur, Lw, host_seq + j * Lw);
+        if (host_best_seq) expand_bits(v[j].best, Lw, host_best_seq + j * Lw);
+    }
+    return LABS_OK;
+}
+
+int labs_stats(labs_ctx* c, int32_t L, labs_counters* out)
+{
+    int rc = need_ws(c);
+    if (rc) return rc;
+    if (!out) return fail(c, LABS_EINVAL, "null output");
+    cudaSetDevice(c->device);
+    DevStatus* st = at<DevStatus>(c, c->off_status);
+    rc = sync_status(c);
+    if (rc) return rc;
+    DevStatus h;
+    cudaError_t e = cudaMemcpy(&h, st, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+    h.best_key = ~0ull;
+    h.st_steps = h.st_evals = h.st_restarts = h.st_overflows = h.st_blocked = h.st_at_target = 0;
+    h.st_target_step = LLONG_MAX;
+    e = cudaMemcpy(st, &h, sizeof(h), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "status write");
+    rc = launch_stats(params(c), L, c->stream);
+    if (rc) return fail(c, rc, "stats launch");
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
+    e = cudaMemcpy(&h, st, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+    out->steps = (int64_t)h.st_steps;
+    out->flip_evaluations = (int64_t)h.st_evals;
+    out->restarts = (int64_t)h.st_restarts;
+    out->overflows = (int64_t)h.st_overflows;
+    out->blocked = (int64_t)h.st_blocked;
+    out->walkers_at_target = (int64_t)h.st_at_target;
+    out->target_step = h.st_target_step == LLONG_MAX ? -1 : (int64_t)h.st_target_step;
+    if (h.best_key == ~0ull) {
+        out->best_isl = -1;
+        out->best_L = 0;
+        out->best_walker = -1;
+    } else {
+        out->best_isl = (int32_t)(h.best_key >> 32);
+        out->best_walker = (int64_t)(h.best_key & 0xFFFFFFFFull);
+        WalkerState ws;
+        cudaMemcpy(&ws, at<WalkerState>(c, c->off_states) + out->best_walker, sizeof(ws), cudaMemcpyDeviceToHost);
+        out->best_L = c->groups[ws.group].L;
+    }
+    return LABS_OK;
+}
+
+int labs_trace(labs_ctx* c, const int64_t* host_walker_ids, int32_t k, int64_t capacity, int32_t* dev_code_log,
+               int32_t* dev_isl_log)
+{
+    int rc = need_ws(c);
+    if (rc) return rc;
+    if (k < 0 || k > kMaxTrace) return fail(c, LABS_EINVAL, "0 <= k <= %d", kMaxTrace);
+    if (k > 0 && (!host_walker_ids || !dev_code_log || !dev_isl_log || capacity < 0))
+        return fail(c, LABS_EINVAL, "bad trace buffers");
+    for (int j = 0; j < k; ++j)
+        if (host_walker_ids[j] < 0 || host_walker_ids[j] >= c->W)
+            return fail(c, LABS_EINVAL, "walker id %lld out of range", (long long)host_walker_ids[j]);
+    cudaSetDevice(c->device);
+    int64_t* ids = at<int64_t>(c, c->off_trace_ids);
+    if (k > 0) {
+        cudaError_t e = cudaMemcpyAsync(ids, host_walker_ids, sizeof(int64_t) * k, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "trace ids upload");
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
+    }
+    rc = launch_trace_arm(params(c), ids, k, dev_code_log, dev_isl_log, capacity, c->stream);
+    return rc ? fail(c, rc, "trace launch") : LABS_OK;
+}
+
+int labs_enumerate_scratch_bytes(int32_t L, size_t* bytes)
+{
+    if (!bytes || L < 3 || L > 63 || (L & 1) == 0) return LABS_EINVAL;
+    *bytes = enum_scratch_bytes(L);
+    return LABS_OK;
+}
+
+int labs_enumerate(int32_t L, void* dev_scratch, size_t scratch_bytes, int64_t* min_isl, uint64_t* count,
+                   uint64_t* first_assignment, void* cuda_stream)
+{
+    if (L < 3 || L > 63 || (L & 1) == 0 || !dev_scratch) return LABS_EINVAL;
+    if (scratch_bytes < enum_scratch_bytes(L)) return LABS_ENOMEM;
+    if (((uintptr_t)dev_scratch & 15) != 0) return LABS_EINVAL;
+    EnumPart r;
+    const int rc = enum_run(L, (EnumPart*)dev_scratch, cuda_stream, &r);
+    if (rc) return rc;
+    if (min_isl) *min_isl = r.min_isl;
+    if (count) *count = r.count;
+    if (first_assignment) *first_assignment = r.first;
+    return LABS_OK;
+}
+
+int labs_checkpoint(labs_ctx* c, int with_tabu, void* host_buf, size_t* bytes)
+{
+    int rc = need_ws(c);
+    if (rc) return rc;
+    if (!bytes) return fail(c, LABS_EINVAL, "null size");
+    const size_t hdr = 64;
+    const size_t sbytes = sizeof(WalkerState) * (size_t)c->W;
+    const size_t tbytes = with_tabu ? sizeof(uint64_t) * ((size_t)c->W << c->cfg.tabu_log2) : 0;
+    const size_t need = hdr + sbytes + tbytes;
+    if (!host_buf) {
+        *bytes = need;
+        return LABS_OK;
+    }
+    if (*bytes < need) return fail(c, LABS_ENOMEM, "checkpoint buffer has %zu bytes, needs %zu", *bytes, need);
+    cudaSetDevice(c->device);
+    rc = sync_status(c);
+    if (rc) return rc;
+    uint64_t h[8] = {kCkptMagic, (uint64_t)c->W, (uint64_t)c->nG, (uint64_t)c->cfg.tabu_log2,
+                     (uint64_t)(with_tabu ? 1 : 0), (uint64_t)c->planned, c->seed, 0};
+    memcpy(host_buf, h, sizeof(h));
+    char* dst = (char*)host_buf + hdr;
+    cudaError_t e = cudaMemcpy(dst, c->ws + c->off_states, sbytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && tbytes) e = cudaMemcpy(dst + sbytes, c->ws + c->off_tabu, tbytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint copy");
+    *bytes = need;
+    return LABS_OK;
+}
+
+int labs_restore(labs_ctx* c, const void* host_buf, size_t bytes)
+{
+    int rc = need_ws(c);
+    if (rc) return rc;
+    if (!host_buf || bytes < 64) return fail(c, LABS_EINVAL, "bad checkpoint");
+    uint64_t h[8];
+    memcpy(h, host_buf, sizeof(h));
+    if (h[0] != kCkptMagic || h[1] != (uint64_t)c->W || h[2] != (uint64_t)c->nG ||
+        h[3] != (uint64_t)c->cfg.tabu_log2 || h[6] != c->seed)
+        return fail(c, LABS_EINVAL, "checkpoint does not match this context");
+    const size_t sbytes = sizeof(WalkerState) * (size_t)c->W;
+    const size_t tbytes = h[4] ? sizeof(uint64_t) * ((size_t)c->W << c->cfg.tabu_log2) : 0;
+    if (bytes < 64 + sbytes + tbytes) return fail(c, LABS_EINVAL, "checkpoint truncated");
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
+    const char* src = (const char*)host_buf + 64;
+    e = cudaMemcpy(c->ws + c->off_states, src, sbytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "restore copy");
+    if (tbytes) {
+        e = cudaMemcpy(c->ws + c->off_tabu, src + sbytes, tbytes, cudaMemcpyHostToDevice);
+    } else {
+        // Without the HT every walker continues with an empty table (zeroed slots hold
+        // generation 0, which no walker uses).
+        e = cudaMemset(c->ws + c->off_tabu, 0, c->total - c->off_tabu);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "restore copy");
+    const int64_t planned = (int64_t)h[5];
+    DevStatus* st = at<DevStatus>(c, c->off_status);
+    e = cudaMemcpy(&st->target_steps, &planned, sizeof(planned), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "restore copy");
+    c->planned = planned;
+    c->catch_up = true;
+    return LABS_OK;
+}
+
+int labs_set_deadline(labs_ctx* c, uint64_t ns_from_now)
+{
+    if (!c || !c->ctrl_host) return LABS_EINVAL;
+    if (ns_from_now == UINT64_MAX) {
+        c->ctrl_host->deadline_ns = UINT64_MAX;
+    } else {
+        const long long now = host_ns() + c->gpu_minus_host_ns;
+        const unsigned long long base = now < 0 ? 0ull : (unsigned long long)now;
+        c->ctrl_host->deadline_ns =
+            ns_from_now == 0 ? 0ull : (UINT64_MAX - base < ns_from_now ? UINT64_MAX : base + ns_from_now);
+    }
+    return LABS_OK;
+}
+
+int labs_cancel(labs_ctx* c)
+{
+    if (!c || !c->ctrl_host) return LABS_EINVAL;
+    c->ctrl_host->stop = 1;
+    return LABS_OK;
+}
+
+int labs_clear_stop(labs_ctx* c)
+{
+    int rc = need_ws(c);
+    if (rc) return rc;
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
+    c->ctrl_host->stop = 0;
+    c->ctrl_host->deadline_ns = UINT64_MAX;
+    const int32_t zero[2] = {0, 0};
+    e = cudaMemcpy(at<DevStatus>(c, c->off_status), zero, sizeof(zero), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "status clear");
+    c->catch_up = true;
+    return LABS_OK;
+}
+
+const char* labs_last_error(const labs_ctx* c)
+{
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+void labs_destroy(labs_ctx* c)
+{
+    if (!c) return;
+    if (c->ws) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    if (c->capture) cudaStreamDestroy(c->capture);
+    if (c->ctrl_host) cudaFreeHost(c->ctrl_host);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,150 @@
+// labs_internal.cuh -- device-memory layout shared by the host API (labs_api.cu) and
+// the kernels (labs_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "labs.h"
+
+namespace labsgpu {
+
+constexpr int kWarp = 32;
+constexpr int kMaxN = (LABS_MAX_L + 1) / 2;  // 256 free variables
+constexpr int kBitWords = kMaxN / 32;        // 8 words of free-variable bits
+constexpr int kMaxChunksPerCall = 4096;      // chunk launches per labs_walk call
+constexpr int kMaxTrace = 4096;              // traced walkers
+constexpr int kCheckEvery = 64;              // steps between stop checks
+constexpr uint64_t kGenMask = 0xFFFFFull;    // HT generation field (low 20 bits)
+constexpr uint32_t kZobristKey0 = 0x1BADB002u;  // Philox key of the HT fingerprint keys
+constexpr uint32_t kZobristKey1 = 0x2011A068u;
+
+// One length group: walkers [first, first+count) of length L, n = (L+1)/2 free vars.
+struct DevGroup {
+    int32_t L;
+    int32_t n;
+    int64_t first;
+    int64_t count;
+    int64_t zkey_off;  // offset of this group's n fingerprint keys in the zkey array
+};
+
+// Persistent state of one walker between chunk launches (the rest -- the +-1 rows,
+// the C_k table, the ISL -- is rebuilt from `cur` at the start of every chunk).
+struct alignas(32) WalkerState {
+    uint32_t cur[kBitWords];   // free variables of the current sequence: bit i set <=> s_i = -1
+    uint32_t best[kBitWords];  // free variables of the best sequence
+    int64_t steps_done;
+    int64_t best_step;         // steps_done when best_isl was first reached
+    int64_t target_step;       // steps_done when the F target first held, -1 never
+    uint64_t fp;               // HT fingerprint of `cur`
+    int32_t isl;
+    int32_t best_isl;
+    int32_t since_best;        // best ISL since the last (re)start
+    int32_t stagnation;        // steps since since_best last improved
+    uint32_t restart_idx;      // Philox counter word of the current start
+    uint32_t gen;              // HT generation
+    int32_t restarts;
+    int32_t overflows;
+    int32_t blocked;
+    int32_t group;
+    int32_t trace_slot;        // -1: not traced
+    int32_t pad_[5];
+};
+static_assert(sizeof(WalkerState) == 160, "WalkerState layout");
+
+// Status block at the start of the workspace.
+struct alignas(256) DevStatus {
+    int32_t error;          // first LABS_E* raised on the device (0 = none)
+    int32_t error_detail;   // walker id / row index of that error
+    int32_t invalid_rows;   // rows rejected by labs_isl / labs_neighbor_delta
+    int32_t pad0;
+    int64_t target_steps;   // every walker advances to this step count
+    int32_t* trace_code;    // trace logs (labs_trace)
+    int32_t* trace_isl;
+    int64_t trace_capacity;
+    unsigned long long best_key;  // (best_isl << 32) | walker, reduction target
+    // stats accumulators (labs_stats)
+    unsigned long long st_steps, st_evals, st_restarts, st_overflows, st_blocked, st_at_target;
+    long long st_target_step;     // min over walkers, LLONG_MAX = none
+    unsigned long long probe_ns;  // %globaltimer sample (clock alignment for deadlines)
+    int32_t pad1[6];
+};
+
+// Host-written control block in mapped pinned host memory (read by running kernels).
+struct Control {
+    volatile int32_t stop;           // 1 = cancel requested
+    int32_t pad;
+    volatile uint64_t deadline_ns;   // GPU %globaltimer deadline, UINT64_MAX = none
+};
+
+struct KParams {
+    DevStatus* status;
+    const DevGroup* groups;
+    const uint64_t* zkeys;
+    WalkerState* states;
+    uint64_t* tabu;
+    int64_t* trace_start;
+    uint32_t* queue;          // one work counter per chunk of a labs_walk call
+    const Control* ctrl;
+    int64_t W;
+    int32_t nG;
+    int32_t n_max;            // largest n among the groups (sizes shared memory)
+    int32_t tabu_log2;
+    int32_t probe_cap;
+    int32_t patience;         // 0 = 2n
+    int32_t target_num, target_den;
+    int32_t chunk_steps;
+    uint64_t seed;
+};
+
+// Shared-memory layout of one walker (one warp), all in int32 words:
+//   A0: even positions s_0, s_2, .. (n values)   padded by apad zeros on both sides
+//   A1: odd positions  s_1, s_3, .. (n-1 values) padded the same way
+//   E : E[d] = C_{2|d|} for 0 < |d| < n, E[0] = 0, zero elsewhere, d in [-kEPad, n+8)
+constexpr int kEPad = 128;
+struct WarpSmem {
+    int apad;      // zero padding on each side of A0/A1 (>= n_max, multiple of 4)
+    int alen;      // apad + n_max + apad, rounded to 4
+    int elen;      // kEPad + n_max + 8
+    int words;     // total words per warp
+};
+__host__ __device__ inline WarpSmem warp_smem(int n_max)
+{
+    WarpSmem w;
+    w.apad = (n_max + 3) & ~3;
+    w.alen = (w.apad + ((n_max + 3) & ~3) + w.apad + 4 + 3) & ~3;
+    w.elen = (kEPad + n_max + 8 + 3) & ~3;
+    w.words = 2 * w.alen + w.elen;
+    return w;
+}
+
+// Launchers (labs_kernels.cu).
+int launch_zobrist(const KParams& p, uint64_t* zkeys, const DevGroup* host_groups, int nG,
+                   void* stream);
+int launch_reset(const KParams& p, int grid, int block, void* stream);
+int launch_prep_walk(const KParams& p, int64_t steps, int nchunks, void* stream);
+int launch_walk_chunk(const KParams& p, int chunk_index, int grid, int warps_per_cta,
+                      size_t smem_bytes, void* stream);
+int walk_kernel_config(int warps_per_cta, size_t smem_bytes, int* ctas_per_sm);
+int launch_isl(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status,
+               void* stream);
+int launch_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status,
+                 void* stream);
+int launch_best(const KParams& p, int32_t L, void* stream);
+int launch_stats(const KParams& p, int32_t L, void* stream);
+int launch_trace_arm(const KParams& p, const int64_t* dev_ids, int32_t k, int32_t* code,
+                     int32_t* isl, int64_t capacity, void* stream);
+int launch_time_probe(unsigned long long* dev_out, void* stream);
+
+// Partial / final result of the exhaustive skew search (labs_enum.cu).
+struct EnumPart {
+    long long min_isl;
+    unsigned long long count;
+    unsigned long long first;
+    unsigned long long pad;
+};
+int enum_blocks(int L);
+size_t enum_scratch_bytes(int L);
+int enum_run(int L, EnumPart* scratch, void* stream, EnumPart* host_out);
+
+}  // namespace labsgpu

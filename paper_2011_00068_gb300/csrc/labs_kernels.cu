@@ -1,0 +1,868 @@
+// labs_kernels.cu -- sm_103a kernels of the skew-symmetric LABS search
+// (Brest & Boskovic, arXiv 2011.00068).
+//
+// One warp owns one walker (or one input row).  A walker's sequence is kept in shared
+// memory split by parity, because for even lags every term of the neighbourhood
+// evaluation pairs positions of equal parity:
+//   A0[u] = s_{2u}   (u = 0..n-1),   A1[u] = s_{2u+1}   (u = 0..n-2),
+// and its even-lag autocorrelations (odd lags vanish by Eq. 4) as the symmetric table
+//   E[d] = C_{2|d|}  (0 < |d| < n),  E[0] = 0.
+//
+// dISL of free variable i = 2v+p (class p, index v), q = L-1-i its mirror, c = n-1:
+//   flipping {i, q} changes C_k, k even, by dC_k = -4 s_i u_k with
+//   u_k = s_{i+k}[i+k != q] + s_{i-k} (out-of-range s = 0; the pair (i,q) is excluded
+//   because both of its ends flip), so with Eq. 2
+//   dISL_i = sum_k dC_k (2 C_k + dC_k)
+//          = -8 s_i (X_i - s_q C_{q-i}) + 16 (N_i - 1) + 32 (P_i - [3i >= L-1] s_q s_{3i-L+1})
+//   X_i = sum_{j != i, j = i mod 2} s_j C_{|j-i|}      (a Toeplitz product: X_v = sum_u A_p[u] E[u-v])
+//   P_i = sum_{k even, 2 <= k <= i} s_{i+k} s_{i-k}
+//   N_i = number of positions of the parity of i, minus one (n-1 for even i, n-2 for odd i).
+//   The centre flips alone: dC_k = -2 s_c (s_{c+k} + s_{c-k}), so
+//   dISL_c = -4 s_c X_c + 16 floor(c/2).
+// X costs n(n-1)/2 multiply-adds per class, i.e. about one per (flip, even lag) pair of
+// the neighbourhood (Algorithm 1's loop over the (L+1)/2 free variables), and is the hot
+// loop.  Lanes 0-15 hold the even class, lanes 16-31 the odd class; each lane owns R
+// consecutive outputs v0..v0+R-1 and slides a window of R values of E along u.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "labs_internal.cuh"
+
+namespace labsgpu {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11):
+// ten rounds of two 32x32->64 multiplies with a Weyl-sequence key schedule.
+__device__ __forceinline__ void philox(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
+                                       uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t hi0 = __umulhi(m0, c0), lo0 = m0 * c0;
+        uint32_t hi1 = __umulhi(m1, c2), lo1 = m1 * c2;
+        uint32_t y0 = hi1 ^ c1 ^ k0, y2 = hi0 ^ c3 ^ k1;
+        c0 = y0;
+        c1 = lo1;
+        c2 = y2;
+        c3 = lo0;
+    }
+}
+
+// Word j (j < 8) of the free-variable bits of start r of walker g: Philox block
+// (g, r, j/4, 0) under key (seed lo, seed hi), word j%4; bits >= n cleared.
+__device__ __forceinline__ uint32_t start_word(uint64_t seed, uint32_t g, uint32_t r, int j, int n)
+{
+    uint32_t c0 = g, c1 = r, c2 = (uint32_t)(j >> 2), c3 = 0u;
+    philox(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+    uint32_t w = (j & 3) == 0 ? c0 : (j & 3) == 1 ? c1 : (j & 3) == 2 ? c2 : c3;
+    int lo = 32 * j;
+    if (n <= lo) return 0u;
+    if (n - lo >= 32) return w;
+    return w & ((1u << (n - lo)) - 1u);
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void raise_error(DevStatus* st, int code, int detail)
+{
+    if (atomicCAS(&st->error, 0, code) == 0) st->error_detail = detail;
+}
+
+// Per-warp views of the shared-memory layout.
+struct View {
+    int* A0;  // A0[-apad .. n_max+apad)
+    int* A1;
+    int* E;   // E[-kEPad .. n_max+8)
+};
+
+__device__ __forceinline__ View make_view(int* base, const WarpSmem& L)
+{
+    View v;
+    v.A0 = base + L.apad;
+    v.A1 = base + L.alen + L.apad;
+    v.E = base + 2 * L.alen + kEPad;
+    return v;
+}
+
+__device__ __forceinline__ void clear_warp(int* base, const WarpSmem& L, int lane)
+{
+    int4* b4 = reinterpret_cast<int4*>(base);
+    for (int t = lane; t < L.words / 4; t += kWarp) b4[t] = make_int4(0, 0, 0, 0);
+    __syncwarp();
+}
+
+// Fills A0/A1 from the free-variable bits (word j of the bits lives in lane j's
+// `word`), by Eq. 4: s_j = x_j for j <= c, s_{c+t} = (-1)^t x_{c-t}.
+__device__ __forceinline__ void rows_from_bits(const View& V, uint32_t word, int L, int n, int lane)
+{
+    const int c = n - 1;
+    for (int j0 = 0; j0 < L; j0 += kWarp) {
+        int j = j0 + lane;
+        int f = j <= c ? j : 2 * c - j;
+        if (j >= L) f = 0;
+        uint32_t w = __shfl_sync(kFull, word, f >> 5);
+        if (j < L) {
+            int x = ((w >> (f & 31)) & 1u) ? -1 : 1;
+            int s = (j > c && ((j - c) & 1)) ? -x : x;
+            if (j & 1) V.A1[j >> 1] = s;
+            else V.A0[j >> 1] = s;
+        }
+    }
+    __syncwarp();
+}
+
+// Even-lag autocorrelations (Eq. 1) into E and the ISL (Eq. 2) from A0/A1.
+__device__ __forceinline__ int build_table(const View& V, int n, int lane)
+{
+    int part = 0;
+    for (int m = 1 + lane; m < n; m += kWarp) {
+        int d = 0;
+        for (int u = 0; u + m < n; ++u) d += V.A0[u] * V.A0[u + m];
+        for (int u = 0; u + m < n - 1; ++u) d += V.A1[u] * V.A1[u + m];
+        V.E[m] = d;
+        if (m <= kEPad) V.E[-m] = d;
+        part += d * d;
+    }
+    __syncwarp();
+    return __reduce_add_sync(kFull, part);
+}
+
+// The neighbourhood: dl[r] = dISL of free variable i = 2(v0+r)+p, or INT_MAX where
+// that output does not exist.  Formula in the header comment.
+template <int R>
+__device__ __forceinline__ void neighbourhood(const View& V, int n, int lane, int (&dl)[R])
+{
+    const int p = lane >> 4;
+    const int v0 = (lane & 15) * R;
+    const int* A = p ? V.A1 : V.A0;
+    const int nv = p ? (n >> 1) : ((n + 1) >> 1);
+    const int* E = V.E;
+
+    int acc[R], win[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        acc[r] = 0;
+        win[r] = E[-1 - v0 - r];
+    }
+    const int nu = (n + 3) & ~3;
+    for (int u = 0; u < nu; u += 4) {
+        const int4 a4 = *reinterpret_cast<const int4*>(A + u);
+        const int a[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+#pragma unroll
+            for (int r = R - 1; r > 0; --r) win[r] = win[r - 1];
+            win[0] = E[u + t - v0];
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] += a[t] * win[r];
+        }
+    }
+
+    const int c = n - 1;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = v0 + r;
+        if (v >= nv) {
+            dl[r] = INT_MAX;
+            continue;
+        }
+        const int i = 2 * v + p;
+        const int av = A[v];
+        if (i == c) {
+            dl[r] = -4 * av * acc[r] + 16 * (c >> 1);
+            continue;
+        }
+        int P = 0;
+        for (int m = 1; m <= v; ++m) P += A[v + m] * A[v - m];
+        const int vq = n - 1 - v - p;
+        const int sq = A[vq];
+        const int ck0 = E[c - i];
+        const int t = 3 * v + p - n + 1;
+        const int corr = t >= 0 ? sq * A[t] : 0;
+        const int N = p ? n - 2 : n - 1;
+        dl[r] = -8 * av * (acc[r] - sq * ck0) + 16 * (N - 1) + 32 * (P - corr);
+    }
+}
+
+// Rebuilds the walker's rows and table from its bits; returns the ISL.
+__device__ __forceinline__ int load_rows(int* base, const WarpSmem& SL, const View& V, uint32_t word,
+                                         int L, int n, int lane)
+{
+    clear_warp(base, SL, lane);
+    rows_from_bits(V, word, L, n, lane);
+    return build_table(V, n, lane);
+}
+
+// HT fingerprint (Zobrist): XOR of the keys of the free variables equal to -1.
+__device__ __forceinline__ uint64_t fingerprint_all(uint32_t word, const uint64_t* zk, int n, int lane)
+{
+    uint64_t f = 0;
+    const int nr = (n + kWarp - 1) & ~(kWarp - 1);
+    for (int i0 = 0; i0 < nr; i0 += kWarp) {
+        const int i = i0 + lane;
+        uint32_t w = __shfl_sync(kFull, word, i0 >> 5);
+        if (i < n && ((w >> (i & 31)) & 1u)) f ^= zk[i];
+    }
+    uint32_t lo = __reduce_xor_sync(kFull, (uint32_t)f);
+    uint32_t hi = __reduce_xor_sync(kFull, (uint32_t)(f >> 32));
+    return (uint64_t)lo | ((uint64_t)hi << 32);
+}
+
+// Registers of one walker while its warp runs it.
+struct Walker {
+    uint32_t word;   // lane j < 8: bits word j
+    uint64_t fp;
+    int isl, best_isl, since, stag;
+    uint32_t restart_idx, gen;
+    int restarts, overflows, blocked;
+    int64_t steps, best_step, target_step;
+};
+
+struct WalkEnv {
+    const KParams* p;
+    uint64_t* T;       // this walker's HT
+    uint64_t tmask;
+    const uint64_t* zk;
+    WalkerState* st;
+    int L, n, patience, lane;
+    uint32_t g;
+};
+
+__device__ __forceinline__ bool target_met(const KParams& p, int L, int isl)
+{
+    if (p.target_num <= 0 || p.target_den <= 0) return false;
+    return (int64_t)p.target_den * L * L >= 2 * (int64_t)p.target_num * isl;
+}
+
+__device__ __forceinline__ void note_best(const WalkEnv& env, Walker& w)
+{
+    if (w.isl < w.best_isl) {
+        w.best_isl = w.isl;
+        w.best_step = w.steps;
+        if (env.lane < kBitWords) env.st->best[env.lane] = w.word;
+    }
+    if (w.target_step < 0 && target_met(*env.p, env.L, w.isl)) w.target_step = w.steps;
+}
+
+// Algorithm 1 start: random skew-symmetric S (restart index w.restart_idx), its ISL,
+// insert it into HT (a fresh generation: its home slot is free), best update.
+__device__ void start_walker(const WalkEnv& env, Walker& w, int* base, const WarpSmem& SL, const View& V)
+{
+    const int lane = env.lane;
+    w.word = lane < kBitWords ? start_word(env.p->seed, env.g, w.restart_idx, lane, env.n) : 0u;
+    w.isl = load_rows(base, SL, V, w.word, env.L, env.n, lane);
+    w.fp = fingerprint_all(w.word, env.zk, env.n, lane);
+    if (lane == 0) env.T[w.fp & env.tmask] = (w.fp & ~kGenMask) | w.gen;
+    __syncwarp();
+    w.since = w.isl;
+    w.stag = 0;
+    note_best(env, w);
+}
+
+__device__ void restart_walker(const WalkEnv& env, Walker& w, int* base, const WarpSmem& SL,
+                               const View& V)
+{
+    w.restart_idx += 1;
+    w.restarts += 1;
+    w.gen += 1;
+    if (w.gen > kGenMask) {
+        const int64_t slots = (int64_t)env.tmask + 1;
+        for (int64_t t = env.lane; t < slots; t += kWarp) env.T[t] = 0ull;
+        __syncwarp();
+        w.gen = 1;
+    }
+    start_walker(env, w, base, SL, V);
+}
+
+// Warp-uniform: lane 0 reads the host-written control block and broadcasts.
+__device__ __forceinline__ int stop_requested(const KParams& p, int lane)
+{
+    int why = 0;
+    if (lane == 0 && p.ctrl != nullptr) {
+        if (p.ctrl->stop) why = LABS_ECANCELLED;
+        else if (global_ns() >= p.ctrl->deadline_ns) why = LABS_ETIMEOUT;
+    }
+    return __shfl_sync(kFull, why, 0);
+}
+
+template <int R>
+__device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* base, const WarpSmem& SL,
+                           const View& V, int trace_slot, int64_t trace_start)
+{
+    const KParams& p = *env.p;
+    const int lane = env.lane, n = env.n, c = n - 1;
+    const int pcls = lane >> 4, v0 = (lane & 15) * R;
+    const int cap = p.probe_cap;
+    while (w.steps < until) {
+        if ((w.steps & (kCheckEvery - 1)) == 0) {
+            const int why = stop_requested(p, lane);
+            if (why) {
+                if (lane == 0) raise_error(p.status, why, (int)env.g);
+                break;
+            }
+        }
+        int dl[R];
+        neighbourhood<R>(V, n, lane, dl);
+
+        // best admissible flip: lowest (dISL, i) whose result is not in HT
+        uint32_t excl = 0;
+        int best_i = -1, best_d = 0;
+        int64_t slot = -1;
+        uint64_t fnew = 0;
+        for (;;) {
+            int lm = INT_MAX, li = INT_MAX;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (!((excl >> r) & 1u) && dl[r] < lm) {
+                    lm = dl[r];
+                    li = 2 * (v0 + r) + pcls;
+                }
+            const int mn = __reduce_min_sync(kFull, lm);
+            if (mn == INT_MAX) break;
+            const int bi = __reduce_min_sync(kFull, lm == mn ? li : INT_MAX);
+            const uint64_t f = w.fp ^ env.zk[bi];
+            const uint64_t tag = (f & ~kGenMask) | w.gen;
+            uint64_t e = 0;
+            if (lane < cap) e = env.T[(f + (uint64_t)lane) & env.tmask];
+            const bool stale = (e & kGenMask) != w.gen;
+            const bool match = e == tag;
+            const unsigned bal = __ballot_sync(kFull, lane < cap && (stale || match));
+            bool visited = false;
+            int64_t sl = -1;
+            if (bal) {
+                const int fl = __ffs(bal) - 1;
+                visited = __shfl_sync(kFull, match ? 1 : 0, fl) != 0;
+                sl = (int64_t)((f + (uint64_t)fl) & env.tmask);
+            }
+            if (!visited) {
+                best_i = bi;
+                best_d = mn;
+                slot = sl;
+                fnew = f;
+                break;
+            }
+            const int vb = bi >> 1, pb = bi & 1;
+            if (lane == pb * 16 + vb / R) excl |= 1u << (vb % R);
+        }
+
+        w.steps += 1;
+        int code;
+        if (best_i < 0) {
+            // Every neighbour is in HT: restart without a move.
+            w.blocked += 1;
+            restart_walker(env, w, base, SL, V);
+            code = LABS_TRACE_BLOCKED;
+        } else {
+            // S <- S_f: update the table, then the rows.
+            const int pb = best_i & 1, vb = best_i >> 1;
+            int* Ab = pb ? V.A1 : V.A0;
+            const int as = Ab[vb];
+            const bool centre = best_i == c;
+            const int vq = n - 1 - vb - pb;
+            int dd[kMaxN / kWarp];
+#pragma unroll
+            for (int t = 0; t < kMaxN / kWarp; ++t) {
+                const int m = lane + 1 + kWarp * t;
+                dd[t] = 0;
+                if (m < n) {
+                    int up = Ab[vb + m];
+                    if (!centre && vb + m == vq) up = 0;
+                    const int dn = Ab[vb - m];
+                    dd[t] = (centre ? -2 : -4) * as * (up + dn);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < kMaxN / kWarp; ++t) {
+                const int m = lane + 1 + kWarp * t;
+                if (m < n) {
+                    V.E[m] += dd[t];
+                    if (m <= kEPad) V.E[-m] += dd[t];
+                }
+            }
+            if (lane == 0) {
+                Ab[vb] = -as;
+                if (!centre) Ab[vq] = -Ab[vq];
+            }
+            const bool stored = slot >= 0;
+            if (lane == 0 && stored) env.T[slot] = (fnew & ~kGenMask) | w.gen;
+            if (lane == (best_i >> 5)) w.word ^= 1u << (best_i & 31);
+            __syncwarp();
+            w.fp = fnew;
+            w.isl += best_d;
+            if (!stored) w.overflows += 1;
+            note_best(env, w);
+            if (w.isl < w.since) {
+                w.since = w.isl;
+                w.stag = 0;
+            } else {
+                w.stag += 1;
+            }
+            code = best_i;
+            if (w.stag >= env.patience || !stored) {
+                restart_walker(env, w, base, SL, V);
+                code |= LABS_TRACE_RESTART;
+            }
+        }
+        if (trace_slot >= 0 && lane == 0) {
+            const int64_t t = w.steps - 1 - trace_start;
+            if (t >= 0 && t < p.status->trace_capacity) {
+                p.status->trace_code[trace_slot * p.status->trace_capacity + t] = code;
+                p.status->trace_isl[trace_slot * p.status->trace_capacity + t] = w.isl;
+            }
+        }
+    }
+}
+
+__device__ void load_walker(const WalkerState* st, Walker& w, int lane)
+{
+    w.word = lane < kBitWords ? st->cur[lane] : 0u;
+    w.fp = st->fp;
+    w.isl = st->isl;
+    w.best_isl = st->best_isl;
+    w.since = st->since_best;
+    w.stag = st->stagnation;
+    w.restart_idx = st->restart_idx;
+    w.gen = st->gen;
+    w.restarts = st->restarts;
+    w.overflows = st->overflows;
+    w.blocked = st->blocked;
+    w.steps = st->steps_done;
+    w.best_step = st->best_step;
+    w.target_step = st->target_step;
+}
+
+__device__ void save_walker(WalkerState* st, const Walker& w, int lane)
+{
+    if (lane < kBitWords) st->cur[lane] = w.word;
+    if (lane == 0) {
+        st->fp = w.fp;
+        st->isl = w.isl;
+        st->best_isl = w.best_isl;
+        st->since_best = w.since;
+        st->stagnation = w.stag;
+        st->restart_idx = w.restart_idx;
+        st->gen = w.gen;
+        st->restarts = w.restarts;
+        st->overflows = w.overflows;
+        st->blocked = w.blocked;
+        st->steps_done = w.steps;
+        st->best_step = w.best_step;
+        st->target_step = w.target_step;
+    }
+}
+
+__device__ __forceinline__ int lanes_R(int n)
+{
+    return (((n + 1) >> 1) + 15) >> 4;
+}
+
+template <int R>
+__device__ void run_chunk(const WalkEnv& env, Walker& w, int64_t until, int* base, const WarpSmem& SL,
+                          const View& V, int trace_slot, int64_t trace_start)
+{
+    walk_steps<R>(env, w, until, base, SL, V, trace_slot, trace_start);
+}
+
+__global__ void __launch_bounds__(512) walk_chunk_kernel(KParams p, int chunk_index)
+{
+    extern __shared__ __align__(16) int smem[];
+    const WarpSmem SL = warp_smem(p.n_max);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int* base = smem + warp * SL.words;
+    const View V = make_view(base, SL);
+    const int64_t target = p.status->target_steps;
+    for (;;) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(&p.queue[chunk_index], 1u);
+        const int64_t wi = (int64_t)__shfl_sync(kFull, t, 0);
+        if (wi >= p.W) break;
+        WalkerState* st = p.states + wi;
+        const int64_t steps_done = st->steps_done;
+        const int64_t until = min(target, steps_done + (int64_t)p.chunk_steps);
+        if (steps_done >= until) continue;
+        const DevGroup G = p.groups[st->group];
+        WalkEnv env;
+        env.p = &p;
+        env.tmask = (1ull << p.tabu_log2) - 1ull;
+        env.T = p.tabu + ((uint64_t)wi << p.tabu_log2);
+        env.zk = p.zkeys + G.zkey_off;
+        env.st = st;
+        env.L = G.L;
+        env.n = G.n;
+        env.patience = p.patience > 0 ? p.patience : 2 * G.n;
+        env.lane = lane;
+        env.g = (uint32_t)wi;
+        Walker w;
+        load_walker(st, w, lane);
+        const int trace_slot = st->trace_slot;
+        const int64_t trace_start = trace_slot >= 0 ? p.trace_start[trace_slot] : 0;
+        const int isl = load_rows(base, SL, V, w.word, G.L, G.n, lane);
+        if (isl != w.isl) {
+            if (lane == 0) raise_error(p.status, LABS_ESTATE, (int)wi);
+            continue;
+        }
+        switch (lanes_R(G.n)) {
+            case 1: run_chunk<1>(env, w, until, base, SL, V, trace_slot, trace_start); break;
+            case 2: run_chunk<2>(env, w, until, base, SL, V, trace_slot, trace_start); break;
+            case 3: run_chunk<3>(env, w, until, base, SL, V, trace_slot, trace_start); break;
+            case 4: run_chunk<4>(env, w, until, base, SL, V, trace_slot, trace_start); break;
+            case 5: run_chunk<5>(env, w, until, base, SL, V, trace_slot, trace_start); break;
+            case 6: run_chunk<6>(env, w, until, base, SL, V, trace_slot, trace_start); break;
+            case 7: run_chunk<7>(env, w, until, base, SL, V, trace_slot, trace_start); break;
+            default: run_chunk<8>(env, w, until, base, SL, V, trace_slot, trace_start); break;
+        }
+        save_walker(st, w, lane);
+        __syncwarp();
+    }
+}
+
+// Start of every walker (restart index 0, HT generation 1; HT zeroed by the caller).
+__global__ void __launch_bounds__(512) reset_kernel(KParams p)
+{
+    extern __shared__ __align__(16) int smem[];
+    const WarpSmem SL = warp_smem(p.n_max);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int* base = smem + warp * SL.words;
+    const View V = make_view(base, SL);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t wi = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; wi < p.W; wi += nwarps) {
+        int gidx = 0;
+        for (int g = 0; g < p.nG; ++g)
+            if (wi >= p.groups[g].first && wi < p.groups[g].first + p.groups[g].count) gidx = g;
+        const DevGroup G = p.groups[gidx];
+        WalkerState* st = p.states + wi;
+        WalkEnv env;
+        env.p = &p;
+        env.tmask = (1ull << p.tabu_log2) - 1ull;
+        env.T = p.tabu + ((uint64_t)wi << p.tabu_log2);
+        env.zk = p.zkeys + G.zkey_off;
+        env.st = st;
+        env.L = G.L;
+        env.n = G.n;
+        env.patience = p.patience > 0 ? p.patience : 2 * G.n;
+        env.lane = lane;
+        env.g = (uint32_t)wi;
+        Walker w;
+        w.restart_idx = 0;
+        w.gen = 1;
+        w.restarts = w.overflows = w.blocked = 0;
+        w.steps = 0;
+        w.best_isl = INT_MAX;
+        w.best_step = 0;
+        w.target_step = -1;
+        start_walker(env, w, base, SL, V);
+        save_walker(st, w, lane);
+        if (lane == 0) {
+            st->group = gidx;
+            st->trace_slot = -1;
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void prep_walk_kernel(DevStatus* st, uint32_t* queue, int64_t steps, int nchunks)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->target_steps += steps;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nchunks; j += gridDim.x * blockDim.x)
+        queue[j] = 0u;
+}
+
+__global__ void zobrist_kernel(uint64_t* zkeys, int64_t off, int L, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t c0 = (uint32_t)i, c1 = (uint32_t)L, c2 = 0u, c3 = 2u;
+    philox(c0, c1, c2, c3, kZobristKey0, kZobristKey1);
+    zkeys[off + i] = (uint64_t)c0 | ((uint64_t)c1 << 32);
+}
+
+// --------------------------------------------------------- batch kernels (rows)
+
+// Eq. 2 for arbitrary +-1 rows, one warp per row.
+__global__ void __launch_bounds__(256) isl_kernel(const int8_t* __restrict__ seqs, int64_t batch, int L,
+                                                  int32_t* __restrict__ out, DevStatus* status)
+{
+    extern __shared__ __align__(16) int smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int stride = (L + 3) & ~3;
+    int* s = smem + warp * stride;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < batch; row += nwarps) {
+        const int8_t* src = seqs + row * (int64_t)L;
+        bool ok = true;
+        for (int j = lane; j < L; j += kWarp) {
+            const int v = src[j];
+            ok = ok && (v == 1 || v == -1);
+            s[j] = v;
+        }
+        __syncwarp();
+        const bool all_ok = __all_sync(kFull, ok);
+        int part = 0;
+        if (all_ok) {
+            for (int k = 1 + lane; k < L; k += kWarp) {
+                int ck = 0;
+                for (int j = 0; j + k < L; ++j) ck += s[j] * s[j + k];
+                part += ck * ck;
+            }
+        }
+        const int e = __reduce_add_sync(kFull, part);
+        if (lane == 0) {
+            out[row] = all_ok ? e : -1;
+            if (!all_ok && status) atomicAdd(&status->invalid_rows, 1);
+        }
+        __syncwarp();
+    }
+}
+
+template <int R>
+__device__ void delta_row(const View& V, int n, int lane, int32_t* dst)
+{
+    int dl[R];
+    neighbourhood<R>(V, n, lane, dl);
+    const int p = lane >> 4, v0 = (lane & 15) * R;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (dl[r] != INT_MAX) dst[2 * (v0 + r) + p] = dl[r];
+}
+
+// The neighbourhood of Algorithm 1 for skew-symmetric rows, one warp per row.
+__global__ void __launch_bounds__(256) delta_kernel(const int8_t* __restrict__ seqs, int64_t batch, int L,
+                                                    int32_t* __restrict__ out, DevStatus* status)
+{
+    extern __shared__ __align__(16) int smem[];
+    const int n = (L + 1) / 2, c = n - 1;
+    const WarpSmem SL = warp_smem(n);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int* base = smem + warp * SL.words;
+    const View V = make_view(base, SL);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int R = lanes_R(n);
+    for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < batch; row += nwarps) {
+        clear_warp(base, SL, lane);
+        const int8_t* src = seqs + row * (int64_t)L;
+        bool ok = true;
+        for (int j = lane; j < L; j += kWarp) {
+            const int v = src[j];
+            ok = ok && (v == 1 || v == -1);
+            if (j & 1) V.A1[j >> 1] = v;
+            else V.A0[j >> 1] = v;
+        }
+        __syncwarp();
+        for (int j = 1 + lane; j <= c; j += kWarp) {  // Eq. 4
+            const int hi = c + j, lo = c - j;
+            const int shi = (hi & 1) ? V.A1[hi >> 1] : V.A0[hi >> 1];
+            const int slo = (lo & 1) ? V.A1[lo >> 1] : V.A0[lo >> 1];
+            ok = ok && (shi == ((j & 1) ? -slo : slo));
+        }
+        int32_t* dst = out + row * (int64_t)n;
+        if (!__all_sync(kFull, ok)) {
+            for (int i = lane; i < n; i += kWarp) dst[i] = INT_MIN;
+            if (lane == 0 && status) atomicAdd(&status->invalid_rows, 1);
+            __syncwarp();
+            continue;
+        }
+        build_table(V, n, lane);
+        switch (R) {
+            case 1: delta_row<1>(V, n, lane, dst); break;
+            case 2: delta_row<2>(V, n, lane, dst); break;
+            case 3: delta_row<3>(V, n, lane, dst); break;
+            case 4: delta_row<4>(V, n, lane, dst); break;
+            case 5: delta_row<5>(V, n, lane, dst); break;
+            case 6: delta_row<6>(V, n, lane, dst); break;
+            case 7: delta_row<7>(V, n, lane, dst); break;
+            default: delta_row<8>(V, n, lane, dst); break;
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------ reductions, tracing
+
+__global__ void best_kernel(KParams p, int L)
+{
+    for (int64_t wi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; wi < p.W;
+         wi += (int64_t)gridDim.x * blockDim.x) {
+        const WalkerState& st = p.states[wi];
+        if (L != 0 && p.groups[st.group].L != L) continue;
+        const unsigned long long key = ((unsigned long long)(uint32_t)st.best_isl << 32) |
+                                       (unsigned long long)(uint32_t)wi;
+        atomicMin(&p.status->best_key, key);
+    }
+}
+
+__global__ void stats_kernel(KParams p, int L)
+{
+    for (int64_t wi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; wi < p.W;
+         wi += (int64_t)gridDim.x * blockDim.x) {
+        const WalkerState& st = p.states[wi];
+        const DevGroup& G = p.groups[st.group];
+        if (L != 0 && G.L != L) continue;
+        DevStatus* s = p.status;
+        atomicAdd(&s->st_steps, (unsigned long long)st.steps_done);
+        atomicAdd(&s->st_evals, (unsigned long long)st.steps_done * (unsigned long long)G.n);
+        atomicAdd(&s->st_restarts, (unsigned long long)st.restarts);
+        atomicAdd(&s->st_overflows, (unsigned long long)st.overflows);
+        atomicAdd(&s->st_blocked, (unsigned long long)st.blocked);
+        if (st.target_step >= 0) {
+            atomicAdd(&s->st_at_target, 1ull);
+            atomicMin(&s->st_target_step, (long long)st.target_step);
+        }
+        const unsigned long long key = ((unsigned long long)(uint32_t)st.best_isl << 32) |
+                                       (unsigned long long)(uint32_t)wi;
+        atomicMin(&s->best_key, key);
+    }
+}
+
+__global__ void trace_clear_kernel(KParams p)
+{
+    for (int64_t wi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; wi < p.W;
+         wi += (int64_t)gridDim.x * blockDim.x)
+        p.states[wi].trace_slot = -1;
+}
+
+__global__ void trace_set_kernel(KParams p, const int64_t* ids, int k, int32_t* code, int32_t* isl,
+                                 int64_t capacity)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j == 0) {
+        p.status->trace_code = code;
+        p.status->trace_isl = isl;
+        p.status->trace_capacity = capacity;
+    }
+    if (j < k) {
+        const int64_t wi = ids[j];
+        p.states[wi].trace_slot = j;
+        p.trace_start[j] = p.states[wi].steps_done;
+    }
+}
+
+__global__ void time_probe_kernel(unsigned long long* out)
+{
+    *out = global_ns();
+}
+
+int status_of(cudaError_t e)
+{
+    return e == cudaSuccess ? LABS_OK : LABS_ECUDA;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------- launchers
+
+int launch_zobrist(const KParams&, uint64_t* zkeys, const DevGroup* host_groups, int nG, void* stream)
+{
+    for (int g = 0; g < nG; ++g) {
+        const DevGroup& G = host_groups[g];
+        zobrist_kernel<<<(G.n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(zkeys, G.zkey_off, G.L, G.n);
+    }
+    return status_of(cudaGetLastError());
+}
+
+int launch_reset(const KParams& p, int grid, int block, void* stream)
+{
+    const size_t smem = (size_t)(block / kWarp) * warp_smem(p.n_max).words * sizeof(int);
+    cudaFuncSetAttribute(reset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    reset_kernel<<<grid, block, smem, (cudaStream_t)stream>>>(p);
+    return status_of(cudaGetLastError());
+}
+
+int launch_prep_walk(const KParams& p, int64_t steps, int nchunks, void* stream)
+{
+    prep_walk_kernel<<<(nchunks + 255) / 256, 256, 0, (cudaStream_t)stream>>>(p.status, p.queue, steps,
+                                                                              nchunks);
+    return status_of(cudaGetLastError());
+}
+
+int walk_kernel_config(int warps_per_cta, size_t smem_bytes, int* ctas_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(walk_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes);
+    if (e != cudaSuccess) return LABS_ECUDA;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, walk_chunk_kernel, warps_per_cta * kWarp,
+                                                      smem_bytes);
+    return status_of(e);
+}
+
+int launch_walk_chunk(const KParams& p, int chunk_index, int grid, int warps_per_cta, size_t smem_bytes,
+                      void* stream)
+{
+    walk_chunk_kernel<<<grid, warps_per_cta * kWarp, smem_bytes, (cudaStream_t)stream>>>(p, chunk_index);
+    return status_of(cudaGetLastError());
+}
+
+static int row_grid(int64_t batch, int warps)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t need = (batch + warps - 1) / warps;
+    int64_t cap = (int64_t)sms * 8;
+    return (int)(need < cap ? need : cap);
+}
+
+int launch_isl(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status, void* stream)
+{
+    if (batch == 0) return LABS_OK;
+    const int warps = 8;
+    const size_t smem = (size_t)warps * ((L + 3) & ~3) * sizeof(int);
+    isl_kernel<<<row_grid(batch, warps), warps * kWarp, smem, (cudaStream_t)stream>>>(seqs, batch, L, out,
+                                                                                       status);
+    return status_of(cudaGetLastError());
+}
+
+int launch_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status, void* stream)
+{
+    if (batch == 0) return LABS_OK;
+    const int warps = 8;
+    const size_t smem = (size_t)warps * warp_smem((L + 1) / 2).words * sizeof(int);
+    cudaFuncSetAttribute(delta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    delta_kernel<<<row_grid(batch, warps), warps * kWarp, smem, (cudaStream_t)stream>>>(seqs, batch, L, out,
+                                                                                         status);
+    return status_of(cudaGetLastError());
+}
+
+int launch_best(const KParams& p, int32_t L, void* stream)
+{
+    best_kernel<<<256, 256, 0, (cudaStream_t)stream>>>(p, L);
+    return status_of(cudaGetLastError());
+}
+
+int launch_stats(const KParams& p, int32_t L, void* stream)
+{
+    stats_kernel<<<256, 256, 0, (cudaStream_t)stream>>>(p, L);
+    return status_of(cudaGetLastError());
+}
+
+int launch_trace_arm(const KParams& p, const int64_t* dev_ids, int32_t k, int32_t* code, int32_t* isl,
+                     int64_t capacity, void* stream)
+{
+    trace_clear_kernel<<<256, 256, 0, (cudaStream_t)stream>>>(p);
+    trace_set_kernel<<<(k + 255) / 256 + 1, 256, 0, (cudaStream_t)stream>>>(p, dev_ids, k, code, isl, capacity);
+    return status_of(cudaGetLastError());
+}
+
+int launch_time_probe(unsigned long long* dev_out, void* stream)
+{
+    time_probe_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(dev_out);
+    return status_of(cudaGetLastError());
+}
+
+}  // namespace labsgpu
