@@ -43,8 +43,8 @@ def parse():
     ap.add_argument("--walk-steps", type=int, default=10000)
     ap.add_argument("--tabu-log2", type=int, default=16)
     ap.add_argument("--seed", type=int, default=7)
-    ap.add_argument("--cpu-walkers", type=int, default=64)
-    ap.add_argument("--cpu-steps", type=int, default=1000)
+    ap.add_argument("--cpu-walkers", type=int, default=128)
+    ap.add_argument("--cpu-steps", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
