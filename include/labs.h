@@ -176,6 +176,25 @@ int labs_enumerate_scratch_bytes(int32_t L, size_t *bytes);
 int labs_enumerate(int32_t L, void *dev_scratch, size_t scratch_bytes, int64_t *min_isl,
                    uint64_t *count, uint64_t *first_assignment, void *cuda_stream);
 
+/* Allocation-free form of labs_enumerate (the paper has no counterpart: it is a
+ * library convenience).  It is for callers that cannot allocate device memory when
+ * they call: for example a real-time signal chain that reserves all of its GPU memory
+ * at start-up and must not call cudaMalloc later (it can synchronise the device and
+ * has no latency bound), or a plugin whose host owns every device allocation.
+ * Same arguments and results as labs_enumerate minus the scratch buffer: the scratch
+ * lives in a fixed array inside the library, 33,280 bytes, which every GPU that loads
+ * the library holds until the process exits.  It fits every L the call accepts
+ * (odd 3 <= L <= 63, at most 1025 partial results); LABS_EINVAL for other L and
+ * LABS_ENOMEM if a length ever needed more than the array holds.  The call allocates
+ * nothing (no cudaMalloc / cudaFree / allocating library routine); it clears the part
+ * of the array it uses, then runs on cuda_stream and synchronises it.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current, so make that first call before any stream capture.  All calls share
+ * the one array: calls that overlap on the GPU (from several host threads or streams)
+ * race and give wrong results. */
+int labs_enumerate_noalloc(int32_t L, int64_t *min_isl, uint64_t *count,
+                           uint64_t *first_assignment, void *cuda_stream);
+
 /* Checkpoint of every walker's state (sequence, ISL, best, counters, random-stream
  * position) and, with with_tabu != 0, its HT.  With the HT included a restored run
  * continues bit-identically; without it the HT restarts empty.  host_buf NULL queries

@@ -33,7 +33,7 @@ EXPORTS = [
     "labs_default_config", "labs_init", "labs_init_multi", "labs_workspace_bytes", "labs_bind_workspace",
     "labs_reset", "labs_isl", "labs_neighbor_delta", "labs_walk", "labs_sync", "labs_best",
     "labs_walker_results", "labs_stats", "labs_trace", "labs_enumerate_scratch_bytes", "labs_enumerate",
-    "labs_checkpoint", "labs_restore", "labs_set_deadline", "labs_cancel", "labs_clear_stop",
+    "labs_enumerate_noalloc", "labs_checkpoint", "labs_restore", "labs_set_deadline", "labs_cancel", "labs_clear_stop",
     "labs_last_error", "labs_destroy",
 ]
 
@@ -98,6 +98,7 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
             "labs_trace": (ctypes.c_int, [P, P, i32, i64, P, P]),
             "labs_enumerate_scratch_bytes": (ctypes.c_int, [i32, ctypes.POINTER(sz)]),
             "labs_enumerate": (ctypes.c_int, [i32, P, sz, P, P, P, P]),
+            "labs_enumerate_noalloc": (ctypes.c_int, [i32, P, P, P, P]),
             "labs_checkpoint": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.POINTER(sz)]),
             "labs_restore": (ctypes.c_int, [P, P, sz]),
             "labs_set_deadline": (ctypes.c_int, [P, u64]),

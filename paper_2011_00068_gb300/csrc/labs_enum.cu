@@ -11,6 +11,7 @@
 
 #include <climits>
 #include <cstdint>
+#include <mutex>
 
 #include "labs_internal.cuh"
 
@@ -173,4 +174,54 @@ int enum_run(int L, EnumPart* scratch, void* stream, EnumPart* host_out)
     return LABS_OK;
 }
 
+// ------------------------------------------------ allocation-free variant
+//
+// labs_enumerate_noalloc runs the same two kernels with their scratch (the per-block
+// partial results and the final result) in the file-scope array below instead of a
+// caller buffer.  The array is part of the library image: every GPU that loads the
+// library holds its kNoAllocParts * 32 bytes (33,280 bytes) until the process exits.
+// Host code cannot use the array's name as a device address, so the first call on
+// each device looks the address up with cudaGetSymbolAddress (with that device
+// current) and keeps it per device.
+constexpr int kNoAllocParts = 1040;  // enum_blocks(63) + 1 = 1025 fit
+constexpr int kNoAllocDevices = 64;
+static __device__ __align__(256) EnumPart g_noalloc_scratch[kNoAllocParts];
+
+namespace {
+std::mutex g_noalloc_mutex;
+EnumPart* g_noalloc_addr[kNoAllocDevices] = {};
+}  // namespace
+
 }  // namespace labsgpu
+
+extern "C" int labs_enumerate_noalloc(int32_t L, int64_t* min_isl, uint64_t* count, uint64_t* first_assignment,
+                                      void* cuda_stream)
+{
+    using namespace labsgpu;
+    if (L < 3 || L > 63 || (L & 1) == 0) return LABS_EINVAL;
+    const int blocks = enum_blocks(L);
+    if (blocks + 1 > kNoAllocParts) return LABS_ENOMEM;  // needs more scratch than the static array holds
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LABS_ECUDA;
+    if (dev < 0 || dev >= kNoAllocDevices) return LABS_EINVAL;
+    EnumPart* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (g_noalloc_addr[dev] == nullptr) {
+            void* addr = nullptr;
+            if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || addr == nullptr) return LABS_ECUDA;
+            g_noalloc_addr[dev] = static_cast<EnumPart*>(addr);
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    // The array keeps the previous call's contents; clear the part this call uses.
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (cudaMemsetAsync(scratch, 0, sizeof(EnumPart) * (size_t)(blocks + 1), s) != cudaSuccess) return LABS_ECUDA;
+    EnumPart r;
+    const int rc = enum_run(L, scratch, cuda_stream, &r);
+    if (rc) return rc;
+    if (min_isl) *min_isl = r.min_isl;
+    if (count) *count = r.count;
+    if (first_assignment) *first_assignment = r.first;
+    return LABS_OK;
+}
