@@ -65,7 +65,7 @@ typedef struct labs_config {
     int32_t target_num;      /* time-to-target threshold F >= target_num/target_den; */
     int32_t target_den;      /* default 17/2 (F >= 8.5); 0/0 disables it */
     int32_t chunk_steps;     /* steps per kernel launch inside labs_walk; 0 = auto */
-    int32_t warps_per_cta;   /* walkers resident per CTA (one warp each); 0 = tuned */
+    int32_t warps_per_cta;   /* walkers resident per CTA (one warp each), 1..8; 0 = 8 */
     int32_t flags;           /* LABS_FLAG_* */
 } labs_config;
 

@@ -71,7 +71,10 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
     with _lock:
         if _lib is not None:
             return _lib
-        if build_if_needed:
+        override = os.environ.get("LABS_LIBRARY")
+        if override:
+            path = override  # a separately built variant of the same sources
+        elif build_if_needed:
             path = _build.build()
         else:
             path = _build.LIB

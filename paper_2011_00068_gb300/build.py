@@ -40,9 +40,11 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if up_to_date() and not force:
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, out: str | None = None) -> str:
+    """Compiles the library (to `out`, default _build/liblabs.so); `extra` nvcc flags."""
+    if out is None and up_to_date() and not force:
         return LIB
+    target = out or LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     cc = nvcc()
     flags = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
@@ -51,7 +53,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         flags += ["-Xptxas", "-v"]
     procs, objs = [], []
     for s in SOURCES:
-        obj = os.path.join(OUT_DIR, s.replace(".cu", ".o"))
+        obj = os.path.join(OUT_DIR, s.replace(".cu", ".%d.o" % os.getpid()))
         objs.append(obj)
         procs.append((s, subprocess.Popen([cc, *flags, "-c", os.path.join(CSRC, s), "-o", obj],
                                           stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -64,12 +66,17 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             failed.append(s)
     if failed:
         raise RuntimeError("nvcc failed on " + ", ".join(failed))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = target + ".%d.tmp" % os.getpid()
     rpath = "-Xlinker=-rpath,/usr/local/cuda/lib64"
     subprocess.run([cc, *ARCH, "-shared", "-cudart", "shared", rpath, *objs, "-o", tmp], check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, target)
+    for o in objs:
+        os.remove(o)
+    return target
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    args = sys.argv[1:]
+    out = args[args.index("--out") + 1] if "--out" in args else None
+    extra = [a for a in args if a.startswith("-D")]
+    print(build(force="--force" in args, verbose="-v" in args, extra=extra, out=out))

@@ -35,7 +35,7 @@ struct labs_ctx {
     Control* ctrl_host = nullptr;
     Control* ctrl_dev = nullptr;
     long long gpu_minus_host_ns = 0;
-    int warps_per_cta = 0, ctas_per_sm = 0, grid = 0, chunk = 0;
+    int warps_per_cta = 0, ctas_per_sm = 0, grid = 0, chunk = 0, regs = 0;
     size_t smem_bytes = 0;
     bool catch_up = false;
     int64_t planned = 0;
@@ -103,6 +103,7 @@ KParams params(labs_ctx* c)
     p.target_num = c->cfg.target_num;
     p.target_den = c->cfg.target_den;
     p.chunk_steps = c->chunk;
+    p.rmax = lanes_for(c->n_max);
     p.seed = c->seed;
     return p;
 }
@@ -156,8 +157,8 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     labs_config& k = c->cfg;
     if (k.tabu_log2 < 1 || k.tabu_log2 > 20) return fail(c, LABS_EINVAL, "tabu_log2 must be 1..20");
     if (k.probe_cap < 1 || k.probe_cap > 32) return fail(c, LABS_EINVAL, "probe_cap must be 1..32");
-    if (k.patience < 0 || k.chunk_steps < 0 || k.warps_per_cta < 0 || k.warps_per_cta > 16)
-        return fail(c, LABS_EINVAL, "bad patience / chunk_steps / warps_per_cta");
+    if (k.patience < 0 || k.chunk_steps < 0 || k.warps_per_cta < 0 || k.warps_per_cta > 8)
+        return fail(c, LABS_EINVAL, "bad patience / chunk_steps / warps_per_cta (0..8)");
     if (nL < 1 || nL > LABS_MAX_GROUPS) return fail(c, LABS_EINVAL, "need 1..%d lengths", LABS_MAX_GROUPS);
     c->seed = seed;
     c->stream = (cudaStream_t)stream;
@@ -207,7 +208,7 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     for (;;) {
         c->smem_bytes = per_warp * (size_t)warps;
         int occ = 0;
-        if (walk_kernel_config(warps, c->smem_bytes, &occ) == LABS_OK && occ > 0) {
+        if (walk_kernel_config(lanes_for(c->n_max), warps, c->smem_bytes, &occ, &c->regs) == LABS_OK && occ > 0) {
             c->ctas_per_sm = occ;
             break;
         }

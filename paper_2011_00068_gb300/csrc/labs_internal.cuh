@@ -94,6 +94,7 @@ struct KParams {
     int32_t patience;         // 0 = 2n
     int32_t target_num, target_den;
     int32_t chunk_steps;
+    int32_t rmax;             // lane block of the walk kernel instantiation (lanes_for(n_max))
     uint64_t seed;
 };
 
@@ -125,7 +126,8 @@ int launch_reset(const KParams& p, int grid, int block, void* stream);
 int launch_prep_walk(const KParams& p, int64_t steps, int nchunks, void* stream);
 int launch_walk_chunk(const KParams& p, int chunk_index, int grid, int warps_per_cta,
                       size_t smem_bytes, void* stream);
-int walk_kernel_config(int warps_per_cta, size_t smem_bytes, int* ctas_per_sm);
+int walk_kernel_config(int rmax, int warps_per_cta, size_t smem_bytes, int* ctas_per_sm, int* regs);
+int lanes_for(int n);  // outputs per lane for n free variables: ceil(ceil(n/2) / 16)
 int launch_isl(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status,
                void* stream);
 int launch_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status,

@@ -36,6 +36,10 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+#ifndef LABS_WALK_MIN_BLOCKS
+#define LABS_WALK_MIN_BLOCKS 2  // CTAs of 8 warps per SM the walk kernel is compiled for (2 measured fastest)
+#endif
+
 // ------------------------------------------------------------------ Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11):
 // ten rounds of two 32x32->64 multiplies with a Weyl-sequence key schedule.
@@ -143,38 +147,136 @@ __device__ __forceinline__ int build_table(const View& V, int n, int lane)
     return __reduce_add_sync(kFull, part);
 }
 
-// The neighbourhood: dl[r] = dISL of free variable i = 2(v0+r)+p, or INT_MAX where
-// that output does not exist.  Formula in the header comment.
+// X_v = sum_u A_p[u] E[u-v] for the lane's R outputs v = v0..v0+R-1 (the Toeplitz
+// product).  The window of E slides one position per u.  When R is a multiple of 4
+// the lane's block starts on a 16-byte boundary and E is read four values at a time
+// (the 16 distinct blocks of a half-warp are then contiguous: no bank conflicts);
+// for other R the scalar reads have an odd or conflict-free stride.
 template <int R>
-__device__ __forceinline__ void neighbourhood(const View& V, int n, int lane, int (&dl)[R])
+__device__ __forceinline__ void toeplitz(const View& V, int n, int lane, int (&acc)[R])
+{
+    const int p = lane >> 4;
+    const int v0 = (lane & 15) * R;
+    const int* A = p ? V.A1 : V.A0;
+    const int* E = V.E;
+    const int nu = (n + 3) & ~3;
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0;
+    if constexpr (R % 4 == 0) {
+        // win[j] = E[u - v0 - R + j], j = 0 .. R+3
+        int win[R + 4];
+#pragma unroll
+        for (int c = 0; c < R / 4; ++c) {
+            const int4 q = *reinterpret_cast<const int4*>(E - v0 - R + 4 * c);
+            win[4 * c] = q.x;
+            win[4 * c + 1] = q.y;
+            win[4 * c + 2] = q.z;
+            win[4 * c + 3] = q.w;
+        }
+        for (int u = 0; u < nu; u += 4) {
+            const int4 q = *reinterpret_cast<const int4*>(E + u - v0);
+            win[R] = q.x;
+            win[R + 1] = q.y;
+            win[R + 2] = q.z;
+            win[R + 3] = q.w;
+            const int4 a4 = *reinterpret_cast<const int4*>(A + u);
+            const int a[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] += a[t] * win[R + t - r];
+#pragma unroll
+            for (int j = 0; j < R; ++j) win[j] = win[j + 4];
+        }
+    } else {
+        // win[r] = E[u - v0 - r]
+        int win[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) win[r] = E[-1 - v0 - r];
+        for (int u = 0; u < nu; u += 4) {
+            const int4 a4 = *reinterpret_cast<const int4*>(A + u);
+            const int a[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+#pragma unroll
+                for (int r = R - 1; r > 0; --r) win[r] = win[r - 1];
+                win[0] = E[u + t - v0];
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] += a[t] * win[r];
+            }
+        }
+    }
+}
+
+// P_v = sum_{m=1}^{v} A_p[v+m] A_p[v-m] from scratch for the lane's outputs.  The loop
+// runs to the largest v of the warp for every lane (A is zero below index 0, so the
+// extra terms vanish) to keep the warp converged.
+template <int R>
+__device__ __forceinline__ void p_direct(const View& V, int n, int lane, int (&P)[R])
+{
+    const int p = lane >> 4;
+    const int v0 = (lane & 15) * R;
+    const int* A = p ? V.A1 : V.A0;
+    const int mmax = ((n + 1) >> 1) - 1;
+    int hi[R], lo[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        P[r] = 0;
+        hi[r] = A[v0 + r];  // A[v + m] at m = 0
+        lo[r] = A[v0 + r];  // A[v - m] at m = 0
+    }
+    for (int m = 1; m <= mmax; ++m) {
+#pragma unroll
+        for (int r = 0; r < R - 1; ++r) hi[r] = hi[r + 1];
+        hi[R - 1] = A[v0 + R - 1 + m];
+#pragma unroll
+        for (int r = R - 1; r > 0; --r) lo[r] = lo[r - 1];
+        lo[0] = A[v0 - m];
+#pragma unroll
+        for (int r = 0; r < R; ++r) P[r] += hi[r] * lo[r];
+    }
+}
+
+// Change of P for a move that negates class-pb entries w1 and w2 (w2 < 0: centre, one
+// entry).  A pair (v+m, v-m) with exactly one negated end changes by -2 x its old
+// product; pairs with both ends negated are unchanged.  Reads A before the flip.
+template <int R>
+__device__ __forceinline__ void p_update(const View& V, int n, int lane, int (&P)[R], int pb, int w1, int w2)
+{
+    const int p = lane >> 4;
+    if (p != pb) return;
+    const int v0 = (lane & 15) * R;
+    const int* A = pb ? V.A1 : V.A0;
+    const int nv = pb ? (n >> 1) : ((n + 1) >> 1);
+    const int a1 = A[w1];
+    const int a2 = w2 >= 0 ? A[w2] : 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = v0 + r;
+        if (v >= nv) continue;
+        int d = 0;
+        const int t1 = 2 * v - w1;
+        if (v != w1 && t1 != w2) d += a1 * A[t1];
+        if (w2 >= 0) {
+            const int t2 = 2 * v - w2;
+            if (v != w2 && t2 != w1) d += a2 * A[t2];
+        }
+        P[r] -= 2 * d;
+    }
+}
+
+// dl[r] = dISL of free variable i = 2(v0+r)+p, or INT_MAX where that output does not
+// exist.  Formula in the header comment.
+template <int R>
+__device__ __forceinline__ void assemble(const View& V, int n, int lane, const int (&X)[R], const int (&P)[R],
+                                         int (&dl)[R])
 {
     const int p = lane >> 4;
     const int v0 = (lane & 15) * R;
     const int* A = p ? V.A1 : V.A0;
     const int nv = p ? (n >> 1) : ((n + 1) >> 1);
-    const int* E = V.E;
-
-    int acc[R], win[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        acc[r] = 0;
-        win[r] = E[-1 - v0 - r];
-    }
-    const int nu = (n + 3) & ~3;
-    for (int u = 0; u < nu; u += 4) {
-        const int4 a4 = *reinterpret_cast<const int4*>(A + u);
-        const int a[4] = {a4.x, a4.y, a4.z, a4.w};
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-#pragma unroll
-            for (int r = R - 1; r > 0; --r) win[r] = win[r - 1];
-            win[0] = E[u + t - v0];
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] += a[t] * win[r];
-        }
-    }
-
     const int c = n - 1;
+    const int N = p ? n - 2 : n - 1;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int v = v0 + r;
@@ -185,18 +287,14 @@ __device__ __forceinline__ void neighbourhood(const View& V, int n, int lane, in
         const int i = 2 * v + p;
         const int av = A[v];
         if (i == c) {
-            dl[r] = -4 * av * acc[r] + 16 * (c >> 1);
+            dl[r] = -4 * av * X[r] + 16 * (c >> 1);
             continue;
         }
-        int P = 0;
-        for (int m = 1; m <= v; ++m) P += A[v + m] * A[v - m];
-        const int vq = n - 1 - v - p;
-        const int sq = A[vq];
-        const int ck0 = E[c - i];
+        const int sq = A[n - 1 - v - p];
+        const int ck0 = V.E[c - i];
         const int t = 3 * v + p - n + 1;
         const int corr = t >= 0 ? sq * A[t] : 0;
-        const int N = p ? n - 2 : n - 1;
-        dl[r] = -8 * av * (acc[r] - sq * ck0) + 16 * (N - 1) + 32 * (P - corr);
+        dl[r] = -8 * av * (X[r] - sq * ck0) + 16 * (N - 1) + 32 * (P[r] - corr);
     }
 }
 
@@ -301,6 +399,53 @@ __device__ __forceinline__ int stop_requested(const KParams& p, int lane)
     return __shfl_sync(kFull, why, 0);
 }
 
+// Result of probing HT for one candidate.
+struct Probe {
+    bool visited;
+    int64_t slot;  // insertion slot when not visited, -1 when no free slot within the cap
+};
+
+// Full linear probe of f (all `cap` slots at once, one per lane).
+__device__ __forceinline__ Probe probe_full(const WalkEnv& env, uint64_t f, uint32_t gen, int cap)
+{
+    const int lane = env.lane;
+    const uint64_t tag = (f & ~kGenMask) | gen;
+    uint64_t e = 0;
+    if (lane < cap) e = env.T[(f + (uint64_t)lane) & env.tmask];
+    const bool match = e == tag;
+    const unsigned bal = __ballot_sync(kFull, lane < cap && (((e & kGenMask) != gen) || match));
+    Probe pr{false, -1};
+    if (bal) {
+        const int fl = __ffs(bal) - 1;
+        pr.visited = __shfl_sync(kFull, match ? 1 : 0, fl) != 0;
+        pr.slot = (int64_t)((f + (uint64_t)fl) & env.tmask);
+    }
+    return pr;
+}
+
+// Lowest (dl, i) among the lane outputs not in `excl` (all lanes get the result;
+// bi = -1 when none is left).
+template <int R>
+__device__ __forceinline__ void warp_argmin(const int (&dl)[R], uint32_t excl, int v0, int pcls, int& bd, int& bi)
+{
+    int lm = INT_MAX, li = INT_MAX;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (!((excl >> r) & 1u) && dl[r] < lm) {
+            lm = dl[r];
+            li = 2 * (v0 + r) + pcls;
+        }
+    bd = __reduce_min_sync(kFull, lm);
+    bi = bd == INT_MAX ? -1 : __reduce_min_sync(kFull, lm == bd ? li : INT_MAX);
+}
+
+template <int R>
+__device__ __forceinline__ void exclude(uint32_t& excl, int bi, int lane)
+{
+    const int vb = bi >> 1, pb = bi & 1;
+    if (lane == pb * 16 + vb / R) excl |= 1u << (vb % R);
+}
+
 template <int R>
 __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* base, const WarpSmem& SL,
                            const View& V, int trace_slot, int64_t trace_start)
@@ -309,6 +454,9 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
     const int lane = env.lane, n = env.n, c = n - 1;
     const int pcls = lane >> 4, v0 = (lane & 15) * R;
     const int cap = p.probe_cap;
+    const int half = lane & 15, grp = lane >> 4;
+    int P[R];
+    p_direct<R>(V, n, lane, P);
     while (w.steps < until) {
         if ((w.steps & (kCheckEvery - 1)) == 0) {
             const int why = stop_requested(p, lane);
@@ -318,47 +466,69 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
             }
         }
         int dl[R];
-        neighbourhood<R>(V, n, lane, dl);
+        {
+            int X[R];
+            toeplitz<R>(V, n, lane, X);
+            assemble<R>(V, n, lane, X, P, dl);
+        }
 
-        // best admissible flip: lowest (dISL, i) whose result is not in HT
+        // Best admissible flip: lowest (dISL, i) whose result is not in HT.  Two
+        // candidates are probed per round, 16 slots each (half a warp per candidate);
+        // a chain longer than 16 slots falls back to a full probe.
         uint32_t excl = 0;
         int best_i = -1, best_d = 0;
         int64_t slot = -1;
         uint64_t fnew = 0;
         for (;;) {
-            int lm = INT_MAX, li = INT_MAX;
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                if (!((excl >> r) & 1u) && dl[r] < lm) {
-                    lm = dl[r];
-                    li = 2 * (v0 + r) + pcls;
+            int d0, i0, d1, i1;
+            warp_argmin<R>(dl, excl, v0, pcls, d0, i0);
+            if (i0 < 0) break;
+            uint32_t ex1 = excl;
+            exclude<R>(ex1, i0, lane);
+            warp_argmin<R>(dl, ex1, v0, pcls, d1, i1);
+            const int ci = grp ? i1 : i0;
+            uint64_t f = 0, e = 0;
+            bool hit = false, match = false;
+            if (ci >= 0) {
+                f = w.fp ^ env.zk[ci];
+                const uint64_t tag = (f & ~kGenMask) | w.gen;
+                if (half < cap) {
+                    e = env.T[(f + (uint64_t)half) & env.tmask];
+                    match = e == tag;
+                    hit = ((e & kGenMask) != w.gen) || match;
                 }
-            const int mn = __reduce_min_sync(kFull, lm);
-            if (mn == INT_MAX) break;
-            const int bi = __reduce_min_sync(kFull, lm == mn ? li : INT_MAX);
-            const uint64_t f = w.fp ^ env.zk[bi];
-            const uint64_t tag = (f & ~kGenMask) | w.gen;
-            uint64_t e = 0;
-            if (lane < cap) e = env.T[(f + (uint64_t)lane) & env.tmask];
-            const bool stale = (e & kGenMask) != w.gen;
-            const bool match = e == tag;
-            const unsigned bal = __ballot_sync(kFull, lane < cap && (stale || match));
-            bool visited = false;
-            int64_t sl = -1;
-            if (bal) {
-                const int fl = __ffs(bal) - 1;
-                visited = __shfl_sync(kFull, match ? 1 : 0, fl) != 0;
-                sl = (int64_t)((f + (uint64_t)fl) & env.tmask);
             }
-            if (!visited) {
-                best_i = bi;
-                best_d = mn;
-                slot = sl;
-                fnew = f;
-                break;
+            const unsigned bal = __ballot_sync(kFull, hit);
+            const int cand[2] = {i0, i1};
+            const int cdl[2] = {d0, d1};
+            bool chosen = false;
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                if (cand[g] < 0) break;
+                const uint64_t fg = w.fp ^ env.zk[cand[g]];
+                const unsigned b = (bal >> (16 * g)) & 0xFFFFu;
+                Probe pr;
+                if (b) {
+                    const int fl = __ffs(b) - 1;
+                    pr.visited = __shfl_sync(kFull, match ? 1 : 0, 16 * g + fl) != 0;
+                    pr.slot = (int64_t)((fg + (uint64_t)fl) & env.tmask);
+                } else if (cap > 16) {
+                    pr = probe_full(env, fg, w.gen, cap);
+                } else {
+                    pr.visited = false;
+                    pr.slot = -1;
+                }
+                if (!pr.visited) {
+                    best_i = cand[g];
+                    best_d = cdl[g];
+                    slot = pr.slot;
+                    fnew = fg;
+                    chosen = true;
+                    break;
+                }
+                exclude<R>(excl, cand[g], lane);
             }
-            const int vb = bi >> 1, pb = bi & 1;
-            if (lane == pb * 16 + vb / R) excl |= 1u << (vb % R);
+            if (chosen) break;
         }
 
         w.steps += 1;
@@ -367,17 +537,18 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
             // Every neighbour is in HT: restart without a move.
             w.blocked += 1;
             restart_walker(env, w, base, SL, V);
+            p_direct<R>(V, n, lane, P);
             code = LABS_TRACE_BLOCKED;
         } else {
-            // S <- S_f: update the table, then the rows.
+            // S <- S_f: table, P and rows (all from the values before the flip).
             const int pb = best_i & 1, vb = best_i >> 1;
             int* Ab = pb ? V.A1 : V.A0;
             const int as = Ab[vb];
             const bool centre = best_i == c;
             const int vq = n - 1 - vb - pb;
-            int dd[kMaxN / kWarp];
+            int dd[R];
 #pragma unroll
-            for (int t = 0; t < kMaxN / kWarp; ++t) {
+            for (int t = 0; t < R; ++t) {  // lags 2m, m = lane+1+32t < n (n <= 32 R)
                 const int m = lane + 1 + kWarp * t;
                 dd[t] = 0;
                 if (m < n) {
@@ -387,9 +558,10 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
                     dd[t] = (centre ? -2 : -4) * as * (up + dn);
                 }
             }
+            p_update<R>(V, n, lane, P, pb, vb, centre ? -1 : vq);
             __syncwarp();
 #pragma unroll
-            for (int t = 0; t < kMaxN / kWarp; ++t) {
+            for (int t = 0; t < R; ++t) {
                 const int m = lane + 1 + kWarp * t;
                 if (m < n) {
                     V.E[m] += dd[t];
@@ -417,6 +589,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
             code = best_i;
             if (w.stag >= env.patience || !stored) {
                 restart_walker(env, w, base, SL, V);
+                p_direct<R>(V, n, lane, P);
                 code |= LABS_TRACE_RESTART;
             }
         }
@@ -480,7 +653,12 @@ __device__ void run_chunk(const WalkEnv& env, Walker& w, int64_t until, int* bas
     walk_steps<R>(env, w, until, base, SL, V, trace_slot, trace_start);
 }
 
-__global__ void __launch_bounds__(512) walk_chunk_kernel(KParams p, int chunk_index)
+// One launch advances every walker by up to chunk_steps steps toward the target.  The
+// kernel is compiled for a largest lane block RMAX (register allocation follows it);
+// walkers whose n needs RMAX-1 or fewer outputs per lane run with RMAX-1, which covers
+// them (any R >= lanes_R(n) computes the same values).
+template <int RMAX>
+__global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(KParams p, int chunk_index)
 {
     extern __shared__ __align__(16) int smem[];
     const WarpSmem SL = warp_smem(p.n_max);
@@ -518,16 +696,10 @@ __global__ void __launch_bounds__(512) walk_chunk_kernel(KParams p, int chunk_in
             if (lane == 0) raise_error(p.status, LABS_ESTATE, (int)wi);
             continue;
         }
-        switch (lanes_R(G.n)) {
-            case 1: run_chunk<1>(env, w, until, base, SL, V, trace_slot, trace_start); break;
-            case 2: run_chunk<2>(env, w, until, base, SL, V, trace_slot, trace_start); break;
-            case 3: run_chunk<3>(env, w, until, base, SL, V, trace_slot, trace_start); break;
-            case 4: run_chunk<4>(env, w, until, base, SL, V, trace_slot, trace_start); break;
-            case 5: run_chunk<5>(env, w, until, base, SL, V, trace_slot, trace_start); break;
-            case 6: run_chunk<6>(env, w, until, base, SL, V, trace_slot, trace_start); break;
-            case 7: run_chunk<7>(env, w, until, base, SL, V, trace_slot, trace_start); break;
-            default: run_chunk<8>(env, w, until, base, SL, V, trace_slot, trace_start); break;
-        }
+        if (RMAX == 1 || lanes_R(G.n) == RMAX)
+            run_chunk<RMAX>(env, w, until, base, SL, V, trace_slot, trace_start);
+        else
+            run_chunk<(RMAX > 1 ? RMAX - 1 : 1)>(env, w, until, base, SL, V, trace_slot, trace_start);
         save_walker(st, w, lane);
         __syncwarp();
     }
@@ -635,14 +807,21 @@ template <int R>
 __device__ void delta_row(const View& V, int n, int lane, int32_t* dst)
 {
     int dl[R];
-    neighbourhood<R>(V, n, lane, dl);
+    {
+        int X[R], P[R];
+        toeplitz<R>(V, n, lane, X);
+        p_direct<R>(V, n, lane, P);
+        assemble<R>(V, n, lane, X, P, dl);
+    }
     const int p = lane >> 4, v0 = (lane & 15) * R;
 #pragma unroll
     for (int r = 0; r < R; ++r)
         if (dl[r] != INT_MAX) dst[2 * (v0 + r) + p] = dl[r];
 }
 
-// The neighbourhood of Algorithm 1 for skew-symmetric rows, one warp per row.
+// The neighbourhood of Algorithm 1 for skew-symmetric rows, one warp per row, R
+// outputs per lane (R = lanes_R(n), chosen by the host).
+template <int R>
 __global__ void __launch_bounds__(256) delta_kernel(const int8_t* __restrict__ seqs, int64_t batch, int L,
                                                     int32_t* __restrict__ out, DevStatus* status)
 {
@@ -653,7 +832,6 @@ __global__ void __launch_bounds__(256) delta_kernel(const int8_t* __restrict__ s
     int* base = smem + warp * SL.words;
     const View V = make_view(base, SL);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int R = lanes_R(n);
     for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < batch; row += nwarps) {
         clear_warp(base, SL, lane);
         const int8_t* src = seqs + row * (int64_t)L;
@@ -679,16 +857,7 @@ __global__ void __launch_bounds__(256) delta_kernel(const int8_t* __restrict__ s
             continue;
         }
         build_table(V, n, lane);
-        switch (R) {
-            case 1: delta_row<1>(V, n, lane, dst); break;
-            case 2: delta_row<2>(V, n, lane, dst); break;
-            case 3: delta_row<3>(V, n, lane, dst); break;
-            case 4: delta_row<4>(V, n, lane, dst); break;
-            case 5: delta_row<5>(V, n, lane, dst); break;
-            case 6: delta_row<6>(V, n, lane, dst); break;
-            case 7: delta_row<7>(V, n, lane, dst); break;
-            default: delta_row<8>(V, n, lane, dst); break;
-        }
+        delta_row<R>(V, n, lane, dst);
         __syncwarp();
     }
 }
@@ -791,20 +960,48 @@ int launch_prep_walk(const KParams& p, int64_t steps, int nchunks, void* stream)
     return status_of(cudaGetLastError());
 }
 
-int walk_kernel_config(int warps_per_cta, size_t smem_bytes, int* ctas_per_sm)
+using WalkFn = void (*)(KParams, int);
+static WalkFn walk_fn(int rmax)
 {
-    cudaError_t e = cudaFuncSetAttribute(walk_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes);
+    switch (rmax) {
+        case 1: return walk_chunk_kernel<1>;
+        case 2: return walk_chunk_kernel<2>;
+        case 3: return walk_chunk_kernel<3>;
+        case 4: return walk_chunk_kernel<4>;
+        case 5: return walk_chunk_kernel<5>;
+        case 6: return walk_chunk_kernel<6>;
+        case 7: return walk_chunk_kernel<7>;
+        default: return walk_chunk_kernel<8>;
+    }
+}
+
+int lanes_for(int n)
+{
+    return (((n + 1) >> 1) + 15) >> 4;
+}
+
+int walk_kernel_config(int rmax, int warps_per_cta, size_t smem_bytes, int* ctas_per_sm, int* regs)
+{
+    const WalkFn fn = walk_fn(rmax);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return LABS_ECUDA;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, walk_chunk_kernel, warps_per_cta * kWarp,
-                                                      smem_bytes);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return LABS_ECUDA;
+    if (regs) *regs = fa.numRegs;
+    if (warps_per_cta * kWarp > fa.maxThreadsPerBlock) {
+        *ctas_per_sm = 0;
+        return LABS_EINVAL;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, warps_per_cta * kWarp, smem_bytes);
     return status_of(e);
 }
 
 int launch_walk_chunk(const KParams& p, int chunk_index, int grid, int warps_per_cta, size_t smem_bytes,
                       void* stream)
 {
-    walk_chunk_kernel<<<grid, warps_per_cta * kWarp, smem_bytes, (cudaStream_t)stream>>>(p, chunk_index);
+    const WalkFn fn = walk_fn(p.rmax);
+    fn<<<grid, warps_per_cta * kWarp, smem_bytes, (cudaStream_t)stream>>>(p, chunk_index);
     return status_of(cudaGetLastError());
 }
 
@@ -833,9 +1030,20 @@ int launch_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, Dev
     if (batch == 0) return LABS_OK;
     const int warps = 8;
     const size_t smem = (size_t)warps * warp_smem((L + 1) / 2).words * sizeof(int);
-    cudaFuncSetAttribute(delta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    delta_kernel<<<row_grid(batch, warps), warps * kWarp, smem, (cudaStream_t)stream>>>(seqs, batch, L, out,
-                                                                                         status);
+    using DeltaFn = void (*)(const int8_t*, int64_t, int, int32_t*, DevStatus*);
+    DeltaFn fn;
+    switch (lanes_for((L + 1) / 2)) {
+        case 1: fn = delta_kernel<1>; break;
+        case 2: fn = delta_kernel<2>; break;
+        case 3: fn = delta_kernel<3>; break;
+        case 4: fn = delta_kernel<4>; break;
+        case 5: fn = delta_kernel<5>; break;
+        case 6: fn = delta_kernel<6>; break;
+        case 7: fn = delta_kernel<7>; break;
+        default: fn = delta_kernel<8>; break;
+    }
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    fn<<<row_grid(batch, warps), warps * kWarp, smem, (cudaStream_t)stream>>>(seqs, batch, L, out, status);
     return status_of(cudaGetLastError());
 }
 

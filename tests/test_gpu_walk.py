@@ -63,7 +63,7 @@ def test_chunking_and_graphs_do_not_change_trajectories():
     L, W, steps = 61, 32, 700
     ref = None
     for cfg in ({}, {"chunk_steps": 7}, {"chunk_steps": 64, "flags": _native.LABS_FLAG_NO_GRAPH},
-                {"warps_per_cta": 2}, {"warps_per_cta": 16, "chunk_steps": 100}):
+                {"warps_per_cta": 2}, {"warps_per_cta": 5, "chunk_steps": 100}):
         s, code, isl = run_traced(L, W, steps, 5, **cfg)
         if ref is None:
             ref = (code, isl)
@@ -187,6 +187,8 @@ def test_bad_arguments_raise():
         labs.Search(513, 4, 1)
     with pytest.raises(labs.LabsError):
         labs.Search(41, 4, 1, tabu_log2=21)
+    with pytest.raises(labs.LabsError):
+        labs.Search(41, 4, 1, warps_per_cta=9)
     s = labs.Search(41, 4, 1)
     with pytest.raises(labs.LabsError):
         s.walk(-1)
