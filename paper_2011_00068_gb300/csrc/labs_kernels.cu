@@ -36,6 +36,11 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+#ifndef LABS_TOEPLITZ_UNROLL
+#define LABS_TOEPLITZ_UNROLL 2  // u-blocks of the Toeplitz loop unrolled together
+#endif
+constexpr int kToeplitzUnroll = LABS_TOEPLITZ_UNROLL;
+
 #ifndef LABS_WALK_MIN_BLOCKS
 #define LABS_WALK_MIN_BLOCKS 2  // CTAs of 8 warps per SM the walk kernel is compiled for (2 measured fastest)
 #endif
@@ -104,10 +109,11 @@ __device__ __forceinline__ View make_view(int* base, const WarpSmem& L)
     return v;
 }
 
+// Zeroes the rows and the table (not the fingerprint keys Z, which stay for the chunk).
 __device__ __forceinline__ void clear_warp(int* base, const WarpSmem& L, int lane)
 {
     int4* b4 = reinterpret_cast<int4*>(base);
-    for (int t = lane; t < L.words / 4; t += kWarp) b4[t] = make_int4(0, 0, 0, 0);
+    for (int t = lane; t < L.zoff / 4; t += kWarp) b4[t] = make_int4(0, 0, 0, 0);
     __syncwarp();
 }
 
@@ -173,6 +179,7 @@ __device__ __forceinline__ void toeplitz(const View& V, int n, int lane, int (&a
             win[4 * c + 2] = q.z;
             win[4 * c + 3] = q.w;
         }
+#pragma unroll kToeplitzUnroll
         for (int u = 0; u < nu; u += 4) {
             const int4 q = *reinterpret_cast<const int4*>(E + u - v0);
             win[R] = q.x;
@@ -454,7 +461,6 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
     const int lane = env.lane, n = env.n, c = n - 1;
     const int pcls = lane >> 4, v0 = (lane & 15) * R;
     const int cap = p.probe_cap;
-    const int half = lane & 15, grp = lane >> 4;
     int P[R];
     p_direct<R>(V, n, lane, P);
     while (w.steps < until) {
@@ -474,7 +480,8 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
 
         // Best admissible flip: lowest (dISL, i) whose result is not in HT.  Two
         // candidates are probed per round, 16 slots each (half a warp per candidate);
-        // a chain longer than 16 slots falls back to a full probe.
+        // a longer chain falls back to a full probe.  The chosen flip is the best one
+        // in about 40% of the steps and one of the best two in about 86% (L = 201).
         uint32_t excl = 0;
         int best_i = -1, best_d = 0;
         int64_t slot = -1;
@@ -486,17 +493,14 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
             uint32_t ex1 = excl;
             exclude<R>(ex1, i0, lane);
             warp_argmin<R>(dl, ex1, v0, pcls, d1, i1);
-            const int ci = grp ? i1 : i0;
-            uint64_t f = 0, e = 0;
+            const int half = lane & 15;
+            const int mine = lane < 16 ? i0 : i1;
             bool hit = false, match = false;
-            if (ci >= 0) {
-                f = w.fp ^ env.zk[ci];
-                const uint64_t tag = (f & ~kGenMask) | w.gen;
-                if (half < cap) {
-                    e = env.T[(f + (uint64_t)half) & env.tmask];
-                    match = e == tag;
-                    hit = ((e & kGenMask) != w.gen) || match;
-                }
+            if (mine >= 0 && half < cap) {
+                const uint64_t f = w.fp ^ env.zk[mine];
+                const uint64_t e = env.T[(f + (uint64_t)half) & env.tmask];
+                match = e == ((f & ~kGenMask) | w.gen);
+                hit = ((e & kGenMask) != w.gen) || match;
             }
             const unsigned bal = __ballot_sync(kFull, hit);
             const int cand[2] = {i0, i1};
@@ -680,7 +684,13 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(K
         env.p = &p;
         env.tmask = (1ull << p.tabu_log2) - 1ull;
         env.T = p.tabu + ((uint64_t)wi << p.tabu_log2);
-        env.zk = p.zkeys + G.zkey_off;
+        {
+            uint64_t* zs = reinterpret_cast<uint64_t*>(base + SL.zoff);
+            const uint64_t* zg = p.zkeys + G.zkey_off;
+            for (int i = lane; i < G.n; i += kWarp) zs[i] = zg[i];
+            env.zk = zs;
+            __syncwarp();
+        }
         env.st = st;
         env.L = G.L;
         env.n = G.n;
