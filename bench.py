@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-delta", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--delta-rows", type=int, default=1 << 20)
     return ap.parse_args()
 
 
@@ -177,6 +180,44 @@ def run_reference(args):
     return 0
 
 
+def delta_kernel_line(args, dev, stream, labs):
+    """labs_neighbor_delta (the stateless neighbourhood evaluation, Algorithm 1's flip
+    loop over given sequences) on a batch larger than L2, timed with CUDA events on
+    the library's stream: throughput and its int32 roofline."""
+    import torch
+
+    import labs_inputs
+
+    L, B = args.L, args.delta_rows
+    n, c = (L + 1) // 2, (L + 1) // 2 - 1
+    with torch.cuda.stream(stream):
+        x = torch.from_numpy(labs_inputs.random_free_vars(B, L, seed=args.seed)).to(dev)
+        j = torch.arange(1, n, device=dev)
+        sign = torch.where(j % 2 == 1, -1, 1).to(torch.int8)
+        rows = torch.cat([x, x[:, c - j] * sign], dim=1).contiguous()  # Eq. 4
+        out = labs.neighbor_delta(rows, stream=stream)
+        ms = []
+        for _ in range(args.warmup + args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            labs.neighbor_delta(rows, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+    ms = statistics.mean(ms[args.warmup:])
+    flips = B * n / (ms / 1e3)
+    peaks = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = INT32_LANES_PER_SM * sms * sm_mhz * 1e6
+    achieved = ALGO_OPS_PER_LAG_TERM * (n - 1) * flips
+    del out
+    return {"kernel": "delta_kernel", "rows": B, "L": L, "ms_per_launch": ms, "value": flips, "unit": UNIT,
+            "input_bytes": B * L, "output_bytes": B * n * 4,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s (int32)",
+                         "frac": achieved / peak, "traffic": None}}
+
+
 def run_ours(args):
     import torch
 
@@ -195,8 +236,16 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(dev)
     n = (args.L + 1) // 2
-    seed = args.seed + 1000003 * rank
-    s = labs.Search(args.L, args.walkers, seed, device=dev, stream=stream, tabu_log2=args.tabu_log2)
+    from paper_2011_00068_gb300 import replicas
+
+    seed = replicas.rank_seed(args.seed, rank)
+    shape = {}
+    if not args.no_tune:
+        from paper_2011_00068_gb300 import tune
+
+        best = tune.tune(args.L, args.walkers, tabu_log2=args.tabu_log2, device=dev)
+        shape = {"warps_per_cta": best["warps_per_cta"], "chunk_steps": best["chunk_steps"]}
+    s = labs.Search(args.L, args.walkers, seed, device=dev, stream=stream, tabu_log2=args.tabu_log2, **shape)
     chunk = int(s.cfg.chunk_steps) or 1024
     nchunks = -(-args.walk_steps // chunk)
 
@@ -228,11 +277,7 @@ def run_ours(args):
         barrier()
         t1 = time.perf_counter()
     walk_ms = [a.elapsed_time(b) for a, b in ev]
-    elapsed = t1 - t0
-    if pg:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = replicas.max_over_ranks(t1 - t0, device=dev)
     flips_per_step = args.walkers * args.walk_steps * n
     value = world * flips_per_step * args.steps / elapsed
     st = s.stats()
@@ -267,15 +312,22 @@ def run_ours(args):
         e2e = {"value": world * flips_per_step / statistics.mean(e2e_times), "unit": UNIT,
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h)}
 
+    delta = None if args.no_delta else delta_kernel_line(args, dev, stream, labs)
+    best_isl, best_rank = replicas.best_over_ranks(st["best_isl"], device=dev)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": config_of(args, world), "roofline": roofline,
+                "config": dict(config_of(args, world), launch={
+                    "warps_per_cta": int(s.cfg.warps_per_cta) or 8, "chunk_steps": chunk,
+                    "tuned": not args.no_tune}),
+                "roofline": roofline,
                 "clocks": clk.summary(), "e2e": e2e,
                 "gpu_launches": args.steps * (2 + nchunks),
                 "walk_ms_per_step": statistics.mean(walk_ms),
-                "best": {"isl": st["best_isl"], "F": args.L ** 2 / (2 * st["best_isl"]), "L": st["best_L"]},
+                "best": {"isl": best_isl, "F": args.L ** 2 / (2 * best_isl), "L": st["best_L"], "rank": best_rank},
+                "delta_kernel": delta,
                 "restarts": st["restarts"]}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)

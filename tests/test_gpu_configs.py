@@ -1,0 +1,93 @@
+"""Parity at the workload sizes the benchmark runs, in the launch configuration it
+times, on walkers the oracle can replay one by one (bit-exact integers).
+
+config 1: L=41, 64 walkers x 1e5 steps, seed 1: every step of every walker.
+config 2: L=201, 16384 walkers x 1e4 steps, seed 7 (the bench step): 48 walkers
+          spread over the batch, final/best ISL, best sequence, time-to-target step.
+config 3: the 52 odd lengths 201..303, 2048 walkers each, 5e3 steps, one launch:
+          LABS_PARITY_PER_L walkers per length (default 3; 64 is the full sample,
+          about five minutes of oracle time on 16 cores).
+largest length: L=501 (the largest length of the scale-up configuration), 8192
+          walkers x 2000 steps.
+"""
+from __future__ import annotations
+
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2011_00068_gb300 as labs
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def oracle_walkers(jobs):
+    """Oracle runs of single walkers (L, seed, steps, walker id), one per host thread
+    (the oracle releases the interpreter lock while it runs)."""
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        return list(ex.map(lambda j: oracle.walk(j[0], j[1], 1, j[2], first_walker=j[3], nthreads=1), jobs))
+
+
+def check_sample(s, L, seed, steps, ids):
+    outs = oracle_walkers([(L, seed, steps, gid) for gid in ids])
+    for gid, o in zip(ids, outs):
+        r = s.results(gid, 1, seqs=True)
+        assert r["isl"][0] == o["final_isl"][0], gid
+        assert r["best_isl"][0] == o["best_isl"][0], gid
+        assert np.array_equal(r["best_seq"][0], o["best_seq"][0]), gid
+        assert r["target_step"][0] == o["target_step"][0], gid
+
+
+def test_config1_L41_full_trajectories():
+    L, W, steps, seed = 41, 64, 100_000, 1
+    s = labs.Search(L, W, seed)
+    code, isl = s.trace(list(range(W)), steps)
+    s.walk(steps)
+    s.sync()
+    o = oracle.walk(L, seed, W, steps, trace=True)
+    assert np.array_equal(code.cpu().numpy(), o["trace_code"])
+    assert np.array_equal(isl.cpu().numpy(), o["trace_isl"])
+    assert int(o["best_isl"].min()) == 108  # the walk reaches the L=41 optimum
+
+
+def test_config2_L201_bench_shape():
+    L, W, steps, seed = 201, 16384, 10_000, 7
+    s = labs.Search(L, W, seed)
+    s.walk(steps)
+    s.sync()
+    st = s.stats()
+    assert st["steps"] == W * steps and st["overflows"] == 0
+    ids = sorted({0, 1, W - 1} | set(list(range(97, W, 353))[:45]))
+    check_sample(s, L, seed, steps, ids)
+    b = s.best()
+    assert oracle.isl(b["seq"]) == b["isl"] == st["best_isl"]
+
+
+def test_config3_mixed_lengths_one_launch():
+    Ls = list(range(201, 304, 2))
+    per, steps, seed = 2048, 5000, 7
+    s = labs.Search(Ls, [per] * len(Ls), seed)
+    s.walk(steps)
+    s.sync()
+    k = int(os.environ.get("LABS_PARITY_PER_L", "3"))
+    rng = np.random.default_rng(3)
+    jobs = []
+    for g, L in enumerate(Ls):
+        jobs += [(L, seed, steps, g * per + int(j)) for j in rng.choice(per, k, replace=False)]
+    outs = oracle_walkers(jobs)
+    for (L, _, _, gid), o in zip(jobs, outs):
+        r = s.results(gid, 1, seqs=True)
+        assert r["isl"][0] == o["final_isl"][0], (L, gid)
+        assert r["best_isl"][0] == o["best_isl"][0], (L, gid)
+        assert np.array_equal(r["best_seq"][0], o["best_seq"][0]), (L, gid)
+
+
+def test_largest_length_L501():
+    L, W, steps, seed = 501, 8192, 2000, 42
+    s = labs.Search(L, W, seed)
+    s.walk(steps)
+    s.sync()
+    check_sample(s, L, seed, steps, [0, 4095, W - 1])
