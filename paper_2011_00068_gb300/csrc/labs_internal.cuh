@@ -103,11 +103,15 @@ struct KParams {
 //   A1: odd positions  s_1, s_3, .. (n-1 values) padded the same way
 //   E : E[d] = C_{2|d|} for 0 < |d| < n, E[0] = 0, zero elsewhere, d in [-kEPad, n+8)
 constexpr int kEPad = 128;
-//   Z : the walker's n fingerprint keys (uint64), after E
+//   B : bit-packed classes (bit u set <=> A_p[u] = -1) and their reversals,
+//       4 vectors x kBitVec words, zero beyond the class length
+//   Z : the walker's n fingerprint keys (uint64)
+constexpr int kBitVec = 9;  // 256 bits per class plus one zero word read by the shifts
 struct WarpSmem {
     int apad;      // zero padding on each side of A0/A1 (>= n_max, multiple of 4)
     int alen;      // apad + n_max + apad, rounded to 4
     int elen;      // kEPad + n_max + 8
+    int boff;      // word offset of B
     int zoff;      // word offset of Z (16-byte aligned)
     int words;     // total words per warp
 };
@@ -117,7 +121,8 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max)
     w.apad = (n_max + 3) & ~3;
     w.alen = (w.apad + ((n_max + 3) & ~3) + w.apad + 4 + 3) & ~3;
     w.elen = (kEPad + n_max + 8 + 3) & ~3;
-    w.zoff = 2 * w.alen + w.elen;
+    w.boff = 2 * w.alen + w.elen;
+    w.zoff = w.boff + 4 * kBitVec;
     w.words = w.zoff + 2 * ((n_max + 1) & ~1);
     return w;
 }

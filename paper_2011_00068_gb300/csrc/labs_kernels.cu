@@ -95,9 +95,10 @@ __device__ __forceinline__ void raise_error(DevStatus* st, int code, int detail)
 
 // Per-warp views of the shared-memory layout.
 struct View {
-    int* A0;  // A0[-apad .. n_max+apad)
+    int* A0;      // A0[-apad .. n_max+apad)
     int* A1;
-    int* E;   // E[-kEPad .. n_max+8)
+    int* E;       // E[-kEPad .. n_max+8)
+    uint32_t* B;  // bit-packed classes and reversals, 4 x kBitVec words
 };
 
 __device__ __forceinline__ View make_view(int* base, const WarpSmem& L)
@@ -106,10 +107,12 @@ __device__ __forceinline__ View make_view(int* base, const WarpSmem& L)
     v.A0 = base + L.apad;
     v.A1 = base + L.alen + L.apad;
     v.E = base + 2 * L.alen + kEPad;
+    v.B = reinterpret_cast<uint32_t*>(base + L.boff);
     return v;
 }
 
-// Zeroes the rows and the table (not the fingerprint keys Z, which stay for the chunk).
+// Zeroes the rows, the table and the bit vectors (not the fingerprint keys Z, which
+// stay for the chunk).
 __device__ __forceinline__ void clear_warp(int* base, const WarpSmem& L, int lane)
 {
     int4* b4 = reinterpret_cast<int4*>(base);
@@ -137,14 +140,59 @@ __device__ __forceinline__ void rows_from_bits(const View& V, uint32_t word, int
     __syncwarp();
 }
 
-// Even-lag autocorrelations (Eq. 1) into E and the ISL (Eq. 2) from A0/A1.
+// Bit-packed classes: B[p*kBitVec + k] holds bits 32k..32k+31 of class p (bit u set
+// <=> A_p[u] = -1); B[(2+p)*kBitVec + k] the same for the reversed class (bit t is
+// class entry n_p-1-t).  One ballot per word; zero beyond the class length.
+__device__ __forceinline__ void bits_from_rows(const View& V, int n, int lane)
+{
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int* A = p ? V.A1 : V.A0;
+        const int np = p ? n - 1 : n;
+        for (int k = 0; k < kBitVec; ++k) {
+            const int u = 32 * k + lane;
+            const uint32_t w = __ballot_sync(kFull, u < np && A[u] < 0);
+            const int t = np - 1 - u;
+            const uint32_t r = __ballot_sync(kFull, u < np && A[t] < 0);
+            if (lane == 0) {
+                V.B[p * kBitVec + k] = w;
+                V.B[(2 + p) * kBitVec + k] = r;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Number of differing bits between x and x >> sh over bits [0, len) (x = B vector).
+__device__ __forceinline__ int shifted_mismatch(const uint32_t* x, const uint32_t* y, int sh, int len)
+{
+    const int q = sh >> 5, r = sh & 31;
+    int cnt = 0;
+    for (int k = 0; 32 * k < len; ++k) {
+        const uint32_t s = __funnelshift_r(y[k + q], y[k + q + 1], r);
+        uint32_t v = x[k] ^ s;
+        const int valid = len - 32 * k;
+        if (valid < 32) v &= (1u << valid) - 1u;
+        cnt += __popc(v);
+    }
+    return cnt;
+}
+
+// Even-lag autocorrelations (Eq. 1) into E and the ISL (Eq. 2) from the bit-packed
+// classes: for each class, sum_u a_u a_{u+m} = (n_p - m) - 2 #{u : a_u != a_{u+m}}.
 __device__ __forceinline__ int build_table(const View& V, int n, int lane)
 {
+    bits_from_rows(V, n, lane);
     int part = 0;
     for (int m = 1 + lane; m < n; m += kWarp) {
         int d = 0;
-        for (int u = 0; u + m < n; ++u) d += V.A0[u] * V.A0[u + m];
-        for (int u = 0; u + m < n - 1; ++u) d += V.A1[u] * V.A1[u + m];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int len = (p ? n - 1 : n) - m;
+            if (len <= 0) continue;
+            const uint32_t* x = V.B + p * kBitVec;
+            d += len - 2 * shifted_mismatch(x, x, m, len);
+        }
         V.E[m] = d;
         if (m <= kEPad) V.E[-m] = d;
         part += d * d;
@@ -215,32 +263,35 @@ __device__ __forceinline__ void toeplitz(const View& V, int n, int lane, int (&a
     }
 }
 
-// P_v = sum_{m=1}^{v} A_p[v+m] A_p[v-m] from scratch for the lane's outputs.  The loop
-// runs to the largest v of the warp for every lane (A is zero below index 0, so the
-// extra terms vanish) to keep the warp converged.
+// P_v = sum_{m=1}^{v} A_p[v+m] A_p[v-m] from scratch for the lane's outputs, from the
+// bit-packed classes (built by build_table): the pairs compare bits v+1.. of the
+// class with bits n_p-v.. of the reversed class, P_v = v - 2 #{mismatches}.
 template <int R>
 __device__ __forceinline__ void p_direct(const View& V, int n, int lane, int (&P)[R])
 {
     const int p = lane >> 4;
     const int v0 = (lane & 15) * R;
-    const int* A = p ? V.A1 : V.A0;
-    const int mmax = ((n + 1) >> 1) - 1;
-    int hi[R], lo[R];
+    const int np = p ? n - 1 : n;
+    const int nv = p ? (n >> 1) : ((n + 1) >> 1);
+    const uint32_t* x = V.B + p * kBitVec;
+    const uint32_t* xr = V.B + (2 + p) * kBitVec;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
+        const int v = v0 + r;
         P[r] = 0;
-        hi[r] = A[v0 + r];  // A[v + m] at m = 0
-        lo[r] = A[v0 + r];  // A[v - m] at m = 0
-    }
-    for (int m = 1; m <= mmax; ++m) {
-#pragma unroll
-        for (int r = 0; r < R - 1; ++r) hi[r] = hi[r + 1];
-        hi[R - 1] = A[v0 + R - 1 + m];
-#pragma unroll
-        for (int r = R - 1; r > 0; --r) lo[r] = lo[r - 1];
-        lo[0] = A[v0 - m];
-#pragma unroll
-        for (int r = 0; r < R; ++r) P[r] += hi[r] * lo[r];
+        if (v >= nv || v == 0) continue;
+        const int q1 = (v + 1) >> 5, r1 = (v + 1) & 31;
+        const int q2 = (np - v) >> 5, r2 = (np - v) & 31;
+        int cnt = 0;
+        for (int k = 0; 32 * k < v; ++k) {
+            const uint32_t a = __funnelshift_r(x[k + q1], x[k + q1 + 1], r1);
+            const uint32_t b = __funnelshift_r(xr[k + q2], xr[k + q2 + 1], r2);
+            uint32_t d = a ^ b;
+            const int valid = v - 32 * k;
+            if (valid < 32) d &= (1u << valid) - 1u;
+            cnt += __popc(d);
+        }
+        P[r] = v - 2 * cnt;
     }
 }
 
