@@ -195,6 +195,34 @@ int labs_enumerate(int32_t L, void *dev_scratch, size_t scratch_bytes, int64_t *
 int labs_enumerate_noalloc(int32_t L, int64_t *min_isl, uint64_t *count,
                            uint64_t *first_assignment, void *cuda_stream);
 
+/* ---- Learned proposal network (the library's addition: the paper has no learned
+ * component).  A small BF16 network ranks flips and restart points; the exact int32
+ * ISL still decides every move.  Per state of n free variables (2 <= n <= 256):
+ *   input x: float32 [batch][3][n] -- s_i, C_{2(i+1)}/sqrt(L) (0 for i = n-1) and
+ *            dISL_i/(8L) per free variable i (rounded to bfloat16 on entry);
+ *   a1..a3 = relu(conv(a_{l-1}) + b_l), Conv1d with 64 channels, 7 taps, zero padding 3;
+ *   h = relu(W4 a3 + b4) per position; score_i = w5 . h_i + b5 (flip score);
+ *   restart = w6 . mean_i(a3_i) + b6 (restart score).
+ * Parameters are one float32 array in the order W1[64][16][7] b1 W2[64][64][7] b2
+ * W3[64][64][7] b3 W4[64][64] b4 w5[64] b5 w6[64] b6 (labs_net_sizes gives the count);
+ * products use bfloat16 copies with float32 accumulation on the tensor cores.
+ * Loss per sample: wf * CE(softmax(score), target) + 0.5 (restart - y)^2, batch mean.
+ * All pointers are device memory; calls are asynchronous on cuda_stream. */
+int labs_net_sizes(int32_t n, int64_t batch, size_t *param_count, size_t *workspace_bytes);
+int labs_net_init(float *dev_params, uint64_t seed, void *cuda_stream);
+int labs_net_forward(const float *dev_params, const float *dev_x, int64_t batch, int32_t n,
+                     float *dev_scores /* [batch][n], nullable */, float *dev_restart /* [batch], nullable */,
+                     void *dev_ws, size_t ws_bytes, void *cuda_stream);
+/* Gradients of the batch-mean loss into dev_grads (overwritten; same layout as the
+ * parameters) and the loss into dev_loss (nullable). */
+int labs_net_gradients(const float *dev_params, const float *dev_x, const int32_t *dev_target,
+                       const float *dev_y, const float *dev_wf, int64_t batch, int32_t n,
+                       float *dev_grads, float *dev_loss, void *dev_ws, size_t ws_bytes,
+                       void *cuda_stream);
+/* One AdamW step (beta 0.9/0.999, eps 1e-8; weight decay on weights, not biases). */
+int labs_net_adamw(float *dev_params, const float *dev_grads, float *dev_m, float *dev_v, int64_t t,
+                   float lr, float weight_decay, void *cuda_stream);
+
 /* Checkpoint of every walker's state (sequence, ISL, best, counters, random-stream
  * position) and, with with_tabu != 0, its HT.  With the HT included a restored run
  * continues bit-identically; without it the HT restarts empty.  host_buf NULL queries

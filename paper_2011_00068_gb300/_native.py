@@ -33,7 +33,8 @@ EXPORTS = [
     "labs_default_config", "labs_init", "labs_init_multi", "labs_workspace_bytes", "labs_bind_workspace",
     "labs_reset", "labs_isl", "labs_neighbor_delta", "labs_walk", "labs_sync", "labs_best",
     "labs_walker_results", "labs_stats", "labs_trace", "labs_enumerate_scratch_bytes", "labs_enumerate",
-    "labs_enumerate_noalloc", "labs_checkpoint", "labs_restore", "labs_set_deadline", "labs_cancel", "labs_clear_stop",
+    "labs_enumerate_noalloc", "labs_net_sizes", "labs_net_init", "labs_net_forward", "labs_net_gradients",
+    "labs_net_adamw", "labs_checkpoint", "labs_restore", "labs_set_deadline", "labs_cancel", "labs_clear_stop",
     "labs_last_error", "labs_destroy",
 ]
 
@@ -102,6 +103,11 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
             "labs_enumerate_scratch_bytes": (ctypes.c_int, [i32, ctypes.POINTER(sz)]),
             "labs_enumerate": (ctypes.c_int, [i32, P, sz, P, P, P, P]),
             "labs_enumerate_noalloc": (ctypes.c_int, [i32, P, P, P, P]),
+            "labs_net_sizes": (ctypes.c_int, [i32, i64, ctypes.POINTER(sz), ctypes.POINTER(sz)]),
+            "labs_net_init": (ctypes.c_int, [P, u64, P]),
+            "labs_net_forward": (ctypes.c_int, [P, P, i64, i32, P, P, P, sz, P]),
+            "labs_net_gradients": (ctypes.c_int, [P, P, P, P, P, i64, i32, P, P, P, sz, P]),
+            "labs_net_adamw": (ctypes.c_int, [P, P, P, P, i64, ctypes.c_float, ctypes.c_float, P]),
             "labs_checkpoint": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.POINTER(sz)]),
             "labs_restore": (ctypes.c_int, [P, P, sz]),
             "labs_set_deadline": (ctypes.c_int, [P, u64]),
