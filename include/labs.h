@@ -71,6 +71,7 @@ typedef struct labs_config {
 
 #define LABS_FLAG_NO_GRAPH 1     /* launch chunks one by one instead of a CUDA graph */
 #define LABS_FLAG_CHECK_STATE 2  /* re-derive ISL from scratch at each chunk end */
+#define LABS_FLAG_LEARNED 4      /* reserve workspace for the learned mode (labs_learned) */
 
 /* Counters of a context, summed over its walkers (labs_stats). */
 typedef struct labs_counters {
@@ -86,6 +87,18 @@ typedef struct labs_counters {
                                   -1 if none did */
     int64_t walkers_at_target; /* walkers that met the target */
 } labs_counters;
+
+/* One record of the walk log (labs_log): the state of a walker at the start of a
+ * chunk of steps and what followed it.  64 bytes. */
+typedef struct labs_log_record {
+    uint32_t bits[8];  /* free variables at the chunk start: bit i set <=> s_i = -1 */
+    int32_t isl;       /* ISL at the chunk start */
+    int32_t first;     /* trace code of the chunk's first step */
+    int32_t min_isl;   /* lowest ISL reached in the chunk before its first restart */
+    int32_t L;
+    int64_t walker;
+    int64_t step;      /* steps done at the chunk start */
+} labs_log_record;
 
 /* Fills *cfg with the defaults above. */
 void labs_default_config(labs_config *cfg);
@@ -222,6 +235,50 @@ int labs_net_gradients(const float *dev_params, const float *dev_x, const int32_
 /* One AdamW step (beta 0.9/0.999, eps 1e-8; weight decay on weights, not biases). */
 int labs_net_adamw(float *dev_params, const float *dev_grads, float *dev_m, float *dev_v, int64_t t,
                    float lr, float weight_decay, void *cuda_stream);
+
+/* ---- Learned proposal in the walk.
+ *
+ * labs_log arms the walk log: from the next labs_walk on, at the start of every chunk
+ * of chunk_steps steps, walker w fills record k*walkers + w of dev_records (k = chunks
+ * since this call) with its state and what followed it in the chunk, while the index
+ * is below capacity.  capacity 0 disarms. */
+int labs_log(labs_ctx *ctx, labs_log_record *dev_records, int64_t capacity);
+
+/* Training inputs of log records: target = the free variable flipped by the first step,
+ * wf = 1 when the ISL later fell below the record's start ISL (else 0; the flip term of
+ * the loss is then off), y = L^2 / (2 min_isl) / 8 (the merit factor reached within
+ * the chunk, scaled). */
+int labs_log_labels(const labs_log_record *dev_records, int64_t count, int32_t *dev_target,
+                    float *dev_y, float *dev_wf, void *cuda_stream);
+
+/* Network inputs (float32 [count][3][n], the layout labs_net_forward takes) of states
+ * given by their free-variable bits: 8 words each, stride_words apart (16 for a
+ * labs_log_record array). */
+int labs_features(int32_t L, const uint32_t *dev_bits, int64_t stride_words, int64_t count,
+                  float *dev_x, void *cuda_stream);
+
+/* Turns the learned mode on (dev_params != NULL) or off.  Needs LABS_FLAG_LEARNED at
+ * init.  Before every chunk launch of labs_walk the library then runs a proposal pass:
+ *   - flip scores of every walker's current state; at the chunk's first step the walker
+ *     tries, among the flips with dISL <= (lowest dISL) + tau, the highest-scored
+ *     (ties: lowest i) first, and continues in the plain order when none is admissible;
+ *   - restart candidates: the walker's own next random start (the plain choice) and
+ *     candidates-1 random perturbations of its best state; the one with the highest
+ *     restart score (ties: lowest index) is used at the walker's next restart.
+ * The exact int32 ISL decides every move; the network only orders candidates.
+ * dev_ws: labs_learned_workspace_bytes bytes.  Chunks run without a CUDA graph. */
+int labs_learned_workspace_bytes(const labs_ctx *ctx, int32_t candidates, size_t *bytes);
+int labs_learned(labs_ctx *ctx, const float *dev_params, int32_t tau, int32_t candidates,
+                 void *dev_ws, size_t ws_bytes);
+
+/* Replay dumps for the walkers armed by labs_trace, in learned mode: per traced walker
+ * j, up to capacity learned steps (the scores it used, [j][capacity][n_max] floats, and
+ * the step, [j][capacity]) and up to capacity proposed restarts (the state used,
+ * [j][capacity][8] words, and the restart index, [j][capacity]).  The count arrays ([k]
+ * int32, zeroed by the caller) receive how many entries each walker wrote. */
+int labs_trace_learned(labs_ctx *ctx, int32_t capacity, float *dev_scores, int64_t *dev_score_step,
+                       int32_t *dev_score_count, uint32_t *dev_restart, int64_t *dev_restart_idx,
+                       int32_t *dev_restart_count);
 
 /* Checkpoint of every walker's state (sequence, ISL, best, counters, random-stream
  * position) and, with with_tabu != 0, its HT.  With the HT included a restored run

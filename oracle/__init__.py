@@ -91,6 +91,9 @@ def lib():
             L.lo_walk.argtypes = [i32, u64, i64, i64, i64, ctypes.POINTER(WalkCfg), P, P, P, P, P, i32]
             L.lo_walk.restype = ctypes.c_int
             L.lo_enumerate.argtypes = [i32, P, P, P, P, i32]; L.lo_enumerate.restype = ctypes.c_int
+            L.lo_walk_replay.argtypes = [i32, u64, i64, i64, ctypes.POINTER(WalkCfg), i32, i32, P, P, i32, i32, P, P,
+                                         P, P, P, P, P]
+            L.lo_walk_replay.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -244,3 +247,32 @@ def enumerate_skew(L: int, nthreads: int = 0) -> tuple[int, int, int, np.ndarray
     if rc != 0:
         raise ValueError("enumeration needs odd 3 <= L <= 79")
     return int(m.value), int(cnt.value), int(first.value), seq
+
+
+def walk_replay(L: int, seed: int, walker: int, steps: int, *, tau: int, score_steps, scores, restart_idx,
+                restart_bits, tabu_log2: int = 16, probe_cap: int = 32, patience: int = 0,
+                target: tuple[int, int] = (17, 2)) -> dict:
+    """One walker of the learned mode, replayed from the choices a GPU run recorded:
+    scores [k][>= n] used at steps score_steps[k], restart states restart_bits [k][8] used
+    at restart indices restart_idx[k]."""
+    cfg = WalkCfg(tabu_log2, probe_cap, patience, target[0], target[1])
+    res = WalkResult()
+    ss = np.ascontiguousarray(score_steps, dtype=np.int64)
+    sc = np.ascontiguousarray(scores, dtype=np.float32)
+    if sc.ndim == 1:
+        sc = sc.reshape(len(ss), -1)
+    ri = np.ascontiguousarray(restart_idx, dtype=np.int64)
+    rb = np.ascontiguousarray(restart_bits, dtype=np.uint32).reshape(-1)
+    best = np.zeros(L, dtype=np.int8)
+    final = np.zeros(L, dtype=np.int8)
+    tc = np.zeros(steps, dtype=np.int32)
+    ti = np.zeros(steps, dtype=np.int32)
+    stride = sc.shape[1] if sc.size else 1
+    rc = lib().lo_walk_replay(L, seed, walker, steps, ctypes.byref(cfg), tau, len(ss), _ptr(ss), _ptr(sc), stride,
+                              len(ri), _ptr(ri), _ptr(rb), ctypes.byref(res), _ptr(best), _ptr(final), _ptr(tc),
+                              _ptr(ti))
+    if rc != 0:
+        raise RuntimeError("oracle replay failed: %d" % rc)
+    out = {f: getattr(res, f) for f in WALK_RESULT_FIELDS}
+    out.update(best_seq=best, final_seq=final, trace_code=tc, trace_isl=ti)
+    return out

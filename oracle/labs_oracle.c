@@ -337,13 +337,28 @@ typedef struct {
  * only restarts).  The ISL trace holds the ISL at the end of the step. */
 #define LO_TRACE_RESTART 0x10000
 
+/* Learned-mode replay inputs (the network's choices recorded by the GPU run):
+ * at step score_step[k] (steps done before it) the walker used scores[k][0..n) with the
+ * threshold tau; at restart index restart_idx[k] it started from restart_bits[k][0..8). */
+typedef struct {
+    int32_t tau;
+    int32_t n_score;
+    const int64_t *score_step;
+    const float *scores;
+    int32_t score_stride;
+    int32_t n_restart;
+    const int64_t *restart_idx;
+    const uint32_t *restart_bits;
+} lo_replay;
+
 typedef struct {
     int32_t L, n;
     uint64_t seed;
     uint32_t g;
     const lo_walk_cfg *cfg;
     const uint64_t *zkey;
-    int8_t *x, *s, *s_best, *sf;
+    const lo_replay *replay;
+    int8_t *x, *s, *s_best, *sf, *tried;
     int64_t *delta;
     int32_t *order;
     lo_ht ht;
@@ -375,7 +390,17 @@ static void note_best(lo_walker *w, int64_t steps_done)
  * insert S into HT, and take it as the best so far. */
 static void start(lo_walker *w, int64_t steps_done)
 {
-    lo_random_start(w->seed, w->g, w->restart_index, w->L, w->x);
+    const lo_replay *rp = w->replay;
+    int32_t k = -1;
+    if (rp)
+        for (int32_t j = 0; j < rp->n_restart; ++j)
+            if (rp->restart_idx[j] == (int64_t)w->restart_index) k = j;
+    if (k >= 0) {
+        for (int32_t i = 0; i < w->n; ++i)
+            w->x[i] = ((rp->restart_bits[8 * k + i / 32] >> (i % 32)) & 1u) ? -1 : 1;
+    } else {
+        lo_random_start(w->seed, w->g, w->restart_index, w->L, w->x);
+    }
     lo_skew_expand(w->x, w->L, w->s);
     w->isl = lo_isl(w->s, w->L);
     w->fp = lo_fingerprint(w->s, w->L);
@@ -399,6 +424,14 @@ static int cmp_pair(const int64_t *delta, int32_t a, int32_t b)
     return a < b ? -1 : (a > b);
 }
 
+/* Scores are compared through a monotone map of their bit pattern to int32. */
+static int32_t score_key(float f)
+{
+    int32_t k;
+    memcpy(&k, &f, sizeof(k));
+    return k >= 0 ? k : (k ^ 0x7FFFFFFF);
+}
+
 /* One step of the walk; returns the trace code, or -99 on an internal mismatch. */
 static int32_t walk_step(lo_walker *w, int64_t steps_done_after)
 {
@@ -415,7 +448,33 @@ static int32_t walk_step(lo_walker *w, int64_t steps_done_after)
     }
     int32_t chosen = -1;
     uint64_t fp_new = 0;
-    for (int32_t t = 0; t < n; ++t) {
+    /* learned step: flips with dISL <= min dISL + tau, by (score desc, i asc), first */
+    const lo_replay *rp = w->replay;
+    int32_t ks = -1;
+    if (rp)
+        for (int32_t j = 0; j < rp->n_score; ++j)
+            if (rp->score_step[j] == steps_done_after - 1) ks = j;
+    if (ks >= 0) {
+        const float *sc = rp->scores + (int64_t)ks * rp->score_stride;
+        int64_t thr = w->delta[w->order[0]] + rp->tau;
+        for (;;) {
+            int32_t pick = -1;
+            for (int32_t i = 0; i < n; ++i) {
+                if (w->delta[i] > thr || w->tried[i]) continue;
+                if (pick < 0 || score_key(sc[i]) > score_key(sc[pick])) pick = i;
+            }
+            if (pick < 0) break;
+            w->tried[pick] = 1;
+            uint64_t f = w->fp ^ w->zkey[pick];
+            if (!ht_contains(&w->ht, f)) {
+                chosen = pick;
+                fp_new = f;
+                break;
+            }
+        }
+        for (int32_t i = 0; i < n; ++i) w->tried[i] = 0;
+    }
+    for (int32_t t = 0; t < n && chosen < 0; ++t) {
         int32_t i = w->order[t];
         uint64_t f = w->fp ^ w->zkey[i];
         if (!ht_contains(&w->ht, f)) {
@@ -468,7 +527,7 @@ typedef struct {
     int status;
 } lo_walk_job;
 
-static int run_walker(lo_walk_job *job, int64_t w_idx)
+static int run_walker(lo_walk_job *job, int64_t w_idx, const lo_replay *replay)
 {
     int32_t L = job->L, n = (L + 1) / 2;
     lo_walker w;
@@ -479,6 +538,8 @@ static int run_walker(lo_walk_job *job, int64_t w_idx)
     w.g = (uint32_t)(job->g0 + w_idx);
     w.cfg = job->cfg;
     w.zkey = job->zkey;
+    w.replay = replay;
+    w.tried = (int8_t *)calloc((size_t)n, 1);
     w.x = (int8_t *)malloc((size_t)L);
     w.s = (int8_t *)malloc((size_t)L);
     w.s_best = (int8_t *)malloc((size_t)L);
@@ -492,7 +553,7 @@ static int run_walker(lo_walk_job *job, int64_t w_idx)
     w.best_isl = INT64_MAX;
     w.res.target_step = -1;
     int rc = 0;
-    if (!w.x || !w.s || !w.s_best || !w.delta || !w.order || !w.ht.slot) {
+    if (!w.x || !w.s || !w.s_best || !w.delta || !w.order || !w.ht.slot || !w.tried) {
         rc = -3;
         goto done;
     }
@@ -514,7 +575,7 @@ static int run_walker(lo_walk_job *job, int64_t w_idx)
     if (job->best_seq) memcpy(job->best_seq + w_idx * L, w.s_best, (size_t)L);
     if (job->final_seq) memcpy(job->final_seq + w_idx * L, w.s, (size_t)L);
 done:
-    free(w.x); free(w.s); free(w.s_best); free(w.delta); free(w.order); free(w.ht.slot);
+    free(w.x); free(w.s); free(w.s_best); free(w.delta); free(w.order); free(w.ht.slot); free(w.tried);
     return rc;
 }
 
@@ -526,7 +587,7 @@ static void *walk_thread(void *arg)
         int64_t w = job->next++;
         pthread_mutex_unlock(&job->lock);
         if (w >= job->count) break;
-        int rc = run_walker(job, w);
+        int rc = run_walker(job, w, NULL);
         if (rc != 0) {
             pthread_mutex_lock(&job->lock);
             job->status = rc;
@@ -569,6 +630,31 @@ int lo_walk(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t steps,
     pthread_mutex_destroy(&job.lock);
     free(zkey);
     return job.status;
+}
+
+/* One walker (id g) replayed with the learned-mode choices of a GPU run (lo_replay);
+ * outputs as lo_walk for a single walker (trace arrays of `steps` entries, nullable). */
+int lo_walk_replay(int32_t L, uint64_t seed, int64_t g, int64_t steps, const lo_walk_cfg *cfg, int32_t tau,
+                   int32_t n_score, const int64_t *score_step, const float *scores, int32_t score_stride,
+                   int32_t n_restart, const int64_t *restart_idx, const uint32_t *restart_bits,
+                   lo_walk_result *res, int8_t *best_seq, int8_t *final_seq, int32_t *trace_code,
+                   int32_t *trace_isl)
+{
+    if (L < 3 || (L & 1) == 0 || steps < 0 || !cfg || !res || g < 0 || g >= 0x100000000ll) return -1;
+    if (cfg->tabu_log2 < 1 || cfg->tabu_log2 > 20 || cfg->probe_cap < 1) return -1;
+    int32_t n = (L + 1) / 2;
+    uint64_t *zkey = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    if (!zkey) return -3;
+    for (int32_t i = 0; i < n; ++i) zkey[i] = lo_zobrist_key(L, i);
+    lo_replay rp = {tau, n_score, score_step, scores, score_stride, n_restart, restart_idx, restart_bits};
+    lo_walk_job job;
+    memset(&job, 0, sizeof(job));
+    job.L = L; job.seed = seed; job.g0 = g; job.count = 1; job.steps = steps;
+    job.cfg = cfg; job.zkey = zkey; job.res = res; job.best_seq = best_seq;
+    job.final_seq = final_seq; job.trace_code = trace_code; job.trace_isl = trace_isl;
+    int rc = run_walker(&job, 0, &rp);
+    free(zkey);
+    return rc;
 }
 
 /* ------------------------------------------------- exhaustive skew enumeration */

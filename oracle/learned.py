@@ -191,6 +191,6 @@ def features(seq: np.ndarray, C_even: np.ndarray, delta: np.ndarray) -> np.ndarr
     x[0] = seq[:n]
     c = np.zeros(n, dtype=np.float32)
     c[:n - 1] = C_even[:n - 1]
-    x[1] = c / np.float32(np.sqrt(L))
+    x[1] = c / np.sqrt(np.float32(L))
     x[2] = np.asarray(delta, dtype=np.float32) / np.float32(8 * L)
     return x

@@ -26,7 +26,10 @@ import torch
 from . import _native
 from ._native import LabsConfig, LabsCounters, LabsError  # noqa: F401
 
-__all__ = ["Search", "isl", "neighbor_delta", "enumerate_skew", "config", "LabsError", "library"]
+__all__ = ["Search", "isl", "neighbor_delta", "enumerate_skew", "config", "LabsError", "library", "features",
+           "log_labels"]
+
+LOG_RECORD_WORDS = 16  # a labs_log_record is 16 32-bit words
 
 
 def library():
@@ -176,6 +179,41 @@ class Search:
         self._trace_bufs = (code, isl_)
         return code[:k], isl_[:k]
 
+    def log(self, capacity: int) -> torch.Tensor:
+        """Arm the walk log: returns the record buffer (uint8 [capacity, 64]); record
+        k*W + w is walker w's k-th chunk from now (see labs_log_record)."""
+        buf = torch.zeros((max(capacity, 1), _native.LOG_RECORD_BYTES), dtype=torch.uint8, device=self.device)
+        self._c(self.lib.labs_log(self.ctx, _ptr(buf), int(capacity)))
+        self._log_buf = buf
+        return buf[:capacity]
+
+    def learned(self, params: torch.Tensor | None, tau: int = 0, candidates: int = 4):
+        """Turn the learned mode on with network parameters (float32 CUDA tensor) or off."""
+        if params is None:
+            self._c(self.lib.labs_learned(self.ctx, None, 0, 1, None, 0))
+            self._learned_ws = None
+            return
+        nbytes = ctypes.c_size_t()
+        self._c(self.lib.labs_learned_workspace_bytes(self.ctx, int(candidates), ctypes.byref(nbytes)))
+        self._learned_ws = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        self._learned_params = params
+        self._c(self.lib.labs_learned(self.ctx, _ptr(params), int(tau), int(candidates), _ptr(self._learned_ws),
+                                      nbytes.value))
+
+    def trace_learned(self, k: int, capacity: int, n_max: int) -> dict:
+        """Replay dumps of the k walkers armed by trace() (learned mode)."""
+        d = {"scores": torch.zeros((k, capacity, n_max), dtype=torch.float32, device=self.device),
+             "score_step": torch.zeros((k, capacity), dtype=torch.int64, device=self.device),
+             "score_count": torch.zeros(k, dtype=torch.int32, device=self.device),
+             "restart": torch.zeros((k, capacity, 8), dtype=torch.int32, device=self.device),
+             "restart_idx": torch.zeros((k, capacity), dtype=torch.int64, device=self.device),
+             "restart_count": torch.zeros(k, dtype=torch.int32, device=self.device)}
+        self._c(self.lib.labs_trace_learned(self.ctx, int(capacity), _ptr(d["scores"]), _ptr(d["score_step"]),
+                                            _ptr(d["score_count"]), _ptr(d["restart"]), _ptr(d["restart_idx"]),
+                                            _ptr(d["restart_count"])))
+        self._dumps = d
+        return d
+
     def checkpoint(self, with_tabu: bool = True) -> bytearray:
         n = ctypes.c_size_t()
         self._c(self.lib.labs_checkpoint(self.ctx, int(with_tabu), None, ctypes.byref(n)))
@@ -267,3 +305,26 @@ def enumerate_skew(L: int, device=None, stream=None) -> tuple[int, int, int]:
         _check(lib.labs_enumerate(int(L), _ptr(scratch), nbytes.value, ctypes.byref(m), ctypes.byref(cnt),
                                   ctypes.byref(first), _stream_handle(stream)), lib)
     return m.value, cnt.value, first.value
+
+
+def log_labels(records: torch.Tensor, stream=None):
+    """(target int32, y float32, wf float32) of walk-log records (uint8 [N, 64])."""
+    lib = library()
+    N = records.shape[0]
+    dev = records.device
+    target = torch.empty(N, dtype=torch.int32, device=dev)
+    y = torch.empty(N, dtype=torch.float32, device=dev)
+    wf = torch.empty(N, dtype=torch.float32, device=dev)
+    stream = stream or torch.cuda.current_stream(dev)
+    _check(lib.labs_log_labels(_ptr(records), N, _ptr(target), _ptr(y), _ptr(wf), _stream_handle(stream)), lib)
+    return target, y, wf
+
+
+def features(L: int, bits: torch.Tensor, stride_words: int, count: int, stream=None) -> torch.Tensor:
+    """Network inputs float32 [count, 3, n] of states given as free-variable bit words."""
+    lib = library()
+    n = (L + 1) // 2
+    x = torch.empty((count, 3, n), dtype=torch.float32, device=bits.device)
+    stream = stream or torch.cuda.current_stream(bits.device)
+    _check(lib.labs_features(int(L), _ptr(bits), int(stride_words), int(count), _ptr(x), _stream_handle(stream)), lib)
+    return x

@@ -24,6 +24,8 @@ LABS_TRACE_RESTART = 0x10000
 LABS_TRACE_BLOCKED = -1
 LABS_FLAG_NO_GRAPH = 1
 LABS_FLAG_CHECK_STATE = 2
+LABS_FLAG_LEARNED = 4
+LOG_RECORD_BYTES = 64
 
 ERRORS = {LABS_EINVAL: "EINVAL", LABS_ENOMEM: "ENOMEM", LABS_ECUDA: "ECUDA", LABS_ETIMEOUT: "ETIMEOUT",
           LABS_ECANCELLED: "ECANCELLED", LABS_ESTATE: "ESTATE"}
@@ -34,7 +36,8 @@ EXPORTS = [
     "labs_reset", "labs_isl", "labs_neighbor_delta", "labs_walk", "labs_sync", "labs_best",
     "labs_walker_results", "labs_stats", "labs_trace", "labs_enumerate_scratch_bytes", "labs_enumerate",
     "labs_enumerate_noalloc", "labs_net_sizes", "labs_net_init", "labs_net_forward", "labs_net_gradients",
-    "labs_net_adamw", "labs_checkpoint", "labs_restore", "labs_set_deadline", "labs_cancel", "labs_clear_stop",
+    "labs_net_adamw", "labs_log", "labs_log_labels", "labs_features", "labs_learned_workspace_bytes",
+    "labs_learned", "labs_trace_learned", "labs_checkpoint", "labs_restore", "labs_set_deadline", "labs_cancel", "labs_clear_stop",
     "labs_last_error", "labs_destroy",
 ]
 
@@ -108,6 +111,12 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
             "labs_net_forward": (ctypes.c_int, [P, P, i64, i32, P, P, P, sz, P]),
             "labs_net_gradients": (ctypes.c_int, [P, P, P, P, P, i64, i32, P, P, P, sz, P]),
             "labs_net_adamw": (ctypes.c_int, [P, P, P, P, i64, ctypes.c_float, ctypes.c_float, P]),
+            "labs_log": (ctypes.c_int, [P, P, i64]),
+            "labs_log_labels": (ctypes.c_int, [P, i64, P, P, P, P]),
+            "labs_features": (ctypes.c_int, [i32, P, i64, i64, P, P]),
+            "labs_learned_workspace_bytes": (ctypes.c_int, [P, i32, ctypes.POINTER(sz)]),
+            "labs_learned": (ctypes.c_int, [P, P, i32, i32, P, sz]),
+            "labs_trace_learned": (ctypes.c_int, [P, i32, P, P, P, P, P, P]),
             "labs_checkpoint": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.POINTER(sz)]),
             "labs_restore": (ctypes.c_int, [P, P, sz]),
             "labs_set_deadline": (ctypes.c_int, [P, u64]),

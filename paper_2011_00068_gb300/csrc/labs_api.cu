@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <ctime>
@@ -30,7 +31,23 @@ struct labs_ctx {
     int n_max = 0;
     // workspace layout (byte offsets)
     size_t off_status = 0, off_groups = 0, off_zkeys = 0, off_states = 0, off_trace_start = 0,
-           off_trace_ids = 0, off_queue = 0, off_tabu = 0, total = 0;
+           off_trace_ids = 0, off_queue = 0, off_l_scores = 0, off_l_step = 0, off_l_slot = 0, off_l_valid = 0,
+           off_tabu = 0, total = 0;
+    // device pointers kept in the status block (restored after every reset)
+    labs_log_record* log = nullptr;
+    int64_t log_capacity = 0, log_start = 0;
+    float* d_scores = nullptr;
+    int64_t* d_score_step = nullptr;
+    int32_t* d_score_count = nullptr;
+    uint32_t* d_restart = nullptr;
+    int64_t* d_restart_idx = nullptr;
+    int32_t* d_restart_count = nullptr;
+    int32_t d_cap = 0;
+    // learned mode
+    const float* l_params = nullptr;
+    int32_t l_tau = 0, l_cands = 0;
+    char* l_ws = nullptr;
+    size_t l_ws_bytes = 0;
     char* ws = nullptr;
     Control* ctrl_host = nullptr;
     Control* ctrl_dev = nullptr;
@@ -199,6 +216,16 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     off = align_up(off + sizeof(int64_t) * kMaxTrace, 256);
     c->off_queue = off;
     off = align_up(off + sizeof(uint32_t) * kMaxChunksPerCall, 256);
+    if (k.flags & LABS_FLAG_LEARNED) {
+        c->off_l_scores = off;
+        off = align_up(off + sizeof(float) * (size_t)c->W * c->n_max, 256);
+        c->off_l_step = off;
+        off = align_up(off + sizeof(int64_t) * (size_t)c->W, 256);
+        c->off_l_slot = off;
+        off = align_up(off + sizeof(uint32_t) * kBitWords * (size_t)c->W, 256);
+        c->off_l_valid = off;
+        off = align_up(off + sizeof(int32_t) * (size_t)c->W, 256);
+    }
     c->off_tabu = off;
     off = align_up(off + sizeof(uint64_t) * ((size_t)c->W << k.tabu_log2), 256);
     c->total = off;
@@ -259,6 +286,75 @@ int sync_status(labs_ctx* c)
         const int32_t zero = 0;
         cudaMemcpy(&at<DevStatus>(c, c->off_status)->invalid_rows, &zero, sizeof(zero), cudaMemcpyHostToDevice);
         return fail(c, LABS_EINVAL, "%d input rows were not +-1 / not skew-symmetric", st.invalid_rows);
+    }
+    return LABS_OK;
+}
+
+// Writes the log / learned / dump pointers into the device status block.
+int push_status(labs_ctx* c)
+{
+    DevStatus h;
+    memset(&h, 0, sizeof(h));
+    h.log = c->log;
+    h.log_capacity = c->log_capacity;
+    h.log_start = c->log_start;
+    const bool lw = (c->cfg.flags & LABS_FLAG_LEARNED) != 0;
+    h.l_scores = lw ? at<float>(c, c->off_l_scores) : nullptr;
+    h.l_score_step = lw ? at<int64_t>(c, c->off_l_step) : nullptr;
+    h.l_slot = lw ? at<uint32_t>(c, c->off_l_slot) : nullptr;
+    h.l_slot_valid = lw ? at<int32_t>(c, c->off_l_valid) : nullptr;
+    h.l_tau = c->l_tau;
+    h.learned = (lw && c->l_params) ? 1 : 0;
+    h.d_scores = c->d_scores;
+    h.d_score_step = c->d_score_step;
+    h.d_score_count = c->d_score_count;
+    h.d_restart = c->d_restart;
+    h.d_restart_idx = c->d_restart_idx;
+    h.d_restart_count = c->d_restart_count;
+    h.d_cap = c->d_cap;
+    const size_t a = offsetof(DevStatus, log), b = offsetof(DevStatus, pad1);
+    cudaError_t e = cudaMemcpyAsync(c->ws + c->off_status + a, reinterpret_cast<char*>(&h) + a, b - a,
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? LABS_OK : cuda_fail(c, e, "status pointers");
+}
+
+constexpr int64_t kProposalBatch = 8192;  // states per network call in a proposal pass
+
+size_t learned_ws_bytes(const labs_ctx* c, int cands)
+{
+    const size_t x = align_up(sizeof(float) * 3 * (size_t)c->n_max * kProposalBatch, 256);
+    const size_t cand = align_up(sizeof(uint32_t) * kBitWords * (size_t)kProposalBatch, 256);
+    (void)cands;
+    return x + cand + net_workspace_bytes(kProposalBatch, c->n_max);
+}
+
+// Flip scores and restart proposals for every walker (learned mode), before a chunk.
+int proposal_pass(labs_ctx* c)
+{
+    const KParams p = params(c);
+    const int P = c->l_cands;
+    float* x = reinterpret_cast<float*>(c->l_ws);
+    uint32_t* cand =
+        reinterpret_cast<uint32_t*>(c->l_ws + align_up(sizeof(float) * 3 * (size_t)c->n_max * kProposalBatch, 256));
+    void* nws = c->l_ws + (learned_ws_bytes(c, P) - net_workspace_bytes(kProposalBatch, c->n_max));
+    const int64_t S = std::max<int64_t>(1, kProposalBatch / P);
+    const WalkerState* states = at<WalkerState>(c, c->off_states);
+    for (int g = 0; g < c->nG; ++g) {
+        const DevGroup& G = c->groups[g];
+        for (int64_t s0 = G.first; s0 < G.first + G.count; s0 += S) {
+            const int64_t cnt = std::min<int64_t>(S, G.first + G.count - s0);
+            const float *sc = nullptr, *rs = nullptr;
+            int rc = launch_features(reinterpret_cast<const uint32_t*>(states + s0), sizeof(WalkerState) / 4, cnt,
+                                     G.L, x, c->stream);
+            if (!rc) rc = net_forward_ws(c->l_params, x, cnt, G.n, nws, &sc, &rs, c->stream);
+            if (!rc) rc = launch_scores(p, s0, cnt, G.n, sc, c->stream);
+            if (!rc) rc = launch_candidates(p, s0, cnt, G.n, P, cand, c->stream);
+            if (!rc) rc = launch_features(cand, kBitWords, cnt * P, G.L, x, c->stream);
+            if (!rc) rc = net_forward_ws(c->l_params, x, cnt * P, G.n, nws, &sc, &rs, c->stream);
+            if (!rc) rc = launch_select(p, s0, cnt, P, rs, cand, c->stream);
+            if (rc) return fail(c, rc, "proposal pass: %s", cudaGetErrorString(cudaGetLastError()));
+        }
     }
     return LABS_OK;
 }
@@ -350,9 +446,15 @@ int labs_reset(labs_ctx* c)
         rc = launch_reset(p, grid, block, c->stream);
         if (rc) return fail(c, rc, "reset launch: %s", cudaGetErrorString(cudaGetLastError()));
     }
+    if (c->cfg.flags & LABS_FLAG_LEARNED) {
+        e = cudaMemsetAsync(c->ws + c->off_l_step, 0xFF, sizeof(int64_t) * (size_t)c->W, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + c->off_l_valid, 0, sizeof(int32_t) * (size_t)c->W, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "learned state clear");
+    }
     c->planned = 0;
     c->catch_up = false;
-    return LABS_OK;
+    c->log_start = 0;
+    return push_status(c);
 }
 
 int labs_bind_workspace(labs_ctx* c, void* dev_workspace, size_t bytes)
@@ -422,8 +524,12 @@ int labs_walk(labs_ctx* c, int64_t steps)
         const int nchunks = (int)std::min<int64_t>((span + c->chunk - 1) / c->chunk, kMaxChunksPerCall);
         rc = launch_prep_walk(p, take, nchunks, c->stream);
         if (rc) return fail(c, rc, "walk preparation launch");
-        if (c->cfg.flags & LABS_FLAG_NO_GRAPH) {
+        if ((c->cfg.flags & LABS_FLAG_NO_GRAPH) || c->l_params) {
             for (int j = 0; j < nchunks; ++j) {
+                if (c->l_params) {
+                    rc = proposal_pass(c);
+                    if (rc) return rc;
+                }
                 rc = launch_walk_chunk(p, j, c->grid, c->warps_per_cta, c->smem_bytes, c->stream);
                 if (rc) return fail(c, rc, "walk launch: %s", cudaGetErrorString(cudaGetLastError()));
             }
@@ -578,6 +684,81 @@ int labs_trace(labs_ctx* c, const int64_t* host_walker_ids, int32_t k, int64_t c
     }
     rc = launch_trace_arm(params(c), ids, k, dev_code_log, dev_isl_log, capacity, c->stream);
     return rc ? fail(c, rc, "trace launch") : LABS_OK;
+}
+
+int labs_log(labs_ctx* c, labs_log_record* dev_records, int64_t capacity)
+{
+    int rc = need_ws(c);
+    if (rc) return rc;
+    if (capacity < 0 || (capacity > 0 && !dev_records)) return fail(c, LABS_EINVAL, "bad log buffer");
+    cudaSetDevice(c->device);
+    c->log = capacity > 0 ? dev_records : nullptr;
+    c->log_capacity = capacity;
+    c->log_start = c->planned;
+    return push_status(c);
+}
+
+int labs_log_labels(const labs_log_record* dev_records, int64_t count, int32_t* dev_target, float* dev_y,
+                    float* dev_wf, void* cuda_stream)
+{
+    if (count < 0 || (count > 0 && (!dev_records || !dev_target || !dev_y || !dev_wf))) return LABS_EINVAL;
+    if (count == 0) return LABS_OK;
+    return launch_labels(dev_records, count, dev_target, dev_y, dev_wf, cuda_stream);
+}
+
+int labs_features(int32_t L, const uint32_t* dev_bits, int64_t stride_words, int64_t count, float* dev_x,
+                  void* cuda_stream)
+{
+    if (!valid_L(L) || count < 0 || stride_words < kBitWords || (count > 0 && (!dev_bits || !dev_x)))
+        return LABS_EINVAL;
+    return launch_features(dev_bits, stride_words, count, L, dev_x, cuda_stream);
+}
+
+int labs_learned_workspace_bytes(const labs_ctx* c, int32_t candidates, size_t* bytes)
+{
+    if (!c || !bytes || candidates < 1 || candidates > 64) return LABS_EINVAL;
+    *bytes = learned_ws_bytes(c, candidates);
+    return LABS_OK;
+}
+
+int labs_learned(labs_ctx* c, const float* dev_params, int32_t tau, int32_t candidates, void* dev_ws, size_t ws_bytes)
+{
+    int rc = need_ws(c);
+    if (rc) return rc;
+    if (dev_params) {
+        if (!(c->cfg.flags & LABS_FLAG_LEARNED)) return fail(c, LABS_EINVAL, "context created without LABS_FLAG_LEARNED");
+        if (tau < 0 || candidates < 1 || candidates > 64) return fail(c, LABS_EINVAL, "bad tau / candidates");
+        if (!dev_ws || ws_bytes < learned_ws_bytes(c, candidates))
+            return fail(c, LABS_ENOMEM, "learned workspace needs %zu bytes", learned_ws_bytes(c, candidates));
+    }
+    cudaSetDevice(c->device);
+    c->l_params = dev_params;
+    c->l_tau = tau;
+    c->l_cands = candidates;
+    c->l_ws = static_cast<char*>(dev_ws);
+    c->l_ws_bytes = ws_bytes;
+    return push_status(c);
+}
+
+int labs_trace_learned(labs_ctx* c, int32_t capacity, float* dev_scores, int64_t* dev_score_step,
+                       int32_t* dev_score_count, uint32_t* dev_restart, int64_t* dev_restart_idx,
+                       int32_t* dev_restart_count)
+{
+    int rc = need_ws(c);
+    if (rc) return rc;
+    if (capacity < 0 || (capacity > 0 && (!dev_scores || !dev_score_step || !dev_score_count || !dev_restart ||
+                                          !dev_restart_idx || !dev_restart_count)))
+        return fail(c, LABS_EINVAL, "bad dump buffers");
+    cudaSetDevice(c->device);
+    const bool on = capacity > 0;
+    c->d_scores = on ? dev_scores : nullptr;
+    c->d_score_step = on ? dev_score_step : nullptr;
+    c->d_score_count = on ? dev_score_count : nullptr;
+    c->d_restart = on ? dev_restart : nullptr;
+    c->d_restart_idx = on ? dev_restart_idx : nullptr;
+    c->d_restart_count = on ? dev_restart_count : nullptr;
+    c->d_cap = capacity;
+    return push_status(c);
 }
 
 int labs_enumerate_scratch_bytes(int32_t L, size_t* bytes)

@@ -67,7 +67,26 @@ struct alignas(256) DevStatus {
     unsigned long long st_steps, st_evals, st_restarts, st_overflows, st_blocked, st_at_target;
     long long st_target_step;     // min over walkers, LLONG_MAX = none
     unsigned long long probe_ns;  // %globaltimer sample (clock alignment for deadlines)
-    int32_t pad1[6];
+    // walk log (labs_log): record k*W + w is walker w's chunk k since arming
+    labs_log_record* log;
+    int64_t log_capacity;
+    int64_t log_start;            // step count at arming
+    // learned mode (labs_learned)
+    float* l_scores;              // [W][n_max] flip scores for the step l_score_step[w]
+    int64_t* l_score_step;        // [W], -1 = none
+    uint32_t* l_slot;             // [W][8] proposed restart state
+    int32_t* l_slot_valid;        // [W]
+    int32_t l_tau;
+    int32_t learned;
+    // replay dumps of traced walkers in learned mode
+    float* d_scores;              // [trace slot][cap][n_max]
+    int64_t* d_score_step;        // [trace slot][cap]
+    int32_t* d_score_count;       // [trace slot]
+    uint32_t* d_restart;          // [trace slot][cap][8]
+    int64_t* d_restart_idx;       // [trace slot][cap]
+    int32_t* d_restart_count;     // [trace slot]
+    int32_t d_cap;
+    int32_t pad1[1];
 };
 
 // Host-written control block in mapped pinned host memory (read by running kernels).
@@ -145,6 +164,19 @@ int launch_stats(const KParams& p, int32_t L, void* stream);
 int launch_trace_arm(const KParams& p, const int64_t* dev_ids, int32_t k, int32_t* code,
                      int32_t* isl, int64_t capacity, void* stream);
 int launch_time_probe(unsigned long long* dev_out, void* stream);
+int launch_features(const uint32_t* bits, int64_t stride, int64_t count, int32_t L, float* x, void* stream);
+int launch_candidates(const KParams& p, int64_t first, int64_t count, int n, int P, uint32_t* out, void* stream);
+int launch_select(const KParams& p, int64_t first, int64_t count, int P, const float* score, const uint32_t* cand,
+                  void* stream);
+int launch_scores(const KParams& p, int64_t first, int64_t count, int n, const float* score, void* stream);
+int launch_labels(const labs_log_record* rec, int64_t count, int32_t* target, float* y, float* wf, void* stream);
+
+// Learned network (labs_net.cu): forward of a batch of float inputs [B][3][n] into the
+// caller's workspace; scores [B][n] and restart [B] are returned as device pointers
+// inside that workspace.
+size_t net_workspace_bytes(int64_t B, int n);
+int net_forward_ws(const float* params, const float* x, int64_t B, int n, void* ws, const float** scores,
+                   const float** restart, void* stream);
 
 // Partial / final result of the exhaustive skew search (labs_enum.cu).
 struct EnumPart {

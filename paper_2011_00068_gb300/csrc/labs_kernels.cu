@@ -398,6 +398,14 @@ struct WalkEnv {
     WalkerState* st;
     int L, n, patience, lane;
     uint32_t g;
+    // learned mode (null when off): proposed restart state and its flag
+    uint32_t* slot;
+    int32_t* slot_valid;
+    // replay dumps of a traced walker in learned mode (null when off)
+    uint32_t* rdump;   // [cap][8]
+    int64_t* rdump_idx;
+    int32_t* rdump_count;
+    int dump_cap;
 };
 
 __device__ __forceinline__ bool target_met(const KParams& p, int L, int isl)
@@ -418,10 +426,27 @@ __device__ __forceinline__ void note_best(const WalkEnv& env, Walker& w)
 
 // Algorithm 1 start: random skew-symmetric S (restart index w.restart_idx), its ISL,
 // insert it into HT (a fresh generation: its home slot is free), best update.
-__device__ void start_walker(const WalkEnv& env, Walker& w, int* base, const WarpSmem& SL, const View& V)
+__device__ void start_walker(const WalkEnv& env, Walker& w, int* base, const WarpSmem& SL, const View& V,
+                             bool proposed = false)
 {
     const int lane = env.lane;
-    w.word = lane < kBitWords ? start_word(env.p->seed, env.g, w.restart_idx, lane, env.n) : 0u;
+    if (proposed) {
+        // learned mode: the restart state chosen by the proposal pass replaces the draw
+        w.word = lane < kBitWords ? env.slot[lane] : 0u;
+        if (env.rdump != nullptr) {
+            const int k = *env.rdump_count;
+            if (k < env.dump_cap) {
+                if (lane < kBitWords) env.rdump[(int64_t)k * kBitWords + lane] = w.word;
+                if (lane == 0) env.rdump_idx[k] = w.restart_idx;
+            }
+            __syncwarp();
+            if (lane == 0) *env.rdump_count = k + 1;
+        }
+        __syncwarp();
+        if (lane == 0) *env.slot_valid = 0;
+    } else {
+        w.word = lane < kBitWords ? start_word(env.p->seed, env.g, w.restart_idx, lane, env.n) : 0u;
+    }
     w.isl = load_rows(base, SL, V, w.word, env.L, env.n, lane);
     w.fp = fingerprint_all(w.word, env.zk, env.n, lane);
     if (lane == 0) env.T[w.fp & env.tmask] = (w.fp & ~kGenMask) | w.gen;
@@ -443,7 +468,8 @@ __device__ void restart_walker(const WalkEnv& env, Walker& w, int* base, const W
         __syncwarp();
         w.gen = 1;
     }
-    start_walker(env, w, base, SL, V);
+    const bool proposed = env.slot_valid != nullptr && *env.slot_valid != 0;
+    start_walker(env, w, base, SL, V, proposed);
 }
 
 // Warp-uniform: lane 0 reads the host-written control block and broadcasts.
@@ -504,9 +530,27 @@ __device__ __forceinline__ void exclude(uint32_t& excl, int bi, int lane)
     if (lane == pb * 16 + vb / R) excl |= 1u << (vb % R);
 }
 
+// Order-preserving map of a float score to int32 (the learned ordering compares these).
+__device__ __forceinline__ int score_key(float f)
+{
+    const int k = __float_as_int(f);
+    return k >= 0 ? k : (k ^ 0x7FFFFFFF);
+}
+
+// What a walk call records besides the trajectory.
+struct StepExtras {
+    const float* scores;  // learned flip scores for the first step of this call, or null
+    int tau;              // learned candidates: dISL <= min dISL + tau
+    float* sdump;         // replay dump of the scores used (traced walker), or null
+    int64_t* sdump_step;
+    int32_t* sdump_count;
+    int dump_cap, n_max;
+    labs_log_record* rec; // log record of this chunk, or null
+};
+
 template <int R>
 __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* base, const WarpSmem& SL,
-                           const View& V, int trace_slot, int64_t trace_start)
+                           const View& V, int trace_slot, int64_t trace_start, const StepExtras& ex)
 {
     const KParams& p = *env.p;
     const int lane = env.lane, n = env.n, c = n - 1;
@@ -514,6 +558,18 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
     const int cap = p.probe_cap;
     int P[R];
     p_direct<R>(V, n, lane, P);
+    const int64_t first_step = w.steps;
+    int log_first = 0, log_min = w.isl;
+    bool log_live = true;
+    if (ex.rec != nullptr) {
+        if (lane < kBitWords) ex.rec->bits[lane] = w.word;
+        if (lane == 0) {
+            ex.rec->isl = w.isl;
+            ex.rec->L = env.L;
+            ex.rec->walker = env.g;
+            ex.rec->step = w.steps;
+        }
+    }
     while (w.steps < until) {
         if ((w.steps & (kCheckEvery - 1)) == 0) {
             const int why = stop_requested(p, lane);
@@ -537,7 +593,60 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
         int best_i = -1, best_d = 0;
         int64_t slot = -1;
         uint64_t fnew = 0;
-        for (;;) {
+        if (ex.scores != nullptr && w.steps == first_step) {
+            // Learned step: among the flips with dISL <= min dISL + tau, try them by
+            // (score descending, i ascending) first; the plain order follows.
+            int lm = INT_MAX;
+#pragma unroll
+            for (int r = 0; r < R; ++r) lm = min(lm, dl[r]);
+            const int dmin = __reduce_min_sync(kFull, lm);
+            const int thr = dmin > INT_MAX - ex.tau ? INT_MAX - 1 : dmin + ex.tau;
+            int keys[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int i = 2 * (v0 + r) + pcls;
+                keys[r] = dl[r] <= thr ? score_key(ex.scores[i]) : INT_MIN;
+            }
+            if (ex.sdump != nullptr) {
+                const int k = *ex.sdump_count;
+                if (k < ex.dump_cap) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int i = 2 * (v0 + r) + pcls;
+                        if (dl[r] != INT_MAX) ex.sdump[(int64_t)k * ex.n_max + i] = ex.scores[i];
+                    }
+                    if (lane == 0) ex.sdump_step[k] = w.steps;
+                }
+                __syncwarp();
+                if (lane == 0) *ex.sdump_count = k + 1;
+                __syncwarp();
+            }
+            for (;;) {
+                int lk = INT_MIN, li = INT_MAX, ld = INT_MAX;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (!((excl >> r) & 1u) && keys[r] > lk && dl[r] != INT_MAX) {
+                        lk = keys[r];
+                        li = 2 * (v0 + r) + pcls;
+                        ld = dl[r];
+                    }
+                const int km = __reduce_max_sync(kFull, lk);
+                if (km == INT_MIN) break;
+                const int bi = __reduce_min_sync(kFull, lk == km ? li : INT_MAX);
+                const int bd = __reduce_min_sync(kFull, li == bi ? ld : INT_MAX);
+                const uint64_t f = w.fp ^ env.zk[bi];
+                const Probe pr = probe_full(env, f, w.gen, cap);
+                if (!pr.visited) {
+                    best_i = bi;
+                    best_d = bd;
+                    slot = pr.slot;
+                    fnew = f;
+                    break;
+                }
+                exclude<R>(excl, bi, lane);
+            }
+        }
+        for (; best_i < 0;) {
             int d0, i0, d1, i1;
             warp_argmin<R>(dl, excl, v0, pcls, d0, i0);
             if (i0 < 0) break;
@@ -655,6 +764,16 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
                 p.status->trace_isl[trace_slot * p.status->trace_capacity + t] = w.isl;
             }
         }
+        if (ex.rec != nullptr && log_live) {
+            // lowest ISL at the end of the chunk's steps before its first restart step
+            if (w.steps == first_step + 1) log_first = code;
+            if (code == LABS_TRACE_BLOCKED || (code & LABS_TRACE_RESTART)) log_live = false;
+            else log_min = min(log_min, w.isl);
+        }
+    }
+    if (ex.rec != nullptr && lane == 0) {
+        ex.rec->first = log_first;
+        ex.rec->min_isl = log_min;
     }
 }
 
@@ -703,9 +822,9 @@ __device__ __forceinline__ int lanes_R(int n)
 
 template <int R>
 __device__ void run_chunk(const WalkEnv& env, Walker& w, int64_t until, int* base, const WarpSmem& SL,
-                          const View& V, int trace_slot, int64_t trace_start)
+                          const View& V, int trace_slot, int64_t trace_start, const StepExtras& ex)
 {
-    walk_steps<R>(env, w, until, base, SL, V, trace_slot, trace_start);
+    walk_steps<R>(env, w, until, base, SL, V, trace_slot, trace_start, ex);
 }
 
 // One launch advances every walker by up to chunk_steps steps toward the target.  The
@@ -757,10 +876,49 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(K
             if (lane == 0) raise_error(p.status, LABS_ESTATE, (int)wi);
             continue;
         }
+        StepExtras ex;
+        ex.scores = nullptr;
+        ex.sdump = nullptr;
+        ex.rec = nullptr;
+        ex.tau = 0;
+        ex.dump_cap = 0;
+        ex.n_max = p.n_max;
+        env.slot = nullptr;
+        env.slot_valid = nullptr;
+        env.rdump = nullptr;
+        env.rdump_idx = nullptr;
+        env.rdump_count = nullptr;
+        env.dump_cap = 0;
+        DevStatus* S = p.status;
+        if (S->learned) {
+            env.slot = S->l_slot + wi * kBitWords;
+            env.slot_valid = S->l_slot_valid + wi;
+            if (S->l_score_step[wi] == steps_done) {
+                ex.scores = S->l_scores + wi * p.n_max;
+                ex.tau = S->l_tau;
+            }
+            if (trace_slot >= 0 && S->d_scores != nullptr) {
+                ex.sdump = S->d_scores + (int64_t)trace_slot * S->d_cap * p.n_max;
+                ex.sdump_step = S->d_score_step + (int64_t)trace_slot * S->d_cap;
+                ex.sdump_count = S->d_score_count + trace_slot;
+                ex.dump_cap = S->d_cap;
+                env.rdump = S->d_restart + (int64_t)trace_slot * S->d_cap * kBitWords;
+                env.rdump_idx = S->d_restart_idx + (int64_t)trace_slot * S->d_cap;
+                env.rdump_count = S->d_restart_count + trace_slot;
+                env.dump_cap = S->d_cap;
+            }
+        }
+        if (S->log != nullptr && p.chunk_steps > 0) {
+            const int64_t since = steps_done - S->log_start;
+            if (since >= 0 && since % p.chunk_steps == 0) {
+                const int64_t idx = (since / p.chunk_steps) * p.W + wi;
+                if (idx < S->log_capacity) ex.rec = S->log + idx;
+            }
+        }
         if (RMAX == 1 || lanes_R(G.n) == RMAX)
-            run_chunk<RMAX>(env, w, until, base, SL, V, trace_slot, trace_start);
+            run_chunk<RMAX>(env, w, until, base, SL, V, trace_slot, trace_start, ex);
         else
-            run_chunk<(RMAX > 1 ? RMAX - 1 : 1)>(env, w, until, base, SL, V, trace_slot, trace_start);
+            run_chunk<(RMAX > 1 ? RMAX - 1 : 1)>(env, w, until, base, SL, V, trace_slot, trace_start, ex);
         save_walker(st, w, lane);
         __syncwarp();
     }
@@ -792,6 +950,12 @@ __global__ void __launch_bounds__(512) reset_kernel(KParams p)
         env.patience = p.patience > 0 ? p.patience : 2 * G.n;
         env.lane = lane;
         env.g = (uint32_t)wi;
+        env.slot = nullptr;
+        env.slot_valid = nullptr;
+        env.rdump = nullptr;
+        env.rdump_idx = nullptr;
+        env.rdump_count = nullptr;
+        env.dump_cap = 0;
         Walker w;
         w.restart_idx = 0;
         w.gen = 1;
@@ -920,6 +1084,142 @@ __global__ void __launch_bounds__(256) delta_kernel(const int8_t* __restrict__ s
         build_table(V, n, lane);
         delta_row<R>(V, n, lane, dst);
         __syncwarp();
+    }
+}
+
+// --------------------------------------------------- learned proposal support
+
+// Network inputs of states given by their free-variable bits (8 words each, `stride`
+// words apart): x[b][0][i] = s_i, x[b][1][i] = C_{2(i+1)}/sqrt(L) (0 for i = n-1),
+// x[b][2][i] = dISL_i/(8L).  One warp per state.
+template <int R>
+__device__ void features_row(const View& V, int n, int L, int lane, float* xb)
+{
+    int dl[R];
+    {
+        int X[R], P[R];
+        toeplitz<R>(V, n, lane, X);
+        p_direct<R>(V, n, lane, P);
+        assemble<R>(V, n, lane, X, P, dl);
+    }
+    const int p = lane >> 4, v0 = (lane & 15) * R;
+    const float inv8L = (float)(8 * L);
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (dl[r] != INT_MAX) xb[2 * n + 2 * (v0 + r) + p] = (float)dl[r] / inv8L;
+}
+
+__global__ void __launch_bounds__(256) features_kernel(const uint32_t* __restrict__ bits, int64_t stride,
+                                                       int64_t count, int L, float* __restrict__ x)
+{
+    extern __shared__ __align__(16) int smem[];
+    const int n = (L + 1) / 2;
+    const WarpSmem SL = warp_smem(n);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int* base = smem + warp * SL.words;
+    const View V = make_view(base, SL);
+    const float sq = sqrtf((float)L);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; b < count; b += nwarps) {
+        const uint32_t word = lane < kBitWords ? bits[b * stride + lane] : 0u;
+        load_rows(base, SL, V, word, L, n, lane);
+        float* xb = x + b * 3 * n;
+        for (int i = lane; i < n; i += kWarp) {
+            xb[i] = (float)((i & 1) ? V.A1[i >> 1] : V.A0[i >> 1]);
+            xb[n + i] = i < n - 1 ? (float)V.E[i + 1] / sq : 0.f;
+        }
+        switch (lanes_R(n)) {
+            case 1: features_row<1>(V, n, L, lane, xb); break;
+            case 2: features_row<2>(V, n, L, lane, xb); break;
+            case 3: features_row<3>(V, n, L, lane, xb); break;
+            case 4: features_row<4>(V, n, L, lane, xb); break;
+            case 5: features_row<5>(V, n, L, lane, xb); break;
+            case 6: features_row<6>(V, n, L, lane, xb); break;
+            case 7: features_row<7>(V, n, L, lane, xb); break;
+            default: features_row<8>(V, n, L, lane, xb); break;
+        }
+        __syncwarp();
+    }
+}
+
+// Restart candidates of walkers [first, first+count) of one length: candidate 0 is the
+// walker's own next random start (what the plain walk would use); candidates c >= 1
+// perturb the walker's best state by flipping r = 1 + (u mod max(1, n/8)) free
+// variables drawn by Philox (key = seed, counter = (walker, next restart index,
+// c << 16 | t, 1)).  Output bits [count][P][8].
+__global__ void candidates_kernel(KParams p, int64_t first, int64_t count, int n, int P, uint32_t* __restrict__ out)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count * P;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t w = first + t / P;
+        const int c = (int)(t % P);
+        const WalkerState& st = p.states[w];
+        const uint32_t ridx = st.restart_idx + 1;
+        uint32_t bits[kBitWords];
+        if (c == 0) {
+#pragma unroll
+            for (int j = 0; j < kBitWords; ++j) bits[j] = start_word(p.seed, (uint32_t)w, ridx, j, n);
+        } else {
+#pragma unroll
+            for (int j = 0; j < kBitWords; ++j) bits[j] = st.best[j];
+            uint32_t c0 = (uint32_t)w, c1 = ridx, c2 = (uint32_t)c << 16, c3 = 1u;
+            philox(c0, c1, c2, c3, (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
+            const int r = 1 + (int)(c0 % (uint32_t)max(1, n / 8));
+            for (int k = 0; k < r; ++k) {
+                uint32_t d0 = (uint32_t)w, d1 = ridx, d2 = ((uint32_t)c << 16) | (uint32_t)(k + 1), d3 = 1u;
+                philox(d0, d1, d2, d3, (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
+                const int i = (int)(d0 % (uint32_t)n);
+#pragma unroll
+                for (int j = 0; j < kBitWords; ++j)
+                    if (j == (i >> 5)) bits[j] ^= 1u << (i & 31);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kBitWords; ++j) out[t * kBitWords + j] = bits[j];
+    }
+}
+
+// Per walker: the candidate with the highest restart score (ties: lowest c) becomes the
+// walker's proposed restart state.
+__global__ void select_kernel(KParams p, int64_t first, int64_t count, int P, const float* __restrict__ score,
+                              const uint32_t* __restrict__ cand)
+{
+    DevStatus* S = p.status;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+        int best = 0;
+        for (int c = 1; c < P; ++c)
+            if (score[t * P + c] > score[t * P + best]) best = c;
+        const int64_t w = first + t;
+#pragma unroll
+        for (int j = 0; j < kBitWords; ++j) S->l_slot[w * kBitWords + j] = cand[(t * P + best) * kBitWords + j];
+        S->l_slot_valid[w] = 1;
+    }
+}
+
+// Flip scores of walkers [first, first+count) for their current step.
+__global__ void scores_kernel(KParams p, int64_t first, int64_t count, int n, const float* __restrict__ score)
+{
+    DevStatus* S = p.status;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count * n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t w = first + t / n;
+        const int i = (int)(t % n);
+        S->l_scores[w * p.n_max + i] = score[t];
+        if (i == 0) S->l_score_step[w] = p.states[w].steps_done;
+    }
+}
+
+// Training labels of log records: target = the flip of the first step (0 when the step
+// moved nowhere), wf = 1 when the ISL fell below the start ISL later in the chunk,
+// y = L^2 / (2 min_isl) / 8 (the merit factor reached, scaled).
+__global__ void labels_kernel(const labs_log_record* __restrict__ rec, int64_t count, int32_t* __restrict__ target,
+                              float* __restrict__ y, float* __restrict__ wf)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+        const labs_log_record r = rec[t];
+        const bool moved = r.first >= 0;
+        target[t] = moved ? (r.first & 0xFFFF) : 0;
+        wf[t] = (moved && r.min_isl < r.isl) ? 1.f : 0.f;
+        y[t] = (float)r.L * (float)r.L / (2.f * (float)r.min_isl) / 8.f;
     }
 }
 
@@ -1125,6 +1425,41 @@ int launch_trace_arm(const KParams& p, const int64_t* dev_ids, int32_t k, int32_
 {
     trace_clear_kernel<<<256, 256, 0, (cudaStream_t)stream>>>(p);
     trace_set_kernel<<<(k + 255) / 256 + 1, 256, 0, (cudaStream_t)stream>>>(p, dev_ids, k, code, isl, capacity);
+    return status_of(cudaGetLastError());
+}
+
+int launch_features(const uint32_t* bits, int64_t stride, int64_t count, int32_t L, float* x, void* stream)
+{
+    if (count == 0) return LABS_OK;
+    const int warps = 8;
+    const size_t smem = (size_t)warps * warp_smem((L + 1) / 2).words * sizeof(int);
+    cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    features_kernel<<<row_grid(count, warps), warps * kWarp, smem, (cudaStream_t)stream>>>(bits, stride, count, L, x);
+    return status_of(cudaGetLastError());
+}
+
+int launch_candidates(const KParams& p, int64_t first, int64_t count, int n, int P, uint32_t* out, void* stream)
+{
+    candidates_kernel<<<256, 256, 0, (cudaStream_t)stream>>>(p, first, count, n, P, out);
+    return status_of(cudaGetLastError());
+}
+
+int launch_select(const KParams& p, int64_t first, int64_t count, int P, const float* score, const uint32_t* cand,
+                  void* stream)
+{
+    select_kernel<<<256, 256, 0, (cudaStream_t)stream>>>(p, first, count, P, score, cand);
+    return status_of(cudaGetLastError());
+}
+
+int launch_scores(const KParams& p, int64_t first, int64_t count, int n, const float* score, void* stream)
+{
+    scores_kernel<<<256, 256, 0, (cudaStream_t)stream>>>(p, first, count, n, score);
+    return status_of(cudaGetLastError());
+}
+
+int launch_labels(const labs_log_record* rec, int64_t count, int32_t* target, float* y, float* wf, void* stream)
+{
+    labels_kernel<<<256, 256, 0, (cudaStream_t)stream>>>(rec, count, target, y, wf);
     return status_of(cudaGetLastError());
 }
 

@@ -572,6 +572,28 @@ int adamw(float* prm, const float* grad, float* m, float* v, int64_t t, float lr
 }  // namespace net
 }  // namespace labsgpu
 
+namespace labsgpu {
+
+size_t net_workspace_bytes(int64_t B, int n)
+{
+    return net::carve(nullptr, B, n).bytes;
+}
+
+int net_forward_ws(const float* params, const float* x, int64_t B, int n, void* ws, const float** scores,
+                   const float** restart, void* stream)
+{
+    const net::NetWs w = net::carve(ws, B, n);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = net::zero_acts(w, (int)B, n, s);
+    if (!rc) rc = net::load_inputs(x, w, (int)B, n, s);
+    if (!rc) rc = net::forward(params, w, (int)B, n, s);
+    if (scores) *scores = w.score;
+    if (restart) *restart = w.restart;
+    return rc;
+}
+
+}  // namespace labsgpu
+
 using namespace labsgpu;
 
 extern "C" {

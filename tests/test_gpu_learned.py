@@ -1,0 +1,123 @@
+"""The learned proposal in the walk: log records, features and labels against the
+oracle; bit-exact replay of learned-mode trajectories by the oracle from the choices
+the GPU recorded; training on the walk's own log lowers the loss."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import labs_inputs
+import oracle
+import paper_2011_00068_gb300 as labs
+from oracle import learned as ln
+from paper_2011_00068_gb300 import _native
+from paper_2011_00068_gb300 import learned as lrn
+
+pytestmark = pytest.mark.gpu
+
+REC = np.dtype([("bits", "<u4", 8), ("isl", "<i4"), ("first", "<i4"), ("min_isl", "<i4"), ("L", "<i4"),
+                ("walker", "<i8"), ("step", "<i8")])
+
+
+def records_np(buf):
+    return np.frombuffer(buf.cpu().numpy().tobytes(), dtype=REC)
+
+
+def seq_of_bits(bits, L):
+    n = (L + 1) // 2
+    x = np.array([-1 if (bits[i // 32] >> (i % 32)) & 1 else 1 for i in range(n)], np.int8)
+    return oracle.skew_expand(x, L)
+
+
+def test_log_records_follow_the_trajectory():
+    L, W, chunk, chunks, seed = 41, 16, 64, 10, 3
+    s = labs.Search(L, W, seed, chunk_steps=chunk)
+    code, isl = s.trace(list(range(W)), chunk * chunks)
+    buf = s.log(W * chunks)
+    s.walk(chunk * chunks)
+    s.sync()
+    recs = records_np(buf)
+    code, isl = code.cpu().numpy(), isl.cpu().numpy()
+    o = oracle.walk(L, seed, W, chunk * chunks, trace=True)
+    assert np.array_equal(code, o["trace_code"]) and np.array_equal(isl, o["trace_isl"])
+    for k in range(chunks):
+        for w in range(W):
+            r = recs[k * W + w]
+            st = k * chunk
+            assert r["walker"] == w and r["step"] == st and r["L"] == L
+            seq = seq_of_bits(r["bits"], L)
+            start_isl = oracle.isl(seq) if st else oracle.isl(oracle.skew_expand(oracle.random_start(seed, w, 0, L), L))
+            assert r["isl"] == start_isl == (isl[w, st - 1] if st else start_isl)
+            assert r["first"] == code[w, st]
+            m = r["isl"]
+            for t in range(st, st + chunk):
+                if code[w, t] == -1 or code[w, t] & oracle.TRACE_RESTART:
+                    break
+                m = min(m, isl[w, t])
+            assert r["min_isl"] == m
+
+
+def test_features_and_labels_match_oracle():
+    L, B = 101, 24
+    xs = labs_inputs.random_free_vars(B, L, seed=4)
+    seqs = [oracle.skew_expand(x, L) for x in xs]
+    bits = np.zeros((B, 8), np.uint32)
+    for b, x in enumerate(xs):
+        for i in range(len(x)):
+            if x[i] < 0:
+                bits[b, i // 32] |= np.uint32(1 << (i % 32))
+    x = labs.features(L, torch.from_numpy(bits.view(np.int32)).cuda(), 8, B).cpu().numpy()
+    for b, sq in enumerate(seqs):
+        C_even = np.array([oracle.ck(sq, 2 * m) for m in range(1, (L + 1) // 2)])
+        want = ln.features(sq, C_even, oracle.neighbor_delta(sq))[:3]
+        assert np.array_equal(x[b], want)
+    # labels of hand-made records
+    rec = np.zeros(4, REC)
+    rec["L"] = 101
+    rec["isl"] = [3000, 3000, 2000, 2500]
+    rec["min_isl"] = [2800, 3000, 1999, 2500]
+    rec["first"] = [7, 12 | 0x10000, 5, -1]
+    t, y, wf = labs.log_labels(torch.from_numpy(rec.view(np.uint8).reshape(4, 64).copy()).cuda())
+    assert list(t.cpu().numpy()) == [7, 12, 5, 0]
+    assert list(wf.cpu().numpy()) == [1, 0, 1, 0]
+    assert np.allclose(y.cpu().numpy(), 101 ** 2 / (2.0 * rec["min_isl"]) / 8, rtol=1e-6)
+
+
+@pytest.mark.parametrize("L,W,steps,chunk,tau,cands", [(61, 12, 640, 64, 200, 4), (101, 8, 500, 50, 800, 3)])
+def test_learned_walk_replays_bit_exactly(L, W, steps, chunk, tau, cands):
+    seed = 5
+    n = (L + 1) // 2
+    s = labs.Search(L, W, seed, chunk_steps=chunk, flags=_native.LABS_FLAG_LEARNED, patience=40)
+    params = lrn.init_params(9)
+    s.learned(params, tau=tau, candidates=cands)
+    code, isl = s.trace(list(range(W)), steps)
+    cap = steps // chunk + 64
+    d = s.trace_learned(W, cap, n)
+    s.walk(steps)
+    s.sync()
+    code, isl = code.cpu().numpy(), isl.cpu().numpy()
+    res = s.results(seqs=True)
+    dd = {k: v.cpu().numpy() for k, v in d.items()}
+    used_restarts = 0
+    for w in range(W):
+        ns, nr = int(dd["score_count"][w]), int(dd["restart_count"][w])
+        assert ns >= steps // chunk - 1 and ns <= cap
+        used_restarts += nr
+        o = oracle.walk_replay(L, seed, w, steps, tau=tau, score_steps=dd["score_step"][w, :ns],
+                               scores=dd["scores"][w, :ns, :n], restart_idx=dd["restart_idx"][w, :nr],
+                               restart_bits=dd["restart"][w, :nr].view(np.uint32), patience=40)
+        assert np.array_equal(code[w], o["trace_code"]), w
+        assert np.array_equal(isl[w], o["trace_isl"]), w
+        assert np.array_equal(res["best_seq"][w], o["best_seq"])
+    assert used_restarts > 0  # restart proposals were taken
+
+
+def test_training_on_the_walk_log_lowers_the_loss():
+    L = 61
+    recs = lrn.collect(L, walkers=512, chunks=16, seed=7, chunk_steps=64)
+    tr = lrn.Trainer(L, batch=256, seed=3, lr=2e-3)
+    losses = tr.fit(recs, steps=300, seed=1)
+    first, last = np.mean(losses[:20]), np.mean(losses[-20:])
+    assert np.isfinite(losses).all()
+    assert last < 0.8 * first, (first, last)
