@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-delta", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--config", choices=["walk", "learned"], default="walk")
+    ap.add_argument("--learned-L", type=int, default=255)
+    ap.add_argument("--learned-walkers", type=int, default=32768)
+    ap.add_argument("--learned-steps", type=int, default=20000)
+    ap.add_argument("--learned-train-steps", type=int, default=20000)
     ap.add_argument("--delta-rows", type=int, default=1 << 20)
     return ap.parse_args()
 
@@ -338,10 +343,37 @@ def run_ours(args):
     return 0
 
 
+def run_learned(args):
+    """Config 4: the learned proposal vs the plain walk at L=255 on the same GPU
+    (time-to-F thresholds and flips/s of both); one JSON line."""
+    import torch
+
+    from paper_2011_00068_gb300 import compare
+
+    torch.cuda.set_device(0)
+    r = compare.run(L=args.learned_L, walkers=args.learned_walkers, steps=args.learned_steps,
+                    train_steps=args.learned_train_steps, batch=4096)
+    for k in ("plain", "learned"):
+        r[k].pop("curve", None)
+    tt = {k: r[k]["time_to_F"]["8.5"] for k in ("plain", "learned")}
+    line = {"metric": "time-to-F>=8.5 at L=%d, learned vs plain (censored at %d steps)" % (args.learned_L,
+                                                                                          args.learned_steps),
+            "value": tt["learned"]["seconds"] if tt["learned"] else None, "unit": "s", "higher_is_better": False,
+            "n_gpus": 1, "dtype": "int32 walk / bf16 net", "data": "synthetic",
+            "config": {"workload": "L=%d, %d walkers, %d steps, trained %d steps x batch 4096 on the walk log" %
+                                   (args.learned_L, args.learned_walkers, args.learned_steps,
+                                    args.learned_train_steps)},
+            "vs_baseline": None, "comparison": r}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "learned":
+        return run_learned(args)
     return run_ours(args)
 
 

@@ -121,3 +121,17 @@ def test_training_on_the_walk_log_lowers_the_loss():
     first, last = np.mean(losses[:20]), np.mean(losses[-20:])
     assert np.isfinite(losses).all()
     assert last < 0.8 * first, (first, last)
+
+
+def test_learned_vs_plain_comparison():
+    """What the trained network changes, measured on identical walkers: both runs see
+    the same seed, lengths and step budget; the numbers are printed for the record."""
+    from paper_2011_00068_gb300 import compare
+
+    r = compare.run(L=101, walkers=2048, steps=3072, segment=512, train_walkers=1024, train_chunks=16,
+                    train_chunk_steps=128, train_steps=200, batch=512, candidates=4)
+    assert r["plain"]["steps"] == r["learned"]["steps"] == 3072
+    assert r["train"]["loss_last"] < r["train"]["loss_first"]
+    assert r["learned"]["best_isl"] > 0 and r["plain"]["best_isl"] > 0
+    print("plain best F %.4f, learned best F %.4f, flips/s %.3e vs %.3e" % (
+        r["plain"]["best_F"], r["learned"]["best_F"], r["plain"]["flips_per_s"], r["learned"]["flips_per_s"]))
