@@ -72,6 +72,7 @@ typedef struct labs_config {
 #define LABS_FLAG_NO_GRAPH 1     /* launch chunks one by one instead of a CUDA graph */
 #define LABS_FLAG_CHECK_STATE 2  /* re-derive ISL from scratch at each chunk end */
 #define LABS_FLAG_LEARNED 4      /* reserve workspace for the learned mode (labs_learned) */
+#define LABS_FLAG_WARP_PER_WALKER 8 /* one walker per warp even where two per warp fit */
 
 /* Counters of a context, summed over its walkers (labs_stats). */
 typedef struct labs_counters {

@@ -25,6 +25,7 @@ LABS_TRACE_BLOCKED = -1
 LABS_FLAG_NO_GRAPH = 1
 LABS_FLAG_CHECK_STATE = 2
 LABS_FLAG_LEARNED = 4
+LABS_FLAG_WARP_PER_WALKER = 8
 LOG_RECORD_BYTES = 64
 
 ERRORS = {LABS_EINVAL: "EINVAL", LABS_ENOMEM: "ENOMEM", LABS_ECUDA: "ECUDA", LABS_ETIMEOUT: "ETIMEOUT",

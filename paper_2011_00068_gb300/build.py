@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblabs.so")
-SOURCES = ["labs_kernels.cu", "labs_enum.cu", "labs_net.cu", "labs_api.cu"]
+SOURCES = ["labs_walk16.cu", "labs_walk32.cu", "labs_kernels.cu", "labs_enum.cu", "labs_net.cu", "labs_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,7 +29,8 @@ def nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "labs_internal.cuh"), os.path.join(ROOT, "include", "labs.h"), __file__]
+    files += [os.path.join(CSRC, h) for h in ("labs_internal.cuh", "labs_device.cuh")]
+    files += [os.path.join(ROOT, "include", "labs.h"), __file__]
     return files
 
 

@@ -52,7 +52,7 @@ struct labs_ctx {
     Control* ctrl_host = nullptr;
     Control* ctrl_dev = nullptr;
     long long gpu_minus_host_ns = 0;
-    int warps_per_cta = 0, ctas_per_sm = 0, grid = 0, chunk = 0, regs = 0;
+    int warps_per_cta = 0, ctas_per_sm = 0, grid = 0, chunk = 0, regs = 0, tile = 32;
     size_t smem_bytes = 0;
     bool catch_up = false;
     int64_t planned = 0;
@@ -120,7 +120,8 @@ KParams params(labs_ctx* c)
     p.target_num = c->cfg.target_num;
     p.target_den = c->cfg.target_den;
     p.chunk_steps = c->chunk;
-    p.rmax = lanes_for(c->n_max);
+    p.rmax = lanes_for(c->n_max, c->tile);
+    p.tile = c->tile;
     p.seed = c->seed;
     return p;
 }
@@ -229,13 +230,17 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     c->off_tabu = off;
     off = align_up(off + sizeof(uint64_t) * ((size_t)c->W << k.tabu_log2), 256);
     c->total = off;
-    // launch shape of the walk kernel
-    const size_t per_warp = (size_t)warp_smem(c->n_max).words * sizeof(int);
+    // launch shape of the walk kernel: two walkers per warp (16 lanes each) while a
+    // half warp covers n with at most 8 outputs per lane, else one walker per warp
+    c->tile = (k.flags & LABS_FLAG_WARP_PER_WALKER) || lanes_for(c->n_max, 16) > 8 ? 32 : 16;
+    const size_t per_warp = (size_t)warp_smem(c->n_max).words * sizeof(int) * (kWarp / c->tile);
     int warps = k.warps_per_cta ? k.warps_per_cta : 8;
     for (;;) {
         c->smem_bytes = per_warp * (size_t)warps;
         int occ = 0;
-        if (walk_kernel_config(lanes_for(c->n_max), warps, c->smem_bytes, &occ, &c->regs) == LABS_OK && occ > 0) {
+        if (walk_kernel_config(c->tile, lanes_for(c->n_max, c->tile), warps, c->smem_bytes, &occ, &c->regs) ==
+                LABS_OK &&
+            occ > 0) {
             c->ctas_per_sm = occ;
             break;
         }

@@ -1,0 +1,981 @@
+// labs_device.cuh -- device code of the walk shared by the kernel translation units
+// (included by labs_kernels.cu and the walk-instantiation units labs_walk16.cu and
+// labs_walk32.cu).  Not part of the public ABI.
+//
+// A tile of lanes owns one walker (or one input row): the whole warp, or half of it when
+// two walkers share a warp.  A walker's sequence is kept in shared
+// memory split by parity, because for even lags every term of the neighbourhood
+// evaluation pairs positions of equal parity:
+//   A0[u] = s_{2u}   (u = 0..n-1),   A1[u] = s_{2u+1}   (u = 0..n-2),
+// and its even-lag autocorrelations (odd lags vanish by Eq. 4) as the symmetric table
+//   E[d] = C_{2|d|}  (0 < |d| < n),  E[0] = 0.
+//
+// dISL of free variable i = 2v+p (class p, index v), q = L-1-i its mirror, c = n-1:
+//   flipping {i, q} changes C_k, k even, by dC_k = -4 s_i u_k with
+//   u_k = s_{i+k}[i+k != q] + s_{i-k} (out-of-range s = 0; the pair (i,q) is excluded
+//   because both of its ends flip), so with Eq. 2
+//   dISL_i = sum_k dC_k (2 C_k + dC_k)
+//          = -8 s_i (X_i - s_q C_{q-i}) + 16 (N_i - 1) + 32 (P_i - [3i >= L-1] s_q s_{3i-L+1})
+//   X_i = sum_{j != i, j = i mod 2} s_j C_{|j-i|}      (a Toeplitz product: X_v = sum_u A_p[u] E[u-v])
+//   P_i = sum_{k even, 2 <= k <= i} s_{i+k} s_{i-k}
+//   N_i = number of positions of the parity of i, minus one (n-1 for even i, n-2 for odd i).
+//   The centre flips alone: dC_k = -2 s_c (s_{c+k} + s_{c-k}), so
+//   dISL_c = -4 s_c X_c + 16 floor(c/2).
+// X costs n(n-1)/2 multiply-adds per class, i.e. about one per (flip, even lag) pair of
+// the neighbourhood (Algorithm 1's loop over the (L+1)/2 free variables), and is the hot
+// loop.  The first half of a tile holds the even class, the second half the odd class;
+// each lane owns R consecutive outputs v0..v0+R-1 and slides a window of R values of E
+// along u.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "labs_internal.cuh"
+
+namespace labsgpu {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+#ifndef LABS_TOEPLITZ_UNROLL
+#define LABS_TOEPLITZ_UNROLL 2  // u-blocks of the Toeplitz loop unrolled together
+#endif
+constexpr int kToeplitzUnroll = LABS_TOEPLITZ_UNROLL;
+
+#ifndef LABS_WALK_MIN_BLOCKS
+#define LABS_WALK_MIN_BLOCKS 2  // CTAs of 8 warps per SM the walk kernel is compiled for (2 measured fastest)
+#endif
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11):
+// ten rounds of two 32x32->64 multiplies with a Weyl-sequence key schedule.
+__device__ __forceinline__ void philox(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
+                                       uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t hi0 = __umulhi(m0, c0), lo0 = m0 * c0;
+        uint32_t hi1 = __umulhi(m1, c2), lo1 = m1 * c2;
+        uint32_t y0 = hi1 ^ c1 ^ k0, y2 = hi0 ^ c3 ^ k1;
+        c0 = y0;
+        c1 = lo1;
+        c2 = y2;
+        c3 = lo0;
+    }
+}
+
+// Word j (j < 8) of the free-variable bits of start r of walker g: Philox block
+// (g, r, j/4, 0) under key (seed lo, seed hi), word j%4; bits >= n cleared.
+__device__ __forceinline__ uint32_t start_word(uint64_t seed, uint32_t g, uint32_t r, int j, int n)
+{
+    uint32_t c0 = g, c1 = r, c2 = (uint32_t)(j >> 2), c3 = 0u;
+    philox(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+    uint32_t w = (j & 3) == 0 ? c0 : (j & 3) == 1 ? c1 : (j & 3) == 2 ? c2 : c3;
+    int lo = 32 * j;
+    if (n <= lo) return 0u;
+    if (n - lo >= 32) return w;
+    return w & ((1u << (n - lo)) - 1u);
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void raise_error(DevStatus* st, int code, int detail)
+{
+    if (atomicCAS(&st->error, 0, code) == 0) st->error_detail = detail;
+}
+
+// A group of TILE lanes that runs one walker (or one row): the whole warp (TILE = 32)
+// or a half warp (TILE = 16, two walkers per warp).  Every warp-level primitive of the
+// walk goes through it with the tile's own lane mask, so the two halves of a warp may
+// take different paths.
+template <int TILE>
+struct Tile {
+    static constexpr int kHalf = TILE / 2;  // lanes per parity class
+    static constexpr unsigned kLow = TILE == 32 ? 0xFFFFFFFFu : ((1u << TILE) - 1u);
+    int lane;       // 0 .. TILE-1
+    int base;       // warp lane of the tile's lane 0
+    unsigned mask;  // the tile's lanes
+    __device__ explicit Tile(int warp_lane)
+        : lane(warp_lane & (TILE - 1)), base(warp_lane & ~(TILE - 1)), mask(kLow << (warp_lane & ~(TILE - 1)))
+    {
+    }
+    __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+    __device__ __forceinline__ unsigned ballot(bool p) const { return (__ballot_sync(mask, p) >> base) & kLow; }
+    __device__ __forceinline__ int shfl(int v, int src) const { return __shfl_sync(mask, v, base + src); }
+    __device__ __forceinline__ uint32_t shfl(uint32_t v, int src) const { return __shfl_sync(mask, v, base + src); }
+    __device__ __forceinline__ int rmin(int v) const { return __reduce_min_sync(mask, v); }
+    __device__ __forceinline__ int rmax(int v) const { return __reduce_max_sync(mask, v); }
+    __device__ __forceinline__ int radd(int v) const { return __reduce_add_sync(mask, v); }
+    __device__ __forceinline__ uint32_t rxor(uint32_t v) const { return __reduce_xor_sync(mask, v); }
+};
+
+// Per-walker views of the shared-memory layout.
+struct View {
+    int* A0;      // A0[-apad .. n_max+apad)
+    int* A1;
+    int* E;       // E[-kEPad .. n_max+8)
+    uint32_t* B;  // bit-packed classes and reversals, 4 x kBitVec words
+};
+
+__device__ __forceinline__ View make_view(int* base, const WarpSmem& L)
+{
+    View v;
+    v.A0 = base + L.apad;
+    v.A1 = base + L.alen + L.apad;
+    v.E = base + 2 * L.alen + kEPad;
+    v.B = reinterpret_cast<uint32_t*>(base + L.boff);
+    return v;
+}
+
+// Zeroes the rows, the table and the bit vectors (not the fingerprint keys Z, which
+// stay for the chunk).
+template <int TILE>
+__device__ __forceinline__ void clear_rows(int* base, const WarpSmem& L, const Tile<TILE>& t)
+{
+    int4* b4 = reinterpret_cast<int4*>(base);
+    for (int i = t.lane; i < L.zoff / 4; i += TILE) b4[i] = make_int4(0, 0, 0, 0);
+    t.sync();
+}
+
+// Fills A0/A1 from the free-variable bits (word j of the bits lives in tile lane j's
+// `word`), by Eq. 4: s_j = x_j for j <= c, s_{c+t} = (-1)^t x_{c-t}.
+template <int TILE>
+__device__ __forceinline__ void rows_from_bits(const View& V, uint32_t word, int L, int n, const Tile<TILE>& t)
+{
+    const int c = n - 1;
+    for (int j0 = 0; j0 < L; j0 += TILE) {
+        const int j = j0 + t.lane;
+        int f = j <= c ? j : 2 * c - j;
+        if (j >= L) f = 0;
+        const uint32_t w = t.shfl(word, f >> 5);
+        if (j < L) {
+            const int x = ((w >> (f & 31)) & 1u) ? -1 : 1;
+            const int s = (j > c && ((j - c) & 1)) ? -x : x;
+            if (j & 1) V.A1[j >> 1] = s;
+            else V.A0[j >> 1] = s;
+        }
+    }
+    t.sync();
+}
+
+// Bit-packed classes: B[p*kBitVec + k] holds bits 32k..32k+31 of class p (bit u set
+// <=> A_p[u] = -1); B[(2+p)*kBitVec + k] the same for the reversed class (bit u is
+// class entry n_p-1-u).  Zero beyond the class length.
+template <int TILE>
+__device__ __forceinline__ void bits_from_rows(const View& V, int n, const Tile<TILE>& t)
+{
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int* A = p ? V.A1 : V.A0;
+        const int np = p ? n - 1 : n;
+        for (int k = 0; k < kBitVec; ++k) {
+            uint32_t w = 0, r = 0;
+#pragma unroll
+            for (int h = 0; h < 32 / TILE; ++h) {
+                const int u = 32 * k + TILE * h + t.lane;
+                const uint32_t bw = t.ballot(u < np && A[u] < 0);
+                const uint32_t br = t.ballot(u < np && A[np - 1 - u] < 0);
+                w |= (TILE == 32) ? bw : (bw << (TILE * h));
+                r |= (TILE == 32) ? br : (br << (TILE * h));
+            }
+            if (t.lane == 0) {
+                V.B[p * kBitVec + k] = w;
+                V.B[(2 + p) * kBitVec + k] = r;
+            }
+        }
+    }
+    t.sync();
+}
+
+// Number of differing bits between x and y >> sh over bits [0, len).
+__device__ __forceinline__ int shifted_mismatch(const uint32_t* x, const uint32_t* y, int sh, int len)
+{
+    const int q = sh >> 5, r = sh & 31;
+    int cnt = 0;
+    for (int k = 0; 32 * k < len; ++k) {
+        const uint32_t s = __funnelshift_r(y[k + q], y[k + q + 1], r);
+        uint32_t v = x[k] ^ s;
+        const int valid = len - 32 * k;
+        if (valid < 32) v &= (1u << valid) - 1u;
+        cnt += __popc(v);
+    }
+    return cnt;
+}
+
+// Even-lag autocorrelations (Eq. 1) into E and the ISL (Eq. 2) from the bit-packed
+// classes: for each class, sum_u a_u a_{u+m} = (n_p - m) - 2 #{u : a_u != a_{u+m}}.
+template <int TILE>
+__device__ __forceinline__ int build_table(const View& V, int n, const Tile<TILE>& t)
+{
+    bits_from_rows(V, n, t);
+    int part = 0;
+    for (int m = 1 + t.lane; m < n; m += TILE) {
+        int d = 0;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int len = (p ? n - 1 : n) - m;
+            if (len <= 0) continue;
+            const uint32_t* x = V.B + p * kBitVec;
+            d += len - 2 * shifted_mismatch(x, x, m, len);
+        }
+        V.E[m] = d;
+        if (m <= kEPad) V.E[-m] = d;
+        part += d * d;
+    }
+    t.sync();
+    return t.radd(part);
+}
+
+// Lane layout of the neighbourhood: the first half of the tile holds the even class,
+// the second half the odd class; lane l of a half owns outputs v0 .. v0+R-1.
+template <int TILE, int R>
+struct Outs {
+    int p, v0;
+    __device__ explicit Outs(const Tile<TILE>& t) : p(t.lane / Tile<TILE>::kHalf), v0((t.lane % Tile<TILE>::kHalf) * R) {}
+};
+
+// X_v = sum_u A_p[u] E[u-v] for the lane's R outputs v = v0..v0+R-1 (the Toeplitz
+// product).  The window of E slides one position per u.  When R is a multiple of 4
+// the lane's block starts on a 16-byte boundary and E is read four values at a time
+// (the distinct blocks of a half tile are contiguous: no bank conflicts); for other R
+// the scalar reads have an odd or conflict-free stride.
+template <int TILE, int R>
+__device__ __forceinline__ void toeplitz(const View& V, int n, const Outs<TILE, R>& o, int (&acc)[R])
+{
+    const int* A = o.p ? V.A1 : V.A0;
+    const int* E = V.E;
+    const int v0 = o.v0;
+    const int nu = (n + 3) & ~3;
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0;
+    if constexpr (R % 4 == 0) {
+        // win[j] = E[u - v0 - R + j], j = 0 .. R+3
+        int win[R + 4];
+#pragma unroll
+        for (int c = 0; c < R / 4; ++c) {
+            const int4 q = *reinterpret_cast<const int4*>(E - v0 - R + 4 * c);
+            win[4 * c] = q.x;
+            win[4 * c + 1] = q.y;
+            win[4 * c + 2] = q.z;
+            win[4 * c + 3] = q.w;
+        }
+#pragma unroll kToeplitzUnroll
+        for (int u = 0; u < nu; u += 4) {
+            const int4 q = *reinterpret_cast<const int4*>(E + u - v0);
+            win[R] = q.x;
+            win[R + 1] = q.y;
+            win[R + 2] = q.z;
+            win[R + 3] = q.w;
+            const int4 a4 = *reinterpret_cast<const int4*>(A + u);
+            const int a[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] += a[s] * win[R + s - r];
+#pragma unroll
+            for (int j = 0; j < R; ++j) win[j] = win[j + 4];
+        }
+    } else {
+        // win[r] = E[u - v0 - r]
+        int win[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) win[r] = E[-1 - v0 - r];
+        for (int u = 0; u < nu; u += 4) {
+            const int4 a4 = *reinterpret_cast<const int4*>(A + u);
+            const int a[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+#pragma unroll
+                for (int r = R - 1; r > 0; --r) win[r] = win[r - 1];
+                win[0] = E[u + s - v0];
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] += a[s] * win[r];
+            }
+        }
+    }
+}
+
+// P_v = sum_{m=1}^{v} A_p[v+m] A_p[v-m] from scratch for the lane's outputs, from the
+// bit-packed classes (built by build_table): the pairs compare bits v+1.. of the
+// class with bits n_p-v.. of the reversed class, P_v = v - 2 #{mismatches}.
+template <int TILE, int R>
+__device__ __forceinline__ void p_direct(const View& V, int n, const Outs<TILE, R>& o, int (&P)[R])
+{
+    const int np = o.p ? n - 1 : n;
+    const int nv = o.p ? (n >> 1) : ((n + 1) >> 1);
+    const uint32_t* x = V.B + o.p * kBitVec;
+    const uint32_t* xr = V.B + (2 + o.p) * kBitVec;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = o.v0 + r;
+        P[r] = 0;
+        if (v >= nv || v == 0) continue;
+        const int q1 = (v + 1) >> 5, r1 = (v + 1) & 31;
+        const int q2 = (np - v) >> 5, r2 = (np - v) & 31;
+        int cnt = 0;
+        for (int k = 0; 32 * k < v; ++k) {
+            const uint32_t a = __funnelshift_r(x[k + q1], x[k + q1 + 1], r1);
+            const uint32_t b = __funnelshift_r(xr[k + q2], xr[k + q2 + 1], r2);
+            uint32_t d = a ^ b;
+            const int valid = v - 32 * k;
+            if (valid < 32) d &= (1u << valid) - 1u;
+            cnt += __popc(d);
+        }
+        P[r] = v - 2 * cnt;
+    }
+}
+
+// Change of P for a move that negates class-pb entries w1 and w2 (w2 < 0: centre, one
+// entry).  A pair (v+m, v-m) with exactly one negated end changes by -2 x its old
+// product; pairs with both ends negated are unchanged.  Reads A before the flip.
+template <int TILE, int R>
+__device__ __forceinline__ void p_update(const View& V, int n, const Outs<TILE, R>& o, int (&P)[R], int pb, int w1,
+                                         int w2)
+{
+    if (o.p != pb) return;
+    const int* A = pb ? V.A1 : V.A0;
+    const int nv = pb ? (n >> 1) : ((n + 1) >> 1);
+    const int a1 = A[w1];
+    const int a2 = w2 >= 0 ? A[w2] : 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = o.v0 + r;
+        if (v >= nv) continue;
+        int d = 0;
+        const int t1 = 2 * v - w1;
+        if (v != w1 && t1 != w2) d += a1 * A[t1];
+        if (w2 >= 0) {
+            const int t2 = 2 * v - w2;
+            if (v != w2 && t2 != w1) d += a2 * A[t2];
+        }
+        P[r] -= 2 * d;
+    }
+}
+
+// dl[r] = dISL of free variable i = 2(v0+r)+p, or INT_MAX where that output does not
+// exist.  Formula in the header comment.
+template <int TILE, int R>
+__device__ __forceinline__ void assemble(const View& V, int n, const Outs<TILE, R>& o, const int (&X)[R],
+                                         const int (&P)[R], int (&dl)[R])
+{
+    const int p = o.p;
+    const int* A = p ? V.A1 : V.A0;
+    const int nv = p ? (n >> 1) : ((n + 1) >> 1);
+    const int c = n - 1;
+    const int N = p ? n - 2 : n - 1;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = o.v0 + r;
+        if (v >= nv) {
+            dl[r] = INT_MAX;
+            continue;
+        }
+        const int i = 2 * v + p;
+        const int av = A[v];
+        if (i == c) {
+            dl[r] = -4 * av * X[r] + 16 * (c >> 1);
+            continue;
+        }
+        const int sq = A[n - 1 - v - p];
+        const int ck0 = V.E[c - i];
+        const int t = 3 * v + p - n + 1;
+        const int corr = t >= 0 ? sq * A[t] : 0;
+        dl[r] = -8 * av * (X[r] - sq * ck0) + 16 * (N - 1) + 32 * (P[r] - corr);
+    }
+}
+
+// Rebuilds the walker's rows and table from its bits; returns the ISL.
+template <int TILE>
+__device__ __forceinline__ int load_rows(int* base, const WarpSmem& SL, const View& V, uint32_t word, int L, int n,
+                                         const Tile<TILE>& t)
+{
+    clear_rows(base, SL, t);
+    rows_from_bits(V, word, L, n, t);
+    return build_table(V, n, t);
+}
+
+// HT fingerprint (Zobrist): XOR of the keys of the free variables equal to -1.
+template <int TILE>
+__device__ __forceinline__ uint64_t fingerprint_all(uint32_t word, const uint64_t* zk, int n, const Tile<TILE>& t)
+{
+    uint64_t f = 0;
+    const int nr = (n + TILE - 1) & ~(TILE - 1);
+    for (int i0 = 0; i0 < nr; i0 += TILE) {
+        const int i = i0 + t.lane;
+        const uint32_t w = t.shfl(word, i0 >> 5);
+        if (i < n && ((w >> (i & 31)) & 1u)) f ^= zk[i];
+    }
+    const uint32_t lo = t.rxor((uint32_t)f);
+    const uint32_t hi = t.rxor((uint32_t)(f >> 32));
+    return (uint64_t)lo | ((uint64_t)hi << 32);
+}
+
+// Registers of one walker while its tile runs it.
+struct Walker {
+    uint32_t word;   // tile lane j < 8: bits word j
+    uint64_t fp;
+    int isl, best_isl, since, stag;
+    uint32_t restart_idx, gen;
+    int restarts, overflows, blocked;
+    int64_t steps, best_step, target_step;
+};
+
+struct WalkEnv {
+    const KParams* p;
+    uint64_t* T;       // this walker's HT
+    uint64_t tmask;
+    const uint64_t* zk;
+    WalkerState* st;
+    int L, n, patience;
+    uint32_t g;
+    // learned mode (null when off): proposed restart state and its flag
+    uint32_t* slot;
+    int32_t* slot_valid;
+    // replay dumps of a traced walker in learned mode (null when off)
+    uint32_t* rdump;   // [cap][8]
+    int64_t* rdump_idx;
+    int32_t* rdump_count;
+    int dump_cap;
+};
+
+__device__ __forceinline__ bool target_met(const KParams& p, int L, int isl)
+{
+    if (p.target_num <= 0 || p.target_den <= 0) return false;
+    return (int64_t)p.target_den * L * L >= 2 * (int64_t)p.target_num * isl;
+}
+
+template <int TILE>
+__device__ __forceinline__ void note_best(const WalkEnv& env, Walker& w, const Tile<TILE>& t)
+{
+    if (w.isl < w.best_isl) {
+        w.best_isl = w.isl;
+        w.best_step = w.steps;
+        if (t.lane < kBitWords) env.st->best[t.lane] = w.word;
+    }
+    if (w.target_step < 0 && target_met(*env.p, env.L, w.isl)) w.target_step = w.steps;
+}
+
+// Algorithm 1 start: random skew-symmetric S (restart index w.restart_idx), its ISL,
+// insert it into HT (a fresh generation: its home slot is free), best update.
+template <int TILE>
+__device__ void start_walker(const WalkEnv& env, Walker& w, int* base, const WarpSmem& SL, const View& V,
+                             const Tile<TILE>& t, bool proposed = false)
+{
+    const int lane = t.lane;
+    if (proposed) {
+        // learned mode: the restart state chosen by the proposal pass replaces the draw
+        w.word = lane < kBitWords ? env.slot[lane] : 0u;
+        if (env.rdump != nullptr) {
+            const int k = *env.rdump_count;
+            if (k < env.dump_cap) {
+                if (lane < kBitWords) env.rdump[(int64_t)k * kBitWords + lane] = w.word;
+                if (lane == 0) env.rdump_idx[k] = w.restart_idx;
+            }
+            t.sync();
+            if (lane == 0) *env.rdump_count = k + 1;
+        }
+        t.sync();
+        if (lane == 0) *env.slot_valid = 0;
+    } else {
+        w.word = lane < kBitWords ? start_word(env.p->seed, env.g, w.restart_idx, lane, env.n) : 0u;
+    }
+    w.isl = load_rows(base, SL, V, w.word, env.L, env.n, t);
+    w.fp = fingerprint_all(w.word, env.zk, env.n, t);
+    if (lane == 0) env.T[w.fp & env.tmask] = (w.fp & ~kGenMask) | w.gen;
+    t.sync();
+    w.since = w.isl;
+    w.stag = 0;
+    note_best(env, w, t);
+}
+
+template <int TILE>
+__device__ void restart_walker(const WalkEnv& env, Walker& w, int* base, const WarpSmem& SL, const View& V,
+                               const Tile<TILE>& t)
+{
+    w.restart_idx += 1;
+    w.restarts += 1;
+    w.gen += 1;
+    if (w.gen > kGenMask) {
+        const int64_t slots = (int64_t)env.tmask + 1;
+        for (int64_t i = t.lane; i < slots; i += TILE) env.T[i] = 0ull;
+        t.sync();
+        w.gen = 1;
+    }
+    int prop = 0;
+    if (t.lane == 0 && env.slot_valid != nullptr) prop = *env.slot_valid != 0;
+    const bool proposed = t.shfl(prop, 0) != 0;
+    start_walker(env, w, base, SL, V, t, proposed);
+}
+
+// Tile-uniform: lane 0 reads the host-written control block and broadcasts.
+template <int TILE>
+__device__ __forceinline__ int stop_requested(const KParams& p, const Tile<TILE>& t)
+{
+    int why = 0;
+    if (t.lane == 0 && p.ctrl != nullptr) {
+        if (p.ctrl->stop) why = LABS_ECANCELLED;
+        else if (global_ns() >= p.ctrl->deadline_ns) why = LABS_ETIMEOUT;
+    }
+    return t.shfl(why, 0);
+}
+
+// Result of probing HT for one candidate.
+struct Probe {
+    bool visited;
+    int64_t slot;  // insertion slot when not visited, -1 when no free slot within the cap
+};
+
+// Full linear probe of f: up to `cap` slots, TILE at a time.
+template <int TILE>
+__device__ __forceinline__ Probe probe_full(const WalkEnv& env, uint64_t f, uint32_t gen, int cap, const Tile<TILE>& t)
+{
+    const uint64_t tag = (f & ~kGenMask) | gen;
+    Probe pr{false, -1};
+    for (int s0 = 0; s0 < cap; s0 += TILE) {
+        const int s = s0 + t.lane;
+        uint64_t e = 0;
+        if (s < cap) e = env.T[(f + (uint64_t)s) & env.tmask];
+        const bool match = e == tag;
+        const unsigned bal = t.ballot(s < cap && (((e & kGenMask) != gen) || match));
+        if (bal) {
+            const int fl = __ffs(bal) - 1;
+            pr.visited = t.shfl(match ? 1 : 0, fl) != 0;
+            pr.slot = (int64_t)((f + (uint64_t)(s0 + fl)) & env.tmask);
+            break;
+        }
+    }
+    return pr;
+}
+
+// Lowest (dl, i) among the lane outputs not in `excl` (every lane of the tile gets the
+// result; bi = -1 when none is left).
+template <int TILE, int R>
+__device__ __forceinline__ void tile_argmin(const int (&dl)[R], uint32_t excl, const Outs<TILE, R>& o,
+                                            const Tile<TILE>& t, int& bd, int& bi)
+{
+    int lm = INT_MAX, li = INT_MAX;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (!((excl >> r) & 1u) && dl[r] < lm) {
+            lm = dl[r];
+            li = 2 * (o.v0 + r) + o.p;
+        }
+    bd = t.rmin(lm);
+    bi = bd == INT_MAX ? -1 : t.rmin(lm == bd ? li : INT_MAX);
+}
+
+template <int TILE, int R>
+__device__ __forceinline__ void exclude(uint32_t& excl, int bi, const Tile<TILE>& t)
+{
+    const int vb = bi >> 1, pb = bi & 1;
+    if (t.lane == pb * Tile<TILE>::kHalf + vb / R) excl |= 1u << (vb % R);
+}
+
+// Order-preserving map of a float score to int32 (the learned ordering compares these).
+__device__ __forceinline__ int score_key(float f)
+{
+    const int k = __float_as_int(f);
+    return k >= 0 ? k : (k ^ 0x7FFFFFFF);
+}
+
+// What a walk call records besides the trajectory.
+struct StepExtras {
+    const float* scores;  // learned flip scores for the first step of this call, or null
+    int tau;              // learned candidates: dISL <= min dISL + tau
+    float* sdump;         // replay dump of the scores used (traced walker), or null
+    int64_t* sdump_step;
+    int32_t* sdump_count;
+    int dump_cap, n_max;
+    labs_log_record* rec; // log record of this chunk, or null
+};
+
+template <int TILE, int R>
+__device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* base, const WarpSmem& SL,
+                           const View& V, int trace_slot, int64_t trace_start, const StepExtras& ex,
+                           const Tile<TILE>& t)
+{
+    const KParams& p = *env.p;
+    const int lane = t.lane, n = env.n, c = n - 1;
+    const Outs<TILE, R> o(t);
+    const int cap = p.probe_cap;
+    constexpr int S = TILE / 2;  // probe slots per candidate in the two-candidate round
+    int P[R];
+    p_direct(V, n, o, P);
+    const int64_t first_step = w.steps;
+    int log_first = 0, log_min = w.isl;
+    bool log_live = true;
+    if (ex.rec != nullptr) {
+        if (lane < kBitWords) ex.rec->bits[lane] = w.word;
+        if (lane == 0) {
+            ex.rec->isl = w.isl;
+            ex.rec->L = env.L;
+            ex.rec->walker = env.g;
+            ex.rec->step = w.steps;
+        }
+    }
+    while (w.steps < until) {
+        if ((w.steps & (kCheckEvery - 1)) == 0) {
+            const int why = stop_requested(p, t);
+            if (why) {
+                if (lane == 0) raise_error(p.status, why, (int)env.g);
+                break;
+            }
+        }
+        int dl[R];
+        {
+            int X[R];
+            toeplitz(V, n, o, X);
+            assemble(V, n, o, X, P, dl);
+        }
+
+        // Best admissible flip: lowest (dISL, i) whose result is not in HT.  Two
+        // candidates are probed per round, TILE/2 slots each (half the tile per
+        // candidate); a longer chain falls back to a full probe.  The chosen flip is
+        // the best one in about 40% of the steps and one of the best two in about 86%
+        // (L = 201).
+        uint32_t excl = 0;
+        int best_i = -1, best_d = 0;
+        int64_t slot = -1;
+        uint64_t fnew = 0;
+        if (ex.scores != nullptr && w.steps == first_step) {
+            // Learned step: among the flips with dISL <= min dISL + tau, try them by
+            // (score descending, i ascending) first; the plain order follows.
+            int lm = INT_MAX;
+#pragma unroll
+            for (int r = 0; r < R; ++r) lm = min(lm, dl[r]);
+            const int dmin = t.rmin(lm);
+            const int thr = dmin > INT_MAX - ex.tau ? INT_MAX - 1 : dmin + ex.tau;
+            int keys[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int i = 2 * (o.v0 + r) + o.p;
+                keys[r] = dl[r] <= thr ? score_key(ex.scores[i]) : INT_MIN;
+            }
+            if (ex.sdump != nullptr) {
+                const int k = *ex.sdump_count;
+                if (k < ex.dump_cap) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int i = 2 * (o.v0 + r) + o.p;
+                        if (dl[r] != INT_MAX) ex.sdump[(int64_t)k * ex.n_max + i] = ex.scores[i];
+                    }
+                    if (lane == 0) ex.sdump_step[k] = w.steps;
+                }
+                t.sync();
+                if (lane == 0) *ex.sdump_count = k + 1;
+                t.sync();
+            }
+            for (;;) {
+                int lk = INT_MIN, li = INT_MAX, ld = INT_MAX;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (!((excl >> r) & 1u) && keys[r] > lk && dl[r] != INT_MAX) {
+                        lk = keys[r];
+                        li = 2 * (o.v0 + r) + o.p;
+                        ld = dl[r];
+                    }
+                const int km = t.rmax(lk);
+                if (km == INT_MIN) break;
+                const int bi = t.rmin(lk == km ? li : INT_MAX);
+                const int bd = t.rmin(li == bi ? ld : INT_MAX);
+                const uint64_t f = w.fp ^ env.zk[bi];
+                const Probe pr = probe_full(env, f, w.gen, cap, t);
+                if (!pr.visited) {
+                    best_i = bi;
+                    best_d = bd;
+                    slot = pr.slot;
+                    fnew = f;
+                    break;
+                }
+                exclude<TILE, R>(excl, bi, t);
+            }
+        }
+        for (; best_i < 0;) {
+            int d0, i0, d1, i1;
+            tile_argmin(dl, excl, o, t, d0, i0);
+            if (i0 < 0) break;
+            uint32_t ex1 = excl;
+            exclude<TILE, R>(ex1, i0, t);
+            tile_argmin(dl, ex1, o, t, d1, i1);
+            const int hs = lane % S;
+            const int mine = lane < S ? i0 : i1;
+            bool hit = false, match = false;
+            if (mine >= 0 && hs < cap) {
+                const uint64_t f = w.fp ^ env.zk[mine];
+                const uint64_t e = env.T[(f + (uint64_t)hs) & env.tmask];
+                match = e == ((f & ~kGenMask) | w.gen);
+                hit = ((e & kGenMask) != w.gen) || match;
+            }
+            const unsigned bal = t.ballot(hit);
+            const int cand[2] = {i0, i1};
+            const int cdl[2] = {d0, d1};
+            bool chosen = false;
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                if (cand[g] < 0) break;
+                const uint64_t fg = w.fp ^ env.zk[cand[g]];
+                const unsigned b = (bal >> (S * g)) & ((1u << S) - 1u);
+                Probe pr;
+                if (b) {
+                    const int fl = __ffs(b) - 1;
+                    pr.visited = t.shfl(match ? 1 : 0, S * g + fl) != 0;
+                    pr.slot = (int64_t)((fg + (uint64_t)fl) & env.tmask);
+                } else if (cap > S) {
+                    pr = probe_full(env, fg, w.gen, cap, t);
+                } else {
+                    pr.visited = false;
+                    pr.slot = -1;
+                }
+                if (!pr.visited) {
+                    best_i = cand[g];
+                    best_d = cdl[g];
+                    slot = pr.slot;
+                    fnew = fg;
+                    chosen = true;
+                    break;
+                }
+                exclude<TILE, R>(excl, cand[g], t);
+            }
+            if (chosen) break;
+        }
+
+        w.steps += 1;
+        int code;
+        if (best_i < 0) {
+            // Every neighbour is in HT: restart without a move.
+            w.blocked += 1;
+            restart_walker(env, w, base, SL, V, t);
+            p_direct(V, n, o, P);
+            code = LABS_TRACE_BLOCKED;
+        } else {
+            // S <- S_f: table, P and rows (all from the values before the flip).
+            const int pb = best_i & 1, vb = best_i >> 1;
+            int* Ab = pb ? V.A1 : V.A0;
+            const int as = Ab[vb];
+            const bool centre = best_i == c;
+            const int vq = n - 1 - vb - pb;
+            int dd[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) {  // lags 2m, m = lane+1+TILE k < n (n <= TILE R)
+                const int m = lane + 1 + TILE * k;
+                dd[k] = 0;
+                if (m < n) {
+                    int up = Ab[vb + m];
+                    if (!centre && vb + m == vq) up = 0;
+                    const int dn = Ab[vb - m];
+                    dd[k] = (centre ? -2 : -4) * as * (up + dn);
+                }
+            }
+            p_update(V, n, o, P, pb, vb, centre ? -1 : vq);
+            t.sync();
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const int m = lane + 1 + TILE * k;
+                if (m < n) {
+                    V.E[m] += dd[k];
+                    if (m <= kEPad) V.E[-m] += dd[k];
+                }
+            }
+            if (lane == 0) {
+                Ab[vb] = -as;
+                if (!centre) Ab[vq] = -Ab[vq];
+            }
+            const bool stored = slot >= 0;
+            if (lane == 0 && stored) env.T[slot] = (fnew & ~kGenMask) | w.gen;
+            if (lane == (best_i >> 5)) w.word ^= 1u << (best_i & 31);
+            t.sync();
+            w.fp = fnew;
+            w.isl += best_d;
+            if (!stored) w.overflows += 1;
+            note_best(env, w, t);
+            if (w.isl < w.since) {
+                w.since = w.isl;
+                w.stag = 0;
+            } else {
+                w.stag += 1;
+            }
+            code = best_i;
+            if (w.stag >= env.patience || !stored) {
+                restart_walker(env, w, base, SL, V, t);
+                p_direct(V, n, o, P);
+                code |= LABS_TRACE_RESTART;
+            }
+        }
+        if (trace_slot >= 0 && lane == 0) {
+            const int64_t s = w.steps - 1 - trace_start;
+            if (s >= 0 && s < p.status->trace_capacity) {
+                p.status->trace_code[trace_slot * p.status->trace_capacity + s] = code;
+                p.status->trace_isl[trace_slot * p.status->trace_capacity + s] = w.isl;
+            }
+        }
+        if (ex.rec != nullptr && log_live) {
+            // lowest ISL at the end of the chunk's steps before its first restart step
+            if (w.steps == first_step + 1) log_first = code;
+            if (code == LABS_TRACE_BLOCKED || (code & LABS_TRACE_RESTART)) log_live = false;
+            else log_min = min(log_min, w.isl);
+        }
+    }
+    if (ex.rec != nullptr && lane == 0) {
+        ex.rec->first = log_first;
+        ex.rec->min_isl = log_min;
+    }
+}
+
+__device__ void load_walker(const WalkerState* st, Walker& w, int lane)
+{
+    w.word = lane < kBitWords ? st->cur[lane] : 0u;
+    w.fp = st->fp;
+    w.isl = st->isl;
+    w.best_isl = st->best_isl;
+    w.since = st->since_best;
+    w.stag = st->stagnation;
+    w.restart_idx = st->restart_idx;
+    w.gen = st->gen;
+    w.restarts = st->restarts;
+    w.overflows = st->overflows;
+    w.blocked = st->blocked;
+    w.steps = st->steps_done;
+    w.best_step = st->best_step;
+    w.target_step = st->target_step;
+}
+
+__device__ void save_walker(WalkerState* st, const Walker& w, int lane)
+{
+    if (lane < kBitWords) st->cur[lane] = w.word;
+    if (lane == 0) {
+        st->fp = w.fp;
+        st->isl = w.isl;
+        st->best_isl = w.best_isl;
+        st->since_best = w.since;
+        st->stagnation = w.stag;
+        st->restart_idx = w.restart_idx;
+        st->gen = w.gen;
+        st->restarts = w.restarts;
+        st->overflows = w.overflows;
+        st->blocked = w.blocked;
+        st->steps_done = w.steps;
+        st->best_step = w.best_step;
+        st->target_step = w.target_step;
+    }
+}
+
+// Outputs per lane for n free variables: ceil(ceil(n/2) / (TILE/2)).
+template <int TILE>
+__device__ __host__ __forceinline__ int lanes_R(int n)
+{
+    return (((n + 1) >> 1) + TILE / 2 - 1) / (TILE / 2);
+}
+
+// One launch advances every walker by up to chunk_steps steps toward the target.  The
+// kernel is compiled for a tile of TILE lanes per walker and a largest lane block RMAX
+// (register allocation follows it); walkers whose n needs fewer outputs per lane run
+// with RMAX-1, which covers them (any R >= lanes_R(n) computes the same values).
+template <int TILE, int RMAX>
+__global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(KParams p, int chunk_index)
+{
+    extern __shared__ __align__(16) int smem[];
+    const WarpSmem SL = warp_smem(p.n_max);
+    const Tile<TILE> t(threadIdx.x & 31);
+    const int slot_id = threadIdx.x / TILE;  // walker slot of this tile in the CTA
+    int* base = smem + slot_id * SL.words;
+    const View V = make_view(base, SL);
+    const int64_t target = p.status->target_steps;
+    for (;;) {
+        uint32_t q = 0;
+        if (t.lane == 0) q = atomicAdd(&p.queue[chunk_index], 1u);
+        const int64_t wi = (int64_t)t.shfl(q, 0);
+        if (wi >= p.W) break;
+        WalkerState* st = p.states + wi;
+        const int64_t steps_done = st->steps_done;
+        const int64_t until = min(target, steps_done + (int64_t)p.chunk_steps);
+        if (steps_done >= until) continue;
+        const DevGroup G = p.groups[st->group];
+        WalkEnv env;
+        env.p = &p;
+        env.tmask = (1ull << p.tabu_log2) - 1ull;
+        env.T = p.tabu + ((uint64_t)wi << p.tabu_log2);
+        {
+            uint64_t* zs = reinterpret_cast<uint64_t*>(base + SL.zoff);
+            const uint64_t* zg = p.zkeys + G.zkey_off;
+            for (int i = t.lane; i < G.n; i += TILE) zs[i] = zg[i];
+            env.zk = zs;
+            t.sync();
+        }
+        env.st = st;
+        env.L = G.L;
+        env.n = G.n;
+        env.patience = p.patience > 0 ? p.patience : 2 * G.n;
+        env.g = (uint32_t)wi;
+        Walker w;
+        load_walker(st, w, t.lane);
+        const int trace_slot = st->trace_slot;
+        const int64_t trace_start = trace_slot >= 0 ? p.trace_start[trace_slot] : 0;
+        const int isl = load_rows(base, SL, V, w.word, G.L, G.n, t);
+        if (isl != w.isl) {
+            if (t.lane == 0) raise_error(p.status, LABS_ESTATE, (int)wi);
+            continue;
+        }
+        StepExtras ex;
+        ex.scores = nullptr;
+        ex.sdump = nullptr;
+        ex.rec = nullptr;
+        ex.tau = 0;
+        ex.dump_cap = 0;
+        ex.n_max = p.n_max;
+        env.slot = nullptr;
+        env.slot_valid = nullptr;
+        env.rdump = nullptr;
+        env.rdump_idx = nullptr;
+        env.rdump_count = nullptr;
+        env.dump_cap = 0;
+        DevStatus* S = p.status;
+        if (S->learned) {
+            env.slot = S->l_slot + wi * kBitWords;
+            env.slot_valid = S->l_slot_valid + wi;
+            if (S->l_score_step[wi] == steps_done) {
+                ex.scores = S->l_scores + wi * p.n_max;
+                ex.tau = S->l_tau;
+            }
+            if (trace_slot >= 0 && S->d_scores != nullptr) {
+                ex.sdump = S->d_scores + (int64_t)trace_slot * S->d_cap * p.n_max;
+                ex.sdump_step = S->d_score_step + (int64_t)trace_slot * S->d_cap;
+                ex.sdump_count = S->d_score_count + trace_slot;
+                ex.dump_cap = S->d_cap;
+                env.rdump = S->d_restart + (int64_t)trace_slot * S->d_cap * kBitWords;
+                env.rdump_idx = S->d_restart_idx + (int64_t)trace_slot * S->d_cap;
+                env.rdump_count = S->d_restart_count + trace_slot;
+                env.dump_cap = S->d_cap;
+            }
+        }
+        if (S->log != nullptr && p.chunk_steps > 0) {
+            const int64_t since = steps_done - S->log_start;
+            if (since >= 0 && since % p.chunk_steps == 0) {
+                const int64_t idx = (since / p.chunk_steps) * p.W + wi;
+                if (idx < S->log_capacity) ex.rec = S->log + idx;
+            }
+        }
+        if (RMAX == 1 || lanes_R<TILE>(G.n) == RMAX)
+            walk_steps<TILE, RMAX>(env, w, until, base, SL, V, trace_slot, trace_start, ex, t);
+        else
+            walk_steps<TILE, (RMAX > 1 ? RMAX - 1 : 1)>(env, w, until, base, SL, V, trace_slot, trace_start, ex, t);
+        save_walker(st, w, t.lane);
+        t.sync();
+    }
+}
+
+}  // namespace
+}  // namespace labsgpu

@@ -113,7 +113,8 @@ struct KParams {
     int32_t patience;         // 0 = 2n
     int32_t target_num, target_den;
     int32_t chunk_steps;
-    int32_t rmax;             // lane block of the walk kernel instantiation (lanes_for(n_max))
+    int32_t rmax;             // lane block of the walk kernel instantiation (lanes_for(n_max, tile))
+    int32_t tile;             // lanes per walker: 32, or 16 (two walkers per warp)
     uint64_t seed;
 };
 
@@ -146,6 +147,11 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max)
     return w;
 }
 
+// Walk kernel instantiations (labs_walk16.cu, labs_walk32.cu).
+using WalkFn = void (*)(KParams, int);
+WalkFn walk_fn16(int rmax);
+WalkFn walk_fn32(int rmax);
+
 // Launchers (labs_kernels.cu).
 int launch_zobrist(const KParams& p, uint64_t* zkeys, const DevGroup* host_groups, int nG,
                    void* stream);
@@ -153,8 +159,8 @@ int launch_reset(const KParams& p, int grid, int block, void* stream);
 int launch_prep_walk(const KParams& p, int64_t steps, int nchunks, void* stream);
 int launch_walk_chunk(const KParams& p, int chunk_index, int grid, int warps_per_cta,
                       size_t smem_bytes, void* stream);
-int walk_kernel_config(int rmax, int warps_per_cta, size_t smem_bytes, int* ctas_per_sm, int* regs);
-int lanes_for(int n);  // outputs per lane for n free variables: ceil(ceil(n/2) / 16)
+int walk_kernel_config(int tile, int rmax, int warps_per_cta, size_t smem_bytes, int* ctas_per_sm, int* regs);
+int lanes_for(int n, int tile);  // outputs per lane for n free variables: ceil(ceil(n/2) / (tile/2))
 int launch_isl(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status,
                void* stream);
 int launch_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status,
