@@ -231,8 +231,10 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     off = align_up(off + sizeof(uint64_t) * ((size_t)c->W << k.tabu_log2), 256);
     c->total = off;
     // launch shape of the walk kernel: two walkers per warp (16 lanes each) while a
-    // half warp covers n with at most 8 outputs per lane, else one walker per warp
-    c->tile = (k.flags & LABS_FLAG_WARP_PER_WALKER) || lanes_for(c->n_max, 16) > 8 ? 32 : 16;
+    // half warp covers n with at most 10 outputs per lane (n <= 160), else one walker
+    // per warp
+    // (the learned mode runs one walker per warp)
+    c->tile = (k.flags & (LABS_FLAG_WARP_PER_WALKER | LABS_FLAG_LEARNED)) || lanes_for(c->n_max, 16) > 10 ? 32 : 16;
     const size_t per_warp = (size_t)warp_smem(c->n_max).words * sizeof(int) * (kWarp / c->tile);
     int warps = k.warps_per_cta ? k.warps_per_cta : 8;
     for (;;) {

@@ -104,6 +104,7 @@ __device__ __forceinline__ void raise_error(DevStatus* st, int code, int detail)
 // take different paths.
 template <int TILE>
 struct Tile {
+    static constexpr int kSize = TILE;
     static constexpr int kHalf = TILE / 2;  // lanes per parity class
     static constexpr unsigned kLow = TILE == 32 ? 0xFFFFFFFFu : ((1u << TILE) - 1u);
     int lane;       // 0 .. TILE-1
@@ -121,6 +122,49 @@ struct Tile {
     __device__ __forceinline__ int rmax(int v) const { return __reduce_max_sync(mask, v); }
     __device__ __forceinline__ int radd(int v) const { return __reduce_add_sync(mask, v); }
     __device__ __forceinline__ uint32_t rxor(uint32_t v) const { return __reduce_xor_sync(mask, v); }
+    __device__ __forceinline__ unsigned rminu(unsigned v) const { return __reduce_min_sync(mask, v); }
+};
+
+// Two walkers per warp advancing in lockstep (lanes 16h..16h+15 belong to walker h):
+// the same interface as Tile<16>, built from full-warp collectives in which each half
+// contributes the neutral value to the other half's reduction.  Only for converged
+// code: both halves must reach every call.
+struct Pair {
+    static constexpr int kSize = 16;
+    static constexpr int kHalf = 8;
+    int lane;  // 0 .. 15
+    int h;     // which walker of the warp
+    int base;  // 16 h
+    __device__ explicit Pair(int warp_lane) : lane(warp_lane & 15), h(warp_lane >> 4), base(warp_lane & 16) {}
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+    __device__ __forceinline__ unsigned ballot(bool p) const { return (__ballot_sync(kFull, p) >> base) & 0xFFFFu; }
+    __device__ __forceinline__ int shfl(int v, int src) const { return __shfl_sync(kFull, v, base + src); }
+    __device__ __forceinline__ uint32_t shfl(uint32_t v, int src) const { return __shfl_sync(kFull, v, base + src); }
+    __device__ __forceinline__ int rmin(int v) const
+    {
+        const int a = __reduce_min_sync(kFull, h ? INT_MAX : v), b = __reduce_min_sync(kFull, h ? v : INT_MAX);
+        return h ? b : a;
+    }
+    __device__ __forceinline__ unsigned rminu(unsigned v) const
+    {
+        const unsigned a = __reduce_min_sync(kFull, h ? 0xFFFFFFFFu : v), b = __reduce_min_sync(kFull, h ? v : 0xFFFFFFFFu);
+        return h ? b : a;
+    }
+    __device__ __forceinline__ int rmax(int v) const
+    {
+        const int a = __reduce_max_sync(kFull, h ? INT_MIN : v), b = __reduce_max_sync(kFull, h ? v : INT_MIN);
+        return h ? b : a;
+    }
+    __device__ __forceinline__ int radd(int v) const
+    {
+        const int a = __reduce_add_sync(kFull, h ? 0 : v), b = __reduce_add_sync(kFull, h ? v : 0);
+        return h ? b : a;
+    }
+    __device__ __forceinline__ uint32_t rxor(uint32_t v) const
+    {
+        const uint32_t a = __reduce_xor_sync(kFull, h ? 0u : v), b = __reduce_xor_sync(kFull, h ? v : 0u);
+        return h ? b : a;
+    }
 };
 
 // Per-walker views of the shared-memory layout.
@@ -143,21 +187,21 @@ __device__ __forceinline__ View make_view(int* base, const WarpSmem& L)
 
 // Zeroes the rows, the table and the bit vectors (not the fingerprint keys Z, which
 // stay for the chunk).
-template <int TILE>
-__device__ __forceinline__ void clear_rows(int* base, const WarpSmem& L, const Tile<TILE>& t)
+template <class TL>
+__device__ __forceinline__ void clear_rows(int* base, const WarpSmem& L, const TL& t)
 {
     int4* b4 = reinterpret_cast<int4*>(base);
-    for (int i = t.lane; i < L.zoff / 4; i += TILE) b4[i] = make_int4(0, 0, 0, 0);
+    for (int i = t.lane; i < L.zoff / 4; i += TL::kSize) b4[i] = make_int4(0, 0, 0, 0);
     t.sync();
 }
 
 // Fills A0/A1 from the free-variable bits (word j of the bits lives in tile lane j's
 // `word`), by Eq. 4: s_j = x_j for j <= c, s_{c+t} = (-1)^t x_{c-t}.
-template <int TILE>
-__device__ __forceinline__ void rows_from_bits(const View& V, uint32_t word, int L, int n, const Tile<TILE>& t)
+template <class TL>
+__device__ __forceinline__ void rows_from_bits(const View& V, uint32_t word, int L, int n, const TL& t)
 {
     const int c = n - 1;
-    for (int j0 = 0; j0 < L; j0 += TILE) {
+    for (int j0 = 0; j0 < L; j0 += TL::kSize) {
         const int j = j0 + t.lane;
         int f = j <= c ? j : 2 * c - j;
         if (j >= L) f = 0;
@@ -175,8 +219,8 @@ __device__ __forceinline__ void rows_from_bits(const View& V, uint32_t word, int
 // Bit-packed classes: B[p*kBitVec + k] holds bits 32k..32k+31 of class p (bit u set
 // <=> A_p[u] = -1); B[(2+p)*kBitVec + k] the same for the reversed class (bit u is
 // class entry n_p-1-u).  Zero beyond the class length.
-template <int TILE>
-__device__ __forceinline__ void bits_from_rows(const View& V, int n, const Tile<TILE>& t)
+template <class TL>
+__device__ __forceinline__ void bits_from_rows(const View& V, int n, const TL& t)
 {
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
@@ -185,12 +229,12 @@ __device__ __forceinline__ void bits_from_rows(const View& V, int n, const Tile<
         for (int k = 0; k < kBitVec; ++k) {
             uint32_t w = 0, r = 0;
 #pragma unroll
-            for (int h = 0; h < 32 / TILE; ++h) {
-                const int u = 32 * k + TILE * h + t.lane;
+            for (int h = 0; h < 32 / TL::kSize; ++h) {
+                const int u = 32 * k + TL::kSize * h + t.lane;
                 const uint32_t bw = t.ballot(u < np && A[u] < 0);
                 const uint32_t br = t.ballot(u < np && A[np - 1 - u] < 0);
-                w |= (TILE == 32) ? bw : (bw << (TILE * h));
-                r |= (TILE == 32) ? br : (br << (TILE * h));
+                w |= (TL::kSize == 32) ? bw : (bw << (TL::kSize * h));
+                r |= (TL::kSize == 32) ? br : (br << (TL::kSize * h));
             }
             if (t.lane == 0) {
                 V.B[p * kBitVec + k] = w;
@@ -218,12 +262,12 @@ __device__ __forceinline__ int shifted_mismatch(const uint32_t* x, const uint32_
 
 // Even-lag autocorrelations (Eq. 1) into E and the ISL (Eq. 2) from the bit-packed
 // classes: for each class, sum_u a_u a_{u+m} = (n_p - m) - 2 #{u : a_u != a_{u+m}}.
-template <int TILE>
-__device__ __forceinline__ int build_table(const View& V, int n, const Tile<TILE>& t)
+template <class TL>
+__device__ __forceinline__ int build_table(const View& V, int n, const TL& t)
 {
     bits_from_rows(V, n, t);
     int part = 0;
-    for (int m = 1 + t.lane; m < n; m += TILE) {
+    for (int m = 1 + t.lane; m < n; m += TL::kSize) {
         int d = 0;
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
@@ -242,10 +286,10 @@ __device__ __forceinline__ int build_table(const View& V, int n, const Tile<TILE
 
 // Lane layout of the neighbourhood: the first half of the tile holds the even class,
 // the second half the odd class; lane l of a half owns outputs v0 .. v0+R-1.
-template <int TILE, int R>
+template <class TL, int R>
 struct Outs {
     int p, v0;
-    __device__ explicit Outs(const Tile<TILE>& t) : p(t.lane / Tile<TILE>::kHalf), v0((t.lane % Tile<TILE>::kHalf) * R) {}
+    __device__ explicit Outs(const TL& t) : p(t.lane / TL::kHalf), v0((t.lane % TL::kHalf) * R) {}
 };
 
 // X_v = sum_u A_p[u] E[u-v] for the lane's R outputs v = v0..v0+R-1 (the Toeplitz
@@ -253,8 +297,8 @@ struct Outs {
 // the lane's block starts on a 16-byte boundary and E is read four values at a time
 // (the distinct blocks of a half tile are contiguous: no bank conflicts); for other R
 // the scalar reads have an odd or conflict-free stride.
-template <int TILE, int R>
-__device__ __forceinline__ void toeplitz(const View& V, int n, const Outs<TILE, R>& o, int (&acc)[R])
+template <class TL, int R>
+__device__ __forceinline__ void toeplitz(const View& V, int n, const Outs<TL, R>& o, int (&acc)[R])
 {
     const int* A = o.p ? V.A1 : V.A0;
     const int* E = V.E;
@@ -312,8 +356,8 @@ __device__ __forceinline__ void toeplitz(const View& V, int n, const Outs<TILE, 
 // P_v = sum_{m=1}^{v} A_p[v+m] A_p[v-m] from scratch for the lane's outputs, from the
 // bit-packed classes (built by build_table): the pairs compare bits v+1.. of the
 // class with bits n_p-v.. of the reversed class, P_v = v - 2 #{mismatches}.
-template <int TILE, int R>
-__device__ __forceinline__ void p_direct(const View& V, int n, const Outs<TILE, R>& o, int (&P)[R])
+template <class TL, int R>
+__device__ __forceinline__ void p_direct(const View& V, int n, const Outs<TL, R>& o, int (&P)[R])
 {
     const int np = o.p ? n - 1 : n;
     const int nv = o.p ? (n >> 1) : ((n + 1) >> 1);
@@ -342,8 +386,8 @@ __device__ __forceinline__ void p_direct(const View& V, int n, const Outs<TILE, 
 // Change of P for a move that negates class-pb entries w1 and w2 (w2 < 0: centre, one
 // entry).  A pair (v+m, v-m) with exactly one negated end changes by -2 x its old
 // product; pairs with both ends negated are unchanged.  Reads A before the flip.
-template <int TILE, int R>
-__device__ __forceinline__ void p_update(const View& V, int n, const Outs<TILE, R>& o, int (&P)[R], int pb, int w1,
+template <class TL, int R>
+__device__ __forceinline__ void p_update(const View& V, int n, const Outs<TL, R>& o, int (&P)[R], int pb, int w1,
                                          int w2)
 {
     if (o.p != pb) return;
@@ -368,8 +412,8 @@ __device__ __forceinline__ void p_update(const View& V, int n, const Outs<TILE, 
 
 // dl[r] = dISL of free variable i = 2(v0+r)+p, or INT_MAX where that output does not
 // exist.  Formula in the header comment.
-template <int TILE, int R>
-__device__ __forceinline__ void assemble(const View& V, int n, const Outs<TILE, R>& o, const int (&X)[R],
+template <class TL, int R>
+__device__ __forceinline__ void assemble(const View& V, int n, const Outs<TL, R>& o, const int (&X)[R],
                                          const int (&P)[R], int (&dl)[R])
 {
     const int p = o.p;
@@ -399,9 +443,9 @@ __device__ __forceinline__ void assemble(const View& V, int n, const Outs<TILE, 
 }
 
 // Rebuilds the walker's rows and table from its bits; returns the ISL.
-template <int TILE>
+template <class TL>
 __device__ __forceinline__ int load_rows(int* base, const WarpSmem& SL, const View& V, uint32_t word, int L, int n,
-                                         const Tile<TILE>& t)
+                                         const TL& t)
 {
     clear_rows(base, SL, t);
     rows_from_bits(V, word, L, n, t);
@@ -409,12 +453,12 @@ __device__ __forceinline__ int load_rows(int* base, const WarpSmem& SL, const Vi
 }
 
 // HT fingerprint (Zobrist): XOR of the keys of the free variables equal to -1.
-template <int TILE>
-__device__ __forceinline__ uint64_t fingerprint_all(uint32_t word, const uint64_t* zk, int n, const Tile<TILE>& t)
+template <class TL>
+__device__ __forceinline__ uint64_t fingerprint_all(uint32_t word, const uint64_t* zk, int n, const TL& t)
 {
     uint64_t f = 0;
-    const int nr = (n + TILE - 1) & ~(TILE - 1);
-    for (int i0 = 0; i0 < nr; i0 += TILE) {
+    const int nr = (n + TL::kSize - 1) & ~(TL::kSize - 1);
+    for (int i0 = 0; i0 < nr; i0 += TL::kSize) {
         const int i = i0 + t.lane;
         const uint32_t w = t.shfl(word, i0 >> 5);
         if (i < n && ((w >> (i & 31)) & 1u)) f ^= zk[i];
@@ -458,8 +502,8 @@ __device__ __forceinline__ bool target_met(const KParams& p, int L, int isl)
     return (int64_t)p.target_den * L * L >= 2 * (int64_t)p.target_num * isl;
 }
 
-template <int TILE>
-__device__ __forceinline__ void note_best(const WalkEnv& env, Walker& w, const Tile<TILE>& t)
+template <class TL>
+__device__ __forceinline__ void note_best(const WalkEnv& env, Walker& w, const TL& t)
 {
     if (w.isl < w.best_isl) {
         w.best_isl = w.isl;
@@ -471,9 +515,9 @@ __device__ __forceinline__ void note_best(const WalkEnv& env, Walker& w, const T
 
 // Algorithm 1 start: random skew-symmetric S (restart index w.restart_idx), its ISL,
 // insert it into HT (a fresh generation: its home slot is free), best update.
-template <int TILE>
+template <class TL>
 __device__ void start_walker(const WalkEnv& env, Walker& w, int* base, const WarpSmem& SL, const View& V,
-                             const Tile<TILE>& t, bool proposed = false)
+                             const TL& t, bool proposed = false)
 {
     const int lane = t.lane;
     if (proposed) {
@@ -502,16 +546,16 @@ __device__ void start_walker(const WalkEnv& env, Walker& w, int* base, const War
     note_best(env, w, t);
 }
 
-template <int TILE>
+template <class TL>
 __device__ void restart_walker(const WalkEnv& env, Walker& w, int* base, const WarpSmem& SL, const View& V,
-                               const Tile<TILE>& t)
+                               const TL& t)
 {
     w.restart_idx += 1;
     w.restarts += 1;
     w.gen += 1;
     if (w.gen > kGenMask) {
         const int64_t slots = (int64_t)env.tmask + 1;
-        for (int64_t i = t.lane; i < slots; i += TILE) env.T[i] = 0ull;
+        for (int64_t i = t.lane; i < slots; i += TL::kSize) env.T[i] = 0ull;
         t.sync();
         w.gen = 1;
     }
@@ -522,8 +566,8 @@ __device__ void restart_walker(const WalkEnv& env, Walker& w, int* base, const W
 }
 
 // Tile-uniform: lane 0 reads the host-written control block and broadcasts.
-template <int TILE>
-__device__ __forceinline__ int stop_requested(const KParams& p, const Tile<TILE>& t)
+template <class TL>
+__device__ __forceinline__ int stop_requested(const KParams& p, const TL& t)
 {
     int why = 0;
     if (t.lane == 0 && p.ctrl != nullptr) {
@@ -540,12 +584,12 @@ struct Probe {
 };
 
 // Full linear probe of f: up to `cap` slots, TILE at a time.
-template <int TILE>
-__device__ __forceinline__ Probe probe_full(const WalkEnv& env, uint64_t f, uint32_t gen, int cap, const Tile<TILE>& t)
+template <class TL>
+__device__ __forceinline__ Probe probe_full(const WalkEnv& env, uint64_t f, uint32_t gen, int cap, const TL& t)
 {
     const uint64_t tag = (f & ~kGenMask) | gen;
     Probe pr{false, -1};
-    for (int s0 = 0; s0 < cap; s0 += TILE) {
+    for (int s0 = 0; s0 < cap; s0 += TL::kSize) {
         const int s = s0 + t.lane;
         uint64_t e = 0;
         if (s < cap) e = env.T[(f + (uint64_t)s) & env.tmask];
@@ -563,9 +607,9 @@ __device__ __forceinline__ Probe probe_full(const WalkEnv& env, uint64_t f, uint
 
 // Lowest (dl, i) among the lane outputs not in `excl` (every lane of the tile gets the
 // result; bi = -1 when none is left).
-template <int TILE, int R>
-__device__ __forceinline__ void tile_argmin(const int (&dl)[R], uint32_t excl, const Outs<TILE, R>& o,
-                                            const Tile<TILE>& t, int& bd, int& bi)
+template <class TL, int R>
+__device__ __forceinline__ void tile_argmin(const int (&dl)[R], uint32_t excl, const Outs<TL, R>& o,
+                                            const TL& t, int& bd, int& bi)
 {
     int lm = INT_MAX, li = INT_MAX;
 #pragma unroll
@@ -578,11 +622,11 @@ __device__ __forceinline__ void tile_argmin(const int (&dl)[R], uint32_t excl, c
     bi = bd == INT_MAX ? -1 : t.rmin(lm == bd ? li : INT_MAX);
 }
 
-template <int TILE, int R>
-__device__ __forceinline__ void exclude(uint32_t& excl, int bi, const Tile<TILE>& t)
+template <class TL, int R>
+__device__ __forceinline__ void exclude(uint32_t& excl, int bi, const TL& t)
 {
     const int vb = bi >> 1, pb = bi & 1;
-    if (t.lane == pb * Tile<TILE>::kHalf + vb / R) excl |= 1u << (vb % R);
+    if (t.lane == pb * TL::kHalf + vb / R) excl |= 1u << (vb % R);
 }
 
 // Order-preserving map of a float score to int32 (the learned ordering compares these).
@@ -603,16 +647,16 @@ struct StepExtras {
     labs_log_record* rec; // log record of this chunk, or null
 };
 
-template <int TILE, int R>
+template <class TL, int R>
 __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* base, const WarpSmem& SL,
                            const View& V, int trace_slot, int64_t trace_start, const StepExtras& ex,
-                           const Tile<TILE>& t)
+                           const TL& t)
 {
     const KParams& p = *env.p;
     const int lane = t.lane, n = env.n, c = n - 1;
-    const Outs<TILE, R> o(t);
+    const Outs<TL, R> o(t);
     const int cap = p.probe_cap;
-    constexpr int S = TILE / 2;  // probe slots per candidate in the two-candidate round
+    constexpr int S = TL::kSize / 2;  // probe slots per candidate in the two-candidate round
     int P[R];
     p_direct(V, n, o, P);
     const int64_t first_step = w.steps;
@@ -701,7 +745,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
                     fnew = f;
                     break;
                 }
-                exclude<TILE, R>(excl, bi, t);
+                exclude<TL, R>(excl, bi, t);
             }
         }
         for (; best_i < 0;) {
@@ -709,7 +753,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
             tile_argmin(dl, excl, o, t, d0, i0);
             if (i0 < 0) break;
             uint32_t ex1 = excl;
-            exclude<TILE, R>(ex1, i0, t);
+            exclude<TL, R>(ex1, i0, t);
             tile_argmin(dl, ex1, o, t, d1, i1);
             const int hs = lane % S;
             const int mine = lane < S ? i0 : i1;
@@ -748,7 +792,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
                     chosen = true;
                     break;
                 }
-                exclude<TILE, R>(excl, cand[g], t);
+                exclude<TL, R>(excl, cand[g], t);
             }
             if (chosen) break;
         }
@@ -771,7 +815,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
             int dd[R];
 #pragma unroll
             for (int k = 0; k < R; ++k) {  // lags 2m, m = lane+1+TILE k < n (n <= TILE R)
-                const int m = lane + 1 + TILE * k;
+                const int m = lane + 1 + TL::kSize * k;
                 dd[k] = 0;
                 if (m < n) {
                     int up = Ab[vb + m];
@@ -784,7 +828,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
             t.sync();
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-                const int m = lane + 1 + TILE * k;
+                const int m = lane + 1 + TL::kSize * k;
                 if (m < n) {
                     V.E[m] += dd[k];
                     if (m <= kEPad) V.E[-m] += dd[k];
@@ -969,11 +1013,349 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(K
             }
         }
         if (RMAX == 1 || lanes_R<TILE>(G.n) == RMAX)
-            walk_steps<TILE, RMAX>(env, w, until, base, SL, V, trace_slot, trace_start, ex, t);
+            walk_steps<Tile<TILE>, RMAX>(env, w, until, base, SL, V, trace_slot, trace_start, ex, t);
         else
-            walk_steps<TILE, (RMAX > 1 ? RMAX - 1 : 1)>(env, w, until, base, SL, V, trace_slot, trace_start, ex, t);
+            walk_steps<Tile<TILE>, (RMAX > 1 ? RMAX - 1 : 1)>(env, w, until, base, SL, V, trace_slot, trace_start, ex,
+                                                              t);
         save_walker(st, w, t.lane);
         t.sync();
+    }
+}
+
+
+// ------------------------------------------------------------ two walkers per warp
+//
+// The step of walk_steps for two walkers of the same length advancing in lockstep in
+// one warp (lanes 16h..16h+15 run walker h).  Both halves stay converged through the
+// hot part of every step, so each full-warp collective (Pair) serves both walkers;
+// what differs between the walkers is carried by predicates.  Restarts, which are
+// rare, run divergently per half with tile-masked primitives (Tile<16>).  The
+// trajectory of each walker is exactly that of walk_steps.
+
+// Lane-local best candidate as a packed key: (dISL + 2^23) << 8 | i, ascending in
+// (dISL, i); 0xFFFFFFFF when the lane has none.  |dISL| < 2^23 and i < 256 for L <= 511.
+template <int R>
+__device__ __forceinline__ unsigned lane_key(const int (&dl)[R], uint32_t excl, const Outs<Pair, R>& o)
+{
+    unsigned best = 0xFFFFFFFFu;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (!((excl >> r) & 1u) && dl[r] != INT_MAX) {
+            const unsigned k = ((unsigned)(dl[r] + (1 << 23)) << 8) | (unsigned)(2 * (o.v0 + r) + o.p);
+            best = min(best, k);
+        }
+    return best;
+}
+
+// Full probe of f for the halves with need set: every lane runs the same rounds.
+__device__ __forceinline__ Probe pair_probe_full(const WalkEnv& env, uint64_t f, uint32_t gen, int cap, bool need,
+                                                 const Pair& t)
+{
+    const uint64_t tag = (f & ~kGenMask) | gen;
+    Probe pr{false, -1};
+    bool found = false;
+    for (int s0 = 0; s0 < cap; s0 += 16) {
+        const int s = s0 + t.lane;
+        uint64_t e = 0;
+        const bool live = need && !found && s < cap;
+        if (live) e = env.T[(f + (uint64_t)s) & env.tmask];
+        const bool match = e == tag;
+        const unsigned bal = t.ballot(live && (((e & kGenMask) != gen) || match));
+        const int fl = bal ? __ffs(bal) - 1 : 0;
+        const bool vis = t.shfl(match ? 1 : 0, fl) != 0;
+        if (bal && !found) {
+            found = true;
+            pr.visited = vis;
+            pr.slot = (int64_t)((f + (uint64_t)(s0 + fl)) & env.tmask);
+        }
+    }
+    return pr;
+}
+
+template <int R>
+__device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool real, int* base, const WarpSmem& SL,
+                          const View& V, int trace_slot, int64_t trace_start, labs_log_record* rec, const Pair& t,
+                          const Tile<16>& tt)
+{
+    const KParams& p = *env.p;
+    const int lane = t.lane, n = env.n, c = n - 1;
+    const Outs<Pair, R> o(t);
+    const int cap = p.probe_cap;
+    int P[R];
+    p_direct(V, n, o, P);
+    const int64_t first_step = w.steps;
+    int log_first = 0, log_min = w.isl;
+    bool log_live = true;
+    if (real && rec != nullptr) {
+        if (lane < kBitWords) rec->bits[lane] = w.word;
+        if (lane == 0) {
+            rec->isl = w.isl;
+            rec->L = env.L;
+            rec->walker = env.g;
+            rec->step = w.steps;
+        }
+    }
+    for (;;) {
+        const bool act = real && w.steps < until;
+        if (!__any_sync(kFull, act)) break;
+        if (__any_sync(kFull, act && (w.steps & (kCheckEvery - 1)) == 0)) {
+            int why = 0;
+            if ((threadIdx.x & 31) == 0 && p.ctrl != nullptr) {
+                if (p.ctrl->stop) why = LABS_ECANCELLED;
+                else if (global_ns() >= p.ctrl->deadline_ns) why = LABS_ETIMEOUT;
+            }
+            why = __shfl_sync(kFull, why, 0);
+            if (why) {
+                if (act && lane == 0) raise_error(p.status, why, (int)env.g);
+                break;
+            }
+        }
+        int dl[R];
+        {
+            int X[R];
+            toeplitz(V, n, o, X);
+            assemble(V, n, o, X, P, dl);
+        }
+
+        // Best admissible flip, as in walk_steps: two candidates per round, 8 slots each.
+        uint32_t excl = 0;
+        int best_i = -1, best_d = 0;
+        int64_t slot = -1;
+        uint64_t fnew = 0;
+        bool done = !act;
+        while (__any_sync(kFull, !done)) {
+            const unsigned k0 = t.rminu(done ? 0xFFFFFFFFu : lane_key(dl, excl, o));
+            const int i0 = k0 == 0xFFFFFFFFu ? -1 : (int)(k0 & 0xFFu);
+            uint32_t ex1 = excl;
+            if (i0 >= 0) exclude<Pair, R>(ex1, i0, t);
+            const unsigned k1 = t.rminu(done || i0 < 0 ? 0xFFFFFFFFu : lane_key(dl, ex1, o));
+            const int i1 = k1 == 0xFFFFFFFFu ? -1 : (int)(k1 & 0xFFu);
+            const int d0 = (int)(k0 >> 8) - (1 << 23), d1 = (int)(k1 >> 8) - (1 << 23);
+            const int mine = lane < 8 ? i0 : i1;
+            const int hs = lane & 7;
+            const uint64_t f0 = i0 >= 0 ? w.fp ^ env.zk[i0] : 0, f1 = i1 >= 0 ? w.fp ^ env.zk[i1] : 0;
+            bool hit = false, match = false;
+            if (!done && mine >= 0 && hs < cap) {
+                const uint64_t f = lane < 8 ? f0 : f1;
+                const uint64_t e = env.T[(f + (uint64_t)hs) & env.tmask];
+                match = e == ((f & ~kGenMask) | w.gen);
+                hit = ((e & kGenMask) != w.gen) || match;
+            }
+            const unsigned bal = t.ballot(hit);
+            const unsigned b0 = bal & 0xFFu, b1 = (bal >> 8) & 0xFFu;
+            const int fl0 = b0 ? __ffs(b0) - 1 : 0, fl1 = b1 ? __ffs(b1) - 1 : 0;
+            const bool vis0 = t.shfl(match ? 1 : 0, fl0) != 0;
+            const bool vis1 = t.shfl(match ? 1 : 0, 8 + fl1) != 0;
+            // chains longer than 8 slots: full probes (rare)
+            const bool need0 = !done && i0 >= 0 && !b0 && cap > 8;
+            const bool need1 = !done && i1 >= 0 && !b1 && cap > 8;
+            Probe pf0{false, -1}, pf1{false, -1};
+            if (__any_sync(kFull, need0)) pf0 = pair_probe_full(env, f0, w.gen, cap, need0, t);
+            if (__any_sync(kFull, need1)) pf1 = pair_probe_full(env, f1, w.gen, cap, need1, t);
+            if (!done) {
+                if (i0 < 0) {
+                    done = true;  // every neighbour is in HT
+                } else {
+                    Probe pr0 = b0 ? Probe{vis0, (int64_t)((f0 + (uint64_t)fl0) & env.tmask)}
+                                   : (cap > 8 ? pf0 : Probe{false, -1});
+                    if (!pr0.visited) {
+                        best_i = i0, best_d = d0, slot = pr0.slot, fnew = f0, done = true;
+                    } else {
+                        exclude<Pair, R>(excl, i0, t);
+                        if (i1 >= 0) {
+                            Probe pr1 = b1 ? Probe{vis1, (int64_t)((f1 + (uint64_t)fl1) & env.tmask)}
+                                           : (cap > 8 ? pf1 : Probe{false, -1});
+                            if (!pr1.visited) {
+                                best_i = i1, best_d = d1, slot = pr1.slot, fnew = f1, done = true;
+                            } else {
+                                exclude<Pair, R>(excl, i1, t);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+
+        // Apply the move (walkers that have one), from the values before the flip.
+        const bool moves = act && best_i >= 0;
+        const int pb = best_i & 1, vb = best_i >> 1;
+        int* Ab = pb ? V.A1 : V.A0;
+        const bool centre = best_i == c;
+        const int vq = n - 1 - vb - pb;
+        int dd[R];
+        const int as = moves ? Ab[vb] : 0;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int m = lane + 1 + 16 * k;
+            dd[k] = 0;
+            if (moves && m < n) {
+                int up = Ab[vb + m];
+                if (!centre && vb + m == vq) up = 0;
+                const int dn = Ab[vb - m];
+                dd[k] = (centre ? -2 : -4) * as * (up + dn);
+            }
+        }
+        if (moves) p_update(V, n, o, P, pb, vb, centre ? -1 : vq);
+        __syncwarp();
+        if (moves) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const int m = lane + 1 + 16 * k;
+                if (m < n) {
+                    V.E[m] += dd[k];
+                    if (m <= kEPad) V.E[-m] += dd[k];
+                }
+            }
+            if (lane == 0) {
+                Ab[vb] = -as;
+                if (!centre) Ab[vq] = -Ab[vq];
+            }
+        }
+        const bool stored = slot >= 0;
+        if (moves && lane == 0 && stored) env.T[slot] = (fnew & ~kGenMask) | w.gen;
+        if (moves && lane == (best_i >> 5)) w.word ^= 1u << (best_i & 31);
+        __syncwarp();
+        int code = 0;
+        bool again = false;
+        if (act) {
+            w.steps += 1;
+            if (best_i < 0) {
+                w.blocked += 1;
+                again = true;
+                code = LABS_TRACE_BLOCKED;
+            } else {
+                w.fp = fnew;
+                w.isl += best_d;
+                if (!stored) w.overflows += 1;
+                note_best(env, w, t);
+                if (w.isl < w.since) {
+                    w.since = w.isl;
+                    w.stag = 0;
+                } else {
+                    w.stag += 1;
+                }
+                code = best_i;
+                if (w.stag >= env.patience || !stored) {
+                    again = true;
+                    code |= LABS_TRACE_RESTART;
+                }
+            }
+        }
+        if (again) {  // divergent: only this half restarts
+            restart_walker(env, w, base, SL, V, tt);
+            p_direct(V, n, o, P);
+        }
+        __syncwarp();
+        if (act) {
+            if (trace_slot >= 0 && lane == 0) {
+                const int64_t s = w.steps - 1 - trace_start;
+                if (s >= 0 && s < p.status->trace_capacity) {
+                    p.status->trace_code[trace_slot * p.status->trace_capacity + s] = code;
+                    p.status->trace_isl[trace_slot * p.status->trace_capacity + s] = w.isl;
+                }
+            }
+            if (rec != nullptr && log_live) {
+                if (w.steps == first_step + 1) log_first = code;
+                if (code == LABS_TRACE_BLOCKED || (code & LABS_TRACE_RESTART)) log_live = false;
+                else log_min = min(log_min, w.isl);
+            }
+        }
+    }
+    if (real && rec != nullptr && lane == 0) {
+        rec->first = log_first;
+        rec->min_isl = log_min;
+    }
+}
+
+// Walk launch with two walkers per warp (n <= 160): the warp takes two consecutive walkers; when
+// their lengths differ (a group boundary) or only one is left, it runs them one after
+// the other with the other half idle.
+template <int RMAX>
+__global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_pair_kernel(KParams p, int chunk_index)
+{
+    extern __shared__ __align__(16) int smem[];
+    const WarpSmem SL = warp_smem(p.n_max);
+    const Pair t(threadIdx.x & 31);
+    const Tile<16> tt(threadIdx.x & 31);
+    int* base = smem + (threadIdx.x / 16) * SL.words;
+    const View V = make_view(base, SL);
+    const int64_t target = p.status->target_steps;
+    DevStatus* S = p.status;
+    for (;;) {
+        uint32_t q = 0;
+        if ((threadIdx.x & 31) == 0) q = atomicAdd(&p.queue[chunk_index], 2u);
+        q = __shfl_sync(kFull, q, 0);
+        if ((int64_t)q >= p.W) break;
+        const int64_t mine_w = (int64_t)q + t.h;
+        const bool exists = mine_w < p.W;
+        const int my_n = exists ? p.groups[p.states[mine_w].group].n : -1;
+        const int other_n = __shfl_xor_sync(kFull, my_n, 16);
+        const bool together = __all_sync(kFull, exists && my_n == other_n);
+        const int passes = together ? 1 : ((int64_t)q + 1 < p.W ? 2 : 1);
+        for (int pass = 0; pass < passes; ++pass) {
+            // together: both halves run their walker; else pass h runs half h alone
+            const bool real0 = exists && (together || pass == t.h);
+            // the idle half mirrors the running half's length so that loops match
+            const int64_t lead_w = together ? mine_w : (int64_t)q + pass;
+            const DevGroup G = p.groups[p.states[lead_w].group];
+            WalkEnv env;
+            env.p = &p;
+            env.tmask = (1ull << p.tabu_log2) - 1ull;
+            env.T = p.tabu + ((uint64_t)mine_w << p.tabu_log2);
+            env.L = G.L;
+            env.n = G.n;
+            env.patience = p.patience > 0 ? p.patience : 2 * G.n;
+            env.g = (uint32_t)mine_w;
+            env.st = p.states + (exists ? mine_w : lead_w);
+            env.slot = nullptr;
+            env.slot_valid = nullptr;
+            env.rdump = nullptr;
+            env.rdump_idx = nullptr;
+            env.rdump_count = nullptr;
+            env.dump_cap = 0;
+            {
+                uint64_t* zs = reinterpret_cast<uint64_t*>(base + SL.zoff);
+                const uint64_t* zg = p.zkeys + G.zkey_off;
+                for (int i = t.lane; i < G.n; i += 16) zs[i] = zg[i];
+                env.zk = zs;
+            }
+            __syncwarp();
+            Walker w;
+            load_walker(env.st, w, t.lane);
+            int64_t steps_done = w.steps;
+            int64_t until = min(target, steps_done + (int64_t)p.chunk_steps);
+            bool real = real0 && steps_done < until;
+            const int trace_slot = real ? env.st->trace_slot : -1;
+            const int64_t trace_start = trace_slot >= 0 ? p.trace_start[trace_slot] : 0;
+            const int isl = load_rows(base, SL, V, w.word, G.L, G.n, t);
+            if (real && isl != w.isl) {
+                if (t.lane == 0) raise_error(p.status, LABS_ESTATE, (int)mine_w);
+                real = false;
+            }
+            labs_log_record* rec = nullptr;
+            if (real && S->log != nullptr && p.chunk_steps > 0) {
+                const int64_t since = steps_done - S->log_start;
+                if (since >= 0 && since % p.chunk_steps == 0) {
+                    const int64_t idx = (since / p.chunk_steps) * p.W + mine_w;
+                    if (idx < S->log_capacity) rec = S->log + idx;
+                }
+            }
+            // lane block: RMAX down to RMAX-3 exactly, anything smaller runs with RMAX-3
+            const int R = lanes_R<16>(G.n);
+            if (R >= RMAX)
+                walk_pair<RMAX>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec, t, tt);
+            else if (R == RMAX - 1)
+                walk_pair<(RMAX > 1 ? RMAX - 1 : 1)>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec,
+                                                     t, tt);
+            else if (R == RMAX - 2)
+                walk_pair<(RMAX > 2 ? RMAX - 2 : 1)>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec,
+                                                     t, tt);
+            else
+                walk_pair<(RMAX > 3 ? RMAX - 3 : 1)>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec,
+                                                     t, tt);
+            if (real) save_walker(env.st, w, t.lane);
+            __syncwarp();
+        }
     }
 }
 

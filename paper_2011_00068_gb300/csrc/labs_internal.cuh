@@ -147,9 +147,11 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max)
     return w;
 }
 
-// Walk kernel instantiations (labs_walk16.cu, labs_walk32.cu).
+// Walk kernel instantiations (labs_walk16a.cu, labs_walk16b.cu: two walkers per warp,
+// lane blocks 1-5 and 6-10; labs_walk32.cu: one walker per warp).
 using WalkFn = void (*)(KParams, int);
-WalkFn walk_fn16(int rmax);
+WalkFn walk_fn16a(int rmax);
+WalkFn walk_fn16b(int rmax);
 WalkFn walk_fn32(int rmax);
 
 // Launchers (labs_kernels.cu).

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256) isl_kernel(const int8_t* __restrict__ seq
 template <int R>
 __device__ void delta_row(const View& V, int n, const Tile<32>& t, int32_t* dst)
 {
-    const Outs<32, R> o(t);
+    const Outs<Tile<32>, R> o(t);
     int dl[R];
     {
         int X[R], P[R];
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) delta_kernel(const int8_t* __restrict__ s
 template <int R>
 __device__ void features_row(const View& V, int n, int L, const Tile<32>& t, float* xb)
 {
-    const Outs<32, R> o(t);
+    const Outs<Tile<32>, R> o(t);
     int dl[R];
     {
         int X[R], P[R];
@@ -410,7 +410,8 @@ int launch_prep_walk(const KParams& p, int64_t steps, int nchunks, void* stream)
 
 static WalkFn walk_fn(int tile, int rmax)
 {
-    return tile == 16 ? walk_fn16(rmax) : walk_fn32(rmax);
+    if (tile == 16) return rmax <= 5 ? walk_fn16a(rmax) : walk_fn16b(rmax);
+    return walk_fn32(rmax);
 }
 
 int lanes_for(int n, int tile)
