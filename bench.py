@@ -30,6 +30,10 @@ UNIT = "flip evaluations/s"
 # Derived int32 peak: 152 SMs x 128 INT32 lanes x 2070 MHz (maximum SM clock).
 INT32_LANES_PER_SM = 128
 ALGO_OPS_PER_LAG_TERM = 4
+PAIR_MAX_N = 160  # two walkers per warp up to n = 160 free variables
+# DRAM bytes per walker step of walk_pair_kernel at L=201 (ncu: dram__bytes_read.sum +
+# dram__bytes_write.sum of a 4864-walker x 256-step launch, profiles/walk_pair_kernel_L201_16384w.md)
+DRAM_BYTES_PER_WALKER_STEP = 255.6
 
 
 def parse():
@@ -296,8 +300,14 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = INT32_LANES_PER_SM * sms * sm_mhz * 1e6
     achieved = ops_per_launch / avg_launch_s
+    pair = (args.L + 1) // 2 <= PAIR_MAX_N
+    steps_per_launch = args.walkers * args.walk_steps / nchunks
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s (int32)",
-                "frac": achieved / peak, "traffic": None, "kernel": "walk_chunk_kernel",
+                "frac": achieved / peak,
+                "traffic": DRAM_BYTES_PER_WALKER_STEP * steps_per_launch if pair and args.L == 201 else None,
+                "traffic_note": "bytes per launch: %.1f B per walker step from one ncu capture of a 4864-walker "
+                                "launch, scaled by walker steps" % DRAM_BYTES_PER_WALKER_STEP,
+                "kernel": "walk_pair_kernel" if pair else "walk_chunk_kernel",
                 "peak_source": "derived: %d SMs x %d INT32 lanes x %.0f MHz" % (sms, INT32_LANES_PER_SM, sm_mhz)}
 
     e2e = None
