@@ -27,13 +27,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "exact flip evaluations/sec"
 UNIT = "flip evaluations/s"
-# Derived int32 peak: 152 SMs x 128 INT32 lanes x 2070 MHz (maximum SM clock).
-INT32_LANES_PER_SM = 128
-ALGO_OPS_PER_LAG_TERM = 4
+# The neighbourhood's work is one multiply-add per lag term (s_j x C_{2|j-i|}, Toeplitz
+# form), n(n-1) lag terms per walker step, run as exact fp32 FMAs.  Derived peak of the
+# FMA pipe: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (maximum SM clock).
+FP32_LANES_PER_SM = 128
+ALGO_FLOP_PER_LAG_TERM = 2
 PAIR_MAX_N = 160  # two walkers per warp up to n = 160 free variables
 # DRAM bytes per walker step of walk_pair_kernel at L=201 (ncu: dram__bytes_read.sum +
-# dram__bytes_write.sum of a 4864-walker x 256-step launch, profiles/walk_pair_kernel_L201_16384w.md)
-DRAM_BYTES_PER_WALKER_STEP = 255.6
+# dram__bytes_write.sum of a 4864-walker x 256-step launch of the current kernel,
+# profiles/walk_pair_kernel_L201_16384w.md); None when not captured
+DRAM_BYTES_PER_WALKER_STEP = 255.5
 
 
 def parse():
@@ -192,7 +195,7 @@ def run_reference(args):
 def delta_kernel_line(args, dev, stream, labs):
     """labs_neighbor_delta (the stateless neighbourhood evaluation, Algorithm 1's flip
     loop over given sequences) on a batch larger than L2, timed with CUDA events on
-    the library's stream: throughput and its int32 roofline."""
+    the library's stream: throughput and its fp32 FMA roofline."""
     import torch
 
     import labs_inputs
@@ -218,12 +221,12 @@ def delta_kernel_line(args, dev, stream, labs):
     peaks = measured_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = INT32_LANES_PER_SM * sms * sm_mhz * 1e6
-    achieved = ALGO_OPS_PER_LAG_TERM * (n - 1) * flips
+    peak = FP32_LANES_PER_SM * 2 * sms * sm_mhz * 1e6
+    achieved = ALGO_FLOP_PER_LAG_TERM * (n - 1) * flips
     del out
     return {"kernel": "delta_kernel", "rows": B, "L": L, "ms_per_launch": ms, "value": flips, "unit": UNIT,
             "input_bytes": B * L, "output_bytes": B * n * 4,
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s (int32)",
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None}}
 
 
@@ -292,23 +295,26 @@ def run_ours(args):
     st = s.stats()
     assert st["steps"] == args.walkers * args.walk_steps, st
 
-    # roofline of the walk kernel: lag terms n(n-1) per walker step, 4 int32 ops each
+    # roofline of the walk kernel: lag terms n(n-1) per walker step, one FMA (2 FLOP) each
     avg_launch_s = statistics.mean(walk_ms) / 1e3 / nchunks
-    ops_per_launch = ALGO_OPS_PER_LAG_TERM * n * (n - 1) * args.walkers * args.walk_steps / nchunks
+    ops_per_launch = ALGO_FLOP_PER_LAG_TERM * n * (n - 1) * args.walkers * args.walk_steps / nchunks
     peaks = measured_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = INT32_LANES_PER_SM * sms * sm_mhz * 1e6
+    peak = FP32_LANES_PER_SM * 2 * sms * sm_mhz * 1e6
     achieved = ops_per_launch / avg_launch_s
     pair = (args.L + 1) // 2 <= PAIR_MAX_N
     steps_per_launch = args.walkers * args.walk_steps / nchunks
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s (int32)",
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": DRAM_BYTES_PER_WALKER_STEP * steps_per_launch if pair and args.L == 201 else None,
-                "traffic_note": "bytes per launch: %.1f B per walker step from one ncu capture of a 4864-walker "
-                                "launch, scaled by walker steps" % DRAM_BYTES_PER_WALKER_STEP,
+                "traffic": (DRAM_BYTES_PER_WALKER_STEP * steps_per_launch
+                            if pair and args.L == 201 and DRAM_BYTES_PER_WALKER_STEP else None),
+                "traffic_note": ("bytes per launch: %.1f B per walker step from one ncu capture of a 4864-walker "
+                                 "launch, scaled by walker steps" % DRAM_BYTES_PER_WALKER_STEP
+                                 if DRAM_BYTES_PER_WALKER_STEP else "not captured for this kernel version"),
                 "kernel": "walk_pair_kernel" if pair else "walk_chunk_kernel",
-                "peak_source": "derived: %d SMs x %d INT32 lanes x %.0f MHz" % (sms, INT32_LANES_PER_SM, sm_mhz)}
+                "peak_source": "derived: %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz (FMA pipe)" % (
+                    sms, FP32_LANES_PER_SM, sm_mhz)}
 
     e2e = None
     if not args.no_e2e:

@@ -235,7 +235,7 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     // per warp
     // (the learned mode runs one walker per warp)
     c->tile = (k.flags & (LABS_FLAG_WARP_PER_WALKER | LABS_FLAG_LEARNED)) || lanes_for(c->n_max, 16) > 10 ? 32 : 16;
-    const size_t per_warp = (size_t)warp_smem(c->n_max).words * sizeof(int) * (kWarp / c->tile);
+    const size_t per_warp = (size_t)warp_smem(c->n_max, c->tile).words * sizeof(int) * (kWarp / c->tile);
     int warps = k.warps_per_cta ? k.warps_per_cta : 8;
     for (;;) {
         c->smem_bytes = per_warp * (size_t)warps;

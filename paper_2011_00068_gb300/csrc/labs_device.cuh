@@ -169,29 +169,39 @@ struct Pair {
 
 // Per-walker views of the shared-memory layout.
 struct View {
-    int* A0;      // A0[-apad .. n_max+apad)
-    int* A1;
-    int* E;       // E[-kEPad .. n_max+8)
+    float* A0;    // A0[-apad .. alen-apad)
+    float* A1;
+    float2* G;    // G[y] = (E[y], E[y+1]), y in [-gpad, glen-gpad)
     uint32_t* B;  // bit-packed classes and reversals, 4 x kBitVec words
+    int gpad;
 };
 
 __device__ __forceinline__ View make_view(int* base, const WarpSmem& L)
 {
     View v;
-    v.A0 = base + L.apad;
-    v.A1 = base + L.alen + L.apad;
-    v.E = base + 2 * L.alen + kEPad;
+    v.A0 = reinterpret_cast<float*>(base) + L.apad;
+    v.A1 = reinterpret_cast<float*>(base) + L.alen + L.apad;
+    v.G = reinterpret_cast<float2*>(base + L.goff) + L.gpad;
     v.B = reinterpret_cast<uint32_t*>(base + L.boff);
+    v.gpad = L.gpad;
     return v;
 }
 
-// Zeroes the rows, the table and the bit vectors (not the fingerprint keys Z, which
-// stay for the chunk).
+// E[m] = e (m >= 1) in every pair of G that holds it, mirrored to E[-m].
+__device__ __forceinline__ void set_E(const View& V, int m, float e)
+{
+    V.G[m].x = e;
+    V.G[m - 1].y = e;
+    if (m <= V.gpad) V.G[-m].x = e;
+    if (m < V.gpad) V.G[-m - 1].y = e;
+}
+
+// Zeroes the walker's rows, table and bit vectors.
 template <class TL>
 __device__ __forceinline__ void clear_rows(int* base, const WarpSmem& L, const TL& t)
 {
     int4* b4 = reinterpret_cast<int4*>(base);
-    for (int i = t.lane; i < L.zoff / 4; i += TL::kSize) b4[i] = make_int4(0, 0, 0, 0);
+    for (int i = t.lane; i < L.words / 4; i += TL::kSize) b4[i] = make_int4(0, 0, 0, 0);
     t.sync();
 }
 
@@ -209,8 +219,8 @@ __device__ __forceinline__ void rows_from_bits(const View& V, uint32_t word, int
         if (j < L) {
             const int x = ((w >> (f & 31)) & 1u) ? -1 : 1;
             const int s = (j > c && ((j - c) & 1)) ? -x : x;
-            if (j & 1) V.A1[j >> 1] = s;
-            else V.A0[j >> 1] = s;
+            if (j & 1) V.A1[j >> 1] = (float)s;
+            else V.A0[j >> 1] = (float)s;
         }
     }
     t.sync();
@@ -224,15 +234,15 @@ __device__ __forceinline__ void bits_from_rows(const View& V, int n, const TL& t
 {
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
-        const int* A = p ? V.A1 : V.A0;
+        const float* A = p ? V.A1 : V.A0;
         const int np = p ? n - 1 : n;
         for (int k = 0; k < kBitVec; ++k) {
             uint32_t w = 0, r = 0;
 #pragma unroll
             for (int h = 0; h < 32 / TL::kSize; ++h) {
                 const int u = 32 * k + TL::kSize * h + t.lane;
-                const uint32_t bw = t.ballot(u < np && A[u] < 0);
-                const uint32_t br = t.ballot(u < np && A[np - 1 - u] < 0);
+                const uint32_t bw = t.ballot(u < np && A[u] < 0.f);
+                const uint32_t br = t.ballot(u < np && A[np - 1 - u] < 0.f);
                 w |= (TL::kSize == 32) ? bw : (bw << (TL::kSize * h));
                 r |= (TL::kSize == 32) ? br : (br << (TL::kSize * h));
             }
@@ -276,8 +286,7 @@ __device__ __forceinline__ int build_table(const View& V, int n, const TL& t)
             const uint32_t* x = V.B + p * kBitVec;
             d += len - 2 * shifted_mismatch(x, x, m, len);
         }
-        V.E[m] = d;
-        if (m <= kEPad) V.E[-m] = d;
+        set_E(V, m, (float)d);
         part += d * d;
     }
     t.sync();
@@ -293,71 +302,48 @@ struct Outs {
 };
 
 // X_v = sum_u A_p[u] E[u-v] for the lane's R outputs v = v0..v0+R-1 (the Toeplitz
-// product).  The window of E slides one position per u.  When R is a multiple of 4
-// the lane's block starts on a 16-byte boundary and E is read four values at a time
-// (the distinct blocks of a half tile are contiguous: no bank conflicts); for other R
-// the scalar reads have an odd or conflict-free stride.
+// product), on the FP32 pipes with packed pairs: accumulator r holds the partial sums
+// of X_{v0+r} over even u (.x) and odd u (.y), so one __ffma2_rn multiplies the pair
+// (A[u], A[u+1]) by G[u-v] = (E[u-v], E[u+1-v]).  The window win[j] = G[u-v0-j] slides
+// two positions per pair of u: two 8-byte loads per R packed FMAs.  All operands and
+// partial sums are integers below 2^24, so the result is exact.
 template <class TL, int R>
-__device__ __forceinline__ void toeplitz(const View& V, int n, const Outs<TL, R>& o, int (&acc)[R])
+__device__ __forceinline__ void toeplitz(const View& V, int n, const Outs<TL, R>& o, float (&X)[R])
 {
-    const int* A = o.p ? V.A1 : V.A0;
-    const int* E = V.E;
-    const int v0 = o.v0;
-    const int nu = (n + 3) & ~3;
+    const float* A = o.p ? V.A1 : V.A0;
+    const float2* G = V.G - o.v0;
+    const int nu = (n + 7) & ~7;
+    float2 acc[R], win[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = 0;
-    if constexpr (R % 4 == 0) {
-        // win[j] = E[u - v0 - R + j], j = 0 .. R+3
-        int win[R + 4];
-#pragma unroll
-        for (int c = 0; c < R / 4; ++c) {
-            const int4 q = *reinterpret_cast<const int4*>(E - v0 - R + 4 * c);
-            win[4 * c] = q.x;
-            win[4 * c + 1] = q.y;
-            win[4 * c + 2] = q.z;
-            win[4 * c + 3] = q.w;
-        }
+    for (int r = 0; r < R; ++r) {
+        acc[r] = make_float2(0.f, 0.f);
+        win[r] = G[-r];
+    }
 #pragma unroll kToeplitzUnroll
-        for (int u = 0; u < nu; u += 4) {
-            const int4 q = *reinterpret_cast<const int4*>(E + u - v0);
-            win[R] = q.x;
-            win[R + 1] = q.y;
-            win[R + 2] = q.z;
-            win[R + 3] = q.w;
-            const int4 a4 = *reinterpret_cast<const int4*>(A + u);
-            const int a[4] = {a4.x, a4.y, a4.z, a4.w};
+    for (int u = 0; u < nu; u += 8) {
+        const float4 a0 = *reinterpret_cast<const float4*>(A + u);
+        const float4 a1 = *reinterpret_cast<const float4*>(A + u + 4);
+        const float2 ap[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
+                              make_float2(a1.z, a1.w)};
 #pragma unroll
-            for (int s = 0; s < 4; ++s)
+        for (int q = 0; q < 4; ++q) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) acc[r] += a[s] * win[R + s - r];
+            for (int r = 0; r < R; ++r) acc[r] = __ffma2_rn(ap[q], win[r], acc[r]);
 #pragma unroll
-            for (int j = 0; j < R; ++j) win[j] = win[j + 4];
-        }
-    } else {
-        // win[r] = E[u - v0 - r]
-        int win[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) win[r] = E[-1 - v0 - r];
-        for (int u = 0; u < nu; u += 4) {
-            const int4 a4 = *reinterpret_cast<const int4*>(A + u);
-            const int a[4] = {a4.x, a4.y, a4.z, a4.w};
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-#pragma unroll
-                for (int r = R - 1; r > 0; --r) win[r] = win[r - 1];
-                win[0] = E[u + s - v0];
-#pragma unroll
-                for (int r = 0; r < R; ++r) acc[r] += a[s] * win[r];
-            }
+            for (int j = R - 1; j >= 2; --j) win[j] = win[j - 2];
+            if (R >= 2) win[1] = G[u + 2 * q + 1];
+            win[0] = G[u + 2 * q + 2];
         }
     }
+#pragma unroll
+    for (int r = 0; r < R; ++r) X[r] = acc[r].x + acc[r].y;
 }
 
 // P_v = sum_{m=1}^{v} A_p[v+m] A_p[v-m] from scratch for the lane's outputs, from the
 // bit-packed classes (built by build_table): the pairs compare bits v+1.. of the
 // class with bits n_p-v.. of the reversed class, P_v = v - 2 #{mismatches}.
 template <class TL, int R>
-__device__ __forceinline__ void p_direct(const View& V, int n, const Outs<TL, R>& o, int (&P)[R])
+__device__ __forceinline__ void p_direct(const View& V, int n, const Outs<TL, R>& o, float (&P)[R])
 {
     const int np = o.p ? n - 1 : n;
     const int nv = o.p ? (n >> 1) : ((n + 1) >> 1);
@@ -366,7 +352,7 @@ __device__ __forceinline__ void p_direct(const View& V, int n, const Outs<TL, R>
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int v = o.v0 + r;
-        P[r] = 0;
+        P[r] = 0.f;
         if (v >= nv || v == 0) continue;
         const int q1 = (v + 1) >> 5, r1 = (v + 1) & 31;
         const int q2 = (np - v) >> 5, r2 = (np - v) & 31;
@@ -379,7 +365,7 @@ __device__ __forceinline__ void p_direct(const View& V, int n, const Outs<TL, R>
             if (valid < 32) d &= (1u << valid) - 1u;
             cnt += __popc(d);
         }
-        P[r] = v - 2 * cnt;
+        P[r] = (float)(v - 2 * cnt);
     }
 }
 
@@ -387,40 +373,41 @@ __device__ __forceinline__ void p_direct(const View& V, int n, const Outs<TL, R>
 // entry).  A pair (v+m, v-m) with exactly one negated end changes by -2 x its old
 // product; pairs with both ends negated are unchanged.  Reads A before the flip.
 template <class TL, int R>
-__device__ __forceinline__ void p_update(const View& V, int n, const Outs<TL, R>& o, int (&P)[R], int pb, int w1,
+__device__ __forceinline__ void p_update(const View& V, int n, const Outs<TL, R>& o, float (&P)[R], int pb, int w1,
                                          int w2)
 {
     if (o.p != pb) return;
-    const int* A = pb ? V.A1 : V.A0;
+    const float* A = pb ? V.A1 : V.A0;
     const int nv = pb ? (n >> 1) : ((n + 1) >> 1);
-    const int a1 = A[w1];
-    const int a2 = w2 >= 0 ? A[w2] : 0;
+    const float a1 = A[w1];
+    const float a2 = w2 >= 0 ? A[w2] : 0.f;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int v = o.v0 + r;
         if (v >= nv) continue;
-        int d = 0;
+        float d = 0.f;
         const int t1 = 2 * v - w1;
-        if (v != w1 && t1 != w2) d += a1 * A[t1];
+        if (v != w1 && t1 != w2) d = a1 * A[t1];
         if (w2 >= 0) {
             const int t2 = 2 * v - w2;
-            if (v != w2 && t2 != w1) d += a2 * A[t2];
+            if (v != w2 && t2 != w1) d = fmaf(a2, A[t2], d);
         }
-        P[r] -= 2 * d;
+        P[r] = fmaf(-2.f, d, P[r]);
     }
 }
 
 // dl[r] = dISL of free variable i = 2(v0+r)+p, or INT_MAX where that output does not
-// exist.  Formula in the header comment.
+// exist.  Formula in the header comment; evaluated in exact float arithmetic (all
+// terms are integers below 2^24) and converted once.
 template <class TL, int R>
-__device__ __forceinline__ void assemble(const View& V, int n, const Outs<TL, R>& o, const int (&X)[R],
-                                         const int (&P)[R], int (&dl)[R])
+__device__ __forceinline__ void assemble(const View& V, int n, const Outs<TL, R>& o, const float (&X)[R],
+                                         const float (&P)[R], int (&dl)[R])
 {
     const int p = o.p;
-    const int* A = p ? V.A1 : V.A0;
+    const float* A = p ? V.A1 : V.A0;
     const int nv = p ? (n >> 1) : ((n + 1) >> 1);
     const int c = n - 1;
-    const int N = p ? n - 2 : n - 1;
+    const float base = (float)(16 * ((p ? n - 2 : n - 1) - 1));
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int v = o.v0 + r;
@@ -429,16 +416,16 @@ __device__ __forceinline__ void assemble(const View& V, int n, const Outs<TL, R>
             continue;
         }
         const int i = 2 * v + p;
-        const int av = A[v];
+        const float av = A[v];
         if (i == c) {
-            dl[r] = -4 * av * X[r] + 16 * (c >> 1);
+            dl[r] = __float2int_rn(fmaf(-4.f * av, X[r], (float)(16 * (c >> 1))));
             continue;
         }
-        const int sq = A[n - 1 - v - p];
-        const int ck0 = V.E[c - i];
+        const float sq = A[n - 1 - v - p];
+        const float ck0 = V.G[c - i].x;
         const int t = 3 * v + p - n + 1;
-        const int corr = t >= 0 ? sq * A[t] : 0;
-        dl[r] = -8 * av * (X[r] - sq * ck0) + 16 * (N - 1) + 32 * (P[r] - corr);
+        const float corr = t >= 0 ? sq * A[t] : 0.f;
+        dl[r] = __float2int_rn(fmaf(-8.f * av, fmaf(-sq, ck0, X[r]), fmaf(32.f, P[r] - corr, base)));
     }
 }
 
@@ -461,7 +448,7 @@ __device__ __forceinline__ uint64_t fingerprint_all(uint32_t word, const uint64_
     for (int i0 = 0; i0 < nr; i0 += TL::kSize) {
         const int i = i0 + t.lane;
         const uint32_t w = t.shfl(word, i0 >> 5);
-        if (i < n && ((w >> (i & 31)) & 1u)) f ^= zk[i];
+        if (i < n && ((w >> (i & 31)) & 1u)) f ^= __ldg(zk + i);
     }
     const uint32_t lo = t.rxor((uint32_t)f);
     const uint32_t hi = t.rxor((uint32_t)(f >> 32));
@@ -657,7 +644,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
     const Outs<TL, R> o(t);
     const int cap = p.probe_cap;
     constexpr int S = TL::kSize / 2;  // probe slots per candidate in the two-candidate round
-    int P[R];
+    float P[R];
     p_direct(V, n, o, P);
     const int64_t first_step = w.steps;
     int log_first = 0, log_min = w.isl;
@@ -681,7 +668,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
         }
         int dl[R];
         {
-            int X[R];
+            float X[R];
             toeplitz(V, n, o, X);
             assemble(V, n, o, X, P, dl);
         }
@@ -736,7 +723,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
                 if (km == INT_MIN) break;
                 const int bi = t.rmin(lk == km ? li : INT_MAX);
                 const int bd = t.rmin(li == bi ? ld : INT_MAX);
-                const uint64_t f = w.fp ^ env.zk[bi];
+                const uint64_t f = w.fp ^ __ldg(env.zk + bi);
                 const Probe pr = probe_full(env, f, w.gen, cap, t);
                 if (!pr.visited) {
                     best_i = bi;
@@ -759,7 +746,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
             const int mine = lane < S ? i0 : i1;
             bool hit = false, match = false;
             if (mine >= 0 && hs < cap) {
-                const uint64_t f = w.fp ^ env.zk[mine];
+                const uint64_t f = w.fp ^ __ldg(env.zk + mine);
                 const uint64_t e = env.T[(f + (uint64_t)hs) & env.tmask];
                 match = e == ((f & ~kGenMask) | w.gen);
                 hit = ((e & kGenMask) != w.gen) || match;
@@ -771,7 +758,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
                 if (cand[g] < 0) break;
-                const uint64_t fg = w.fp ^ env.zk[cand[g]];
+                const uint64_t fg = w.fp ^ __ldg(env.zk + cand[g]);
                 const unsigned b = (bal >> (S * g)) & ((1u << S) - 1u);
                 Probe pr;
                 if (b) {
@@ -808,20 +795,20 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
         } else {
             // S <- S_f: table, P and rows (all from the values before the flip).
             const int pb = best_i & 1, vb = best_i >> 1;
-            int* Ab = pb ? V.A1 : V.A0;
-            const int as = Ab[vb];
+            float* Ab = pb ? V.A1 : V.A0;
+            const float as = Ab[vb];
             const bool centre = best_i == c;
             const int vq = n - 1 - vb - pb;
-            int dd[R];
+            float dd[R];
 #pragma unroll
             for (int k = 0; k < R; ++k) {  // lags 2m, m = lane+1+TILE k < n (n <= TILE R)
                 const int m = lane + 1 + TL::kSize * k;
-                dd[k] = 0;
+                dd[k] = 0.f;
                 if (m < n) {
-                    int up = Ab[vb + m];
-                    if (!centre && vb + m == vq) up = 0;
-                    const int dn = Ab[vb - m];
-                    dd[k] = (centre ? -2 : -4) * as * (up + dn);
+                    float up = Ab[vb + m];
+                    if (!centre && vb + m == vq) up = 0.f;
+                    const float dn = Ab[vb - m];
+                    dd[k] = ((centre ? -2.f : -4.f) * as) * (up + dn);
                 }
             }
             p_update(V, n, o, P, pb, vb, centre ? -1 : vq);
@@ -829,10 +816,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 const int m = lane + 1 + TL::kSize * k;
-                if (m < n) {
-                    V.E[m] += dd[k];
-                    if (m <= kEPad) V.E[-m] += dd[k];
-                }
+                if (m < n) set_E(V, m, V.G[m].x + dd[k]);
             }
             if (lane == 0) {
                 Ab[vb] = -as;
@@ -917,22 +901,16 @@ __device__ void save_walker(WalkerState* st, const Walker& w, int lane)
     }
 }
 
-// Outputs per lane for n free variables: ceil(ceil(n/2) / (TILE/2)).
-template <int TILE>
-__device__ __host__ __forceinline__ int lanes_R(int n)
-{
-    return (((n + 1) >> 1) + TILE / 2 - 1) / (TILE / 2);
-}
-
 // One launch advances every walker by up to chunk_steps steps toward the target.  The
 // kernel is compiled for a tile of TILE lanes per walker and a largest lane block RMAX
-// (register allocation follows it); walkers whose n needs fewer outputs per lane run
-// with RMAX-1, which covers them (any R >= lanes_R(n) computes the same values).
+// = block_R(n_max, TILE) (register allocation follows it; odd for TILE = 32); walkers
+// whose n needs a smaller block run with RMAX-2, which covers them (any R >=
+// block_R(n) computes the same values).
 template <int TILE, int RMAX>
 __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(KParams p, int chunk_index)
 {
     extern __shared__ __align__(16) int smem[];
-    const WarpSmem SL = warp_smem(p.n_max);
+    const WarpSmem SL = warp_smem(p.n_max, TILE);
     const Tile<TILE> t(threadIdx.x & 31);
     const int slot_id = threadIdx.x / TILE;  // walker slot of this tile in the CTA
     int* base = smem + slot_id * SL.words;
@@ -952,13 +930,7 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(K
         env.p = &p;
         env.tmask = (1ull << p.tabu_log2) - 1ull;
         env.T = p.tabu + ((uint64_t)wi << p.tabu_log2);
-        {
-            uint64_t* zs = reinterpret_cast<uint64_t*>(base + SL.zoff);
-            const uint64_t* zg = p.zkeys + G.zkey_off;
-            for (int i = t.lane; i < G.n; i += TILE) zs[i] = zg[i];
-            env.zk = zs;
-            t.sync();
-        }
+        env.zk = p.zkeys + G.zkey_off;
         env.st = st;
         env.L = G.L;
         env.n = G.n;
@@ -1012,10 +984,10 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(K
                 if (idx < S->log_capacity) ex.rec = S->log + idx;
             }
         }
-        if (RMAX == 1 || lanes_R<TILE>(G.n) == RMAX)
+        if (RMAX <= 2 || block_R(G.n, TILE) >= RMAX)
             walk_steps<Tile<TILE>, RMAX>(env, w, until, base, SL, V, trace_slot, trace_start, ex, t);
         else
-            walk_steps<Tile<TILE>, (RMAX > 1 ? RMAX - 1 : 1)>(env, w, until, base, SL, V, trace_slot, trace_start, ex,
+            walk_steps<Tile<TILE>, (RMAX > 2 ? RMAX - 2 : 1)>(env, w, until, base, SL, V, trace_slot, trace_start, ex,
                                                               t);
         save_walker(st, w, t.lane);
         t.sync();
@@ -1081,7 +1053,7 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
     const int lane = t.lane, n = env.n, c = n - 1;
     const Outs<Pair, R> o(t);
     const int cap = p.probe_cap;
-    int P[R];
+    float P[R];
     p_direct(V, n, o, P);
     const int64_t first_step = w.steps;
     int log_first = 0, log_min = w.isl;
@@ -1112,7 +1084,7 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
         }
         int dl[R];
         {
-            int X[R];
+            float X[R];
             toeplitz(V, n, o, X);
             assemble(V, n, o, X, P, dl);
         }
@@ -1133,7 +1105,7 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
             const int d0 = (int)(k0 >> 8) - (1 << 23), d1 = (int)(k1 >> 8) - (1 << 23);
             const int mine = lane < 8 ? i0 : i1;
             const int hs = lane & 7;
-            const uint64_t f0 = i0 >= 0 ? w.fp ^ env.zk[i0] : 0, f1 = i1 >= 0 ? w.fp ^ env.zk[i1] : 0;
+            const uint64_t f0 = i0 >= 0 ? w.fp ^ __ldg(env.zk + i0) : 0, f1 = i1 >= 0 ? w.fp ^ __ldg(env.zk + i1) : 0;
             bool hit = false, match = false;
             if (!done && mine >= 0 && hs < cap) {
                 const uint64_t f = lane < 8 ? f0 : f1;
@@ -1179,20 +1151,20 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
         // Apply the move (walkers that have one), from the values before the flip.
         const bool moves = act && best_i >= 0;
         const int pb = best_i & 1, vb = best_i >> 1;
-        int* Ab = pb ? V.A1 : V.A0;
+        float* Ab = pb ? V.A1 : V.A0;
         const bool centre = best_i == c;
         const int vq = n - 1 - vb - pb;
-        int dd[R];
-        const int as = moves ? Ab[vb] : 0;
+        float dd[R];
+        const float as = moves ? Ab[vb] : 0.f;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const int m = lane + 1 + 16 * k;
-            dd[k] = 0;
+            dd[k] = 0.f;
             if (moves && m < n) {
-                int up = Ab[vb + m];
-                if (!centre && vb + m == vq) up = 0;
-                const int dn = Ab[vb - m];
-                dd[k] = (centre ? -2 : -4) * as * (up + dn);
+                float up = Ab[vb + m];
+                if (!centre && vb + m == vq) up = 0.f;
+                const float dn = Ab[vb - m];
+                dd[k] = ((centre ? -2.f : -4.f) * as) * (up + dn);
             }
         }
         if (moves) p_update(V, n, o, P, pb, vb, centre ? -1 : vq);
@@ -1201,10 +1173,7 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 const int m = lane + 1 + 16 * k;
-                if (m < n) {
-                    V.E[m] += dd[k];
-                    if (m <= kEPad) V.E[-m] += dd[k];
-                }
+                if (m < n) set_E(V, m, V.G[m].x + dd[k]);
             }
             if (lane == 0) {
                 Ab[vb] = -as;
@@ -1274,7 +1243,7 @@ template <int RMAX>
 __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_pair_kernel(KParams p, int chunk_index)
 {
     extern __shared__ __align__(16) int smem[];
-    const WarpSmem SL = warp_smem(p.n_max);
+    const WarpSmem SL = warp_smem(p.n_max, 16);
     const Pair t(threadIdx.x & 31);
     const Tile<16> tt(threadIdx.x & 31);
     int* base = smem + (threadIdx.x / 16) * SL.words;
@@ -1313,13 +1282,7 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_pair_kernel(KP
             env.rdump_idx = nullptr;
             env.rdump_count = nullptr;
             env.dump_cap = 0;
-            {
-                uint64_t* zs = reinterpret_cast<uint64_t*>(base + SL.zoff);
-                const uint64_t* zg = p.zkeys + G.zkey_off;
-                for (int i = t.lane; i < G.n; i += 16) zs[i] = zg[i];
-                env.zk = zs;
-            }
-            __syncwarp();
+            env.zk = p.zkeys + G.zkey_off;
             Walker w;
             load_walker(env.st, w, t.lane);
             int64_t steps_done = w.steps;
@@ -1340,8 +1303,11 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_pair_kernel(KP
                     if (idx < S->log_capacity) rec = S->log + idx;
                 }
             }
-            // lane block: RMAX down to RMAX-3 exactly, anything smaller runs with RMAX-3
-            const int R = lanes_R<16>(G.n);
+            // lane block: block_R(n) when it is one of RMAX .. RMAX-3, else the smallest
+            // bank-conflict-free one of those (RMAX-3, or RMAX-2 when RMAX-3 is a
+            // multiple of 4)
+            int R = block_R(G.n, 16);
+            if (R < RMAX - 3) R = ((RMAX - 3) & 3) ? RMAX - 3 : RMAX - 2;
             if (R >= RMAX)
                 walk_pair<RMAX>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec, t, tt);
             else if (R == RMAX - 1)

@@ -113,37 +113,60 @@ struct KParams {
     int32_t patience;         // 0 = 2n
     int32_t target_num, target_den;
     int32_t chunk_steps;
-    int32_t rmax;             // lane block of the walk kernel instantiation (lanes_for(n_max, tile))
+    int32_t rmax;             // lane block of the walk kernel instantiation (block_R(n_max, tile))
     int32_t tile;             // lanes per walker: 32, or 16 (two walkers per warp)
     uint64_t seed;
 };
 
-// Shared-memory layout of one walker (one warp), all in int32 words:
-//   A0: even positions s_0, s_2, .. (n values)   padded by apad zeros on both sides
-//   A1: odd positions  s_1, s_3, .. (n-1 values) padded the same way
-//   E : E[d] = C_{2|d|} for 0 < |d| < n, E[0] = 0, zero elsewhere, d in [-kEPad, n+8)
-constexpr int kEPad = 128;
+// Shared-memory layout of one walker, in 32-bit words.  Rows and table hold small
+// integers as floats (exact: every value and every partial sum of the neighbourhood
+// stays below 2^24 in magnitude for L <= 511), so that the Toeplitz product runs on
+// the FP32 pipes.
+//   A0: even positions s_0, s_2, .. (n values) as +-1.0f; zero from -apad up to the
+//       row end (indices [-apad, alen - apad))
+//   A1: odd positions s_1, s_3, .. (n-1 values), laid out the same way
+//   G : pairs G[y] = (E[y], E[y+1]) for y in [-gpad, glen - gpad), where
+//       E[d] = C_{2|d|} for 0 < |d| < n and E[d] = 0 otherwise (E[0] = 0)
 //   B : bit-packed classes (bit u set <=> A_p[u] = -1) and their reversals,
 //       4 vectors x kBitVec words, zero beyond the class length
-//   Z : the walker's n fingerprint keys (uint64)
 constexpr int kBitVec = 9;  // 256 bits per class plus one zero word read by the shifts
 struct WarpSmem {
-    int apad;      // zero padding on each side of A0/A1 (>= n_max, multiple of 4)
-    int alen;      // apad + n_max + apad, rounded to 4
-    int elen;      // kEPad + n_max + 8
-    int boff;      // word offset of B
-    int zoff;      // word offset of Z (16-byte aligned)
-    int words;     // total words per warp
+    int apad;   // zero words below index 0 of each row (>= n_max - 1, multiple of 4)
+    int alen;   // words per row (multiple of 4)
+    int gpad;   // pairs of G below y = 0 (>= the deepest window read, (tile/2) R - 1)
+    int glen;   // pairs of G
+    int goff;   // word offset of G[-gpad] (even)
+    int boff;   // word offset of B
+    int words;  // total words per walker (multiple of 4: walkers stay 16-byte aligned)
 };
-__host__ __device__ inline WarpSmem warp_smem(int n_max)
+// Outputs per lane (the lane block R) for n free variables and `tile` lanes per walker
+// (tile/2 lanes per parity class): at least ceil(ceil(n/2) / (tile/2)), raised until
+// the lanes of a class, whose table windows lie 8R bytes apart, read 16 distinct pairs
+// of banks, i.e. until 16 / gcd(R, 16) >= tile/2.
+__host__ __device__ inline int block_R(int n, int tile)
+{
+    const int h = tile / 2;
+    int R = (((n + 1) >> 1) + h - 1) / h;
+    for (;;) {
+        const int low = R & -R;  // gcd(R, 16) for R < 32
+        if (16 / (low < 16 ? low : 16) >= h) return R;
+        ++R;
+    }
+}
+
+// n_max: largest number of free variables served; tile: lanes per walker (32 or 16).
+__host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
 {
     WarpSmem w;
+    const int R = block_R(n_max, tile);
+    const int hi = (3 * n_max) / 2 + 2 > n_max + 8 ? (3 * n_max) / 2 + 2 : n_max + 8;
     w.apad = (n_max + 3) & ~3;
-    w.alen = (w.apad + ((n_max + 3) & ~3) + w.apad + 4 + 3) & ~3;
-    w.elen = (kEPad + n_max + 8 + 3) & ~3;
-    w.boff = 2 * w.alen + w.elen;
-    w.zoff = w.boff + 4 * kBitVec;
-    w.words = w.zoff + 2 * ((n_max + 1) & ~1);
+    w.alen = w.apad + ((hi + 7) & ~7);
+    w.gpad = (tile / 2) * R;
+    w.glen = w.gpad + ((n_max + 7) & ~7) + 2;
+    w.goff = 2 * w.alen;
+    w.boff = w.goff + 2 * w.glen;
+    w.words = (w.boff + 4 * kBitVec + 3) & ~3;
     return w;
 }
 
@@ -162,7 +185,7 @@ int launch_prep_walk(const KParams& p, int64_t steps, int nchunks, void* stream)
 int launch_walk_chunk(const KParams& p, int chunk_index, int grid, int warps_per_cta,
                       size_t smem_bytes, void* stream);
 int walk_kernel_config(int tile, int rmax, int warps_per_cta, size_t smem_bytes, int* ctas_per_sm, int* regs);
-int lanes_for(int n, int tile);  // outputs per lane for n free variables: ceil(ceil(n/2) / (tile/2))
+int lanes_for(int n, int tile);  // block_R(n, tile)
 int launch_isl(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status,
                void* stream);
 int launch_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status,

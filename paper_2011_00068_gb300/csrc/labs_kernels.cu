@@ -13,7 +13,7 @@ namespace {
 __global__ void __launch_bounds__(512) reset_kernel(KParams p)
 {
     extern __shared__ __align__(16) int smem[];
-    const WarpSmem SL = warp_smem(p.n_max);
+    const WarpSmem SL = warp_smem(p.n_max, 32);
     const Tile<32> t(threadIdx.x & 31);
     const int warp = threadIdx.x >> 5;
     int* base = smem + warp * SL.words;
@@ -119,7 +119,7 @@ __device__ void delta_row(const View& V, int n, const Tile<32>& t, int32_t* dst)
     const Outs<Tile<32>, R> o(t);
     int dl[R];
     {
-        int X[R], P[R];
+        float X[R], P[R];
         toeplitz(V, n, o, X);
         p_direct(V, n, o, P);
         assemble(V, n, o, X, P, dl);
@@ -130,14 +130,14 @@ __device__ void delta_row(const View& V, int n, const Tile<32>& t, int32_t* dst)
 }
 
 // The neighbourhood of Algorithm 1 for skew-symmetric rows, one warp per row, R
-// outputs per lane (R = lanes_R<32>(n), chosen by the host).
+// outputs per lane (R = block_R(n, 32), odd, chosen by the host).
 template <int R>
 __global__ void __launch_bounds__(256) delta_kernel(const int8_t* __restrict__ seqs, int64_t batch, int L,
                                                     int32_t* __restrict__ out, DevStatus* status)
 {
     extern __shared__ __align__(16) int smem[];
     const int n = (L + 1) / 2, c = n - 1;
-    const WarpSmem SL = warp_smem(n);
+    const WarpSmem SL = warp_smem(n, 32);
     const Tile<32> t(threadIdx.x & 31);
     const int lane = t.lane, warp = threadIdx.x >> 5;
     int* base = smem + warp * SL.words;
@@ -150,14 +150,14 @@ __global__ void __launch_bounds__(256) delta_kernel(const int8_t* __restrict__ s
         for (int j = lane; j < L; j += kWarp) {
             const int v = src[j];
             ok = ok && (v == 1 || v == -1);
-            if (j & 1) V.A1[j >> 1] = v;
-            else V.A0[j >> 1] = v;
+            if (j & 1) V.A1[j >> 1] = (float)v;
+            else V.A0[j >> 1] = (float)v;
         }
         t.sync();
         for (int j = 1 + lane; j <= c; j += kWarp) {  // Eq. 4
             const int hi = c + j, lo = c - j;
-            const int shi = (hi & 1) ? V.A1[hi >> 1] : V.A0[hi >> 1];
-            const int slo = (lo & 1) ? V.A1[lo >> 1] : V.A0[lo >> 1];
+            const float shi = (hi & 1) ? V.A1[hi >> 1] : V.A0[hi >> 1];
+            const float slo = (lo & 1) ? V.A1[lo >> 1] : V.A0[lo >> 1];
             ok = ok && (shi == ((j & 1) ? -slo : slo));
         }
         int32_t* dst = out + row * (int64_t)n;
@@ -184,7 +184,7 @@ __device__ void features_row(const View& V, int n, int L, const Tile<32>& t, flo
     const Outs<Tile<32>, R> o(t);
     int dl[R];
     {
-        int X[R], P[R];
+        float X[R], P[R];
         toeplitz(V, n, o, X);
         p_direct(V, n, o, P);
         assemble(V, n, o, X, P, dl);
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256) features_kernel(const uint32_t* __restric
 {
     extern __shared__ __align__(16) int smem[];
     const int n = (L + 1) / 2;
-    const WarpSmem SL = warp_smem(n);
+    const WarpSmem SL = warp_smem(n, 32);
     const Tile<32> t(threadIdx.x & 31);
     const int lane = t.lane, warp = threadIdx.x >> 5;
     int* base = smem + warp * SL.words;
@@ -212,18 +212,15 @@ __global__ void __launch_bounds__(256) features_kernel(const uint32_t* __restric
         load_rows(base, SL, V, word, L, n, t);
         float* xb = x + b * 3 * n;
         for (int i = lane; i < n; i += kWarp) {
-            xb[i] = (float)((i & 1) ? V.A1[i >> 1] : V.A0[i >> 1]);
-            xb[n + i] = i < n - 1 ? (float)V.E[i + 1] / sq : 0.f;
+            xb[i] = (i & 1) ? V.A1[i >> 1] : V.A0[i >> 1];
+            xb[n + i] = i < n - 1 ? V.G[i + 1].x / sq : 0.f;
         }
-        switch (lanes_R<32>(n)) {
+        switch (block_R(n, 32)) {
             case 1: features_row<1>(V, n, L, t, xb); break;
-            case 2: features_row<2>(V, n, L, t, xb); break;
             case 3: features_row<3>(V, n, L, t, xb); break;
-            case 4: features_row<4>(V, n, L, t, xb); break;
             case 5: features_row<5>(V, n, L, t, xb); break;
-            case 6: features_row<6>(V, n, L, t, xb); break;
             case 7: features_row<7>(V, n, L, t, xb); break;
-            default: features_row<8>(V, n, L, t, xb); break;
+            default: features_row<9>(V, n, L, t, xb); break;
         }
         t.sync();
     }
@@ -395,7 +392,7 @@ int launch_zobrist(const KParams&, uint64_t* zkeys, const DevGroup* host_groups,
 
 int launch_reset(const KParams& p, int grid, int block, void* stream)
 {
-    const size_t smem = (size_t)(block / kWarp) * warp_smem(p.n_max).words * sizeof(int);
+    const size_t smem = (size_t)(block / kWarp) * warp_smem(p.n_max, 32).words * sizeof(int);
     cudaFuncSetAttribute(reset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     reset_kernel<<<grid, block, smem, (cudaStream_t)stream>>>(p);
     return status_of(cudaGetLastError());
@@ -416,7 +413,7 @@ static WalkFn walk_fn(int tile, int rmax)
 
 int lanes_for(int n, int tile)
 {
-    return tile == 16 ? lanes_R<16>(n) : lanes_R<32>(n);
+    return block_R(n, tile);
 }
 
 int walk_kernel_config(int tile, int rmax, int warps_per_cta, size_t smem_bytes, int* ctas_per_sm, int* regs)
@@ -468,18 +465,15 @@ int launch_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, Dev
 {
     if (batch == 0) return LABS_OK;
     const int warps = 8;
-    const size_t smem = (size_t)warps * warp_smem((L + 1) / 2).words * sizeof(int);
+    const size_t smem = (size_t)warps * warp_smem((L + 1) / 2, 32).words * sizeof(int);
     using DeltaFn = void (*)(const int8_t*, int64_t, int, int32_t*, DevStatus*);
     DeltaFn fn;
     switch (lanes_for((L + 1) / 2, 32)) {
         case 1: fn = delta_kernel<1>; break;
-        case 2: fn = delta_kernel<2>; break;
         case 3: fn = delta_kernel<3>; break;
-        case 4: fn = delta_kernel<4>; break;
         case 5: fn = delta_kernel<5>; break;
-        case 6: fn = delta_kernel<6>; break;
         case 7: fn = delta_kernel<7>; break;
-        default: fn = delta_kernel<8>; break;
+        default: fn = delta_kernel<9>; break;
     }
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     fn<<<row_grid(batch, warps), warps * kWarp, smem, (cudaStream_t)stream>>>(seqs, batch, L, out, status);
@@ -510,7 +504,7 @@ int launch_features(const uint32_t* bits, int64_t stride, int64_t count, int32_t
 {
     if (count == 0) return LABS_OK;
     const int warps = 8;
-    const size_t smem = (size_t)warps * warp_smem((L + 1) / 2).words * sizeof(int);
+    const size_t smem = (size_t)warps * warp_smem((L + 1) / 2, 32).words * sizeof(int);
     cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     features_kernel<<<row_grid(count, warps), warps * kWarp, smem, (cudaStream_t)stream>>>(bits, stride, count, L, x);
     return status_of(cudaGetLastError());

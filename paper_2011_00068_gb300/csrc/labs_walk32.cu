@@ -5,15 +5,12 @@ namespace labsgpu {
 
 WalkFn walk_fn32(int rmax)
 {
-    switch (rmax) {
+    switch (rmax) {  // block_R(n, 32) is odd
         case 1: return walk_chunk_kernel<32, 1>;
-        case 2: return walk_chunk_kernel<32, 2>;
         case 3: return walk_chunk_kernel<32, 3>;
-        case 4: return walk_chunk_kernel<32, 4>;
         case 5: return walk_chunk_kernel<32, 5>;
-        case 6: return walk_chunk_kernel<32, 6>;
         case 7: return walk_chunk_kernel<32, 7>;
-        default: return walk_chunk_kernel<32, 8>;
+        default: return walk_chunk_kernel<32, 9>;
     }
 }
 
