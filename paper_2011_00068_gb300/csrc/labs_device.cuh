@@ -1004,19 +1004,33 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(K
 // rare, run divergently per half with tile-masked primitives (Tile<16>).  The
 // trajectory of each walker is exactly that of walk_steps.
 
-// Lane-local best candidate as a packed key: (dISL + 2^23) << 8 | i, ascending in
-// (dISL, i); 0xFFFFFFFF when the lane has none.  |dISL| < 2^23 and i < 256 for L <= 511.
-template <int R>
-__device__ __forceinline__ unsigned lane_key(const int (&dl)[R], uint32_t excl, const Outs<Pair, R>& o)
+// Neighbourhood as packed keys: (dISL + 2^23) << 8 | i, ascending in (dISL, i), or
+// 0xFFFFFFFF where the lane output does not exist (|dISL| < 2^23 and i < 256 for
+// L <= 511, so keys are unique and above 0).
+template <class TL, int R>
+__device__ __forceinline__ void assemble_keys(const View& V, int n, const Outs<TL, R>& o, const float (&X)[R],
+                                              const float (&P)[R], unsigned (&key)[R])
 {
-    unsigned best = 0xFFFFFFFFu;
+    int dl[R];
+    assemble(V, n, o, X, P, dl);
 #pragma unroll
     for (int r = 0; r < R; ++r)
-        if (!((excl >> r) & 1u) && dl[r] != INT_MAX) {
-            const unsigned k = ((unsigned)(dl[r] + (1 << 23)) << 8) | (unsigned)(2 * (o.v0 + r) + o.p);
-            best = min(best, k);
-        }
-    return best;
+        key[r] = dl[r] == INT_MAX ? 0xFFFFFFFFu
+                                  : ((unsigned)(dl[r] + (1 << 23)) << 8) | (unsigned)(2 * (o.v0 + r) + o.p);
+}
+
+// The lane's two lowest keys above `floor` (0xFFFFFFFF where there are fewer).
+template <int R>
+__device__ __forceinline__ void top2_above(const unsigned (&key)[R], unsigned floor, unsigned& b1, unsigned& b2)
+{
+    b1 = 0xFFFFFFFFu;
+    b2 = 0xFFFFFFFFu;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const unsigned k = key[r] > floor ? key[r] : 0xFFFFFFFFu;
+        b2 = min(b2, max(b1, k));
+        b1 = min(b1, k);
+    }
 }
 
 // Full probe of f for the halves with need set: every lane runs the same rounds.
@@ -1044,6 +1058,9 @@ __device__ __forceinline__ Probe pair_probe_full(const WalkEnv& env, uint64_t f,
     return pr;
 }
 
+// Outcome of probing HT for a candidate.
+enum : int { kProbeFree = 0, kProbeVisited = 1, kProbeUnknown = 2, kProbeNone = 3 };
+
 template <int R>
 __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool real, int* base, const WarpSmem& SL,
                           const View& V, int trace_slot, int64_t trace_start, labs_log_record* rec, const Pair& t,
@@ -1053,6 +1070,12 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
     const int lane = t.lane, n = env.n, c = n - 1;
     const Outs<Pair, R> o(t);
     const int cap = p.probe_cap;
+    const uint32_t tmask = (uint32_t)env.tmask;  // HT slots <= 2^20
+    // ISL at or below which the target merit factor is met (-1: no target)
+    const int tisl = (p.target_num <= 0 || p.target_den <= 0)
+                         ? -1
+                         : (int)min((int64_t)INT_MAX, (int64_t)p.target_den * env.L * env.L / (2 * (int64_t)p.target_num));
+    const int m0 = 1 + lane * R;  // this lane's lags 2m of the table update, m = m0 .. m0+R-1
     float P[R];
     p_direct(V, n, o, P);
     const int64_t first_step = w.steps;
@@ -1082,103 +1105,127 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
                 break;
             }
         }
-        int dl[R];
+        unsigned key[R];
         {
             float X[R];
             toeplitz(V, n, o, X);
-            assemble(V, n, o, X, P, dl);
+            assemble_keys(V, n, o, X, P, key);
         }
 
-        // Best admissible flip, as in walk_steps: two candidates per round, 8 slots each.
-        uint32_t excl = 0;
-        int best_i = -1, best_d = 0;
-        int64_t slot = -1;
+        // Best admissible flip, as in walk_steps: candidates in ascending key order, two
+        // per round, the first 8 HT slots of each probed by one half of the walker's
+        // lanes; keys <= floor are known to lead to visited states.
+        unsigned floor = 0u, kc = 0xFFFFFFFFu;
+        int slot = -1;
         uint64_t fnew = 0;
         bool done = !act;
-        while (__any_sync(kFull, !done)) {
-            const unsigned k0 = t.rminu(done ? 0xFFFFFFFFu : lane_key(dl, excl, o));
-            const int i0 = k0 == 0xFFFFFFFFu ? -1 : (int)(k0 & 0xFFu);
-            uint32_t ex1 = excl;
-            if (i0 >= 0) exclude<Pair, R>(ex1, i0, t);
-            const unsigned k1 = t.rminu(done || i0 < 0 ? 0xFFFFFFFFu : lane_key(dl, ex1, o));
-            const int i1 = k1 == 0xFFFFFFFFu ? -1 : (int)(k1 & 0xFFu);
-            const int d0 = (int)(k0 >> 8) - (1 << 23), d1 = (int)(k1 >> 8) - (1 << 23);
-            const int mine = lane < 8 ? i0 : i1;
+        do {
+            unsigned b1, b2;
+            top2_above(key, floor, b1, b2);
+            const unsigned k0 = t.rminu(done ? 0xFFFFFFFFu : b1);
+            const unsigned k1 = t.rminu(done ? 0xFFFFFFFFu : (b1 == k0 ? b2 : b1));
+            const bool has0 = k0 != 0xFFFFFFFFu, has1 = k1 != 0xFFFFFFFFu;
+            const uint64_t f0 = w.fp ^ (has0 ? __ldg(env.zk + (k0 & 0xFFu)) : 0ull);
+            const uint64_t f1 = w.fp ^ (has1 ? __ldg(env.zk + (k1 & 0xFFu)) : 0ull);
             const int hs = lane & 7;
-            const uint64_t f0 = i0 >= 0 ? w.fp ^ __ldg(env.zk + i0) : 0, f1 = i1 >= 0 ? w.fp ^ __ldg(env.zk + i1) : 0;
-            bool hit = false, match = false;
-            if (!done && mine >= 0 && hs < cap) {
-                const uint64_t f = lane < 8 ? f0 : f1;
-                const uint64_t e = env.T[(f + (uint64_t)hs) & env.tmask];
-                match = e == ((f & ~kGenMask) | w.gen);
-                hit = ((e & kGenMask) != w.gen) || match;
-            }
-            const unsigned bal = t.ballot(hit);
-            const unsigned b0 = bal & 0xFFu, b1 = (bal >> 8) & 0xFFu;
-            const int fl0 = b0 ? __ffs(b0) - 1 : 0, fl1 = b1 ? __ffs(b1) - 1 : 0;
-            const bool vis0 = t.shfl(match ? 1 : 0, fl0) != 0;
-            const bool vis1 = t.shfl(match ? 1 : 0, 8 + fl1) != 0;
-            // chains longer than 8 slots: full probes (rare)
-            const bool need0 = !done && i0 >= 0 && !b0 && cap > 8;
-            const bool need1 = !done && i1 >= 0 && !b1 && cap > 8;
-            Probe pf0{false, -1}, pf1{false, -1};
-            if (__any_sync(kFull, need0)) pf0 = pair_probe_full(env, f0, w.gen, cap, need0, t);
-            if (__any_sync(kFull, need1)) pf1 = pair_probe_full(env, f1, w.gen, cap, need1, t);
-            if (!done) {
-                if (i0 < 0) {
-                    done = true;  // every neighbour is in HT
-                } else {
-                    Probe pr0 = b0 ? Probe{vis0, (int64_t)((f0 + (uint64_t)fl0) & env.tmask)}
-                                   : (cap > 8 ? pf0 : Probe{false, -1});
-                    if (!pr0.visited) {
-                        best_i = i0, best_d = d0, slot = pr0.slot, fnew = f0, done = true;
-                    } else {
-                        exclude<Pair, R>(excl, i0, t);
-                        if (i1 >= 0) {
-                            Probe pr1 = b1 ? Probe{vis1, (int64_t)((f1 + (uint64_t)fl1) & env.tmask)}
-                                           : (cap > 8 ? pf1 : Probe{false, -1});
-                            if (!pr1.visited) {
-                                best_i = i1, best_d = d1, slot = pr1.slot, fnew = f1, done = true;
-                            } else {
-                                exclude<Pair, R>(excl, i1, t);
-                            }
-                        }
-                    }
+            const bool second = lane >= 8;
+            const uint64_t f = second ? f1 : f0;
+            const bool live = !done && (second ? has1 : has0) && hs < cap;
+            uint64_t e = 0;
+            if (live) e = env.T[((uint32_t)f + (uint32_t)hs) & tmask];
+            const bool match = live && e == ((f & ~kGenMask) | w.gen);
+            const bool hit = live && ((((uint32_t)e & (uint32_t)kGenMask) != w.gen) || match);
+            const unsigned hb = t.ballot(hit), mb = t.ballot(match);
+            const unsigned h0 = hb & 0xFFu, h1 = hb >> 8;
+            int st0 = !has0 ? kProbeNone
+                            : h0 ? ((mb & h0 & (0u - h0)) ? kProbeVisited : kProbeFree)
+                                 : (cap > 8 ? kProbeUnknown : kProbeFree);
+            int st1 = !has1 ? kProbeNone
+                            : h1 ? (((mb >> 8) & h1 & (0u - h1)) ? kProbeVisited : kProbeFree)
+                                 : (cap > 8 ? kProbeUnknown : kProbeFree);
+            int s0 = h0 ? (int)(((uint32_t)f0 + (uint32_t)(__ffs(h0) - 1)) & tmask) : -1;
+            int s1 = h1 ? (int)(((uint32_t)f1 + (uint32_t)(__ffs(h1) - 1)) & tmask) : -1;
+            // chains longer than 8 slots (rare): full probes, of the second candidate only
+            // when the first leads to a visited state
+            const bool need0 = !done && st0 == kProbeUnknown;
+            if (__any_sync(kFull, need0)) {
+                const Probe pf = pair_probe_full(env, f0, w.gen, cap, need0, t);
+                if (need0) {
+                    st0 = pf.visited ? kProbeVisited : kProbeFree;
+                    s0 = (int)pf.slot;
                 }
             }
-        }
+            const bool need1 = !done && st0 == kProbeVisited && st1 == kProbeUnknown;
+            if (__any_sync(kFull, need1)) {
+                const Probe pf = pair_probe_full(env, f1, w.gen, cap, need1, t);
+                if (need1) {
+                    st1 = pf.visited ? kProbeVisited : kProbeFree;
+                    s1 = (int)pf.slot;
+                }
+            }
+            if (!done) {
+                if (st0 == kProbeFree) {
+                    kc = k0, slot = s0, fnew = f0, done = true;
+                } else if (st0 == kProbeNone || st1 == kProbeNone) {
+                    done = true;  // every neighbour is in HT
+                } else if (st1 == kProbeFree) {
+                    kc = k1, slot = s1, fnew = f1, done = true;
+                } else {
+                    floor = k1;
+                }
+            }
+        } while (__any_sync(kFull, !done));
 
         // Apply the move (walkers that have one), from the values before the flip.
-        const bool moves = act && best_i >= 0;
+        const bool moves = act && kc != 0xFFFFFFFFu;
+        const int best_i = (int)(kc & 0xFFu), best_d = (int)(kc >> 8) - (1 << 23);
         const int pb = best_i & 1, vb = best_i >> 1;
         float* Ab = pb ? V.A1 : V.A0;
         const bool centre = best_i == c;
         const int vq = n - 1 - vb - pb;
+        const int mx = centre ? -1 : vq - vb;  // lag whose upper end is the mirror q: unchanged pair
+        const float coef = moves ? (centre ? -2.f : -4.f) * Ab[vb] : 0.f;
         float dd[R];
-        const float as = moves ? Ab[vb] : 0.f;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-            const int m = lane + 1 + 16 * k;
+            const int m = m0 + k;
             dd[k] = 0.f;
             if (moves && m < n) {
                 float up = Ab[vb + m];
-                if (!centre && vb + m == vq) up = 0.f;
-                const float dn = Ab[vb - m];
-                dd[k] = ((centre ? -2.f : -4.f) * as) * (up + dn);
+                if (m == mx) up = 0.f;
+                dd[k] = coef * (up + Ab[vb - m]);
             }
         }
         if (moves) p_update(V, n, o, P, pb, vb, centre ? -1 : vq);
         __syncwarp();
-        if (moves) {
+        if (moves && m0 < n) {
+            // E[m] += dd for this lane's m, in the pairs G[y] = (E[y], E[y+1]) and their
+            // mirrors at -y (pairs owned by two lanes are written field by field)
+            float e[R + 1];
 #pragma unroll
-            for (int k = 0; k < R; ++k) {
-                const int m = lane + 1 + 16 * k;
-                if (m < n) set_E(V, m, V.G[m].x + dd[k]);
+            for (int k = 0; k <= R; ++k) e[k] = 0.f;
+#pragma unroll
+            for (int k = 0; k < R; k += 2) {
+                if (m0 + k < n) {
+                    const float2 g = V.G[m0 + k];
+                    e[k] = g.x + dd[k];
+                    if (k + 1 < R) e[k + 1] = g.y + dd[k + 1];
+                }
             }
-            if (lane == 0) {
-                Ab[vb] = -as;
-                if (!centre) Ab[vq] = -Ab[vq];
-            }
+            V.G[m0 - 1].y = e[0];
+#pragma unroll
+            for (int k = 0; k + 1 < R; ++k)
+                if (m0 + k < n) V.G[m0 + k] = make_float2(e[k], e[k + 1]);
+            if (m0 + R - 1 < n) V.G[m0 + R - 1].x = e[R - 1];
+            if (m0 <= V.gpad) V.G[-m0].x = e[0];
+#pragma unroll
+            for (int k = 0; k + 1 < R; ++k)
+                if (m0 + k + 1 <= V.gpad) V.G[-m0 - k - 1] = make_float2(e[k + 1], e[k]);
+            if (m0 + R <= V.gpad) V.G[-m0 - R].y = e[R - 1];
+        }
+        if (moves && lane == 0) {
+            Ab[vb] = -Ab[vb];
+            if (!centre) Ab[vq] = -Ab[vq];
         }
         const bool stored = slot >= 0;
         if (moves && lane == 0 && stored) env.T[slot] = (fnew & ~kGenMask) | w.gen;
@@ -1188,7 +1235,7 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
         bool again = false;
         if (act) {
             w.steps += 1;
-            if (best_i < 0) {
+            if (!moves) {
                 w.blocked += 1;
                 again = true;
                 code = LABS_TRACE_BLOCKED;
@@ -1196,7 +1243,12 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
                 w.fp = fnew;
                 w.isl += best_d;
                 if (!stored) w.overflows += 1;
-                note_best(env, w, t);
+                if (w.isl < w.best_isl) {
+                    w.best_isl = w.isl;
+                    w.best_step = w.steps;
+                    if (lane < kBitWords) env.st->best[lane] = w.word;
+                }
+                if (w.target_step < 0 && w.isl <= tisl) w.target_step = w.steps;
                 if (w.isl < w.since) {
                     w.since = w.isl;
                     w.stag = 0;
