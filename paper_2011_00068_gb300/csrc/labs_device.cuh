@@ -1176,56 +1176,66 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
             }
         } while (__any_sync(kFull, !done));
 
-        // Apply the move (walkers that have one), from the values before the flip.
+        // Apply the move (walkers that have one), from the values before the flip.  The
+        // walker's rows are padded so that no read or write below needs a bounds test;
+        // lanes of a walker without a move rewrite unchanged values.
         const bool moves = act && kc != 0xFFFFFFFFu;
-        const int best_i = (int)(kc & 0xFFu), best_d = (int)(kc >> 8) - (1 << 23);
+        const int best_i = moves ? (int)(kc & 0xFFu) : 0, best_d = (int)(kc >> 8) - (1 << 23);
         const int pb = best_i & 1, vb = best_i >> 1;
         float* Ab = pb ? V.A1 : V.A0;
         const bool centre = best_i == c;
-        const int vq = n - 1 - vb - pb;
-        const int mx = centre ? -1 : vq - vb;  // lag whose upper end is the mirror q: unchanged pair
-        const float coef = moves ? (centre ? -2.f : -4.f) * Ab[vb] : 0.f;
-        float dd[R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            const int m = m0 + k;
-            dd[k] = 0.f;
-            if (moves && m < n) {
-                float up = Ab[vb + m];
-                if (m == mx) up = 0.f;
-                dd[k] = coef * (up + Ab[vb - m]);
-            }
-        }
-        if (moves) p_update(V, n, o, P, pb, vb, centre ? -1 : vq);
+        const int vq = centre ? vb : n - 1 - vb - pb;
+        const float as = Ab[vb], aq = centre ? 0.f : Ab[vq];
         __syncwarp();
-        if (moves && m0 < n) {
-            // E[m] += dd for this lane's m, in the pairs G[y] = (E[y], E[y+1]) and their
-            // mirrors at -y (pairs owned by two lanes are written field by field)
-            float e[R + 1];
+        // The flipped entries read as 0 while the changes are taken: that drops the pairs
+        // whose two ends both flip (unchanged) and the lag-0 terms from every sum below.
+        if (moves && lane == 0) {
+            Ab[vb] = 0.f;
+            Ab[vq] = 0.f;
+        }
+        __syncwarp();
+        // dC_{2m} = -4 s_i (s_{i+2m} + s_{i-2m}) (centre: -2 s_c (..)) for this lane's m
+        const float coef = moves ? (centre ? -2.f : -4.f) * as : 0.f;
+        float dd[R];
+        {
+            const float* up = Ab + vb + m0;
+            const float* dn = Ab + vb - m0;
 #pragma unroll
-            for (int k = 0; k <= R; ++k) e[k] = 0.f;
+            for (int k = 0; k < R; ++k) dd[k] = coef * (up[k] + dn[-k]);
+        }
+        // P_v of the moved class: each pair (v+m, v-m) with exactly one flipped end
+        // changes by -2 x its old product; the partner of w is 2v - w
+        {
+            const float g = (moves && o.p == pb) ? -2.f : 0.f;
+            const float* B1 = Ab + 2 * o.v0 - vb;
+            const float* B2 = Ab + 2 * o.v0 - vq;
+#pragma unroll
+            for (int r = 0; r < R; ++r) P[r] = fmaf(g, fmaf(aq, B2[2 * r], as * B1[2 * r]), P[r]);
+        }
+        {
+            // E[m] += dd for this lane's m, in the pairs G[y] = (E[y], E[y+1]) and their
+            // mirrors at -y (pairs shared with a neighbour lane are written field by field)
+            float e[R + 1];
+            e[R] = 0.f;
 #pragma unroll
             for (int k = 0; k < R; k += 2) {
-                if (m0 + k < n) {
-                    const float2 g = V.G[m0 + k];
-                    e[k] = g.x + dd[k];
-                    if (k + 1 < R) e[k + 1] = g.y + dd[k + 1];
-                }
+                const float2 g = V.G[m0 + k];
+                e[k] = g.x + dd[k];
+                if (k + 1 < R) e[k + 1] = g.y + dd[k + 1];
             }
             V.G[m0 - 1].y = e[0];
 #pragma unroll
-            for (int k = 0; k + 1 < R; ++k)
-                if (m0 + k < n) V.G[m0 + k] = make_float2(e[k], e[k + 1]);
-            if (m0 + R - 1 < n) V.G[m0 + R - 1].x = e[R - 1];
-            if (m0 <= V.gpad) V.G[-m0].x = e[0];
+            for (int k = 0; k + 1 < R; ++k) V.G[m0 + k] = make_float2(e[k], e[k + 1]);
+            V.G[m0 + R - 1].x = e[R - 1];
+            V.G[-m0].x = e[0];
 #pragma unroll
-            for (int k = 0; k + 1 < R; ++k)
-                if (m0 + k + 1 <= V.gpad) V.G[-m0 - k - 1] = make_float2(e[k + 1], e[k]);
-            if (m0 + R <= V.gpad) V.G[-m0 - R].y = e[R - 1];
+            for (int k = 0; k + 1 < R; ++k) V.G[-m0 - k - 1] = make_float2(e[k + 1], e[k]);
+            V.G[-m0 - R].y = e[R - 1];
         }
+        __syncwarp();
         if (moves && lane == 0) {
-            Ab[vb] = -Ab[vb];
-            if (!centre) Ab[vq] = -Ab[vq];
+            Ab[vb] = -as;
+            if (!centre) Ab[vq] = -aq;
         }
         const bool stored = slot >= 0;
         if (moves && lane == 0 && stored) env.T[slot] = (fnew & ~kGenMask) | w.gen;

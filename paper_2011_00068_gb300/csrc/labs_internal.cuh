@@ -123,7 +123,8 @@ struct KParams {
 // stays below 2^24 in magnitude for L <= 511), so that the Toeplitz product runs on
 // the FP32 pipes.
 //   A0: even positions s_0, s_2, .. (n values) as +-1.0f; zero from -apad up to the
-//       row end (indices [-apad, alen - apad))
+//       row end (indices [-apad, alen - apad)); the padding covers every index the
+//       walk reads without a bounds test
 //   A1: odd positions s_1, s_3, .. (n-1 values), laid out the same way
 //   G : pairs G[y] = (E[y], E[y+1]) for y in [-gpad, glen - gpad), where
 //       E[d] = C_{2|d|} for 0 < |d| < n and E[d] = 0 otherwise (E[0] = 0)
@@ -131,9 +132,9 @@ struct KParams {
 //       4 vectors x kBitVec words, zero beyond the class length
 constexpr int kBitVec = 9;  // 256 bits per class plus one zero word read by the shifts
 struct WarpSmem {
-    int apad;   // zero words below index 0 of each row (>= n_max - 1, multiple of 4)
+    int apad;   // zero words below index 0 of each row (multiple of 4)
     int alen;   // words per row (multiple of 4)
-    int gpad;   // pairs of G below y = 0 (>= the deepest window read, (tile/2) R - 1)
+    int gpad;   // pairs of G below y = 0 (>= the deepest read or write)
     int glen;   // pairs of G
     int goff;   // word offset of G[-gpad] (even)
     int boff;   // word offset of B
@@ -159,11 +160,16 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
 {
     WarpSmem w;
     const int R = block_R(n_max, tile);
-    const int hi = (3 * n_max) / 2 + 2 > n_max + 8 ? (3 * n_max) / 2 + 2 : n_max + 8;
-    w.apad = (n_max + 3) & ~3;
+    // two walkers per warp: the table update of lane l covers lags m = 1+lR .. (l+1)R
+    // of its walker (up to 16R) without bounds tests, in the rows and in G
+    const int span = tile == 16 ? 16 * R + 2 : 0;
+    int hi = (3 * n_max) / 2 + 2 > n_max + 8 ? (3 * n_max) / 2 + 2 : n_max + 8;
+    if ((n_max + 1) / 2 + span > hi) hi = (n_max + 1) / 2 + span;
+    const int lo = n_max > span ? n_max : span;
+    w.apad = (lo + 3) & ~3;
     w.alen = w.apad + ((hi + 7) & ~7);
-    w.gpad = (tile / 2) * R;
-    w.glen = w.gpad + ((n_max + 7) & ~7) + 2;
+    w.gpad = (tile / 2) * R > span ? (tile / 2) * R : span;
+    w.glen = w.gpad + (((n_max + 7) & ~7) + 2 > span ? ((n_max + 7) & ~7) + 2 : span);
     w.goff = 2 * w.alen;
     w.boff = w.goff + 2 * w.glen;
     w.words = (w.boff + 4 * kBitVec + 3) & ~3;
