@@ -552,17 +552,33 @@ __device__ void restart_walker(const WalkEnv& env, Walker& w, int* base, const W
     start_walker(env, w, base, SL, V, t, proposed);
 }
 
-// Tile-uniform: lane 0 reads the host-written control block and broadcasts.
-template <class TL>
-__device__ __forceinline__ int stop_requested(const KParams& p, const TL& t)
-{
-    int why = 0;
-    if (t.lane == 0 && p.ctrl != nullptr) {
-        if (p.ctrl->stop) why = LABS_ECANCELLED;
-        else if (global_ns() >= p.ctrl->deadline_ns) why = LABS_ETIMEOUT;
+// Stop requests from the host-written control block (mapped host memory, slow to
+// read).  One lane (`reader`) reads the deadline and the cancel flag when a walk call
+// starts; after that it re-reads the cancel flag at every poll without waiting for it:
+// the value lands while the steps run and is acted on at the next poll, kCheckEvery
+// steps later.  The deadline is compared with %globaltimer at every poll.
+struct StopCheck {
+    uint64_t deadline = ~0ull;
+    int next = 0;
+    __device__ __forceinline__ void start(const KParams& p, bool reader)
+    {
+        if (reader && p.ctrl != nullptr) {
+            deadline = p.ctrl->deadline_ns;
+            next = p.ctrl->stop;
+        }
     }
-    return t.shfl(why, 0);
-}
+    // LABS_ECANCELLED, LABS_ETIMEOUT or 0, in the reader lane (0 elsewhere)
+    __device__ __forceinline__ int poll(const KParams& p, bool reader)
+    {
+        int why = 0;
+        if (reader && p.ctrl != nullptr) {
+            if (next) why = LABS_ECANCELLED;
+            else if (global_ns() >= deadline) why = LABS_ETIMEOUT;
+            next = p.ctrl->stop;
+        }
+        return why;
+    }
+};
 
 // Result of probing HT for one candidate.
 struct Probe {
@@ -649,6 +665,8 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
     const int64_t first_step = w.steps;
     int log_first = 0, log_min = w.isl;
     bool log_live = true;
+    StopCheck stop;
+    stop.start(p, lane == 0);
     if (ex.rec != nullptr) {
         if (lane < kBitWords) ex.rec->bits[lane] = w.word;
         if (lane == 0) {
@@ -660,7 +678,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
     }
     while (w.steps < until) {
         if ((w.steps & (kCheckEvery - 1)) == 0) {
-            const int why = stop_requested(p, t);
+            const int why = t.shfl(stop.poll(p, lane == 0), 0);
             if (why) {
                 if (lane == 0) raise_error(p.status, why, (int)env.g);
                 break;
@@ -1004,19 +1022,35 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(K
 // rare, run divergently per half with tile-masked primitives (Tile<16>).  The
 // trajectory of each walker is exactly that of walk_steps.
 
-// Neighbourhood as packed keys: (dISL + 2^23) << 8 | i, ascending in (dISL, i), or
-// 0xFFFFFFFF where the lane output does not exist (|dISL| < 2^23 and i < 256 for
-// L <= 511, so keys are unique and above 0).
-template <class TL, int R>
-__device__ __forceinline__ void assemble_keys(const View& V, int n, const Outs<TL, R>& o, const float (&X)[R],
-                                              const float (&P)[R], unsigned (&key)[R])
+// Neighbourhood of two walkers per warp as packed keys: (dISL + 2^23) << 8 | i,
+// ascending in (dISL, i), or 0xFFFFFFFF where the lane output does not exist
+// (|dISL| < 2^23 and i < 256 for L <= 511, so keys are unique and above 0).  The
+// assembly of `assemble`, without bounds tests or branches: the rows and the table are
+// padded for every lane output (existing or not), s_{3i-L+1} reads as 0 below index 0,
+// and the centre's formula is selected per output.
+template <int R>
+__device__ __forceinline__ void pair_keys(const View& V, int n, const Outs<Pair, R>& o, const float (&X)[R],
+                                          const float (&P)[R], unsigned (&key)[R])
 {
-    int dl[R];
-    assemble(V, n, o, X, P, dl);
+    const int p = o.p, c = n - 1;
+    const float* A = p ? V.A1 : V.A0;
+    const int rv = (p ? (n >> 1) : ((n + 1) >> 1)) - o.v0;  // outputs r < rv exist
+    const int rc = (c & 1) == p ? ((c - p) >> 1) - o.v0 : -1;  // the centre's r, if this lane has it
+    const float base = (float)(16 * ((p ? n - 2 : n - 1) - 1)), cbase = (float)(16 * (c >> 1));
+    const float* Av = A + o.v0;                    // s_i          = Av[r]
+    const float* Aq = A + (n - 1 - p - o.v0);      // s_q          = Aq[-r]
+    const float* At = A + (3 * o.v0 + p - n + 1);  // s_{3i-L+1}   = At[3r]
+    const float2* Gc = V.G + (c - p - 2 * o.v0);   // C_{q-i}      = Gc[-2r].x
+    const unsigned i0 = (unsigned)(2 * o.v0 + p) + (1u << 31);
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-        key[r] = dl[r] == INT_MAX ? 0xFFFFFFFFu
-                                  : ((unsigned)(dl[r] + (1 << 23)) << 8) | (unsigned)(2 * (o.v0 + r) + o.p);
+    for (int r = 0; r < R; ++r) {
+        const float av = Av[r], sq = Aq[-r], ck0 = Gc[-2 * r].x, st = At[3 * r];
+        const bool ctr = r == rc;
+        const float add = ctr ? cbase : fmaf(32.f, fmaf(-sq, st, P[r]), base);
+        const float mul = (ctr ? -4.f : -8.f) * av;
+        const int dl = __float2int_rn(fmaf(mul, fmaf(-sq, ck0, X[r]), add));
+        key[r] = r < rv ? ((unsigned)dl << 8) + i0 + 2u * r : 0xFFFFFFFFu;
+    }
 }
 
 // The lane's two lowest keys above `floor` (0xFFFFFFFF where there are fewer).
@@ -1081,6 +1115,8 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
     const int64_t first_step = w.steps;
     int log_first = 0, log_min = w.isl;
     bool log_live = true;
+    StopCheck stop;
+    stop.start(p, (threadIdx.x & 31) == 0);
     if (real && rec != nullptr) {
         if (lane < kBitWords) rec->bits[lane] = w.word;
         if (lane == 0) {
@@ -1094,12 +1130,7 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
         const bool act = real && w.steps < until;
         if (!__any_sync(kFull, act)) break;
         if (__any_sync(kFull, act && (w.steps & (kCheckEvery - 1)) == 0)) {
-            int why = 0;
-            if ((threadIdx.x & 31) == 0 && p.ctrl != nullptr) {
-                if (p.ctrl->stop) why = LABS_ECANCELLED;
-                else if (global_ns() >= p.ctrl->deadline_ns) why = LABS_ETIMEOUT;
-            }
-            why = __shfl_sync(kFull, why, 0);
+            const int why = __shfl_sync(kFull, stop.poll(p, (threadIdx.x & 31) == 0), 0);
             if (why) {
                 if (act && lane == 0) raise_error(p.status, why, (int)env.g);
                 break;
@@ -1109,7 +1140,7 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
         {
             float X[R];
             toeplitz(V, n, o, X);
-            assemble_keys(V, n, o, X, P, key);
+            pair_keys(V, n, o, X, P, key);
         }
 
         // Best admissible flip, as in walk_steps: candidates in ascending key order, two

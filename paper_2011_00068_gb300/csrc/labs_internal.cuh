@@ -165,6 +165,7 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
     const int span = tile == 16 ? 16 * R + 2 : 0;
     int hi = (3 * n_max) / 2 + 2 > n_max + 8 ? (3 * n_max) / 2 + 2 : n_max + 8;
     if ((n_max + 1) / 2 + span > hi) hi = (n_max + 1) / 2 + span;
+    if (tile == 16 && 24 * R > hi) hi = 24 * R;  // the keys read s_{3i-L+1} for every lane output
     const int lo = n_max > span ? n_max : span;
     w.apad = (lo + 3) & ~3;
     w.alen = w.apad + ((hi + 7) & ~7);
