@@ -919,108 +919,15 @@ __device__ void save_walker(WalkerState* st, const Walker& w, int lane)
     }
 }
 
-// One launch advances every walker by up to chunk_steps steps toward the target.  The
-// kernel is compiled for a tile of TILE lanes per walker and a largest lane block RMAX
-// = block_R(n_max, TILE) (register allocation follows it; odd for TILE = 32); walkers
-// whose n needs a smaller block run with RMAX-2, which covers them (any R >=
-// block_R(n) computes the same values).
-template <int TILE, int RMAX>
-__global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(KParams p, int chunk_index)
-{
-    extern __shared__ __align__(16) int smem[];
-    const WarpSmem SL = warp_smem(p.n_max, TILE);
-    const Tile<TILE> t(threadIdx.x & 31);
-    const int slot_id = threadIdx.x / TILE;  // walker slot of this tile in the CTA
-    int* base = smem + slot_id * SL.words;
-    const View V = make_view(base, SL);
-    const int64_t target = p.status->target_steps;
-    for (;;) {
-        uint32_t q = 0;
-        if (t.lane == 0) q = atomicAdd(&p.queue[chunk_index], 1u);
-        const int64_t wi = (int64_t)t.shfl(q, 0);
-        if (wi >= p.W) break;
-        WalkerState* st = p.states + wi;
-        const int64_t steps_done = st->steps_done;
-        const int64_t until = min(target, steps_done + (int64_t)p.chunk_steps);
-        if (steps_done >= until) continue;
-        const DevGroup G = p.groups[st->group];
-        WalkEnv env;
-        env.p = &p;
-        env.tmask = (1ull << p.tabu_log2) - 1ull;
-        env.T = p.tabu + ((uint64_t)wi << p.tabu_log2);
-        env.zk = p.zkeys + G.zkey_off;
-        env.st = st;
-        env.L = G.L;
-        env.n = G.n;
-        env.patience = p.patience > 0 ? p.patience : 2 * G.n;
-        env.g = (uint32_t)wi;
-        Walker w;
-        load_walker(st, w, t.lane);
-        const int trace_slot = st->trace_slot;
-        const int64_t trace_start = trace_slot >= 0 ? p.trace_start[trace_slot] : 0;
-        const int isl = load_rows(base, SL, V, w.word, G.L, G.n, t);
-        if (isl != w.isl) {
-            if (t.lane == 0) raise_error(p.status, LABS_ESTATE, (int)wi);
-            continue;
-        }
-        StepExtras ex;
-        ex.scores = nullptr;
-        ex.sdump = nullptr;
-        ex.rec = nullptr;
-        ex.tau = 0;
-        ex.dump_cap = 0;
-        ex.n_max = p.n_max;
-        env.slot = nullptr;
-        env.slot_valid = nullptr;
-        env.rdump = nullptr;
-        env.rdump_idx = nullptr;
-        env.rdump_count = nullptr;
-        env.dump_cap = 0;
-        DevStatus* S = p.status;
-        if (S->learned) {
-            env.slot = S->l_slot + wi * kBitWords;
-            env.slot_valid = S->l_slot_valid + wi;
-            if (S->l_score_step[wi] == steps_done) {
-                ex.scores = S->l_scores + wi * p.n_max;
-                ex.tau = S->l_tau;
-            }
-            if (trace_slot >= 0 && S->d_scores != nullptr) {
-                ex.sdump = S->d_scores + (int64_t)trace_slot * S->d_cap * p.n_max;
-                ex.sdump_step = S->d_score_step + (int64_t)trace_slot * S->d_cap;
-                ex.sdump_count = S->d_score_count + trace_slot;
-                ex.dump_cap = S->d_cap;
-                env.rdump = S->d_restart + (int64_t)trace_slot * S->d_cap * kBitWords;
-                env.rdump_idx = S->d_restart_idx + (int64_t)trace_slot * S->d_cap;
-                env.rdump_count = S->d_restart_count + trace_slot;
-                env.dump_cap = S->d_cap;
-            }
-        }
-        if (S->log != nullptr && p.chunk_steps > 0) {
-            const int64_t since = steps_done - S->log_start;
-            if (since >= 0 && since % p.chunk_steps == 0) {
-                const int64_t idx = (since / p.chunk_steps) * p.W + wi;
-                if (idx < S->log_capacity) ex.rec = S->log + idx;
-            }
-        }
-        if (RMAX <= 2 || block_R(G.n, TILE) >= RMAX)
-            walk_steps<Tile<TILE>, RMAX>(env, w, until, base, SL, V, trace_slot, trace_start, ex, t);
-        else
-            walk_steps<Tile<TILE>, (RMAX > 2 ? RMAX - 2 : 1)>(env, w, until, base, SL, V, trace_slot, trace_start, ex,
-                                                              t);
-        save_walker(st, w, t.lane);
-        t.sync();
-    }
-}
-
-
-// ------------------------------------------------------------ two walkers per warp
+// ------------------------------------------------------------------ lockstep step
 //
-// The step of walk_steps for two walkers of the same length advancing in lockstep in
-// one warp (lanes 16h..16h+15 run walker h).  Both halves stay converged through the
-// hot part of every step, so each full-warp collective (Pair) serves both walkers;
-// what differs between the walkers is carried by predicates.  Restarts, which are
-// rare, run divergently per half with tile-masked primitives (Tile<16>).  The
-// trajectory of each walker is exactly that of walk_steps.
+// The step of walk_steps without the learned extras, written for a warp that runs
+// either one walker (lane group Tile<32>) or two walkers of the same length in
+// lockstep (Pair: lanes 16h..16h+15 run walker h).  With two walkers both halves stay
+// converged through the hot part of every step, so each full-warp collective serves
+// both walkers and what differs between them is carried by predicates; restarts,
+// which are rare, run divergently per half with tile-masked primitives (Tile<16>).
+// The trajectory of each walker is exactly that of walk_steps.
 
 // Neighbourhood of two walkers per warp as packed keys: (dISL + 2^23) << 8 | i,
 // ascending in (dISL, i), or 0xFFFFFFFF where the lane output does not exist
@@ -1028,8 +935,8 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(K
 // assembly of `assemble`, without bounds tests or branches: the rows and the table are
 // padded for every lane output (existing or not), s_{3i-L+1} reads as 0 below index 0,
 // and the centre's formula is selected per output.
-template <int R>
-__device__ __forceinline__ void pair_keys(const View& V, int n, const Outs<Pair, R>& o, const float (&X)[R],
+template <class LG, int R>
+__device__ __forceinline__ void lane_keys(const View& V, int n, const Outs<LG, R>& o, const float (&X)[R],
                                           const float (&P)[R], unsigned (&key)[R])
 {
     const int p = o.p, c = n - 1;
@@ -1067,14 +974,15 @@ __device__ __forceinline__ void top2_above(const unsigned (&key)[R], unsigned fl
     }
 }
 
-// Full probe of f for the halves with need set: every lane runs the same rounds.
-__device__ __forceinline__ Probe pair_probe_full(const WalkEnv& env, uint64_t f, uint32_t gen, int cap, bool need,
-                                                 const Pair& t)
+// Full probe of f for the walkers (halves) with need set: every lane runs the same rounds.
+template <class LG>
+__device__ __forceinline__ Probe lockstep_probe_full(const WalkEnv& env, uint64_t f, uint32_t gen, int cap, bool need,
+                                                     const LG& t)
 {
     const uint64_t tag = (f & ~kGenMask) | gen;
     Probe pr{false, -1};
     bool found = false;
-    for (int s0 = 0; s0 < cap; s0 += 16) {
+    for (int s0 = 0; s0 < cap; s0 += LG::kSize) {
         const int s = s0 + t.lane;
         uint64_t e = 0;
         const bool live = need && !found && s < cap;
@@ -1095,14 +1003,16 @@ __device__ __forceinline__ Probe pair_probe_full(const WalkEnv& env, uint64_t f,
 // Outcome of probing HT for a candidate.
 enum : int { kProbeFree = 0, kProbeVisited = 1, kProbeUnknown = 2, kProbeNone = 3 };
 
-template <int R>
-__device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool real, int* base, const WarpSmem& SL,
-                          const View& V, int trace_slot, int64_t trace_start, labs_log_record* rec, const Pair& t,
-                          const Tile<16>& tt)
+template <class LG, class RT, int R>
+__device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool real, int* base, const WarpSmem& SL,
+                              const View& V, int trace_slot, int64_t trace_start, labs_log_record* rec, const LG& t,
+                              const RT& tt)
 {
+    constexpr int S = LG::kSize / 2;            // HT slots probed per candidate in a round
+    constexpr unsigned SM = (1u << S) - 1u;
     const KParams& p = *env.p;
     const int lane = t.lane, n = env.n, c = n - 1;
-    const Outs<Pair, R> o(t);
+    const Outs<LG, R> o(t);
     const int cap = p.probe_cap;
     const uint32_t tmask = (uint32_t)env.tmask;  // HT slots <= 2^20
     // ISL at or below which the target merit factor is met (-1: no target)
@@ -1140,11 +1050,11 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
         {
             float X[R];
             toeplitz(V, n, o, X);
-            pair_keys(V, n, o, X, P, key);
+            lane_keys(V, n, o, X, P, key);
         }
 
         // Best admissible flip, as in walk_steps: candidates in ascending key order, two
-        // per round, the first 8 HT slots of each probed by one half of the walker's
+        // per round, the first S HT slots of each probed by one half of the walker's
         // lanes; keys <= floor are known to lead to visited states.
         unsigned floor = 0u, kc = 0xFFFFFFFFu;
         int slot = -1;
@@ -1158,8 +1068,8 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
             const bool has0 = k0 != 0xFFFFFFFFu, has1 = k1 != 0xFFFFFFFFu;
             const uint64_t f0 = w.fp ^ (has0 ? __ldg(env.zk + (k0 & 0xFFu)) : 0ull);
             const uint64_t f1 = w.fp ^ (has1 ? __ldg(env.zk + (k1 & 0xFFu)) : 0ull);
-            const int hs = lane & 7;
-            const bool second = lane >= 8;
+            const int hs = lane & (S - 1);
+            const bool second = lane >= S;
             const uint64_t f = second ? f1 : f0;
             const bool live = !done && (second ? has1 : has0) && hs < cap;
             uint64_t e = 0;
@@ -1167,20 +1077,20 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
             const bool match = live && e == ((f & ~kGenMask) | w.gen);
             const bool hit = live && ((((uint32_t)e & (uint32_t)kGenMask) != w.gen) || match);
             const unsigned hb = t.ballot(hit), mb = t.ballot(match);
-            const unsigned h0 = hb & 0xFFu, h1 = hb >> 8;
+            const unsigned h0 = hb & SM, h1 = (hb >> S) & SM;
             int st0 = !has0 ? kProbeNone
                             : h0 ? ((mb & h0 & (0u - h0)) ? kProbeVisited : kProbeFree)
-                                 : (cap > 8 ? kProbeUnknown : kProbeFree);
+                                 : (cap > S ? kProbeUnknown : kProbeFree);
             int st1 = !has1 ? kProbeNone
-                            : h1 ? (((mb >> 8) & h1 & (0u - h1)) ? kProbeVisited : kProbeFree)
-                                 : (cap > 8 ? kProbeUnknown : kProbeFree);
+                            : h1 ? (((mb >> S) & h1 & (0u - h1)) ? kProbeVisited : kProbeFree)
+                                 : (cap > S ? kProbeUnknown : kProbeFree);
             int s0 = h0 ? (int)(((uint32_t)f0 + (uint32_t)(__ffs(h0) - 1)) & tmask) : -1;
             int s1 = h1 ? (int)(((uint32_t)f1 + (uint32_t)(__ffs(h1) - 1)) & tmask) : -1;
-            // chains longer than 8 slots (rare): full probes, of the second candidate only
+            // chains longer than S slots (rare): full probes, of the second candidate only
             // when the first leads to a visited state
             const bool need0 = !done && st0 == kProbeUnknown;
             if (__any_sync(kFull, need0)) {
-                const Probe pf = pair_probe_full(env, f0, w.gen, cap, need0, t);
+                const Probe pf = lockstep_probe_full(env, f0, w.gen, cap, need0, t);
                 if (need0) {
                     st0 = pf.visited ? kProbeVisited : kProbeFree;
                     s0 = (int)pf.slot;
@@ -1188,7 +1098,7 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
             }
             const bool need1 = !done && st0 == kProbeVisited && st1 == kProbeUnknown;
             if (__any_sync(kFull, need1)) {
-                const Probe pf = pair_probe_full(env, f1, w.gen, cap, need1, t);
+                const Probe pf = lockstep_probe_full(env, f1, w.gen, cap, need1, t);
                 if (need1) {
                     st1 = pf.visited ? kProbeVisited : kProbeFree;
                     s1 = (int)pf.slot;
@@ -1303,7 +1213,7 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
                 }
             }
         }
-        if (again) {  // divergent: only this half restarts
+        if (again) {  // two walkers per warp: divergent, only this half restarts
             restart_walker(env, w, base, SL, V, tt);
             p_direct(V, n, o, P);
         }
@@ -1328,6 +1238,111 @@ __device__ void walk_pair(const WalkEnv& env, Walker& w, int64_t until, bool rea
         rec->min_isl = log_min;
     }
 }
+
+// One launch advances every walker by up to chunk_steps steps toward the target.  The
+// kernel is compiled for a tile of TILE lanes per walker and a largest lane block RMAX
+// = block_R(n_max, TILE) (register allocation follows it; odd for TILE = 32); walkers
+// whose n needs a smaller block run with RMAX-2, which covers them (any R >=
+// block_R(n) computes the same values).
+template <int TILE, int RMAX>
+__global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(KParams p, int chunk_index)
+{
+    extern __shared__ __align__(16) int smem[];
+    const WarpSmem SL = warp_smem(p.n_max, TILE);
+    const Tile<TILE> t(threadIdx.x & 31);
+    const int slot_id = threadIdx.x / TILE;  // walker slot of this tile in the CTA
+    int* base = smem + slot_id * SL.words;
+    const View V = make_view(base, SL);
+    const int64_t target = p.status->target_steps;
+    for (;;) {
+        uint32_t q = 0;
+        if (t.lane == 0) q = atomicAdd(&p.queue[chunk_index], 1u);
+        const int64_t wi = (int64_t)t.shfl(q, 0);
+        if (wi >= p.W) break;
+        WalkerState* st = p.states + wi;
+        const int64_t steps_done = st->steps_done;
+        const int64_t until = min(target, steps_done + (int64_t)p.chunk_steps);
+        if (steps_done >= until) continue;
+        const DevGroup G = p.groups[st->group];
+        WalkEnv env;
+        env.p = &p;
+        env.tmask = (1ull << p.tabu_log2) - 1ull;
+        env.T = p.tabu + ((uint64_t)wi << p.tabu_log2);
+        env.zk = p.zkeys + G.zkey_off;
+        env.st = st;
+        env.L = G.L;
+        env.n = G.n;
+        env.patience = p.patience > 0 ? p.patience : 2 * G.n;
+        env.g = (uint32_t)wi;
+        Walker w;
+        load_walker(st, w, t.lane);
+        const int trace_slot = st->trace_slot;
+        const int64_t trace_start = trace_slot >= 0 ? p.trace_start[trace_slot] : 0;
+        const int isl = load_rows(base, SL, V, w.word, G.L, G.n, t);
+        if (isl != w.isl) {
+            if (t.lane == 0) raise_error(p.status, LABS_ESTATE, (int)wi);
+            continue;
+        }
+        StepExtras ex;
+        ex.scores = nullptr;
+        ex.sdump = nullptr;
+        ex.rec = nullptr;
+        ex.tau = 0;
+        ex.dump_cap = 0;
+        ex.n_max = p.n_max;
+        env.slot = nullptr;
+        env.slot_valid = nullptr;
+        env.rdump = nullptr;
+        env.rdump_idx = nullptr;
+        env.rdump_count = nullptr;
+        env.dump_cap = 0;
+        DevStatus* S = p.status;
+        if (S->learned) {
+            env.slot = S->l_slot + wi * kBitWords;
+            env.slot_valid = S->l_slot_valid + wi;
+            if (S->l_score_step[wi] == steps_done) {
+                ex.scores = S->l_scores + wi * p.n_max;
+                ex.tau = S->l_tau;
+            }
+            if (trace_slot >= 0 && S->d_scores != nullptr) {
+                ex.sdump = S->d_scores + (int64_t)trace_slot * S->d_cap * p.n_max;
+                ex.sdump_step = S->d_score_step + (int64_t)trace_slot * S->d_cap;
+                ex.sdump_count = S->d_score_count + trace_slot;
+                ex.dump_cap = S->d_cap;
+                env.rdump = S->d_restart + (int64_t)trace_slot * S->d_cap * kBitWords;
+                env.rdump_idx = S->d_restart_idx + (int64_t)trace_slot * S->d_cap;
+                env.rdump_count = S->d_restart_count + trace_slot;
+                env.dump_cap = S->d_cap;
+            }
+        }
+        if (S->log != nullptr && p.chunk_steps > 0) {
+            const int64_t since = steps_done - S->log_start;
+            if (since >= 0 && since % p.chunk_steps == 0) {
+                const int64_t idx = (since / p.chunk_steps) * p.W + wi;
+                if (idx < S->log_capacity) ex.rec = S->log + idx;
+            }
+        }
+        // the learned mode's step (walk_steps) or the lockstep step of the plain walk
+        constexpr int R2 = RMAX > 2 ? RMAX - 2 : 1;
+        const bool full = RMAX <= 2 || block_R(G.n, TILE) >= RMAX;
+        if (S->learned) {
+            if (full)
+                walk_steps<Tile<TILE>, RMAX>(env, w, until, base, SL, V, trace_slot, trace_start, ex, t);
+            else
+                walk_steps<Tile<TILE>, R2>(env, w, until, base, SL, V, trace_slot, trace_start, ex, t);
+        } else {
+            if (full)
+                walk_lockstep<Tile<TILE>, Tile<TILE>, RMAX>(env, w, until, true, base, SL, V, trace_slot, trace_start,
+                                                            ex.rec, t, t);
+            else
+                walk_lockstep<Tile<TILE>, Tile<TILE>, R2>(env, w, until, true, base, SL, V, trace_slot, trace_start,
+                                                          ex.rec, t, t);
+        }
+        save_walker(st, w, t.lane);
+        t.sync();
+    }
+}
+
 
 // Walk launch with two walkers per warp (n <= 160): the warp takes two consecutive walkers; when
 // their lengths differ (a group boundary) or only one is left, it runs them one after
@@ -1402,16 +1417,17 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_pair_kernel(KP
             int R = block_R(G.n, 16);
             if (R < RMAX - 3) R = ((RMAX - 3) & 3) ? RMAX - 3 : RMAX - 2;
             if (R >= RMAX)
-                walk_pair<RMAX>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec, t, tt);
+                walk_lockstep<Pair, Tile<16>, RMAX>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec, t,
+                                                    tt);
             else if (R == RMAX - 1)
-                walk_pair<(RMAX > 1 ? RMAX - 1 : 1)>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec,
-                                                     t, tt);
+                walk_lockstep<Pair, Tile<16>, (RMAX > 1 ? RMAX - 1 : 1)>(env, w, until, real, base, SL, V, trace_slot,
+                                                                         trace_start, rec, t, tt);
             else if (R == RMAX - 2)
-                walk_pair<(RMAX > 2 ? RMAX - 2 : 1)>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec,
-                                                     t, tt);
+                walk_lockstep<Pair, Tile<16>, (RMAX > 2 ? RMAX - 2 : 1)>(env, w, until, real, base, SL, V, trace_slot,
+                                                                         trace_start, rec, t, tt);
             else
-                walk_pair<(RMAX > 3 ? RMAX - 3 : 1)>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec,
-                                                     t, tt);
+                walk_lockstep<Pair, Tile<16>, (RMAX > 3 ? RMAX - 3 : 1)>(env, w, until, real, base, SL, V, trace_slot,
+                                                                         trace_start, rec, t, tt);
             if (real) save_walker(env.st, w, t.lane);
             __syncwarp();
         }

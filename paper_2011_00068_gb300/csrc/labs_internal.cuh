@@ -160,12 +160,13 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
 {
     WarpSmem w;
     const int R = block_R(n_max, tile);
-    // two walkers per warp: the table update of lane l covers lags m = 1+lR .. (l+1)R
-    // of its walker (up to 16R) without bounds tests, in the rows and in G
-    const int span = tile == 16 ? 16 * R + 2 : 0;
+    // the lockstep walk step: the table update of lane l covers lags m = 1+lR .. (l+1)R
+    // of its walker (up to tile R) without bounds tests, in the rows and in G, and the
+    // keys read s_{3i-L+1} for every lane output (index below 3 (tile/2) R)
+    const int span = tile * R + 2;
     int hi = (3 * n_max) / 2 + 2 > n_max + 8 ? (3 * n_max) / 2 + 2 : n_max + 8;
     if ((n_max + 1) / 2 + span > hi) hi = (n_max + 1) / 2 + span;
-    if (tile == 16 && 24 * R > hi) hi = 24 * R;  // the keys read s_{3i-L+1} for every lane output
+    if (3 * (tile / 2) * R > hi) hi = 3 * (tile / 2) * R;
     const int lo = n_max > span ? n_max : span;
     w.apad = (lo + 3) & ~3;
     w.alen = w.apad + ((hi + 7) & ~7);
