@@ -32,6 +32,16 @@ UNIT = "flip evaluations/s"
 # FMA pipe: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (maximum SM clock).
 FP32_LANES_PER_SM = 128
 ALGO_FLOP_PER_LAG_TERM = 2
+# For comparison with an int32 formulation: one int32 multiply-add per lag term is the
+# least such a path executes, and IMAD issues at half the FP32 FMA rate (64 lanes/clk/SM).
+INT32_MAD_LANES_PER_SM = 64
+
+
+def int32_equivalent(lag_terms_per_s, sms, sm_mhz):
+    peak = INT32_MAD_LANES_PER_SM * sms * sm_mhz * 1e6
+    return {"lag_terms_per_s": lag_terms_per_s, "int32_mad_peak": peak, "frac": lag_terms_per_s / peak,
+            "note": "lag terms per second over the int32 multiply-add rate (%d SMs x %d lanes x %.0f MHz)"
+                    % (sms, INT32_MAD_LANES_PER_SM, sm_mhz)}
 PAIR_MAX_N = 160  # two walkers per warp up to n = 160 free variables
 # DRAM bytes per walker step of walk_pair_kernel at L=201 (ncu: dram__bytes_read.sum +
 # dram__bytes_write.sum of a 4864-walker x 256-step launch of the current kernel,
@@ -184,7 +194,7 @@ def run_reference(args):
     sample = "L=%d, %d walkers x %d steps per step (a bounded sample of the workload)" % (args.L, args.cpu_walkers, steps)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_of(args, 1),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -227,7 +237,8 @@ def delta_kernel_line(args, dev, stream, labs):
     return {"kernel": "delta_kernel", "rows": B, "L": L, "ms_per_launch": ms, "value": flips, "unit": UNIT,
             "input_bytes": B * L, "output_bytes": B * n * 4,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None}}
+                         "frac": achieved / peak, "traffic": None},
+            "int32_equivalent": int32_equivalent((n - 1) * flips, sms, sm_mhz)}
 
 
 def run_ours(args):
@@ -339,11 +350,12 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(config_of(args, world), launch={
                     "warps_per_cta": int(s.cfg.warps_per_cta) or 8, "chunk_steps": chunk,
                     "tuned": not args.no_tune}),
                 "roofline": roofline,
+                "int32_equivalent": int32_equivalent(value / world * (n - 1), sms, sm_mhz),
                 "clocks": clk.summary(), "e2e": e2e,
                 "gpu_launches": args.steps * (2 + nchunks),
                 "walk_ms_per_step": statistics.mean(walk_ms),
@@ -375,7 +387,7 @@ def run_learned(args):
     line = {"metric": "time-to-F>=8.5 at L=%d, learned vs plain (censored at %d steps)" % (args.learned_L,
                                                                                           args.learned_steps),
             "value": tt["learned"]["seconds"] if tt["learned"] else None, "unit": "s", "higher_is_better": False,
-            "n_gpus": 1, "dtype": "int32 walk / bf16 net", "data": "synthetic",
+            "n_gpus": 1, "dtype": "f32 walk / bf16 net", "data": "synthetic",
             "config": {"workload": "L=%d, %d walkers, %d steps, trained %d steps x batch 4096 on the walk log" %
                                    (args.learned_L, args.learned_walkers, args.learned_steps,
                                     args.learned_train_steps)},

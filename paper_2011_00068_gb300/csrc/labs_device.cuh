@@ -929,35 +929,44 @@ __device__ void save_walker(WalkerState* st, const Walker& w, int lane)
 // which are rare, run divergently per half with tile-masked primitives (Tile<16>).
 // The trajectory of each walker is exactly that of walk_steps.
 
-// Neighbourhood of two walkers per warp as packed keys: (dISL + 2^23) << 8 | i,
-// ascending in (dISL, i), or 0xFFFFFFFF where the lane output does not exist
-// (|dISL| < 2^23 and i < 256 for L <= 511, so keys are unique and above 0).  The
-// assembly of `assemble`, without bounds tests or branches: the rows and the table are
-// padded for every lane output (existing or not), s_{3i-L+1} reads as 0 below index 0,
-// and the centre's formula is selected per output.
+// dISL of the lane's R outputs (returns how many exist): the assembly of `assemble`
+// without bounds tests or branches, for the lockstep layouts (warp_smem pads the rows
+// and the table for every lane output, existing or not), s_{3i-L+1} reading as 0 below
+// index 0, and the centre's formula selected per output.  lane_keys packs them as
+// (dISL + 2^23) << 8 | i, ascending in (dISL, i), or 0xFFFFFFFF where the output does
+// not exist (|dISL| < 2^23 and i < 256 for L <= 511, so keys are unique and above 0).
 template <class LG, int R>
-__device__ __forceinline__ void lane_keys(const View& V, int n, const Outs<LG, R>& o, const float (&X)[R],
-                                          const float (&P)[R], unsigned (&key)[R])
+__device__ __forceinline__ int lane_dl(const View& V, int n, const Outs<LG, R>& o, const float (&X)[R],
+                                       const float (&P)[R], int (&dl)[R])
 {
     const int p = o.p, c = n - 1;
     const float* A = p ? V.A1 : V.A0;
-    const int rv = (p ? (n >> 1) : ((n + 1) >> 1)) - o.v0;  // outputs r < rv exist
     const int rc = (c & 1) == p ? ((c - p) >> 1) - o.v0 : -1;  // the centre's r, if this lane has it
     const float base = (float)(16 * ((p ? n - 2 : n - 1) - 1)), cbase = (float)(16 * (c >> 1));
     const float* Av = A + o.v0;                    // s_i          = Av[r]
     const float* Aq = A + (n - 1 - p - o.v0);      // s_q          = Aq[-r]
     const float* At = A + (3 * o.v0 + p - n + 1);  // s_{3i-L+1}   = At[3r]
     const float2* Gc = V.G + (c - p - 2 * o.v0);   // C_{q-i}      = Gc[-2r].x
-    const unsigned i0 = (unsigned)(2 * o.v0 + p) + (1u << 31);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const float av = Av[r], sq = Aq[-r], ck0 = Gc[-2 * r].x, st = At[3 * r];
         const bool ctr = r == rc;
         const float add = ctr ? cbase : fmaf(32.f, fmaf(-sq, st, P[r]), base);
         const float mul = (ctr ? -4.f : -8.f) * av;
-        const int dl = __float2int_rn(fmaf(mul, fmaf(-sq, ck0, X[r]), add));
-        key[r] = r < rv ? ((unsigned)dl << 8) + i0 + 2u * r : 0xFFFFFFFFu;
+        dl[r] = __float2int_rn(fmaf(mul, fmaf(-sq, ck0, X[r]), add));
     }
+    return (p ? (n >> 1) : ((n + 1) >> 1)) - o.v0;  // outputs r below this exist
+}
+
+template <class LG, int R>
+__device__ __forceinline__ void lane_keys(const View& V, int n, const Outs<LG, R>& o, const float (&X)[R],
+                                          const float (&P)[R], unsigned (&key)[R])
+{
+    int dl[R];
+    const int rv = lane_dl(V, n, o, X, P, dl);
+    const unsigned i0 = (unsigned)(2 * o.v0 + o.p) + (1u << 31);
+#pragma unroll
+    for (int r = 0; r < R; ++r) key[r] = r < rv ? ((unsigned)dl[r] << 8) + i0 + 2u * r : 0xFFFFFFFFu;
 }
 
 // The lane's two lowest keys above `floor` (0xFFFFFFFF where there are fewer).

@@ -173,6 +173,70 @@ __global__ void __launch_bounds__(256) delta_kernel(const int8_t* __restrict__ s
     }
 }
 
+// The same for two rows per warp (n <= 160), 16 lanes per row in lockstep: rows r0, r0+1
+// of each warp; R = block_R(n, 16).  The rows' shared memory is cleared once, each row
+// overwrites every entry the previous one set.
+template <int R>
+__global__ void __launch_bounds__(256) delta_pair_kernel(const int8_t* __restrict__ seqs, int64_t batch, int L,
+                                                         int32_t* __restrict__ out, DevStatus* status)
+{
+    extern __shared__ __align__(16) int smem[];
+    const int n = (L + 1) / 2, c = n - 1;
+    const WarpSmem SL = warp_smem(n, 16);
+    const Pair t(threadIdx.x & 31);
+    const int lane = t.lane;
+    int* base = smem + (threadIdx.x / 16) * SL.words;
+    const View V = make_view(base, SL);
+    const Outs<Pair, R> o(t);
+    clear_rows(base, SL, t);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r0 = 2 * ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); r0 < batch;
+         r0 += 2 * nwarps) {
+        const int64_t row = r0 + t.h;
+        const bool has = row < batch;
+        const int8_t* src = seqs + row * (int64_t)L;
+        bool ok = true;
+        if (has) {
+            for (int j = lane; j < L; j += 16) {
+                const int v = src[j];
+                ok = ok && (v == 1 || v == -1);
+                if (j & 1) V.A1[j >> 1] = (float)v;
+                else V.A0[j >> 1] = (float)v;
+            }
+        }
+        t.sync();
+        if (has) {
+            for (int j = 1 + lane; j <= c; j += 16) {  // Eq. 4
+                const int hi = c + j, lo = c - j;
+                const float shi = (hi & 1) ? V.A1[hi >> 1] : V.A0[hi >> 1];
+                const float slo = (lo & 1) ? V.A1[lo >> 1] : V.A0[lo >> 1];
+                ok = ok && (shi == ((j & 1) ? -slo : slo));
+            }
+        }
+        const bool valid = has && t.ballot(!ok) == 0u;
+        int32_t* dst = out + row * (int64_t)n;
+        if (has && !valid) {
+            for (int i = lane; i < n; i += 16) dst[i] = INT_MIN;
+            if (lane == 0 && status) atomicAdd(&status->invalid_rows, 1);
+        }
+        build_table(V, n, t);
+        int dl[R];
+        int rv;
+        {
+            float X[R], P[R];
+            toeplitz(V, n, o, X);
+            p_direct(V, n, o, P);
+            rv = lane_dl(V, n, o, X, P, dl);
+        }
+        if (valid) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (r < rv) dst[2 * (o.v0 + r) + o.p] = dl[r];
+        }
+        t.sync();
+    }
+}
+
 // --------------------------------------------------- learned proposal support
 
 // Network inputs of states given by their free-variable bits (8 words each, `stride`
@@ -464,11 +528,28 @@ int launch_isl(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevSt
 int launch_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status, void* stream)
 {
     if (batch == 0) return LABS_OK;
-    const int warps = 8;
-    const size_t smem = (size_t)warps * warp_smem((L + 1) / 2, 32).words * sizeof(int);
+    const int warps = 8, n = (L + 1) / 2;
     using DeltaFn = void (*)(const int8_t*, int64_t, int, int32_t*, DevStatus*);
     DeltaFn fn;
-    switch (lanes_for((L + 1) / 2, 32)) {
+    if (block_R(n, 16) <= 10) {  // two rows per warp
+        const size_t smem = (size_t)2 * warps * warp_smem(n, 16).words * sizeof(int);
+        switch (block_R(n, 16)) {
+            case 1: fn = delta_pair_kernel<1>; break;
+            case 2: fn = delta_pair_kernel<2>; break;
+            case 3: fn = delta_pair_kernel<3>; break;
+            case 5: fn = delta_pair_kernel<5>; break;
+            case 6: fn = delta_pair_kernel<6>; break;
+            case 7: fn = delta_pair_kernel<7>; break;
+            case 9: fn = delta_pair_kernel<9>; break;
+            default: fn = delta_pair_kernel<10>; break;
+        }
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fn<<<row_grid((batch + 1) / 2, warps), warps * kWarp, smem, (cudaStream_t)stream>>>(seqs, batch, L, out,
+                                                                                           status);
+        return status_of(cudaGetLastError());
+    }
+    const size_t smem = (size_t)warps * warp_smem(n, 32).words * sizeof(int);
+    switch (lanes_for(n, 32)) {
         case 1: fn = delta_kernel<1>; break;
         case 3: fn = delta_kernel<3>; break;
         case 5: fn = delta_kernel<5>; break;
