@@ -42,11 +42,11 @@ def int32_equivalent(lag_terms_per_s, sms, sm_mhz):
     return {"lag_terms_per_s": lag_terms_per_s, "int32_mad_peak": peak, "frac": lag_terms_per_s / peak,
             "note": "lag terms per second over the int32 multiply-add rate (%d SMs x %d lanes x %.0f MHz)"
                     % (sms, INT32_MAD_LANES_PER_SM, sm_mhz)}
-PAIR_MAX_N = 160  # two walkers per warp up to n = 160 free variables
-# DRAM bytes per walker step of walk_pair_kernel at L=201 (ncu: dram__bytes_read.sum +
-# dram__bytes_write.sum of a 4864-walker x 256-step launch of the current kernel,
-# profiles/walk_pair_kernel_L201_16384w.md); None when not captured
-DRAM_BYTES_PER_WALKER_STEP = 255.5
+WALK_KERNELS = {4: "walk_quad_kernel", 2: "walk_pair_kernel", 1: "walk_chunk_kernel"}  # by walkers per warp
+# DRAM bytes per walker step of the L=201 walk kernel (ncu: dram__bytes_read.sum +
+# dram__bytes_write.sum of one small launch of the current kernel, see profiles/);
+# None when not captured for the current kernel
+DRAM_BYTES_PER_WALKER_STEP = None
 
 
 def parse():
@@ -314,16 +314,16 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = FP32_LANES_PER_SM * 2 * sms * sm_mhz * 1e6
     achieved = ops_per_launch / avg_launch_s
-    pair = (args.L + 1) // 2 <= PAIR_MAX_N
+    kernel = WALK_KERNELS[st["walkers_per_warp"]]
     steps_per_launch = args.walkers * args.walk_steps / nchunks
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": (DRAM_BYTES_PER_WALKER_STEP * steps_per_launch
-                            if pair and args.L == 201 and DRAM_BYTES_PER_WALKER_STEP else None),
-                "traffic_note": ("bytes per launch: %.1f B per walker step from one ncu capture of a 4864-walker "
+                            if args.L == 201 and DRAM_BYTES_PER_WALKER_STEP else None),
+                "traffic_note": ("bytes per launch: %.1f B per walker step from one ncu capture of a small "
                                  "launch, scaled by walker steps" % DRAM_BYTES_PER_WALKER_STEP
                                  if DRAM_BYTES_PER_WALKER_STEP else "not captured for this kernel version"),
-                "kernel": "walk_pair_kernel" if pair else "walk_chunk_kernel",
+                "kernel": kernel, "lane_block": st["lane_block"],
                 "peak_source": "derived: %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz (FMA pipe)" % (
                     sms, FP32_LANES_PER_SM, sm_mhz)}
 

@@ -73,6 +73,7 @@ typedef struct labs_config {
 #define LABS_FLAG_CHECK_STATE 2  /* re-derive ISL from scratch at each chunk end */
 #define LABS_FLAG_LEARNED 4      /* reserve workspace for the learned mode (labs_learned) */
 #define LABS_FLAG_WARP_PER_WALKER 8 /* one walker per warp even where two per warp fit */
+#define LABS_FLAG_TWO_PER_WARP 16   /* at most two walkers per warp even where four fit */
 
 /* Counters of a context, summed over its walkers (labs_stats). */
 typedef struct labs_counters {
@@ -87,6 +88,8 @@ typedef struct labs_counters {
     int64_t target_step;       /* fewest steps after which some walker met the target,
                                   -1 if none did */
     int64_t walkers_at_target; /* walkers that met the target */
+    int32_t walkers_per_warp;  /* launch shape of the walk kernel: 4, 2 or 1 */
+    int32_t lane_block;        /* outputs per lane of the widest walker (R) */
 } labs_counters;
 
 /* One record of the walk log (labs_log): the state of a walker at the start of a

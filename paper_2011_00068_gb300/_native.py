@@ -26,6 +26,7 @@ LABS_FLAG_NO_GRAPH = 1
 LABS_FLAG_CHECK_STATE = 2
 LABS_FLAG_LEARNED = 4
 LABS_FLAG_WARP_PER_WALKER = 8
+LABS_FLAG_TWO_PER_WARP = 16
 LOG_RECORD_BYTES = 64
 
 ERRORS = {LABS_EINVAL: "EINVAL", LABS_ENOMEM: "ENOMEM", LABS_ECUDA: "ECUDA", LABS_ETIMEOUT: "ETIMEOUT",
@@ -53,7 +54,8 @@ class LabsCounters(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("flip_evaluations", ctypes.c_int64), ("restarts", ctypes.c_int64),
                 ("overflows", ctypes.c_int64), ("blocked", ctypes.c_int64), ("best_isl", ctypes.c_int32),
                 ("best_L", ctypes.c_int32), ("best_walker", ctypes.c_int64), ("target_step", ctypes.c_int64),
-                ("walkers_at_target", ctypes.c_int64)]
+                ("walkers_at_target", ctypes.c_int64), ("walkers_per_warp", ctypes.c_int32),
+                ("lane_block", ctypes.c_int32)]
 
 
 class LabsError(RuntimeError):

@@ -230,11 +230,17 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     c->off_tabu = off;
     off = align_up(off + sizeof(uint64_t) * ((size_t)c->W << k.tabu_log2), 256);
     c->total = off;
-    // launch shape of the walk kernel: two walkers per warp (16 lanes each) while a
-    // half warp covers n with at most 10 outputs per lane (n <= 160), else one walker
-    // per warp
-    // (the learned mode runs one walker per warp)
-    c->tile = (k.flags & (LABS_FLAG_WARP_PER_WALKER | LABS_FLAG_LEARNED)) || lanes_for(c->n_max, 16) > 10 ? 32 : 16;
+    // launch shape of the walk kernel: four walkers per warp (8 lanes each) while 8
+    // lanes cover n with at most kQuadMaxR outputs per lane (n <= 80; measured faster
+    // than two per warp there, equal from n = 88 to 104), two walkers per warp (16 lanes
+    // each) up to 10 outputs per lane (n <= 160), else one walker per warp (the learned
+    // mode runs one walker per warp)
+    if ((k.flags & (LABS_FLAG_WARP_PER_WALKER | LABS_FLAG_LEARNED)) || lanes_for(c->n_max, 16) > 10)
+        c->tile = 32;
+    else if (!(k.flags & LABS_FLAG_TWO_PER_WARP) && lanes_for(c->n_max, 8) <= kQuadMaxR)
+        c->tile = 8;
+    else
+        c->tile = 16;
     const size_t per_warp = (size_t)warp_smem(c->n_max, c->tile).words * sizeof(int) * (kWarp / c->tile);
     int warps = k.warps_per_cta ? k.warps_per_cta : 8;
     for (;;) {
@@ -655,6 +661,8 @@ int labs_stats(labs_ctx* c, int32_t L, labs_counters* out)
     out->overflows = (int64_t)h.st_overflows;
     out->blocked = (int64_t)h.st_blocked;
     out->walkers_at_target = (int64_t)h.st_at_target;
+    out->walkers_per_warp = kWarp / c->tile;
+    out->lane_block = lanes_for(c->n_max, c->tile);
     out->target_step = h.st_target_step == LLONG_MAX ? -1 : (int64_t)h.st_target_step;
     if (h.best_key == ~0ull) {
         out->best_isl = -1;

@@ -167,6 +167,52 @@ struct Pair {
     }
 };
 
+// Four walkers per warp advancing in lockstep (lanes 8h..8h+7 belong to walker h): the
+// reductions are butterflies of xor-shuffles that stay inside each group of 8 lanes, so
+// one sequence serves all four walkers.  Only for converged code.
+struct Quad {
+    static constexpr int kSize = 8;
+    static constexpr int kHalf = 4;
+    int lane;  // 0 .. 7
+    int h;     // which walker of the warp
+    int base;  // 8 h
+    __device__ explicit Quad(int warp_lane) : lane(warp_lane & 7), h(warp_lane >> 3), base(warp_lane & 24) {}
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+    __device__ __forceinline__ unsigned ballot(bool p) const { return (__ballot_sync(kFull, p) >> base) & 0xFFu; }
+    __device__ __forceinline__ int shfl(int v, int src) const { return __shfl_sync(kFull, v, base + src); }
+    __device__ __forceinline__ uint32_t shfl(uint32_t v, int src) const { return __shfl_sync(kFull, v, base + src); }
+    __device__ __forceinline__ int rmin(int v) const
+    {
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
+        return v;
+    }
+    __device__ __forceinline__ unsigned rminu(unsigned v) const
+    {
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
+        return v;
+    }
+    __device__ __forceinline__ int rmax(int v) const
+    {
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+        return v;
+    }
+    __device__ __forceinline__ int radd(int v) const
+    {
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        return v;
+    }
+    __device__ __forceinline__ uint32_t rxor(uint32_t v) const
+    {
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) v ^= __shfl_xor_sync(kFull, v, o);
+        return v;
+    }
+};
+
 // Per-walker views of the shared-memory layout.
 struct View {
     float* A0;    // A0[-apad .. alen-apad)
@@ -307,17 +353,15 @@ struct Outs {
 // (A[u], A[u+1]) by G[u-v] = (E[u-v], E[u+1-v]).  The window win[j] = G[u-v0-j] slides
 // two positions per pair of u: two 8-byte loads per R packed FMAs.  All operands and
 // partial sums are integers below 2^24, so the result is exact.
-template <class TL, int R>
-__device__ __forceinline__ void toeplitz(const View& V, int n, const Outs<TL, R>& o, float (&X)[R])
+// Outputs C0 .. C0+RC-1 of the lane's block (G already offset by -v0).
+template <int R, int C0, int RC>
+__device__ __forceinline__ void toeplitz_part(const float* A, const float2* G, int nu, float (&X)[R])
 {
-    const float* A = o.p ? V.A1 : V.A0;
-    const float2* G = V.G - o.v0;
-    const int nu = (n + 7) & ~7;
-    float2 acc[R], win[R];
+    float2 acc[RC], win[RC];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < RC; ++r) {
         acc[r] = make_float2(0.f, 0.f);
-        win[r] = G[-r];
+        win[r] = G[-C0 - r];
     }
 #pragma unroll kToeplitzUnroll
     for (int u = 0; u < nu; u += 8) {
@@ -328,15 +372,24 @@ __device__ __forceinline__ void toeplitz(const View& V, int n, const Outs<TL, R>
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] = __ffma2_rn(ap[q], win[r], acc[r]);
+            for (int r = 0; r < RC; ++r) acc[r] = __ffma2_rn(ap[q], win[r], acc[r]);
 #pragma unroll
-            for (int j = R - 1; j >= 2; --j) win[j] = win[j - 2];
-            if (R >= 2) win[1] = G[u + 2 * q + 1];
-            win[0] = G[u + 2 * q + 2];
+            for (int j = RC - 1; j >= 2; --j) win[j] = win[j - 2];
+            if (RC >= 2) win[1] = G[u + 2 * q + 1 - C0];
+            win[0] = G[u + 2 * q + 2 - C0];
         }
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) X[r] = acc[r].x + acc[r].y;
+    for (int r = 0; r < RC; ++r) X[C0 + r] = acc[r].x + acc[r].y;
+}
+
+// All R outputs in one pass over u (a two-pass split of a 13-output block, fewer
+// registers, ran the four-walker step 13-29% slower than one pass).
+template <class TL, int R>
+__device__ __forceinline__ void toeplitz(const View& V, int n, const Outs<TL, R>& o, float (&X)[R])
+{
+    const float* A = o.p ? V.A1 : V.A0;
+    toeplitz_part<R, 0, R>(A, V.G - o.v0, (n + 7) & ~7, X);
 }
 
 // P_v = sum_{m=1}^{v} A_p[v+m] A_p[v-m] from scratch for the lane's outputs, from the
@@ -939,7 +992,10 @@ template <class LG, int R>
 __device__ __forceinline__ int lane_dl(const View& V, int n, const Outs<LG, R>& o, const float (&X)[R],
                                        const float (&P)[R], int (&dl)[R])
 {
+    // four walkers per warp: the rows are not padded for the missing outputs' reads
+    constexpr bool kGuard = LG::kSize == 8;
     const int p = o.p, c = n - 1;
+    const int rv = (p ? (n >> 1) : ((n + 1) >> 1)) - o.v0;
     const float* A = p ? V.A1 : V.A0;
     const int rc = (c & 1) == p ? ((c - p) >> 1) - o.v0 : -1;  // the centre's r, if this lane has it
     const float base = (float)(16 * ((p ? n - 2 : n - 1) - 1)), cbase = (float)(16 * (c >> 1));
@@ -949,13 +1005,15 @@ __device__ __forceinline__ int lane_dl(const View& V, int n, const Outs<LG, R>& 
     const float2* Gc = V.G + (c - p - 2 * o.v0);   // C_{q-i}      = Gc[-2r].x
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const float av = Av[r], sq = Aq[-r], ck0 = Gc[-2 * r].x, st = At[3 * r];
+        const bool ok = !kGuard || r < rv;
+        const float av = Av[r], sq = Aq[-r];
+        const float ck0 = ok ? Gc[-2 * r].x : 0.f, st = ok ? At[3 * r] : 0.f;
         const bool ctr = r == rc;
         const float add = ctr ? cbase : fmaf(32.f, fmaf(-sq, st, P[r]), base);
         const float mul = (ctr ? -4.f : -8.f) * av;
         dl[r] = __float2int_rn(fmaf(mul, fmaf(-sq, ck0, X[r]), add));
     }
-    return (p ? (n >> 1) : ((n + 1) >> 1)) - o.v0;  // outputs r below this exist
+    return rv;  // outputs r below this exist
 }
 
 template <class LG, int R>
@@ -1019,6 +1077,7 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
 {
     constexpr int S = LG::kSize / 2;            // HT slots probed per candidate in a round
     constexpr unsigned SM = (1u << S) - 1u;
+    constexpr bool kQuad = LG::kSize == 8;      // rows and G less padded (warp_smem)
     const KParams& p = *env.p;
     const int lane = t.lane, n = env.n, c = n - 1;
     const Outs<LG, R> o(t);
@@ -1150,8 +1209,9 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
         {
             const float* up = Ab + vb + m0;
             const float* dn = Ab + vb - m0;
+            const int ku = kQuad ? (pb ? n - 1 : n) - vb - m0 : R;  // s_{i+2m} inside the class for k < ku
 #pragma unroll
-            for (int k = 0; k < R; ++k) dd[k] = coef * (up[k] + dn[-k]);
+            for (int k = 0; k < R; ++k) dd[k] = coef * ((k < ku ? up[k] : 0.f) + dn[-k]);
         }
         // P_v of the moved class: each pair (v+m, v-m) with exactly one flipped end
         // changes by -2 x its old product; the partner of w is 2v - w
@@ -1177,10 +1237,12 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
 #pragma unroll
             for (int k = 0; k + 1 < R; ++k) V.G[m0 + k] = make_float2(e[k], e[k + 1]);
             V.G[m0 + R - 1].x = e[R - 1];
-            V.G[-m0].x = e[0];
+            if (!kQuad || m0 + R <= V.gpad) {
+                V.G[-m0].x = e[0];
 #pragma unroll
-            for (int k = 0; k + 1 < R; ++k) V.G[-m0 - k - 1] = make_float2(e[k + 1], e[k]);
-            V.G[-m0 - R].y = e[R - 1];
+                for (int k = 0; k + 1 < R; ++k) V.G[-m0 - k - 1] = make_float2(e[k + 1], e[k]);
+                V.G[-m0 - R].y = e[R - 1];
+            }
         }
         __syncwarp();
         if (moves && lane == 0) {
@@ -1353,35 +1415,37 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(K
 }
 
 
-// Walk launch with two walkers per warp (n <= 160): the warp takes two consecutive walkers; when
-// their lengths differ (a group boundary) or only one is left, it runs them one after
-// the other with the other half idle.
-template <int RMAX>
-__global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_pair_kernel(KParams p, int chunk_index)
+// Walk launch with WPW = 32 / LG::kSize walkers per warp (two for n <= 160, four for
+// short sequences): the warp takes WPW consecutive walkers; when their lengths differ
+// (a group boundary) or fewer are left, it runs them one after the other with the other
+// lane groups idle.  RT is the tile type a lane group restarts with (divergently).
+template <class LG, class RT, int RMAX>
+__device__ __forceinline__ void walk_group(const KParams& p, int chunk_index)
 {
+    constexpr int WPW = 32 / LG::kSize;
     extern __shared__ __align__(16) int smem[];
-    const WarpSmem SL = warp_smem(p.n_max, 16);
-    const Pair t(threadIdx.x & 31);
-    const Tile<16> tt(threadIdx.x & 31);
-    int* base = smem + (threadIdx.x / 16) * SL.words;
+    const WarpSmem SL = warp_smem(p.n_max, LG::kSize);
+    const LG t(threadIdx.x & 31);
+    const RT tt(threadIdx.x & 31);
+    int* base = smem + (threadIdx.x / LG::kSize) * SL.words;
     const View V = make_view(base, SL);
     const int64_t target = p.status->target_steps;
     DevStatus* S = p.status;
     for (;;) {
         uint32_t q = 0;
-        if ((threadIdx.x & 31) == 0) q = atomicAdd(&p.queue[chunk_index], 2u);
+        if ((threadIdx.x & 31) == 0) q = atomicAdd(&p.queue[chunk_index], (uint32_t)WPW);
         q = __shfl_sync(kFull, q, 0);
         if ((int64_t)q >= p.W) break;
         const int64_t mine_w = (int64_t)q + t.h;
         const bool exists = mine_w < p.W;
         const int my_n = exists ? p.groups[p.states[mine_w].group].n : -1;
-        const int other_n = __shfl_xor_sync(kFull, my_n, 16);
-        const bool together = __all_sync(kFull, exists && my_n == other_n);
-        const int passes = together ? 1 : ((int64_t)q + 1 < p.W ? 2 : 1);
+        const int n0 = __shfl_sync(kFull, my_n, 0);
+        const bool together = __all_sync(kFull, exists && my_n == n0);
+        const int passes = together ? 1 : (int)min((int64_t)WPW, p.W - (int64_t)q);
         for (int pass = 0; pass < passes; ++pass) {
-            // together: both halves run their walker; else pass h runs half h alone
+            // together: every group runs its walker; else pass k runs group k alone
             const bool real0 = exists && (together || pass == t.h);
-            // the idle half mirrors the running half's length so that loops match
+            // the idle groups mirror the running group's length so that loops match
             const int64_t lead_w = together ? mine_w : (int64_t)q + pass;
             const DevGroup G = p.groups[p.states[lead_w].group];
             WalkEnv env;
@@ -1421,26 +1485,36 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_pair_kernel(KP
                 }
             }
             // lane block: block_R(n) when it is one of RMAX .. RMAX-3, else the smallest
-            // bank-conflict-free one of those (RMAX-3, or RMAX-2 when RMAX-3 is a
-            // multiple of 4)
-            int R = block_R(G.n, 16);
-            if (R < RMAX - 3) R = ((RMAX - 3) & 3) ? RMAX - 3 : RMAX - 2;
+            // bank-conflict-free one of those
+            int R = block_R(G.n, LG::kSize);
+            if (R < RMAX - 3) R = conflict_free_R(RMAX - 3, LG::kSize);
             if (R >= RMAX)
-                walk_lockstep<Pair, Tile<16>, RMAX>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec, t,
-                                                    tt);
+                walk_lockstep<LG, RT, RMAX>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec, t, tt);
             else if (R == RMAX - 1)
-                walk_lockstep<Pair, Tile<16>, (RMAX > 1 ? RMAX - 1 : 1)>(env, w, until, real, base, SL, V, trace_slot,
-                                                                         trace_start, rec, t, tt);
+                walk_lockstep<LG, RT, (RMAX > 1 ? RMAX - 1 : 1)>(env, w, until, real, base, SL, V, trace_slot,
+                                                                 trace_start, rec, t, tt);
             else if (R == RMAX - 2)
-                walk_lockstep<Pair, Tile<16>, (RMAX > 2 ? RMAX - 2 : 1)>(env, w, until, real, base, SL, V, trace_slot,
-                                                                         trace_start, rec, t, tt);
+                walk_lockstep<LG, RT, (RMAX > 2 ? RMAX - 2 : 1)>(env, w, until, real, base, SL, V, trace_slot,
+                                                                 trace_start, rec, t, tt);
             else
-                walk_lockstep<Pair, Tile<16>, (RMAX > 3 ? RMAX - 3 : 1)>(env, w, until, real, base, SL, V, trace_slot,
-                                                                         trace_start, rec, t, tt);
+                walk_lockstep<LG, RT, (RMAX > 3 ? RMAX - 3 : 1)>(env, w, until, real, base, SL, V, trace_slot,
+                                                                 trace_start, rec, t, tt);
             if (real) save_walker(env.st, w, t.lane);
             __syncwarp();
         }
     }
+}
+
+template <int RMAX>
+__global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_pair_kernel(KParams p, int chunk_index)
+{
+    walk_group<Pair, Tile<16>, RMAX>(p, chunk_index);
+}
+
+template <int RMAX>
+__global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_quad_kernel(KParams p, int chunk_index)
+{
+    walk_group<Quad, Tile<8>, RMAX>(p, chunk_index);
 }
 
 }  // namespace

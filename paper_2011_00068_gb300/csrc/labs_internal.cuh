@@ -12,6 +12,7 @@ namespace labsgpu {
 constexpr int kWarp = 32;
 constexpr int kMaxN = (LABS_MAX_L + 1) / 2;  // 256 free variables
 constexpr int kBitWords = kMaxN / 32;        // 8 words of free-variable bits
+constexpr int kQuadMaxR = 10;                // largest lane block of four walkers per warp (n <= 80)
 constexpr int kMaxChunksPerCall = 4096;      // chunk launches per labs_walk call
 constexpr int kMaxTrace = 4096;              // traced walkers
 constexpr int kCheckEvery = 64;              // steps between stop checks
@@ -144,43 +145,63 @@ struct WarpSmem {
 // (tile/2 lanes per parity class): at least ceil(ceil(n/2) / (tile/2)), raised until
 // the lanes of a class, whose table windows lie 8R bytes apart, read 16 distinct pairs
 // of banks, i.e. until 16 / gcd(R, 16) >= tile/2.
-__host__ __device__ inline int block_R(int n, int tile)
+__host__ __device__ inline int conflict_free_R(int R, int tile)  // smallest such R' >= R
 {
-    const int h = tile / 2;
-    int R = (((n + 1) >> 1) + h - 1) / h;
     for (;;) {
         const int low = R & -R;  // gcd(R, 16) for R < 32
-        if (16 / (low < 16 ? low : 16) >= h) return R;
+        if (16 / (low < 16 ? low : 16) >= tile / 2) return R;
         ++R;
     }
 }
+__host__ __device__ inline int block_R(int n, int tile)
+{
+    const int h = tile / 2;
+    return conflict_free_R((((n + 1) >> 1) + h - 1) / h, tile);
+}
 
-// n_max: largest number of free variables served; tile: lanes per walker (32 or 16).
+// n_max: largest number of free variables served; tile: lanes per walker (32, 16 or 8).
 __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
 {
     WarpSmem w;
     const int R = block_R(n_max, tile);
-    // the lockstep walk step: the table update of lane l covers lags m = 1+lR .. (l+1)R
-    // of its walker (up to tile R) without bounds tests, in the rows and in G, and the
-    // keys read s_{3i-L+1} for every lane output (index below 3 (tile/2) R)
-    const int span = tile * R + 2;
-    int hi = (3 * n_max) / 2 + 2 > n_max + 8 ? (3 * n_max) / 2 + 2 : n_max + 8;
-    if ((n_max + 1) / 2 + span > hi) hi = (n_max + 1) / 2 + span;
-    if (3 * (tile / 2) * R > hi) hi = 3 * (tile / 2) * R;
-    const int lo = n_max > span ? n_max : span;
-    w.apad = (lo + 3) & ~3;
-    w.alen = w.apad + ((hi + 7) & ~7);
-    w.gpad = (tile / 2) * R > span ? (tile / 2) * R : span;
-    w.glen = w.gpad + (((n_max + 7) & ~7) + 2 > span ? ((n_max + 7) & ~7) + 2 : span);
+    const int top = ((n_max + 7) & ~7) + 2;  // G above 0: the Toeplitz window reaches round8(n)
+    if (tile == 8) {
+        // four walkers per warp (tight on shared memory): the lag update of lane l covers
+        // m = 1+lR .. (l+1)R (up to 8R) and reads s_{i+2m} only inside the class, the
+        // keys read s_{3i-L+1} and C_{q-i} only for existing outputs, and the mirror half
+        // of G is kept down to E[-(4R+1)], what the Toeplitz window reads
+        const int lo = n_max > 8 * R + 1 ? n_max : 8 * R + 1;
+        const int hi = n_max + 8 > 8 * R + 2 ? n_max + 8 : 8 * R + 2;
+        w.apad = (lo + 3) & ~3;
+        w.alen = w.apad + ((hi + 7) & ~7);
+        w.gpad = 4 * R + 1;
+        w.glen = w.gpad + (top > 8 * R + 2 ? top : 8 * R + 2);
+    } else {
+        // the lockstep walk step: the lag update of lane l covers m = 1+lR .. (l+1)R of
+        // its walker (up to tile R) without bounds tests, in the rows and in G, and the
+        // keys read s_{3i-L+1} for every lane output (index below 3 (tile/2) R)
+        const int span = tile * R + 2;
+        int hi = (3 * n_max) / 2 + 2 > n_max + 8 ? (3 * n_max) / 2 + 2 : n_max + 8;
+        if ((n_max + 1) / 2 + span > hi) hi = (n_max + 1) / 2 + span;
+        if (3 * (tile / 2) * R > hi) hi = 3 * (tile / 2) * R;
+        const int lo = n_max > span ? n_max : span;
+        w.apad = (lo + 3) & ~3;
+        w.alen = w.apad + ((hi + 7) & ~7);
+        w.gpad = (tile / 2) * R > span ? (tile / 2) * R : span;
+        w.glen = w.gpad + (top > span ? top : span);
+    }
     w.goff = 2 * w.alen;
     w.boff = w.goff + 2 * w.glen;
     w.words = (w.boff + 4 * kBitVec + 3) & ~3;
     return w;
 }
 
-// Walk kernel instantiations (labs_walk16a.cu, labs_walk16b.cu: two walkers per warp,
+// Walk kernel instantiations (labs_walk8a.cu, labs_walk8b.cu: four walkers per warp,
+// lane blocks 1-6 and 7-10; labs_walk16a.cu, labs_walk16b.cu: two walkers per warp,
 // lane blocks 1-5 and 6-10; labs_walk32.cu: one walker per warp).
 using WalkFn = void (*)(KParams, int);
+WalkFn walk_fn8a(int rmax);
+WalkFn walk_fn8b(int rmax);
 WalkFn walk_fn16a(int rmax);
 WalkFn walk_fn16b(int rmax);
 WalkFn walk_fn32(int rmax);

@@ -79,6 +79,39 @@ def test_chunking_and_graphs_do_not_change_trajectories():
     assert np.array_equal(code.cpu().numpy(), ref[0]) and np.array_equal(isl.cpu().numpy(), ref[1])
 
 
+@pytest.mark.parametrize("L,W", [(41, 13), (151, 10), (61, 6)])
+def test_launch_shapes_agree_with_oracle(L, W):
+    """Four, two and one walker per warp run the same trajectories; walker counts that
+    are not a multiple of the walkers per warp leave partly idle warps."""
+    steps, seed = 500, 12
+    o = oracle.walk(L, seed, W, steps, trace=True)
+    shapes = []
+    for flags in (0, _native.LABS_FLAG_TWO_PER_WARP, _native.LABS_FLAG_WARP_PER_WALKER):
+        s, code, isl = run_traced(L, W, steps, seed, flags=flags)
+        shapes.append(s.stats()["walkers_per_warp"])
+        assert np.array_equal(code, o["trace_code"]) and np.array_equal(isl, o["trace_isl"]), flags
+        s.close()
+    assert shapes == [4, 2, 1]
+
+
+def test_mixed_short_lengths_four_per_warp():
+    """Lengths that change inside a warp of four walkers run group by group."""
+    Ls, counts = [41, 23, 61, 5, 101], [5, 6, 7, 3, 2]
+    steps, seed = 400, 4
+    s = labs.Search(Ls, counts, seed)
+    assert s.stats()["walkers_per_warp"] == 4
+    code, isl = s.trace(list(range(sum(counts))), steps)
+    s.walk(steps)
+    s.sync()
+    code, isl = code.cpu().numpy(), isl.cpu().numpy()
+    first = 0
+    for L, cnt in zip(Ls, counts):
+        o = oracle.walk(L, seed, cnt, steps, first_walker=first, trace=True)
+        assert np.array_equal(code[first:first + cnt], o["trace_code"]), L
+        assert np.array_equal(isl[first:first + cnt], o["trace_isl"]), L
+        first += cnt
+
+
 def test_mixed_lengths_one_launch():
     Ls = [201, 23, 303, 41, 255]
     counts = [6, 5, 4, 7, 3]
