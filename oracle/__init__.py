@@ -17,6 +17,8 @@ the passage of the paper it follows:
 * ``philox4x32_10`` / ``random_start`` -- Philox4x32-10 (Salmon et al., SC'11) and
   the random start of Algorithm 1.
 * ``walk`` -- Algorithm 1 in the self-avoiding-walk form with restarts (lssOrel).
+* ``bestfirst`` -- Algorithm 1 as printed: best-first search with a fixed-size
+  priority queue of evaluated neighbours (impxLast, Section 3).
 * ``enumerate_skew`` -- exhaustive search over skew-symmetric sequences.
 """
 from __future__ import annotations
@@ -91,6 +93,8 @@ def lib():
             L.lo_walk.argtypes = [i32, u64, i64, i64, i64, ctypes.POINTER(WalkCfg), P, P, P, P, P, i32]
             L.lo_walk.restype = ctypes.c_int
             L.lo_enumerate.argtypes = [i32, P, P, P, P, i32]; L.lo_enumerate.restype = ctypes.c_int
+            L.lo_bestfirst.argtypes = [i32, u64, i64, i64, i64, ctypes.POINTER(WalkCfg), i32, P, P, P, P, P, i32]
+            L.lo_bestfirst.restype = ctypes.c_int
             L.lo_walk_replay.argtypes = [i32, u64, i64, i64, ctypes.POINTER(WalkCfg), i32, i32, P, P, i32, i32, P, P,
                                          P, P, P, P, P]
             L.lo_walk_replay.restype = ctypes.c_int
@@ -226,6 +230,37 @@ def walk(L: int, seed: int, walkers: int, steps: int, *, first_walker: int = 0,
                        ctypes.cast(res, ctypes.c_void_p), _ptr(best), _ptr(final), tcp, tip, nthreads)
     if rc != 0:
         raise RuntimeError("oracle walk failed: %d" % rc)
+    out = {f: np.array([getattr(res[w], f) for w in range(walkers)]) for f in WALK_RESULT_FIELDS}
+    out["best_seq"] = best
+    out["final_seq"] = final
+    if trace:
+        out["trace_code"] = tc
+        out["trace_isl"] = ti
+    return out
+
+
+def bestfirst(L: int, seed: int, walkers: int, steps: int, *, pq_size: int = 32, first_walker: int = 0,
+              tabu_log2: int = 16, probe_cap: int = 32, target: tuple[int, int] = (17, 2), trace: bool = False,
+              nthreads: int = 0) -> dict:
+    """Algorithm 1 as printed (best-first search with a priority queue of pq_size
+    entries), for walkers first_walker.. (+walkers); outputs as walk().  Trace codes:
+    the low 16 bits of each new S's fingerprint, TRACE_RESTART set after an HT overflow,
+    -1 when the queue ran empty."""
+    cfg = WalkCfg(tabu_log2, probe_cap, 0, target[0], target[1])
+    res = (WalkResult * max(walkers, 1))()
+    best = np.zeros((walkers, L), dtype=np.int8)
+    final = np.zeros((walkers, L), dtype=np.int8)
+    if trace:
+        tc = np.zeros((walkers, steps), dtype=np.int32)
+        ti = np.zeros((walkers, steps), dtype=np.int32)
+        tcp, tip = _ptr(tc), _ptr(ti)
+    else:
+        tc = ti = None
+        tcp = tip = None
+    rc = lib().lo_bestfirst(L, seed, first_walker, walkers, steps, ctypes.byref(cfg), pq_size,
+                            ctypes.cast(res, ctypes.c_void_p), _ptr(best), _ptr(final), tcp, tip, nthreads)
+    if rc != 0:
+        raise RuntimeError("oracle best-first search failed: %d" % rc)
     out = {f: np.array([getattr(res[w], f) for w in range(walkers)]) for f in WALK_RESULT_FIELDS}
     out["best_seq"] = best
     out["final_seq"] = final

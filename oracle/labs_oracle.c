@@ -522,10 +522,13 @@ typedef struct {
     int8_t *best_seq;
     int8_t *final_seq;
     int32_t *trace_code, *trace_isl;
+    int32_t pq_size;  /* 0: the walk; > 0: best-first search with this queue size */
     int64_t next;
     pthread_mutex_t lock;
     int status;
 } lo_walk_job;
+
+static int run_bestfirst(lo_walk_job *job, int64_t w_idx);
 
 static int run_walker(lo_walk_job *job, int64_t w_idx, const lo_replay *replay)
 {
@@ -587,7 +590,7 @@ static void *walk_thread(void *arg)
         int64_t w = job->next++;
         pthread_mutex_unlock(&job->lock);
         if (w >= job->count) break;
-        int rc = run_walker(job, w, NULL);
+        int rc = job->pq_size > 0 ? run_bestfirst(job, w) : run_walker(job, w, NULL);
         if (rc != 0) {
             pthread_mutex_lock(&job->lock);
             job->status = rc;
@@ -602,9 +605,9 @@ static void *walk_thread(void *arg)
  * NULL, per-step traces ([count][steps]).  nthreads <= 0 uses every online core.
  * Returns 0, -1 on bad arguments, -2 on an internal mismatch, -3 on allocation
  * failure. */
-int lo_walk(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t steps,
-            const lo_walk_cfg *cfg, lo_walk_result *res, int8_t *best_seq, int8_t *final_seq,
-            int32_t *trace_code, int32_t *trace_isl, int32_t nthreads)
+static int walk_many(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t steps,
+                     const lo_walk_cfg *cfg, int32_t pq_size, lo_walk_result *res, int8_t *best_seq,
+                     int8_t *final_seq, int32_t *trace_code, int32_t *trace_isl, int32_t nthreads)
 {
     if (L < 3 || (L & 1) == 0 || count < 0 || steps < 0 || !cfg || !res) return -1;
     if (cfg->tabu_log2 < 1 || cfg->tabu_log2 > 20 || cfg->probe_cap < 1) return -1;
@@ -619,6 +622,7 @@ int lo_walk(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t steps,
     job.L = L; job.seed = seed; job.g0 = g0; job.count = count; job.steps = steps;
     job.cfg = cfg; job.zkey = zkey; job.res = res; job.best_seq = best_seq;
     job.final_seq = final_seq; job.trace_code = trace_code; job.trace_isl = trace_isl;
+    job.pq_size = pq_size;
     pthread_mutex_init(&job.lock, NULL);
     if (nthreads <= 0) nthreads = (int32_t)sysconf(_SC_NPROCESSORS_ONLN);
     if (nthreads < 1) nthreads = 1;
@@ -630,6 +634,13 @@ int lo_walk(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t steps,
     pthread_mutex_destroy(&job.lock);
     free(zkey);
     return job.status;
+}
+
+int lo_walk(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t steps,
+            const lo_walk_cfg *cfg, lo_walk_result *res, int8_t *best_seq, int8_t *final_seq,
+            int32_t *trace_code, int32_t *trace_isl, int32_t nthreads)
+{
+    return walk_many(L, seed, g0, count, steps, cfg, 0, res, best_seq, final_seq, trace_code, trace_isl, nthreads);
 }
 
 /* One walker (id g) replayed with the learned-mode choices of a GPU run (lo_replay);
@@ -655,6 +666,205 @@ int lo_walk_replay(int32_t L, uint64_t seed, int64_t g, int64_t steps, const lo_
     int rc = run_walker(&job, 0, &rp);
     free(zkey);
     return rc;
+}
+
+/* ------------------------------------------- best-first search (Algorithm 1) */
+
+/* Algorithm 1 as printed (impxLast): every neighbour of the current S that is not in
+ * HT is evaluated and goes into a priority queue of fixed size K ordered by merit
+ * factor (the best is kept), and the next S is removed from the front of the queue.
+ * Readings where the paper is silent:
+ *   - HT holds the sequences that have been S, as in the walk; a neighbour in HT is
+ *     skipped, and an entry taken from the queue that is in HT by then is discarded.
+ *   - queue order: ISL ascending (F descending), then the step that produced the
+ *     entry (steps done before it), then i, all ascending.  A full queue takes a new
+ *     entry only if it comes before its last entry, which it then drops; neighbours
+ *     are considered in that order, so the queue after a step holds the K first of
+ *     its old entries and the step's new ones.
+ *   - when the queue runs empty, or HT has no free slot for the new S, the walker
+ *     restarts from a fresh random S with HT and queue emptied; there is no other
+ *     restart rule (Alg. 1 has none).
+ *   - the best sequence is updated by every neighbour that enters the queue (a
+ *     neighbour that does not enter it cannot beat the best: the best is at least as
+ *     good as every queue entry).
+ * Trace codes, one per step: the low 16 bits of the new S's fingerprint, with bit 16
+ * set when the step ended in a restart after an HT overflow, or -1 when the queue ran
+ * empty (restart); the ISL trace holds the ISL of S at the end of the step. */
+typedef struct {
+    int64_t isl, born;
+    int32_t i;
+    uint64_t fp;
+    int8_t *s;
+} lo_pq_entry;
+
+typedef struct {
+    int32_t cap, size;
+    lo_pq_entry *e;
+} lo_pq;
+
+static int pq_before(const lo_pq_entry *a, const lo_pq_entry *b)
+{
+    if (a->isl != b->isl) return a->isl < b->isl;
+    if (a->born != b->born) return a->born < b->born;
+    return a->i < b->i;
+}
+
+static int32_t pq_extreme(const lo_pq *q, int want_last)
+{
+    int32_t k = 0;
+    for (int32_t j = 1; j < q->size; ++j) {
+        int b = pq_before(&q->e[j], &q->e[k]);
+        if (want_last ? !b : b) k = j;
+    }
+    return k;
+}
+
+/* removes entry k, keeping the storage of every entry */
+static void pq_remove(lo_pq *q, int32_t k)
+{
+    lo_pq_entry t = q->e[k];
+    q->e[k] = q->e[q->size - 1];
+    q->e[q->size - 1] = t;
+    q->size -= 1;
+}
+
+static void bf_note(lo_walker *w, const int8_t *s, int64_t isl, int64_t steps_done)
+{
+    if (isl < w->best_isl) {
+        w->best_isl = isl;
+        memcpy(w->s_best, s, (size_t)w->L);
+        w->res.best_step = steps_done;
+    }
+    if (w->res.target_step < 0 && target_met(w, isl)) w->res.target_step = steps_done;
+}
+
+/* One step (expansion of S); e = steps done before it.  Returns the trace code, or
+ * -99 on an internal mismatch. */
+static int32_t bf_step(lo_walker *w, lo_pq *q, int64_t e)
+{
+    int32_t L = w->L, n = w->n;
+    if (lo_neighbor_delta(w->s, L, w->delta) != 0) return -99;
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t j = i;
+        while (j > 0 && cmp_pair(w->delta, i, w->order[j - 1]) < 0) {
+            w->order[j] = w->order[j - 1];
+            --j;
+        }
+        w->order[j] = i;
+    }
+    for (int32_t t = 0; t < n; ++t) {
+        int32_t i = w->order[t];
+        lo_pq_entry c = {w->isl + w->delta[i], e, i, w->fp ^ w->zkey[i], NULL};
+        int32_t last = -1;
+        if (q->size == q->cap) {
+            last = pq_extreme(q, 1);
+            if (!pq_before(&c, &q->e[last])) break;  /* the rest come later still */
+        }
+        if (ht_contains(&w->ht, c.fp)) continue;
+        if (last >= 0) pq_remove(q, last);
+        lo_pq_entry *d = &q->e[q->size++];
+        c.s = d->s;
+        *d = c;
+        memcpy(d->s, w->s, (size_t)L);
+        int32_t m = L - 1 - i;
+        d->s[i] = (int8_t)(-d->s[i]);
+        if (m != i) d->s[m] = (int8_t)(-d->s[m]);
+        if (lo_isl(d->s, L) != d->isl) return -99;
+        bf_note(w, d->s, d->isl, e + 1);
+    }
+    for (;;) {
+        if (q->size == 0) {
+            restart(w, e + 1);
+            return -1;
+        }
+        int32_t k = pq_extreme(q, 0);
+        lo_pq_entry *d = &q->e[k];
+        if (ht_contains(&w->ht, d->fp)) {
+            pq_remove(q, k);
+            continue;
+        }
+        memcpy(w->s, d->s, (size_t)L);
+        w->isl = d->isl;
+        w->fp = d->fp;
+        pq_remove(q, k);
+        int32_t code = (int32_t)(w->fp & 0xFFFFu);
+        if (!ht_insert(&w->ht, w->fp)) {
+            w->res.overflows += 1;
+            q->size = 0;
+            restart(w, e + 1);
+            return code | LO_TRACE_RESTART;
+        }
+        return code;
+    }
+}
+
+static int run_bestfirst(lo_walk_job *job, int64_t w_idx)
+{
+    int32_t L = job->L, n = (L + 1) / 2, K = job->pq_size;
+    lo_walker w;
+    lo_pq q;
+    memset(&w, 0, sizeof(w));
+    memset(&q, 0, sizeof(q));
+    w.L = L;
+    w.n = n;
+    w.seed = job->seed;
+    w.g = (uint32_t)(job->g0 + w_idx);
+    w.cfg = job->cfg;
+    w.zkey = job->zkey;
+    w.x = (int8_t *)malloc((size_t)L);
+    w.s = (int8_t *)malloc((size_t)L);
+    w.s_best = (int8_t *)malloc((size_t)L);
+    w.delta = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    w.order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    w.ht.mask = (1ull << job->cfg->tabu_log2) - 1;
+    w.ht.cap = job->cfg->probe_cap;
+    if ((uint64_t)w.ht.cap > w.ht.mask + 1) w.ht.cap = (int32_t)(w.ht.mask + 1);
+    w.ht.slot = (uint64_t *)calloc((size_t)(w.ht.mask + 1), sizeof(uint64_t));
+    w.ht.gen = 1;
+    w.best_isl = INT64_MAX;
+    w.res.target_step = -1;
+    q.cap = K;
+    q.e = (lo_pq_entry *)calloc((size_t)K, sizeof(lo_pq_entry));
+    int8_t *store = (int8_t *)malloc((size_t)K * (size_t)L);
+    int rc = 0;
+    if (!w.x || !w.s || !w.s_best || !w.delta || !w.order || !w.ht.slot || !q.e || !store) {
+        rc = -3;
+        goto done;
+    }
+    for (int32_t k = 0; k < K; ++k) q.e[k].s = store + (size_t)k * (size_t)L;
+    start(&w, 0);
+    for (int64_t t = 0; t < job->steps; ++t) {
+        int32_t code = bf_step(&w, &q, t);
+        if (code == -99) {
+            rc = -2;
+            break;
+        }
+        if (code == -1 || (code & LO_TRACE_RESTART)) q.size = 0;
+        if (job->trace_code) {
+            job->trace_code[w_idx * job->steps + t] = code;
+            job->trace_isl[w_idx * job->steps + t] = (int32_t)w.isl;
+        }
+    }
+    w.res.final_isl = (int32_t)w.isl;
+    w.res.best_isl = (int32_t)w.best_isl;
+    job->res[w_idx] = w.res;
+    if (job->best_seq) memcpy(job->best_seq + w_idx * L, w.s_best, (size_t)L);
+    if (job->final_seq) memcpy(job->final_seq + w_idx * L, w.s, (size_t)L);
+done:
+    free(w.x); free(w.s); free(w.s_best); free(w.delta); free(w.order); free(w.ht.slot); free(q.e); free(store);
+    return rc;
+}
+
+/* Walkers g0 .. g0+count-1 of length L each take `steps` steps of the best-first
+ * search with a queue of pq_size entries (cfg->patience is not used); arguments and
+ * results as lo_walk. */
+int lo_bestfirst(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t steps, const lo_walk_cfg *cfg,
+                 int32_t pq_size, lo_walk_result *res, int8_t *best_seq, int8_t *final_seq, int32_t *trace_code,
+                 int32_t *trace_isl, int32_t nthreads)
+{
+    if (pq_size < 1) return -1;
+    return walk_many(L, seed, g0, count, steps, cfg, pq_size, res, best_seq, final_seq, trace_code, trace_isl,
+                     nthreads);
 }
 
 /* ------------------------------------------------- exhaustive skew enumeration */

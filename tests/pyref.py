@@ -168,3 +168,77 @@ def walk(L, seed, g, steps, tabu_log2=16, cap=32, patience=0):
         codes.append(code)
         isls.append(e)
     return codes, isls, st["best"], st["restarts"]
+
+
+def bestfirst(L, seed, g, steps, K, tabu_log2=16, cap=32):
+    """Algorithm 1 with a queue of K entries (the readings of the oracle's best-first
+    search); returns (trace_code, trace_isl, best_isl, restarts, overflows)."""
+    n = (L + 1) // 2
+    keys = [zkey(L, i) for i in range(n)]
+    ht = HT(tabu_log2, cap)
+    st = {"r": 0, "best": None, "restarts": 0, "overflows": 0}
+
+    def fp_of(s):
+        f = 0
+        for i in range(n):
+            if s[i] < 0:
+                f ^= keys[i]
+        return f
+
+    def begin():
+        s = skew(start_vars(seed, g, st["r"], L), L)
+        e = isl_np(s)
+        f = fp_of(s)
+        ht.insert(f)
+        if st["best"] is None or e < st["best"]:
+            st["best"] = e
+        return s, e, f
+
+    def again():
+        st["r"] += 1
+        st["restarts"] += 1
+        ht.new_generation()
+        return begin()
+
+    s, e, f = begin()
+    queue = []  # entries (isl, born, i, fp, state)
+    codes, isls = [], []
+    for t in range(steps):
+        cands = []
+        for i in range(n):
+            u = s.copy()
+            u[i] = -u[i]
+            if L - 1 - i != i:
+                u[L - 1 - i] = -u[L - 1 - i]
+            cands.append((isl_np(u), t, i, f ^ keys[i], u))
+        cands.sort(key=lambda c: c[:3])
+        for c in cands:
+            if len(queue) == K and c[:3] > max(q[:3] for q in queue):
+                break
+            if ht.contains(c[3]):
+                continue
+            if len(queue) == K:
+                queue.remove(max(queue, key=lambda q: q[:3]))
+            queue.append(c)
+            st["best"] = min(st["best"], c[0])
+        code = None
+        while queue:
+            top = min(queue, key=lambda q: q[:3])
+            queue.remove(top)
+            if ht.contains(top[3]):
+                continue
+            s, e, f = top[4], top[0], top[3]
+            code = f & 0xFFFF
+            if not ht.insert(f):
+                st["overflows"] += 1
+                queue = []
+                s, e, f = again()
+                code |= 0x10000
+            break
+        if code is None:
+            queue = []
+            s, e, f = again()
+            code = -1
+        codes.append(code)
+        isls.append(e)
+    return codes, isls, st["best"], st["restarts"], st["overflows"]

@@ -93,3 +93,61 @@ def test_stagnation_restart_interval():
             stag += 1
         assert stag < P
     assert saw_restart
+
+
+# ------------------------------------------------------ best-first search (Alg. 1)
+
+@pytest.mark.parametrize("L,steps,K,log2,cap", [(13, 300, 3, 16, 32), (21, 300, 32, 16, 32), (21, 400, 5, 4, 3),
+                                                (41, 200, 32, 16, 32), (5, 80, 2, 16, 32)])
+def test_bestfirst_matches_python_statement(L, steps, K, log2, cap):
+    """The queue rules (order, eviction of the last entry, discarding entries that
+    became S, restarts) against the Python statement, whose dISL is flip-and-recompute."""
+    seed = 2
+    out = oracle.bestfirst(L, seed, 3, steps, pq_size=K, tabu_log2=log2, probe_cap=cap, trace=True, nthreads=2)
+    for g in range(3):
+        codes, isls, best, restarts, overflows = pyref.bestfirst(L, seed, g, steps, K, log2, cap)
+        assert list(out["trace_code"][g]) == codes
+        assert list(out["trace_isl"][g]) == isls
+        assert out["best_isl"][g] == best
+        assert out["restarts"][g] == restarts and out["overflows"][g] == overflows
+
+
+@pytest.mark.parametrize("L", [21, 41, 61])
+def test_bestfirst_with_a_queue_of_one_is_the_walk(L):
+    """With K = 1 the queue holds only the best neighbour not in HT, which is what the
+    walk moves to: the two searches coincide when the walk never restarts on stagnation."""
+    a = oracle.walk(L, 3, 6, 1500, patience=1 << 30, trace=True)
+    b = oracle.bestfirst(L, 3, 6, 1500, pq_size=1, trace=True)
+    for k in ("trace_isl", "final_seq", "best_seq", "best_isl", "restarts", "overflows"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(a["trace_code"] == -1, b["trace_code"] == -1)
+
+
+def test_bestfirst_with_an_unbounded_queue_expands_every_state_once():
+    """L = 21 (2^11 skew states) with K >= 2^11: no entry is ever dropped, so every
+    state becomes S exactly once, the queue runs empty after step 2^11, and the best
+    found is the exhaustive optimum."""
+    L, n = 21, 11
+    opt = oracle.enumerate_skew(L)[0]
+    out = oracle.bestfirst(L, 5, 2, 2 ** n + 10, pq_size=4096, trace=True)
+    for g in range(2):
+        codes = out["trace_code"][g]
+        assert int(np.argmax(codes == -1)) + 1 == 2 ** n
+        assert (codes[: 2 ** n - 1] >= 0).all()
+        assert out["best_isl"][g] == opt
+        assert oracle.isl(out["best_seq"][g]) == opt
+
+
+def test_bestfirst_invariants_L201():
+    L, steps = 201, 300
+    a = oracle.bestfirst(L, 7, 4, steps, pq_size=32, trace=True, nthreads=4)
+    b = oracle.bestfirst(L, 7, 4, steps, pq_size=32, trace=True, nthreads=1)
+    n = (L + 1) // 2
+    for k in ("trace_code", "trace_isl", "best_isl", "final_isl", "best_seq"):
+        assert np.array_equal(a[k], b[k])
+    for g in range(4):
+        assert a["best_isl"][g] <= a["trace_isl"][g].min()
+        assert oracle.isl(a["best_seq"][g]) == a["best_isl"][g]
+        assert oracle.isl(a["final_seq"][g]) == a["final_isl"][g] == a["trace_isl"][g][-1]
+        assert (a["trace_isl"][g] % 8 == (n - 1) % 8).all()
+        assert (oracle.fingerprint(a["final_seq"][g]) & 0xFFFF) == a["trace_code"][g][-1]
