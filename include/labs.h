@@ -49,9 +49,12 @@ extern "C" {
 #define LABS_MAX_L 511       /* n = (L+1)/2 <= 256 free variables */
 #define LABS_MAX_GROUPS 64   /* distinct lengths in one context */
 
-/* Step trace codes written by labs_trace (one int32 per walker step). */
-#define LABS_TRACE_RESTART 0x10000 /* OR-ed into the flipped index: the step ended in a restart */
-#define LABS_TRACE_BLOCKED (-1)    /* every neighbour was already visited: restart, no move */
+/* Step trace codes written by labs_trace (one int32 per walker step).  The walk writes
+ * the flipped free variable i; the best-first search the low 16 bits of the new S's
+ * fingerprint (the XOR of its Zobrist keys). */
+#define LABS_TRACE_RESTART 0x10000 /* OR-ed into the code: the step ended in a restart */
+#define LABS_TRACE_BLOCKED (-1)    /* no admissible next state (every neighbour visited, or
+                                      an empty best-first queue): restart */
 
 typedef struct labs_ctx labs_ctx;
 
@@ -74,6 +77,12 @@ typedef struct labs_config {
 #define LABS_FLAG_LEARNED 4      /* reserve workspace for the learned mode (labs_learned) */
 #define LABS_FLAG_WARP_PER_WALKER 8 /* one walker per warp even where two per warp fit */
 #define LABS_FLAG_TWO_PER_WARP 16   /* at most two walkers per warp even where four fit */
+#define LABS_FLAG_BEST_FIRST 32     /* labs_walk runs Algorithm 1 as printed: best-first
+                                       search with a queue of LABS_QUEUE_SIZE evaluated
+                                       neighbours per walker (see labs_walk); one walker per
+                                       warp; not with LABS_FLAG_LEARNED, no checkpoints */
+#define LABS_QUEUE_SIZE 32           /* entries of a walker's best-first queue */
+#define LABS_BEST_FIRST_MAX_STEPS (1ll << 28) /* steps per walker the queue order can number */
 
 /* Counters of a context, summed over its walkers (labs_stats). */
 typedef struct labs_counters {
@@ -146,12 +155,21 @@ int labs_neighbor_delta(labs_ctx *ctx, const int8_t *dev_seqs, int64_t batch,
                         int32_t *dev_delta_out);
 
 /* Advances every walker by `steps` steps of the walk (Algorithm 1, self-avoiding
- * form; the step rule is stated here and implemented in csrc/labs_kernels.cu):
+ * form; the step rule is stated here and implemented in csrc/labs_device.cuh):
  *   evaluate all n flips; take the flip with the lowest dISL whose result is not in
  *   the walker's HT (ties to the lowest i); move there and insert it into HT; keep
  *   the best sequence (strictly lower ISL); restart from a new random sequence with
  *   an empty HT after `patience` steps without a new best since the last restart,
  *   when every neighbour is in HT, or when HT has no free slot for the new state.
+ * With LABS_FLAG_BEST_FIRST a step is Algorithm 1 as printed (impxLast, Section 3):
+ *   evaluate all n flips of S; every neighbour not in HT enters the walker's queue,
+ *   ordered by (ISL, step that produced it, i) ascending, while it comes before the
+ *   queue's last entry or the queue has a free place (a full queue drops its last
+ *   entry); then S becomes the queue's first entry that is not in HT by now (entries
+ *   that are get dropped) and is inserted into HT.  The best sequence is kept as in
+ *   the walk; the walker restarts (HT and queue emptied) when the queue runs empty or
+ *   HT has no free slot for the new S; `patience` is not used.  At most
+ *   LABS_BEST_FIRST_MAX_STEPS steps per walker (LABS_EINVAL beyond).
  * The trajectory of a walker depends only on (seed, walker id, L, cfg), never on
  * chunking, launch shape or the other walkers. */
 int labs_walk(labs_ctx *ctx, int64_t steps);
@@ -287,7 +305,8 @@ int labs_trace_learned(labs_ctx *ctx, int32_t capacity, float *dev_scores, int64
 /* Checkpoint of every walker's state (sequence, ISL, best, counters, random-stream
  * position) and, with with_tabu != 0, its HT.  With the HT included a restored run
  * continues bit-identically; without it the HT restarts empty.  host_buf NULL queries
- * the size.  Synchronising. */
+ * the size.  Synchronising.  LABS_EINVAL for a context with LABS_FLAG_BEST_FIRST (its
+ * queues are not part of the checkpoint). */
 int labs_checkpoint(labs_ctx *ctx, int with_tabu, void *host_buf, size_t *bytes);
 int labs_restore(labs_ctx *ctx, const void *host_buf, size_t bytes);
 

@@ -27,6 +27,9 @@ LABS_FLAG_CHECK_STATE = 2
 LABS_FLAG_LEARNED = 4
 LABS_FLAG_WARP_PER_WALKER = 8
 LABS_FLAG_TWO_PER_WARP = 16
+LABS_FLAG_BEST_FIRST = 32
+LABS_QUEUE_SIZE = 32
+LABS_BEST_FIRST_MAX_STEPS = 1 << 28
 LOG_RECORD_BYTES = 64
 
 ERRORS = {LABS_EINVAL: "EINVAL", LABS_ENOMEM: "ENOMEM", LABS_ECUDA: "ECUDA", LABS_ETIMEOUT: "ETIMEOUT",

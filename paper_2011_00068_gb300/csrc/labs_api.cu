@@ -32,7 +32,7 @@ struct labs_ctx {
     // workspace layout (byte offsets)
     size_t off_status = 0, off_groups = 0, off_zkeys = 0, off_states = 0, off_trace_start = 0,
            off_trace_ids = 0, off_queue = 0, off_l_scores = 0, off_l_step = 0, off_l_slot = 0, off_l_valid = 0,
-           off_tabu = 0, total = 0;
+           off_pq_key = 0, off_pq_bits = 0, off_tabu = 0, total = 0;
     // device pointers kept in the status block (restored after every reset)
     labs_log_record* log = nullptr;
     int64_t log_capacity = 0, log_start = 0;
@@ -123,6 +123,9 @@ KParams params(labs_ctx* c)
     p.rmax = lanes_for(c->n_max, c->tile);
     p.tile = c->tile;
     p.seed = c->seed;
+    p.best_first = (c->cfg.flags & LABS_FLAG_BEST_FIRST) ? 1 : 0;
+    p.pq_key = p.best_first ? at<uint64_t>(c, c->off_pq_key) : nullptr;
+    p.pq_bits = p.best_first ? at<uint32_t>(c, c->off_pq_bits) : nullptr;
     return p;
 }
 
@@ -178,6 +181,8 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     if (k.patience < 0 || k.chunk_steps < 0 || k.warps_per_cta < 0 || k.warps_per_cta > 8)
         return fail(c, LABS_EINVAL, "bad patience / chunk_steps / warps_per_cta (0..8)");
     if (nL < 1 || nL > LABS_MAX_GROUPS) return fail(c, LABS_EINVAL, "need 1..%d lengths", LABS_MAX_GROUPS);
+    if ((k.flags & LABS_FLAG_BEST_FIRST) && (k.flags & LABS_FLAG_LEARNED))
+        return fail(c, LABS_EINVAL, "LABS_FLAG_BEST_FIRST and LABS_FLAG_LEARNED do not combine");
     c->seed = seed;
     c->stream = (cudaStream_t)stream;
     c->nG = nL;
@@ -227,6 +232,12 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
         c->off_l_valid = off;
         off = align_up(off + sizeof(int32_t) * (size_t)c->W, 256);
     }
+    if (k.flags & LABS_FLAG_BEST_FIRST) {
+        c->off_pq_key = off;
+        off = align_up(off + sizeof(uint64_t) * LABS_QUEUE_SIZE * (size_t)c->W, 256);
+        c->off_pq_bits = off;
+        off = align_up(off + sizeof(uint32_t) * kBitWords * LABS_QUEUE_SIZE * (size_t)c->W, 256);
+    }
     c->off_tabu = off;
     off = align_up(off + sizeof(uint64_t) * ((size_t)c->W << k.tabu_log2), 256);
     c->total = off;
@@ -235,7 +246,8 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     // than two per warp there, equal from n = 88 to 104), two walkers per warp (16 lanes
     // each) up to 10 outputs per lane (n <= 160), else one walker per warp (the learned
     // mode runs one walker per warp)
-    if ((k.flags & (LABS_FLAG_WARP_PER_WALKER | LABS_FLAG_LEARNED)) || lanes_for(c->n_max, 16) > 10)
+    if ((k.flags & (LABS_FLAG_WARP_PER_WALKER | LABS_FLAG_LEARNED | LABS_FLAG_BEST_FIRST)) ||
+        lanes_for(c->n_max, 16) > 10)
         c->tile = 32;
     else if (!(k.flags & LABS_FLAG_TWO_PER_WARP) && lanes_for(c->n_max, 8) <= kQuadMaxR)
         c->tile = 8;
@@ -524,6 +536,8 @@ int labs_walk(labs_ctx* c, int64_t steps)
     int rc = need_ws(c);
     if (rc) return rc;
     if (steps < 0) return fail(c, LABS_EINVAL, "negative steps");
+    if ((c->cfg.flags & LABS_FLAG_BEST_FIRST) && c->planned + steps > LABS_BEST_FIRST_MAX_STEPS)
+        return fail(c, LABS_EINVAL, "best-first search: at most %lld steps per walker", LABS_BEST_FIRST_MAX_STEPS);
     if ((steps == 0 && !c->catch_up) || c->W == 0) return LABS_OK;
     cudaSetDevice(c->device);
     const KParams p = params(c);
@@ -802,6 +816,7 @@ int labs_checkpoint(labs_ctx* c, int with_tabu, void* host_buf, size_t* bytes)
 {
     int rc = need_ws(c);
     if (rc) return rc;
+    if (c->cfg.flags & LABS_FLAG_BEST_FIRST) return fail(c, LABS_EINVAL, "no checkpoints of a best-first search");
     if (!bytes) return fail(c, LABS_EINVAL, "null size");
     const size_t hdr = 64;
     const size_t sbytes = sizeof(WalkerState) * (size_t)c->W;
@@ -830,6 +845,7 @@ int labs_restore(labs_ctx* c, const void* host_buf, size_t bytes)
 {
     int rc = need_ws(c);
     if (rc) return rc;
+    if (c->cfg.flags & LABS_FLAG_BEST_FIRST) return fail(c, LABS_EINVAL, "no checkpoints of a best-first search");
     if (!host_buf || bytes < 64) return fail(c, LABS_EINVAL, "bad checkpoint");
     uint64_t h[8];
     memcpy(h, host_buf, sizeof(h));

@@ -1067,6 +1067,86 @@ __device__ __forceinline__ Probe lockstep_probe_full(const WalkEnv& env, uint64_
     return pr;
 }
 
+// Flips free variable best_i (and its mirror) in the walker's rows, even-lag table and
+// P, all from the values before the flip, when `moves` (the lanes of a walker without a
+// move rewrite unchanged values).  The rows are padded so that no read or write needs a
+// bounds test (four walkers per warp: reads of s_{i+2m} stay inside the class and the
+// mirror half of the table is kept only as deep as the Toeplitz window reads).
+template <class LG, int R>
+__device__ __forceinline__ void apply_flip(const View& V, int n, const Outs<LG, R>& o, int lane, bool moves,
+                                           int best_i, float (&P)[R])
+{
+    constexpr bool kQuad = LG::kSize == 8;
+    const int c = n - 1;
+    const int m0 = 1 + lane * R;  // this lane's lags 2m of the update, m = m0 .. m0+R-1
+    const int pb = best_i & 1, vb = best_i >> 1;
+    float* Ab = pb ? V.A1 : V.A0;
+    const bool centre = best_i == c;
+    const int vq = centre ? vb : n - 1 - vb - pb;
+    const float as = Ab[vb], aq = centre ? 0.f : Ab[vq];
+    __syncwarp();
+    // The flipped entries read as 0 while the changes are taken: that drops the pairs
+    // whose two ends both flip (unchanged) and the lag-0 terms from every sum below.
+    if (moves && lane == 0) {
+        Ab[vb] = 0.f;
+        Ab[vq] = 0.f;
+    }
+    __syncwarp();
+    // dC_{2m} = -4 s_i (s_{i+2m} + s_{i-2m}) (centre: -2 s_c (..)) for this lane's m
+    const float coef = moves ? (centre ? -2.f : -4.f) * as : 0.f;
+    float dd[R];
+    {
+        const float* up = Ab + vb + m0;
+        const float* dn = Ab + vb - m0;
+        const int ku = kQuad ? (pb ? n - 1 : n) - vb - m0 : R;  // s_{i+2m} inside the class for k < ku
+#pragma unroll
+        for (int k = 0; k < R; ++k) dd[k] = coef * ((k < ku ? up[k] : 0.f) + dn[-k]);
+    }
+    // P_v of the moved class: each pair (v+m, v-m) with exactly one flipped end
+    // changes by -2 x its old product; the partner of w is 2v - w
+    {
+        const float g = (moves && o.p == pb) ? -2.f : 0.f;
+        const float* B1 = Ab + 2 * o.v0 - vb;
+        const float* B2 = Ab + 2 * o.v0 - vq;
+#pragma unroll
+        for (int r = 0; r < R; ++r) P[r] = fmaf(g, fmaf(aq, B2[2 * r], as * B1[2 * r]), P[r]);
+    }
+    {
+        // E[m] += dd for this lane's m, in the pairs G[y] = (E[y], E[y+1]) and their
+        // mirrors at -y (pairs shared with a neighbour lane are written field by field)
+        float e[R + 1];
+        e[R] = 0.f;
+#pragma unroll
+        for (int k = 0; k < R; k += 2) {
+            const float2 g = V.G[m0 + k];
+            e[k] = g.x + dd[k];
+            if (k + 1 < R) e[k + 1] = g.y + dd[k + 1];
+        }
+        V.G[m0 - 1].y = e[0];
+#pragma unroll
+        for (int k = 0; k + 1 < R; ++k) V.G[m0 + k] = make_float2(e[k], e[k + 1]);
+        V.G[m0 + R - 1].x = e[R - 1];
+        if (!kQuad || m0 + R <= V.gpad) {
+            V.G[-m0].x = e[0];
+#pragma unroll
+            for (int k = 0; k + 1 < R; ++k) V.G[-m0 - k - 1] = make_float2(e[k + 1], e[k]);
+            V.G[-m0 - R].y = e[R - 1];
+        }
+    }
+    __syncwarp();
+    if (moves && lane == 0) {
+        Ab[vb] = -as;
+        if (!centre) Ab[vq] = -aq;
+    }
+}
+
+// ISL at or below which the target merit factor is met (-1: no target).
+__device__ __forceinline__ int target_isl(const KParams& p, int L)
+{
+    if (p.target_num <= 0 || p.target_den <= 0) return -1;
+    return (int)min((int64_t)INT_MAX, (int64_t)p.target_den * L * L / (2 * (int64_t)p.target_num));
+}
+
 // Outcome of probing HT for a candidate.
 enum : int { kProbeFree = 0, kProbeVisited = 1, kProbeUnknown = 2, kProbeNone = 3 };
 
@@ -1077,17 +1157,13 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
 {
     constexpr int S = LG::kSize / 2;            // HT slots probed per candidate in a round
     constexpr unsigned SM = (1u << S) - 1u;
-    constexpr bool kQuad = LG::kSize == 8;      // rows and G less padded (warp_smem)
     const KParams& p = *env.p;
-    const int lane = t.lane, n = env.n, c = n - 1;
+    const int lane = t.lane, n = env.n;
     const Outs<LG, R> o(t);
     const int cap = p.probe_cap;
     const uint32_t tmask = (uint32_t)env.tmask;  // HT slots <= 2^20
     // ISL at or below which the target merit factor is met (-1: no target)
-    const int tisl = (p.target_num <= 0 || p.target_den <= 0)
-                         ? -1
-                         : (int)min((int64_t)INT_MAX, (int64_t)p.target_den * env.L * env.L / (2 * (int64_t)p.target_num));
-    const int m0 = 1 + lane * R;  // this lane's lags 2m of the table update, m = m0 .. m0+R-1
+    const int tisl = target_isl(p, env.L);
     float P[R];
     p_direct(V, n, o, P);
     const int64_t first_step = w.steps;
@@ -1185,70 +1261,10 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
             }
         } while (__any_sync(kFull, !done));
 
-        // Apply the move (walkers that have one), from the values before the flip.  The
-        // walker's rows are padded so that no read or write below needs a bounds test;
-        // lanes of a walker without a move rewrite unchanged values.
+        // Apply the move (walkers that have one), from the values before the flip.
         const bool moves = act && kc != 0xFFFFFFFFu;
         const int best_i = moves ? (int)(kc & 0xFFu) : 0, best_d = (int)(kc >> 8) - (1 << 23);
-        const int pb = best_i & 1, vb = best_i >> 1;
-        float* Ab = pb ? V.A1 : V.A0;
-        const bool centre = best_i == c;
-        const int vq = centre ? vb : n - 1 - vb - pb;
-        const float as = Ab[vb], aq = centre ? 0.f : Ab[vq];
-        __syncwarp();
-        // The flipped entries read as 0 while the changes are taken: that drops the pairs
-        // whose two ends both flip (unchanged) and the lag-0 terms from every sum below.
-        if (moves && lane == 0) {
-            Ab[vb] = 0.f;
-            Ab[vq] = 0.f;
-        }
-        __syncwarp();
-        // dC_{2m} = -4 s_i (s_{i+2m} + s_{i-2m}) (centre: -2 s_c (..)) for this lane's m
-        const float coef = moves ? (centre ? -2.f : -4.f) * as : 0.f;
-        float dd[R];
-        {
-            const float* up = Ab + vb + m0;
-            const float* dn = Ab + vb - m0;
-            const int ku = kQuad ? (pb ? n - 1 : n) - vb - m0 : R;  // s_{i+2m} inside the class for k < ku
-#pragma unroll
-            for (int k = 0; k < R; ++k) dd[k] = coef * ((k < ku ? up[k] : 0.f) + dn[-k]);
-        }
-        // P_v of the moved class: each pair (v+m, v-m) with exactly one flipped end
-        // changes by -2 x its old product; the partner of w is 2v - w
-        {
-            const float g = (moves && o.p == pb) ? -2.f : 0.f;
-            const float* B1 = Ab + 2 * o.v0 - vb;
-            const float* B2 = Ab + 2 * o.v0 - vq;
-#pragma unroll
-            for (int r = 0; r < R; ++r) P[r] = fmaf(g, fmaf(aq, B2[2 * r], as * B1[2 * r]), P[r]);
-        }
-        {
-            // E[m] += dd for this lane's m, in the pairs G[y] = (E[y], E[y+1]) and their
-            // mirrors at -y (pairs shared with a neighbour lane are written field by field)
-            float e[R + 1];
-            e[R] = 0.f;
-#pragma unroll
-            for (int k = 0; k < R; k += 2) {
-                const float2 g = V.G[m0 + k];
-                e[k] = g.x + dd[k];
-                if (k + 1 < R) e[k + 1] = g.y + dd[k + 1];
-            }
-            V.G[m0 - 1].y = e[0];
-#pragma unroll
-            for (int k = 0; k + 1 < R; ++k) V.G[m0 + k] = make_float2(e[k], e[k + 1]);
-            V.G[m0 + R - 1].x = e[R - 1];
-            if (!kQuad || m0 + R <= V.gpad) {
-                V.G[-m0].x = e[0];
-#pragma unroll
-                for (int k = 0; k + 1 < R; ++k) V.G[-m0 - k - 1] = make_float2(e[k + 1], e[k]);
-                V.G[-m0 - R].y = e[R - 1];
-            }
-        }
-        __syncwarp();
-        if (moves && lane == 0) {
-            Ab[vb] = -as;
-            if (!centre) Ab[vq] = -aq;
-        }
+        apply_flip<LG, R>(V, n, o, lane, moves, best_i, P);
         const bool stored = slot >= 0;
         if (moves && lane == 0 && stored) env.T[slot] = (fnew & ~kGenMask) | w.gen;
         if (moves && lane == (best_i >> 5)) w.word ^= 1u << (best_i & 31);
@@ -1308,6 +1324,153 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
         rec->first = log_first;
         rec->min_isl = log_min;
     }
+}
+
+// ------------------------------------------------------------- best-first search
+//
+// Algorithm 1 as printed (impxLast, Section 3): the neighbourhood of S fills a queue
+// of LABS_QUEUE_SIZE evaluated neighbours ordered by merit factor and the next S is the
+// queue's first entry (the readings are stated with labs_walk in labs.h).  One walker
+// per warp; lane l holds queue entry l as a 64-bit key
+//   ISL << 36 | (steps done before the step that produced it) << 8 | i
+// (ascending = the queue order; ~0 = empty) and the entry's free variables live in
+// global memory.  An entry produced by the current step is a neighbour of S and is
+// applied incrementally; an older one rebuilds the rows and the table from its bits.
+
+__device__ __forceinline__ uint64_t warp_min64(uint64_t v)
+{
+    const unsigned hi = __reduce_min_sync(kFull, (unsigned)(v >> 32));
+    const unsigned lo = __reduce_min_sync(kFull, (unsigned)(v >> 32) == hi ? (unsigned)v : 0xFFFFFFFFu);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+__device__ __forceinline__ uint64_t warp_max64(uint64_t v)
+{
+    const unsigned hi = __reduce_max_sync(kFull, (unsigned)(v >> 32));
+    const unsigned lo = __reduce_max_sync(kFull, (unsigned)(v >> 32) == hi ? (unsigned)v : 0u);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+template <int R>
+__device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int* base, const WarpSmem& SL,
+                               const View& V, int trace_slot, int64_t trace_start, const Tile<32>& t, uint64_t* qkey,
+                               uint32_t* qbits)
+{
+    static_assert(LABS_QUEUE_SIZE == 32, "one queue entry per lane");
+    const KParams& p = *env.p;
+    const int lane = t.lane, n = env.n;
+    const Outs<Tile<32>, R> o(t);
+    const int cap = p.probe_cap;
+    const int tisl = target_isl(p, env.L);
+    uint64_t qk = qkey[lane];
+    float P[R];
+    p_direct(V, n, o, P);
+    StopCheck stop;
+    stop.start(p, lane == 0);
+    while (w.steps < until) {
+        if ((w.steps & (kCheckEvery - 1)) == 0) {
+            const int why = t.shfl(stop.poll(p, lane == 0), 0);
+            if (why) {
+                if (lane == 0) raise_error(p.status, why, (int)env.g);
+                break;
+            }
+        }
+        const int64_t e = w.steps;
+        unsigned key[R];
+        {
+            float X[R];
+            toeplitz(V, n, o, X);
+            lane_keys(V, n, o, X, P, key);
+        }
+        // Neighbours in queue order (ISL, then i: the packed keys' order) while they
+        // come before the queue's last entry or the queue has a free place.
+        unsigned floor = 0u;
+        for (;;) {
+            unsigned b = 0xFFFFFFFFu;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (key[r] > floor) b = min(b, key[r]);
+            const unsigned k = t.rminu(b);
+            if (k == 0xFFFFFFFFu) break;
+            floor = k;
+            const int i = (int)(k & 0xFFu);
+            const int isl_f = w.isl + (int)(k >> 8) - (1 << 23);
+            const uint64_t ck = ((uint64_t)isl_f << 36) | ((uint64_t)e << 8) | (uint64_t)i;
+            const unsigned empty = t.ballot(qk == ~0ull);
+            int dst;
+            if (empty) {
+                dst = __ffs(empty) - 1;
+            } else {
+                const uint64_t last = warp_max64(qk);
+                if (ck > last) break;  // every later neighbour comes after it too
+                dst = __ffs(t.ballot(qk == last)) - 1;
+            }
+            const uint64_t f = w.fp ^ __ldg(env.zk + i);
+            if (probe_full(env, f, w.gen, cap, t).visited) continue;
+            if (lane == dst) qk = ck;
+            const uint32_t word = w.word ^ (lane == (i >> 5) ? 1u << (i & 31) : 0u);
+            if (lane < kBitWords) qbits[dst * kBitWords + lane] = word;
+            if (isl_f < w.best_isl) {
+                w.best_isl = isl_f;
+                w.best_step = e + 1;
+                if (lane < kBitWords) env.st->best[lane] = word;
+            }
+            if (w.target_step < 0 && isl_f <= tisl) w.target_step = e + 1;
+        }
+        t.sync();
+        // S <- the queue's first entry not in HT (entries that are get dropped)
+        int code = LABS_TRACE_BLOCKED;
+        bool again = true;
+        for (;;) {
+            if (!t.ballot(qk != ~0ull)) {
+                w.blocked += 1;  // empty queue: restart
+                break;
+            }
+            const uint64_t first = warp_min64(qk);
+            const int src = __ffs(t.ballot(qk == first)) - 1;
+            const uint32_t word = lane < kBitWords ? qbits[src * kBitWords + lane] : 0u;
+            if (lane == src) qk = ~0ull;
+            const int i = (int)(first & 0xFFu);
+            const bool nb = ((first >> 8) & 0xFFFFFFFull) == (uint64_t)e;  // a neighbour of S
+            const uint64_t f = nb ? (w.fp ^ __ldg(env.zk + i)) : fingerprint_all(word, env.zk, n, t);
+            const Probe pr = probe_full(env, f, w.gen, cap, t);
+            if (pr.visited) continue;
+            if (nb) {
+                apply_flip<Tile<32>, R>(V, n, o, lane, true, i, P);
+                t.sync();
+            } else {
+                load_rows(base, SL, V, word, env.L, n, t);
+                p_direct(V, n, o, P);
+            }
+            w.word = word;
+            w.isl = (int)(first >> 36);
+            w.fp = f;
+            code = (int)(f & 0xFFFFu);
+            if (pr.slot >= 0) {
+                if (lane == 0) env.T[pr.slot] = (f & ~kGenMask) | w.gen;
+                again = false;
+            } else {
+                w.overflows += 1;  // no free HT slot for the new S: restart
+                code |= LABS_TRACE_RESTART;
+            }
+            break;
+        }
+        w.steps += 1;
+        if (again) {
+            qk = ~0ull;
+            restart_walker(env, w, base, SL, V, t);
+            p_direct(V, n, o, P);
+        }
+        t.sync();
+        if (trace_slot >= 0 && lane == 0) {
+            const int64_t s = w.steps - 1 - trace_start;
+            if (s >= 0 && s < p.status->trace_capacity) {
+                p.status->trace_code[trace_slot * p.status->trace_capacity + s] = code;
+                p.status->trace_isl[trace_slot * p.status->trace_capacity + s] = w.isl;
+            }
+        }
+    }
+    qkey[lane] = qk;
 }
 
 // One launch advances every walker by up to chunk_steps steps toward the target.  The
@@ -1393,10 +1556,18 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(K
                 if (idx < S->log_capacity) ex.rec = S->log + idx;
             }
         }
-        // the learned mode's step (walk_steps) or the lockstep step of the plain walk
+        // the learned mode's step (walk_steps), the best-first search, or the lockstep
+        // step of the plain walk
         constexpr int R2 = RMAX > 2 ? RMAX - 2 : 1;
         const bool full = RMAX <= 2 || block_R(G.n, TILE) >= RMAX;
-        if (S->learned) {
+        if (p.best_first) {
+            uint64_t* qk = p.pq_key + wi * LABS_QUEUE_SIZE;
+            uint32_t* qb = p.pq_bits + wi * LABS_QUEUE_SIZE * kBitWords;
+            if (full)
+                walk_bestfirst<RMAX>(env, w, until, base, SL, V, trace_slot, trace_start, t, qk, qb);
+            else
+                walk_bestfirst<R2>(env, w, until, base, SL, V, trace_slot, trace_start, t, qk, qb);
+        } else if (S->learned) {
             if (full)
                 walk_steps<Tile<TILE>, RMAX>(env, w, until, base, SL, V, trace_slot, trace_start, ex, t);
             else

@@ -115,7 +115,10 @@ struct KParams {
     int32_t target_num, target_den;
     int32_t chunk_steps;
     int32_t rmax;             // lane block of the walk kernel instantiation (block_R(n_max, tile))
-    int32_t tile;             // lanes per walker: 32, or 16 (two walkers per warp)
+    int32_t tile;             // lanes per walker: 32, 16 (two walkers per warp) or 8 (four)
+    int32_t best_first;       // 1: best-first search (one walker per warp, queue below)
+    uint64_t* pq_key;         // [W][LABS_QUEUE_SIZE] queue keys, ~0 = empty
+    uint32_t* pq_bits;        // [W][LABS_QUEUE_SIZE][kBitWords] queue entries' free variables
     uint64_t seed;
 };
 

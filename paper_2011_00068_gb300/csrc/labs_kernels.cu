@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(512) reset_kernel(KParams p)
         w.target_step = -1;
         start_walker(env, w, base, SL, V, t);
         save_walker(st, w, t.lane);
+        if (p.best_first) p.pq_key[wi * LABS_QUEUE_SIZE + t.lane] = ~0ull;  // empty queue
         if (t.lane == 0) {
             st->group = gidx;
             st->trace_slot = -1;
