@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-delta", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--config", choices=["walk", "learned"], default="walk")
+    ap.add_argument("--search", choices=["walk", "bestfirst"], default="walk",
+                    help="walk: the self-avoiding walk; bestfirst: Algorithm 1 as printed (queue of 32)")
     ap.add_argument("--learned-L", type=int, default=255)
     ap.add_argument("--learned-walkers", type=int, default=32768)
     ap.add_argument("--learned-steps", type=int, default=20000)
@@ -151,7 +153,11 @@ def cpu_baseline(args):
 
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    oracle.walk(args.L, args.seed, args.cpu_walkers, args.cpu_steps, tabu_log2=args.tabu_log2, nthreads=cores)
+    if args.search == "bestfirst":
+        oracle.bestfirst(args.L, args.seed, args.cpu_walkers, args.cpu_steps, tabu_log2=args.tabu_log2,
+                         nthreads=cores)
+    else:
+        oracle.walk(args.L, args.seed, args.cpu_walkers, args.cpu_steps, tabu_log2=args.tabu_log2, nthreads=cores)
     dt = time.perf_counter() - t0
     n = (args.L + 1) // 2
     flips = args.cpu_walkers * args.cpu_steps * n
@@ -161,8 +167,10 @@ def cpu_baseline(args):
 
 
 def config_of(args, world):
-    return {"workload": "L=%d skew-symmetric self-avoiding walk, %d walkers/GPU x %d steps, HT 2^%d slots/walker, "
-                        "uniform random +-1 Philox starts, seed %d" % (args.L, args.walkers, args.walk_steps,
+    what = ("best-first search (Algorithm 1, queue of 32)" if args.search == "bestfirst"
+            else "self-avoiding walk")
+    return {"workload": "L=%d skew-symmetric %s, %d walkers/GPU x %d steps, HT 2^%d slots/walker, "
+                        "uniform random +-1 Philox starts, seed %d" % (args.L, what, args.walkers, args.walk_steps,
                                                                       args.tabu_log2, args.seed),
             "L": args.L, "walkers_per_gpu": args.walkers, "walk_steps": args.walk_steps,
             "tabu_slots_per_walker": 1 << args.tabu_log2,
@@ -184,7 +192,10 @@ def run_reference(args):
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.walk(args.L, args.seed, args.cpu_walkers, steps, tabu_log2=args.tabu_log2, nthreads=cores)
+        if args.search == "bestfirst":
+            oracle.bestfirst(args.L, args.seed, args.cpu_walkers, steps, tabu_log2=args.tabu_log2, nthreads=cores)
+        else:
+            oracle.walk(args.L, args.seed, args.cpu_walkers, steps, tabu_log2=args.tabu_log2, nthreads=cores)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
@@ -263,12 +274,16 @@ def run_ours(args):
 
     seed = replicas.rank_seed(args.seed, rank)
     shape = {}
+    from paper_2011_00068_gb300 import _native
+
+    flags = _native.LABS_FLAG_BEST_FIRST if args.search == "bestfirst" else 0
     if not args.no_tune:
         from paper_2011_00068_gb300 import tune
 
-        best = tune.tune(args.L, args.walkers, tabu_log2=args.tabu_log2, device=dev)
+        best = tune.tune(args.L, args.walkers, tabu_log2=args.tabu_log2, device=dev, flags=flags)
         shape = {"warps_per_cta": best["warps_per_cta"], "chunk_steps": best["chunk_steps"]}
-    s = labs.Search(args.L, args.walkers, seed, device=dev, stream=stream, tabu_log2=args.tabu_log2, **shape)
+    s = labs.Search(args.L, args.walkers, seed, device=dev, stream=stream, tabu_log2=args.tabu_log2, flags=flags,
+                    **shape)
     chunk = int(s.cfg.chunk_steps) or 1024
     nchunks = -(-args.walk_steps // chunk)
 
@@ -319,7 +334,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": (DRAM_BYTES_PER_WALKER_STEP * steps_per_launch
-                            if args.L == 201 and DRAM_BYTES_PER_WALKER_STEP else None),
+                            if args.L == 201 and args.search == "walk" and DRAM_BYTES_PER_WALKER_STEP else None),
                 "traffic_note": ("bytes per launch: %.1f B per walker step from one ncu capture of a small "
                                  "launch, scaled by walker steps" % DRAM_BYTES_PER_WALKER_STEP
                                  if DRAM_BYTES_PER_WALKER_STEP else "not captured for this kernel version"),

@@ -1383,13 +1383,48 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
             lane_keys(V, n, o, X, P, key);
         }
         // Neighbours in queue order (ISL, then i: the packed keys' order) while they
-        // come before the queue's last entry or the queue has a free place.
+        // come before the queue's last entry or the queue has a free place.  The queue's
+        // last entry only moves forward during the step, so the neighbours after its
+        // value at the start cannot enter: the others are looked up in HT all at once
+        // (each lane its own, home slots first), then inserted in order.
+        const bool full0 = t.ballot(qk == ~0ull) == 0u;
+        const uint64_t last0 = full0 ? warp_max64(qk) : ~0ull;
+        bool fresh[R];  // candidate r: not in HT, before last0
+        {
+            uint64_t fr[R], er[R];
+            const uint64_t gen = w.gen;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const unsigned k = key[r];
+                const int i = (int)(k & 0xFFu);
+                const uint64_t ck = ((uint64_t)(w.isl + (int)(k >> 8) - (1 << 23)) << 36) | ((uint64_t)e << 8) |
+                                    (uint64_t)i;
+                fresh[r] = k != 0xFFFFFFFFu && ck < last0;
+                fr[r] = fresh[r] ? w.fp ^ __ldg(env.zk + i) : 0ull;
+                er[r] = fresh[r] ? env.T[fr[r] & env.tmask] : 0ull;
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (!fresh[r]) continue;
+                const uint64_t tag = (fr[r] & ~kGenMask) | gen;
+                uint64_t x = er[r];
+                for (int sl = 1;; ++sl) {
+                    if ((x & kGenMask) != gen) break;  // free slot: not in HT
+                    if (x == tag) {
+                        fresh[r] = false;
+                        break;
+                    }
+                    if (sl >= cap) break;  // chain full within the cap: not found
+                    x = env.T[(fr[r] + (uint64_t)sl) & env.tmask];
+                }
+            }
+        }
         unsigned floor = 0u;
         for (;;) {
             unsigned b = 0xFFFFFFFFu;
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                if (key[r] > floor) b = min(b, key[r]);
+                if (fresh[r] && key[r] > floor) b = min(b, key[r]);
             const unsigned k = t.rminu(b);
             if (k == 0xFFFFFFFFu) break;
             floor = k;
@@ -1405,8 +1440,6 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
                 if (ck > last) break;  // every later neighbour comes after it too
                 dst = __ffs(t.ballot(qk == last)) - 1;
             }
-            const uint64_t f = w.fp ^ __ldg(env.zk + i);
-            if (probe_full(env, f, w.gen, cap, t).visited) continue;
             if (lane == dst) qk = ck;
             const uint32_t word = w.word ^ (lane == (i >> 5) ? 1u << (i & 31) : 0u);
             if (lane < kBitWords) qbits[dst * kBitWords + lane] = word;

@@ -37,14 +37,15 @@ def _load() -> dict:
 
 
 def tune(Ls, walkers, *, seed: int = 0, tabu_log2: int = 16, steps: int = 512, device=None,
-         refresh: bool = False) -> dict:
-    """Fastest {"warps_per_cta", "chunk_steps"} for this length mix on this GPU."""
+         refresh: bool = False, flags: int = 0) -> dict:
+    """Fastest {"warps_per_cta", "chunk_steps"} for this length mix on this GPU (flags:
+    the context flags that change the kernel, e.g. LABS_FLAG_BEST_FIRST)."""
     from . import Search
 
     Ls = list(Ls) if isinstance(Ls, (list, tuple)) else [int(Ls)]
     walkers = list(walkers) if isinstance(walkers, (list, tuple)) else [int(walkers)]
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-    key = _key(Ls, walkers, tabu_log2, dev)
+    key = _key(Ls, walkers, tabu_log2, dev) + ("" if not flags else "/flags%d" % flags)
     with _lock:
         cache = _load()
         if key in cache and not refresh:
@@ -55,7 +56,7 @@ def tune(Ls, walkers, *, seed: int = 0, tabu_log2: int = 16, steps: int = 512, d
         for chunk in CHUNKS:
             # the shape is fixed at context creation: one context per candidate
             s = Search(Ls if multi else Ls[0], walkers if multi else walkers[0], seed, device=dev,
-                       tabu_log2=tabu_log2, warps_per_cta=wpc, chunk_steps=chunk)
+                       tabu_log2=tabu_log2, warps_per_cta=wpc, chunk_steps=chunk, flags=flags)
             s.walk(min(steps, 64))  # warm-up: graph capture, first touch of the tables
             s.sync()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
