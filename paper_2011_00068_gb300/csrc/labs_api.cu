@@ -126,6 +126,7 @@ KParams params(labs_ctx* c)
     p.best_first = (c->cfg.flags & LABS_FLAG_BEST_FIRST) ? 1 : 0;
     p.pq_key = p.best_first ? at<uint64_t>(c, c->off_pq_key) : nullptr;
     p.pq_bits = p.best_first ? at<uint32_t>(c, c->off_pq_bits) : nullptr;
+    p.mode = p.best_first ? 2 : (c->l_params ? 1 : 0);
     return p;
 }
 
@@ -258,7 +259,8 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     for (;;) {
         c->smem_bytes = per_warp * (size_t)warps;
         int occ = 0;
-        if (walk_kernel_config(c->tile, lanes_for(c->n_max, c->tile), warps, c->smem_bytes, &occ, &c->regs) ==
+        if (walk_kernel_config(c->tile, lanes_for(c->n_max, c->tile), (k.flags & LABS_FLAG_BEST_FIRST) ? 2 : 0, warps,
+                               c->smem_bytes, &occ, &c->regs) ==
                 LABS_OK &&
             occ > 0) {
             c->ctas_per_sm = occ;

@@ -1472,7 +1472,9 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
                 apply_flip<Tile<32>, R>(V, n, o, lane, true, i, P);
                 t.sync();
             } else {
-                load_rows(base, SL, V, word, env.L, n, t);
+                // rebuild from the bits; the walker's padding is still zero, so no clear
+                rows_from_bits(V, word, env.L, n, t);
+                build_table(V, n, t);
                 p_direct(V, n, o, P);
             }
             w.word = word;
@@ -1510,8 +1512,9 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
 // kernel is compiled for a tile of TILE lanes per walker and a largest lane block RMAX
 // = block_R(n_max, TILE) (register allocation follows it; odd for TILE = 32); walkers
 // whose n needs a smaller block run with RMAX-2, which covers them (any R >=
-// block_R(n) computes the same values).
-template <int TILE, int RMAX>
+// block_R(n) computes the same values).  MODE picks the step: 0 the plain walk, 1 the
+// learned mode, 2 the best-first search (one variant per kernel keeps the code small).
+template <int TILE, int RMAX, int MODE>
 __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(KParams p, int chunk_index)
 {
     extern __shared__ __align__(16) int smem[];
@@ -1564,7 +1567,7 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(K
         env.rdump_count = nullptr;
         env.dump_cap = 0;
         DevStatus* S = p.status;
-        if (S->learned) {
+        if (MODE == 1 && S->learned) {
             env.slot = S->l_slot + wi * kBitWords;
             env.slot_valid = S->l_slot_valid + wi;
             if (S->l_score_step[wi] == steps_done) {
@@ -1593,14 +1596,14 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(K
         // step of the plain walk
         constexpr int R2 = RMAX > 2 ? RMAX - 2 : 1;
         const bool full = RMAX <= 2 || block_R(G.n, TILE) >= RMAX;
-        if (p.best_first) {
+        if constexpr (MODE == 2) {
             uint64_t* qk = p.pq_key + wi * LABS_QUEUE_SIZE;
             uint32_t* qb = p.pq_bits + wi * LABS_QUEUE_SIZE * kBitWords;
             if (full)
                 walk_bestfirst<RMAX>(env, w, until, base, SL, V, trace_slot, trace_start, t, qk, qb);
             else
                 walk_bestfirst<R2>(env, w, until, base, SL, V, trace_slot, trace_start, t, qk, qb);
-        } else if (S->learned) {
+        } else if constexpr (MODE == 1) {
             if (full)
                 walk_steps<Tile<TILE>, RMAX>(env, w, until, base, SL, V, trace_slot, trace_start, ex, t);
             else

@@ -117,6 +117,7 @@ struct KParams {
     int32_t rmax;             // lane block of the walk kernel instantiation (block_R(n_max, tile))
     int32_t tile;             // lanes per walker: 32, 16 (two walkers per warp) or 8 (four)
     int32_t best_first;       // 1: best-first search (one walker per warp, queue below)
+    int32_t mode;             // walk kernel variant: 0 plain walk, 1 learned mode, 2 best-first
     uint64_t* pq_key;         // [W][LABS_QUEUE_SIZE] queue keys, ~0 = empty
     uint32_t* pq_bits;        // [W][LABS_QUEUE_SIZE][kBitWords] queue entries' free variables
     uint64_t seed;
@@ -207,7 +208,9 @@ WalkFn walk_fn8a(int rmax);
 WalkFn walk_fn8b(int rmax);
 WalkFn walk_fn16a(int rmax);
 WalkFn walk_fn16b(int rmax);
-WalkFn walk_fn32(int rmax);
+WalkFn walk_fn32(int rmax);   // one walker per warp: plain walk
+WalkFn walk_fn32l(int rmax);  // learned mode (labs_walk32l.cu)
+WalkFn walk_fn32b(int rmax);  // best-first search (labs_walk32b.cu)
 
 // Launchers (labs_kernels.cu).
 int launch_zobrist(const KParams& p, uint64_t* zkeys, const DevGroup* host_groups, int nG,
@@ -216,7 +219,8 @@ int launch_reset(const KParams& p, int grid, int block, void* stream);
 int launch_prep_walk(const KParams& p, int64_t steps, int nchunks, void* stream);
 int launch_walk_chunk(const KParams& p, int chunk_index, int grid, int warps_per_cta,
                       size_t smem_bytes, void* stream);
-int walk_kernel_config(int tile, int rmax, int warps_per_cta, size_t smem_bytes, int* ctas_per_sm, int* regs);
+int walk_kernel_config(int tile, int rmax, int mode, int warps_per_cta, size_t smem_bytes, int* ctas_per_sm,
+                       int* regs);
 int lanes_for(int n, int tile);  // block_R(n, tile)
 int launch_isl(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status,
                void* stream);

@@ -470,11 +470,11 @@ int launch_prep_walk(const KParams& p, int64_t steps, int nchunks, void* stream)
     return status_of(cudaGetLastError());
 }
 
-static WalkFn walk_fn(int tile, int rmax)
+static WalkFn walk_fn(int tile, int rmax, int mode)
 {
     if (tile == 8) return rmax <= 6 ? walk_fn8a(rmax) : walk_fn8b(rmax);
     if (tile == 16) return rmax <= 5 ? walk_fn16a(rmax) : walk_fn16b(rmax);
-    return walk_fn32(rmax);
+    return mode == 2 ? walk_fn32b(rmax) : mode == 1 ? walk_fn32l(rmax) : walk_fn32(rmax);
 }
 
 int lanes_for(int n, int tile)
@@ -482,11 +482,18 @@ int lanes_for(int n, int tile)
     return block_R(n, tile);
 }
 
-int walk_kernel_config(int tile, int rmax, int warps_per_cta, size_t smem_bytes, int* ctas_per_sm, int* regs)
+int walk_kernel_config(int tile, int rmax, int mode, int warps_per_cta, size_t smem_bytes, int* ctas_per_sm,
+                       int* regs)
 {
-    const WalkFn fn = walk_fn(tile, rmax);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-    if (e != cudaSuccess) return LABS_ECUDA;
+    const WalkFn fn = walk_fn(tile, rmax, mode);
+    // every variant a context of this shape may launch (the learned mode is switched on
+    // and off at run time) gets the shared-memory size
+    for (int m = 0; m < (tile == 32 ? 3 : 1); ++m) {
+        const cudaError_t e = cudaFuncSetAttribute(walk_fn(tile, rmax, m), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem_bytes);
+        if (e != cudaSuccess) return LABS_ECUDA;
+    }
+    cudaError_t e;
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return LABS_ECUDA;
@@ -502,7 +509,7 @@ int walk_kernel_config(int tile, int rmax, int warps_per_cta, size_t smem_bytes,
 int launch_walk_chunk(const KParams& p, int chunk_index, int grid, int warps_per_cta, size_t smem_bytes,
                       void* stream)
 {
-    const WalkFn fn = walk_fn(p.tile, p.rmax);
+    const WalkFn fn = walk_fn(p.tile, p.rmax, p.mode);
     fn<<<grid, warps_per_cta * kWarp, smem_bytes, (cudaStream_t)stream>>>(p, chunk_index);
     return status_of(cudaGetLastError());
 }
