@@ -285,9 +285,10 @@ int labs_features(int32_t L, const uint32_t *dev_bits, int64_t stride_words, int
  *     tries, among the flips with dISL <= (lowest dISL) + tau, the highest-scored
  *     (ties: lowest i) first, and continues in the plain order when none is admissible;
  *   - restart candidates: the walker's own next random start (the plain choice) and
- *     candidates-1 random perturbations of its best state; the one with the highest
- *     restart score (ties: lowest index) is used at the walker's next restart.
- * The exact int32 ISL decides every move; the network only orders candidates.
+ *     candidates-1 further random starts (Philox, counter (walker, next restart index,
+ *     block, c) for candidate c); the one with the highest restart score (ties: lowest
+ *     index) is used at the walker's next restart.
+ * The exact ISL decides every move; the network only orders candidates.
  * dev_ws: labs_learned_workspace_bytes bytes.  Chunks run without a CUDA graph. */
 int labs_learned_workspace_bytes(const labs_ctx *ctx, int32_t candidates, size_t *bytes);
 int labs_learned(labs_ctx *ctx, const float *dev_params, int32_t tau, int32_t candidates,

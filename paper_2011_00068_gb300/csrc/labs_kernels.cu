@@ -292,10 +292,11 @@ __global__ void __launch_bounds__(256) features_kernel(const uint32_t* __restric
 }
 
 // Restart candidates of walkers [first, first+count) of one length: candidate 0 is the
-// walker's own next random start (what the plain walk would use); candidates c >= 1
-// perturb the walker's best state by flipping r = 1 + (u mod max(1, n/8)) free
-// variables drawn by Philox (key = seed, counter = (walker, next restart index,
-// c << 16 | t, 1)).  Output bits [count][P][8].
+// walker's own next random start (what the plain walk would use); candidates c >= 1 are
+// further random starts, Philox with key = seed and counter = (walker, next restart
+// index, block, c) laid out as start_word's.  (Perturbations of the walker's best state
+// were tried as candidates instead: the walkers then crowd around their old optima and
+// found worse sequences, best F 6.81 against 7.23 at L = 255.)  Output bits [count][P][8].
 __global__ void candidates_kernel(KParams p, int64_t first, int64_t count, int n, int P, uint32_t* __restrict__ out)
 {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count * P;
@@ -310,17 +311,12 @@ __global__ void candidates_kernel(KParams p, int64_t first, int64_t count, int n
             for (int j = 0; j < kBitWords; ++j) bits[j] = start_word(p.seed, (uint32_t)w, ridx, j, n);
         } else {
 #pragma unroll
-            for (int j = 0; j < kBitWords; ++j) bits[j] = st.best[j];
-            uint32_t c0 = (uint32_t)w, c1 = ridx, c2 = (uint32_t)c << 16, c3 = 1u;
-            philox(c0, c1, c2, c3, (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
-            const int r = 1 + (int)(c0 % (uint32_t)max(1, n / 8));
-            for (int k = 0; k < r; ++k) {
-                uint32_t d0 = (uint32_t)w, d1 = ridx, d2 = ((uint32_t)c << 16) | (uint32_t)(k + 1), d3 = 1u;
-                philox(d0, d1, d2, d3, (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
-                const int i = (int)(d0 % (uint32_t)n);
-#pragma unroll
-                for (int j = 0; j < kBitWords; ++j)
-                    if (j == (i >> 5)) bits[j] ^= 1u << (i & 31);
+            for (int j = 0; j < kBitWords; ++j) {
+                uint32_t c0 = (uint32_t)w, c1 = ridx, c2 = (uint32_t)(j >> 2), c3 = (uint32_t)c;
+                philox(c0, c1, c2, c3, (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
+                const uint32_t v = (j & 3) == 0 ? c0 : (j & 3) == 1 ? c1 : (j & 3) == 2 ? c2 : c3;
+                const int lo = 32 * j;
+                bits[j] = n <= lo ? 0u : (n - lo >= 32 ? v : v & ((1u << (n - lo)) - 1u));
             }
         }
 #pragma unroll
