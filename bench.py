@@ -66,7 +66,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-delta", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--config", choices=["walk", "learned"], default="walk")
+    ap.add_argument("--config", choices=["walk", "learned", "scaleup"], default="walk")
+    ap.add_argument("--scaleup-walkers", type=int, default=131072)
+    ap.add_argument("--scaleup-steps", type=int, default=20000)
     ap.add_argument("--search", choices=["walk", "bestfirst"], default="walk",
                     help="walk: the self-avoiding walk; bestfirst: Algorithm 1 as printed (queue of 32)")
     ap.add_argument("--learned-L", type=int, default=255)
@@ -411,12 +413,71 @@ def run_learned(args):
     return 0
 
 
+def run_scaleup(args):
+    """Config 5: L=303 and L=501, 131072 walkers each, 2e4 steps of the plain walk (the
+    learned proposal is measured by --config learned): flips/s, the walk kernel's
+    roofline fraction, best F and the time to F >= 8 (sampled every 1000 steps); one
+    JSON line."""
+    import torch
+
+    import paper_2011_00068_gb300 as labs
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = float(measured_peaks().get("sm_max_mhz", 2070.0))
+    peak = FP32_LANES_PER_SM * 2 * sms * sm_mhz * 1e6
+    out = {}
+    seg = 1000
+    for L in (303, 501):
+        n = (L + 1) // 2
+        s = labs.Search(L, args.scaleup_walkers, 42, device=dev)
+        s.walk(64)
+        s.sync()
+        s.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done, t8 = 0, None
+        while done < args.scaleup_steps:
+            k = min(seg, args.scaleup_steps - done)
+            s.walk(k)
+            done += k
+            b = s.best()
+            if t8 is None and 2 * 8 * b["isl"] <= L * L:
+                t8 = {"steps": done, "seconds": time.perf_counter() - t0}
+        dt = time.perf_counter() - t0
+        st = s.stats()
+        flips = st["flip_evaluations"] / dt
+        b = s.best()
+        out[str(L)] = {"flips_per_s": flips, "seconds": dt, "steps": done, "walkers": args.scaleup_walkers,
+                       "best_isl": b["isl"], "best_F": b["F"], "best_hex": b["hex"], "time_to_F8": t8,
+                       "kernel": WALK_KERNELS[st["walkers_per_warp"]],
+                       "roofline_frac": ALGO_FLOP_PER_LAG_TERM * (n - 1) * flips / peak,
+                       "tabu_bytes": (args.scaleup_walkers << 16) * 8}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    total = sum(v["flips_per_s"] * v["seconds"] for v in out.values()) / sum(v["seconds"] for v in out.values())
+    line = {"metric": "exact flip evaluations/sec, L=303 and L=501 scale-up", "value": total,
+            "unit": "flip evaluations/s", "higher_is_better": True, "n_gpus": 1, "dtype": "f32",
+            "data": "synthetic", "vs_baseline": None,
+            "config": {"workload": "L=303 and L=501, %d walkers each, %d steps, seed 42, uniform random +-1 Philox "
+                                   "starts, HT 2^16 slots/walker" % (args.scaleup_walkers, args.scaleup_steps),
+                       "peak_source": "derived: %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz (FMA pipe)" % (
+                           sms, FP32_LANES_PER_SM, sm_mhz)},
+            "per_L": out}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.config == "learned":
         return run_learned(args)
+    if args.config == "scaleup":
+        return run_scaleup(args)
     return run_ours(args)
 
 
