@@ -1351,6 +1351,12 @@ __device__ __forceinline__ uint64_t warp_max64(uint64_t v)
     return ((uint64_t)hi << 32) | lo;
 }
 
+// A new S that differs from S in at most this many free variables is reached by that
+// many incremental flips (a neighbour of S, about half the steps, by one) rather than
+// a rebuild from its bits; about four of five steps at L = 101..151 (measured with the
+// Python statement), each flip costing about a sixth of a rebuild.
+constexpr int kBestFirstMaxFlips = 5;
+
 template <int R>
 __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int* base, const WarpSmem& SL,
                                const View& V, int trace_slot, int64_t trace_start, const Tile<32>& t, uint64_t* qkey,
@@ -1468,9 +1474,19 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
             const uint64_t f = nb ? (w.fp ^ __ldg(env.zk + i)) : fingerprint_all(word, env.zk, n, t);
             const Probe pr = probe_full(env, f, w.gen, cap, t);
             if (pr.visited) continue;
-            if (nb) {
-                apply_flip<Tile<32>, R>(V, n, o, lane, true, i, P);
-                t.sync();
+            // free variables in which the new S differs from S (1 for a neighbour)
+            uint32_t diff = lane < kBitWords ? (word ^ w.word) : 0u;
+            const int k = nb ? 1 : t.radd(__popc(diff));
+            if (k <= kBestFirstMaxFlips) {
+                // flip them one by one (lowest first) with the walk's incremental update
+                for (int j = 0; j < k; ++j) {
+                    const unsigned bl = t.ballot(diff != 0u);
+                    const int src_lane = __ffs(bl) - 1;
+                    const int fi = nb ? i : 32 * src_lane + t.shfl(__ffs(diff) - 1, src_lane);
+                    apply_flip<Tile<32>, R>(V, n, o, lane, true, fi, P);
+                    t.sync();
+                    if (lane == src_lane) diff &= diff - 1u;
+                }
             } else {
                 // rebuild from the bits; the walker's padding is still zero, so no clear
                 rows_from_bits(V, word, env.L, n, t);
