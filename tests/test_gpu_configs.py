@@ -9,6 +9,9 @@ config 3: the 52 odd lengths 201..303, 2048 walkers each, 5e3 steps, one launch:
           about five minutes of oracle time on 16 cores).
 largest length: L=501 (the largest length of the scale-up configuration), 8192
           walkers x 2000 steps.
+best-first search: the config-2 workload with LABS_FLAG_BEST_FIRST (bench.py
+          --search bestfirst), 24 walkers spread over the batch.
+short lengths: L=151 (four walkers per warp), 16384 walkers x 1e4 steps, 24 walkers.
 """
 from __future__ import annotations
 
@@ -31,8 +34,12 @@ def oracle_walkers(jobs):
         return list(ex.map(lambda j: oracle.walk(j[0], j[1], 1, j[2], first_walker=j[3], nthreads=1), jobs))
 
 
-def check_sample(s, L, seed, steps, ids):
-    outs = oracle_walkers([(L, seed, steps, gid) for gid in ids])
+def check_sample(s, L, seed, steps, ids, bestfirst=False):
+    if bestfirst:
+        with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+            outs = list(ex.map(lambda g: oracle.bestfirst(L, seed, 1, steps, first_walker=g, nthreads=1), ids))
+    else:
+        outs = oracle_walkers([(L, seed, steps, gid) for gid in ids])
     for gid, o in zip(ids, outs):
         r = s.results(gid, 1, seqs=True)
         assert r["isl"][0] == o["final_isl"][0], gid
@@ -91,3 +98,29 @@ def test_largest_length_L501():
     s.walk(steps)
     s.sync()
     check_sample(s, L, seed, steps, [0, 4095, W - 1])
+
+
+def test_bestfirst_L201_bench_shape():
+    from paper_2011_00068_gb300 import _native
+
+    L, W, steps, seed = 201, 16384, 10_000, 7
+    s = labs.Search(L, W, seed, flags=_native.LABS_FLAG_BEST_FIRST)
+    s.walk(steps)
+    s.sync()
+    st = s.stats()
+    assert st["steps"] == W * steps
+    ids = sorted({0, W - 1} | set(list(range(211, W, 719))[:22]))
+    check_sample(s, L, seed, steps, ids, bestfirst=True)
+    b = s.best()
+    assert oracle.isl(b["seq"]) == b["isl"] == st["best_isl"]
+
+
+def test_four_walkers_per_warp_L151_bench_shape():
+    L, W, steps, seed = 151, 16384, 10_000, 7
+    s = labs.Search(L, W, seed)
+    s.walk(steps)
+    s.sync()
+    st = s.stats()
+    assert st["steps"] == W * steps and st["walkers_per_warp"] == 4
+    ids = sorted({0, 3, W - 1} | set(list(range(5, W, 701))[:21]))
+    check_sample(s, L, seed, steps, ids)
