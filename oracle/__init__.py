@@ -61,7 +61,8 @@ class WalkCfg(ctypes.Structure):
 class WalkResult(ctypes.Structure):
     _fields_ = [("final_isl", ctypes.c_int32), ("best_isl", ctypes.c_int32),
                 ("best_step", ctypes.c_int64), ("target_step", ctypes.c_int64),
-                ("restarts", ctypes.c_int32), ("overflows", ctypes.c_int32)]
+                ("restarts", ctypes.c_int32), ("overflows", ctypes.c_int32),
+                ("final_psl", ctypes.c_int32), ("best_psl", ctypes.c_int32)]
 
 
 WALK_RESULT_FIELDS = [f[0] for f in WalkResult._fields_]
@@ -92,6 +93,8 @@ def lib():
             L.lo_fingerprint.argtypes = [P, i32]; L.lo_fingerprint.restype = u64
             L.lo_walk.argtypes = [i32, u64, i64, i64, i64, ctypes.POINTER(WalkCfg), P, P, P, P, P, i32]
             L.lo_walk.restype = ctypes.c_int
+            L.lo_walk_psl.argtypes = L.lo_walk.argtypes
+            L.lo_walk_psl.restype = ctypes.c_int
             L.lo_enumerate.argtypes = [i32, P, P, P, P, i32]; L.lo_enumerate.restype = ctypes.c_int
             L.lo_bestfirst.argtypes = [i32, u64, i64, i64, i64, ctypes.POINTER(WalkCfg), i32, P, P, P, P, P, i32]
             L.lo_bestfirst.restype = ctypes.c_int
@@ -209,12 +212,17 @@ def fingerprint(s) -> int:
 
 def walk(L: int, seed: int, walkers: int, steps: int, *, first_walker: int = 0,
          tabu_log2: int = 16, probe_cap: int = 32, patience: int = 0,
-         target: tuple[int, int] = (17, 2), trace: bool = False, nthreads: int = 0) -> dict:
+         target: tuple[int, int] = (17, 2), trace: bool = False, nthreads: int = 0,
+         objective: str = "isl") -> dict:
     """Algorithm 1, self-avoiding-walk form, for walkers first_walker.. (+walkers).
+    objective "isl" minimises ISL (Eq. 2); "psl" minimises PSL (Section 1) with ties
+    broken by ISL, every neighbour measured from its recomputed C_k.
 
     Returns a dict of numpy arrays: the WalkResult fields per walker, ``best_seq`` and
     ``final_seq`` [walkers, L], and with ``trace`` the per-step ``trace_code`` and
     ``trace_isl`` [walkers, steps]."""
+    if objective not in ("isl", "psl"):
+        raise ValueError("objective is 'isl' or 'psl'")
     cfg = WalkCfg(tabu_log2, probe_cap, patience, target[0], target[1])
     res = (WalkResult * max(walkers, 1))()
     best = np.zeros((walkers, L), dtype=np.int8)
@@ -226,8 +234,9 @@ def walk(L: int, seed: int, walkers: int, steps: int, *, first_walker: int = 0,
     else:
         tc = ti = None
         tcp = tip = None
-    rc = lib().lo_walk(L, seed, first_walker, walkers, steps, ctypes.byref(cfg),
-                       ctypes.cast(res, ctypes.c_void_p), _ptr(best), _ptr(final), tcp, tip, nthreads)
+    fn = lib().lo_walk_psl if objective == "psl" else lib().lo_walk
+    rc = fn(L, seed, first_walker, walkers, steps, ctypes.byref(cfg),
+            ctypes.cast(res, ctypes.c_void_p), _ptr(best), _ptr(final), tcp, tip, nthreads)
     if rc != 0:
         raise RuntimeError("oracle walk failed: %d" % rc)
     out = {f: np.array([getattr(res[w], f) for w in range(walkers)]) for f in WALK_RESULT_FIELDS}

@@ -21,6 +21,9 @@
  *   - the search loop of Algorithm 1 in the self-avoiding-walk form (move to the best
  *     neighbour that is not in the visited set HT, ties to the lowest i), with
  *     restarts from a fresh random sequence as in lssOrel (Section 2).
+ *   - the same walk with PSL (Section 1) as the objective instead of ISL: every
+ *     neighbour is built and its PSL and ISL recomputed from Eq. 1.  The paper only
+ *     reports PSL (Table 1, Section 4); ordering by (PSL, ISL) is the library's reading.
  *   - Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) for every random draw.
  * Where the paper is silent (tie-break, restart rule, hash-table layout, random
  * stream layout) the reading is fixed in the comments below and mirrored by the
@@ -330,6 +333,8 @@ typedef struct {
     int64_t target_step;  /* steps completed when F >= target first held, or -1 */
     int32_t restarts;
     int32_t overflows;    /* HT insertions that found no free slot */
+    int32_t final_psl;    /* PSL (Section 1) of the final and of the best sequence */
+    int32_t best_psl;
 } lo_walk_result;
 
 /* Trace codes, one per step: the flipped free variable i (0..n-1), with bit 16 set
@@ -358,12 +363,14 @@ typedef struct {
     const lo_walk_cfg *cfg;
     const uint64_t *zkey;
     const lo_replay *replay;
+    int32_t objective;  /* 0: ISL (Eq. 2); 1: PSL first, ties by ISL */
     int8_t *x, *s, *s_best, *sf, *tried;
-    int64_t *delta;
+    int64_t *delta, *cand_psl, *cand_isl;
     int32_t *order;
     lo_ht ht;
     uint32_t restart_index;
     int64_t isl, best_isl, since_restart_best;
+    int64_t psl, best_psl, since_restart_best_psl;
     int32_t stagnation;
     uint64_t fp;
     lo_walk_result res;
@@ -376,10 +383,21 @@ static int target_met(const lo_walker *w, int64_t isl)
     return (int64_t)w->cfg->target_den * w->L * w->L >= 2 * (int64_t)w->cfg->target_num * isl;
 }
 
+/* Is (psl, isl) better than (psl0, isl0) under the walker's objective?  The ISL
+ * objective compares ISL alone; the PSL objective compares PSL and breaks ties by ISL
+ * (the paper optimises F and only reports PSL; this order is the library's reading of
+ * a PSL search that stays comparable with it). */
+static int better(const lo_walker *w, int64_t psl, int64_t isl, int64_t psl0, int64_t isl0)
+{
+    if (w->objective) return psl < psl0 || (psl == psl0 && isl < isl0);
+    return isl < isl0;
+}
+
 static void note_best(lo_walker *w, int64_t steps_done)
 {
-    if (w->isl < w->best_isl) {
+    if (better(w, w->psl, w->isl, w->best_psl, w->best_isl)) {
         w->best_isl = w->isl;
+        w->best_psl = w->psl;
         memcpy(w->s_best, w->s, (size_t)w->L);
         w->res.best_step = steps_done;
     }
@@ -403,9 +421,11 @@ static void start(lo_walker *w, int64_t steps_done)
     }
     lo_skew_expand(w->x, w->L, w->s);
     w->isl = lo_isl(w->s, w->L);
+    w->psl = lo_psl(w->s, w->L);
     w->fp = lo_fingerprint(w->s, w->L);
     ht_insert(&w->ht, w->fp);
     w->since_restart_best = w->isl;
+    w->since_restart_best_psl = w->psl;
     w->stagnation = 0;
     note_best(w, steps_done);
 }
@@ -512,6 +532,72 @@ static int32_t walk_step(lo_walker *w, int64_t steps_done_after)
     return chosen;
 }
 
+/* One step of the walk under the PSL objective.  Every neighbour S_i (free variable i
+ * and its mirror negated) is built and measured from the definitions: PSL_i = max |C_k|
+ * (Section 1) and ISL_i (Eq. 2), C_k by Eq. 1.  The walker moves to the first
+ * neighbour not in HT in the order (PSL_i, ISL_i, i) ascending; HT, the best sequence,
+ * the stagnation count and the restarts follow the same rules as the ISL walk, with
+ * "better" meaning a lower (PSL, ISL) pair. */
+static int32_t walk_step_psl(lo_walker *w, int64_t steps_done_after)
+{
+    int32_t L = w->L, n = w->n;
+    for (int32_t i = 0; i < n; ++i) {
+        memcpy(w->sf, w->s, (size_t)L);
+        w->sf[i] = (int8_t)(-w->sf[i]);
+        if (L - 1 - i != i) w->sf[L - 1 - i] = (int8_t)(-w->sf[L - 1 - i]);
+        w->cand_psl[i] = lo_psl(w->sf, L);
+        w->cand_isl[i] = lo_isl(w->sf, L);
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t j = i;
+        while (j > 0) {
+            int32_t o = w->order[j - 1];
+            int before = w->cand_psl[i] < w->cand_psl[o] ||
+                         (w->cand_psl[i] == w->cand_psl[o] && w->cand_isl[i] < w->cand_isl[o]);
+            if (!before) break;
+            w->order[j] = o;
+            --j;
+        }
+        w->order[j] = i;
+    }
+    int32_t chosen = -1;
+    uint64_t fp_new = 0;
+    for (int32_t t = 0; t < n && chosen < 0; ++t) {
+        int32_t i = w->order[t];
+        uint64_t f = w->fp ^ w->zkey[i];
+        if (!ht_contains(&w->ht, f)) {
+            chosen = i;
+            fp_new = f;
+        }
+    }
+    if (chosen < 0) {
+        restart(w, steps_done_after);
+        return -1;
+    }
+    int32_t q = L - 1 - chosen;
+    w->s[chosen] = (int8_t)(-w->s[chosen]);
+    if (q != chosen) w->s[q] = (int8_t)(-w->s[q]);
+    w->isl = w->cand_isl[chosen];
+    w->psl = w->cand_psl[chosen];
+    w->fp = fp_new;
+    int stored = ht_insert(&w->ht, fp_new);
+    if (!stored) w->res.overflows += 1;
+    note_best(w, steps_done_after);
+    if (better(w, w->psl, w->isl, w->since_restart_best_psl, w->since_restart_best)) {
+        w->since_restart_best = w->isl;
+        w->since_restart_best_psl = w->psl;
+        w->stagnation = 0;
+    } else {
+        w->stagnation += 1;
+    }
+    int32_t patience = w->cfg->patience > 0 ? w->cfg->patience : 2 * n;
+    if (w->stagnation >= patience || !stored) {
+        restart(w, steps_done_after);
+        return chosen | LO_TRACE_RESTART;
+    }
+    return chosen;
+}
+
 typedef struct {
     int32_t L;
     uint64_t seed;
@@ -523,6 +609,7 @@ typedef struct {
     int8_t *final_seq;
     int32_t *trace_code, *trace_isl;
     int32_t pq_size;  /* 0: the walk; > 0: best-first search with this queue size */
+    int32_t objective;  /* walk only: 0 ISL, 1 PSL then ISL */
     int64_t next;
     pthread_mutex_t lock;
     int status;
@@ -542,27 +629,33 @@ static int run_walker(lo_walk_job *job, int64_t w_idx, const lo_replay *replay)
     w.cfg = job->cfg;
     w.zkey = job->zkey;
     w.replay = replay;
+    w.objective = job->objective;
     w.tried = (int8_t *)calloc((size_t)n, 1);
     w.x = (int8_t *)malloc((size_t)L);
     w.s = (int8_t *)malloc((size_t)L);
     w.s_best = (int8_t *)malloc((size_t)L);
     w.delta = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     w.order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    w.sf = (int8_t *)malloc((size_t)L);
+    w.cand_psl = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    w.cand_isl = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     w.ht.mask = (1ull << job->cfg->tabu_log2) - 1;
     w.ht.cap = job->cfg->probe_cap;
     if ((uint64_t)w.ht.cap > w.ht.mask + 1) w.ht.cap = (int32_t)(w.ht.mask + 1);
     w.ht.slot = (uint64_t *)calloc((size_t)(w.ht.mask + 1), sizeof(uint64_t));
     w.ht.gen = 1;
     w.best_isl = INT64_MAX;
+    w.best_psl = INT64_MAX;
     w.res.target_step = -1;
     int rc = 0;
-    if (!w.x || !w.s || !w.s_best || !w.delta || !w.order || !w.ht.slot || !w.tried) {
+    if (!w.x || !w.s || !w.s_best || !w.delta || !w.order || !w.ht.slot || !w.tried || !w.sf || !w.cand_psl ||
+        !w.cand_isl) {
         rc = -3;
         goto done;
     }
     start(&w, 0);
     for (int64_t t = 0; t < job->steps; ++t) {
-        int32_t code = walk_step(&w, t + 1);
+        int32_t code = w.objective ? walk_step_psl(&w, t + 1) : walk_step(&w, t + 1);
         if (code == -99) {
             rc = -2;
             break;
@@ -574,11 +667,14 @@ static int run_walker(lo_walk_job *job, int64_t w_idx, const lo_replay *replay)
     }
     w.res.final_isl = (int32_t)w.isl;
     w.res.best_isl = (int32_t)w.best_isl;
+    w.res.final_psl = (int32_t)lo_psl(w.s, L);
+    w.res.best_psl = (int32_t)lo_psl(w.s_best, L);
     job->res[w_idx] = w.res;
     if (job->best_seq) memcpy(job->best_seq + w_idx * L, w.s_best, (size_t)L);
     if (job->final_seq) memcpy(job->final_seq + w_idx * L, w.s, (size_t)L);
 done:
     free(w.x); free(w.s); free(w.s_best); free(w.delta); free(w.order); free(w.ht.slot); free(w.tried);
+    free(w.sf); free(w.cand_psl); free(w.cand_isl);
     return rc;
 }
 
@@ -606,7 +702,7 @@ static void *walk_thread(void *arg)
  * Returns 0, -1 on bad arguments, -2 on an internal mismatch, -3 on allocation
  * failure. */
 static int walk_many(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t steps,
-                     const lo_walk_cfg *cfg, int32_t pq_size, lo_walk_result *res, int8_t *best_seq,
+                     const lo_walk_cfg *cfg, int32_t pq_size, int32_t objective, lo_walk_result *res, int8_t *best_seq,
                      int8_t *final_seq, int32_t *trace_code, int32_t *trace_isl, int32_t nthreads)
 {
     if (L < 3 || (L & 1) == 0 || count < 0 || steps < 0 || !cfg || !res) return -1;
@@ -623,6 +719,7 @@ static int walk_many(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_
     job.cfg = cfg; job.zkey = zkey; job.res = res; job.best_seq = best_seq;
     job.final_seq = final_seq; job.trace_code = trace_code; job.trace_isl = trace_isl;
     job.pq_size = pq_size;
+    job.objective = objective;
     pthread_mutex_init(&job.lock, NULL);
     if (nthreads <= 0) nthreads = (int32_t)sysconf(_SC_NPROCESSORS_ONLN);
     if (nthreads < 1) nthreads = 1;
@@ -640,7 +737,17 @@ int lo_walk(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t steps,
             const lo_walk_cfg *cfg, lo_walk_result *res, int8_t *best_seq, int8_t *final_seq,
             int32_t *trace_code, int32_t *trace_isl, int32_t nthreads)
 {
-    return walk_many(L, seed, g0, count, steps, cfg, 0, res, best_seq, final_seq, trace_code, trace_isl, nthreads);
+    return walk_many(L, seed, g0, count, steps, cfg, 0, 0, res, best_seq, final_seq, trace_code, trace_isl, nthreads);
+}
+
+/* As lo_walk with the PSL objective (walk_step_psl): the ISL trace still holds the ISL
+ * at the end of each step, and res[].best_psl / best_isl describe the best sequence in
+ * the (PSL, ISL) order. */
+int lo_walk_psl(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t steps,
+                const lo_walk_cfg *cfg, lo_walk_result *res, int8_t *best_seq, int8_t *final_seq,
+                int32_t *trace_code, int32_t *trace_isl, int32_t nthreads)
+{
+    return walk_many(L, seed, g0, count, steps, cfg, 0, 1, res, best_seq, final_seq, trace_code, trace_isl, nthreads);
 }
 
 /* One walker (id g) replayed with the learned-mode choices of a GPU run (lo_replay);
@@ -847,6 +954,8 @@ static int run_bestfirst(lo_walk_job *job, int64_t w_idx)
     }
     w.res.final_isl = (int32_t)w.isl;
     w.res.best_isl = (int32_t)w.best_isl;
+    w.res.final_psl = (int32_t)lo_psl(w.s, L);
+    w.res.best_psl = (int32_t)lo_psl(w.s_best, L);
     job->res[w_idx] = w.res;
     if (job->best_seq) memcpy(job->best_seq + w_idx * L, w.s_best, (size_t)L);
     if (job->final_seq) memcpy(job->final_seq + w_idx * L, w.s, (size_t)L);
@@ -863,7 +972,7 @@ int lo_bestfirst(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t st
                  int32_t *trace_isl, int32_t nthreads)
 {
     if (pq_size < 1) return -1;
-    return walk_many(L, seed, g0, count, steps, cfg, pq_size, res, best_seq, final_seq, trace_code, trace_isl,
+    return walk_many(L, seed, g0, count, steps, cfg, pq_size, 0, res, best_seq, final_seq, trace_code, trace_isl,
                      nthreads);
 }
 

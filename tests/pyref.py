@@ -5,6 +5,8 @@ oracle/labs_oracle.c, used only to pin the oracle in the CPU tests.
 * Philox4x32-10 in Python integers (Salmon et al., SC'11).
 * The walk of Algorithm 1 (self-avoiding form) with dISL by flip-and-recompute, not
   by the two-position formula the oracle uses.
+* The same walk under the PSL objective, with PSL and ISL of every neighbour from
+  numpy's correlate.
 """
 from __future__ import annotations
 
@@ -19,6 +21,13 @@ def isl_np(s) -> int:
     full = np.correlate(s, s, mode="full")  # index L-1+k holds C_k
     side = full[L:]
     return int(np.dot(side, side))
+
+
+def psl_np(s) -> int:
+    s = np.asarray(s, dtype=np.int64)
+    L = s.size
+    side = np.correlate(s, s, mode="full")[L:]
+    return int(np.abs(side).max()) if side.size else 0
 
 
 def philox(ctr, key):
@@ -242,3 +251,71 @@ def bestfirst(L, seed, g, steps, K, tabu_log2=16, cap=32):
         codes.append(code)
         isls.append(e)
     return codes, isls, st["best"], st["restarts"], st["overflows"]
+
+
+def walk_psl(L, seed, g, steps, tabu_log2=16, cap=32, patience=0):
+    """The walk with (PSL, ISL) as the objective, compared as pairs; returns
+    (trace_code, trace_isl, (best_psl, best_isl), restarts)."""
+    n = (L + 1) // 2
+    patience = patience or 2 * n
+    keys = [zkey(L, i) for i in range(n)]
+    ht = HT(tabu_log2, cap)
+    st = {"r": 0, "best": None, "restarts": 0}
+
+    def begin():
+        s = skew(start_vars(seed, g, st["r"], L), L)
+        obj = (psl_np(s), isl_np(s))
+        f = 0
+        for i in range(n):
+            if s[i] < 0:
+                f ^= keys[i]
+        ht.insert(f)
+        if st["best"] is None or obj < st["best"]:
+            st["best"] = obj
+        return s, obj, f, obj, 0
+
+    def again():
+        st["r"] += 1
+        st["restarts"] += 1
+        ht.new_generation()
+        return begin()
+
+    s, obj, f, since, stag = begin()
+    codes, isls = [], []
+    for _ in range(steps):
+        cand = []
+        for i in range(n):
+            t = s.copy()
+            t[i] = -t[i]
+            if L - 1 - i != i:
+                t[L - 1 - i] = -t[L - 1 - i]
+            cand.append(((psl_np(t), isl_np(t)), i))
+        chosen = None
+        for o, i in sorted(cand):
+            if not ht.contains(f ^ keys[i]):
+                chosen, new = i, o
+                break
+        if chosen is None:
+            s, obj, f, since, stag = again()
+            codes.append(-1)
+            isls.append(obj[1])
+            continue
+        s[chosen] = -s[chosen]
+        if L - 1 - chosen != chosen:
+            s[L - 1 - chosen] = -s[L - 1 - chosen]
+        obj = new
+        f ^= keys[chosen]
+        stored = ht.insert(f)
+        if obj < st["best"]:
+            st["best"] = obj
+        if obj < since:
+            since, stag = obj, 0
+        else:
+            stag += 1
+        code = chosen
+        if stag >= patience or not stored:
+            s, obj, f, since, stag = again()
+            code |= 0x10000
+        codes.append(code)
+        isls.append(obj[1])
+    return codes, isls, st["best"], st["restarts"]

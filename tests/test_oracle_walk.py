@@ -151,3 +151,63 @@ def test_bestfirst_invariants_L201():
         assert oracle.isl(a["final_seq"][g]) == a["final_isl"][g] == a["trace_isl"][g][-1]
         assert (a["trace_isl"][g] % 8 == (n - 1) % 8).all()
         assert (oracle.fingerprint(a["final_seq"][g]) & 0xFFFF) == a["trace_code"][g][-1]
+
+
+# ------------------------------------------------------------ PSL objective walk
+
+@pytest.mark.parametrize("L,steps,log2,cap,patience",
+                         [(13, 200, 16, 32, 0), (21, 250, 16, 32, 0), (21, 300, 4, 3, 7),
+                          (5, 60, 16, 32, 0), (3, 20, 16, 32, 0), (41, 150, 16, 32, 0)])
+def test_psl_walk_matches_python_statement(L, steps, log2, cap, patience):
+    """Candidate order (PSL, ISL, i), best and stagnation on (PSL, ISL) pairs, against
+    the Python statement, whose PSL and ISL come from numpy's correlate."""
+    seed = 4
+    out = oracle.walk(L, seed, 3, steps, tabu_log2=log2, probe_cap=cap, patience=patience,
+                      trace=True, nthreads=2, objective="psl")
+    for g in range(3):
+        codes, isls, best, restarts = pyref.walk_psl(L, seed, g, steps, log2, cap, patience)
+        assert list(out["trace_code"][g]) == codes
+        assert list(out["trace_isl"][g]) == isls
+        assert (out["best_psl"][g], out["best_isl"][g]) == best
+        assert out["restarts"][g] == restarts
+
+
+def test_psl_walk_reaches_barker_13():
+    """The Barker sequence of length 13 is skew-symmetric with PSL 1, the lowest PSL any
+    sequence can have; an exhaustive pass over the 2^7 skew states finds exactly it, its
+    reversal and their negations, and every PSL walker ends at one of them."""
+    L, n = 13, 7
+    barker = np.array([1 if ch == "+" else -1 for ch in "+++++--++-+-+"], dtype=np.int8)
+    family = [barker, -barker, barker[::-1].copy(), -barker[::-1]]
+    psl1 = []
+    for a in range(1 << n):
+        x = np.array([-1 if (a >> i) & 1 else 1 for i in range(n)], dtype=np.int8)
+        s = oracle.skew_expand(x, L)
+        if oracle.psl(s) == 1:
+            psl1.append(s)
+    assert len(psl1) == 4
+    assert all(any(np.array_equal(s, b) for b in family) for s in psl1)
+    out = oracle.walk(L, 11, 4, 300, objective="psl")
+    for g in range(4):
+        assert out["best_psl"][g] == 1
+        assert oracle.psl(out["best_seq"][g]) == 1
+        assert any(np.array_equal(out["best_seq"][g], s) for s in psl1)
+
+
+def test_psl_walk_invariants_L101():
+    L, steps = 101, 120
+    a = oracle.walk(L, 7, 3, steps, trace=True, nthreads=3, objective="psl")
+    b = oracle.walk(L, 7, 3, steps, trace=True, nthreads=1, objective="psl")
+    for k in ("trace_code", "trace_isl", "best_isl", "best_psl", "final_isl", "best_seq"):
+        assert np.array_equal(a[k], b[k])
+    n = (L + 1) // 2
+    for g in range(3):
+        assert oracle.psl(a["best_seq"][g]) == a["best_psl"][g]
+        assert oracle.isl(a["best_seq"][g]) == a["best_isl"][g]
+        assert oracle.psl(a["final_seq"][g]) == a["final_psl"][g]
+        assert oracle.isl(a["final_seq"][g]) == a["final_isl"][g] == a["trace_isl"][g][-1]
+        assert oracle.is_skew(a["final_seq"][g])
+        assert (a["trace_isl"][g] % 8 == (n - 1) % 8).all()
+    # the PSL walk ends at a lower PSL than the ISL walk's best sequences, on average
+    c = oracle.walk(L, 7, 3, steps)
+    assert a["best_psl"].mean() < c["best_psl"].mean()
