@@ -81,6 +81,10 @@ typedef struct labs_config {
                                        search with a queue of LABS_QUEUE_SIZE evaluated
                                        neighbours per walker (see labs_walk); one walker per
                                        warp; not with LABS_FLAG_LEARNED, no checkpoints */
+#define LABS_FLAG_PSL 64            /* labs_walk minimises PSL (Section 1) instead of ISL: the
+                                       walk's rules with (PSL, ISL) pairs as the objective (see
+                                       labs_walk); one walker per warp; not with
+                                       LABS_FLAG_BEST_FIRST or LABS_FLAG_LEARNED */
 #define LABS_QUEUE_SIZE 32           /* entries of a walker's best-first queue */
 #define LABS_BEST_FIRST_MAX_STEPS (1ll << 28) /* steps per walker the queue order can number */
 
@@ -99,6 +103,9 @@ typedef struct labs_counters {
     int64_t walkers_at_target; /* walkers that met the target */
     int32_t walkers_per_warp;  /* launch shape of the walk kernel: 4, 2 or 1 */
     int32_t lane_block;        /* outputs per lane of the widest walker (R) */
+    int32_t best_psl;          /* LABS_FLAG_PSL: PSL of the best sequence (whose ISL is
+                                  best_isl; best in the (PSL, ISL) order); else -1 */
+    int32_t pad_;
 } labs_counters;
 
 /* One record of the walk log (labs_log): the state of a walker at the start of a
@@ -170,6 +177,12 @@ int labs_neighbor_delta(labs_ctx *ctx, const int8_t *dev_seqs, int64_t batch,
  *   the walk; the walker restarts (HT and queue emptied) when the queue runs empty or
  *   HT has no free slot for the new S; `patience` is not used.  At most
  *   LABS_BEST_FIRST_MAX_STEPS steps per walker (LABS_EINVAL beyond).
+ * With LABS_FLAG_PSL the objective is the pair (PSL, ISL), compared lexicographically
+ *   (PSL = max_k |C_k|, Section 1; the paper optimises F and reports PSL in Table 1,
+ *   so this order is the library's reading of a PSL search): the step takes the flip
+ *   with the lowest (PSL, ISL, i) whose result is not in HT, the best sequence and the
+ *   stagnation count use "strictly lower pair", and HT and the restarts are as in the
+ *   walk.  The trace's ISL log still holds ISL.
  * The trajectory of a walker depends only on (seed, walker id, L, cfg), never on
  * chunking, launch shape or the other walkers. */
 int labs_walk(labs_ctx *ctx, int64_t steps);
@@ -178,11 +191,21 @@ int labs_walk(labs_ctx *ctx, int64_t steps);
 int labs_sync(labs_ctx *ctx);
 
 /* Best sequence found so far among walkers of length L (L = 0: all lengths):
- * lowest ISL, ties to the lowest walker id.  Synchronising.  host_seq_out: int8 [L]
+ * lowest ISL (with LABS_FLAG_PSL: lowest (PSL, ISL) pair), ties to the lowest walker id.  Synchronising.  host_seq_out: int8 [L]
  * (nullable; sized for the winning length, which *L_out gives), isl/F/L_out nullable,
  * hex_out: ceil(L/4)+1 chars in the encoding described below Table 1 (nullable). */
 int labs_best(labs_ctx *ctx, int32_t L, int8_t *host_seq_out, int32_t *isl, double *F,
               int32_t *L_out, char *hex_out);
+
+/* LABS_FLAG_PSL contexts only (LABS_EINVAL otherwise): the best sequence in the
+ * (PSL, ISL) order, as labs_best, with its PSL and ISL. */
+int labs_best_psl(labs_ctx *ctx, int32_t L, int8_t *host_seq_out, int32_t *psl, int32_t *isl,
+                  int32_t *L_out, char *hex_out);
+
+/* LABS_FLAG_PSL contexts only: PSL of the current and of the best sequence of walkers
+ * [first, first+count) (host int32 arrays, nullable).  Synchronising. */
+int labs_walker_psl(labs_ctx *ctx, int64_t first, int64_t count, int32_t *host_psl,
+                    int32_t *host_best_psl);
 
 /* Per-walker results for walkers [first, first+count): current and best ISL (int32),
  * and optionally their sequences (int8 [count][Lw], all walkers in the range must have
@@ -260,7 +283,8 @@ int labs_net_adamw(float *dev_params, const float *dev_grads, float *dev_m, floa
 
 /* ---- Learned proposal in the walk.
  *
- * labs_log arms the walk log: from the next labs_walk on, at the start of every chunk
+ * labs_log arms the walk log (plain walk only: LABS_EINVAL with LABS_FLAG_BEST_FIRST or
+ * LABS_FLAG_PSL): from the next labs_walk on, at the start of every chunk
  * of chunk_steps steps, walker w fills record k*walkers + w of dev_records (k = chunks
  * since this call) with its state and what followed it in the chunk, while the index
  * is below capacity.  capacity 0 disarms. */
@@ -306,7 +330,7 @@ int labs_trace_learned(labs_ctx *ctx, int32_t capacity, float *dev_scores, int64
 /* Checkpoint of every walker's state (sequence, ISL, best, counters, random-stream
  * position) and, with with_tabu != 0, its HT.  With the HT included a restored run
  * continues bit-identically; without it the HT restarts empty.  host_buf NULL queries
- * the size.  Synchronising.  LABS_EINVAL for a context with LABS_FLAG_BEST_FIRST (its
+ * the size; a checkpoint restores only into a context with the same LABS_FLAG_PSL.  Synchronising.  LABS_EINVAL for a context with LABS_FLAG_BEST_FIRST (its
  * queues are not part of the checkpoint). */
 int labs_checkpoint(labs_ctx *ctx, int with_tabu, void *host_buf, size_t *bytes);
 int labs_restore(labs_ctx *ctx, const void *host_buf, size_t bytes);

@@ -72,9 +72,15 @@ class Search:
     ``L`` and ``walkers`` are an int each, or equal-length sequences for a context that
     mixes lengths (walker ids then run length by length).  Extra keyword arguments are
     labs_config fields (tabu_log2, probe_cap, patience, target_num, target_den,
-    chunk_steps, warps_per_cta, flags)."""
+    chunk_steps, warps_per_cta, flags).  ``objective="psl"`` sets LABS_FLAG_PSL: the
+    walkers minimise (PSL, ISL) pairs instead of ISL."""
 
-    def __init__(self, L, walkers, seed: int, *, device=None, stream=None, **cfg):
+    def __init__(self, L, walkers, seed: int, *, device=None, stream=None, objective: str = "isl", **cfg):
+        if objective not in ("isl", "psl"):
+            raise ValueError("objective is 'isl' or 'psl'")
+        if objective == "psl":
+            cfg["flags"] = int(cfg.get("flags", 0)) | _native.LABS_FLAG_PSL
+        self.psl = objective == "psl"
         self.lib = library()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         if self.device.type != "cuda":
@@ -143,8 +149,13 @@ class Search:
         hexbuf = ctypes.create_string_buffer((Lmax + 3) // 4 + 1)
         self._c(self.lib.labs_best(self.ctx, int(L), seq.ctypes.data_as(ctypes.c_void_p), ctypes.byref(isl_),
                                    ctypes.byref(F), ctypes.byref(Lo), hexbuf))
-        return {"L": Lo.value, "isl": isl_.value, "F": F.value, "seq": seq[:Lo.value].copy(),
-                "hex": hexbuf.value.decode()}
+        out = {"L": Lo.value, "isl": isl_.value, "F": F.value, "seq": seq[:Lo.value].copy(),
+               "hex": hexbuf.value.decode()}
+        if self.psl:
+            psl_ = ctypes.c_int32()
+            self._c(self.lib.labs_best_psl(self.ctx, int(L), None, ctypes.byref(psl_), None, None, None))
+            out["psl"] = psl_.value
+        return out
 
     def results(self, first: int = 0, count: int | None = None, seqs: bool = False) -> dict:
         count = self.W - first if count is None else count
@@ -161,6 +172,12 @@ class Search:
             args += [None, None]
         args.append(out["target_step"].ctypes.data_as(ctypes.c_void_p))
         self._c(self.lib.labs_walker_results(self.ctx, int(first), int(count), *args))
+        if self.psl:
+            out["psl"] = np.zeros(count, np.int32)
+            out["best_psl"] = np.zeros(count, np.int32)
+            self._c(self.lib.labs_walker_psl(self.ctx, int(first), int(count),
+                                             out["psl"].ctypes.data_as(ctypes.c_void_p),
+                                             out["best_psl"].ctypes.data_as(ctypes.c_void_p)))
         return out
 
     def stats(self, L: int = 0) -> dict:

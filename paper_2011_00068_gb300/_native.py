@@ -28,6 +28,7 @@ LABS_FLAG_LEARNED = 4
 LABS_FLAG_WARP_PER_WALKER = 8
 LABS_FLAG_TWO_PER_WARP = 16
 LABS_FLAG_BEST_FIRST = 32
+LABS_FLAG_PSL = 64
 LABS_QUEUE_SIZE = 32
 LABS_BEST_FIRST_MAX_STEPS = 1 << 28
 LOG_RECORD_BYTES = 64
@@ -39,7 +40,7 @@ ERRORS = {LABS_EINVAL: "EINVAL", LABS_ENOMEM: "ENOMEM", LABS_ECUDA: "ECUDA", LAB
 EXPORTS = [
     "labs_default_config", "labs_init", "labs_init_multi", "labs_workspace_bytes", "labs_bind_workspace",
     "labs_reset", "labs_isl", "labs_neighbor_delta", "labs_walk", "labs_sync", "labs_best",
-    "labs_walker_results", "labs_stats", "labs_trace", "labs_enumerate_scratch_bytes", "labs_enumerate",
+    "labs_best_psl", "labs_walker_psl", "labs_walker_results", "labs_stats", "labs_trace", "labs_enumerate_scratch_bytes", "labs_enumerate",
     "labs_enumerate_noalloc", "labs_net_sizes", "labs_net_init", "labs_net_forward", "labs_net_gradients",
     "labs_net_adamw", "labs_log", "labs_log_labels", "labs_features", "labs_learned_workspace_bytes",
     "labs_learned", "labs_trace_learned", "labs_checkpoint", "labs_restore", "labs_set_deadline", "labs_cancel", "labs_clear_stop",
@@ -58,7 +59,7 @@ class LabsCounters(ctypes.Structure):
                 ("overflows", ctypes.c_int64), ("blocked", ctypes.c_int64), ("best_isl", ctypes.c_int32),
                 ("best_L", ctypes.c_int32), ("best_walker", ctypes.c_int64), ("target_step", ctypes.c_int64),
                 ("walkers_at_target", ctypes.c_int64), ("walkers_per_warp", ctypes.c_int32),
-                ("lane_block", ctypes.c_int32)]
+                ("lane_block", ctypes.c_int32), ("best_psl", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class LabsError(RuntimeError):
@@ -106,6 +107,8 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
             "labs_walk": (ctypes.c_int, [P, i64]),
             "labs_sync": (ctypes.c_int, [P]),
             "labs_best": (ctypes.c_int, [P, i32, P, P, P, P, ctypes.c_char_p]),
+            "labs_best_psl": (ctypes.c_int, [P, i32, P, P, P, P, ctypes.c_char_p]),
+            "labs_walker_psl": (ctypes.c_int, [P, i64, i64, P, P]),
             "labs_walker_results": (ctypes.c_int, [P, i64, i64, P, P, P, P, P]),
             "labs_stats": (ctypes.c_int, [P, i32, ctypes.POINTER(LabsCounters)]),
             "labs_trace": (ctypes.c_int, [P, P, i32, i64, P, P]),

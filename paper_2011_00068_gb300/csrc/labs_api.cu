@@ -126,7 +126,7 @@ KParams params(labs_ctx* c)
     p.best_first = (c->cfg.flags & LABS_FLAG_BEST_FIRST) ? 1 : 0;
     p.pq_key = p.best_first ? at<uint64_t>(c, c->off_pq_key) : nullptr;
     p.pq_bits = p.best_first ? at<uint32_t>(c, c->off_pq_bits) : nullptr;
-    p.mode = p.best_first ? 2 : (c->l_params ? 1 : 0);
+    p.mode = (c->cfg.flags & LABS_FLAG_PSL) ? 3 : p.best_first ? 2 : (c->l_params ? 1 : 0);
     return p;
 }
 
@@ -184,6 +184,8 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     if (nL < 1 || nL > LABS_MAX_GROUPS) return fail(c, LABS_EINVAL, "need 1..%d lengths", LABS_MAX_GROUPS);
     if ((k.flags & LABS_FLAG_BEST_FIRST) && (k.flags & LABS_FLAG_LEARNED))
         return fail(c, LABS_EINVAL, "LABS_FLAG_BEST_FIRST and LABS_FLAG_LEARNED do not combine");
+    if ((k.flags & LABS_FLAG_PSL) && (k.flags & (LABS_FLAG_BEST_FIRST | LABS_FLAG_LEARNED)))
+        return fail(c, LABS_EINVAL, "LABS_FLAG_PSL combines with neither LABS_FLAG_BEST_FIRST nor LABS_FLAG_LEARNED");
     c->seed = seed;
     c->stream = (cudaStream_t)stream;
     c->nG = nL;
@@ -247,7 +249,7 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     // than two per warp there, equal from n = 88 to 104), two walkers per warp (16 lanes
     // each) up to 10 outputs per lane (n <= 160), else one walker per warp (the learned
     // mode runs one walker per warp)
-    if ((k.flags & (LABS_FLAG_WARP_PER_WALKER | LABS_FLAG_LEARNED | LABS_FLAG_BEST_FIRST)) ||
+    if ((k.flags & (LABS_FLAG_WARP_PER_WALKER | LABS_FLAG_LEARNED | LABS_FLAG_BEST_FIRST | LABS_FLAG_PSL)) ||
         lanes_for(c->n_max, 16) > 10)
         c->tile = 32;
     else if (!(k.flags & LABS_FLAG_TWO_PER_WARP) && lanes_for(c->n_max, 8) <= kQuadMaxR)
@@ -259,7 +261,8 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     for (;;) {
         c->smem_bytes = per_warp * (size_t)warps;
         int occ = 0;
-        if (walk_kernel_config(c->tile, lanes_for(c->n_max, c->tile), (k.flags & LABS_FLAG_BEST_FIRST) ? 2 : 0, warps,
+        const int mode = (k.flags & LABS_FLAG_PSL) ? 3 : (k.flags & LABS_FLAG_BEST_FIRST) ? 2 : 0;
+        if (walk_kernel_config(c->tile, lanes_for(c->n_max, c->tile), mode, warps,
                                c->smem_bytes, &occ, &c->regs) ==
                 LABS_OK &&
             occ > 0) {
@@ -587,14 +590,15 @@ int labs_sync(labs_ctx* c)
     return sync_status(c);
 }
 
-int labs_best(labs_ctx* c, int32_t L, int8_t* host_seq_out, int32_t* isl, double* F, int32_t* L_out,
-              char* hex_out)
+// The walker with the best sequence among walkers of length L (0: all): lowest best
+// ISL, or under the PSL objective lowest (best PSL, best ISL); ties to the lowest id.
+static int best_state(labs_ctx* c, int32_t L, WalkerState* out)
 {
     int rc = need_ws(c);
     if (rc) return rc;
     cudaSetDevice(c->device);
     DevStatus* st = at<DevStatus>(c, c->off_status);
-    cudaError_t e = cudaMemsetAsync(&st->best_key, 0xFF, sizeof(st->best_key), c->stream);
+    cudaError_t e = cudaMemsetAsync(&st->best_key, 0xFF, sizeof(st->best_key) + sizeof(st->best_obj), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "best reset");
     rc = launch_best(params(c), L, c->stream);
     if (rc) return fail(c, rc, "best launch");
@@ -605,17 +609,67 @@ int labs_best(labs_ctx* c, int32_t L, int8_t* host_seq_out, int32_t* isl, double
     if (e != cudaSuccess) return cuda_fail(c, e, "best read");
     if (key == ~0ull) return fail(c, LABS_EINVAL, "no walker of length %d", L);
     const int64_t w = (int64_t)(key & 0xFFFFFFFFull);
-    WalkerState ws;
-    e = cudaMemcpy(&ws, at<WalkerState>(c, c->off_states) + w, sizeof(ws), cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(out, at<WalkerState>(c, c->off_states) + w, sizeof(*out), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "best state read");
+    return LABS_OK;
+}
+
+static void best_outputs(const labs_ctx* c, const WalkerState& ws, int8_t* host_seq_out, int32_t* L_out,
+                         char* hex_out)
+{
     const int Lw = c->groups[ws.group].L;
     std::vector<int8_t> seq((size_t)Lw);
     expand_bits(ws.best, Lw, seq.data());
     if (host_seq_out) memcpy(host_seq_out, seq.data(), (size_t)Lw);
-    if (isl) *isl = ws.best_isl;
-    if (F) *F = (double)Lw * Lw / (2.0 * ws.best_isl);
     if (L_out) *L_out = Lw;
     if (hex_out) hex_of(seq.data(), Lw, hex_out);
+}
+
+int labs_best(labs_ctx* c, int32_t L, int8_t* host_seq_out, int32_t* isl, double* F, int32_t* L_out,
+              char* hex_out)
+{
+    WalkerState ws;
+    const int rc = best_state(c, L, &ws);
+    if (rc) return rc;
+    const int Lw = c->groups[ws.group].L;
+    best_outputs(c, ws, host_seq_out, L_out, hex_out);
+    if (isl) *isl = ws.best_isl;
+    if (F) *F = (double)Lw * Lw / (2.0 * ws.best_isl);
+    return LABS_OK;
+}
+
+int labs_best_psl(labs_ctx* c, int32_t L, int8_t* host_seq_out, int32_t* psl, int32_t* isl, int32_t* L_out,
+                  char* hex_out)
+{
+    if (c && !(c->cfg.flags & LABS_FLAG_PSL)) return fail(c, LABS_EINVAL, "context created without LABS_FLAG_PSL");
+    WalkerState ws;
+    const int rc = best_state(c, L, &ws);
+    if (rc) return rc;
+    best_outputs(c, ws, host_seq_out, L_out, hex_out);
+    if (psl) *psl = ws.best_psl;
+    if (isl) *isl = ws.best_isl;
+    return LABS_OK;
+}
+
+int labs_walker_psl(labs_ctx* c, int64_t first, int64_t count, int32_t* host_psl, int32_t* host_best_psl)
+{
+    int rc = need_ws(c);
+    if (rc) return rc;
+    if (!(c->cfg.flags & LABS_FLAG_PSL)) return fail(c, LABS_EINVAL, "context created without LABS_FLAG_PSL");
+    if (first < 0 || count < 0 || first + count > c->W) return fail(c, LABS_EINVAL, "walker range out of bounds");
+    cudaSetDevice(c->device);
+    rc = sync_status(c);
+    if (rc) return rc;
+    std::vector<WalkerState> v((size_t)count);
+    if (count) {
+        cudaError_t e = cudaMemcpy(v.data(), at<WalkerState>(c, c->off_states) + first, sizeof(WalkerState) * count,
+                                   cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "walker state read");
+    }
+    for (int64_t j = 0; j < count; ++j) {
+        if (host_psl) host_psl[j] = v[j].psl;
+        if (host_best_psl) host_best_psl[j] = v[j].best_psl;
+    }
     return LABS_OK;
 }
 
@@ -661,6 +715,7 @@ int labs_stats(labs_ctx* c, int32_t L, labs_counters* out)
     cudaError_t e = cudaMemcpy(&h, st, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "status read");
     h.best_key = ~0ull;
+    h.best_obj = ~0ull;
     h.st_steps = h.st_evals = h.st_restarts = h.st_overflows = h.st_blocked = h.st_at_target = 0;
     h.st_target_step = LLONG_MAX;
     e = cudaMemcpy(st, &h, sizeof(h), cudaMemcpyHostToDevice);
@@ -680,6 +735,7 @@ int labs_stats(labs_ctx* c, int32_t L, labs_counters* out)
     out->walkers_per_warp = kWarp / c->tile;
     out->lane_block = lanes_for(c->n_max, c->tile);
     out->target_step = h.st_target_step == LLONG_MAX ? -1 : (int64_t)h.st_target_step;
+    out->best_psl = -1;
     if (h.best_key == ~0ull) {
         out->best_isl = -1;
         out->best_L = 0;
@@ -690,6 +746,7 @@ int labs_stats(labs_ctx* c, int32_t L, labs_counters* out)
         WalkerState ws;
         cudaMemcpy(&ws, at<WalkerState>(c, c->off_states) + out->best_walker, sizeof(ws), cudaMemcpyDeviceToHost);
         out->best_L = c->groups[ws.group].L;
+        if (c->cfg.flags & LABS_FLAG_PSL) out->best_psl = ws.best_psl;
     }
     return LABS_OK;
 }
@@ -722,6 +779,8 @@ int labs_log(labs_ctx* c, labs_log_record* dev_records, int64_t capacity)
     int rc = need_ws(c);
     if (rc) return rc;
     if (capacity < 0 || (capacity > 0 && !dev_records)) return fail(c, LABS_EINVAL, "bad log buffer");
+    if (capacity > 0 && (c->cfg.flags & (LABS_FLAG_BEST_FIRST | LABS_FLAG_PSL)))
+        return fail(c, LABS_EINVAL, "the walk log records the plain walk only");
     cudaSetDevice(c->device);
     c->log = capacity > 0 ? dev_records : nullptr;
     c->log_capacity = capacity;
@@ -833,7 +892,8 @@ int labs_checkpoint(labs_ctx* c, int with_tabu, void* host_buf, size_t* bytes)
     rc = sync_status(c);
     if (rc) return rc;
     uint64_t h[8] = {kCkptMagic, (uint64_t)c->W, (uint64_t)c->nG, (uint64_t)c->cfg.tabu_log2,
-                     (uint64_t)(with_tabu ? 1 : 0), (uint64_t)c->planned, c->seed, 0};
+                     (uint64_t)(with_tabu ? 1 : 0), (uint64_t)c->planned, c->seed,
+                     (uint64_t)(c->cfg.flags & LABS_FLAG_PSL)};
     memcpy(host_buf, h, sizeof(h));
     char* dst = (char*)host_buf + hdr;
     cudaError_t e = cudaMemcpy(dst, c->ws + c->off_states, sbytes, cudaMemcpyDeviceToHost);
@@ -852,7 +912,7 @@ int labs_restore(labs_ctx* c, const void* host_buf, size_t bytes)
     uint64_t h[8];
     memcpy(h, host_buf, sizeof(h));
     if (h[0] != kCkptMagic || h[1] != (uint64_t)c->W || h[2] != (uint64_t)c->nG ||
-        h[3] != (uint64_t)c->cfg.tabu_log2 || h[6] != c->seed)
+        h[3] != (uint64_t)c->cfg.tabu_log2 || h[6] != c->seed || h[7] != (uint64_t)(c->cfg.flags & LABS_FLAG_PSL))
         return fail(c, LABS_EINVAL, "checkpoint does not match this context");
     const size_t sbytes = sizeof(WalkerState) * (size_t)c->W;
     const size_t tbytes = h[4] ? sizeof(uint64_t) * ((size_t)c->W << c->cfg.tabu_log2) : 0;

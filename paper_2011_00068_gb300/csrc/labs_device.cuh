@@ -542,11 +542,37 @@ __device__ __forceinline__ bool target_met(const KParams& p, int L, int isl)
     return (int64_t)p.target_den * L * L >= 2 * (int64_t)p.target_num * isl;
 }
 
-template <class TL>
-__device__ __forceinline__ void note_best(const WalkEnv& env, Walker& w, const TL& t)
+// PSL objective: the current sequence's PSL, and the PSL halves of the (PSL, ISL)
+// pairs of the best sequence and of the best since the last (re)start.
+struct PslTrack {
+    int psl, best_psl, since_psl;
+};
+
+// Lower (PSL, ISL) pair, compared lexicographically.
+__device__ __forceinline__ bool psl_better(int psl, int isl, int psl0, int isl0)
 {
-    if (w.isl < w.best_isl) {
+    return psl < psl0 || (psl == psl0 && isl < isl0);
+}
+
+// max |C_{2m}| over m = 1..n-1 from the table: the PSL of a skew-symmetric sequence
+// (Section 1; its odd-lag C_k vanish).
+template <class TL>
+__device__ __forceinline__ int table_psl(const View& V, int n, const TL& t)
+{
+    int mx = 0;
+    for (int m = 1 + t.lane; m < n; m += TL::kSize) mx = max(mx, abs(__float2int_rn(V.G[m].x)));
+    return t.rmax(mx);
+}
+
+// Best-sequence update: strictly lower ISL, or under the PSL objective (ps != null) a
+// strictly lower (PSL, ISL) pair.
+template <class TL>
+__device__ __forceinline__ void note_best(const WalkEnv& env, Walker& w, const TL& t, PslTrack* ps = nullptr)
+{
+    const bool better = ps ? psl_better(ps->psl, w.isl, ps->best_psl, w.best_isl) : w.isl < w.best_isl;
+    if (better) {
         w.best_isl = w.isl;
+        if (ps) ps->best_psl = ps->psl;
         w.best_step = w.steps;
         if (t.lane < kBitWords) env.st->best[t.lane] = w.word;
     }
@@ -557,7 +583,7 @@ __device__ __forceinline__ void note_best(const WalkEnv& env, Walker& w, const T
 // insert it into HT (a fresh generation: its home slot is free), best update.
 template <class TL>
 __device__ void start_walker(const WalkEnv& env, Walker& w, int* base, const WarpSmem& SL, const View& V,
-                             const TL& t, bool proposed = false)
+                             const TL& t, bool proposed = false, PslTrack* ps = nullptr)
 {
     const int lane = t.lane;
     if (proposed) {
@@ -583,12 +609,16 @@ __device__ void start_walker(const WalkEnv& env, Walker& w, int* base, const War
     t.sync();
     w.since = w.isl;
     w.stag = 0;
-    note_best(env, w, t);
+    if (ps) {
+        ps->psl = table_psl(V, env.n, t);
+        ps->since_psl = ps->psl;
+    }
+    note_best(env, w, t, ps);
 }
 
 template <class TL>
 __device__ void restart_walker(const WalkEnv& env, Walker& w, int* base, const WarpSmem& SL, const View& V,
-                               const TL& t)
+                               const TL& t, PslTrack* ps = nullptr)
 {
     w.restart_idx += 1;
     w.restarts += 1;
@@ -602,7 +632,7 @@ __device__ void restart_walker(const WalkEnv& env, Walker& w, int* base, const W
     int prop = 0;
     if (t.lane == 0 && env.slot_valid != nullptr) prop = *env.slot_valid != 0;
     const bool proposed = t.shfl(prop, 0) != 0;
-    start_walker(env, w, base, SL, V, t, proposed);
+    start_walker(env, w, base, SL, V, t, proposed, ps);
 }
 
 // Stop requests from the host-written control block (mapped host memory, slow to
@@ -690,6 +720,44 @@ __device__ __forceinline__ int score_key(float f)
 {
     const int k = __float_as_int(f);
     return k >= 0 ? k : (k ^ 0x7FFFFFFF);
+}
+
+// S <- S_f for free variable bi: the table E (C_{2m} += -4 s_i (s_{i-2m} + s_{i+2m}),
+// the mirror's own term left out, -2 s_c (..) at the centre), P and the two row
+// entries, all from the values before the flip.  Ends without a tile barrier.
+template <class TL, int R>
+__device__ __forceinline__ void flip_rows_table(const View& V, int n, const Outs<TL, R>& o, float (&P)[R], int bi,
+                                                const TL& t)
+{
+    const int lane = t.lane, c = n - 1;
+    const int pb = bi & 1, vb = bi >> 1;
+    float* Ab = pb ? V.A1 : V.A0;
+    const float as = Ab[vb];
+    const bool centre = bi == c;
+    const int vq = n - 1 - vb - pb;
+    float dd[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {  // lags 2m, m = lane+1+TILE k < n (n <= TILE R)
+        const int m = lane + 1 + TL::kSize * k;
+        dd[k] = 0.f;
+        if (m < n) {
+            float up = Ab[vb + m];
+            if (!centre && vb + m == vq) up = 0.f;
+            const float dn = Ab[vb - m];
+            dd[k] = ((centre ? -2.f : -4.f) * as) * (up + dn);
+        }
+    }
+    p_update(V, n, o, P, pb, vb, centre ? -1 : vq);
+    t.sync();
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int m = lane + 1 + TL::kSize * k;
+        if (m < n) set_E(V, m, V.G[m].x + dd[k]);
+    }
+    if (lane == 0) {
+        Ab[vb] = -as;
+        if (!centre) Ab[vq] = -Ab[vq];
+    }
 }
 
 // What a walk call records besides the trajectory.
@@ -864,35 +932,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
             p_direct(V, n, o, P);
             code = LABS_TRACE_BLOCKED;
         } else {
-            // S <- S_f: table, P and rows (all from the values before the flip).
-            const int pb = best_i & 1, vb = best_i >> 1;
-            float* Ab = pb ? V.A1 : V.A0;
-            const float as = Ab[vb];
-            const bool centre = best_i == c;
-            const int vq = n - 1 - vb - pb;
-            float dd[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) {  // lags 2m, m = lane+1+TILE k < n (n <= TILE R)
-                const int m = lane + 1 + TL::kSize * k;
-                dd[k] = 0.f;
-                if (m < n) {
-                    float up = Ab[vb + m];
-                    if (!centre && vb + m == vq) up = 0.f;
-                    const float dn = Ab[vb - m];
-                    dd[k] = ((centre ? -2.f : -4.f) * as) * (up + dn);
-                }
-            }
-            p_update(V, n, o, P, pb, vb, centre ? -1 : vq);
-            t.sync();
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                const int m = lane + 1 + TL::kSize * k;
-                if (m < n) set_E(V, m, V.G[m].x + dd[k]);
-            }
-            if (lane == 0) {
-                Ab[vb] = -as;
-                if (!centre) Ab[vq] = -Ab[vq];
-            }
+            flip_rows_table(V, n, o, P, best_i, t);
             const bool stored = slot >= 0;
             if (lane == 0 && stored) env.T[slot] = (fnew & ~kGenMask) | w.gen;
             if (lane == (best_i >> 5)) w.word ^= 1u << (best_i & 31);
@@ -1530,6 +1570,162 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
 // whose n needs a smaller block run with RMAX-2, which covers them (any R >=
 // block_R(n) computes the same values).  MODE picks the step: 0 the plain walk, 1 the
 // learned mode, 2 the best-first search (one variant per kernel keeps the code small).
+// ------------------------------------------------------------ PSL objective walk
+
+// PSL of every neighbour S_i for the lane's outputs i = 2(v0+r)+p: flipping s_i and its
+// mirror s_{L-1-i} changes C_{2m} by -4 s_i (s_{i-2m} + s_{i+2m}) with the mirror's own
+// term (i+2m = L-1-i, m = c-i) left out, or by -2 s_c (s_{c-2m} + s_{c+2m}) at the
+// centre; the odd-lag C_k stay zero.  pl[r] = max_m |C_{2m} + dC_{2m}| (Section 1's
+// PSL), m = 1..n-1.  The class entries s_{i-2m} = A_p[v-m] and s_{i+2m} = A_p[v+m] sit
+// in two register windows of R values that slide by one entry per m, so that each m
+// costs three shared loads (two window entries and C_{2m}) for R outputs; the windows
+// are ring buffers indexed modulo R, with m stepping through blocks of R.  Exact in
+// fp32: every value is an integer of magnitude below 2^10.
+template <int R>
+__device__ __forceinline__ void psl_eval(const View& V, int n, const Outs<Tile<32>, R>& o, int (&pl)[R])
+{
+    const float* A = (o.p ? V.A1 : V.A0) + o.v0;
+    const int c = n - 1;
+    float cs[R], mx[R], lo[R], hi[R];
+    int q0[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = 2 * (o.v0 + r) + o.p;
+        cs[r] = (i == c ? -2.f : -4.f) * A[r];
+        q0[r] = c - i;
+        mx[r] = 0.f;
+    }
+    // lo[e mod R] = A[-e] for e = m-R+1 .. m, hi[e mod R] = A[e] for e = m .. m+R-1
+#pragma unroll
+    for (int k = 1; k < R; ++k) lo[k] = A[R - k];
+#pragma unroll
+    for (int e = 0; e + 1 < R; ++e) hi[e] = A[e];
+    for (int m0 = 0; m0 < n; m0 += R) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int m = m0 + j;
+            if (m >= n) break;
+            lo[j] = A[-m];
+            hi[(j + R - 1) % R] = A[m + R - 1];
+            if (m == 0) continue;
+            const float C = V.G[m].x;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float a = lo[(j - r + R) % R];
+                const float b = m == q0[r] ? 0.f : hi[(j + r) % R];
+                mx[r] = fmaxf(mx[r], fabsf(fmaf(cs[r], a + b, C)));
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) pl[r] = (int)mx[r];
+}
+
+// The walk under the PSL objective, one walker per warp: evaluate all n flips (dISL by
+// the Toeplitz step of the plain walk, PSL by psl_eval), move to the lowest
+// (PSL, ISL, i) whose result is not in HT, and keep the best sequence, the stagnation
+// count and the restarts on (PSL, ISL) pairs; HT and the restart rules are the walk's.
+template <int R>
+__device__ void walk_psl(const WalkEnv& env, Walker& w, PslTrack& ps, int64_t until, int* base, const WarpSmem& SL,
+                         const View& V, int trace_slot, int64_t trace_start, const Tile<32>& t)
+{
+    using TL = Tile<32>;
+    const KParams& p = *env.p;
+    const int lane = t.lane, n = env.n;
+    const Outs<TL, R> o(t);
+    const int cap = p.probe_cap;
+    float P[R];
+    p_direct(V, n, o, P);
+    StopCheck stop;
+    stop.start(p, lane == 0);
+    while (w.steps < until) {
+        if ((w.steps & (kCheckEvery - 1)) == 0) {
+            const int why = t.shfl(stop.poll(p, lane == 0), 0);
+            if (why) {
+                if (lane == 0) raise_error(p.status, why, (int)env.g);
+                break;
+            }
+        }
+        int dl[R], pl[R];
+        {
+            float X[R];
+            toeplitz(V, n, o, X);
+            assemble(V, n, o, X, P, dl);
+        }
+        psl_eval(V, n, o, pl);
+        // key = PSL' << 40 | ISL' << 8 | i (PSL' < 2^9, ISL' < 2^26 for L <= 511)
+        uint64_t key[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            key[r] = dl[r] == INT_MAX ? ~0ull
+                                      : ((uint64_t)pl[r] << 40) | ((uint64_t)(uint32_t)(w.isl + dl[r]) << 8) |
+                                            (uint64_t)(2 * (o.v0 + r) + o.p);
+        uint32_t excl = 0;
+        int best_i = -1;
+        uint64_t best_key = 0, fnew = 0;
+        int64_t slot = -1;
+        for (;;) {
+            uint64_t lm = ~0ull;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (!((excl >> r) & 1u) && key[r] < lm) lm = key[r];
+            const uint64_t km = warp_min64(lm);
+            if (km == ~0ull) break;
+            const int bi = (int)(km & 0xFFu);
+            const uint64_t f = w.fp ^ __ldg(env.zk + bi);
+            const Probe pr = probe_full(env, f, w.gen, cap, t);
+            if (!pr.visited) {
+                best_i = bi;
+                best_key = km;
+                slot = pr.slot;
+                fnew = f;
+                break;
+            }
+            exclude<TL, R>(excl, bi, t);
+        }
+
+        w.steps += 1;
+        int code;
+        if (best_i < 0) {
+            w.blocked += 1;
+            restart_walker(env, w, base, SL, V, t, &ps);
+            p_direct(V, n, o, P);
+            code = LABS_TRACE_BLOCKED;
+        } else {
+            flip_rows_table(V, n, o, P, best_i, t);
+            const bool stored = slot >= 0;
+            if (lane == 0 && stored) env.T[slot] = (fnew & ~kGenMask) | w.gen;
+            if (lane == (best_i >> 5)) w.word ^= 1u << (best_i & 31);
+            t.sync();
+            w.fp = fnew;
+            w.isl = (int)((best_key >> 8) & 0xFFFFFFFFull);
+            ps.psl = (int)(best_key >> 40);
+            if (!stored) w.overflows += 1;
+            note_best(env, w, t, &ps);
+            if (psl_better(ps.psl, w.isl, ps.since_psl, w.since)) {
+                w.since = w.isl;
+                ps.since_psl = ps.psl;
+                w.stag = 0;
+            } else {
+                w.stag += 1;
+            }
+            code = best_i;
+            if (w.stag >= env.patience || !stored) {
+                restart_walker(env, w, base, SL, V, t, &ps);
+                p_direct(V, n, o, P);
+                code |= LABS_TRACE_RESTART;
+            }
+        }
+        if (trace_slot >= 0 && lane == 0) {
+            const int64_t s = w.steps - 1 - trace_start;
+            if (s >= 0 && s < p.status->trace_capacity) {
+                p.status->trace_code[trace_slot * p.status->trace_capacity + s] = code;
+                p.status->trace_isl[trace_slot * p.status->trace_capacity + s] = w.isl;
+            }
+        }
+    }
+}
+
 template <int TILE, int RMAX, int MODE>
 __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(KParams p, int chunk_index)
 {
@@ -1612,7 +1808,25 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(K
         // step of the plain walk
         constexpr int R2 = RMAX > 2 ? RMAX - 2 : 1;
         const bool full = RMAX <= 2 || block_R(G.n, TILE) >= RMAX;
-        if constexpr (MODE == 2) {
+        if constexpr (MODE == 3) {
+            PslTrack ps;
+            ps.psl = table_psl(V, G.n, t);
+            ps.best_psl = st->best_psl;
+            ps.since_psl = st->since_psl;
+            if (ps.psl != st->psl) {
+                if (t.lane == 0) raise_error(p.status, LABS_ESTATE, (int)wi);
+                continue;
+            }
+            if (full)
+                walk_psl<RMAX>(env, w, ps, until, base, SL, V, trace_slot, trace_start, t);
+            else
+                walk_psl<R2>(env, w, ps, until, base, SL, V, trace_slot, trace_start, t);
+            if (t.lane == 0) {
+                st->psl = ps.psl;
+                st->best_psl = ps.best_psl;
+                st->since_psl = ps.since_psl;
+            }
+        } else if constexpr (MODE == 2) {
             uint64_t* qk = p.pq_key + wi * LABS_QUEUE_SIZE;
             uint32_t* qb = p.pq_bits + wi * LABS_QUEUE_SIZE * kBitWords;
             if (full)

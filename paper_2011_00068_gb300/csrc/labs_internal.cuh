@@ -49,7 +49,10 @@ struct alignas(32) WalkerState {
     int32_t blocked;
     int32_t group;
     int32_t trace_slot;        // -1: not traced
-    int32_t pad_[5];
+    int32_t psl;               // PSL objective only: PSL of `cur`, of `best`, and the
+    int32_t best_psl;          // PSL of the best (PSL, ISL) pair since the last (re)start
+    int32_t since_psl;         // (whose ISL is since_best)
+    int32_t pad_[2];
 };
 static_assert(sizeof(WalkerState) == 160, "WalkerState layout");
 
@@ -64,6 +67,7 @@ struct alignas(256) DevStatus {
     int32_t* trace_isl;
     int64_t trace_capacity;
     unsigned long long best_key;  // (best_isl << 32) | walker, reduction target
+    unsigned long long best_obj;  // PSL objective: lowest (best_psl << 32) | best_isl
     // stats accumulators (labs_stats)
     unsigned long long st_steps, st_evals, st_restarts, st_overflows, st_blocked, st_at_target;
     long long st_target_step;     // min over walkers, LLONG_MAX = none
@@ -117,7 +121,8 @@ struct KParams {
     int32_t rmax;             // lane block of the walk kernel instantiation (block_R(n_max, tile))
     int32_t tile;             // lanes per walker: 32, 16 (two walkers per warp) or 8 (four)
     int32_t best_first;       // 1: best-first search (one walker per warp, queue below)
-    int32_t mode;             // walk kernel variant: 0 plain walk, 1 learned mode, 2 best-first
+    int32_t mode;             // walk kernel variant: 0 plain walk, 1 learned mode, 2 best-first,
+                              // 3 walk under the PSL objective
     uint64_t* pq_key;         // [W][LABS_QUEUE_SIZE] queue keys, ~0 = empty
     uint32_t* pq_bits;        // [W][LABS_QUEUE_SIZE][kBitWords] queue entries' free variables
     uint64_t seed;
@@ -188,6 +193,8 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
         int hi = (3 * n_max) / 2 + 2 > n_max + 8 ? (3 * n_max) / 2 + 2 : n_max + 8;
         if ((n_max + 1) / 2 + span > hi) hi = (n_max + 1) / 2 + span;
         if (3 * (tile / 2) * R > hi) hi = 3 * (tile / 2) * R;
+        // the PSL neighbourhood reads class entries up to v0 + n + R - 2 (v0 <= (tile/2 - 1) R)
+        if (n_max + (tile / 2) * R > hi) hi = n_max + (tile / 2) * R;
         const int lo = n_max > span ? n_max : span;
         w.apad = (lo + 3) & ~3;
         w.alen = w.apad + ((hi + 7) & ~7);
@@ -211,6 +218,7 @@ WalkFn walk_fn16b(int rmax);
 WalkFn walk_fn32(int rmax);   // one walker per warp: plain walk
 WalkFn walk_fn32l(int rmax);  // learned mode (labs_walk32l.cu)
 WalkFn walk_fn32b(int rmax);  // best-first search (labs_walk32b.cu)
+WalkFn walk_fn32p(int rmax);  // walk under the PSL objective (labs_walk32p.cu)
 
 // Launchers (labs_kernels.cu).
 int launch_zobrist(const KParams& p, uint64_t* zkeys, const DevGroup* host_groups, int nG,

@@ -49,12 +49,17 @@ __global__ void __launch_bounds__(512) reset_kernel(KParams p)
         w.best_isl = INT_MAX;
         w.best_step = 0;
         w.target_step = -1;
-        start_walker(env, w, base, SL, V, t);
+        PslTrack ps;
+        ps.best_psl = INT_MAX;
+        start_walker(env, w, base, SL, V, t, false, p.mode == 3 ? &ps : nullptr);
         save_walker(st, w, t.lane);
         if (p.best_first) p.pq_key[wi * LABS_QUEUE_SIZE + t.lane] = ~0ull;  // empty queue
         if (t.lane == 0) {
             st->group = gidx;
             st->trace_slot = -1;
+            st->psl = p.mode == 3 ? ps.psl : -1;
+            st->best_psl = p.mode == 3 ? ps.best_psl : -1;
+            st->since_psl = p.mode == 3 ? ps.since_psl : -1;
         }
         t.sync();
     }
@@ -370,12 +375,34 @@ __global__ void labels_kernel(const labs_log_record* __restrict__ rec, int64_t c
 
 // ------------------------------------------------------------ reductions, tracing
 
+// Objective of a walker's best sequence: its ISL, or (PSL << 32) | ISL under the PSL
+// objective.
+__device__ __forceinline__ unsigned long long best_objective(const KParams& p, const WalkerState& st)
+{
+    const unsigned long long isl = (uint32_t)st.best_isl;
+    return p.mode == 3 ? ((unsigned long long)(uint32_t)st.best_psl << 32) | isl : isl;
+}
+
+// Lowest objective over the walkers of length L (0: all), into status->best_obj.
+__global__ void best_obj_kernel(KParams p, int L)
+{
+    for (int64_t wi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; wi < p.W;
+         wi += (int64_t)gridDim.x * blockDim.x) {
+        const WalkerState& st = p.states[wi];
+        if (L != 0 && p.groups[st.group].L != L) continue;
+        atomicMin(&p.status->best_obj, best_objective(p, st));
+    }
+}
+
+// Lowest (best ISL, walker); under the PSL objective only among the walkers whose
+// objective equals status->best_obj (best_obj_kernel ran first).
 __global__ void best_kernel(KParams p, int L)
 {
     for (int64_t wi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; wi < p.W;
          wi += (int64_t)gridDim.x * blockDim.x) {
         const WalkerState& st = p.states[wi];
         if (L != 0 && p.groups[st.group].L != L) continue;
+        if (p.mode == 3 && best_objective(p, st) != p.status->best_obj) continue;
         const unsigned long long key = ((unsigned long long)(uint32_t)st.best_isl << 32) |
                                        (unsigned long long)(uint32_t)wi;
         atomicMin(&p.status->best_key, key);
@@ -398,6 +425,10 @@ __global__ void stats_kernel(KParams p, int L)
         if (st.target_step >= 0) {
             atomicAdd(&s->st_at_target, 1ull);
             atomicMin(&s->st_target_step, (long long)st.target_step);
+        }
+        if (p.mode == 3) {
+            atomicMin(&s->best_obj, best_objective(p, st));
+            continue;
         }
         const unsigned long long key = ((unsigned long long)(uint32_t)st.best_isl << 32) |
                                        (unsigned long long)(uint32_t)wi;
@@ -470,7 +501,12 @@ static WalkFn walk_fn(int tile, int rmax, int mode)
 {
     if (tile == 8) return rmax <= 6 ? walk_fn8a(rmax) : walk_fn8b(rmax);
     if (tile == 16) return rmax <= 5 ? walk_fn16a(rmax) : walk_fn16b(rmax);
-    return mode == 2 ? walk_fn32b(rmax) : mode == 1 ? walk_fn32l(rmax) : walk_fn32(rmax);
+    switch (mode) {
+        case 1: return walk_fn32l(rmax);
+        case 2: return walk_fn32b(rmax);
+        case 3: return walk_fn32p(rmax);
+        default: return walk_fn32(rmax);
+    }
 }
 
 int lanes_for(int n, int tile)
@@ -489,7 +525,8 @@ int walk_kernel_config(int tile, int rmax, int mode, int warps_per_cta, size_t s
                                                    (int)smem_bytes);
         if (e != cudaSuccess) return LABS_ECUDA;
     }
-    cudaError_t e;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return LABS_ECUDA;
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return LABS_ECUDA;
@@ -568,6 +605,7 @@ int launch_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, Dev
 
 int launch_best(const KParams& p, int32_t L, void* stream)
 {
+    if (p.mode == 3) best_obj_kernel<<<256, 256, 0, (cudaStream_t)stream>>>(p, L);
     best_kernel<<<256, 256, 0, (cudaStream_t)stream>>>(p, L);
     return status_of(cudaGetLastError());
 }
@@ -575,6 +613,7 @@ int launch_best(const KParams& p, int32_t L, void* stream)
 int launch_stats(const KParams& p, int32_t L, void* stream)
 {
     stats_kernel<<<256, 256, 0, (cudaStream_t)stream>>>(p, L);
+    if (p.mode == 3) best_kernel<<<256, 256, 0, (cudaStream_t)stream>>>(p, L);
     return status_of(cudaGetLastError());
 }
 
