@@ -42,6 +42,10 @@ def int32_equivalent(lag_terms_per_s, sms, sm_mhz):
     return {"lag_terms_per_s": lag_terms_per_s, "int32_mad_peak": peak, "frac": lag_terms_per_s / peak,
             "note": "lag terms per second over the int32 multiply-add rate (%d SMs x %d lanes x %.0f MHz)"
                     % (sms, INT32_MAD_LANES_PER_SM, sm_mhz)}
+# The PSL objective adds, per lag term of every flip, C' = C + cs (a + b) and max |C'|:
+# an add, an FMA and a max beside the Toeplitz FMA, i.e. four FP32 lane operations,
+# against the pipe's 128 lane operations per clock per SM.
+PSL_LANE_OPS_PER_LAG_TERM = 4
 WALK_KERNELS = {4: "walk_quad_kernel", 2: "walk_pair_kernel", 1: "walk_chunk_kernel"}  # by walkers per warp
 # DRAM bytes per walker step of the L=201 walk kernel (ncu: dram__bytes_read.sum +
 # dram__bytes_write.sum of a 4864-walker x 256-step launch of the current kernel,
@@ -69,8 +73,12 @@ def parse():
     ap.add_argument("--config", choices=["walk", "learned", "scaleup"], default="walk")
     ap.add_argument("--scaleup-walkers", type=int, default=131072)
     ap.add_argument("--scaleup-steps", type=int, default=20000)
-    ap.add_argument("--search", choices=["walk", "bestfirst"], default="walk",
-                    help="walk: the self-avoiding walk; bestfirst: Algorithm 1 as printed (queue of 32)")
+    ap.add_argument("--search", choices=["walk", "bestfirst", "psl"], default="walk",
+                    help="walk: the self-avoiding walk; bestfirst: Algorithm 1 as printed (queue of 32); "
+                         "psl: the walk under the PSL objective")
+    ap.add_argument("--cpu-steps-psl", type=int, default=600,
+                    help="oracle steps per walker of the CPU sample for --search psl (its oracle rebuilds "
+                         "every neighbour: O(L^3) per step)")
     ap.add_argument("--learned-L", type=int, default=255)
     ap.add_argument("--learned-walkers", type=int, default=32768)
     ap.add_argument("--learned-steps", type=int, default=20000)
@@ -154,23 +162,34 @@ def cpu_baseline(args):
     import oracle
 
     cores = os.cpu_count() or 1
+    steps = cpu_steps(args)
     t0 = time.perf_counter()
-    if args.search == "bestfirst":
-        oracle.bestfirst(args.L, args.seed, args.cpu_walkers, args.cpu_steps, tabu_log2=args.tabu_log2,
-                         nthreads=cores)
-    else:
-        oracle.walk(args.L, args.seed, args.cpu_walkers, args.cpu_steps, tabu_log2=args.tabu_log2, nthreads=cores)
+    oracle_run(args, steps, cores)
     dt = time.perf_counter() - t0
     n = (args.L + 1) // 2
-    flips = args.cpu_walkers * args.cpu_steps * n
+    flips = args.cpu_walkers * steps * n
     return {"value": flips / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "L=%d, %d walkers x %d steps (walkers 0..%d of the workload), %.2f s" %
-                      (args.L, args.cpu_walkers, args.cpu_steps, args.cpu_walkers - 1, dt)}
+                      (args.L, args.cpu_walkers, steps, args.cpu_walkers - 1, dt)}
+
+
+def cpu_steps(args):
+    return args.cpu_steps_psl if args.search == "psl" else args.cpu_steps
+
+
+def oracle_run(args, steps, cores):
+    import oracle
+
+    if args.search == "bestfirst":
+        oracle.bestfirst(args.L, args.seed, args.cpu_walkers, steps, tabu_log2=args.tabu_log2, nthreads=cores)
+    else:
+        oracle.walk(args.L, args.seed, args.cpu_walkers, steps, tabu_log2=args.tabu_log2, nthreads=cores,
+                    objective="psl" if args.search == "psl" else "isl")
 
 
 def config_of(args, world):
-    what = ("best-first search (Algorithm 1, queue of 32)" if args.search == "bestfirst"
-            else "self-avoiding walk")
+    what = {"bestfirst": "best-first search (Algorithm 1, queue of 32)",
+            "psl": "self-avoiding walk under the PSL objective"}.get(args.search, "self-avoiding walk")
     return {"workload": "L=%d skew-symmetric %s, %d walkers/GPU x %d steps, HT 2^%d slots/walker, "
                         "uniform random +-1 Philox starts, seed %d" % (args.L, what, args.walkers, args.walk_steps,
                                                                       args.tabu_log2, args.seed),
@@ -190,14 +209,11 @@ def run_reference(args):
     oracle.build()
     cores = os.cpu_count() or 1
     n = (args.L + 1) // 2
-    steps = args.cpu_steps
+    steps = cpu_steps(args)
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        if args.search == "bestfirst":
-            oracle.bestfirst(args.L, args.seed, args.cpu_walkers, steps, tabu_log2=args.tabu_log2, nthreads=cores)
-        else:
-            oracle.walk(args.L, args.seed, args.cpu_walkers, steps, tabu_log2=args.tabu_log2, nthreads=cores)
+        oracle_run(args, steps, cores)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
@@ -278,7 +294,7 @@ def run_ours(args):
     shape = {}
     from paper_2011_00068_gb300 import _native
 
-    flags = _native.LABS_FLAG_BEST_FIRST if args.search == "bestfirst" else 0
+    flags = {"bestfirst": _native.LABS_FLAG_BEST_FIRST, "psl": _native.LABS_FLAG_PSL}.get(args.search, 0)
     if not args.no_tune:
         from paper_2011_00068_gb300 import tune
 
@@ -331,18 +347,25 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = FP32_LANES_PER_SM * 2 * sms * sm_mhz * 1e6
     achieved = ops_per_launch / avg_launch_s
+    unit = "TFLOP/s"
+    if args.search == "psl":
+        # FP32 lane operations: PSL_LANE_OPS_PER_LAG_TERM per lag term, one per lane per clock
+        achieved *= PSL_LANE_OPS_PER_LAG_TERM / ALGO_FLOP_PER_LAG_TERM
+        peak /= 2
+        unit = "Tops/s (FP32 lane operations)"
     kernel = WALK_KERNELS[st["walkers_per_warp"]]
     steps_per_launch = args.walkers * args.walk_steps / nchunks
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": unit,
                 "frac": achieved / peak,
                 "traffic": (DRAM_BYTES_PER_WALKER_STEP * steps_per_launch
                             if args.L == 201 and args.search == "walk" and DRAM_BYTES_PER_WALKER_STEP else None),
                 "traffic_note": ("bytes per launch: %.1f B per walker step from one ncu capture of a small "
                                  "launch, scaled by walker steps" % DRAM_BYTES_PER_WALKER_STEP
-                                 if DRAM_BYTES_PER_WALKER_STEP else "not captured for this kernel version"),
+                                 if DRAM_BYTES_PER_WALKER_STEP and args.search == "walk" and args.L == 201
+                                 else "not captured for this kernel and workload"),
                 "kernel": kernel, "lane_block": st["lane_block"],
-                "peak_source": "derived: %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz (FMA pipe)" % (
-                    sms, FP32_LANES_PER_SM, sm_mhz)}
+                "peak_source": "derived: %d SMs x %d FP32 lanes x %s x %.0f MHz (FMA pipe)" % (
+                    sms, FP32_LANES_PER_SM, "1 op" if args.search == "psl" else "2 FLOP", sm_mhz)}
 
     e2e = None
     if not args.no_e2e:
@@ -362,7 +385,12 @@ def run_ours(args):
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h)}
 
     delta = None if args.no_delta else delta_kernel_line(args, dev, stream, labs)
-    best_isl, best_rank = replicas.best_over_ranks(st["best_isl"], device=dev)
+    if args.search == "psl":
+        # lowest (PSL, ISL) pair over ranks: PSL < 2^9 above ISL < 2^26 in one key
+        obj, best_rank = replicas.best_over_ranks((st["best_psl"] << 26) | st["best_isl"], device=dev)
+        best_isl, best_psl = obj & ((1 << 26) - 1), obj >> 26
+    else:
+        best_isl, best_rank = replicas.best_over_ranks(st["best_isl"], device=dev)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -376,7 +404,8 @@ def run_ours(args):
                 "clocks": clk.summary(), "e2e": e2e,
                 "gpu_launches": args.steps * (2 + nchunks),
                 "walk_ms_per_step": statistics.mean(walk_ms),
-                "best": {"isl": best_isl, "F": args.L ** 2 / (2 * best_isl), "L": st["best_L"], "rank": best_rank},
+                "best": dict({"isl": best_isl, "F": args.L ** 2 / (2 * best_isl), "L": st["best_L"],
+                              "rank": best_rank}, **({"psl": best_psl} if args.search == "psl" else {})),
                 "delta_kernel": delta,
                 "restarts": st["restarts"]}
         if world == 1 and not args.no_cpu_baseline:

@@ -80,7 +80,6 @@ class Search:
             raise ValueError("objective is 'isl' or 'psl'")
         if objective == "psl":
             cfg["flags"] = int(cfg.get("flags", 0)) | _native.LABS_FLAG_PSL
-        self.psl = objective == "psl"
         self.lib = library()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         if self.device.type != "cuda":
@@ -88,6 +87,7 @@ class Search:
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             self.cfg = config(**cfg)
+            self.psl = bool(self.cfg.flags & _native.LABS_FLAG_PSL)
             self.ctx = ctypes.c_void_p()
             if isinstance(L, (list, tuple)):
                 self.Ls = [int(x) for x in L]
