@@ -70,7 +70,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-delta", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--config", choices=["walk", "learned", "scaleup"], default="walk")
+    ap.add_argument("--config", choices=["walk", "learned", "scaleup", "long"], default="walk")
+    ap.add_argument("--long-walkers", type=int, default=608)
+    ap.add_argument("--long-steps", type=int, default=512)
     ap.add_argument("--scaleup-walkers", type=int, default=131072)
     ap.add_argument("--scaleup-steps", type=int, default=20000)
     ap.add_argument("--search", choices=["walk", "bestfirst", "psl"], default="walk",
@@ -499,10 +501,63 @@ def run_scaleup(args):
     return 0
 
 
+def run_long(args):
+    """Long sequences (one walker per CTA): L = 2047, 4095 and 8191, long_walkers
+    walkers x long_steps steps each: flips/s, the walk kernel's roofline fraction (one
+    FMA per lag term, as the warp kernels), best F; one JSON line."""
+    import torch
+
+    import paper_2011_00068_gb300 as labs
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = float(measured_peaks().get("sm_max_mhz", 2070.0))
+    peak = FP32_LANES_PER_SM * 2 * sms * sm_mhz * 1e6
+    out = {}
+    for L in (2047, 4095, 8191):
+        n = (L + 1) // 2
+        s = labs.Search(L, args.long_walkers, 42, device=dev)
+        s.walk(8)  # warm-up: graph capture, first touch of the tables
+        s.sync()
+        s.reset()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s.stream)
+        s.walk(args.long_steps)
+        b.record(s.stream)
+        s.sync()
+        ms = a.elapsed_time(b)
+        st = s.stats()
+        flips = st["flip_evaluations"] / (ms / 1e3)
+        best = s.best()
+        out[str(L)] = {"flips_per_s": flips, "ms": ms, "steps": args.long_steps, "walkers": args.long_walkers,
+                       "walker_steps_per_s": st["steps"] / (ms / 1e3), "best_isl": best["isl"],
+                       "best_F": best["F"], "lane_block": st["lane_block"],
+                       "roofline_frac": ALGO_FLOP_PER_LAG_TERM * (n - 1) * flips / peak}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    total = sum(v["flips_per_s"] * v["ms"] for v in out.values()) / sum(v["ms"] for v in out.values())
+    line = {"metric": "exact flip evaluations/sec, long sequences", "value": total, "unit": "flip evaluations/s",
+            "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic", "vs_baseline": None,
+            "config": {"workload": "L=2047, 4095 and 8191, %d walkers each (one per CTA of 512 threads), %d steps, "
+                                   "seed 42, uniform random +-1 Philox starts, HT 2^16 slots/walker"
+                                   % (args.long_walkers, args.long_steps),
+                       "kernel": "long_walk_kernel",
+                       "peak_source": "derived: %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz (FMA pipe)" % (
+                           sms, FP32_LANES_PER_SM, sm_mhz)},
+            "per_L": out}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "long":
+        return run_long(args)
     if args.config == "learned":
         return run_learned(args)
     if args.config == "scaleup":

@@ -25,7 +25,9 @@
  *     (a cudaStream_t passed as void*; NULL = the legacy default stream).  Errors
  *     detected on the device are reported by the next synchronising call
  *     (labs_sync, labs_best, labs_walker_results, labs_stats, labs_checkpoint).
- *   - Lengths: odd L with 3 <= L <= LABS_MAX_L.
+ *   - Lengths: odd L with 3 <= L <= LABS_MAX_L (walkers run one, two or four per warp),
+ *     or LABS_MAX_L < L <= LABS_MAX_L_LONG (long sequences: one walker per CTA of 512
+ *     threads, the same step rule); a context holds lengths of one kind only.
  *   - A context is not thread-safe; use one per host thread.
  */
 #ifndef LABS_H
@@ -45,8 +47,12 @@ extern "C" {
 #define LABS_ETIMEOUT (-4)   /* the deadline set by labs_set_deadline passed */
 #define LABS_ECANCELLED (-5) /* labs_cancel was called */
 #define LABS_ESTATE (-6)     /* a walker's stored state failed its consistency check */
+#define LABS_ERANGE (-7)     /* a long sequence left the range in which the library's fp32
+                                neighbourhood is exact (ISL above the bound stated at
+                                labs_walk); random starts and walks stay far below it */
 
 #define LABS_MAX_L 511       /* n = (L+1)/2 <= 256 free variables */
+#define LABS_MAX_L_LONG 8191 /* long sequences: n <= 4096 free variables */
 #define LABS_MAX_GROUPS 64   /* distinct lengths in one context */
 
 /* Step trace codes written by labs_trace (one int32 per walker step).  The walk writes

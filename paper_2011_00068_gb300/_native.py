@@ -18,7 +18,9 @@ LABS_ECUDA = -3
 LABS_ETIMEOUT = -4
 LABS_ECANCELLED = -5
 LABS_ESTATE = -6
+LABS_ERANGE = -7
 LABS_MAX_L = 511
+LABS_MAX_L_LONG = 8191
 LABS_MAX_GROUPS = 64
 LABS_TRACE_RESTART = 0x10000
 LABS_TRACE_BLOCKED = -1
@@ -34,7 +36,7 @@ LABS_BEST_FIRST_MAX_STEPS = 1 << 28
 LOG_RECORD_BYTES = 64
 
 ERRORS = {LABS_EINVAL: "EINVAL", LABS_ENOMEM: "ENOMEM", LABS_ECUDA: "ECUDA", LABS_ETIMEOUT: "ETIMEOUT",
-          LABS_ECANCELLED: "ECANCELLED", LABS_ESTATE: "ESTATE"}
+          LABS_ECANCELLED: "ECANCELLED", LABS_ESTATE: "ESTATE", LABS_ERANGE: "ERANGE"}
 
 # Every exported symbol of include/labs.h, in declaration order.
 EXPORTS = [

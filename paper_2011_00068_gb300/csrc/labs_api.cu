@@ -32,7 +32,8 @@ struct labs_ctx {
     // workspace layout (byte offsets)
     size_t off_status = 0, off_groups = 0, off_zkeys = 0, off_states = 0, off_trace_start = 0,
            off_trace_ids = 0, off_queue = 0, off_l_scores = 0, off_l_step = 0, off_l_slot = 0, off_l_valid = 0,
-           off_pq_key = 0, off_pq_bits = 0, off_tabu = 0, total = 0;
+           off_pq_key = 0, off_pq_bits = 0, off_cur_bits = 0, off_best_bits = 0, off_tabu = 0, total = 0;
+    bool long_mode = false;  // lengths above LABS_MAX_L: one walker per CTA, bits beside the states
     // device pointers kept in the status block (restored after every reset)
     labs_log_record* log = nullptr;
     int64_t log_capacity = 0, log_start = 0;
@@ -120,8 +121,11 @@ KParams params(labs_ctx* c)
     p.target_num = c->cfg.target_num;
     p.target_den = c->cfg.target_den;
     p.chunk_steps = c->chunk;
-    p.rmax = lanes_for(c->n_max, c->tile);
+    p.rmax = c->long_mode ? long_R(c->n_max) : lanes_for(c->n_max, c->tile);
     p.tile = c->tile;
+    p.long_mode = c->long_mode ? 1 : 0;
+    p.cur_bits = c->long_mode ? at<uint32_t>(c, c->off_cur_bits) : nullptr;
+    p.best_bits = c->long_mode ? at<uint32_t>(c, c->off_best_bits) : nullptr;
     p.seed = c->seed;
     p.best_first = (c->cfg.flags & LABS_FLAG_BEST_FIRST) ? 1 : 0;
     p.pq_key = p.best_first ? at<uint64_t>(c, c->off_pq_key) : nullptr;
@@ -133,6 +137,30 @@ KParams params(labs_ctx* c)
 bool valid_L(int32_t L)
 {
     return L >= 3 && L <= LABS_MAX_L && (L & 1) == 1;
+}
+
+bool valid_long_L(int32_t L)
+{
+    return L > LABS_MAX_L && L <= LABS_MAX_L_LONG && (L & 1) == 1;
+}
+
+// Free-variable bits of walker w's current (best = false) or best sequence.
+int walker_bits(labs_ctx* c, int64_t w, const WalkerState& ws, bool best, uint32_t* out)
+{
+    if (!c->long_mode) {
+        memcpy(out, best ? ws.best : ws.cur, sizeof(uint32_t) * kBitWords);
+        return LABS_OK;
+    }
+    const size_t off = (best ? c->off_best_bits : c->off_cur_bits) + sizeof(uint32_t) * kBitWordsLong * (size_t)w;
+    const cudaError_t e = cudaMemcpy(out, c->ws + off, sizeof(uint32_t) * kBitWordsLong, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? LABS_OK : cuda_fail(c, e, "walker bits read");
+}
+
+// One chunk launch of the walk kernel of this context.
+int launch_chunk(labs_ctx* c, const KParams& p, int j, cudaStream_t stream)
+{
+    if (c->long_mode) return launch_long_walk_chunk(p, j, c->grid, c->smem_bytes, stream);
+    return launch_walk_chunk(p, j, c->grid, c->warps_per_cta, c->smem_bytes, stream);
 }
 
 int need_ws(labs_ctx* c)
@@ -186,12 +214,19 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
         return fail(c, LABS_EINVAL, "LABS_FLAG_BEST_FIRST and LABS_FLAG_LEARNED do not combine");
     if ((k.flags & LABS_FLAG_PSL) && (k.flags & (LABS_FLAG_BEST_FIRST | LABS_FLAG_LEARNED)))
         return fail(c, LABS_EINVAL, "LABS_FLAG_PSL combines with neither LABS_FLAG_BEST_FIRST nor LABS_FLAG_LEARNED");
+    if (nL >= 1 && Ls && valid_long_L(Ls[0])) {
+        c->long_mode = true;
+        if (k.flags & (LABS_FLAG_BEST_FIRST | LABS_FLAG_LEARNED | LABS_FLAG_PSL))
+            return fail(c, LABS_EINVAL, "lengths above %d run the plain walk only", LABS_MAX_L);
+    }
     c->seed = seed;
     c->stream = (cudaStream_t)stream;
     c->nG = nL;
     int64_t first = 0, zoff = 0;
     for (int g = 0; g < nL; ++g) {
-        if (!valid_L(Ls[g])) return fail(c, LABS_EINVAL, "L=%d: need odd 3 <= L <= %d", Ls[g], LABS_MAX_L);
+        if (c->long_mode ? !valid_long_L(Ls[g]) : !valid_L(Ls[g]))
+            return fail(c, LABS_EINVAL, "L=%d: need odd 3 <= L <= %d, or odd %d < L <= %d (every length of a context "
+                        "on the same side)", Ls[g], LABS_MAX_L, LABS_MAX_L, LABS_MAX_L_LONG);
         if (counts[g] < 0) return fail(c, LABS_EINVAL, "negative walker count");
         DevGroup& G = c->groups[g];
         G.L = Ls[g];
@@ -219,6 +254,12 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     off = align_up(off + sizeof(uint64_t) * (size_t)zoff, 256);
     c->off_states = off;
     off = align_up(off + sizeof(WalkerState) * (size_t)c->W, 256);
+    if (c->long_mode) {
+        c->off_cur_bits = off;
+        off = align_up(off + sizeof(uint32_t) * kBitWordsLong * (size_t)c->W, 256);
+        c->off_best_bits = off;
+        off = align_up(off + sizeof(uint32_t) * kBitWordsLong * (size_t)c->W, 256);
+    }
     c->off_trace_start = off;
     off = align_up(off + sizeof(int64_t) * kMaxTrace, 256);
     c->off_trace_ids = off;
@@ -249,32 +290,45 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     // than two per warp there, equal from n = 88 to 104), two walkers per warp (16 lanes
     // each) up to 10 outputs per lane (n <= 160), else one walker per warp (the learned
     // mode runs one walker per warp)
-    if ((k.flags & (LABS_FLAG_WARP_PER_WALKER | LABS_FLAG_LEARNED | LABS_FLAG_BEST_FIRST | LABS_FLAG_PSL)) ||
-        lanes_for(c->n_max, 16) > 10)
-        c->tile = 32;
-    else if (!(k.flags & LABS_FLAG_TWO_PER_WARP) && lanes_for(c->n_max, 8) <= kQuadMaxR)
-        c->tile = 8;
-    else
-        c->tile = 16;
-    const size_t per_warp = (size_t)warp_smem(c->n_max, c->tile).words * sizeof(int) * (kWarp / c->tile);
-    int warps = k.warps_per_cta ? k.warps_per_cta : 8;
-    for (;;) {
-        c->smem_bytes = per_warp * (size_t)warps;
+    if (c->long_mode) {
+        // one walker per CTA of kLongThreads threads
+        c->tile = kLongThreads;
+        c->smem_bytes = (size_t)long_smem(c->n_max).words * sizeof(int);
         int occ = 0;
-        const int mode = (k.flags & LABS_FLAG_PSL) ? 3 : (k.flags & LABS_FLAG_BEST_FIRST) ? 2 : 0;
-        if (walk_kernel_config(c->tile, lanes_for(c->n_max, c->tile), mode, warps,
-                               c->smem_bytes, &occ, &c->regs) ==
-                LABS_OK &&
-            occ > 0) {
-            c->ctas_per_sm = occ;
-            break;
+        if (long_kernel_config(long_R(c->n_max), c->smem_bytes, &occ, &c->regs) != LABS_OK || occ < 1)
+            return fail(c, LABS_ECUDA, "long walk kernel does not fit on an SM (%zu bytes of shared memory)",
+                        c->smem_bytes);
+        c->ctas_per_sm = occ;
+        c->warps_per_cta = kLongThreads / kWarp;
+        c->grid = c->sms * c->ctas_per_sm;
+        c->chunk = k.chunk_steps ? k.chunk_steps : 64;
+    } else {
+        if ((k.flags & (LABS_FLAG_WARP_PER_WALKER | LABS_FLAG_LEARNED | LABS_FLAG_BEST_FIRST | LABS_FLAG_PSL)) ||
+            lanes_for(c->n_max, 16) > 10)
+            c->tile = 32;
+        else if (!(k.flags & LABS_FLAG_TWO_PER_WARP) && lanes_for(c->n_max, 8) <= kQuadMaxR)
+            c->tile = 8;
+        else
+            c->tile = 16;
+        const size_t per_warp = (size_t)warp_smem(c->n_max, c->tile).words * sizeof(int) * (kWarp / c->tile);
+        int warps = k.warps_per_cta ? k.warps_per_cta : 8;
+        for (;;) {
+            c->smem_bytes = per_warp * (size_t)warps;
+            int occ = 0;
+            const int mode = (k.flags & LABS_FLAG_PSL) ? 3 : (k.flags & LABS_FLAG_BEST_FIRST) ? 2 : 0;
+            if (walk_kernel_config(c->tile, lanes_for(c->n_max, c->tile), mode, warps, c->smem_bytes, &occ,
+                                   &c->regs) == LABS_OK &&
+                occ > 0) {
+                c->ctas_per_sm = occ;
+                break;
+            }
+            if (warps == 1) return fail(c, LABS_ECUDA, "walk kernel does not fit on an SM");
+            warps /= 2;
         }
-        if (warps == 1) return fail(c, LABS_ECUDA, "walk kernel does not fit on an SM");
-        warps /= 2;
+        c->warps_per_cta = warps;
+        c->grid = c->sms * c->ctas_per_sm;
+        c->chunk = k.chunk_steps ? k.chunk_steps : 1024;
     }
-    c->warps_per_cta = warps;
-    c->grid = c->sms * c->ctas_per_sm;
-    c->chunk = k.chunk_steps ? k.chunk_steps : 1024;
     e = cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamCreate");
     e = cudaHostAlloc((void**)&c->ctrl_host, sizeof(Control), cudaHostAllocMapped);
@@ -400,8 +454,7 @@ int graph_for(labs_ctx* c, int nchunks, cudaGraphExec_t* exec)
     cudaError_t e = cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
     int rc = LABS_OK;
-    for (int j = 0; j < nchunks && rc == LABS_OK; ++j)
-        rc = launch_walk_chunk(p, j, c->grid, c->warps_per_cta, c->smem_bytes, c->capture);
+    for (int j = 0; j < nchunks && rc == LABS_OK; ++j) rc = launch_chunk(c, p, j, c->capture);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(c->capture, &g);
     if (rc != LABS_OK || e != cudaSuccess) {
@@ -469,7 +522,10 @@ int labs_reset(labs_ctx* c)
         e = cudaMemsetAsync(c->ws + c->off_tabu, 0, c->total - c->off_tabu, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "workspace clear");
     const KParams p = params(c);
-    if (c->W > 0) {
+    if (c->W > 0 && c->long_mode) {
+        rc = launch_long_reset(p, c->smem_bytes, c->stream);
+        if (rc) return fail(c, rc, "reset launch: %s", cudaGetErrorString(cudaGetLastError()));
+    } else if (c->W > 0) {
         const int block = 8 * kWarp;
         const int64_t need = (c->W + 7) / 8;
         const int grid = (int)std::min<int64_t>(need, (int64_t)c->sms * 4);
@@ -532,7 +588,8 @@ int labs_neighbor_delta(labs_ctx* c, const int8_t* dev_seqs, int64_t batch, int3
     if (batch < 0 || (batch > 0 && (!dev_seqs || !dev_delta_out))) return fail(c, LABS_EINVAL, "bad batch");
     cudaSetDevice(c->device);
     DevStatus* st = c->ws ? at<DevStatus>(c, c->off_status) : nullptr;
-    const int rc = launch_delta(dev_seqs, batch, c->groups[0].L, dev_delta_out, st, c->stream);
+    const int rc = c->long_mode ? launch_long_delta(dev_seqs, batch, c->groups[0].L, dev_delta_out, st, c->stream)
+                                : launch_delta(dev_seqs, batch, c->groups[0].L, dev_delta_out, st, c->stream);
     return rc ? fail(c, rc, "labs_neighbor_delta launch: %s", cudaGetErrorString(cudaGetLastError())) : LABS_OK;
 }
 
@@ -562,7 +619,7 @@ int labs_walk(labs_ctx* c, int64_t steps)
                     rc = proposal_pass(c);
                     if (rc) return rc;
                 }
-                rc = launch_walk_chunk(p, j, c->grid, c->warps_per_cta, c->smem_bytes, c->stream);
+                rc = launch_chunk(c, p, j, c->stream);
                 if (rc) return fail(c, rc, "walk launch: %s", cudaGetErrorString(cudaGetLastError()));
             }
         } else {
@@ -592,7 +649,7 @@ int labs_sync(labs_ctx* c)
 
 // The walker with the best sequence among walkers of length L (0: all): lowest best
 // ISL, or under the PSL objective lowest (best PSL, best ISL); ties to the lowest id.
-static int best_state(labs_ctx* c, int32_t L, WalkerState* out)
+static int best_state(labs_ctx* c, int32_t L, WalkerState* out, int64_t* walker)
 {
     int rc = need_ws(c);
     if (rc) return rc;
@@ -611,28 +668,35 @@ static int best_state(labs_ctx* c, int32_t L, WalkerState* out)
     const int64_t w = (int64_t)(key & 0xFFFFFFFFull);
     e = cudaMemcpy(out, at<WalkerState>(c, c->off_states) + w, sizeof(*out), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "best state read");
+    *walker = w;
     return LABS_OK;
 }
 
-static void best_outputs(const labs_ctx* c, const WalkerState& ws, int8_t* host_seq_out, int32_t* L_out,
-                         char* hex_out)
+static int best_outputs(labs_ctx* c, int64_t w, const WalkerState& ws, int8_t* host_seq_out, int32_t* L_out,
+                        char* hex_out)
 {
     const int Lw = c->groups[ws.group].L;
+    std::vector<uint32_t> bits(kBitWordsLong);
+    const int rc = walker_bits(c, w, ws, true, bits.data());
+    if (rc) return rc;
     std::vector<int8_t> seq((size_t)Lw);
-    expand_bits(ws.best, Lw, seq.data());
+    expand_bits(bits.data(), Lw, seq.data());
     if (host_seq_out) memcpy(host_seq_out, seq.data(), (size_t)Lw);
     if (L_out) *L_out = Lw;
     if (hex_out) hex_of(seq.data(), Lw, hex_out);
+    return LABS_OK;
 }
 
 int labs_best(labs_ctx* c, int32_t L, int8_t* host_seq_out, int32_t* isl, double* F, int32_t* L_out,
               char* hex_out)
 {
     WalkerState ws;
-    const int rc = best_state(c, L, &ws);
+    int64_t w = 0;
+    int rc = best_state(c, L, &ws, &w);
     if (rc) return rc;
     const int Lw = c->groups[ws.group].L;
-    best_outputs(c, ws, host_seq_out, L_out, hex_out);
+    rc = best_outputs(c, w, ws, host_seq_out, L_out, hex_out);
+    if (rc) return rc;
     if (isl) *isl = ws.best_isl;
     if (F) *F = (double)Lw * Lw / (2.0 * ws.best_isl);
     return LABS_OK;
@@ -643,9 +707,11 @@ int labs_best_psl(labs_ctx* c, int32_t L, int8_t* host_seq_out, int32_t* psl, in
 {
     if (c && !(c->cfg.flags & LABS_FLAG_PSL)) return fail(c, LABS_EINVAL, "context created without LABS_FLAG_PSL");
     WalkerState ws;
-    const int rc = best_state(c, L, &ws);
+    int64_t w = 0;
+    int rc = best_state(c, L, &ws, &w);
     if (rc) return rc;
-    best_outputs(c, ws, host_seq_out, L_out, hex_out);
+    rc = best_outputs(c, w, ws, host_seq_out, L_out, hex_out);
+    if (rc) return rc;
     if (psl) *psl = ws.best_psl;
     if (isl) *isl = ws.best_isl;
     return LABS_OK;
@@ -692,12 +758,26 @@ int labs_walker_results(labs_ctx* c, int64_t first, int64_t count, int32_t* host
     if ((host_seq || host_best_seq))
         for (auto& s : v)
             if (c->groups[s.group].L != Lw) return fail(c, LABS_EINVAL, "walkers in the range differ in length");
+    std::vector<uint32_t> cur, best;
+    if (c->long_mode && count && (host_seq || host_best_seq)) {
+        cur.resize((size_t)count * kBitWordsLong);
+        best.resize((size_t)count * kBitWordsLong);
+        const size_t row = sizeof(uint32_t) * kBitWordsLong;
+        cudaError_t e = cudaMemcpy(cur.data(), c->ws + c->off_cur_bits + row * (size_t)first, row * count,
+                                   cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(best.data(), c->ws + c->off_best_bits + row * (size_t)first, row * count,
+                           cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "walker bits read");
+    }
     for (int64_t j = 0; j < count; ++j) {
         if (host_isl) host_isl[j] = v[j].isl;
         if (host_best_isl) host_best_isl[j] = v[j].best_isl;
         if (host_target_step) host_target_step[j] = v[j].target_step;
-        if (host_seq) expand_bits(v[j].cur, Lw, host_seq + j * Lw);
-        if (host_best_seq) expand_bits(v[j].best, Lw, host_best_seq + j * Lw);
+        const uint32_t* cb = c->long_mode ? cur.data() + j * kBitWordsLong : v[j].cur;
+        const uint32_t* bb = c->long_mode ? best.data() + j * kBitWordsLong : v[j].best;
+        if (host_seq) expand_bits(cb, Lw, host_seq + j * Lw);
+        if (host_best_seq) expand_bits(bb, Lw, host_best_seq + j * Lw);
     }
     return LABS_OK;
 }
@@ -732,8 +812,8 @@ int labs_stats(labs_ctx* c, int32_t L, labs_counters* out)
     out->overflows = (int64_t)h.st_overflows;
     out->blocked = (int64_t)h.st_blocked;
     out->walkers_at_target = (int64_t)h.st_at_target;
-    out->walkers_per_warp = kWarp / c->tile;
-    out->lane_block = lanes_for(c->n_max, c->tile);
+    out->walkers_per_warp = kWarp / c->tile;  // 0 for long sequences: one walker per CTA
+    out->lane_block = c->long_mode ? long_R(c->n_max) : lanes_for(c->n_max, c->tile);
     out->target_step = h.st_target_step == LLONG_MAX ? -1 : (int64_t)h.st_target_step;
     out->best_psl = -1;
     if (h.best_key == ~0ull) {
@@ -779,8 +859,8 @@ int labs_log(labs_ctx* c, labs_log_record* dev_records, int64_t capacity)
     int rc = need_ws(c);
     if (rc) return rc;
     if (capacity < 0 || (capacity > 0 && !dev_records)) return fail(c, LABS_EINVAL, "bad log buffer");
-    if (capacity > 0 && (c->cfg.flags & (LABS_FLAG_BEST_FIRST | LABS_FLAG_PSL)))
-        return fail(c, LABS_EINVAL, "the walk log records the plain walk only");
+    if (capacity > 0 && ((c->cfg.flags & (LABS_FLAG_BEST_FIRST | LABS_FLAG_PSL)) || c->long_mode))
+        return fail(c, LABS_EINVAL, "the walk log records the plain walk of lengths up to %d only", LABS_MAX_L);
     cudaSetDevice(c->device);
     c->log = capacity > 0 ? dev_records : nullptr;
     c->log_capacity = capacity;
@@ -880,7 +960,11 @@ int labs_checkpoint(labs_ctx* c, int with_tabu, void* host_buf, size_t* bytes)
     if (c->cfg.flags & LABS_FLAG_BEST_FIRST) return fail(c, LABS_EINVAL, "no checkpoints of a best-first search");
     if (!bytes) return fail(c, LABS_EINVAL, "null size");
     const size_t hdr = 64;
-    const size_t sbytes = sizeof(WalkerState) * (size_t)c->W;
+    // walker states, and for long sequences the two bit rows of every walker (they follow
+    // the states in the workspace)
+    const size_t sbytes = c->long_mode ? c->off_best_bits + sizeof(uint32_t) * kBitWordsLong * (size_t)c->W -
+                                             c->off_states
+                                       : sizeof(WalkerState) * (size_t)c->W;
     const size_t tbytes = with_tabu ? sizeof(uint64_t) * ((size_t)c->W << c->cfg.tabu_log2) : 0;
     const size_t need = hdr + sbytes + tbytes;
     if (!host_buf) {
@@ -893,7 +977,7 @@ int labs_checkpoint(labs_ctx* c, int with_tabu, void* host_buf, size_t* bytes)
     if (rc) return rc;
     uint64_t h[8] = {kCkptMagic, (uint64_t)c->W, (uint64_t)c->nG, (uint64_t)c->cfg.tabu_log2,
                      (uint64_t)(with_tabu ? 1 : 0), (uint64_t)c->planned, c->seed,
-                     (uint64_t)(c->cfg.flags & LABS_FLAG_PSL)};
+                     (uint64_t)(c->cfg.flags & LABS_FLAG_PSL) | (c->long_mode ? 0x100u : 0u)};
     memcpy(host_buf, h, sizeof(h));
     char* dst = (char*)host_buf + hdr;
     cudaError_t e = cudaMemcpy(dst, c->ws + c->off_states, sbytes, cudaMemcpyDeviceToHost);
@@ -912,9 +996,11 @@ int labs_restore(labs_ctx* c, const void* host_buf, size_t bytes)
     uint64_t h[8];
     memcpy(h, host_buf, sizeof(h));
     if (h[0] != kCkptMagic || h[1] != (uint64_t)c->W || h[2] != (uint64_t)c->nG ||
-        h[3] != (uint64_t)c->cfg.tabu_log2 || h[6] != c->seed || h[7] != (uint64_t)(c->cfg.flags & LABS_FLAG_PSL))
+        h[3] != (uint64_t)c->cfg.tabu_log2 || h[6] != c->seed || h[7] != ((uint64_t)(c->cfg.flags & LABS_FLAG_PSL) | (c->long_mode ? 0x100u : 0u)))
         return fail(c, LABS_EINVAL, "checkpoint does not match this context");
-    const size_t sbytes = sizeof(WalkerState) * (size_t)c->W;
+    const size_t sbytes = c->long_mode ? c->off_best_bits + sizeof(uint32_t) * kBitWordsLong * (size_t)c->W -
+                                             c->off_states
+                                       : sizeof(WalkerState) * (size_t)c->W;
     const size_t tbytes = h[4] ? sizeof(uint64_t) * ((size_t)c->W << c->cfg.tabu_log2) : 0;
     if (bytes < 64 + sbytes + tbytes) return fail(c, LABS_EINVAL, "checkpoint truncated");
     cudaSetDevice(c->device);

@@ -218,8 +218,9 @@ struct View {
     float* A0;    // A0[-apad .. alen-apad)
     float* A1;
     float2* G;    // G[y] = (E[y], E[y+1]), y in [-gpad, glen-gpad)
-    uint32_t* B;  // bit-packed classes and reversals, 4 x kBitVec words
+    uint32_t* B;  // bit-packed classes and reversals, 4 x bvec words
     int gpad;
+    int bvec;
 };
 
 __device__ __forceinline__ View make_view(int* base, const WarpSmem& L)
@@ -230,6 +231,7 @@ __device__ __forceinline__ View make_view(int* base, const WarpSmem& L)
     v.G = reinterpret_cast<float2*>(base + L.goff) + L.gpad;
     v.B = reinterpret_cast<uint32_t*>(base + L.boff);
     v.gpad = L.gpad;
+    v.bvec = L.bvec;
     return v;
 }
 
@@ -272,9 +274,10 @@ __device__ __forceinline__ void rows_from_bits(const View& V, uint32_t word, int
     t.sync();
 }
 
-// Bit-packed classes: B[p*kBitVec + k] holds bits 32k..32k+31 of class p (bit u set
-// <=> A_p[u] = -1); B[(2+p)*kBitVec + k] the same for the reversed class (bit u is
-// class entry n_p-1-u).  Zero beyond the class length.
+// Bit-packed classes: B[p*bvec + k] holds bits 32k..32k+31 of class p (bit u set
+// <=> A_p[u] = -1); B[(2+p)*bvec + k] the same for the reversed class (bit u is
+// class entry n_p-1-u).  Zero beyond the class length.  A lane group wider than a warp
+// (one walker per CTA) builds one word per warp and round.
 template <class TL>
 __device__ __forceinline__ void bits_from_rows(const View& V, int n, const TL& t)
 {
@@ -282,19 +285,32 @@ __device__ __forceinline__ void bits_from_rows(const View& V, int n, const TL& t
     for (int p = 0; p < 2; ++p) {
         const float* A = p ? V.A1 : V.A0;
         const int np = p ? n - 1 : n;
-        for (int k = 0; k < kBitVec; ++k) {
-            uint32_t w = 0, r = 0;
-#pragma unroll
-            for (int h = 0; h < 32 / TL::kSize; ++h) {
-                const int u = 32 * k + TL::kSize * h + t.lane;
-                const uint32_t bw = t.ballot(u < np && A[u] < 0.f);
-                const uint32_t br = t.ballot(u < np && A[np - 1 - u] < 0.f);
-                w |= (TL::kSize == 32) ? bw : (bw << (TL::kSize * h));
-                r |= (TL::kSize == 32) ? br : (br << (TL::kSize * h));
+        if constexpr (TL::kSize > 32) {
+            const int wl = t.lane & 31;
+            for (int k = t.lane >> 5; k < V.bvec; k += TL::kSize / 32) {
+                const int u = 32 * k + wl;
+                const uint32_t w = __ballot_sync(kFull, u < np && A[u] < 0.f);
+                const uint32_t r = __ballot_sync(kFull, u < np && A[np - 1 - u] < 0.f);
+                if (wl == 0) {
+                    V.B[p * V.bvec + k] = w;
+                    V.B[(2 + p) * V.bvec + k] = r;
+                }
             }
-            if (t.lane == 0) {
-                V.B[p * kBitVec + k] = w;
-                V.B[(2 + p) * kBitVec + k] = r;
+        } else {
+            for (int k = 0; k < V.bvec; ++k) {
+                uint32_t w = 0, r = 0;
+#pragma unroll
+                for (int h = 0; h < 32 / TL::kSize; ++h) {
+                    const int u = 32 * k + TL::kSize * h + t.lane;
+                    const uint32_t bw = t.ballot(u < np && A[u] < 0.f);
+                    const uint32_t br = t.ballot(u < np && A[np - 1 - u] < 0.f);
+                    w |= (TL::kSize == 32) ? bw : (bw << (TL::kSize * h));
+                    r |= (TL::kSize == 32) ? br : (br << (TL::kSize * h));
+                }
+                if (t.lane == 0) {
+                    V.B[p * V.bvec + k] = w;
+                    V.B[(2 + p) * V.bvec + k] = r;
+                }
             }
         }
     }
@@ -329,7 +345,7 @@ __device__ __forceinline__ int build_table(const View& V, int n, const TL& t)
         for (int p = 0; p < 2; ++p) {
             const int len = (p ? n - 1 : n) - m;
             if (len <= 0) continue;
-            const uint32_t* x = V.B + p * kBitVec;
+            const uint32_t* x = V.B + p * V.bvec;
             d += len - 2 * shifted_mismatch(x, x, m, len);
         }
         set_E(V, m, (float)d);
@@ -400,8 +416,8 @@ __device__ __forceinline__ void p_direct(const View& V, int n, const Outs<TL, R>
 {
     const int np = o.p ? n - 1 : n;
     const int nv = o.p ? (n >> 1) : ((n + 1) >> 1);
-    const uint32_t* x = V.B + o.p * kBitVec;
-    const uint32_t* xr = V.B + (2 + o.p) * kBitVec;
+    const uint32_t* x = V.B + o.p * V.bvec;
+    const uint32_t* xr = V.B + (2 + o.p) * V.bvec;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int v = o.v0 + r;
@@ -992,10 +1008,18 @@ __device__ void load_walker(const WalkerState* st, Walker& w, int lane)
     w.target_step = st->target_step;
 }
 
+__device__ void save_scalars(WalkerState* st, const Walker& w);
+
 __device__ void save_walker(WalkerState* st, const Walker& w, int lane)
 {
     if (lane < kBitWords) st->cur[lane] = w.word;
-    if (lane == 0) {
+    if (lane == 0) save_scalars(st, w);
+}
+
+// Everything of the walker state but the bits (one thread).
+__device__ void save_scalars(WalkerState* st, const Walker& w)
+{
+    {
         st->fp = w.fp;
         st->isl = w.isl;
         st->best_isl = w.best_isl;

@@ -12,6 +12,11 @@ namespace labsgpu {
 constexpr int kWarp = 32;
 constexpr int kMaxN = (LABS_MAX_L + 1) / 2;  // 256 free variables
 constexpr int kBitWords = kMaxN / 32;        // 8 words of free-variable bits
+// Long sequences (LABS_MAX_L < L <= LABS_MAX_L_LONG) run one walker per CTA of
+// kLongThreads threads; their free-variable bits live beside the walker states.
+constexpr int kMaxNLong = (LABS_MAX_L_LONG + 1) / 2;  // 4096 free variables
+constexpr int kBitWordsLong = kMaxNLong / 32;          // 128 words
+constexpr int kLongThreads = 512;
 constexpr int kQuadMaxR = 10;                // largest lane block of four walkers per warp (n <= 80)
 constexpr int kMaxChunksPerCall = 4096;      // chunk launches per labs_walk call
 constexpr int kMaxTrace = 4096;              // traced walkers
@@ -123,6 +128,9 @@ struct KParams {
     int32_t best_first;       // 1: best-first search (one walker per warp, queue below)
     int32_t mode;             // walk kernel variant: 0 plain walk, 1 learned mode, 2 best-first,
                               // 3 walk under the PSL objective
+    int32_t long_mode;        // 1: lengths above LABS_MAX_L, one walker per CTA
+    uint32_t* cur_bits;       // long mode: [W][kBitWordsLong] free variables of the current
+    uint32_t* best_bits;      // and of the best sequence (WalkerState.cur / best unused)
     uint64_t* pq_key;         // [W][LABS_QUEUE_SIZE] queue keys, ~0 = empty
     uint32_t* pq_bits;        // [W][LABS_QUEUE_SIZE][kBitWords] queue entries' free variables
     uint64_t seed;
@@ -148,6 +156,9 @@ struct WarpSmem {
     int glen;   // pairs of G
     int goff;   // word offset of G[-gpad] (even)
     int boff;   // word offset of B
+    int bvec;   // words per bit vector of B
+    int xoff;   // long layout: word offset of the CTA scratch (kLongThreads words) and the
+                // free-variable bits (kBitWordsLong words)
     int words;  // total words per walker (multiple of 4: walkers stay 16-byte aligned)
 };
 // Outputs per lane (the lane block R) for n free variables and `tile` lanes per walker
@@ -203,8 +214,55 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
     }
     w.goff = 2 * w.alen;
     w.boff = w.goff + 2 * w.glen;
+    w.bvec = kBitVec;
+    w.xoff = 0;
     w.words = (w.boff + 4 * kBitVec + 3) & ~3;
     return w;
+}
+
+// Lane block of the long layout: ceil(ceil(n/2) / (kLongThreads/2)) raised to odd, so that
+// the lanes of a warp (all in one parity class, R entries apart) hit distinct banks.
+__host__ __device__ inline int long_R(int n)
+{
+    const int h = kLongThreads / 2;
+    const int R = (((n + 1) >> 1) + h - 1) / h;
+    return R | 1;
+}
+
+// Shared-memory layout of one long walker (one CTA): the rows and the table as in the
+// warp layout (bounds from the tile code with tile = kLongThreads), bit vectors sized
+// for n_max, then the CTA scratch and the bits.
+__host__ __device__ inline WarpSmem long_smem(int n_max)
+{
+    WarpSmem w;
+    const int tile = kLongThreads, R = long_R(n_max);
+    const int top = ((n_max + 7) & ~7) + 2;
+    const int span = tile * R + 2;
+    int hi = (3 * n_max) / 2 + 2 > n_max + 8 ? (3 * n_max) / 2 + 2 : n_max + 8;
+    if ((n_max + 1) / 2 + span > hi) hi = (n_max + 1) / 2 + span;
+    const int lo = n_max > span ? n_max : span;
+    w.apad = (lo + 3) & ~3;
+    w.alen = w.apad + ((hi + 7) & ~7);
+    w.gpad = (tile / 2) * R > span ? (tile / 2) * R : span;
+    w.glen = w.gpad + (top > span ? top : span);
+    w.goff = 2 * w.alen;
+    w.boff = w.goff + 2 * w.glen;
+    w.bvec = (n_max + 31) / 32 + 2;
+    w.xoff = (w.boff + 4 * w.bvec + 3) & ~3;
+    w.words = w.xoff + kLongThreads + kBitWordsLong;
+    return w;
+}
+
+// Largest ISL for which the long walk's fp32 neighbourhood stays exact.  Every value in
+// the dISL assembly is bounded by 16 sum_m |C_{2m}| + 8L + 32n + 32, and by
+// Cauchy-Schwarz sum_m |C_{2m}| <= sqrt((n-1) ISL); the limit keeps the bound below
+// 2^24 (and ISL far below 2^31).
+__host__ __device__ inline int long_isl_limit(int L, int n)
+{
+    const double room = ((double)(1 << 24) - 8.0 * L - 32.0 * n - 32.0) / 16.0;
+    double lim = room * room / (double)(n > 1 ? n - 1 : 1);
+    if (lim > (double)(1 << 30)) lim = (double)(1 << 30);
+    return (int)lim - 1;
 }
 
 // Walk kernel instantiations (labs_walk8a.cu, labs_walk8b.cu: four walkers per warp,
@@ -219,6 +277,12 @@ WalkFn walk_fn32(int rmax);   // one walker per warp: plain walk
 WalkFn walk_fn32l(int rmax);  // learned mode (labs_walk32l.cu)
 WalkFn walk_fn32b(int rmax);  // best-first search (labs_walk32b.cu)
 WalkFn walk_fn32p(int rmax);  // walk under the PSL objective (labs_walk32p.cu)
+
+// Long-L walk (labs_long.cu).
+int long_kernel_config(int R, size_t smem_bytes, int* ctas_per_sm, int* regs);
+int launch_long_reset(const KParams& p, size_t smem_bytes, void* stream);
+int launch_long_walk_chunk(const KParams& p, int chunk_index, int grid, size_t smem_bytes, void* stream);
+int launch_long_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status, void* stream);
 
 // Launchers (labs_kernels.cu).
 int launch_zobrist(const KParams& p, uint64_t* zkeys, const DevGroup* host_groups, int nG,

@@ -3,6 +3,8 @@
 // (ISL, neighbourhood), learned-proposal support, reductions and the launchers.
 // The walk itself is in labs_device.cuh, instantiated by labs_walk16.cu and
 // labs_walk32.cu.
+#include <algorithm>
+
 #include "labs_device.cuh"
 
 namespace labsgpu {
@@ -102,18 +104,21 @@ __global__ void __launch_bounds__(256) isl_kernel(const int8_t* __restrict__ seq
         }
         __syncwarp();
         const bool all_ok = __all_sync(kFull, ok);
-        int part = 0;
+        long long part = 0;
         if (all_ok) {
             for (int k = 1 + lane; k < L; k += kWarp) {
                 int ck = 0;
                 for (int j = 0; j + k < L; ++j) ck += s[j] * s[j + k];
-                part += ck * ck;
+                part += (long long)ck * ck;
             }
         }
-        const int e = __reduce_add_sync(kFull, part);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
         if (lane == 0) {
-            out[row] = all_ok ? e : -1;
+            // an ISL above INT32_MAX (long rows only) is reported as -2 with LABS_ERANGE
+            out[row] = !all_ok ? -1 : part > INT_MAX ? -2 : (int32_t)part;
             if (!all_ok && status) atomicAdd(&status->invalid_rows, 1);
+            if (all_ok && part > INT_MAX && status) raise_error(status, LABS_ERANGE, (int)row);
         }
         __syncwarp();
     }
@@ -560,8 +565,10 @@ static int row_grid(int64_t batch, int warps)
 int launch_isl(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status, void* stream)
 {
     if (batch == 0) return LABS_OK;
-    const int warps = 8;
-    const size_t smem = (size_t)warps * ((L + 3) & ~3) * sizeof(int);
+    // one row of ints per warp; long rows take fewer warps per CTA (48 KB of shared memory)
+    const size_t row_bytes = (size_t)((L + 3) & ~3) * sizeof(int);
+    const int warps = (int)std::max<size_t>(1, std::min<size_t>(8, (48 * 1024) / row_bytes));
+    const size_t smem = (size_t)warps * row_bytes;
     isl_kernel<<<row_grid(batch, warps), warps * kWarp, smem, (cudaStream_t)stream>>>(seqs, batch, L, out,
                                                                                        status);
     return status_of(cudaGetLastError());

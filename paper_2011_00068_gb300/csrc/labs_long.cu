@@ -1,0 +1,523 @@
+// labs_long.cu -- the walk for long sequences (LABS_MAX_L < L <= LABS_MAX_L_LONG): one
+// CTA of kLongThreads threads runs one walker.  The step is the walk's (Algorithm 1 in
+// its self-avoiding form): all n flips evaluated by the Toeplitz form of dISL, the
+// lowest (dISL, i) whose result is not in HT taken, C_k and P updated in O(n) per move.
+// The per-lane arithmetic is the warp kernels' (labs_device.cuh), run by a lane group
+// that spans the CTA; the collectives go through shared memory.
+#include "labs_device.cuh"
+
+namespace labsgpu {
+
+namespace {
+
+// The CTA as one lane group (the interface of Tile<>; every call must be reached by all
+// threads).  x: kLongThreads words of shared scratch.
+template <int NT>
+struct Blk {
+    static constexpr int kSize = NT;
+    static constexpr int kHalf = NT / 2;
+    static constexpr int kWarps = NT / 32;
+    int lane;
+    int* x;
+    __device__ Blk(int tid, int* scratch) : lane(tid), x(scratch) {}
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ int shfl(int v, int src) const
+    {
+        x[lane] = v;
+        __syncthreads();
+        const int r = x[src];
+        __syncthreads();
+        return r;
+    }
+    __device__ __forceinline__ uint32_t shfl(uint32_t v, int src) const { return (uint32_t)shfl((int)v, src); }
+    // warp partials in x[0 .. kWarps), combined by every thread
+    __device__ __forceinline__ int rmin(int v) const
+    {
+        v = __reduce_min_sync(kFull, v);
+        if ((lane & 31) == 0) x[lane >> 5] = v;
+        __syncthreads();
+        int r = x[0];
+#pragma unroll
+        for (int k = 1; k < kWarps; ++k) r = min(r, x[k]);
+        __syncthreads();
+        return r;
+    }
+    __device__ __forceinline__ int rmax(int v) const { return -rmin(-v); }
+    __device__ __forceinline__ unsigned rminu(unsigned v) const
+    {
+        v = __reduce_min_sync(kFull, v);
+        if ((lane & 31) == 0) x[lane >> 5] = (int)v;
+        __syncthreads();
+        unsigned r = (unsigned)x[0];
+#pragma unroll
+        for (int k = 1; k < kWarps; ++k) r = min(r, (unsigned)x[k]);
+        __syncthreads();
+        return r;
+    }
+    __device__ __forceinline__ uint32_t rxor(uint32_t v) const
+    {
+        v = __reduce_xor_sync(kFull, v);
+        if ((lane & 31) == 0) x[lane >> 5] = (int)v;
+        __syncthreads();
+        uint32_t r = 0;
+#pragma unroll
+        for (int k = 0; k < kWarps; ++k) r ^= (uint32_t)x[k];
+        __syncthreads();
+        return r;
+    }
+    // sum in 64 bits, saturated to INT_MAX (a saturated ISL fails the range check)
+    __device__ __forceinline__ int radd(int v) const
+    {
+        long long a = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
+        long long* y = reinterpret_cast<long long*>(x);
+        if ((lane & 31) == 0) y[lane >> 5] = a;
+        __syncthreads();
+        long long r = 0;
+#pragma unroll
+        for (int k = 0; k < kWarps; ++k) r += y[k];
+        __syncthreads();
+        return r > INT_MAX ? INT_MAX : (int)r;
+    }
+};
+
+using LB = Blk<kLongThreads>;
+
+// One long walker: the walk's environment plus its bit rows in global memory and the
+// CTA's shared copy of the current bits.
+struct LongWalk {
+    WalkEnv e;
+    uint32_t* cur;    // [kBitWordsLong] in global memory
+    uint32_t* best;
+    uint32_t* bits;   // shared copy of the current bits (kBitWordsLong words)
+    int nw;           // words of free-variable bits, ceil(n / 32)
+    int isl_limit;    // exact-range bound of the ISL (long_isl_limit)
+};
+
+// Zeroes rows, table and bit vectors (everything below the scratch and the bits).
+__device__ __forceinline__ void long_clear(int* base, const WarpSmem& SL, const LB& t)
+{
+    int4* b4 = reinterpret_cast<int4*>(base);
+    for (int i = t.lane; i < SL.xoff / 4; i += LB::kSize) b4[i] = make_int4(0, 0, 0, 0);
+    t.sync();
+}
+
+// Rows from the shared bits (Eq. 4: s_j = x_j for j <= c, s_{c+t} = (-1)^t x_{c-t}),
+// then the table; returns the ISL.
+__device__ int long_load_rows(const LongWalk& lw, const WarpSmem& SL, int* base, const View& V, uint32_t word,
+                              const LB& t)
+{
+    const int L = lw.e.L, n = lw.e.n, c = n - 1;
+    if (t.lane < lw.nw) lw.bits[t.lane] = word;
+    long_clear(base, SL, t);  // ends with a barrier
+    for (int j = t.lane; j < L; j += LB::kSize) {
+        const int f = j <= c ? j : 2 * c - j;
+        const int x = ((lw.bits[f >> 5] >> (f & 31)) & 1u) ? -1 : 1;
+        const int s = (j > c && ((j - c) & 1)) ? -x : x;
+        if (j & 1) V.A1[j >> 1] = (float)s;
+        else V.A0[j >> 1] = (float)s;
+    }
+    t.sync();
+    return build_table(V, n, t);
+}
+
+// HT fingerprint of the shared bits (long_load_rows ran first).
+__device__ uint64_t long_fingerprint(const LongWalk& lw, const LB& t)
+{
+    uint64_t f = 0;
+    for (int i = t.lane; i < lw.e.n; i += LB::kSize)
+        if ((lw.bits[i >> 5] >> (i & 31)) & 1u) f ^= __ldg(lw.e.zk + i);
+    const uint32_t lo = t.rxor((uint32_t)f);
+    const uint32_t hi = t.rxor((uint32_t)(f >> 32));
+    return (uint64_t)lo | ((uint64_t)hi << 32);
+}
+
+__device__ __forceinline__ void long_note_best(const LongWalk& lw, Walker& w, const LB& t)
+{
+    if (w.isl < w.best_isl) {
+        w.best_isl = w.isl;
+        w.best_step = w.steps;
+        if (t.lane < lw.nw) lw.best[t.lane] = w.word;
+    }
+    if (w.target_step < 0 && target_met(*lw.e.p, lw.e.L, w.isl)) w.target_step = w.steps;
+}
+
+// Algorithm 1 start: random S (restart index w.restart_idx), rows, table, ISL, HT
+// insertion, best update.
+__device__ void long_start(const LongWalk& lw, Walker& w, const WarpSmem& SL, int* base, const View& V,
+                           const LB& t)
+{
+    const WalkEnv& env = lw.e;
+    w.word = t.lane < lw.nw ? start_word(env.p->seed, env.g, w.restart_idx, t.lane, env.n) : 0u;
+    w.isl = long_load_rows(lw, SL, base, V, w.word, t);
+    w.fp = long_fingerprint(lw, t);
+    if (t.lane == 0) env.T[w.fp & env.tmask] = (w.fp & ~kGenMask) | w.gen;
+    t.sync();
+    w.since = w.isl;
+    w.stag = 0;
+    long_note_best(lw, w, t);
+}
+
+__device__ void long_restart(const LongWalk& lw, Walker& w, const WarpSmem& SL, int* base, const View& V,
+                             const LB& t)
+{
+    w.restart_idx += 1;
+    w.restarts += 1;
+    w.gen += 1;
+    if (w.gen > kGenMask) {
+        const int64_t slots = (int64_t)lw.e.tmask + 1;
+        for (int64_t i = t.lane; i < slots; i += LB::kSize) lw.e.T[i] = 0ull;
+        t.sync();
+        w.gen = 1;
+    }
+    long_start(lw, w, SL, base, V, t);
+}
+
+// HT probe of f by the first warp (the walk's linear probe of up to probe_cap <= 32
+// slots), result shared with the CTA.
+__device__ Probe long_probe(const LongWalk& lw, uint64_t f, uint32_t gen, const LB& t)
+{
+    long long* y = reinterpret_cast<long long*>(t.x);
+    if (t.lane < 32) {
+        const Tile<32> tw(t.lane);
+        const Probe pr = probe_full(lw.e, f, gen, lw.e.p->probe_cap, tw);
+        if (t.lane == 0) {
+            y[0] = pr.visited ? 1 : 0;
+            y[1] = pr.slot;
+        }
+    }
+    __syncthreads();
+    Probe pr;
+    pr.visited = y[0] != 0;
+    pr.slot = y[1];
+    __syncthreads();
+    return pr;
+}
+
+// Steps of one long walker until `until` (or a stop request, or the exact-range check).
+template <int R>
+__device__ void long_walk(const LongWalk& lw, Walker& w, int64_t until, const WarpSmem& SL, int* base,
+                          const View& V, int trace_slot, int64_t trace_start, const LB& t)
+{
+    const WalkEnv& env = lw.e;
+    const KParams& p = *env.p;
+    const int lane = t.lane, n = env.n;
+    const Outs<LB, R> o(t);
+    float P[R];
+    p_direct(V, n, o, P);
+    StopCheck stop;
+    stop.start(p, lane == 0);
+    while (w.steps < until) {
+        if (w.isl > lw.isl_limit) {
+            if (lane == 0) raise_error(p.status, LABS_ERANGE, (int)env.g);
+            break;
+        }
+        if ((w.steps & (kCheckEvery - 1)) == 0) {
+            const int why = t.shfl(stop.poll(p, lane == 0), 0);
+            if (why) {
+                if (lane == 0) raise_error(p.status, why, (int)env.g);
+                break;
+            }
+        }
+        int dl[R];
+        {
+            float X[R];
+            toeplitz(V, n, o, X);
+            assemble(V, n, o, X, P, dl);
+        }
+        // lowest (dISL, i) whose result is not in HT
+        uint32_t excl = 0;
+        int best_i = -1, best_d = 0;
+        int64_t slot = -1;
+        uint64_t fnew = 0;
+        for (;;) {
+            int bd, bi;
+            tile_argmin(dl, excl, o, t, bd, bi);
+            if (bi < 0) break;
+            const uint64_t f = w.fp ^ __ldg(env.zk + bi);
+            const Probe pr = long_probe(lw, f, w.gen, t);
+            if (!pr.visited) {
+                best_i = bi;
+                best_d = bd;
+                slot = pr.slot;
+                fnew = f;
+                break;
+            }
+            exclude<LB, R>(excl, bi, t);
+        }
+        w.steps += 1;
+        int code;
+        if (best_i < 0) {
+            w.blocked += 1;
+            long_restart(lw, w, SL, base, V, t);
+            p_direct(V, n, o, P);
+            code = LABS_TRACE_BLOCKED;
+        } else {
+            flip_rows_table(V, n, o, P, best_i, t);
+            const bool stored = slot >= 0;
+            if (lane == 0 && stored) env.T[slot] = (fnew & ~kGenMask) | w.gen;
+            if (lane == (best_i >> 5)) w.word ^= 1u << (best_i & 31);
+            t.sync();
+            w.fp = fnew;
+            w.isl += best_d;
+            if (!stored) w.overflows += 1;
+            long_note_best(lw, w, t);
+            if (w.isl < w.since) {
+                w.since = w.isl;
+                w.stag = 0;
+            } else {
+                w.stag += 1;
+            }
+            code = best_i;
+            if (w.stag >= env.patience || !stored) {
+                long_restart(lw, w, SL, base, V, t);
+                p_direct(V, n, o, P);
+                code |= LABS_TRACE_RESTART;
+            }
+        }
+        if (trace_slot >= 0 && lane == 0) {
+            const int64_t s = w.steps - 1 - trace_start;
+            if (s >= 0 && s < p.status->trace_capacity) {
+                p.status->trace_code[trace_slot * p.status->trace_capacity + s] = code;
+                p.status->trace_isl[trace_slot * p.status->trace_capacity + s] = w.isl;
+            }
+        }
+    }
+}
+
+__device__ LongWalk long_env(const KParams& p, int64_t wi, const DevGroup& G, uint32_t* bits)
+{
+    LongWalk lw;
+    lw.e.p = &p;
+    lw.e.tmask = (1ull << p.tabu_log2) - 1ull;
+    lw.e.T = p.tabu + ((uint64_t)wi << p.tabu_log2);
+    lw.e.zk = p.zkeys + G.zkey_off;
+    lw.e.st = p.states + wi;
+    lw.e.L = G.L;
+    lw.e.n = G.n;
+    lw.e.patience = p.patience > 0 ? p.patience : 2 * G.n;
+    lw.e.g = (uint32_t)wi;
+    lw.e.slot = nullptr;
+    lw.e.slot_valid = nullptr;
+    lw.e.rdump = nullptr;
+    lw.e.rdump_idx = nullptr;
+    lw.e.rdump_count = nullptr;
+    lw.e.dump_cap = 0;
+    lw.cur = p.cur_bits + wi * kBitWordsLong;
+    lw.best = p.best_bits + wi * kBitWordsLong;
+    lw.bits = bits;
+    lw.nw = (G.n + 31) / 32;
+    lw.isl_limit = long_isl_limit(G.L, G.n);
+    return lw;
+}
+
+// First start of every long walker (restart index 0, HT generation 1; HT zeroed by the
+// caller), one walker per CTA at a time.
+__global__ void __launch_bounds__(kLongThreads, 1) long_reset_kernel(KParams p)
+{
+    extern __shared__ __align__(16) int smem[];
+    const WarpSmem SL = long_smem(p.n_max);
+    const LB t(threadIdx.x, smem + SL.xoff);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(smem + SL.xoff + kLongThreads);
+    const View V = make_view(smem, SL);
+    for (int64_t wi = blockIdx.x; wi < p.W; wi += gridDim.x) {
+        int gidx = 0;
+        for (int g = 0; g < p.nG; ++g)
+            if (wi >= p.groups[g].first && wi < p.groups[g].first + p.groups[g].count) gidx = g;
+        const DevGroup G = p.groups[gidx];
+        const LongWalk lw = long_env(p, wi, G, bits);
+        Walker w;
+        w.restart_idx = 0;
+        w.gen = 1;
+        w.restarts = w.overflows = w.blocked = 0;
+        w.steps = 0;
+        w.best_isl = INT_MAX;
+        w.best_step = 0;
+        w.target_step = -1;
+        long_start(lw, w, SL, smem, V, t);
+        if (t.lane < lw.nw) lw.cur[t.lane] = w.word;
+        if (t.lane == 0) {
+            WalkerState* st = lw.e.st;
+            save_scalars(st, w);
+            st->group = gidx;
+            st->trace_slot = -1;
+            st->psl = st->best_psl = st->since_psl = -1;
+        }
+        t.sync();
+    }
+}
+
+// One chunk of steps for every long walker; walkers are taken from a counter.
+template <int R>
+__global__ void __launch_bounds__(kLongThreads, 1) long_walk_kernel(KParams p, int chunk_index)
+{
+    extern __shared__ __align__(16) int smem[];
+    const WarpSmem SL = long_smem(p.n_max);
+    const LB t(threadIdx.x, smem + SL.xoff);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(smem + SL.xoff + kLongThreads);
+    const View V = make_view(smem, SL);
+    const int64_t target = p.status->target_steps;
+    for (;;) {
+        int q = 0;
+        if (t.lane == 0) q = (int)atomicAdd(&p.queue[chunk_index], 1u);
+        const int64_t wi = (int64_t)(uint32_t)t.shfl(q, 0);
+        if (wi >= p.W) break;
+        WalkerState* st = p.states + wi;
+        const int64_t steps_done = st->steps_done;
+        const int64_t until = min(target, steps_done + (int64_t)p.chunk_steps);
+        if (steps_done >= until) continue;
+        const DevGroup G = p.groups[st->group];
+        const LongWalk lw = long_env(p, wi, G, bits);
+        Walker w;
+        load_walker(st, w, 32);  // scalars only (lane 32 reads no bits)
+        w.word = t.lane < lw.nw ? lw.cur[t.lane] : 0u;
+        const int trace_slot = st->trace_slot;
+        const int64_t trace_start = trace_slot >= 0 ? p.trace_start[trace_slot] : 0;
+        const int isl = long_load_rows(lw, SL, smem, V, w.word, t);
+        if (isl != w.isl) {
+            if (t.lane == 0) raise_error(p.status, LABS_ESTATE, (int)wi);
+            continue;
+        }
+        long_walk<R>(lw, w, until, SL, smem, V, trace_slot, trace_start, t);
+        if (t.lane < lw.nw) lw.cur[t.lane] = w.word;
+        if (t.lane == 0) save_scalars(st, w);
+        t.sync();
+    }
+}
+
+// The neighbourhood of Algorithm 1 for long skew-symmetric rows, one row per CTA.
+// Rows that are not +-1 or break Eq. 4 get INT32_MIN (LABS_EINVAL); rows whose ISL is
+// above the exact-range bound get INT32_MIN too (LABS_ERANGE).
+template <int R>
+__global__ void __launch_bounds__(kLongThreads, 1) long_delta_kernel(const int8_t* __restrict__ seqs, int64_t batch,
+                                                                    int L, int32_t* __restrict__ out,
+                                                                    DevStatus* status)
+{
+    extern __shared__ __align__(16) int smem[];
+    const int n = (L + 1) / 2, c = n - 1;
+    const WarpSmem SL = long_smem(n);
+    const LB t(threadIdx.x, smem + SL.xoff);
+    const View V = make_view(smem, SL);
+    const Outs<LB, R> o(t);
+    for (int64_t row = blockIdx.x; row < batch; row += gridDim.x) {
+        const int8_t* src = seqs + row * (int64_t)L;
+        long_clear(smem, SL, t);
+        bool ok = true;
+        for (int j = t.lane; j < L; j += LB::kSize) {
+            const int v = src[j];
+            ok = ok && (v == 1 || v == -1);
+            if (j > c) {
+                const int m = src[2 * c - j];
+                ok = ok && (v == ((((j - c) & 1) ? -m : m)));
+            }
+            if (j & 1) V.A1[j >> 1] = (float)v;
+            else V.A0[j >> 1] = (float)v;
+        }
+        const bool all_ok = t.rmin(ok ? 1 : 0) != 0;
+        int32_t* dst = out + row * (int64_t)n;
+        if (!all_ok) {
+            for (int i = t.lane; i < n; i += LB::kSize) dst[i] = INT32_MIN;
+            if (t.lane == 0 && status) {
+                atomicAdd(&status->invalid_rows, 1);
+                raise_error(status, LABS_EINVAL, (int)row);
+            }
+            t.sync();
+            continue;
+        }
+        const int isl = build_table(V, n, t);
+        if (isl > long_isl_limit(L, n)) {
+            for (int i = t.lane; i < n; i += LB::kSize) dst[i] = INT32_MIN;
+            if (t.lane == 0 && status) raise_error(status, LABS_ERANGE, (int)row);
+            t.sync();
+            continue;
+        }
+        int dl[R];
+        {
+            float X[R], P[R];
+            toeplitz(V, n, o, X);
+            p_direct(V, n, o, P);
+            assemble(V, n, o, X, P, dl);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (dl[r] != INT_MAX) dst[2 * (o.v0 + r) + o.p] = dl[r];
+        t.sync();
+    }
+}
+
+using LongFn = void (*)(KParams, int);
+using LongDeltaFn = void (*)(const int8_t*, int64_t, int, int32_t*, DevStatus*);
+
+LongFn long_fn(int R)
+{
+    switch (R) {
+        case 1: return long_walk_kernel<1>;
+        case 3: return long_walk_kernel<3>;
+        case 5: return long_walk_kernel<5>;
+        case 7: return long_walk_kernel<7>;
+        default: return long_walk_kernel<9>;
+    }
+}
+
+LongDeltaFn long_delta_fn(int R)
+{
+    switch (R) {
+        case 1: return long_delta_kernel<1>;
+        case 3: return long_delta_kernel<3>;
+        case 5: return long_delta_kernel<5>;
+        case 7: return long_delta_kernel<7>;
+        default: return long_delta_kernel<9>;
+    }
+}
+
+}  // namespace
+
+int long_kernel_config(int R, size_t smem_bytes, int* ctas_per_sm, int* regs)
+{
+    const LongFn fn = long_fn(R);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return LABS_ECUDA;
+    e = cudaFuncSetAttribute(long_reset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return LABS_ECUDA;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return LABS_ECUDA;
+    if (regs) *regs = fa.numRegs;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, kLongThreads, smem_bytes);
+    return e == cudaSuccess ? LABS_OK : LABS_ECUDA;
+}
+
+int launch_long_reset(const KParams& p, size_t smem_bytes, void* stream)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t grid = p.W < sms ? (p.W > 0 ? p.W : 1) : sms;
+    long_reset_kernel<<<(int)grid, kLongThreads, smem_bytes, (cudaStream_t)stream>>>(p);
+    return cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ECUDA;
+}
+
+int launch_long_walk_chunk(const KParams& p, int chunk_index, int grid, size_t smem_bytes, void* stream)
+{
+    long_fn(p.rmax)<<<grid, kLongThreads, smem_bytes, (cudaStream_t)stream>>>(p, chunk_index);
+    return cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ECUDA;
+}
+
+int launch_long_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status, void* stream)
+{
+    if (batch == 0) return LABS_OK;
+    const int n = (L + 1) / 2;
+    const size_t smem = (size_t)long_smem(n).words * sizeof(int);
+    const LongDeltaFn fn = long_delta_fn(long_R(n));
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return LABS_ECUDA;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)(batch < sms ? batch : sms);
+    fn<<<grid, kLongThreads, smem, (cudaStream_t)stream>>>(seqs, batch, L, out, status);
+    return cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ECUDA;
+}
+
+}  // namespace labsgpu

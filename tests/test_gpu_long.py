@@ -1,0 +1,161 @@
+"""GPU parity of the long-sequence walk (LABS_MAX_L < L <= LABS_MAX_L_LONG, one walker
+per CTA) against the oracle, whose walk has no length limit: per-step trace codes and
+ISLs, best and final sequences, counters, bit-exact; chunking, graphs and mixed long
+lengths; checkpoints; the long row kernels (ISL, neighbourhood) including the rows
+outside the exact range; the combinations the library refuses."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import labs_inputs
+import oracle
+import paper_2011_00068_gb300 as labs
+from paper_2011_00068_gb300 import _native
+
+pytestmark = pytest.mark.gpu
+
+
+def traced(L, walkers, steps, seed, **cfg):
+    s = labs.Search(L, walkers, seed, **cfg)
+    code, isl = s.trace(list(range(walkers)), steps)
+    s.walk(steps)
+    s.sync()
+    return s, code.cpu().numpy(), isl.cpu().numpy()
+
+
+@pytest.mark.parametrize("L,walkers,steps,kw", [
+    (513, 6, 400, {}),
+    (601, 4, 300, {"tabu_log2": 4, "probe_cap": 3}),
+    (1025, 4, 300, {"patience": 40}),
+    (2047, 3, 120, {}),
+    (4095, 2, 60, {}),
+    (8191, 2, 16, {}),
+])
+def test_long_trajectory_parity(L, walkers, steps, kw):
+    seed = 6
+    s, code, isl = traced(L, walkers, steps, seed, **kw)
+    o = oracle.walk(L, seed, walkers, steps, trace=True, **kw)
+    assert np.array_equal(code, o["trace_code"])
+    assert np.array_equal(isl, o["trace_isl"])
+    res = s.results(seqs=True)
+    for k in ("best_isl", "target_step"):
+        assert np.array_equal(res[k], o[k]), k
+    assert np.array_equal(res["isl"], o["final_isl"])
+    assert np.array_equal(res["seq"], o["final_seq"])
+    assert np.array_equal(res["best_seq"], o["best_seq"])
+    st = s.stats()
+    assert st["walkers_per_warp"] == 0  # one walker per CTA
+    assert st["steps"] == walkers * steps
+    assert st["restarts"] == int(o["restarts"].sum())
+    assert st["overflows"] == int(o["overflows"].sum())
+    assert st["blocked"] == int((o["trace_code"] == -1).sum())
+    g = int(np.argmin(o["best_isl"]))
+    b = s.best()
+    assert b["isl"] == o["best_isl"][g] and np.array_equal(b["seq"], o["best_seq"][g])
+    assert b["hex"] == oracle.hex_encode(o["best_seq"][g])
+    s.close()
+
+
+def test_long_chunking_graphs_and_mixed_lengths():
+    L, W, steps, seed = 1025, 4, 200, 5
+    ref = None
+    for cfg in ({}, {"chunk_steps": 7}, {"chunk_steps": 50, "flags": _native.LABS_FLAG_NO_GRAPH}):
+        s, code, isl = traced(L, W, steps, seed, **cfg)
+        if ref is None:
+            ref = (code, isl)
+        else:
+            assert np.array_equal(code, ref[0]) and np.array_equal(isl, ref[1])
+        s.close()
+    o = oracle.walk(L, seed, W, steps, trace=True)
+    assert np.array_equal(ref[0], o["trace_code"]) and np.array_equal(ref[1], o["trace_isl"])
+    # several calls == one call; long lengths mixed in one launch
+    Ls, counts = [601, 2001, 1025], [3, 2, 3]
+    s = labs.Search(Ls, counts, 9)
+    code, isl = s.trace(list(range(sum(counts))), 150)
+    for part in (1, 70, 79):
+        s.walk(part)
+    s.sync()
+    code, isl = code.cpu().numpy(), isl.cpu().numpy()
+    first = 0
+    for Lg, cnt in zip(Ls, counts):
+        o = oracle.walk(Lg, 9, cnt, 150, first_walker=first, trace=True)
+        assert np.array_equal(code[first:first + cnt], o["trace_code"]), Lg
+        assert np.array_equal(isl[first:first + cnt], o["trace_isl"]), Lg
+        first += cnt
+    s.close()
+
+
+def exact_limit(L):
+    """The long kernels' exact-range bound on ISL: every value of the fp32 dISL
+    assembly stays below 2^24 (restated from the library's derivation)."""
+    n = (L + 1) // 2
+    room = ((1 << 24) - 8 * L - 32 * n - 32) / 16
+    return int(min(room * room / (n - 1), 2 ** 30)) - 1
+
+
+@pytest.mark.parametrize("L", [513, 1025, 4095, 8191])
+def test_long_rows(L):
+    n = (L + 1) // 2
+    xs = labs_inputs.random_free_vars(5, L, seed=L)
+    rows = [oracle.skew_expand(x, L) for x in xs]
+    rows.append(oracle.skew_expand(np.ones(n, np.int8), L))            # degenerate
+    rows.append(oracle.skew_expand(np.array([(-1) ** i for i in range(n)], np.int8), L))
+    bad = rows[0].copy()
+    bad[L - 1] = -bad[L - 1]                                            # breaks Eq. 4
+    rows.append(bad)
+    R = np.stack(rows)
+    dev = torch.from_numpy(R).cuda()
+    d = labs.neighbor_delta(dev).cpu().numpy()
+    e = labs.isl(dev).cpu().numpy()
+    over = 0
+    for k, r in enumerate(rows[:-1]):
+        want = oracle.isl(r)
+        assert e[k] == (want if want <= 2 ** 31 - 1 else -2), k
+        if want > exact_limit(L):
+            over += 1
+            assert (d[k] == np.iinfo(np.int32).min).all(), k
+        else:
+            assert np.array_equal(d[k], oracle.neighbor_delta(r)), k
+    assert (d[-1] == np.iinfo(np.int32).min).all()
+    assert e[-1] == oracle.isl(bad)  # any +-1 row has an ISL
+    if L >= 4095:
+        assert over == 2  # both degenerate rows lie outside the exact range
+
+
+def test_long_checkpoint_round_trip():
+    L, W, seed = 1025, 3, 2
+    a = labs.Search(L, W, seed)
+    a.walk(60)
+    buf = a.checkpoint(with_tabu=True)
+    a.walk(90)
+    ra = a.results(seqs=True)
+    b = labs.Search(L, W, seed)
+    b.restore(buf)
+    b.walk(90)
+    rb = b.results(seqs=True)
+    for k in ("isl", "best_isl", "seq", "best_seq"):
+        assert np.array_equal(ra[k], rb[k]), k
+    o = oracle.walk(L, seed, W, 150)
+    assert np.array_equal(ra["seq"], o["final_seq"]) and np.array_equal(ra["best_isl"], o["best_isl"])
+    # a long checkpoint does not restore into a context of short walkers
+    c = labs.Search(511, W, seed)
+    with pytest.raises(labs.LabsError):
+        c.restore(buf)
+    for x in (a, b, c):
+        x.close()
+
+
+def test_long_refusals():
+    with pytest.raises(labs.LabsError):
+        labs.Search([201, 1025], [2, 2], 1)  # short and long lengths in one context
+    with pytest.raises(labs.LabsError):
+        labs.Search(8193, 2, 1)
+    for f in (_native.LABS_FLAG_BEST_FIRST, _native.LABS_FLAG_LEARNED, _native.LABS_FLAG_PSL):
+        with pytest.raises(labs.LabsError):
+            labs.Search(1025, 2, 1, flags=f)
+    s = labs.Search(1025, 2, 1)
+    with pytest.raises(labs.LabsError):
+        s.log(4)
+    s.close()

@@ -16,7 +16,7 @@ from tests import pyref
 
 @pytest.mark.parametrize("L,steps,log2,cap,patience",
                          [(13, 300, 16, 32, 0), (21, 400, 16, 32, 0), (21, 300, 4, 3, 7),
-                          (5, 60, 16, 32, 0), (41, 250, 16, 32, 0)])
+                          (5, 60, 16, 32, 0), (41, 250, 16, 32, 0), (601, 40, 16, 32, 0)])
 def test_walk_matches_python_statement(L, steps, log2, cap, patience):
     seed = 1
     out = oracle.walk(L, seed, 3, steps, tabu_log2=log2, probe_cap=cap, patience=patience,
