@@ -107,7 +107,8 @@ typedef struct labs_counters {
     int64_t target_step;       /* fewest steps after which some walker met the target,
                                   -1 if none did */
     int64_t walkers_at_target; /* walkers that met the target */
-    int32_t walkers_per_warp;  /* launch shape of the walk kernel: 4, 2 or 1 */
+    int32_t walkers_per_warp;  /* launch shape of the walk kernel: 4, 2 or 1; 0 for long
+                                  sequences (one walker per CTA) */
     int32_t lane_block;        /* outputs per lane of the widest walker (R) */
     int32_t best_psl;          /* LABS_FLAG_PSL: PSL of the best sequence (whose ISL is
                                   best_isl; best in the (PSL, ISL) order); else -1 */
@@ -156,14 +157,17 @@ int labs_reset(labs_ctx *ctx);
 /* Eq. 2 for a batch of arbitrary +-1 rows: dev_seqs is int8 [batch][L] (row-major,
  * L = the context's single length), dev_isl_out is int32 [batch].  A row holding a
  * value other than +-1 gets ISL -1 (and labs_sync then reports LABS_EINVAL when a
- * workspace is bound).  batch may be 0. */
+ * workspace is bound); a long row whose ISL exceeds INT32_MAX gets -2 (LABS_ERANGE).
+ * batch may be 0. */
 int labs_isl(labs_ctx *ctx, const int8_t *dev_seqs, int64_t batch, int32_t *dev_isl_out);
 
 /* The neighbourhood of Algorithm 1 ("fast calculate merit factor of S_f") for a
  * batch of skew-symmetric rows: dev_delta_out is int32 [batch][n], entry i = ISL after
  * flipping free variable i (and its mirror) minus ISL before, i = 0..n-1.  A row that
  * is not +-1 or breaks Eq. 4 gets INT32_MIN in every entry (and labs_sync reports
- * LABS_EINVAL when a workspace is bound). */
+ * LABS_EINVAL when a workspace is bound).  For long rows (L > LABS_MAX_L) a row whose
+ * ISL is above the exact-range bound stated at labs_walk gets INT32_MIN too
+ * (LABS_ERANGE). */
 int labs_neighbor_delta(labs_ctx *ctx, const int8_t *dev_seqs, int64_t batch,
                         int32_t *dev_delta_out);
 
@@ -189,6 +193,10 @@ int labs_neighbor_delta(labs_ctx *ctx, const int8_t *dev_seqs, int64_t batch,
  *   with the lowest (PSL, ISL, i) whose result is not in HT, the best sequence and the
  *   stagnation count use "strictly lower pair", and HT and the restarts are as in the
  *   walk.  The trace's ISL log still holds ISL.
+ * Long sequences (L > LABS_MAX_L) take the same steps with the neighbourhood in exact
+ *   fp32 arithmetic, which holds while ISL < ((2^24 - 8L - 32n - 32) / 16)^2 / (n - 1)
+ *   (capped at 2^30; 2.6e8 at L = 8191, far above random starts, whose ISL is near
+ *   L^2/2): a walker whose ISL exceeds it stops and labs_sync reports LABS_ERANGE.
  * The trajectory of a walker depends only on (seed, walker id, L, cfg), never on
  * chunking, launch shape or the other walkers. */
 int labs_walk(labs_ctx *ctx, int64_t steps);
