@@ -62,7 +62,7 @@ class WalkResult(ctypes.Structure):
     _fields_ = [("final_isl", ctypes.c_int32), ("best_isl", ctypes.c_int32),
                 ("best_step", ctypes.c_int64), ("target_step", ctypes.c_int64),
                 ("restarts", ctypes.c_int32), ("overflows", ctypes.c_int32),
-                ("final_psl", ctypes.c_int32), ("best_psl", ctypes.c_int32)]
+                ("final_psl", ctypes.c_int32), ("best_psl", ctypes.c_int32), ("cache_hits", ctypes.c_int64)]
 
 
 WALK_RESULT_FIELDS = [f[0] for f in WalkResult._fields_]
@@ -98,6 +98,8 @@ def lib():
             L.lo_enumerate.argtypes = [i32, P, P, P, P, i32]; L.lo_enumerate.restype = ctypes.c_int
             L.lo_bestfirst.argtypes = [i32, u64, i64, i64, i64, ctypes.POINTER(WalkCfg), i32, P, P, P, P, P, i32]
             L.lo_bestfirst.restype = ctypes.c_int
+            L.lo_bestfirst_cached.argtypes = L.lo_bestfirst.argtypes
+            L.lo_bestfirst_cached.restype = ctypes.c_int
             L.lo_walk_replay.argtypes = [i32, u64, i64, i64, ctypes.POINTER(WalkCfg), i32, i32, P, P, i32, i32, P, P,
                                          P, P, P, P, P]
             L.lo_walk_replay.restype = ctypes.c_int
@@ -250,11 +252,12 @@ def walk(L: int, seed: int, walkers: int, steps: int, *, first_walker: int = 0,
 
 def bestfirst(L: int, seed: int, walkers: int, steps: int, *, pq_size: int = 32, first_walker: int = 0,
               tabu_log2: int = 16, probe_cap: int = 32, target: tuple[int, int] = (17, 2), trace: bool = False,
-              nthreads: int = 0) -> dict:
+              nthreads: int = 0, second_hash: bool = False) -> dict:
     """Algorithm 1 as printed (best-first search with a priority queue of pq_size
     entries), for walkers first_walker.. (+walkers); outputs as walk().  Trace codes:
     the low 16 bits of each new S's fingerprint, TRACE_RESTART set after an HT overflow,
-    -1 when the queue ran empty."""
+    -1 when the queue ran empty.  second_hash adds xLastovka's second table of evaluated
+    neighbours (those it holds are skipped; ``cache_hits`` counts them)."""
     cfg = WalkCfg(tabu_log2, probe_cap, 0, target[0], target[1])
     res = (WalkResult * max(walkers, 1))()
     best = np.zeros((walkers, L), dtype=np.int8)
@@ -266,8 +269,9 @@ def bestfirst(L: int, seed: int, walkers: int, steps: int, *, pq_size: int = 32,
     else:
         tc = ti = None
         tcp = tip = None
-    rc = lib().lo_bestfirst(L, seed, first_walker, walkers, steps, ctypes.byref(cfg), pq_size,
-                            ctypes.cast(res, ctypes.c_void_p), _ptr(best), _ptr(final), tcp, tip, nthreads)
+    fn = lib().lo_bestfirst_cached if second_hash else lib().lo_bestfirst
+    rc = fn(L, seed, first_walker, walkers, steps, ctypes.byref(cfg), pq_size,
+            ctypes.cast(res, ctypes.c_void_p), _ptr(best), _ptr(final), tcp, tip, nthreads)
     if rc != 0:
         raise RuntimeError("oracle best-first search failed: %d" % rc)
     out = {f: np.array([getattr(res[w], f) for w in range(walkers)]) for f in WALK_RESULT_FIELDS}

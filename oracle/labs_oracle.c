@@ -335,6 +335,8 @@ typedef struct {
     int32_t overflows;    /* HT insertions that found no free slot */
     int32_t final_psl;    /* PSL (Section 1) of the final and of the best sequence */
     int32_t best_psl;
+    int64_t cache_hits;   /* best-first search with the second table: neighbours skipped
+                             because the table held them (not evaluated) */
 } lo_walk_result;
 
 /* Trace codes, one per step: the flipped free variable i (0..n-1), with bit 16 set
@@ -364,6 +366,8 @@ typedef struct {
     const uint64_t *zkey;
     const lo_replay *replay;
     int32_t objective;  /* 0: ISL (Eq. 2); 1: PSL first, ties by ISL */
+    uint64_t *cache;    /* best-first search: xLastovka's second table of evaluated
+                           neighbours (NULL when off), as many slots as HT */
     int8_t *x, *s, *s_best, *sf, *tried;
     int64_t *delta, *cand_psl, *cand_isl;
     int32_t *order;
@@ -434,7 +438,9 @@ static void restart(lo_walker *w, int64_t steps_done)
 {
     w->restart_index += 1;
     w->res.restarts += 1;
+    uint64_t gen0 = w->ht.gen;
     ht_new_generation(&w->ht);
+    if (w->cache && w->ht.gen < gen0) memset(w->cache, 0, sizeof(uint64_t) * (size_t)(w->ht.mask + 1));
     start(w, steps_done);
 }
 
@@ -610,6 +616,7 @@ typedef struct {
     int32_t *trace_code, *trace_isl;
     int32_t pq_size;  /* 0: the walk; > 0: best-first search with this queue size */
     int32_t objective;  /* walk only: 0 ISL, 1 PSL then ISL */
+    int32_t second_hash;  /* best-first only: xLastovka's second table of evaluated neighbours */
     int64_t next;
     pthread_mutex_t lock;
     int status;
@@ -696,7 +703,9 @@ static void *walk_thread(void *arg)
     return NULL;
 }
 
-/* Walkers g0 .. g0+count-1 of length L each take `steps` steps.  Results per walker
+/* Walkers g0 .. g0+count-1 of length L each take `steps` steps of the walk (pq_size 0)
+ * or of the best-first search with a queue of pq_size entries (pq_size > 0; -pq_size
+ * entries and xLastovka's second table when pq_size < 0).  Results per walker
  * go to res[], best_seq/final_seq ([count][L], nullable) and, when trace_code is not
  * NULL, per-step traces ([count][steps]).  nthreads <= 0 uses every online core.
  * Returns 0, -1 on bad arguments, -2 on an internal mismatch, -3 on allocation
@@ -718,7 +727,8 @@ static int walk_many(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_
     job.L = L; job.seed = seed; job.g0 = g0; job.count = count; job.steps = steps;
     job.cfg = cfg; job.zkey = zkey; job.res = res; job.best_seq = best_seq;
     job.final_seq = final_seq; job.trace_code = trace_code; job.trace_isl = trace_isl;
-    job.pq_size = pq_size;
+    job.pq_size = pq_size < 0 ? -pq_size : pq_size;
+    job.second_hash = pq_size < 0;
     job.objective = objective;
     pthread_mutex_init(&job.lock, NULL);
     if (nthreads <= 0) nthreads = (int32_t)sysconf(_SC_NPROCESSORS_ONLN);
@@ -847,10 +857,29 @@ static void bf_note(lo_walker *w, const int8_t *s, int64_t isl, int64_t steps_do
 
 /* One step (expansion of S); e = steps done before it.  Returns the trace code, or
  * -99 on an internal mismatch. */
+/* xLastovka's second table (the reading used here): one 64-bit word per slot, slot =
+ * fingerprint mod its size; a neighbour with fingerprint f is in the table when its slot
+ * holds (gen << 40) | (~f mod 2^40), gen being HT's generation (so a restart empties
+ * both); inserting keeps the larger of the old and the new word, which makes the table's
+ * content independent of the order of the insertions within a step. */
+#define LO_CACHE_LOW 0xFFFFFFFFFFull
+static uint64_t cache_tag(const lo_walker *w, uint64_t f)
+{
+    return ((uint64_t)w->ht.gen << 40) | (~f & LO_CACHE_LOW);
+}
+
 static int32_t bf_step(lo_walker *w, lo_pq *q, int64_t e)
 {
     int32_t L = w->L, n = w->n;
     if (lo_neighbor_delta(w->s, L, w->delta) != 0) return -99;
+    if (w->cache) {
+        /* neighbours held by the second table are skipped: not evaluated, not queued */
+        for (int32_t i = 0; i < n; ++i) {
+            uint64_t f = w->fp ^ w->zkey[i];
+            w->tried[i] = w->cache[f & w->ht.mask] == cache_tag(w, f);
+            w->res.cache_hits += w->tried[i];
+        }
+    }
     for (int32_t i = 0; i < n; ++i) {
         int32_t j = i;
         while (j > 0 && cmp_pair(w->delta, i, w->order[j - 1]) < 0) {
@@ -861,6 +890,7 @@ static int32_t bf_step(lo_walker *w, lo_pq *q, int64_t e)
     }
     for (int32_t t = 0; t < n; ++t) {
         int32_t i = w->order[t];
+        if (w->cache && w->tried[i]) continue;
         lo_pq_entry c = {w->isl + w->delta[i], e, i, w->fp ^ w->zkey[i], NULL};
         int32_t last = -1;
         if (q->size == q->cap) {
@@ -878,6 +908,15 @@ static int32_t bf_step(lo_walker *w, lo_pq *q, int64_t e)
         if (m != i) d->s[m] = (int8_t)(-d->s[m]);
         if (lo_isl(d->s, L) != d->isl) return -99;
         bf_note(w, d->s, d->isl, e + 1);
+    }
+    if (w->cache) {
+        /* every neighbour evaluated in this step enters the second table */
+        for (int32_t i = 0; i < n; ++i) {
+            if (w->tried[i]) continue;
+            uint64_t f = w->fp ^ w->zkey[i], tag = cache_tag(w, f);
+            uint64_t *slot = &w->cache[f & w->ht.mask];
+            if (tag > *slot) *slot = tag;
+        }
     }
     for (;;) {
         if (q->size == 0) {
@@ -923,10 +962,12 @@ static int run_bestfirst(lo_walk_job *job, int64_t w_idx)
     w.s_best = (int8_t *)malloc((size_t)L);
     w.delta = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     w.order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    w.tried = (int8_t *)calloc((size_t)n, 1);
     w.ht.mask = (1ull << job->cfg->tabu_log2) - 1;
     w.ht.cap = job->cfg->probe_cap;
     if ((uint64_t)w.ht.cap > w.ht.mask + 1) w.ht.cap = (int32_t)(w.ht.mask + 1);
     w.ht.slot = (uint64_t *)calloc((size_t)(w.ht.mask + 1), sizeof(uint64_t));
+    if (job->second_hash) w.cache = (uint64_t *)calloc((size_t)(w.ht.mask + 1), sizeof(uint64_t));
     w.ht.gen = 1;
     w.best_isl = INT64_MAX;
     w.res.target_step = -1;
@@ -934,7 +975,8 @@ static int run_bestfirst(lo_walk_job *job, int64_t w_idx)
     q.e = (lo_pq_entry *)calloc((size_t)K, sizeof(lo_pq_entry));
     int8_t *store = (int8_t *)malloc((size_t)K * (size_t)L);
     int rc = 0;
-    if (!w.x || !w.s || !w.s_best || !w.delta || !w.order || !w.ht.slot || !q.e || !store) {
+    if (!w.x || !w.s || !w.s_best || !w.delta || !w.order || !w.ht.slot || !q.e || !store || !w.tried ||
+        (job->second_hash && !w.cache)) {
         rc = -3;
         goto done;
     }
@@ -961,6 +1003,7 @@ static int run_bestfirst(lo_walk_job *job, int64_t w_idx)
     if (job->final_seq) memcpy(job->final_seq + w_idx * L, w.s, (size_t)L);
 done:
     free(w.x); free(w.s); free(w.s_best); free(w.delta); free(w.order); free(w.ht.slot); free(q.e); free(store);
+    free(w.tried); free(w.cache);
     return rc;
 }
 
@@ -973,6 +1016,17 @@ int lo_bestfirst(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t st
 {
     if (pq_size < 1) return -1;
     return walk_many(L, seed, g0, count, steps, cfg, pq_size, 0, res, best_seq, final_seq, trace_code, trace_isl,
+                     nthreads);
+}
+
+/* As lo_bestfirst with xLastovka's second table (see cache_tag): neighbours it holds are
+ * skipped, every evaluated neighbour enters it; res[].cache_hits counts the skips. */
+int lo_bestfirst_cached(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t steps, const lo_walk_cfg *cfg,
+                        int32_t pq_size, lo_walk_result *res, int8_t *best_seq, int8_t *final_seq,
+                        int32_t *trace_code, int32_t *trace_isl, int32_t nthreads)
+{
+    if (pq_size < 1) return -1;
+    return walk_many(L, seed, g0, count, steps, cfg, -pq_size, 0, res, best_seq, final_seq, trace_code, trace_isl,
                      nthreads);
 }
 

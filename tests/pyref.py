@@ -179,13 +179,20 @@ def walk(L, seed, g, steps, tabu_log2=16, cap=32, patience=0):
     return codes, isls, st["best"], st["restarts"]
 
 
-def bestfirst(L, seed, g, steps, K, tabu_log2=16, cap=32):
+def bestfirst(L, seed, g, steps, K, tabu_log2=16, cap=32, second=False):
     """Algorithm 1 with a queue of K entries (the readings of the oracle's best-first
-    search); returns (trace_code, trace_isl, best_isl, restarts, overflows)."""
+    search); returns (trace_code, trace_isl, best_isl, restarts, overflows, cache_hits).
+    second: xLastovka's second table of evaluated neighbours, a list of slots holding
+    (generation << 40) | (~fingerprint mod 2^40), the larger word kept on insertion."""
     n = (L + 1) // 2
     keys = [zkey(L, i) for i in range(n)]
     ht = HT(tabu_log2, cap)
-    st = {"r": 0, "best": None, "restarts": 0, "overflows": 0}
+    cache = [0] * ht.size if second else None
+    st = {"r": 0, "best": None, "restarts": 0, "overflows": 0, "hits": 0}
+    low = (1 << 40) - 1
+
+    def tag(f):
+        return (ht.gen << 40) | (~f & low)
 
     def fp_of(s):
         f = 0
@@ -204,9 +211,13 @@ def bestfirst(L, seed, g, steps, K, tabu_log2=16, cap=32):
         return s, e, f
 
     def again():
+        nonlocal cache
         st["r"] += 1
         st["restarts"] += 1
+        g0 = ht.gen
         ht.new_generation()
+        if cache is not None and ht.gen < g0:
+            cache = [0] * ht.size
         return begin()
 
     s, e, f = begin()
@@ -214,7 +225,13 @@ def bestfirst(L, seed, g, steps, K, tabu_log2=16, cap=32):
     codes, isls = [], []
     for t in range(steps):
         cands = []
+        held = set()
+        if cache is not None:
+            held = {i for i in range(n) if cache[(f ^ keys[i]) % ht.size] == tag(f ^ keys[i])}
+            st["hits"] += len(held)
         for i in range(n):
+            if i in held:
+                continue
             u = s.copy()
             u[i] = -u[i]
             if L - 1 - i != i:
@@ -230,6 +247,10 @@ def bestfirst(L, seed, g, steps, K, tabu_log2=16, cap=32):
                 queue.remove(max(queue, key=lambda q: q[:3]))
             queue.append(c)
             st["best"] = min(st["best"], c[0])
+        if cache is not None:
+            for c in cands:
+                j = c[3] % ht.size
+                cache[j] = max(cache[j], tag(c[3]))
         code = None
         while queue:
             top = min(queue, key=lambda q: q[:3])
@@ -250,7 +271,7 @@ def bestfirst(L, seed, g, steps, K, tabu_log2=16, cap=32):
             code = -1
         codes.append(code)
         isls.append(e)
-    return codes, isls, st["best"], st["restarts"], st["overflows"]
+    return codes, isls, st["best"], st["restarts"], st["overflows"], st["hits"]
 
 
 def walk_psl(L, seed, g, steps, tabu_log2=16, cap=32, patience=0):

@@ -105,7 +105,7 @@ def test_bestfirst_matches_python_statement(L, steps, K, log2, cap):
     seed = 2
     out = oracle.bestfirst(L, seed, 3, steps, pq_size=K, tabu_log2=log2, probe_cap=cap, trace=True, nthreads=2)
     for g in range(3):
-        codes, isls, best, restarts, overflows = pyref.bestfirst(L, seed, g, steps, K, log2, cap)
+        codes, isls, best, restarts, overflows, _ = pyref.bestfirst(L, seed, g, steps, K, log2, cap)
         assert list(out["trace_code"][g]) == codes
         assert list(out["trace_isl"][g]) == isls
         assert out["best_isl"][g] == best
@@ -211,3 +211,36 @@ def test_psl_walk_invariants_L101():
     # the PSL walk ends at a lower PSL than the ISL walk's best sequences, on average
     c = oracle.walk(L, 7, 3, steps)
     assert a["best_psl"].mean() < c["best_psl"].mean()
+
+
+# ------------------------------------------ best-first search with xLastovka's second table
+
+@pytest.mark.parametrize("L,steps,K,log2", [(21, 300, 32, 16), (21, 300, 5, 4), (41, 200, 32, 16),
+                                            (13, 300, 3, 6)])
+def test_bestfirst_second_table_matches_python_statement(L, steps, K, log2):
+    """Skipping the neighbours the second table holds, inserting every evaluated one with
+    the larger-word rule, and emptying it with HT at restarts, against the Python
+    statement; the skips happen (cycles are frequent on the skew-symmetric space)."""
+    seed = 3
+    out = oracle.bestfirst(L, seed, 3, steps, pq_size=K, tabu_log2=log2, trace=True, second_hash=True)
+    for g in range(3):
+        codes, isls, best, restarts, overflows, hits = pyref.bestfirst(L, seed, g, steps, K, log2, 32, second=True)
+        assert list(out["trace_code"][g]) == codes
+        assert list(out["trace_isl"][g]) == isls
+        assert out["best_isl"][g] == best and out["restarts"][g] == restarts
+        assert out["overflows"][g] == overflows and out["cache_hits"][g] == hits
+    assert out["cache_hits"].sum() > 0
+
+
+def test_bestfirst_second_table_without_hits_is_the_search():
+    """A neighbour is only ever skipped when the table holds it, so when no skip occurs
+    (a single step from each start, i.e. before anything was inserted) the two searches
+    agree; over a run the table changes the trajectory and saves evaluations."""
+    L = 41
+    a = oracle.bestfirst(L, 5, 4, 1, trace=True)
+    b = oracle.bestfirst(L, 5, 4, 1, trace=True, second_hash=True)
+    assert (b["cache_hits"] == 0).all()
+    for k in ("trace_code", "trace_isl", "best_isl"):
+        assert np.array_equal(a[k], b[k])
+    c = oracle.bestfirst(L, 5, 4, 400, second_hash=True)
+    assert (c["cache_hits"] > 0).all()
