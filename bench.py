@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-delta", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--config", choices=["walk", "learned", "scaleup", "long"], default="walk")
+    ap.add_argument("--config", choices=["walk", "learned", "scaleup", "long", "secondhash"], default="walk")
     ap.add_argument("--long-walkers", type=int, default=608)
     ap.add_argument("--long-steps", type=int, default=512)
     ap.add_argument("--scaleup-walkers", type=int, default=131072)
@@ -552,10 +552,62 @@ def run_long(args):
     return 0
 
 
+def run_secondhash(args):
+    """The ablation of Section 3: the best-first search at L = args.L with and without
+    xLastovka's second table of evaluated neighbours, args.walkers walkers x
+    args.walk_steps steps each: time, flips/s, the share of neighbours the table
+    skipped, best F; one JSON line."""
+    import torch
+
+    import paper_2011_00068_gb300 as labs
+    from paper_2011_00068_gb300 import _native
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = (args.L + 1) // 2
+    out = {}
+    plain, cached = _native.LABS_FLAG_BEST_FIRST, _native.LABS_FLAG_BEST_FIRST | _native.LABS_FLAG_SECOND_HASH
+    runs = [("without", plain, args.walk_steps), ("with", cached, args.walk_steps), ("without_equal_time", plain, 0)]
+    for name, flags, steps in runs:
+        if name == "without_equal_time":  # as many steps as fit in the time the table's run took
+            steps = int(round(args.walk_steps * out["with"]["ms"] / out["without"]["ms"]))
+        s = labs.Search(args.L, args.walkers, args.seed, device=dev, flags=flags)
+        s.walk(64)
+        s.sync()
+        s.reset()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s.stream)
+        s.walk(steps)
+        b.record(s.stream)
+        s.sync()
+        ms = a.elapsed_time(b)
+        st = s.stats()
+        best = s.best()
+        out[name] = {"ms": ms, "steps": steps, "flips_per_s": st["flip_evaluations"] / (ms / 1e3),
+                     "skipped_share": st["cache_hits"] / st["flip_evaluations"],
+                     "new_evaluations_per_s": (st["flip_evaluations"] - st["cache_hits"]) / (ms / 1e3),
+                     "best_isl": best["isl"], "best_F": best["F"], "restarts": st["restarts"]}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    line = {"metric": "best-first search with and without the second table", "value": out["with"]["flips_per_s"],
+            "unit": "flip evaluations/s", "higher_is_better": True, "n_gpus": 1, "dtype": "f32",
+            "data": "synthetic", "vs_baseline": None,
+            "config": {"workload": "L=%d best-first search (queue of 32), %d walkers x %d steps, seed %d, HT and "
+                                   "second table 2^16 slots/walker each" % (args.L, args.walkers, args.walk_steps,
+                                                                           args.seed), "n": n},
+            "runs": out}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "secondhash":
+        return run_secondhash(args)
     if args.config == "long":
         return run_long(args)
     if args.config == "learned":

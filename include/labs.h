@@ -87,6 +87,10 @@ typedef struct labs_config {
                                        search with a queue of LABS_QUEUE_SIZE evaluated
                                        neighbours per walker (see labs_walk); one walker per
                                        warp; not with LABS_FLAG_LEARNED, no checkpoints */
+#define LABS_FLAG_SECOND_HASH 128   /* with LABS_FLAG_BEST_FIRST: xLastovka's second table of
+                                       evaluated neighbours (Section 3), one per walker with
+                                       as many slots as HT; neighbours it holds are skipped
+                                       (see labs_walk) */
 #define LABS_FLAG_PSL 64            /* labs_walk minimises PSL (Section 1) instead of ISL: the
                                        walk's rules with (PSL, ISL) pairs as the objective (see
                                        labs_walk); one walker per warp; not with
@@ -113,6 +117,9 @@ typedef struct labs_counters {
     int32_t best_psl;          /* LABS_FLAG_PSL: PSL of the best sequence (whose ISL is
                                   best_isl; best in the (PSL, ISL) order); else -1 */
     int32_t pad_;
+    int64_t cache_hits;        /* LABS_FLAG_SECOND_HASH: neighbours skipped because the
+                                  second table held them (flip_evaluations counts all n
+                                  per step: the GPU evaluates them anyway) */
 } labs_counters;
 
 /* One record of the walk log (labs_log): the state of a walker at the start of a
@@ -187,6 +194,13 @@ int labs_neighbor_delta(labs_ctx *ctx, const int8_t *dev_seqs, int64_t batch,
  *   the walk; the walker restarts (HT and queue emptied) when the queue runs empty or
  *   HT has no free slot for the new S; `patience` is not used.  At most
  *   LABS_BEST_FIRST_MAX_STEPS steps per walker (LABS_EINVAL beyond).
+ *   LABS_FLAG_SECOND_HASH adds xLastovka's second table (the library's reading of
+ *   Section 3): a slot (fingerprint mod size) holds (HT generation << 40) | (~f mod 2^40)
+ *   of a neighbour f; at the start of a step every neighbour whose slot holds its word is
+ *   skipped (not offered to the queue, counted in cache_hits), and after the queue
+ *   update every other neighbour is inserted by keeping the larger of the slot's old and
+ *   new word (so the table does not depend on the insertion order); a restart empties it
+ *   with HT.
  * With LABS_FLAG_PSL the objective is the pair (PSL, ISL), compared lexicographically
  *   (PSL = max_k |C_k|, Section 1; the paper optimises F and reports PSL in Table 1,
  *   so this order is the library's reading of a PSL search): the step takes the flip

@@ -31,6 +31,7 @@ LABS_FLAG_WARP_PER_WALKER = 8
 LABS_FLAG_TWO_PER_WARP = 16
 LABS_FLAG_BEST_FIRST = 32
 LABS_FLAG_PSL = 64
+LABS_FLAG_SECOND_HASH = 128
 LABS_QUEUE_SIZE = 32
 LABS_BEST_FIRST_MAX_STEPS = 1 << 28
 LOG_RECORD_BYTES = 64
@@ -61,7 +62,8 @@ class LabsCounters(ctypes.Structure):
                 ("overflows", ctypes.c_int64), ("blocked", ctypes.c_int64), ("best_isl", ctypes.c_int32),
                 ("best_L", ctypes.c_int32), ("best_walker", ctypes.c_int64), ("target_step", ctypes.c_int64),
                 ("walkers_at_target", ctypes.c_int64), ("walkers_per_warp", ctypes.c_int32),
-                ("lane_block", ctypes.c_int32), ("best_psl", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("lane_block", ctypes.c_int32), ("best_psl", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("cache_hits", ctypes.c_int64)]
 
 
 class LabsError(RuntimeError):

@@ -32,7 +32,8 @@ struct labs_ctx {
     // workspace layout (byte offsets)
     size_t off_status = 0, off_groups = 0, off_zkeys = 0, off_states = 0, off_trace_start = 0,
            off_trace_ids = 0, off_queue = 0, off_l_scores = 0, off_l_step = 0, off_l_slot = 0, off_l_valid = 0,
-           off_pq_key = 0, off_pq_bits = 0, off_cur_bits = 0, off_best_bits = 0, off_tabu = 0, total = 0;
+           off_pq_key = 0, off_pq_bits = 0, off_cur_bits = 0, off_best_bits = 0, off_tabu = 0, off_tabu2 = 0,
+           total = 0;
     bool long_mode = false;  // lengths above LABS_MAX_L: one walker per CTA, bits beside the states
     // device pointers kept in the status block (restored after every reset)
     labs_log_record* log = nullptr;
@@ -130,6 +131,7 @@ KParams params(labs_ctx* c)
     p.best_first = (c->cfg.flags & LABS_FLAG_BEST_FIRST) ? 1 : 0;
     p.pq_key = p.best_first ? at<uint64_t>(c, c->off_pq_key) : nullptr;
     p.pq_bits = p.best_first ? at<uint32_t>(c, c->off_pq_bits) : nullptr;
+    p.tabu2 = (c->cfg.flags & LABS_FLAG_SECOND_HASH) ? at<uint64_t>(c, c->off_tabu2) : nullptr;
     p.mode = (c->cfg.flags & LABS_FLAG_PSL) ? 3 : p.best_first ? 2 : (c->l_params ? 1 : 0);
     return p;
 }
@@ -212,6 +214,8 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     if (nL < 1 || nL > LABS_MAX_GROUPS) return fail(c, LABS_EINVAL, "need 1..%d lengths", LABS_MAX_GROUPS);
     if ((k.flags & LABS_FLAG_BEST_FIRST) && (k.flags & LABS_FLAG_LEARNED))
         return fail(c, LABS_EINVAL, "LABS_FLAG_BEST_FIRST and LABS_FLAG_LEARNED do not combine");
+    if ((k.flags & LABS_FLAG_SECOND_HASH) && !(k.flags & LABS_FLAG_BEST_FIRST))
+        return fail(c, LABS_EINVAL, "LABS_FLAG_SECOND_HASH needs LABS_FLAG_BEST_FIRST");
     if ((k.flags & LABS_FLAG_PSL) && (k.flags & (LABS_FLAG_BEST_FIRST | LABS_FLAG_LEARNED)))
         return fail(c, LABS_EINVAL, "LABS_FLAG_PSL combines with neither LABS_FLAG_BEST_FIRST nor LABS_FLAG_LEARNED");
     if (nL >= 1 && Ls && valid_long_L(Ls[0])) {
@@ -284,6 +288,10 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     }
     c->off_tabu = off;
     off = align_up(off + sizeof(uint64_t) * ((size_t)c->W << k.tabu_log2), 256);
+    if (k.flags & LABS_FLAG_SECOND_HASH) {  // zeroed with HT by labs_reset (it follows HT)
+        c->off_tabu2 = off;
+        off = align_up(off + sizeof(uint64_t) * ((size_t)c->W << k.tabu_log2), 256);
+    }
     c->total = off;
     // launch shape of the walk kernel: four walkers per warp (8 lanes each) while 8
     // lanes cover n with at most kQuadMaxR outputs per lane (n <= 80; measured faster
@@ -796,7 +804,7 @@ int labs_stats(labs_ctx* c, int32_t L, labs_counters* out)
     if (e != cudaSuccess) return cuda_fail(c, e, "status read");
     h.best_key = ~0ull;
     h.best_obj = ~0ull;
-    h.st_steps = h.st_evals = h.st_restarts = h.st_overflows = h.st_blocked = h.st_at_target = 0;
+    h.st_steps = h.st_evals = h.st_restarts = h.st_overflows = h.st_blocked = h.st_at_target = h.st_cache_hits = 0;
     h.st_target_step = LLONG_MAX;
     e = cudaMemcpy(st, &h, sizeof(h), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e, "status write");
@@ -811,6 +819,7 @@ int labs_stats(labs_ctx* c, int32_t L, labs_counters* out)
     out->restarts = (int64_t)h.st_restarts;
     out->overflows = (int64_t)h.st_overflows;
     out->blocked = (int64_t)h.st_blocked;
+    out->cache_hits = (int64_t)h.st_cache_hits;
     out->walkers_at_target = (int64_t)h.st_at_target;
     out->walkers_per_warp = kWarp / c->tile;  // 0 for long sequences: one walker per CTA
     out->lane_block = c->long_mode ? long_R(c->n_max) : lanes_for(c->n_max, c->tile);

@@ -1433,6 +1433,11 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
     const int cap = p.probe_cap;
     const int tisl = target_isl(p, env.L);
     uint64_t qk = qkey[lane];
+    // xLastovka's second table (null when off): slot f mod size holds
+    // (generation << 40) | (~f mod 2^40) of an evaluated neighbour f
+    uint64_t* T2 = p.tabu2 != nullptr ? p.tabu2 + (env.T - p.tabu) : nullptr;
+    constexpr uint64_t kLow40 = 0xFFFFFFFFFFull;
+    int64_t hits = 0;
     float P[R];
     p_direct(V, n, o, P);
     StopCheck stop;
@@ -1451,6 +1456,34 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
             float X[R];
             toeplitz(V, n, o, X);
             lane_keys(V, n, o, X, P, key);
+        }
+        if (T2 != nullptr) {
+            // neighbours the table holds are skipped (their keys dropped); every other
+            // one is inserted once all lanes have looked (larger word kept: the table
+            // does not depend on the order of the insertions)
+            uint64_t ins[R];
+            int h = 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                ins[r] = 0ull;
+                if (key[r] == 0xFFFFFFFFu) continue;
+                const uint64_t f = w.fp ^ __ldg(env.zk + (key[r] & 0xFFu));
+                const uint64_t tag = ((uint64_t)w.gen << 40) | (~f & kLow40);
+                if (T2[f & env.tmask] == tag) {
+                    key[r] = 0xFFFFFFFFu;
+                    ++h;
+                } else {
+                    ins[r] = f;
+                }
+            }
+            hits += t.radd(h);
+            t.sync();
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (key[r] != 0xFFFFFFFFu)
+                    atomicMax(reinterpret_cast<unsigned long long*>(T2 + (ins[r] & env.tmask)),
+                              (unsigned long long)(((uint64_t)w.gen << 40) | (~ins[r] & kLow40)));
+            t.sync();
         }
         // Neighbours in queue order (ISL, then i: the packed keys' order) while they
         // come before the queue's last entry or the queue has a free place.  The queue's
@@ -1573,7 +1606,12 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
         w.steps += 1;
         if (again) {
             qk = ~0ull;
+            const uint32_t gen0 = w.gen;
             restart_walker(env, w, base, SL, V, t);
+            if (T2 != nullptr && w.gen < gen0) {  // generations wrapped: HT was zeroed, so is T2
+                for (int64_t i = lane; i <= (int64_t)env.tmask; i += 32) T2[i] = 0ull;
+                t.sync();
+            }
             p_direct(V, n, o, P);
         }
         t.sync();
@@ -1586,6 +1624,7 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
         }
     }
     qkey[lane] = qk;
+    if (lane == 0) env.st->cache_hits += hits;
 }
 
 // One launch advances every walker by up to chunk_steps steps toward the target.  The

@@ -57,7 +57,7 @@ struct alignas(32) WalkerState {
     int32_t psl;               // PSL objective only: PSL of `cur`, of `best`, and the
     int32_t best_psl;          // PSL of the best (PSL, ISL) pair since the last (re)start
     int32_t since_psl;         // (whose ISL is since_best)
-    int32_t pad_[2];
+    int64_t cache_hits;        // best-first search with the second table: skipped neighbours
 };
 static_assert(sizeof(WalkerState) == 160, "WalkerState layout");
 
@@ -74,7 +74,7 @@ struct alignas(256) DevStatus {
     unsigned long long best_key;  // (best_isl << 32) | walker, reduction target
     unsigned long long best_obj;  // PSL objective: lowest (best_psl << 32) | best_isl
     // stats accumulators (labs_stats)
-    unsigned long long st_steps, st_evals, st_restarts, st_overflows, st_blocked, st_at_target;
+    unsigned long long st_steps, st_evals, st_restarts, st_overflows, st_blocked, st_at_target, st_cache_hits;
     long long st_target_step;     // min over walkers, LLONG_MAX = none
     unsigned long long probe_ns;  // %globaltimer sample (clock alignment for deadlines)
     // walk log (labs_log): record k*W + w is walker w's chunk k since arming
@@ -133,6 +133,8 @@ struct KParams {
     uint32_t* best_bits;      // and of the best sequence (WalkerState.cur / best unused)
     uint64_t* pq_key;         // [W][LABS_QUEUE_SIZE] queue keys, ~0 = empty
     uint32_t* pq_bits;        // [W][LABS_QUEUE_SIZE][kBitWords] queue entries' free variables
+    uint64_t* tabu2;          // best-first search: xLastovka's second table, as many slots per
+                              // walker as HT (null when off)
     uint64_t seed;
 };
 

@@ -427,6 +427,7 @@ __global__ void stats_kernel(KParams p, int L)
         atomicAdd(&s->st_restarts, (unsigned long long)st.restarts);
         atomicAdd(&s->st_overflows, (unsigned long long)st.overflows);
         atomicAdd(&s->st_blocked, (unsigned long long)st.blocked);
+        atomicAdd(&s->st_cache_hits, (unsigned long long)st.cache_hits);
         if (st.target_step >= 0) {
             atomicAdd(&s->st_at_target, 1ull);
             atomicMin(&s->st_target_step, (long long)st.target_step);

@@ -96,3 +96,48 @@ def test_bestfirst_refusals():
     with pytest.raises(labs.LabsError):
         s.walk(_native.LABS_BEST_FIRST_MAX_STEPS)
     s.close()
+
+
+SH = _native.LABS_FLAG_SECOND_HASH
+
+
+@pytest.mark.parametrize("L,walkers,steps,kw", [
+    (21, 6, 500, {}),
+    (21, 4, 400, {"tabu_log2": 4, "probe_cap": 3}),
+    (41, 8, 600, {}),
+    (201, 6, 300, {}),
+    (303, 3, 200, {"tabu_log2": 10}),
+])
+def test_second_table_parity(L, walkers, steps, kw):
+    """xLastovka's second table: skipped neighbours, insertions and the emptying at
+    restarts give the oracle's trajectory, results and skip count bit for bit."""
+    seed = 4
+    s, code, isl = traced(L, walkers, steps, seed, flags=BF | SH, **kw)
+    o = oracle.bestfirst(L, seed, walkers, steps, pq_size=K, trace=True, second_hash=True, **kw)
+    assert np.array_equal(code, o["trace_code"])
+    assert np.array_equal(isl, o["trace_isl"])
+    res = s.results(seqs=True)
+    assert np.array_equal(res["best_isl"], o["best_isl"])
+    assert np.array_equal(res["seq"], o["final_seq"])
+    assert np.array_equal(res["best_seq"], o["best_seq"])
+    st = s.stats()
+    assert st["cache_hits"] == int(o["cache_hits"].sum()) > 0
+    assert st["restarts"] == int(o["restarts"].sum())
+    s.close()
+
+
+def test_second_table_chunking_and_refusal():
+    L, W, steps, seed = 61, 8, 500, 7
+    ref = None
+    for cfg in ({}, {"chunk_steps": 13}, {"chunk_steps": 100, "warps_per_cta": 2}):
+        s, code, isl = traced(L, W, steps, seed, flags=BF | SH, **cfg)
+        if ref is None:
+            ref = (code, isl, s.stats()["cache_hits"])
+        else:
+            assert np.array_equal(code, ref[0]) and np.array_equal(isl, ref[1])
+            assert s.stats()["cache_hits"] == ref[2]
+        s.close()
+    o = oracle.bestfirst(L, seed, W, steps, pq_size=K, trace=True, second_hash=True)
+    assert np.array_equal(ref[0], o["trace_code"]) and ref[2] == int(o["cache_hits"].sum())
+    with pytest.raises(labs.LabsError):
+        labs.Search(41, 4, 1, flags=SH)  # the second table belongs to the best-first search
