@@ -1488,39 +1488,19 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
         // Neighbours in queue order (ISL, then i: the packed keys' order) while they
         // come before the queue's last entry or the queue has a free place.  The queue's
         // last entry only moves forward during the step, so the neighbours after its
-        // value at the start cannot enter: the others are looked up in HT all at once
-        // (each lane its own, home slots first), then inserted in order.
+        // value at the start cannot enter; the others are looked up in HT one by one as
+        // the insertion reaches them (HT does not change during the insertion, so this
+        // equals looking them all up first, at a few probes per step instead of one per
+        // neighbour).
         const bool full0 = t.ballot(qk == ~0ull) == 0u;
         const uint64_t last0 = full0 ? warp_max64(qk) : ~0ull;
-        bool fresh[R];  // candidate r: not in HT, before last0
-        {
-            uint64_t fr[R], er[R];
-            const uint64_t gen = w.gen;
+        bool fresh[R];  // candidate r: before last0
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const unsigned k = key[r];
-                const int i = (int)(k & 0xFFu);
-                const uint64_t ck = ((uint64_t)(w.isl + (int)(k >> 8) - (1 << 23)) << 36) | ((uint64_t)e << 8) |
-                                    (uint64_t)i;
-                fresh[r] = k != 0xFFFFFFFFu && ck < last0;
-                fr[r] = fresh[r] ? w.fp ^ __ldg(env.zk + i) : 0ull;
-                er[r] = fresh[r] ? env.T[fr[r] & env.tmask] : 0ull;
-            }
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (!fresh[r]) continue;
-                const uint64_t tag = (fr[r] & ~kGenMask) | gen;
-                uint64_t x = er[r];
-                for (int sl = 1;; ++sl) {
-                    if ((x & kGenMask) != gen) break;  // free slot: not in HT
-                    if (x == tag) {
-                        fresh[r] = false;
-                        break;
-                    }
-                    if (sl >= cap) break;  // chain full within the cap: not found
-                    x = env.T[(fr[r] + (uint64_t)sl) & env.tmask];
-                }
-            }
+        for (int r = 0; r < R; ++r) {
+            const unsigned k = key[r];
+            const uint64_t ck = ((uint64_t)(w.isl + (int)(k >> 8) - (1 << 23)) << 36) | ((uint64_t)e << 8) |
+                                (uint64_t)(k & 0xFFu);
+            fresh[r] = k != 0xFFFFFFFFu && ck < last0;
         }
         unsigned floor = 0u;
         for (;;) {
@@ -1542,6 +1522,22 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
                 const uint64_t last = warp_max64(qk);
                 if (ck > last) break;  // every later neighbour comes after it too
                 dst = __ffs(t.ballot(qk == last)) - 1;
+            }
+            {
+                // HT lookup of this neighbour: up to probe_cap slots, four per round
+                const uint64_t f = w.fp ^ __ldg(env.zk + i);
+                const uint64_t tag = (f & ~kGenMask) | w.gen;
+                bool visited = false;
+                for (int s0 = 0; s0 < cap; s0 += 4) {
+                    const bool mine = lane < 4 && s0 + lane < cap;
+                    const uint64_t x = mine ? env.T[(f + (uint64_t)(s0 + lane)) & env.tmask] : 0ull;
+                    const unsigned bal = t.ballot(mine && (((x & kGenMask) != w.gen) || x == tag));
+                    if (bal) {
+                        visited = t.shfl(x == tag ? 1 : 0, __ffs(bal) - 1) != 0;
+                        break;
+                    }
+                }
+                if (visited) continue;
             }
             if (lane == dst) qk = ck;
             const uint32_t word = w.word ^ (lane == (i >> 5) ? 1u << (i & 31) : 0u);
