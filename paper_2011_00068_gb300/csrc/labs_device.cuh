@@ -1631,17 +1631,12 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
 // learned mode, 2 the best-first search (one variant per kernel keeps the code small).
 // ------------------------------------------------------------ PSL objective walk
 
-// PSL of every neighbour S_i for the lane's outputs i = 2(v0+r)+p: flipping s_i and its
-// mirror s_{L-1-i} changes C_{2m} by -4 s_i (s_{i-2m} + s_{i+2m}) with the mirror's own
-// term (i+2m = L-1-i, m = c-i) left out, or by -2 s_c (s_{c-2m} + s_{c+2m}) at the
-// centre; the odd-lag C_k stay zero.  pl[r] = max_m |C_{2m} + dC_{2m}| (Section 1's
-// PSL), m = 1..n-1.  The class entries s_{i-2m} = A_p[v-m] and s_{i+2m} = A_p[v+m] sit
-// in two register windows of R values that slide by one entry per m, so that each m
-// costs three shared loads (two window entries and C_{2m}) for R outputs; the windows
-// are ring buffers indexed modulo R, with m stepping through blocks of R.  Exact in
-// fp32: every value is an integer of magnitude below 2^10.
+// The same PSL values for wide lane blocks (R >= 7), where the three rings of psl_eval
+// would not fit the registers: s_{i-2m} and s_{i+2m} of the R outputs in two windows of
+// R values that slide one class entry per lag (three shared loads per lag), and the
+// mirror's term dropped by a compare and select per lag term.
 template <int R>
-__device__ __forceinline__ void psl_eval(const View& V, int n, const Outs<Tile<32>, R>& o, int (&pl)[R])
+__device__ __forceinline__ void psl_eval_select(const View& V, int n, const Outs<Tile<32>, R>& o, int (&pl)[R])
 {
     const float* A = (o.p ? V.A1 : V.A0) + o.v0;
     const int c = n - 1;
@@ -1673,6 +1668,85 @@ __device__ __forceinline__ void psl_eval(const View& V, int n, const Outs<Tile<3
                 const float a = lo[(j - r + R) % R];
                 const float b = m == q0[r] ? 0.f : hi[(j + r) % R];
                 mx[r] = fmaxf(mx[r], fabsf(fmaf(cs[r], a + b, C)));
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) pl[r] = (int)mx[r];
+}
+
+// PSL of every neighbour S_i for the lane's outputs i = 2(v0+r)+p: flipping s_i and its
+// mirror s_{L-1-i} changes C_{2m} by -4 s_i (s_{i-2m} + s_{i+2m}) with the mirror's own
+// term (i+2m = L-1-i, i.e. m = c-i) left out, or by -2 s_c (s_{c-2m} + s_{c+2m}) at the
+// centre; the odd-lag C_k stay zero.  pl[r] = max_m |C_{2m} + dC_{2m}(i)| over
+// m = 1..n-1 (Section 1's PSL).
+// Output r takes lag m = t - 2r at iteration t, so that every output of the lane meets
+// its mirror at the same iteration t* = c - p - 2 v0 (where m = c - i): there one
+// multiplier z = 0 drops the mirror term of all of them, and a lag term costs three
+// instructions (FMA, FMA, max of the absolute value).  s_{i-2m} = A_p[v0 + 3r - t],
+// C_{2m} = E[t - 2r] and s_{i+2m} = A_p[v0 + t - r] come from three register rings of
+// P = 3R - 2 entries indexed by t mod P (one new shared load each per iteration, the
+// loop unrolled by P so that the ring indices are constants).  Lags outside 1..n-1 (the
+// first 2R - 2 and the last iterations) are masked in the blocks that hold them.  Exact
+// in fp32: every value is an integer of magnitude below 2^10.
+template <int R>
+__device__ __forceinline__ void psl_eval(const View& V, int n, const Outs<Tile<32>, R>& o, int (&pl)[R])
+{
+    if constexpr (R >= 7) {
+        psl_eval_select<R>(V, n, o, pl);
+        return;
+    }
+    constexpr int P = 3 * R - 2;
+    const float* A = (o.p ? V.A1 : V.A0) + o.v0;
+    const int c = n - 1;
+    const int tstar = c - o.p - 2 * o.v0;
+    const int tend = n - 1 + 2 * (R - 1);
+    float cs[R], mx[R], ra[P], rc[P], rb[P];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = 2 * (o.v0 + r) + o.p;
+        cs[r] = (i == c ? -2.f : -4.f) * A[r];
+        mx[r] = 0.f;
+    }
+    // entries e = -P+1 .. -1 (read only by masked lags)
+#pragma unroll
+    for (int k = 1; k < P; ++k) {
+        ra[k] = A[P - k];
+        rc[k] = V.G[k - P].x;
+        rb[k] = A[k - P];
+    }
+    for (int t0 = 0; t0 <= tend; t0 += P) {
+        if (t0 >= 2 * R - 1 && t0 + P - 1 <= c) {
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                const int t = t0 + j;
+                ra[j] = A[-t];
+                rc[j] = V.G[t].x;
+                rb[j] = A[t];
+                const float z = t == tstar ? 0.f : 1.f;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float cp = fmaf(cs[r], fmaf(rb[(j - r + P) % P], z, ra[(j - 3 * r + 3 * P) % P]),
+                                          rc[(j - 2 * r + 2 * P) % P]);
+                    mx[r] = fmaxf(mx[r], fabsf(cp));
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                const int t = t0 + j;
+                if (t > tend) break;
+                ra[j] = A[-t];
+                rc[j] = V.G[t].x;
+                rb[j] = A[t];
+                const float z = t == tstar ? 0.f : 1.f;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float cp = fmaf(cs[r], fmaf(rb[(j - r + P) % P], z, ra[(j - 3 * r + 3 * P) % P]),
+                                          rc[(j - 2 * r + 2 * P) % P]);
+                    const int m = t - 2 * r;
+                    if (m >= 1 && m <= c) mx[r] = fmaxf(mx[r], fabsf(cp));
+                }
             }
         }
     }

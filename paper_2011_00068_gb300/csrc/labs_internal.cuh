@@ -206,13 +206,20 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
         int hi = (3 * n_max) / 2 + 2 > n_max + 8 ? (3 * n_max) / 2 + 2 : n_max + 8;
         if ((n_max + 1) / 2 + span > hi) hi = (n_max + 1) / 2 + span;
         if (3 * (tile / 2) * R > hi) hi = 3 * (tile / 2) * R;
-        // the PSL neighbourhood reads class entries up to v0 + n + R - 2 (v0 <= (tile/2 - 1) R)
-        if (n_max + (tile / 2) * R > hi) hi = n_max + (tile / 2) * R;
-        const int lo = n_max > span ? n_max : span;
+        int lo = n_max > span ? n_max : span;
+        int gtop = top > span ? top : span;
+        if (tile == 32) {
+            // the PSL neighbourhood (one walker per warp) runs its lags 2R - 2 past n - 1:
+            // class entries from v0 - n - 2R up to v0 + n + 2R (v0 <= (tile/2 - 1) R) and
+            // the table up to n + 2R
+            if (n_max + (tile / 2 + 2) * R > hi) hi = n_max + (tile / 2 + 2) * R;
+            if (n_max + 2 * R > lo) lo = n_max + 2 * R;
+            if (n_max + 2 * R > gtop) gtop = n_max + 2 * R;
+        }
         w.apad = (lo + 3) & ~3;
         w.alen = w.apad + ((hi + 7) & ~7);
         w.gpad = (tile / 2) * R > span ? (tile / 2) * R : span;
-        w.glen = w.gpad + (top > span ? top : span);
+        w.glen = w.gpad + gtop;
     }
     w.goff = 2 * w.alen;
     w.boff = w.goff + 2 * w.glen;
