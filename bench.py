@@ -541,7 +541,7 @@ def run_long(args):
     total = sum(v["flips_per_s"] * v["ms"] for v in out.values()) / sum(v["ms"] for v in out.values())
     line = {"metric": "exact flip evaluations/sec, long sequences", "value": total, "unit": "flip evaluations/s",
             "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic", "vs_baseline": None,
-            "config": {"workload": "L=2047, 4095 and 8191, %d walkers each (one per CTA of 512 threads), %d steps, "
+            "config": {"workload": "L=2047, 4095 and 8191, %d walkers each (one per CTA of 256 or 512 threads), %d steps, "
                                    "seed 42, uniform random +-1 Philox starts, HT 2^16 slots/walker"
                                    % (args.long_walkers, args.long_steps),
                        "kernel": "long_walk_kernel",

@@ -122,7 +122,7 @@ KParams params(labs_ctx* c)
     p.target_num = c->cfg.target_num;
     p.target_den = c->cfg.target_den;
     p.chunk_steps = c->chunk;
-    p.rmax = c->long_mode ? long_R(c->n_max) : lanes_for(c->n_max, c->tile);
+    p.rmax = c->long_mode ? long_R(c->n_max, c->tile) : lanes_for(c->n_max, c->tile);
     p.tile = c->tile;
     p.long_mode = c->long_mode ? 1 : 0;
     p.cur_bits = c->long_mode ? at<uint32_t>(c, c->off_cur_bits) : nullptr;
@@ -299,15 +299,15 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     // each) up to 10 outputs per lane (n <= 160), else one walker per warp (the learned
     // mode runs one walker per warp)
     if (c->long_mode) {
-        // one walker per CTA of kLongThreads threads
-        c->tile = kLongThreads;
-        c->smem_bytes = (size_t)long_smem(c->n_max).words * sizeof(int);
+        // one walker per CTA of 256 or 512 threads
+        c->tile = long_threads(c->n_max);
+        c->smem_bytes = (size_t)long_smem(c->n_max, c->tile).words * sizeof(int);
         int occ = 0;
-        if (long_kernel_config(long_R(c->n_max), c->smem_bytes, &occ, &c->regs) != LABS_OK || occ < 1)
+        if (long_kernel_config(c->n_max, c->smem_bytes, &occ, &c->regs) != LABS_OK || occ < 1)
             return fail(c, LABS_ECUDA, "long walk kernel does not fit on an SM (%zu bytes of shared memory)",
                         c->smem_bytes);
         c->ctas_per_sm = occ;
-        c->warps_per_cta = kLongThreads / kWarp;
+        c->warps_per_cta = c->tile / kWarp;
         c->grid = c->sms * c->ctas_per_sm;
         c->chunk = k.chunk_steps ? k.chunk_steps : 64;
     } else {
@@ -822,7 +822,7 @@ int labs_stats(labs_ctx* c, int32_t L, labs_counters* out)
     out->cache_hits = (int64_t)h.st_cache_hits;
     out->walkers_at_target = (int64_t)h.st_at_target;
     out->walkers_per_warp = kWarp / c->tile;  // 0 for long sequences: one walker per CTA
-    out->lane_block = c->long_mode ? long_R(c->n_max) : lanes_for(c->n_max, c->tile);
+    out->lane_block = c->long_mode ? long_R(c->n_max, c->tile) : lanes_for(c->n_max, c->tile);
     out->target_step = h.st_target_step == LLONG_MAX ? -1 : (int64_t)h.st_target_step;
     out->best_psl = -1;
     if (h.best_key == ~0ull) {

@@ -16,7 +16,9 @@ constexpr int kBitWords = kMaxN / 32;        // 8 words of free-variable bits
 // kLongThreads threads; their free-variable bits live beside the walker states.
 constexpr int kMaxNLong = (LABS_MAX_L_LONG + 1) / 2;  // 4096 free variables
 constexpr int kBitWordsLong = kMaxNLong / 32;          // 128 words
-constexpr int kLongThreads = 512;
+constexpr int kLongThreads = 512;       // threads of a long walker's CTA, n > kLongSmallMaxN
+constexpr int kLongThreadsSmall = 256;  // ... for n <= kLongSmallMaxN (two CTAs per SM)
+constexpr int kLongSmallMaxN = 2304;    // lane block <= 9 with 256 threads
 constexpr int kQuadMaxR = 10;                // largest lane block of four walkers per warp (n <= 80)
 constexpr int kMaxChunksPerCall = 4096;      // chunk launches per labs_walk call
 constexpr int kMaxTrace = 4096;              // traced walkers
@@ -229,11 +231,17 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
     return w;
 }
 
-// Lane block of the long layout: ceil(ceil(n/2) / (kLongThreads/2)) raised to odd, so that
-// the lanes of a warp (all in one parity class, R entries apart) hit distinct banks.
-__host__ __device__ inline int long_R(int n)
+// Threads of a long walker's CTA for n_max free variables.
+__host__ __device__ inline int long_threads(int n_max)
 {
-    const int h = kLongThreads / 2;
+    return n_max <= kLongSmallMaxN ? kLongThreadsSmall : kLongThreads;
+}
+
+// Lane block of the long layout: ceil(ceil(n/2) / (threads/2)) raised to odd, so that the
+// lanes of a warp (all in one parity class, R entries apart) hit distinct banks.
+__host__ __device__ inline int long_R(int n, int threads)
+{
+    const int h = threads / 2;
     const int R = (((n + 1) >> 1) + h - 1) / h;
     return R | 1;
 }
@@ -241,10 +249,10 @@ __host__ __device__ inline int long_R(int n)
 // Shared-memory layout of one long walker (one CTA): the rows and the table as in the
 // warp layout (bounds from the tile code with tile = kLongThreads), bit vectors sized
 // for n_max, then the CTA scratch and the bits.
-__host__ __device__ inline WarpSmem long_smem(int n_max)
+__host__ __device__ inline WarpSmem long_smem(int n_max, int tile)
 {
     WarpSmem w;
-    const int tile = kLongThreads, R = long_R(n_max);
+    const int R = long_R(n_max, tile);
     const int top = ((n_max + 7) & ~7) + 2;
     const int span = tile * R + 2;
     int hi = (3 * n_max) / 2 + 2 > n_max + 8 ? (3 * n_max) / 2 + 2 : n_max + 8;
@@ -258,7 +266,7 @@ __host__ __device__ inline WarpSmem long_smem(int n_max)
     w.boff = w.goff + 2 * w.glen;
     w.bvec = (n_max + 31) / 32 + 2;
     w.xoff = (w.boff + 4 * w.bvec + 3) & ~3;
-    w.words = w.xoff + kLongThreads + kBitWordsLong;
+    w.words = w.xoff + tile + kBitWordsLong;
     return w;
 }
 
@@ -288,7 +296,7 @@ WalkFn walk_fn32b(int rmax);  // best-first search (labs_walk32b.cu)
 WalkFn walk_fn32p(int rmax);  // walk under the PSL objective (labs_walk32p.cu)
 
 // Long-L walk (labs_long.cu).
-int long_kernel_config(int R, size_t smem_bytes, int* ctas_per_sm, int* regs);
+int long_kernel_config(int n_max, size_t smem_bytes, int* ctas_per_sm, int* regs);
 int launch_long_reset(const KParams& p, size_t smem_bytes, void* stream);
 int launch_long_walk_chunk(const KParams& p, int chunk_index, int grid, size_t smem_bytes, void* stream);
 int launch_long_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status, void* stream);

@@ -1,5 +1,5 @@
 // labs_long.cu -- the walk for long sequences (LABS_MAX_L < L <= LABS_MAX_L_LONG): one
-// CTA of kLongThreads threads runs one walker.  The step is the walk's (Algorithm 1 in
+// CTA of 256 or 512 threads runs one walker (long_threads).  The step is the walk's (Algorithm 1 in
 // its self-avoiding form): all n flips evaluated by the Toeplitz form of dISL, the
 // lowest (dISL, i) whose result is not in HT taken, C_k and P updated in O(n) per move.
 // The per-lane arithmetic is the warp kernels' (labs_device.cuh), run by a lane group
@@ -11,7 +11,7 @@ namespace labsgpu {
 namespace {
 
 // The CTA as one lane group (the interface of Tile<>; every call must be reached by all
-// threads).  x: kLongThreads words of shared scratch.
+// threads).  x: NT words of shared scratch.
 template <int NT>
 struct Blk {
     static constexpr int kSize = NT;
@@ -82,8 +82,6 @@ struct Blk {
     }
 };
 
-using LB = Blk<kLongThreads>;
-
 // One long walker: the walk's environment plus its bit rows in global memory and the
 // CTA's shared copy of the current bits.
 struct LongWalk {
@@ -96,6 +94,7 @@ struct LongWalk {
 };
 
 // Zeroes rows, table and bit vectors (everything below the scratch and the bits).
+template <class LB>
 __device__ __forceinline__ void long_clear(int* base, const WarpSmem& SL, const LB& t)
 {
     int4* b4 = reinterpret_cast<int4*>(base);
@@ -105,6 +104,7 @@ __device__ __forceinline__ void long_clear(int* base, const WarpSmem& SL, const 
 
 // Rows from the shared bits (Eq. 4: s_j = x_j for j <= c, s_{c+t} = (-1)^t x_{c-t}),
 // then the table; returns the ISL.
+template <class LB>
 __device__ int long_load_rows(const LongWalk& lw, const WarpSmem& SL, int* base, const View& V, uint32_t word,
                               const LB& t)
 {
@@ -123,6 +123,7 @@ __device__ int long_load_rows(const LongWalk& lw, const WarpSmem& SL, int* base,
 }
 
 // HT fingerprint of the shared bits (long_load_rows ran first).
+template <class LB>
 __device__ uint64_t long_fingerprint(const LongWalk& lw, const LB& t)
 {
     uint64_t f = 0;
@@ -133,6 +134,7 @@ __device__ uint64_t long_fingerprint(const LongWalk& lw, const LB& t)
     return (uint64_t)lo | ((uint64_t)hi << 32);
 }
 
+template <class LB>
 __device__ __forceinline__ void long_note_best(const LongWalk& lw, Walker& w, const LB& t)
 {
     if (w.isl < w.best_isl) {
@@ -145,6 +147,7 @@ __device__ __forceinline__ void long_note_best(const LongWalk& lw, Walker& w, co
 
 // Algorithm 1 start: random S (restart index w.restart_idx), rows, table, ISL, HT
 // insertion, best update.
+template <class LB>
 __device__ void long_start(const LongWalk& lw, Walker& w, const WarpSmem& SL, int* base, const View& V,
                            const LB& t)
 {
@@ -159,6 +162,7 @@ __device__ void long_start(const LongWalk& lw, Walker& w, const WarpSmem& SL, in
     long_note_best(lw, w, t);
 }
 
+template <class LB>
 __device__ void long_restart(const LongWalk& lw, Walker& w, const WarpSmem& SL, int* base, const View& V,
                              const LB& t)
 {
@@ -176,6 +180,7 @@ __device__ void long_restart(const LongWalk& lw, Walker& w, const WarpSmem& SL, 
 
 // HT probe of f by the first warp (the walk's linear probe of up to probe_cap <= 32
 // slots), result shared with the CTA.
+template <class LB>
 __device__ Probe long_probe(const LongWalk& lw, uint64_t f, uint32_t gen, const LB& t)
 {
     long long* y = reinterpret_cast<long long*>(t.x);
@@ -196,7 +201,7 @@ __device__ Probe long_probe(const LongWalk& lw, uint64_t f, uint32_t gen, const 
 }
 
 // Steps of one long walker until `until` (or a stop request, or the exact-range check).
-template <int R>
+template <class LB, int R>
 __device__ void long_walk(const LongWalk& lw, Walker& w, int64_t until, const WarpSmem& SL, int* base,
                           const View& V, int trace_slot, int64_t trace_start, const LB& t)
 {
@@ -314,12 +319,14 @@ __device__ LongWalk long_env(const KParams& p, int64_t wi, const DevGroup& G, ui
 
 // First start of every long walker (restart index 0, HT generation 1; HT zeroed by the
 // caller), one walker per CTA at a time.
-__global__ void __launch_bounds__(kLongThreads, 1) long_reset_kernel(KParams p)
+template <int NT>
+__global__ void __launch_bounds__(NT, kLongThreads / NT) long_reset_kernel(KParams p)
 {
+    using LB = Blk<NT>;
     extern __shared__ __align__(16) int smem[];
-    const WarpSmem SL = long_smem(p.n_max);
+    const WarpSmem SL = long_smem(p.n_max, NT);
     const LB t(threadIdx.x, smem + SL.xoff);
-    uint32_t* bits = reinterpret_cast<uint32_t*>(smem + SL.xoff + kLongThreads);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(smem + SL.xoff + NT);
     const View V = make_view(smem, SL);
     for (int64_t wi = blockIdx.x; wi < p.W; wi += gridDim.x) {
         int gidx = 0;
@@ -349,13 +356,14 @@ __global__ void __launch_bounds__(kLongThreads, 1) long_reset_kernel(KParams p)
 }
 
 // One chunk of steps for every long walker; walkers are taken from a counter.
-template <int R>
-__global__ void __launch_bounds__(kLongThreads, 1) long_walk_kernel(KParams p, int chunk_index)
+template <int NT, int R>
+__global__ void __launch_bounds__(NT, kLongThreads / NT) long_walk_kernel(KParams p, int chunk_index)
 {
+    using LB = Blk<NT>;
     extern __shared__ __align__(16) int smem[];
-    const WarpSmem SL = long_smem(p.n_max);
+    const WarpSmem SL = long_smem(p.n_max, NT);
     const LB t(threadIdx.x, smem + SL.xoff);
-    uint32_t* bits = reinterpret_cast<uint32_t*>(smem + SL.xoff + kLongThreads);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(smem + SL.xoff + NT);
     const View V = make_view(smem, SL);
     const int64_t target = p.status->target_steps;
     for (;;) {
@@ -379,7 +387,7 @@ __global__ void __launch_bounds__(kLongThreads, 1) long_walk_kernel(KParams p, i
             if (t.lane == 0) raise_error(p.status, LABS_ESTATE, (int)wi);
             continue;
         }
-        long_walk<R>(lw, w, until, SL, smem, V, trace_slot, trace_start, t);
+        long_walk<LB, R>(lw, w, until, SL, smem, V, trace_slot, trace_start, t);
         if (t.lane < lw.nw) lw.cur[t.lane] = w.word;
         if (t.lane == 0) save_scalars(st, w);
         t.sync();
@@ -389,14 +397,15 @@ __global__ void __launch_bounds__(kLongThreads, 1) long_walk_kernel(KParams p, i
 // The neighbourhood of Algorithm 1 for long skew-symmetric rows, one row per CTA.
 // Rows that are not +-1 or break Eq. 4 get INT32_MIN (LABS_EINVAL); rows whose ISL is
 // above the exact-range bound get INT32_MIN too (LABS_ERANGE).
-template <int R>
-__global__ void __launch_bounds__(kLongThreads, 1) long_delta_kernel(const int8_t* __restrict__ seqs, int64_t batch,
-                                                                    int L, int32_t* __restrict__ out,
-                                                                    DevStatus* status)
+template <int NT, int R>
+__global__ void __launch_bounds__(NT, kLongThreads / NT) long_delta_kernel(const int8_t* __restrict__ seqs,
+                                                                          int64_t batch, int L,
+                                                                          int32_t* __restrict__ out, DevStatus* status)
 {
+    using LB = Blk<NT>;
     extern __shared__ __align__(16) int smem[];
     const int n = (L + 1) / 2, c = n - 1;
-    const WarpSmem SL = long_smem(n);
+    const WarpSmem SL = long_smem(n, NT);
     const LB t(threadIdx.x, smem + SL.xoff);
     const View V = make_view(smem, SL);
     const Outs<LB, R> o(t);
@@ -449,42 +458,64 @@ __global__ void __launch_bounds__(kLongThreads, 1) long_delta_kernel(const int8_
 using LongFn = void (*)(KParams, int);
 using LongDeltaFn = void (*)(const int8_t*, int64_t, int, int32_t*, DevStatus*);
 
-LongFn long_fn(int R)
+template <int NT>
+LongFn long_fn_nt(int R)
 {
     switch (R) {
-        case 1: return long_walk_kernel<1>;
-        case 3: return long_walk_kernel<3>;
-        case 5: return long_walk_kernel<5>;
-        case 7: return long_walk_kernel<7>;
-        default: return long_walk_kernel<9>;
+        case 1: return long_walk_kernel<NT, 1>;
+        case 3: return long_walk_kernel<NT, 3>;
+        case 5: return long_walk_kernel<NT, 5>;
+        case 7: return long_walk_kernel<NT, 7>;
+        default: return long_walk_kernel<NT, 9>;
     }
 }
 
-LongDeltaFn long_delta_fn(int R)
+template <int NT>
+LongDeltaFn long_delta_fn_nt(int R)
 {
     switch (R) {
-        case 1: return long_delta_kernel<1>;
-        case 3: return long_delta_kernel<3>;
-        case 5: return long_delta_kernel<5>;
-        case 7: return long_delta_kernel<7>;
-        default: return long_delta_kernel<9>;
+        case 1: return long_delta_kernel<NT, 1>;
+        case 3: return long_delta_kernel<NT, 3>;
+        case 5: return long_delta_kernel<NT, 5>;
+        case 7: return long_delta_kernel<NT, 7>;
+        default: return long_delta_kernel<NT, 9>;
     }
+}
+
+// kernels for n_max free variables: CTA width long_threads(n_max), lane block long_R
+LongFn long_fn(int n_max)
+{
+    const int NT = long_threads(n_max), R = long_R(n_max, NT);
+    return NT == kLongThreadsSmall ? long_fn_nt<kLongThreadsSmall>(R) : long_fn_nt<kLongThreads>(R);
+}
+
+LongDeltaFn long_delta_fn(int n)
+{
+    const int NT = long_threads(n), R = long_R(n, NT);
+    return NT == kLongThreadsSmall ? long_delta_fn_nt<kLongThreadsSmall>(R) : long_delta_fn_nt<kLongThreads>(R);
+}
+
+using ResetFn = void (*)(KParams);
+ResetFn long_reset_fn(int n_max)
+{
+    return long_threads(n_max) == kLongThreadsSmall ? long_reset_kernel<kLongThreadsSmall>
+                                                    : long_reset_kernel<kLongThreads>;
 }
 
 }  // namespace
 
-int long_kernel_config(int R, size_t smem_bytes, int* ctas_per_sm, int* regs)
+int long_kernel_config(int n_max, size_t smem_bytes, int* ctas_per_sm, int* regs)
 {
-    const LongFn fn = long_fn(R);
+    const LongFn fn = long_fn(n_max);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return LABS_ECUDA;
-    e = cudaFuncSetAttribute(long_reset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    e = cudaFuncSetAttribute(long_reset_fn(n_max), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return LABS_ECUDA;
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return LABS_ECUDA;
     if (regs) *regs = fa.numRegs;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, kLongThreads, smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, long_threads(n_max), smem_bytes);
     return e == cudaSuccess ? LABS_OK : LABS_ECUDA;
 }
 
@@ -494,13 +525,13 @@ int launch_long_reset(const KParams& p, size_t smem_bytes, void* stream)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t grid = p.W < sms ? (p.W > 0 ? p.W : 1) : sms;
-    long_reset_kernel<<<(int)grid, kLongThreads, smem_bytes, (cudaStream_t)stream>>>(p);
+    long_reset_fn(p.n_max)<<<(int)grid, long_threads(p.n_max), smem_bytes, (cudaStream_t)stream>>>(p);
     return cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ECUDA;
 }
 
 int launch_long_walk_chunk(const KParams& p, int chunk_index, int grid, size_t smem_bytes, void* stream)
 {
-    long_fn(p.rmax)<<<grid, kLongThreads, smem_bytes, (cudaStream_t)stream>>>(p, chunk_index);
+    long_fn(p.n_max)<<<grid, long_threads(p.n_max), smem_bytes, (cudaStream_t)stream>>>(p, chunk_index);
     return cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ECUDA;
 }
 
@@ -508,15 +539,15 @@ int launch_long_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out
 {
     if (batch == 0) return LABS_OK;
     const int n = (L + 1) / 2;
-    const size_t smem = (size_t)long_smem(n).words * sizeof(int);
-    const LongDeltaFn fn = long_delta_fn(long_R(n));
+    const size_t smem = (size_t)long_smem(n, long_threads(n)).words * sizeof(int);
+    const LongDeltaFn fn = long_delta_fn(n);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LABS_ECUDA;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = (int)(batch < sms ? batch : sms);
-    fn<<<grid, kLongThreads, smem, (cudaStream_t)stream>>>(seqs, batch, L, out, status);
+    const int grid = (int)(batch < 2 * sms ? batch : 2 * sms);
+    fn<<<grid, long_threads(n), smem, (cudaStream_t)stream>>>(seqs, batch, L, out, status);
     return cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ECUDA;
 }
 
