@@ -220,6 +220,10 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
         }
         w.apad = (lo + 3) & ~3;
         w.alen = w.apad + ((hi + 7) & ~7);
+        // one walker per warp: lanes 0-15 read row A0 and lanes 16-31 row A1 at the same
+        // offsets v0 + d, v0 = hR with R odd, i.e. banks {hR + d} and {hR + d + alen}:
+        // the two sets are disjoint (no conflicts) when alen = 16 (mod 32)
+        if (tile == 32) w.alen += (48 - (w.alen & 31)) & 31;
         w.gpad = (tile / 2) * R > span ? (tile / 2) * R : span;
         w.glen = w.gpad + gtop;
     }
