@@ -12,6 +12,8 @@ largest length: L=501 (the largest length of the scale-up configuration), 8192
 best-first search: the config-2 workload with LABS_FLAG_BEST_FIRST (bench.py
           --search bestfirst), 24 walkers spread over the batch.
 short lengths: L=151 (four walkers per warp), 16384 walkers x 1e4 steps, 24 walkers.
+PSL objective: the config-2 workload with LABS_FLAG_PSL, 3 walkers.
+long sequences: L=4095, 608 walkers x 512 steps (bench.py --config long), 3 walkers.
 """
 from __future__ import annotations
 
@@ -124,3 +126,36 @@ def test_four_walkers_per_warp_L151_bench_shape():
     assert st["steps"] == W * steps and st["walkers_per_warp"] == 4
     ids = sorted({0, 3, W - 1} | set(list(range(5, W, 701))[:21]))
     check_sample(s, L, seed, steps, ids)
+
+
+def test_psl_L201_bench_shape():
+    """The PSL-objective walk on the config-2 workload (bench.py --search psl): walkers
+    0, 8191 and 16383 against the oracle, which rebuilds every neighbour (about 20 s of
+    host time per walker for 1e4 steps)."""
+    L, W, steps, seed = 201, 16384, 10_000, 7
+    s = labs.Search(L, W, seed, objective="psl")
+    s.walk(steps)
+    s.sync()
+    ids = [0, 8191, W - 1]
+    with ThreadPoolExecutor(max_workers=len(ids)) as ex:
+        outs = list(ex.map(lambda g: oracle.walk(L, seed, 1, steps, first_walker=g, nthreads=1, objective="psl"),
+                           ids))
+    for gid, o in zip(ids, outs):
+        r = s.results(gid, 1, seqs=True)
+        for k, ok in (("isl", "final_isl"), ("psl", "final_psl"), ("best_isl", "best_isl"),
+                      ("best_psl", "best_psl")):
+            assert r[k][0] == o[ok][0], (gid, k)
+        assert np.array_equal(r["best_seq"][0], o["best_seq"][0]), gid
+    b = s.best()
+    assert oracle.psl(b["seq"]) == b["psl"] and oracle.isl(b["seq"]) == b["isl"]
+
+
+def test_long_L4095_bench_shape():
+    """Long sequences at the size bench.py --config long runs (608 walkers x 512 steps
+    of L=4095, 256-thread CTAs): walkers 0, 303 and 607 against the oracle."""
+    L, W, steps, seed = 4095, 608, 512, 42
+    s = labs.Search(L, W, seed)
+    s.walk(steps)
+    s.sync()
+    assert s.stats()["steps"] == W * steps
+    check_sample(s, L, seed, steps, [0, 303, W - 1])
