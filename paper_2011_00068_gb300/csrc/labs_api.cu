@@ -371,6 +371,7 @@ int sync_status(labs_ctx* c)
         const char* what = st.error == LABS_ETIMEOUT     ? "deadline passed"
                            : st.error == LABS_ECANCELLED ? "cancelled"
                            : st.error == LABS_ESTATE     ? "walker state failed its consistency check"
+                           : st.error == LABS_ERANGE     ? "sequence outside the exact range of the long walk"
                                                          : "device error";
         return fail(c, st.error, "%s (walker %d)", what, st.error_detail);
     }

@@ -159,3 +159,31 @@ def test_long_refusals():
     with pytest.raises(labs.LabsError):
         s.log(4)
     s.close()
+
+
+def test_long_walker_outside_exact_range_stops_with_erange():
+    """A walker put (through a checkpoint) on a state whose ISL is above the exact-range
+    bound stops before evaluating it and labs_sync reports LABS_ERANGE; the other walker
+    is unaffected.  Checkpoint layout: 64-byte header, then the walker states (160 bytes
+    each, ISL at byte 96), then the rows of current and best bits (128 words per walker,
+    each array 256-byte aligned)."""
+    import struct
+
+    L, W, seed = 4095, 2, 5
+    s = labs.Search(L, W, seed)
+    buf = s.checkpoint(with_tabu=False)
+    hdr, state_bytes = 64, 160
+    cur = hdr + ((W * state_bytes + 255) // 256) * 256
+    buf[cur:cur + 512] = bytes(512)                       # walker 0: every free variable +1
+    struct.pack_into("<i", buf, hdr + 96, 2 ** 31 - 1)    # its ISL as the kernel finds it (saturated)
+    assert oracle.isl(oracle.skew_expand(np.ones((L + 1) // 2, np.int8), L)) > 2 ** 31 - 1
+    s.restore(buf)
+    s.walk(4)
+    with pytest.raises(labs.LabsError) as err:
+        s.sync()
+    assert err.value.code == _native.LABS_ERANGE
+    s.clear_stop()  # errors are sticky until cleared
+    r = s.results(1, 1)
+    o = oracle.walk(L, seed, 1, 4, first_walker=1)
+    assert r["isl"][0] == o["final_isl"][0]
+    s.close()
