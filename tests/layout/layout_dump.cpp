@@ -1,0 +1,27 @@
+// Prints the shared-memory layouts the kernels use (labs_internal.cuh, compiled for the
+// host): one line per (kind, tile, n_max): apad alen gpad glen bvec xoff words R.
+#define __host__
+#define __device__
+#include <cstdio>
+
+#include "labs_internal.cuh"
+
+using namespace labsgpu;
+
+int main()
+{
+    const int tiles[3] = {8, 16, 32};
+    for (int ti = 0; ti < 3; ++ti)
+        for (int n = 2; n <= kMaxN; ++n) {
+            const WarpSmem w = warp_smem(n, tiles[ti]);
+            std::printf("warp %d %d %d %d %d %d %d %d %d %d\n", tiles[ti], n, w.apad, w.alen, w.gpad, w.glen, w.bvec,
+                        w.xoff, w.words, block_R(n, tiles[ti]));
+        }
+    for (int n = kMaxN + 1; n <= kMaxNLong; ++n) {
+        const int nt = long_threads(n);
+        const WarpSmem w = long_smem(n, nt);
+        std::printf("long %d %d %d %d %d %d %d %d %d %d %d\n", nt, n, w.apad, w.alen, w.gpad, w.glen, w.bvec, w.xoff,
+                    w.words, long_R(n, nt), long_isl_limit(2 * n - 1, n));
+    }
+    return 0;
+}

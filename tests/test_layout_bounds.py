@@ -1,0 +1,206 @@
+"""Shared-memory bounds of every walker layout, checked on the CPU.
+
+tests/layout/layout_dump.cpp compiles the layout functions of labs_internal.cuh for the
+host and prints each layout (row padding and length, table padding and length, bit
+vectors, lane block).  For every length the kernels serve and every lane block the
+launch code can pick, the extreme index of every family of shared-memory accesses (the
+rows, the table, the bit vectors, in the walk, the best-first search, the PSL walk, the
+row kernels and the long-sequence kernels) must fall inside its region.  The index
+families are restated here from the kernels; the lane and output indices enter them
+monotonically, so the first and last lane of each parity class bound them.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def layouts(tmp_path_factory):
+    exe = str(tmp_path_factory.mktemp("layout") / "layout_dump")
+    src = os.path.join(ROOT, "tests", "layout", "layout_dump.cpp")
+    subprocess.run(["g++", "-std=c++17", "-O1", "-I", os.path.join(ROOT, "include"), "-I",
+                    os.path.join(ROOT, "paper_2011_00068_gb300", "csrc"), src, "-o", exe], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    warp, long_ = {}, {}
+    for line in out.splitlines():
+        f = line.split()
+        v = list(map(int, f[1:]))
+        if f[0] == "warp":
+            tile, n = v[0], v[1]
+            warp[(tile, n)] = dict(apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], R=v[9])
+        else:
+            nt, n = v[0], v[1]
+            long_[n] = dict(nt=nt, apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], xoff=v[7],
+                            words=v[8], R=v[9], limit=v[10])
+    return warp, long_
+
+
+def conflict_free_R(R, tile):
+    while 16 // min(R & -R, 16) < tile // 2:
+        R += 1
+    return R
+
+
+class Region:
+    def __init__(self, S):
+        self.S, self.bad = S, []
+
+    def a(self, idx, what):
+        if not (-self.S["apad"] <= idx < self.S["alen"] - self.S["apad"]):
+            self.bad.append(("A", what, idx))
+
+    def g(self, y, what):
+        if not (-self.S["gpad"] <= y < self.S["glen"] - self.S["gpad"]):
+            self.bad.append(("G", what, y))
+
+    def b(self, word, what):
+        if not (0 <= word < self.S["bvec"]):
+            self.bad.append(("B", what, word))
+
+
+def common(reg, n, tile, R, valid_only):
+    """Rows, Toeplitz window, assembly, table and bit vectors (all layouts)."""
+    c = n - 1
+    half = tile // 2
+    v0max = (half - 1) * R
+    nu = (n + 7) & ~7
+    reg.a(n - 1, "row")                     # s_j -> A_{j&1}[j>>1], j < L
+    reg.a(0, "toe A0")
+    reg.a(nu - 1, "toe A")                  # float4 rows A[u .. u+7], u < round8(n)
+    reg.g(-v0max - (R - 1), "toe win0")     # initial window G[-v0 - r]
+    reg.g(nu, "toe top")                    # G[u + 2q + 2 - v0] at v0 = 0
+    reg.g(1 - v0max, "toe low")
+    for p in (0, 1):
+        nv = (n >> 1) if p else ((n + 1) >> 1)
+        vmax = (nv - 1) if valid_only else (v0max + R - 1)
+        for v in (0, vmax):
+            i = 2 * v + p
+            reg.a(v, "asm v")
+            reg.a(n - 1 - v - p, "asm q")
+            reg.a(3 * v + p - n + 1, "asm t")
+            reg.g(c - i, "asm G")
+    for m in (1, n - 1):                    # set_E
+        reg.g(m, "E")
+        reg.g(m - 1, "E.y")
+        if m <= reg.S["gpad"]:
+            reg.g(-m, "mirror E")
+        if m < reg.S["gpad"]:
+            reg.g(-m - 1, "mirror E.y")
+    for p in (0, 1):                        # shifted mismatch counts (table) and P
+        np_ = n - 1 if p else n
+        for m in (1, 2, 31, 32, 33, n - 2, n - 1):
+            if 1 <= m < n and np_ - m > 0:
+                reg.b((np_ - m - 1) // 32 + (m >> 5) + 1, "table")
+        nv = (n >> 1) if p else ((n + 1) >> 1)
+        for v in range(max(1, nv - 40), nv):
+            k = (v - 1) // 32
+            reg.b(k + ((v + 1) >> 5) + 1, "P x")
+            reg.b(k + ((np_ - v) >> 5) + 1, "P xr")
+    reg.b(((n + 31) // 32), "bits zero word")
+
+
+def test_warp_layouts(layouts):
+    warp, _ = layouts
+    bad = []
+    for tile in (8, 16, 32):
+        for n_max in range(2, 257):
+            S = warp[(tile, n_max)]
+            RMAX = S["R"]
+            for n in range(2, n_max + 1):
+                need = warp[(tile, n)]["R"]
+                if tile in (8, 16):   # walk_group's choice
+                    R = need if need >= RMAX - 3 else conflict_free_R(RMAX - 3, tile)
+                    R = min(R, RMAX)
+                else:                 # walk_chunk_kernel's choice
+                    R = RMAX if (RMAX <= 2 or need >= RMAX) else RMAX - 2
+                assert R >= need
+                reg = Region(S)
+                c = n - 1
+                common(reg, n, tile, R, valid_only=(tile == 8))
+                half = tile // 2
+                v0max = (half - 1) * R
+                # lockstep lag update: lane l covers m = 1 + lR .. (l+1)R, no bounds test
+                # (tile 8: reads above stay inside the class)
+                for i in (0, 1, c - 1, c):
+                    if i < 0:
+                        continue
+                    vb, pb = i >> 1, i & 1
+                    vq = vb if i == c else n - 1 - vb - pb
+                    reg.a(vq, "vq")
+                    npc = n - 1 if pb else n
+                    top = vb + tile * R
+                    reg.a(min(top, npc - 1) if tile == 8 else top, "up")
+                    reg.a(vb - tile * R, "dn")
+                    reg.a(2 * v0max + 2 * (R - 1) - vb, "p1")
+                    reg.a(-vq, "p2")
+                    if tile == 32:      # strided lags (learned mode, PSL and best-first moves)
+                        reg.a(vb + n - 1, "up32")
+                        reg.a(vb - (n - 1), "dn32")
+                reg.g(tile * R, "E load")
+                if tile != 8 or 1 + (tile - 1) * R + R <= S["gpad"]:
+                    reg.g(-(1 + (tile - 1) * R) - R, "mirror E load")
+                if tile == 8:           # the mirror half of the table as deep as the window reads
+                    covered = set()
+                    for l in range(8):
+                        m0 = 1 + l * R
+                        if m0 + R <= S["gpad"]:
+                            covered.update(range(m0, m0 + R))
+                    if not set(range(1, min(n, 4 * R))) <= covered:
+                        reg.bad.append(("mirror coverage", n, R))
+                if tile == 32:          # the PSL neighbourhood
+                    if R <= 5:
+                        P = 3 * R - 2
+                        tend = n - 1 + 2 * (R - 1)
+                        reg.a(v0max + P - 1, "psl ring init hi")
+                        reg.a(1 - P, "psl ring init lo")
+                        reg.g(1 - P, "psl ring init G")
+                        reg.a(-tend, "psl a")
+                        reg.a(v0max + tend, "psl b")
+                        reg.g(tend, "psl C")
+                    else:
+                        reg.a(-(n - 1), "psl sel a")
+                        reg.a(v0max + n + R - 2, "psl sel b")
+                        reg.a(v0max + R - 1, "psl sel init")
+                if reg.bad:
+                    bad.append((tile, n_max, n, R, reg.bad[:3]))
+    assert not bad, bad[:5]
+
+
+def test_long_layouts(layouts):
+    _, long_ = layouts
+    bad = []
+    for n_max in range(257, 4097):
+        S = long_[n_max]
+        nt, R = S["nt"], S["R"]
+        assert nt * R >= n_max and S["words"] >= S["xoff"] + nt + 128
+        assert S["words"] * 4 <= (227 * 1024 if nt == 512 else 113 * 1024)  # one / two CTAs per SM
+        for n in sorted({257, (257 + n_max) // 2, n_max}):
+            reg = Region(S)
+            common(reg, n, nt, R, valid_only=True)
+            c = n - 1
+            for vb in (0, c >> 1):
+                reg.a(vb + n - 1, "flip up")
+                reg.a(vb - (n - 1), "flip dn")
+            reg.a(-(n - 1), "p")
+            reg.a(2 * ((n + 1) >> 1), "p hi")
+            if reg.bad:
+                bad.append((n_max, n, R, reg.bad[:3]))
+    assert not bad, bad[:5]
+
+
+def test_long_exact_range_bound(layouts):
+    """The bound on ISL keeps 16 sqrt((n-1) ISL) + 8L + 32n + 32 below 2^24 (Cauchy-Schwarz
+    on sum |C_2m|), the condition for the long kernels' fp32 arithmetic to be exact, and
+    stays far above the ISL of random starts (about L^2/2)."""
+    _, long_ = layouts
+    for n in (257, 1024, 2048, 4096):
+        L = 2 * n - 1
+        lim = long_[n]["limit"]
+        assert 16 * ((n - 1) * lim) ** 0.5 + 8 * L + 32 * n + 32 < 2 ** 24
+        assert lim > 4 * L * L // 2
+        assert lim < 2 ** 30
