@@ -297,7 +297,10 @@ __device__ __forceinline__ void bits_from_rows(const View& V, int n, const TL& t
                 }
             }
         } else {
-            for (int k = 0; k < V.bvec; ++k) {
+            // words beyond the class (and its zero word) stay zero: every caller cleared
+            // them and no walker of another length shares this walker's memory since
+            const int nwd = min(V.bvec, (np + 31) / 32 + 1);
+            for (int k = 0; k < nwd; ++k) {
                 uint32_t w = 0, r = 0;
 #pragma unroll
                 for (int h = 0; h < 32 / TL::kSize; ++h) {

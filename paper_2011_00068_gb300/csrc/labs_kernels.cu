@@ -211,8 +211,7 @@ __global__ void __launch_bounds__(256) delta_pair_kernel(const int8_t* __restric
             for (int j = lane; j < L; j += 16) {
                 const int v = src[j];
                 ok = ok && (v == 1 || v == -1);
-                if (j & 1) V.A1[j >> 1] = (float)v;
-                else V.A0[j >> 1] = (float)v;
+                ((j & 1) ? V.A1 : V.A0)[j >> 1] = (float)v;
             }
         }
         t.sync();
