@@ -342,15 +342,20 @@ __device__ __forceinline__ int build_table(const View& V, int n, const TL& t)
 {
     bits_from_rows(V, n, t);
     int part = 0;
+    const uint32_t* x0 = V.B;
+    const uint32_t* x1 = V.B + V.bvec;
     for (int m = 1 + t.lane; m < n; m += TL::kSize) {
-        int d = 0;
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            const int len = (p ? n - 1 : n) - m;
-            if (len <= 0) continue;
-            const uint32_t* x = V.B + p * V.bvec;
-            d += len - 2 * shifted_mismatch(x, x, m, len);
+        // both classes in one pass over the words (lengths n - m and n - 1 - m, same shift)
+        const int q = m >> 5, r = m & 31, len0 = n - m, len1 = n - 1 - m;
+        int c0 = 0, c1 = 0;
+        for (int k = 0; 32 * k < len0; ++k) {
+            const int v0 = len0 - 32 * k, v1 = len1 - 32 * k;
+            const uint32_t m0 = v0 >= 32 ? ~0u : (1u << v0) - 1u;
+            const uint32_t m1 = v1 >= 32 ? ~0u : (v1 > 0 ? (1u << v1) - 1u : 0u);
+            c0 += __popc((x0[k] ^ __funnelshift_r(x0[k + q], x0[k + q + 1], r)) & m0);
+            c1 += __popc((x1[k] ^ __funnelshift_r(x1[k + q], x1[k + q + 1], r)) & m1);
         }
+        const int d = len0 - 2 * c0 + (len1 > 0 ? len1 - 2 * c1 : 0);
         set_E(V, m, (float)d);
         part += d * d;
     }
@@ -421,23 +426,28 @@ __device__ __forceinline__ void p_direct(const View& V, int n, const Outs<TL, R>
     const int nv = o.p ? (n >> 1) : ((n + 1) >> 1);
     const uint32_t* x = V.B + o.p * V.bvec;
     const uint32_t* xr = V.B + (2 + o.p) * V.bvec;
+    // the R outputs word by word (independent chains); output v compares v bits
+    int cnt[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) cnt[r] = 0;
+    const int vtop = min(o.v0 + R - 1, nv - 1);
+    for (int k = 0; 32 * k < vtop; ++k) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int v = o.v0 + r;
+            const int valid = v - 32 * k;
+            if (v < nv && valid > 0) {
+                const uint32_t a = __funnelshift_r(x[k + ((v + 1) >> 5)], x[k + ((v + 1) >> 5) + 1], (v + 1) & 31);
+                const uint32_t b = __funnelshift_r(xr[k + ((np - v) >> 5)], xr[k + ((np - v) >> 5) + 1], (np - v) & 31);
+                const uint32_t mk = valid >= 32 ? ~0u : (1u << valid) - 1u;
+                cnt[r] += __popc((a ^ b) & mk);
+            }
+        }
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int v = o.v0 + r;
-        P[r] = 0.f;
-        if (v >= nv || v == 0) continue;
-        const int q1 = (v + 1) >> 5, r1 = (v + 1) & 31;
-        const int q2 = (np - v) >> 5, r2 = (np - v) & 31;
-        int cnt = 0;
-        for (int k = 0; 32 * k < v; ++k) {
-            const uint32_t a = __funnelshift_r(x[k + q1], x[k + q1 + 1], r1);
-            const uint32_t b = __funnelshift_r(xr[k + q2], xr[k + q2 + 1], r2);
-            uint32_t d = a ^ b;
-            const int valid = v - 32 * k;
-            if (valid < 32) d &= (1u << valid) - 1u;
-            cnt += __popc(d);
-        }
-        P[r] = (float)(v - 2 * cnt);
+        P[r] = (v >= nv || v == 0) ? 0.f : (float)(v - 2 * cnt[r]);
     }
 }
 

@@ -94,8 +94,8 @@ def common(reg, n, tile, R, valid_only):
     for p in (0, 1):                        # shifted mismatch counts (table) and P
         np_ = n - 1 if p else n
         for m in (1, 2, 31, 32, 33, n - 2, n - 1):
-            if 1 <= m < n and np_ - m > 0:
-                reg.b((np_ - m - 1) // 32 + (m >> 5) + 1, "table")
+            if 1 <= m < n:                  # both classes run over the even class's words
+                reg.b((n - m - 1) // 32 + (m >> 5) + 1, "table")
         nv = (n >> 1) if p else ((n + 1) >> 1)
         for v in range(max(1, nv - 40), nv):
             k = (v - 1) // 32
