@@ -320,21 +320,6 @@ __device__ __forceinline__ void bits_from_rows(const View& V, int n, const TL& t
     t.sync();
 }
 
-// Number of differing bits between x and y >> sh over bits [0, len).
-__device__ __forceinline__ int shifted_mismatch(const uint32_t* x, const uint32_t* y, int sh, int len)
-{
-    const int q = sh >> 5, r = sh & 31;
-    int cnt = 0;
-    for (int k = 0; 32 * k < len; ++k) {
-        const uint32_t s = __funnelshift_r(y[k + q], y[k + q + 1], r);
-        uint32_t v = x[k] ^ s;
-        const int valid = len - 32 * k;
-        if (valid < 32) v &= (1u << valid) - 1u;
-        cnt += __popc(v);
-    }
-    return cnt;
-}
-
 // Even-lag autocorrelations (Eq. 1) into E and the ISL (Eq. 2) from the bit-packed
 // classes: for each class, sum_u a_u a_{u+m} = (n_p - m) - 2 #{u : a_u != a_{u+m}}.
 template <class TL>
