@@ -329,20 +329,36 @@ __device__ __forceinline__ int build_table(const View& V, int n, const TL& t)
     int part = 0;
     const uint32_t* x0 = V.B;
     const uint32_t* x1 = V.B + V.bvec;
-    for (int m = 1 + t.lane; m < n; m += TL::kSize) {
-        // both classes in one pass over the words (lengths n - m and n - 1 - m, same shift)
-        const int q = m >> 5, r = m & 31, len0 = n - m, len1 = n - 1 - m;
-        int c0 = 0, c1 = 0;
-        for (int k = 0; 32 * k < len0; ++k) {
-            const int v0 = len0 - 32 * k, v1 = len1 - 32 * k;
-            const uint32_t m0 = v0 >= 32 ? ~0u : (1u << v0) - 1u;
-            const uint32_t m1 = v1 >= 32 ? ~0u : (v1 > 0 ? (1u << v1) - 1u : 0u);
-            c0 += __popc((x0[k] ^ __funnelshift_r(x0[k + q], x0[k + q + 1], r)) & m0);
-            c1 += __popc((x1[k] ^ __funnelshift_r(x1[k + q], x1[k + q + 1], r)) & m1);
+    // lags m = mb + g kSize, g < 4, together (eight independent counts), both classes in
+    // one pass over the words (lengths n - m and n - 1 - m, same shift)
+    constexpr int kG = 4;
+    for (int mb = 1 + t.lane; mb < n; mb += kG * TL::kSize) {
+        int c0[kG], c1[kG];
+#pragma unroll
+        for (int g = 0; g < kG; ++g) c0[g] = c1[g] = 0;
+        for (int k = 0; 32 * k < n - mb; ++k) {
+#pragma unroll
+            for (int g = 0; g < kG; ++g) {
+                const int m = mb + g * TL::kSize, len0 = n - m, v0 = len0 - 32 * k, v1 = v0 - 1;
+                if (v0 > 0) {
+                    const int q = m >> 5, r = m & 31;
+                    const uint32_t m0 = v0 >= 32 ? ~0u : (1u << v0) - 1u;
+                    const uint32_t m1 = v1 >= 32 ? ~0u : (v1 > 0 ? (1u << v1) - 1u : 0u);
+                    c0[g] += __popc((x0[k] ^ __funnelshift_r(x0[k + q], x0[k + q + 1], r)) & m0);
+                    c1[g] += __popc((x1[k] ^ __funnelshift_r(x1[k + q], x1[k + q + 1], r)) & m1);
+                }
+            }
         }
-        const int d = len0 - 2 * c0 + (len1 > 0 ? len1 - 2 * c1 : 0);
-        set_E(V, m, (float)d);
-        part += d * d;
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            const int m = mb + g * TL::kSize;
+            if (m < n) {
+                const int len0 = n - m, len1 = len0 - 1;
+                const int d = len0 - 2 * c0[g] + (len1 > 0 ? len1 - 2 * c1[g] : 0);
+                set_E(V, m, (float)d);
+                part += d * d;
+            }
+        }
     }
     t.sync();
     return t.radd(part);
