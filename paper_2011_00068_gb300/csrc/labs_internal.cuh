@@ -151,7 +151,8 @@ struct KParams {
 //   G : pairs G[y] = (E[y], E[y+1]) for y in [-gpad, glen - gpad), where
 //       E[d] = C_{2|d|} for 0 < |d| < n and E[d] = 0 otherwise (E[0] = 0)
 //   B : bit-packed classes (bit u set <=> A_p[u] = -1) and their reversals,
-//       4 vectors x kBitVec words, zero beyond the class length
+//       4 vectors x bvec words (kBitVec in the warp layouts), zero beyond the class
+//       length
 constexpr int kBitVec = 9;  // 256 bits per class plus one zero word read by the shifts
 struct WarpSmem {
     int apad;   // zero words below index 0 of each row (multiple of 4)
