@@ -515,9 +515,10 @@ def run_long(args):
     sm_mhz = float(measured_peaks().get("sm_max_mhz", 2070.0))
     peak = FP32_LANES_PER_SM * 2 * sms * sm_mhz * 1e6
     out = {}
+    objective = "psl" if args.search == "psl" else "isl"
     for L in (2047, 4095, 8191):
         n = (L + 1) // 2
-        s = labs.Search(L, args.long_walkers, 42, device=dev)
+        s = labs.Search(L, args.long_walkers, 42, device=dev, objective=objective)
         s.walk(8)  # warm-up: graph capture, first touch of the tables
         s.sync()
         s.reset()
@@ -534,12 +535,16 @@ def run_long(args):
         out[str(L)] = {"flips_per_s": flips, "ms": ms, "steps": args.long_steps, "walkers": args.long_walkers,
                        "walker_steps_per_s": st["steps"] / (ms / 1e3), "best_isl": best["isl"],
                        "best_F": best["F"], "lane_block": st["lane_block"],
-                       "roofline_frac": ALGO_FLOP_PER_LAG_TERM * (n - 1) * flips / peak}
+                       "roofline_frac": (PSL_LANE_OPS_PER_LAG_TERM * (n - 1) * flips / (peak / 2) if objective == "psl"
+                                         else ALGO_FLOP_PER_LAG_TERM * (n - 1) * flips / peak)}
+        if objective == "psl":
+            out[str(L)]["best_psl"] = best["psl"]
         s.close()
         del s
         torch.cuda.empty_cache()
     total = sum(v["flips_per_s"] * v["ms"] for v in out.values()) / sum(v["ms"] for v in out.values())
-    line = {"metric": "exact flip evaluations/sec, long sequences", "value": total, "unit": "flip evaluations/s",
+    line = {"metric": "exact flip evaluations/sec, long sequences" + (", PSL objective" if objective == "psl" else ""),
+            "value": total, "unit": "flip evaluations/s",
             "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic", "vs_baseline": None,
             "config": {"workload": "L=2047, 4095 and 8191, %d walkers each (one per CTA of 256 or 512 threads), %d steps, "
                                    "seed 42, uniform random +-1 Philox starts, HT 2^16 slots/walker"

@@ -209,7 +209,7 @@ int labs_neighbor_delta(labs_ctx *ctx, const int8_t *dev_seqs, int64_t batch,
  *   walk.  The trace's ISL log still holds ISL.
  * Long sequences (L > LABS_MAX_L) take the same steps with the neighbourhood in exact
  *   fp32 arithmetic, which holds while ISL < ((2^24 - 8L - 32n - 32) / 16)^2 / (n - 1)
- *   (capped at 2^30; 2.6e8 at L = 8191, far above random starts, whose ISL is near
+ *   (capped at 2^29; 2.6e8 at L = 8191, far above random starts, whose ISL is near
  *   L^2/2): a walker whose ISL exceeds it stops and labs_sync reports LABS_ERANGE.
  * The trajectory of a walker depends only on (seed, walker id, L, cfg), never on
  * chunking, launch shape or the other walkers. */

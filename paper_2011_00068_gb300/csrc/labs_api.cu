@@ -220,8 +220,8 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
         return fail(c, LABS_EINVAL, "LABS_FLAG_PSL combines with neither LABS_FLAG_BEST_FIRST nor LABS_FLAG_LEARNED");
     if (nL >= 1 && Ls && valid_long_L(Ls[0])) {
         c->long_mode = true;
-        if (k.flags & (LABS_FLAG_BEST_FIRST | LABS_FLAG_LEARNED | LABS_FLAG_PSL))
-            return fail(c, LABS_EINVAL, "lengths above %d run the plain walk only", LABS_MAX_L);
+        if (k.flags & (LABS_FLAG_BEST_FIRST | LABS_FLAG_LEARNED))
+            return fail(c, LABS_EINVAL, "lengths above %d run the walk only (plain or PSL objective)", LABS_MAX_L);
     }
     c->seed = seed;
     c->stream = (cudaStream_t)stream;
@@ -303,7 +303,8 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
         c->tile = long_threads(c->n_max);
         c->smem_bytes = (size_t)long_smem(c->n_max, c->tile).words * sizeof(int);
         int occ = 0;
-        if (long_kernel_config(c->n_max, c->smem_bytes, &occ, &c->regs) != LABS_OK || occ < 1)
+        if (long_kernel_config(c->n_max, (k.flags & LABS_FLAG_PSL) != 0, c->smem_bytes, &occ, &c->regs) != LABS_OK ||
+            occ < 1)
             return fail(c, LABS_ECUDA, "long walk kernel does not fit on an SM (%zu bytes of shared memory)",
                         c->smem_bytes);
         c->ctas_per_sm = occ;

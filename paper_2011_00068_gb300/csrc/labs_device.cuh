@@ -1645,12 +1645,22 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
 // learned mode, 2 the best-first search (one variant per kernel keeps the code small).
 // ------------------------------------------------------------ PSL objective walk
 
+// Order key of a flip under the PSL objective: PSL' << 42 | ISL' << 12 | i (PSL' < 2^13,
+// ISL' < 2^30, i < 2^12 for every length served).
+__device__ __forceinline__ uint64_t psl_key(int psl, int isl, int i)
+{
+    return ((uint64_t)psl << 42) | ((uint64_t)(uint32_t)isl << 12) | (uint64_t)i;
+}
+__device__ __forceinline__ int psl_key_i(uint64_t k) { return (int)(k & 0xFFFu); }
+__device__ __forceinline__ int psl_key_isl(uint64_t k) { return (int)((k >> 12) & 0x3FFFFFFFull); }
+__device__ __forceinline__ int psl_key_psl(uint64_t k) { return (int)(k >> 42); }
+
 // The same PSL values for wide lane blocks (R >= 7), where the three rings of psl_eval
 // would not fit the registers: s_{i-2m} and s_{i+2m} of the R outputs in two windows of
 // R values that slide one class entry per lag (three shared loads per lag), and the
 // mirror's term dropped by a compare and select per lag term.
-template <int R>
-__device__ __forceinline__ void psl_eval_select(const View& V, int n, const Outs<Tile<32>, R>& o, int (&pl)[R])
+template <class TL, int R>
+__device__ __forceinline__ void psl_eval_select(const View& V, int n, const Outs<TL, R>& o, int (&pl)[R])
 {
     const float* A = (o.p ? V.A1 : V.A0) + o.v0;
     const int c = n - 1;
@@ -1703,11 +1713,11 @@ __device__ __forceinline__ void psl_eval_select(const View& V, int n, const Outs
 // loop unrolled by P so that the ring indices are constants).  Lags outside 1..n-1 (the
 // first 2R - 2 and the last iterations) are masked in the blocks that hold them.  Exact
 // in fp32: every value is an integer of magnitude below 2^10.
-template <int R>
-__device__ __forceinline__ void psl_eval(const View& V, int n, const Outs<Tile<32>, R>& o, int (&pl)[R])
+template <class TL, int R>
+__device__ __forceinline__ void psl_eval(const View& V, int n, const Outs<TL, R>& o, int (&pl)[R])
 {
     if constexpr (R >= 7) {
-        psl_eval_select<R>(V, n, o, pl);
+        psl_eval_select<TL, R>(V, n, o, pl);
         return;
     }
     constexpr int P = 3 * R - 2;
@@ -1800,13 +1810,10 @@ __device__ void walk_psl(const WalkEnv& env, Walker& w, PslTrack& ps, int64_t un
             assemble(V, n, o, X, P, dl);
         }
         psl_eval(V, n, o, pl);
-        // key = PSL' << 40 | ISL' << 8 | i (PSL' < 2^9, ISL' < 2^26 for L <= 511)
         uint64_t key[R];
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            key[r] = dl[r] == INT_MAX ? ~0ull
-                                      : ((uint64_t)pl[r] << 40) | ((uint64_t)(uint32_t)(w.isl + dl[r]) << 8) |
-                                            (uint64_t)(2 * (o.v0 + r) + o.p);
+            key[r] = dl[r] == INT_MAX ? ~0ull : psl_key(pl[r], w.isl + dl[r], 2 * (o.v0 + r) + o.p);
         uint32_t excl = 0;
         int best_i = -1;
         uint64_t best_key = 0, fnew = 0;
@@ -1818,7 +1825,7 @@ __device__ void walk_psl(const WalkEnv& env, Walker& w, PslTrack& ps, int64_t un
                 if (!((excl >> r) & 1u) && key[r] < lm) lm = key[r];
             const uint64_t km = warp_min64(lm);
             if (km == ~0ull) break;
-            const int bi = (int)(km & 0xFFu);
+            const int bi = psl_key_i(km);
             const uint64_t f = w.fp ^ __ldg(env.zk + bi);
             const Probe pr = probe_full(env, f, w.gen, cap, t);
             if (!pr.visited) {
@@ -1845,8 +1852,8 @@ __device__ void walk_psl(const WalkEnv& env, Walker& w, PslTrack& ps, int64_t un
             if (lane == (best_i >> 5)) w.word ^= 1u << (best_i & 31);
             t.sync();
             w.fp = fnew;
-            w.isl = (int)((best_key >> 8) & 0xFFFFFFFFull);
-            ps.psl = (int)(best_key >> 40);
+            w.isl = psl_key_isl(best_key);
+            ps.psl = psl_key_psl(best_key);
             if (!stored) w.overflows += 1;
             note_best(env, w, t, &ps);
             if (psl_better(ps.psl, w.isl, ps.since_psl, w.since)) {

@@ -262,11 +262,16 @@ __host__ __device__ inline WarpSmem long_smem(int n_max, int tile)
     const int span = tile * R + 2;
     int hi = (3 * n_max) / 2 + 2 > n_max + 8 ? (3 * n_max) / 2 + 2 : n_max + 8;
     if ((n_max + 1) / 2 + span > hi) hi = (n_max + 1) / 2 + span;
-    const int lo = n_max > span ? n_max : span;
+    int lo = n_max > span ? n_max : span;
+    int gtop = top > span ? top : span;
+    // the PSL neighbourhood runs its lags 2R - 2 past n - 1 (as in the warp layout)
+    if (n_max + (tile / 2 + 2) * R > hi) hi = n_max + (tile / 2 + 2) * R;
+    if (n_max + 2 * R > lo) lo = n_max + 2 * R;
+    if (n_max + 2 * R > gtop) gtop = n_max + 2 * R;
     w.apad = (lo + 3) & ~3;
     w.alen = w.apad + ((hi + 7) & ~7);
     w.gpad = (tile / 2) * R > span ? (tile / 2) * R : span;
-    w.glen = w.gpad + (top > span ? top : span);
+    w.glen = w.gpad + gtop;
     w.goff = 2 * w.alen;
     w.boff = w.goff + 2 * w.glen;
     w.bvec = (n_max + 31) / 32 + 2;
@@ -278,12 +283,13 @@ __host__ __device__ inline WarpSmem long_smem(int n_max, int tile)
 // Largest ISL for which the long walk's fp32 neighbourhood stays exact.  Every value in
 // the dISL assembly is bounded by 16 sum_m |C_{2m}| + 8L + 32n + 32, and by
 // Cauchy-Schwarz sum_m |C_{2m}| <= sqrt((n-1) ISL); the limit keeps the bound below
-// 2^24 (and ISL far below 2^31).
+// 2^24, and caps ISL at 2^29 so that a neighbour's ISL (at most 2^24 more) fits the 30
+// bits the PSL objective's order key gives it.
 __host__ __device__ inline int long_isl_limit(int L, int n)
 {
     const double room = ((double)(1 << 24) - 8.0 * L - 32.0 * n - 32.0) / 16.0;
     double lim = room * room / (double)(n > 1 ? n - 1 : 1);
-    if (lim > (double)(1 << 30)) lim = (double)(1 << 30);
+    if (lim > (double)(1 << 29)) lim = (double)(1 << 29);
     return (int)lim - 1;
 }
 
@@ -301,7 +307,7 @@ WalkFn walk_fn32b(int rmax);  // best-first search (labs_walk32b.cu)
 WalkFn walk_fn32p(int rmax);  // walk under the PSL objective (labs_walk32p.cu)
 
 // Long-L walk (labs_long.cu).
-int long_kernel_config(int n_max, size_t smem_bytes, int* ctas_per_sm, int* regs);
+int long_kernel_config(int n_max, bool psl, size_t smem_bytes, int* ctas_per_sm, int* regs);
 int launch_long_reset(const KParams& p, size_t smem_bytes, void* stream);
 int launch_long_walk_chunk(const KParams& p, int chunk_index, int grid, size_t smem_bytes, void* stream);
 int launch_long_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status, void* stream);

@@ -65,6 +65,19 @@ struct Blk {
         __syncthreads();
         return r;
     }
+    // 64-bit minimum (order keys of the PSL objective)
+    __device__ __forceinline__ uint64_t rmin64(uint64_t v) const
+    {
+        v = warp_min64(v);
+        unsigned long long* y = reinterpret_cast<unsigned long long*>(x);
+        if ((lane & 31) == 0) y[lane >> 5] = v;
+        __syncthreads();
+        uint64_t r = y[0];
+#pragma unroll
+        for (int k = 1; k < kWarps; ++k) r = min(r, (uint64_t)y[k]);
+        __syncthreads();
+        return r;
+    }
     // sum in 64 bits, saturated to INT_MAX (a saturated ISL fails the range check)
     __device__ __forceinline__ int radd(int v) const
     {
@@ -135,10 +148,12 @@ __device__ uint64_t long_fingerprint(const LongWalk& lw, const LB& t)
 }
 
 template <class LB>
-__device__ __forceinline__ void long_note_best(const LongWalk& lw, Walker& w, const LB& t)
+__device__ __forceinline__ void long_note_best(const LongWalk& lw, Walker& w, const LB& t, PslTrack* ps = nullptr)
 {
-    if (w.isl < w.best_isl) {
+    const bool better = ps ? psl_better(ps->psl, w.isl, ps->best_psl, w.best_isl) : w.isl < w.best_isl;
+    if (better) {
         w.best_isl = w.isl;
+        if (ps) ps->best_psl = ps->psl;
         w.best_step = w.steps;
         if (t.lane < lw.nw) lw.best[t.lane] = w.word;
     }
@@ -149,7 +164,7 @@ __device__ __forceinline__ void long_note_best(const LongWalk& lw, Walker& w, co
 // insertion, best update.
 template <class LB>
 __device__ void long_start(const LongWalk& lw, Walker& w, const WarpSmem& SL, int* base, const View& V,
-                           const LB& t)
+                           const LB& t, PslTrack* ps = nullptr)
 {
     const WalkEnv& env = lw.e;
     w.word = t.lane < lw.nw ? start_word(env.p->seed, env.g, w.restart_idx, t.lane, env.n) : 0u;
@@ -159,12 +174,16 @@ __device__ void long_start(const LongWalk& lw, Walker& w, const WarpSmem& SL, in
     t.sync();
     w.since = w.isl;
     w.stag = 0;
-    long_note_best(lw, w, t);
+    if (ps) {
+        ps->psl = table_psl(V, env.n, t);
+        ps->since_psl = ps->psl;
+    }
+    long_note_best(lw, w, t, ps);
 }
 
 template <class LB>
 __device__ void long_restart(const LongWalk& lw, Walker& w, const WarpSmem& SL, int* base, const View& V,
-                             const LB& t)
+                             const LB& t, PslTrack* ps = nullptr)
 {
     w.restart_idx += 1;
     w.restarts += 1;
@@ -175,7 +194,7 @@ __device__ void long_restart(const LongWalk& lw, Walker& w, const WarpSmem& SL, 
         t.sync();
         w.gen = 1;
     }
-    long_start(lw, w, SL, base, V, t);
+    long_start(lw, w, SL, base, V, t, ps);
 }
 
 // HT probe of f by the first warp (the walk's linear probe of up to probe_cap <= 32
@@ -291,6 +310,109 @@ __device__ void long_walk(const LongWalk& lw, Walker& w, int64_t until, const Wa
     }
 }
 
+// The walk under the PSL objective for a long walker (the rules of walk_psl): the
+// Toeplitz dISL and the PSL of every neighbour, the lowest (PSL, ISL, i) not in HT, best
+// and stagnation on (PSL, ISL) pairs.
+template <class LB, int R>
+__device__ void long_walk_psl(const LongWalk& lw, Walker& w, PslTrack& ps, int64_t until, const WarpSmem& SL,
+                              int* base, const View& V, int trace_slot, int64_t trace_start, const LB& t)
+{
+    const WalkEnv& env = lw.e;
+    const KParams& p = *env.p;
+    const int lane = t.lane, n = env.n;
+    const Outs<LB, R> o(t);
+    float P[R];
+    p_direct(V, n, o, P);
+    StopCheck stop;
+    stop.start(p, lane == 0);
+    while (w.steps < until) {
+        if (w.isl > lw.isl_limit) {
+            if (lane == 0) raise_error(p.status, LABS_ERANGE, (int)env.g);
+            break;
+        }
+        if ((w.steps & (kCheckEvery - 1)) == 0) {
+            const int why = t.shfl(stop.poll(p, lane == 0), 0);
+            if (why) {
+                if (lane == 0) raise_error(p.status, why, (int)env.g);
+                break;
+            }
+        }
+        int dl[R], pl[R];
+        {
+            float X[R];
+            toeplitz(V, n, o, X);
+            assemble(V, n, o, X, P, dl);
+        }
+        psl_eval(V, n, o, pl);
+        uint64_t key[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            key[r] = dl[r] == INT_MAX ? ~0ull : psl_key(pl[r], w.isl + dl[r], 2 * (o.v0 + r) + o.p);
+        uint32_t excl = 0;
+        int best_i = -1;
+        uint64_t best_key = 0, fnew = 0;
+        int64_t slot = -1;
+        for (;;) {
+            uint64_t lm = ~0ull;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (!((excl >> r) & 1u) && key[r] < lm) lm = key[r];
+            const uint64_t km = t.rmin64(lm);
+            if (km == ~0ull) break;
+            const int bi = psl_key_i(km);
+            const uint64_t f = w.fp ^ __ldg(env.zk + bi);
+            const Probe pr = long_probe(lw, f, w.gen, t);
+            if (!pr.visited) {
+                best_i = bi;
+                best_key = km;
+                slot = pr.slot;
+                fnew = f;
+                break;
+            }
+            exclude<LB, R>(excl, bi, t);
+        }
+        w.steps += 1;
+        int code;
+        if (best_i < 0) {
+            w.blocked += 1;
+            long_restart(lw, w, SL, base, V, t, &ps);
+            p_direct(V, n, o, P);
+            code = LABS_TRACE_BLOCKED;
+        } else {
+            flip_rows_table(V, n, o, P, best_i, t);
+            const bool stored = slot >= 0;
+            if (lane == 0 && stored) env.T[slot] = (fnew & ~kGenMask) | w.gen;
+            if (lane == (best_i >> 5)) w.word ^= 1u << (best_i & 31);
+            t.sync();
+            w.fp = fnew;
+            w.isl = psl_key_isl(best_key);
+            ps.psl = psl_key_psl(best_key);
+            if (!stored) w.overflows += 1;
+            long_note_best(lw, w, t, &ps);
+            if (psl_better(ps.psl, w.isl, ps.since_psl, w.since)) {
+                w.since = w.isl;
+                ps.since_psl = ps.psl;
+                w.stag = 0;
+            } else {
+                w.stag += 1;
+            }
+            code = best_i;
+            if (w.stag >= env.patience || !stored) {
+                long_restart(lw, w, SL, base, V, t, &ps);
+                p_direct(V, n, o, P);
+                code |= LABS_TRACE_RESTART;
+            }
+        }
+        if (trace_slot >= 0 && lane == 0) {
+            const int64_t s = w.steps - 1 - trace_start;
+            if (s >= 0 && s < p.status->trace_capacity) {
+                p.status->trace_code[trace_slot * p.status->trace_capacity + s] = code;
+                p.status->trace_isl[trace_slot * p.status->trace_capacity + s] = w.isl;
+            }
+        }
+    }
+}
+
 __device__ LongWalk long_env(const KParams& p, int64_t wi, const DevGroup& G, uint32_t* bits)
 {
     LongWalk lw;
@@ -342,21 +464,26 @@ __global__ void __launch_bounds__(NT, kLongThreads / NT) long_reset_kernel(KPara
         w.best_isl = INT_MAX;
         w.best_step = 0;
         w.target_step = -1;
-        long_start(lw, w, SL, smem, V, t);
+        PslTrack ps;
+        ps.best_psl = INT_MAX;
+        const bool psl = p.mode == 3;
+        long_start(lw, w, SL, smem, V, t, psl ? &ps : nullptr);
         if (t.lane < lw.nw) lw.cur[t.lane] = w.word;
         if (t.lane == 0) {
             WalkerState* st = lw.e.st;
             save_scalars(st, w);
             st->group = gidx;
             st->trace_slot = -1;
-            st->psl = st->best_psl = st->since_psl = -1;
+            st->psl = psl ? ps.psl : -1;
+            st->best_psl = psl ? ps.best_psl : -1;
+            st->since_psl = psl ? ps.since_psl : -1;
         }
         t.sync();
     }
 }
 
 // One chunk of steps for every long walker; walkers are taken from a counter.
-template <int NT, int R>
+template <int NT, int R, bool PSL>
 __global__ void __launch_bounds__(NT, kLongThreads / NT) long_walk_kernel(KParams p, int chunk_index)
 {
     using LB = Blk<NT>;
@@ -387,7 +514,24 @@ __global__ void __launch_bounds__(NT, kLongThreads / NT) long_walk_kernel(KParam
             if (t.lane == 0) raise_error(p.status, LABS_ESTATE, (int)wi);
             continue;
         }
-        long_walk<LB, R>(lw, w, until, SL, smem, V, trace_slot, trace_start, t);
+        if constexpr (PSL) {
+            PslTrack ps;
+            ps.psl = table_psl(V, G.n, t);
+            ps.best_psl = st->best_psl;
+            ps.since_psl = st->since_psl;
+            if (ps.psl != st->psl) {
+                if (t.lane == 0) raise_error(p.status, LABS_ESTATE, (int)wi);
+                continue;
+            }
+            long_walk_psl<LB, R>(lw, w, ps, until, SL, smem, V, trace_slot, trace_start, t);
+            if (t.lane == 0) {
+                st->psl = ps.psl;
+                st->best_psl = ps.best_psl;
+                st->since_psl = ps.since_psl;
+            }
+        } else {
+            long_walk<LB, R>(lw, w, until, SL, smem, V, trace_slot, trace_start, t);
+        }
         if (t.lane < lw.nw) lw.cur[t.lane] = w.word;
         if (t.lane == 0) save_scalars(st, w);
         t.sync();
@@ -458,15 +602,15 @@ __global__ void __launch_bounds__(NT, kLongThreads / NT) long_delta_kernel(const
 using LongFn = void (*)(KParams, int);
 using LongDeltaFn = void (*)(const int8_t*, int64_t, int, int32_t*, DevStatus*);
 
-template <int NT>
+template <int NT, bool PSL>
 LongFn long_fn_nt(int R)
 {
     switch (R) {
-        case 1: return long_walk_kernel<NT, 1>;
-        case 3: return long_walk_kernel<NT, 3>;
-        case 5: return long_walk_kernel<NT, 5>;
-        case 7: return long_walk_kernel<NT, 7>;
-        default: return long_walk_kernel<NT, 9>;
+        case 1: return long_walk_kernel<NT, 1, PSL>;
+        case 3: return long_walk_kernel<NT, 3, PSL>;
+        case 5: return long_walk_kernel<NT, 5, PSL>;
+        case 7: return long_walk_kernel<NT, 7, PSL>;
+        default: return long_walk_kernel<NT, 9, PSL>;
     }
 }
 
@@ -482,11 +626,14 @@ LongDeltaFn long_delta_fn_nt(int R)
     }
 }
 
-// kernels for n_max free variables: CTA width long_threads(n_max), lane block long_R
-LongFn long_fn(int n_max)
+// kernels for n_max free variables: CTA width long_threads(n_max), lane block long_R;
+// psl: the walk under the PSL objective
+LongFn long_fn(int n_max, bool psl)
 {
     const int NT = long_threads(n_max), R = long_R(n_max, NT);
-    return NT == kLongThreadsSmall ? long_fn_nt<kLongThreadsSmall>(R) : long_fn_nt<kLongThreads>(R);
+    if (psl)
+        return NT == kLongThreadsSmall ? long_fn_nt<kLongThreadsSmall, true>(R) : long_fn_nt<kLongThreads, true>(R);
+    return NT == kLongThreadsSmall ? long_fn_nt<kLongThreadsSmall, false>(R) : long_fn_nt<kLongThreads, false>(R);
 }
 
 LongDeltaFn long_delta_fn(int n)
@@ -504,9 +651,9 @@ ResetFn long_reset_fn(int n_max)
 
 }  // namespace
 
-int long_kernel_config(int n_max, size_t smem_bytes, int* ctas_per_sm, int* regs)
+int long_kernel_config(int n_max, bool psl, size_t smem_bytes, int* ctas_per_sm, int* regs)
 {
-    const LongFn fn = long_fn(n_max);
+    const LongFn fn = long_fn(n_max, psl);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return LABS_ECUDA;
     e = cudaFuncSetAttribute(long_reset_fn(n_max), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
@@ -531,7 +678,7 @@ int launch_long_reset(const KParams& p, size_t smem_bytes, void* stream)
 
 int launch_long_walk_chunk(const KParams& p, int chunk_index, int grid, size_t smem_bytes, void* stream)
 {
-    long_fn(p.n_max)<<<grid, long_threads(p.n_max), smem_bytes, (cudaStream_t)stream>>>(p, chunk_index);
+    long_fn(p.n_max, p.mode == 3)<<<grid, long_threads(p.n_max), smem_bytes, (cudaStream_t)stream>>>(p, chunk_index);
     return cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ECUDA;
 }
 

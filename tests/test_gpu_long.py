@@ -92,7 +92,7 @@ def exact_limit(L):
     assembly stays below 2^24 (restated from the library's derivation)."""
     n = (L + 1) // 2
     room = ((1 << 24) - 8 * L - 32 * n - 32) / 16
-    return int(min(room * room / (n - 1), 2 ** 30)) - 1
+    return int(min(room * room / (n - 1), 2 ** 29)) - 1
 
 
 @pytest.mark.parametrize("L", [513, 1025, 4095, 8191])
@@ -152,7 +152,7 @@ def test_long_refusals():
         labs.Search([201, 1025], [2, 2], 1)  # short and long lengths in one context
     with pytest.raises(labs.LabsError):
         labs.Search(8193, 2, 1)
-    for f in (_native.LABS_FLAG_BEST_FIRST, _native.LABS_FLAG_LEARNED, _native.LABS_FLAG_PSL):
+    for f in (_native.LABS_FLAG_BEST_FIRST, _native.LABS_FLAG_LEARNED):
         with pytest.raises(labs.LabsError):
             labs.Search(1025, 2, 1, flags=f)
     s = labs.Search(1025, 2, 1)
@@ -186,4 +186,46 @@ def test_long_walker_outside_exact_range_stops_with_erange():
     r = s.results(1, 1)
     o = oracle.walk(L, seed, 1, 4, first_walker=1)
     assert r["isl"][0] == o["final_isl"][0]
+    s.close()
+
+
+@pytest.mark.parametrize("L,walkers,steps,kw", [
+    (513, 3, 60, {}),
+    (601, 2, 50, {"tabu_log2": 4, "probe_cap": 3}),
+    (1025, 2, 12, {}),
+])
+def test_long_psl_parity(L, walkers, steps, kw):
+    """The walk under the PSL objective for long sequences (one walker per CTA) against
+    the oracle, which rebuilds every neighbour: traces, final and best sequences with
+    their PSL and ISL, the best walker in the (PSL, ISL) order."""
+    seed = 8
+    s, code, isl = traced(L, walkers, steps, seed, objective="psl", **kw)
+    o = oracle.walk(L, seed, walkers, steps, trace=True, objective="psl", **kw)
+    assert np.array_equal(code, o["trace_code"])
+    assert np.array_equal(isl, o["trace_isl"])
+    res = s.results(seqs=True)
+    for k, ok in (("best_isl", "best_isl"), ("best_psl", "best_psl"), ("isl", "final_isl"), ("psl", "final_psl")):
+        assert np.array_equal(res[k], o[ok]), k
+    assert np.array_equal(res["best_seq"], o["best_seq"])
+    g = min(range(walkers), key=lambda j: (o["best_psl"][j], o["best_isl"][j], j))
+    b = s.best()
+    assert (b["psl"], b["isl"]) == (o["best_psl"][g], o["best_isl"][g])
+    assert s.stats()["walkers_per_warp"] == 0
+    s.close()
+
+
+def test_long_psl_chunking_and_mixed_lengths():
+    Ls, counts = [601, 1025], [2, 2]
+    s = labs.Search(Ls, counts, 4, objective="psl", chunk_steps=5)
+    code, isl = s.trace(list(range(4)), 14)
+    for part in (3, 11):
+        s.walk(part)
+    s.sync()
+    code, isl = code.cpu().numpy(), isl.cpu().numpy()
+    first = 0
+    for Lg, cnt in zip(Ls, counts):
+        o = oracle.walk(Lg, 4, cnt, 14, first_walker=first, trace=True, objective="psl")
+        assert np.array_equal(code[first:first + cnt], o["trace_code"]), Lg
+        assert np.array_equal(isl[first:first + cnt], o["trace_isl"]), Lg
+        first += cnt
     s.close()

@@ -5,7 +5,7 @@ host and prints each layout (row padding and length, table padding and length, b
 vectors, lane block).  For every length the kernels serve and every lane block the
 launch code can pick, the extreme index of every family of shared-memory accesses (the
 rows, the table, the bit vectors, in the walk, the best-first search, the PSL walk, the
-row kernels and the long-sequence kernels) must fall inside its region.  The index
+row kernels and the long-sequence kernels, plain and PSL) must fall inside its region.  The index
 families are restated here from the kernels; the lane and output indices enter them
 monotonically, so the first and last lane of each parity class bound them.
 """
@@ -188,6 +188,20 @@ def test_long_layouts(layouts):
                 reg.a(vb - (n - 1), "flip dn")
             reg.a(-(n - 1), "p")
             reg.a(2 * ((n + 1) >> 1), "p hi")
+            v0max = (nt // 2 - 1) * R        # the PSL neighbourhood (long PSL walk)
+            if R <= 5:
+                P = 3 * R - 2
+                tend = n - 1 + 2 * (R - 1)
+                reg.a(v0max + P - 1, "psl ring init hi")
+                reg.a(1 - P, "psl ring init lo")
+                reg.g(1 - P, "psl ring init G")
+                reg.a(-tend, "psl a")
+                reg.a(v0max + tend, "psl b")
+                reg.g(tend, "psl C")
+            else:
+                reg.a(-(n - 1), "psl sel a")
+                reg.a(v0max + n + R - 2, "psl sel b")
+                reg.a(v0max + R - 1, "psl sel init")
             if reg.bad:
                 bad.append((n_max, n, R, reg.bad[:3]))
     assert not bad, bad[:5]
@@ -203,4 +217,4 @@ def test_long_exact_range_bound(layouts):
         lim = long_[n]["limit"]
         assert 16 * ((n - 1) * lim) ** 0.5 + 8 * L + 32 * n + 32 < 2 ** 24
         assert lim > 4 * L * L // 2
-        assert lim < 2 ** 30
+        assert lim < 2 ** 29
