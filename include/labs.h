@@ -27,7 +27,8 @@
  *     (labs_sync, labs_best, labs_walker_results, labs_stats, labs_checkpoint).
  *   - Lengths: odd L with 3 <= L <= LABS_MAX_L (walkers run one, two or four per warp),
  *     or LABS_MAX_L < L <= LABS_MAX_L_LONG (long sequences: one walker per CTA of 256
- *     or 512 threads, the same step rule); a context holds lengths of one kind only.
+ *     or 512 threads, the same step rule, the walk under the ISL or the PSL objective
+ *     only); a context holds lengths of one kind only.
  *   - A context is not thread-safe; use one per host thread.
  */
 #ifndef LABS_H
