@@ -94,8 +94,9 @@ typedef struct labs_config {
                                        (see labs_walk) */
 #define LABS_FLAG_PSL 64            /* labs_walk minimises PSL (Section 1) instead of ISL: the
                                        walk's rules with (PSL, ISL) pairs as the objective (see
-                                       labs_walk); one walker per warp; not with
-                                       LABS_FLAG_BEST_FIRST or LABS_FLAG_LEARNED */
+                                       labs_walk); one walker per warp (per CTA for long
+                                       sequences); not with LABS_FLAG_BEST_FIRST or
+                                       LABS_FLAG_LEARNED */
 #define LABS_QUEUE_SIZE 32           /* entries of a walker's best-first queue */
 #define LABS_BEST_FIRST_MAX_STEPS (1ll << 28) /* steps per walker the queue order can number */
 
