@@ -704,14 +704,15 @@ static void *walk_thread(void *arg)
 }
 
 /* Walkers g0 .. g0+count-1 of length L each take `steps` steps of the walk (pq_size 0)
- * or of the best-first search with a queue of pq_size entries (pq_size > 0; -pq_size
- * entries and xLastovka's second table when pq_size < 0).  Results per walker
+ * or of the best-first search with a queue of pq_size entries (pq_size > 0, with
+ * xLastovka's second table when second_hash is set).  Results per walker
  * go to res[], best_seq/final_seq ([count][L], nullable) and, when trace_code is not
  * NULL, per-step traces ([count][steps]).  nthreads <= 0 uses every online core.
  * Returns 0, -1 on bad arguments, -2 on an internal mismatch, -3 on allocation
  * failure. */
 static int walk_many(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t steps,
-                     const lo_walk_cfg *cfg, int32_t pq_size, int32_t objective, lo_walk_result *res, int8_t *best_seq,
+                     const lo_walk_cfg *cfg, int32_t pq_size, int32_t second_hash, int32_t objective,
+                     lo_walk_result *res, int8_t *best_seq,
                      int8_t *final_seq, int32_t *trace_code, int32_t *trace_isl, int32_t nthreads)
 {
     if (L < 3 || (L & 1) == 0 || count < 0 || steps < 0 || !cfg || !res) return -1;
@@ -727,8 +728,8 @@ static int walk_many(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_
     job.L = L; job.seed = seed; job.g0 = g0; job.count = count; job.steps = steps;
     job.cfg = cfg; job.zkey = zkey; job.res = res; job.best_seq = best_seq;
     job.final_seq = final_seq; job.trace_code = trace_code; job.trace_isl = trace_isl;
-    job.pq_size = pq_size < 0 ? -pq_size : pq_size;
-    job.second_hash = pq_size < 0;
+    job.pq_size = pq_size;
+    job.second_hash = second_hash;
     job.objective = objective;
     pthread_mutex_init(&job.lock, NULL);
     if (nthreads <= 0) nthreads = (int32_t)sysconf(_SC_NPROCESSORS_ONLN);
@@ -747,7 +748,8 @@ int lo_walk(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t steps,
             const lo_walk_cfg *cfg, lo_walk_result *res, int8_t *best_seq, int8_t *final_seq,
             int32_t *trace_code, int32_t *trace_isl, int32_t nthreads)
 {
-    return walk_many(L, seed, g0, count, steps, cfg, 0, 0, res, best_seq, final_seq, trace_code, trace_isl, nthreads);
+    return walk_many(L, seed, g0, count, steps, cfg, 0, 0, 0, res, best_seq, final_seq, trace_code, trace_isl,
+                     nthreads);
 }
 
 /* As lo_walk with the PSL objective (walk_step_psl): the ISL trace still holds the ISL
@@ -757,7 +759,8 @@ int lo_walk_psl(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t ste
                 const lo_walk_cfg *cfg, lo_walk_result *res, int8_t *best_seq, int8_t *final_seq,
                 int32_t *trace_code, int32_t *trace_isl, int32_t nthreads)
 {
-    return walk_many(L, seed, g0, count, steps, cfg, 0, 1, res, best_seq, final_seq, trace_code, trace_isl, nthreads);
+    return walk_many(L, seed, g0, count, steps, cfg, 0, 0, 1, res, best_seq, final_seq, trace_code, trace_isl,
+                     nthreads);
 }
 
 /* One walker (id g) replayed with the learned-mode choices of a GPU run (lo_replay);
@@ -1015,7 +1018,7 @@ int lo_bestfirst(int32_t L, uint64_t seed, int64_t g0, int64_t count, int64_t st
                  int32_t *trace_isl, int32_t nthreads)
 {
     if (pq_size < 1) return -1;
-    return walk_many(L, seed, g0, count, steps, cfg, pq_size, 0, res, best_seq, final_seq, trace_code, trace_isl,
+    return walk_many(L, seed, g0, count, steps, cfg, pq_size, 0, 0, res, best_seq, final_seq, trace_code, trace_isl,
                      nthreads);
 }
 
@@ -1026,7 +1029,7 @@ int lo_bestfirst_cached(int32_t L, uint64_t seed, int64_t g0, int64_t count, int
                         int32_t *trace_code, int32_t *trace_isl, int32_t nthreads)
 {
     if (pq_size < 1) return -1;
-    return walk_many(L, seed, g0, count, steps, cfg, -pq_size, 0, res, best_seq, final_seq, trace_code, trace_isl,
+    return walk_many(L, seed, g0, count, steps, cfg, pq_size, 1, 0, res, best_seq, final_seq, trace_code, trace_isl,
                      nthreads);
 }
 
