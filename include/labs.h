@@ -27,8 +27,9 @@
  *     (labs_sync, labs_best, labs_walker_results, labs_stats, labs_checkpoint).
  *   - Lengths: odd L with 3 <= L <= LABS_MAX_L (walkers run one, two or four per warp),
  *     or LABS_MAX_L < L <= LABS_MAX_L_LONG (long sequences: one walker per CTA of 256
- *     or 512 threads, the same step rule, the walk under the ISL or the PSL objective
- *     only); a context holds lengths of one kind only.
+ *     or 512 threads, the same step rules: the walk under the ISL or the PSL objective,
+ *     or the best-first search without the second table); a context holds lengths of one
+ *     kind only.
  *   - A context is not thread-safe; use one per host thread.
  */
 #ifndef LABS_H
@@ -87,11 +88,12 @@ typedef struct labs_config {
 #define LABS_FLAG_BEST_FIRST 32     /* labs_walk runs Algorithm 1 as printed: best-first
                                        search with a queue of LABS_QUEUE_SIZE evaluated
                                        neighbours per walker (see labs_walk); one walker per
-                                       warp; not with LABS_FLAG_LEARNED, no checkpoints */
+                                       warp (per CTA for long sequences); not with
+                                       LABS_FLAG_LEARNED, no checkpoints */
 #define LABS_FLAG_SECOND_HASH 128   /* with LABS_FLAG_BEST_FIRST: xLastovka's second table of
                                        evaluated neighbours (Section 3), one per walker with
                                        as many slots as HT; neighbours it holds are skipped
-                                       (see labs_walk) */
+                                       (see labs_walk); lengths up to LABS_MAX_L */
 #define LABS_FLAG_PSL 64            /* labs_walk minimises PSL (Section 1) instead of ISL: the
                                        walk's rules with (PSL, ISL) pairs as the objective (see
                                        labs_walk); one walker per warp (per CTA for long
@@ -99,6 +101,7 @@ typedef struct labs_config {
                                        LABS_FLAG_LEARNED */
 #define LABS_QUEUE_SIZE 32           /* entries of a walker's best-first queue */
 #define LABS_BEST_FIRST_MAX_STEPS (1ll << 28) /* steps per walker the queue order can number */
+#define LABS_BEST_FIRST_MAX_STEPS_LONG (1ll << 22) /* the same for lengths above LABS_MAX_L */
 
 /* Counters of a context, summed over its walkers (labs_stats). */
 typedef struct labs_counters {
@@ -195,7 +198,8 @@ int labs_neighbor_delta(labs_ctx *ctx, const int8_t *dev_seqs, int64_t batch,
  *   that are get dropped) and is inserted into HT.  The best sequence is kept as in
  *   the walk; the walker restarts (HT and queue emptied) when the queue runs empty or
  *   HT has no free slot for the new S; `patience` is not used.  At most
- *   LABS_BEST_FIRST_MAX_STEPS steps per walker (LABS_EINVAL beyond).
+ *   LABS_BEST_FIRST_MAX_STEPS steps per walker, LABS_BEST_FIRST_MAX_STEPS_LONG for
+ *   lengths above LABS_MAX_L (LABS_EINVAL beyond).
  *   LABS_FLAG_SECOND_HASH adds xLastovka's second table (the library's reading of
  *   Section 3): a slot (fingerprint mod size) holds (HT generation << 40) | (~f mod 2^40)
  *   of a neighbour f; at the start of a step every neighbour whose slot holds its word is

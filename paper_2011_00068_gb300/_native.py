@@ -34,6 +34,7 @@ LABS_FLAG_PSL = 64
 LABS_FLAG_SECOND_HASH = 128
 LABS_QUEUE_SIZE = 32
 LABS_BEST_FIRST_MAX_STEPS = 1 << 28
+LABS_BEST_FIRST_MAX_STEPS_LONG = 1 << 22
 LOG_RECORD_BYTES = 64
 
 ERRORS = {LABS_EINVAL: "EINVAL", LABS_ENOMEM: "ENOMEM", LABS_ECUDA: "ECUDA", LABS_ETIMEOUT: "ETIMEOUT",

@@ -220,8 +220,9 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
         return fail(c, LABS_EINVAL, "LABS_FLAG_PSL combines with neither LABS_FLAG_BEST_FIRST nor LABS_FLAG_LEARNED");
     if (nL >= 1 && Ls && valid_long_L(Ls[0])) {
         c->long_mode = true;
-        if (k.flags & (LABS_FLAG_BEST_FIRST | LABS_FLAG_LEARNED))
-            return fail(c, LABS_EINVAL, "lengths above %d run the walk only (plain or PSL objective)", LABS_MAX_L);
+        if (k.flags & (LABS_FLAG_LEARNED | LABS_FLAG_SECOND_HASH))
+            return fail(c, LABS_EINVAL, "lengths above %d run the walk (plain or PSL objective) or the best-first "
+                        "search without the second table", LABS_MAX_L);
     }
     c->seed = seed;
     c->stream = (cudaStream_t)stream;
@@ -284,7 +285,8 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
         c->off_pq_key = off;
         off = align_up(off + sizeof(uint64_t) * LABS_QUEUE_SIZE * (size_t)c->W, 256);
         c->off_pq_bits = off;
-        off = align_up(off + sizeof(uint32_t) * kBitWords * LABS_QUEUE_SIZE * (size_t)c->W, 256);
+        const size_t qwords = c->long_mode ? kBitWordsLong : kBitWords;
+        off = align_up(off + sizeof(uint32_t) * qwords * LABS_QUEUE_SIZE * (size_t)c->W, 256);
     }
     c->off_tabu = off;
     off = align_up(off + sizeof(uint64_t) * ((size_t)c->W << k.tabu_log2), 256);
@@ -303,7 +305,8 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
         c->tile = long_threads(c->n_max);
         c->smem_bytes = (size_t)long_smem(c->n_max, c->tile).words * sizeof(int);
         int occ = 0;
-        if (long_kernel_config(c->n_max, (k.flags & LABS_FLAG_PSL) != 0, c->smem_bytes, &occ, &c->regs) != LABS_OK ||
+        const int mode = (k.flags & LABS_FLAG_PSL) ? 1 : (k.flags & LABS_FLAG_BEST_FIRST) ? 2 : 0;
+        if (long_kernel_config(c->n_max, mode, c->smem_bytes, &occ, &c->regs) != LABS_OK ||
             occ < 1)
             return fail(c, LABS_ECUDA, "long walk kernel does not fit on an SM (%zu bytes of shared memory)",
                         c->smem_bytes);
@@ -608,8 +611,9 @@ int labs_walk(labs_ctx* c, int64_t steps)
     int rc = need_ws(c);
     if (rc) return rc;
     if (steps < 0) return fail(c, LABS_EINVAL, "negative steps");
-    if ((c->cfg.flags & LABS_FLAG_BEST_FIRST) && c->planned + steps > LABS_BEST_FIRST_MAX_STEPS)
-        return fail(c, LABS_EINVAL, "best-first search: at most %lld steps per walker", LABS_BEST_FIRST_MAX_STEPS);
+    const long long bf_max = c->long_mode ? LABS_BEST_FIRST_MAX_STEPS_LONG : LABS_BEST_FIRST_MAX_STEPS;
+    if ((c->cfg.flags & LABS_FLAG_BEST_FIRST) && c->planned + steps > bf_max)
+        return fail(c, LABS_EINVAL, "best-first search: at most %lld steps per walker", bf_max);
     if ((steps == 0 && !c->catch_up) || c->W == 0) return LABS_OK;
     cudaSetDevice(c->device);
     const KParams p = params(c);

@@ -252,8 +252,8 @@ __host__ __device__ inline int long_R(int n, int threads)
 }
 
 // Shared-memory layout of one long walker (one CTA): the rows and the table as in the
-// warp layout (bounds from the tile code with tile = kLongThreads), bit vectors sized
-// for n_max, then the CTA scratch and the bits.
+// warp layout (bounds from the tile code with tile = the CTA width), bit vectors sized
+// for n_max, then the CTA scratch, the bits and the best-first queue's keys.
 __host__ __device__ inline WarpSmem long_smem(int n_max, int tile)
 {
     WarpSmem w;
@@ -276,7 +276,8 @@ __host__ __device__ inline WarpSmem long_smem(int n_max, int tile)
     w.boff = w.goff + 2 * w.glen;
     w.bvec = (n_max + 31) / 32 + 2;
     w.xoff = (w.boff + 4 * w.bvec + 3) & ~3;
-    w.words = w.xoff + tile + kBitWordsLong;
+    // scratch, bits, then the best-first queue's keys (LABS_QUEUE_SIZE 64-bit words)
+    w.words = w.xoff + tile + kBitWordsLong + 2 * LABS_QUEUE_SIZE;
     return w;
 }
 
@@ -307,7 +308,7 @@ WalkFn walk_fn32b(int rmax);  // best-first search (labs_walk32b.cu)
 WalkFn walk_fn32p(int rmax);  // walk under the PSL objective (labs_walk32p.cu)
 
 // Long-L walk (labs_long.cu).
-int long_kernel_config(int n_max, bool psl, size_t smem_bytes, int* ctas_per_sm, int* regs);
+int long_kernel_config(int n_max, int mode, size_t smem_bytes, int* ctas_per_sm, int* regs);
 int launch_long_reset(const KParams& p, size_t smem_bytes, void* stream);
 int launch_long_walk_chunk(const KParams& p, int chunk_index, int grid, size_t smem_bytes, void* stream);
 int launch_long_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status, void* stream);

@@ -413,6 +413,190 @@ __device__ void long_walk_psl(const LongWalk& lw, Walker& w, PslTrack& ps, int64
     }
 }
 
+// Best-first search for a long walker (the rules of walk_bestfirst, Algorithm 1 as
+// printed): the queue's 32 keys ISL << 34 | (steps before the producing step) << 12 | i
+// (ISL < 2^30 under the exact-range bound, at most LABS_BEST_FIRST_MAX_STEPS_LONG steps)
+// sit in shared memory, where every thread reads them, so every decision below is taken
+// identically by the whole CTA; the entries' bits (kBitWordsLong words each) are in
+// global memory.  An entry that differs from S in at most kBestFirstMaxFlips free
+// variables is reached by that many incremental flips, any other by a rebuild.
+constexpr uint64_t kLongEmpty = ~0ull;
+
+__device__ __forceinline__ int long_queue_min(const uint64_t* Q, uint64_t& v)
+{
+    int k = -1;
+    v = kLongEmpty;
+#pragma unroll
+    for (int j = 0; j < LABS_QUEUE_SIZE; ++j)
+        if (Q[j] < v) {
+            v = Q[j];
+            k = j;
+        }
+    return k;
+}
+
+template <class LB, int R>
+__device__ void long_walk_bestfirst(const LongWalk& lw, Walker& w, int64_t until, const WarpSmem& SL, int* base,
+                                    const View& V, int trace_slot, int64_t trace_start, const LB& t, uint64_t* Q,
+                                    uint32_t* qbits)
+{
+    const WalkEnv& env = lw.e;
+    const KParams& p = *env.p;
+    const int lane = t.lane, n = env.n;
+    const Outs<LB, R> o(t);
+    const int tisl = target_isl(p, env.L);
+    float P[R];
+    p_direct(V, n, o, P);
+    StopCheck stop;
+    stop.start(p, lane == 0);
+    while (w.steps < until) {
+        if (w.isl > lw.isl_limit) {
+            if (lane == 0) raise_error(p.status, LABS_ERANGE, (int)env.g);
+            break;
+        }
+        if ((w.steps & (kCheckEvery - 1)) == 0) {
+            const int why = t.shfl(stop.poll(p, lane == 0), 0);
+            if (why) {
+                if (lane == 0) raise_error(p.status, why, (int)env.g);
+                break;
+            }
+        }
+        const uint64_t e = (uint64_t)w.steps;
+        int dl[R];
+        {
+            float X[R];
+            toeplitz(V, n, o, X);
+            assemble(V, n, o, X, P, dl);
+        }
+        // the queue's last entry at the start of the step (empty place: no bound)
+        uint64_t last0 = 0;
+        bool full0 = true;
+#pragma unroll
+        for (int j = 0; j < LABS_QUEUE_SIZE; ++j) {
+            if (Q[j] == kLongEmpty) full0 = false;
+            else last0 = max(last0, Q[j]);
+        }
+        if (!full0) last0 = kLongEmpty;
+        uint64_t key[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            key[r] = kLongEmpty;
+            if (dl[r] != INT_MAX) {
+                const uint64_t ck = ((uint64_t)(uint32_t)(w.isl + dl[r]) << 34) | (e << 12) |
+                                    (uint64_t)(2 * (o.v0 + r) + o.p);
+                if (ck < last0) key[r] = ck;
+            }
+        }
+        // neighbours in queue order while they come before the queue's last entry or the
+        // queue has a free place; each looked up in HT when the insertion reaches it
+        uint64_t floor = 0;
+        for (;;) {
+            uint64_t b = kLongEmpty;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (key[r] > floor) b = min(b, key[r]);
+            const uint64_t ck = t.rmin64(b);
+            if (ck == kLongEmpty) break;
+            floor = ck;
+            int dst = -1;
+            uint64_t last = 0;
+#pragma unroll
+            for (int j = 0; j < LABS_QUEUE_SIZE; ++j) {
+                if (Q[j] == kLongEmpty) {
+                    if (dst < 0) dst = j;
+                } else {
+                    last = max(last, Q[j]);
+                }
+            }
+            if (dst < 0) {
+                if (ck > last) break;  // every later neighbour comes after it too
+#pragma unroll
+                for (int j = LABS_QUEUE_SIZE - 1; j >= 0; --j)
+                    if (Q[j] == last) dst = j;
+            }
+            const int i = (int)(ck & 0xFFFu);
+            const uint64_t f = w.fp ^ __ldg(env.zk + i);
+            const Probe pr = long_probe(lw, f, w.gen, t);
+            if (pr.visited) continue;
+            const uint32_t word = w.word ^ (lane == (i >> 5) ? 1u << (i & 31) : 0u);
+            if (lane < lw.nw) qbits[dst * kBitWordsLong + lane] = word;
+            const int isl_f = (int)(ck >> 34);
+            if (isl_f < w.best_isl) {
+                w.best_isl = isl_f;
+                w.best_step = (int64_t)e + 1;
+                if (lane < lw.nw) lw.best[lane] = word;
+            }
+            if (w.target_step < 0 && isl_f <= tisl) w.target_step = (int64_t)e + 1;
+            t.sync();  // every thread has read Q for this candidate
+            if (lane == 0) Q[dst] = ck;
+            t.sync();
+        }
+        // S <- the queue's first entry not in HT (entries that are get dropped)
+        int code = LABS_TRACE_BLOCKED;
+        bool again = true;
+        for (;;) {
+            uint64_t first;
+            const int src = long_queue_min(Q, first);
+            if (src < 0) {
+                w.blocked += 1;  // empty queue: restart
+                break;
+            }
+            const uint32_t word = lane < lw.nw ? qbits[src * kBitWordsLong + lane] : 0u;
+            t.sync();  // every thread has read Q
+            if (lane == 0) Q[src] = kLongEmpty;
+            if (lane < lw.nw) lw.bits[lane] = word;
+            t.sync();
+            const int i = (int)(first & 0xFFFu);
+            const bool nb = ((first >> 12) & 0x3FFFFFull) == e;  // a neighbour of S
+            const uint64_t f = nb ? (w.fp ^ __ldg(env.zk + i)) : long_fingerprint(lw, t);
+            const Probe pr = long_probe(lw, f, w.gen, t);
+            if (pr.visited) continue;
+            // free variables in which the new S differs from S (1 for a neighbour)
+            uint32_t diff = lane < lw.nw ? (word ^ w.word) : 0u;
+            const int k = nb ? 1 : t.radd(__popc(diff));
+            if (k <= kBestFirstMaxFlips) {
+                for (int j = 0; j < k; ++j) {
+                    const int lo = diff ? 32 * lane + __ffs(diff) - 1 : INT_MAX;
+                    const int fi = nb ? i : t.rmin(lo);
+                    flip_rows_table(V, n, o, P, fi, t);
+                    t.sync();
+                    if (lane == (fi >> 5)) diff &= ~(1u << (fi & 31));
+                }
+            } else {
+                long_load_rows(lw, SL, base, V, word, t);
+                p_direct(V, n, o, P);
+            }
+            w.word = word;
+            w.isl = (int)(first >> 34);
+            w.fp = f;
+            code = (int)(f & 0xFFFFu);
+            if (pr.slot >= 0) {
+                if (lane == 0) env.T[pr.slot] = (f & ~kGenMask) | w.gen;
+                again = false;
+            } else {
+                w.overflows += 1;  // no free HT slot for the new S: restart
+                code |= LABS_TRACE_RESTART;
+            }
+            break;
+        }
+        w.steps += 1;
+        if (again) {
+            t.sync();
+            if (lane < LABS_QUEUE_SIZE) Q[lane] = kLongEmpty;
+            long_restart(lw, w, SL, base, V, t);
+            p_direct(V, n, o, P);
+        }
+        t.sync();
+        if (trace_slot >= 0 && lane == 0) {
+            const int64_t s = w.steps - 1 - trace_start;
+            if (s >= 0 && s < p.status->trace_capacity) {
+                p.status->trace_code[trace_slot * p.status->trace_capacity + s] = code;
+                p.status->trace_isl[trace_slot * p.status->trace_capacity + s] = w.isl;
+            }
+        }
+    }
+}
+
 __device__ LongWalk long_env(const KParams& p, int64_t wi, const DevGroup& G, uint32_t* bits)
 {
     LongWalk lw;
@@ -469,6 +653,7 @@ __global__ void __launch_bounds__(NT, kLongThreads / NT) long_reset_kernel(KPara
         const bool psl = p.mode == 3;
         long_start(lw, w, SL, smem, V, t, psl ? &ps : nullptr);
         if (t.lane < lw.nw) lw.cur[t.lane] = w.word;
+        if (p.best_first && t.lane < LABS_QUEUE_SIZE) p.pq_key[wi * LABS_QUEUE_SIZE + t.lane] = ~0ull;
         if (t.lane == 0) {
             WalkerState* st = lw.e.st;
             save_scalars(st, w);
@@ -483,7 +668,7 @@ __global__ void __launch_bounds__(NT, kLongThreads / NT) long_reset_kernel(KPara
 }
 
 // One chunk of steps for every long walker; walkers are taken from a counter.
-template <int NT, int R, bool PSL>
+template <int NT, int R, int MODE>
 __global__ void __launch_bounds__(NT, kLongThreads / NT) long_walk_kernel(KParams p, int chunk_index)
 {
     using LB = Blk<NT>;
@@ -514,7 +699,7 @@ __global__ void __launch_bounds__(NT, kLongThreads / NT) long_walk_kernel(KParam
             if (t.lane == 0) raise_error(p.status, LABS_ESTATE, (int)wi);
             continue;
         }
-        if constexpr (PSL) {
+        if constexpr (MODE == 1) {
             PslTrack ps;
             ps.psl = table_psl(V, G.n, t);
             ps.best_psl = st->best_psl;
@@ -529,6 +714,15 @@ __global__ void __launch_bounds__(NT, kLongThreads / NT) long_walk_kernel(KParam
                 st->best_psl = ps.best_psl;
                 st->since_psl = ps.since_psl;
             }
+        } else if constexpr (MODE == 2) {
+            uint64_t* Q = reinterpret_cast<uint64_t*>(smem + SL.xoff + NT + kBitWordsLong);
+            uint64_t* qk = p.pq_key + wi * LABS_QUEUE_SIZE;
+            if (t.lane < LABS_QUEUE_SIZE) Q[t.lane] = qk[t.lane];
+            t.sync();
+            long_walk_bestfirst<LB, R>(lw, w, until, SL, smem, V, trace_slot, trace_start, t, Q,
+                                       p.pq_bits + wi * LABS_QUEUE_SIZE * kBitWordsLong);
+            t.sync();
+            if (t.lane < LABS_QUEUE_SIZE) qk[t.lane] = Q[t.lane];
         } else {
             long_walk<LB, R>(lw, w, until, SL, smem, V, trace_slot, trace_start, t);
         }
@@ -602,16 +796,22 @@ __global__ void __launch_bounds__(NT, kLongThreads / NT) long_delta_kernel(const
 using LongFn = void (*)(KParams, int);
 using LongDeltaFn = void (*)(const int8_t*, int64_t, int, int32_t*, DevStatus*);
 
-template <int NT, bool PSL>
+template <int NT, int MODE>
 LongFn long_fn_nt(int R)
 {
     switch (R) {
-        case 1: return long_walk_kernel<NT, 1, PSL>;
-        case 3: return long_walk_kernel<NT, 3, PSL>;
-        case 5: return long_walk_kernel<NT, 5, PSL>;
-        case 7: return long_walk_kernel<NT, 7, PSL>;
-        default: return long_walk_kernel<NT, 9, PSL>;
+        case 1: return long_walk_kernel<NT, 1, MODE>;
+        case 3: return long_walk_kernel<NT, 3, MODE>;
+        case 5: return long_walk_kernel<NT, 5, MODE>;
+        case 7: return long_walk_kernel<NT, 7, MODE>;
+        default: return long_walk_kernel<NT, 9, MODE>;
     }
+}
+
+template <int MODE>
+LongFn long_fn_mode(int NT, int R)
+{
+    return NT == kLongThreadsSmall ? long_fn_nt<kLongThreadsSmall, MODE>(R) : long_fn_nt<kLongThreads, MODE>(R);
 }
 
 template <int NT>
@@ -627,13 +827,11 @@ LongDeltaFn long_delta_fn_nt(int R)
 }
 
 // kernels for n_max free variables: CTA width long_threads(n_max), lane block long_R;
-// psl: the walk under the PSL objective
-LongFn long_fn(int n_max, bool psl)
+// mode 0 the walk, 1 the walk under the PSL objective, 2 the best-first search
+LongFn long_fn(int n_max, int mode)
 {
     const int NT = long_threads(n_max), R = long_R(n_max, NT);
-    if (psl)
-        return NT == kLongThreadsSmall ? long_fn_nt<kLongThreadsSmall, true>(R) : long_fn_nt<kLongThreads, true>(R);
-    return NT == kLongThreadsSmall ? long_fn_nt<kLongThreadsSmall, false>(R) : long_fn_nt<kLongThreads, false>(R);
+    return mode == 1 ? long_fn_mode<1>(NT, R) : mode == 2 ? long_fn_mode<2>(NT, R) : long_fn_mode<0>(NT, R);
 }
 
 LongDeltaFn long_delta_fn(int n)
@@ -651,9 +849,9 @@ ResetFn long_reset_fn(int n_max)
 
 }  // namespace
 
-int long_kernel_config(int n_max, bool psl, size_t smem_bytes, int* ctas_per_sm, int* regs)
+int long_kernel_config(int n_max, int mode, size_t smem_bytes, int* ctas_per_sm, int* regs)
 {
-    const LongFn fn = long_fn(n_max, psl);
+    const LongFn fn = long_fn(n_max, mode);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return LABS_ECUDA;
     e = cudaFuncSetAttribute(long_reset_fn(n_max), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
@@ -678,7 +876,8 @@ int launch_long_reset(const KParams& p, size_t smem_bytes, void* stream)
 
 int launch_long_walk_chunk(const KParams& p, int chunk_index, int grid, size_t smem_bytes, void* stream)
 {
-    long_fn(p.n_max, p.mode == 3)<<<grid, long_threads(p.n_max), smem_bytes, (cudaStream_t)stream>>>(p, chunk_index);
+    const int mode = p.mode == 3 ? 1 : p.mode == 2 ? 2 : 0;
+    long_fn(p.n_max, mode)<<<grid, long_threads(p.n_max), smem_bytes, (cudaStream_t)stream>>>(p, chunk_index);
     return cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ECUDA;
 }
 

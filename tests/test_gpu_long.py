@@ -152,12 +152,20 @@ def test_long_refusals():
         labs.Search([201, 1025], [2, 2], 1)  # short and long lengths in one context
     with pytest.raises(labs.LabsError):
         labs.Search(8193, 2, 1)
-    for f in (_native.LABS_FLAG_BEST_FIRST, _native.LABS_FLAG_LEARNED):
+    BF = _native.LABS_FLAG_BEST_FIRST
+    for f in (_native.LABS_FLAG_LEARNED, BF | _native.LABS_FLAG_SECOND_HASH):
         with pytest.raises(labs.LabsError):
             labs.Search(1025, 2, 1, flags=f)
     s = labs.Search(1025, 2, 1)
     with pytest.raises(labs.LabsError):
         s.log(4)
+    s.close()
+    s = labs.Search(1025, 2, 1, flags=BF)
+    s.walk(3)
+    with pytest.raises(labs.LabsError):
+        s.checkpoint()
+    with pytest.raises(labs.LabsError):
+        s.walk(_native.LABS_BEST_FIRST_MAX_STEPS_LONG)
     s.close()
 
 
@@ -225,6 +233,54 @@ def test_long_psl_chunking_and_mixed_lengths():
     first = 0
     for Lg, cnt in zip(Ls, counts):
         o = oracle.walk(Lg, 4, cnt, 14, first_walker=first, trace=True, objective="psl")
+        assert np.array_equal(code[first:first + cnt], o["trace_code"]), Lg
+        assert np.array_equal(isl[first:first + cnt], o["trace_isl"]), Lg
+        first += cnt
+    s.close()
+
+
+@pytest.mark.parametrize("L,walkers,steps,kw", [
+    (513, 3, 80, {}),
+    (601, 2, 60, {"tabu_log2": 4, "probe_cap": 3}),
+    (1025, 2, 40, {}),
+    (2049, 1, 20, {}),
+    (4801, 1, 6, {}),
+])
+def test_long_bestfirst_parity(L, walkers, steps, kw):
+    """The best-first search (Algorithm 1 as printed) for long sequences, one walker per
+    CTA of 256 threads (512 at L = 4801), against the oracle: per-step trace codes and
+    ISLs, best and final sequences, counters."""
+    seed = 3
+    s, code, isl = traced(L, walkers, steps, seed, flags=_native.LABS_FLAG_BEST_FIRST, **kw)
+    o = oracle.bestfirst(L, seed, walkers, steps, pq_size=_native.LABS_QUEUE_SIZE, trace=True, **kw)
+    assert np.array_equal(code, o["trace_code"])
+    assert np.array_equal(isl, o["trace_isl"])
+    res = s.results(seqs=True)
+    for k, ok in (("best_isl", "best_isl"), ("target_step", "target_step"), ("isl", "final_isl")):
+        assert np.array_equal(res[k], o[ok]), k
+    assert np.array_equal(res["seq"], o["final_seq"])
+    assert np.array_equal(res["best_seq"], o["best_seq"])
+    st = s.stats()
+    assert st["steps"] == walkers * steps and st["walkers_per_warp"] == 0
+    assert st["restarts"] == int(o["restarts"].sum())
+    assert st["overflows"] == int(o["overflows"].sum())
+    assert st["blocked"] == int((o["trace_code"] == -1).sum())
+    s.close()
+
+
+def test_long_bestfirst_chunking_and_mixed_lengths():
+    """The queue survives the ends of chunks and of labs_walk calls: the same traces
+    with 5-step chunks over three calls, two lengths in one launch."""
+    Ls, counts = [601, 1025], [2, 2]
+    s = labs.Search(Ls, counts, 6, flags=_native.LABS_FLAG_BEST_FIRST, chunk_steps=5)
+    code, isl = s.trace(list(range(4)), 30)
+    for part in (3, 11, 16):
+        s.walk(part)
+    s.sync()
+    code, isl = code.cpu().numpy(), isl.cpu().numpy()
+    first = 0
+    for Lg, cnt in zip(Ls, counts):
+        o = oracle.bestfirst(Lg, 6, cnt, 30, pq_size=_native.LABS_QUEUE_SIZE, first_walker=first, trace=True)
         assert np.array_equal(code[first:first + cnt], o["trace_code"]), Lg
         assert np.array_equal(isl[first:first + cnt], o["trace_isl"]), Lg
         first += cnt

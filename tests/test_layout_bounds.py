@@ -5,7 +5,7 @@ host and prints each layout (row padding and length, table padding and length, b
 vectors, lane block).  For every length the kernels serve and every lane block the
 launch code can pick, the extreme index of every family of shared-memory accesses (the
 rows, the table, the bit vectors, in the walk, the best-first search, the PSL walk, the
-row kernels and the long-sequence kernels, plain and PSL) must fall inside its region.  The index
+row kernels and the long-sequence kernels, plain, PSL and best-first) must fall inside its region.  The index
 families are restated here from the kernels; the lane and output indices enter them
 monotonically, so the first and last lane of each parity class bound them.
 """
@@ -177,7 +177,9 @@ def test_long_layouts(layouts):
     for n_max in range(257, 4097):
         S = long_[n_max]
         nt, R = S["nt"], S["R"]
-        assert nt * R >= n_max and S["words"] >= S["xoff"] + nt + 128
+        # scratch (nt words), bits (128 words), then the best-first queue's 32 keys, 8-byte aligned
+        assert nt * R >= n_max and S["words"] >= S["xoff"] + nt + 128 + 2 * 32
+        assert (S["xoff"] + nt + 128) % 2 == 0
         assert S["words"] * 4 <= (227 * 1024 if nt == 512 else 113 * 1024)  # one / two CTAs per SM
         for n in sorted({257, (257 + n_max) // 2, n_max}):
             reg = Region(S)
