@@ -503,11 +503,13 @@ def run_scaleup(args):
 
 def run_long(args):
     """Long sequences (one walker per CTA): L = 2047, 4095 and 8191, long_walkers
-    walkers x long_steps steps each: flips/s, the walk kernel's roofline fraction (one
-    FMA per lag term, as the warp kernels), best F; one JSON line."""
+    walkers x long_steps steps each of the walk (ISL or PSL objective) or the best-first
+    search: flips/s, the kernel's roofline fraction (one FMA per lag term, as the warp
+    kernels), best F; one JSON line."""
     import torch
 
     import paper_2011_00068_gb300 as labs
+    from paper_2011_00068_gb300 import _native
 
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
@@ -516,9 +518,10 @@ def run_long(args):
     peak = FP32_LANES_PER_SM * 2 * sms * sm_mhz * 1e6
     out = {}
     objective = "psl" if args.search == "psl" else "isl"
+    flags = _native.LABS_FLAG_BEST_FIRST if args.search == "bestfirst" else 0
     for L in (2047, 4095, 8191):
         n = (L + 1) // 2
-        s = labs.Search(L, args.long_walkers, 42, device=dev, objective=objective)
+        s = labs.Search(L, args.long_walkers, 42, device=dev, objective=objective, flags=flags)
         s.walk(8)  # warm-up: graph capture, first touch of the tables
         s.sync()
         s.reset()
@@ -543,7 +546,8 @@ def run_long(args):
         del s
         torch.cuda.empty_cache()
     total = sum(v["flips_per_s"] * v["ms"] for v in out.values()) / sum(v["ms"] for v in out.values())
-    line = {"metric": "exact flip evaluations/sec, long sequences" + (", PSL objective" if objective == "psl" else ""),
+    what = {"psl": ", PSL objective", "bestfirst": ", best-first search"}.get(args.search, "")
+    line = {"metric": "exact flip evaluations/sec, long sequences" + what,
             "value": total, "unit": "flip evaluations/s",
             "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic", "vs_baseline": None,
             "config": {"workload": "L=2047, 4095 and 8191, %d walkers each (one per CTA of 256 or 512 threads), %d steps, "
