@@ -276,8 +276,11 @@ __host__ __device__ inline WarpSmem long_smem(int n_max, int tile)
     w.boff = w.goff + 2 * w.glen;
     w.bvec = (n_max + 31) / 32 + 2;
     w.xoff = (w.boff + 4 * w.bvec + 3) & ~3;
-    // scratch, bits, then the best-first queue's keys (LABS_QUEUE_SIZE 64-bit words)
-    w.words = w.xoff + tile + kBitWordsLong + 2 * LABS_QUEUE_SIZE;
+    // scratch, bits, then the best-first search's queue keys (LABS_QUEUE_SIZE 64-bit
+    // words), each warp's lowest candidate keys (32 per warp), the keys entered in a
+    // round, two words of round state and the entered keys' places (LABS_QUEUE_SIZE ints)
+    w.words = w.xoff + tile + kBitWordsLong + 2 * LABS_QUEUE_SIZE + 2 * tile + 2 * LABS_QUEUE_SIZE + 4 +
+              LABS_QUEUE_SIZE;
     return w;
 }
 

@@ -445,6 +445,10 @@ __device__ void long_walk_bestfirst(const LongWalk& lw, Walker& w, int64_t until
     const int lane = t.lane, n = env.n;
     const Outs<LB, R> o(t);
     const int tisl = target_isl(p, env.L);
+    uint64_t* WL = Q + LABS_QUEUE_SIZE;                  // [warps][32] each warp's lowest keys
+    uint64_t* IK = WL + LB::kSize;                       // [32] keys entered in a round
+    uint64_t* meta = IK + LABS_QUEUE_SIZE;               // entered | another round << 8; last key
+    int* ID = reinterpret_cast<int*>(meta + 2);          // [32] their places in the queue
     float P[R];
     p_direct(V, n, o, P);
     StopCheck stop;
@@ -487,49 +491,111 @@ __device__ void long_walk_bestfirst(const LongWalk& lw, Walker& w, int64_t until
                 if (ck < last0) key[r] = ck;
             }
         }
-        // neighbours in queue order while they come before the queue's last entry or the
-        // queue has a free place; each looked up in HT when the insertion reaches it
+        // Neighbours in queue order while they come before the queue's last entry or the
+        // queue has a free place, in rounds of LABS_QUEUE_SIZE candidates: each warp sorts
+        // out its lowest keys, the first warp merges them into the CTA's lowest, looks
+        // them all up in HT at once (one per lane; HT does not change during the
+        // insertion, so this equals looking each up when the insertion reaches it) and
+        // runs the insertion on its registers; the other threads then write the entered
+        // entries' bits.  An entry entered during the step is never replaced in the same
+        // step (every later neighbour comes after it), so the places written are distinct.
+        // A further round runs only when all LABS_QUEUE_SIZE candidates were taken or
+        // skipped without reaching the queue's last entry.
         uint64_t floor = 0;
         for (;;) {
-            uint64_t b = kLongEmpty;
+            {
+                const int wl = lane & 31, wid = lane >> 5;
+                uint64_t fl = floor;
+                for (int k = 0; k < 32; ++k) {
+                    uint64_t b = kLongEmpty;
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-                if (key[r] > floor) b = min(b, key[r]);
-            const uint64_t ck = t.rmin64(b);
-            if (ck == kLongEmpty) break;
-            floor = ck;
-            int dst = -1;
-            uint64_t last = 0;
-#pragma unroll
-            for (int j = 0; j < LABS_QUEUE_SIZE; ++j) {
-                if (Q[j] == kLongEmpty) {
-                    if (dst < 0) dst = j;
-                } else {
-                    last = max(last, Q[j]);
+                    for (int r = 0; r < R; ++r)
+                        if (key[r] > fl) b = min(b, key[r]);
+                    b = warp_min64(b);
+                    if (wl == 0) WL[wid * 32 + k] = b;
+                    if (b == kLongEmpty) break;
+                    fl = b;
                 }
             }
-            if (dst < 0) {
-                if (ck > last) break;  // every later neighbour comes after it too
-#pragma unroll
-                for (int j = LABS_QUEUE_SIZE - 1; j >= 0; --j)
-                    if (Q[j] == last) dst = j;
-            }
-            const int i = (int)(ck & 0xFFFu);
-            const uint64_t f = w.fp ^ __ldg(env.zk + i);
-            const Probe pr = long_probe(lw, f, w.gen, t);
-            if (pr.visited) continue;
-            const uint32_t word = w.word ^ (lane == (i >> 5) ? 1u << (i & 31) : 0u);
-            if (lane < lw.nw) qbits[dst * kBitWordsLong + lane] = word;
-            const int isl_f = (int)(ck >> 34);
-            if (isl_f < w.best_isl) {
-                w.best_isl = isl_f;
-                w.best_step = (int64_t)e + 1;
-                if (lane < lw.nw) lw.best[lane] = word;
-            }
-            if (w.target_step < 0 && isl_f <= tisl) w.target_step = (int64_t)e + 1;
-            t.sync();  // every thread has read Q for this candidate
-            if (lane == 0) Q[dst] = ck;
             t.sync();
+            if (lane < 32) {
+                int h = 0, cnt = 0;
+                uint64_t v = lane < LB::kWarps ? WL[lane * 32] : kLongEmpty, mine = kLongEmpty;
+                for (; cnt < LABS_QUEUE_SIZE; ++cnt) {
+                    const uint64_t m = warp_min64(v);
+                    if (m == kLongEmpty) break;
+                    if (lane == cnt) mine = m;
+                    if (v == m) {
+                        ++h;
+                        v = h < 32 ? WL[lane * 32 + h] : kLongEmpty;
+                    }
+                }
+                bool vis = false;
+                if (lane < cnt) {
+                    const uint64_t f = w.fp ^ __ldg(env.zk + (int)(mine & 0xFFFu));
+                    const uint64_t tag = (f & ~kGenMask) | w.gen;
+                    for (int s = 0; s < p.probe_cap; ++s) {
+                        const uint64_t x = env.T[(f + (uint64_t)s) & env.tmask];
+                        if (x == tag) {
+                            vis = true;
+                            break;
+                        }
+                        if ((x & kGenMask) != w.gen) break;
+                    }
+                }
+                const unsigned visited = __ballot_sync(kFull, vis);
+                uint64_t qk = Q[lane];
+                int nins = 0;
+                bool stopped = false;
+                for (int k = 0; k < cnt; ++k) {
+                    if ((visited >> k) & 1u) continue;
+                    const uint64_t ck = __shfl_sync(kFull, mine, k);
+                    const unsigned empty = __ballot_sync(kFull, qk == kLongEmpty);
+                    int dst;
+                    if (empty) {
+                        dst = __ffs(empty) - 1;
+                    } else {
+                        const uint64_t last = warp_max64(qk);
+                        if (ck > last) {
+                            stopped = true;  // every later neighbour comes after it too
+                            break;
+                        }
+                        dst = __ffs(__ballot_sync(kFull, qk == last)) - 1;
+                    }
+                    if (lane == dst) qk = ck;
+                    if (lane == 0) {
+                        IK[nins] = ck;
+                        ID[nins] = dst;
+                    }
+                    ++nins;
+                }
+                Q[lane] = qk;
+                const uint64_t lastc = __shfl_sync(kFull, mine, cnt > 0 ? cnt - 1 : 0);
+                if (lane == 0) {
+                    meta[0] = (uint64_t)nins | (!stopped && cnt == LABS_QUEUE_SIZE ? 256u : 0u);
+                    meta[1] = lastc;
+                }
+            }
+            t.sync();
+            const int m0 = (int)meta[0], nins = m0 & 0xFF;
+            for (int j = 0; j < nins; ++j) {
+                const int i = (int)(IK[j] & 0xFFFu);
+                if (lane < lw.nw)
+                    qbits[ID[j] * kBitWordsLong + lane] = w.word ^ (lane == (i >> 5) ? 1u << (i & 31) : 0u);
+            }
+            if (nins > 0) {  // the round's first entry has the lowest ISL entered so far
+                const uint64_t ck = IK[0];
+                const int i = (int)(ck & 0xFFFu), isl_f = (int)(ck >> 34);
+                if (isl_f < w.best_isl) {
+                    w.best_isl = isl_f;
+                    w.best_step = (int64_t)e + 1;
+                    if (lane < lw.nw) lw.best[lane] = w.word ^ (lane == (i >> 5) ? 1u << (i & 31) : 0u);
+                }
+                if (w.target_step < 0 && isl_f <= tisl) w.target_step = (int64_t)e + 1;
+            }
+            if (!(m0 & 256)) break;
+            floor = meta[1];
+            t.sync();  // this round's lists are read before the next round writes them
         }
         // S <- the queue's first entry not in HT (entries that are get dropped)
         int code = LABS_TRACE_BLOCKED;

@@ -177,9 +177,12 @@ def test_long_layouts(layouts):
     for n_max in range(257, 4097):
         S = long_[n_max]
         nt, R = S["nt"], S["R"]
-        # scratch (nt words), bits (128 words), then the best-first queue's 32 keys, 8-byte aligned
-        assert nt * R >= n_max and S["words"] >= S["xoff"] + nt + 128 + 2 * 32
-        assert (S["xoff"] + nt + 128) % 2 == 0
+        # scratch (nt words), bits (128 words), then the best-first search's 32 queue keys,
+        # nt / 32 warps x 32 candidate keys, 32 entered keys (all 64-bit, so 8-byte aligned),
+        # two words of round state and 32 places
+        q = S["xoff"] + nt + 128
+        assert nt * R >= n_max and S["words"] >= q + 2 * 32 + 2 * nt + 2 * 32 + 4 + 32
+        assert q % 2 == 0
         assert S["words"] * 4 <= (227 * 1024 if nt == 512 else 113 * 1024)  # one / two CTAs per SM
         for n in sorted({257, (257 + n_max) // 2, n_max}):
             reg = Region(S)
