@@ -502,7 +502,7 @@ def run_scaleup(args):
 
 
 def run_long(args):
-    """Long sequences (one walker per CTA): L = 2047, 4095 and 8191, long_walkers
+    """Long sequences (one walker per CTA): L = 2047, 4095, 8191 and 11263, long_walkers
     walkers x long_steps steps each of the walk (ISL or PSL objective) or the best-first
     search: flips/s, the kernel's roofline fraction (one FMA per lag term, as the warp
     kernels), best F; one JSON line."""
@@ -519,7 +519,7 @@ def run_long(args):
     out = {}
     objective = "psl" if args.search == "psl" else "isl"
     flags = _native.LABS_FLAG_BEST_FIRST if args.search == "bestfirst" else 0
-    for L in (2047, 4095, 8191):
+    for L in (2047, 4095, 8191, 11263):
         n = (L + 1) // 2
         s = labs.Search(L, args.long_walkers, 42, device=dev, objective=objective, flags=flags)
         s.walk(8)  # warm-up: graph capture, first touch of the tables
@@ -550,7 +550,7 @@ def run_long(args):
     line = {"metric": "exact flip evaluations/sec, long sequences" + what,
             "value": total, "unit": "flip evaluations/s",
             "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic", "vs_baseline": None,
-            "config": {"workload": "L=2047, 4095 and 8191, %d walkers each (one per CTA of 256 or 512 threads), %d steps, "
+            "config": {"workload": "L=2047, 4095, 8191 and 11263, %d walkers each (one per CTA of 256 or 512 threads), %d steps, "
                                    "seed 42, uniform random +-1 Philox starts, HT 2^16 slots/walker"
                                    % (args.long_walkers, args.long_steps),
                        "kernel": "long_walk_kernel",

@@ -54,7 +54,7 @@ extern "C" {
                                 labs_walk); random starts and walks stay far below it */
 
 #define LABS_MAX_L 511       /* n = (L+1)/2 <= 256 free variables */
-#define LABS_MAX_L_LONG 8191 /* long sequences: n <= 4096 free variables */
+#define LABS_MAX_L_LONG 11263 /* long sequences: n <= 5632 free variables */
 #define LABS_MAX_GROUPS 64   /* distinct lengths in one context */
 
 /* Step trace codes written by labs_trace (one int32 per walker step).  The walk writes
@@ -101,7 +101,7 @@ typedef struct labs_config {
                                        LABS_FLAG_LEARNED */
 #define LABS_QUEUE_SIZE 32           /* entries of a walker's best-first queue */
 #define LABS_BEST_FIRST_MAX_STEPS (1ll << 28) /* steps per walker the queue order can number */
-#define LABS_BEST_FIRST_MAX_STEPS_LONG (1ll << 22) /* the same for lengths above LABS_MAX_L */
+#define LABS_BEST_FIRST_MAX_STEPS_LONG (1ll << 21) /* the same for lengths above LABS_MAX_L */
 
 /* Counters of a context, summed over its walkers (labs_stats). */
 typedef struct labs_counters {
@@ -215,8 +215,9 @@ int labs_neighbor_delta(labs_ctx *ctx, const int8_t *dev_seqs, int64_t batch,
  *   walk.  The trace's ISL log still holds ISL.
  * Long sequences (L > LABS_MAX_L) take the same steps with the neighbourhood in exact
  *   fp32 arithmetic, which holds while ISL < ((2^24 - 8L - 32n - 32) / 16)^2 / (n - 1)
- *   (capped at 2^29; 2.6e8 at L = 8191, far above random starts, whose ISL is near
- *   L^2/2): a walker whose ISL exceeds it stops and labs_sync reports LABS_ERANGE.
+ *   (capped at 2^29; 2.6e8 at L = 8191 and 1.9e8 at L = 11263, above random starts,
+ *   whose ISL is near L^2/2, by a factor of 8 and 3): a walker whose ISL exceeds it
+ *   stops and labs_sync reports LABS_ERANGE.
  * The trajectory of a walker depends only on (seed, walker id, L, cfg), never on
  * chunking, launch shape or the other walkers. */
 int labs_walk(labs_ctx *ctx, int64_t steps);

@@ -20,7 +20,7 @@ LABS_ECANCELLED = -5
 LABS_ESTATE = -6
 LABS_ERANGE = -7
 LABS_MAX_L = 511
-LABS_MAX_L_LONG = 8191
+LABS_MAX_L_LONG = 11263
 LABS_MAX_GROUPS = 64
 LABS_TRACE_RESTART = 0x10000
 LABS_TRACE_BLOCKED = -1
@@ -34,7 +34,7 @@ LABS_FLAG_PSL = 64
 LABS_FLAG_SECOND_HASH = 128
 LABS_QUEUE_SIZE = 32
 LABS_BEST_FIRST_MAX_STEPS = 1 << 28
-LABS_BEST_FIRST_MAX_STEPS_LONG = 1 << 22
+LABS_BEST_FIRST_MAX_STEPS_LONG = 1 << 21
 LOG_RECORD_BYTES = 64
 
 ERRORS = {LABS_EINVAL: "EINVAL", LABS_ENOMEM: "ENOMEM", LABS_ECUDA: "ECUDA", LABS_ETIMEOUT: "ETIMEOUT",

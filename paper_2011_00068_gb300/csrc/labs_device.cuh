@@ -1645,15 +1645,15 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
 // learned mode, 2 the best-first search (one variant per kernel keeps the code small).
 // ------------------------------------------------------------ PSL objective walk
 
-// Order key of a flip under the PSL objective: PSL' << 42 | ISL' << 12 | i (PSL' < 2^13,
-// ISL' < 2^30, i < 2^12 for every length served).
+// Order key of a flip under the PSL objective: PSL' << 43 | ISL' << 13 | i (PSL' < 2^21,
+// ISL' < 2^30, i < 2^13 for every length served).
 __device__ __forceinline__ uint64_t psl_key(int psl, int isl, int i)
 {
-    return ((uint64_t)psl << 42) | ((uint64_t)(uint32_t)isl << 12) | (uint64_t)i;
+    return ((uint64_t)psl << 43) | ((uint64_t)(uint32_t)isl << 13) | (uint64_t)i;
 }
-__device__ __forceinline__ int psl_key_i(uint64_t k) { return (int)(k & 0xFFFu); }
-__device__ __forceinline__ int psl_key_isl(uint64_t k) { return (int)((k >> 12) & 0x3FFFFFFFull); }
-__device__ __forceinline__ int psl_key_psl(uint64_t k) { return (int)(k >> 42); }
+__device__ __forceinline__ int psl_key_i(uint64_t k) { return (int)(k & 0x1FFFu); }
+__device__ __forceinline__ int psl_key_isl(uint64_t k) { return (int)((k >> 13) & 0x3FFFFFFFull); }
+__device__ __forceinline__ int psl_key_psl(uint64_t k) { return (int)(k >> 43); }
 
 // The same PSL values for wide lane blocks (R >= 7), where the three rings of psl_eval
 // would not fit the registers: s_{i-2m} and s_{i+2m} of the R outputs in two windows of

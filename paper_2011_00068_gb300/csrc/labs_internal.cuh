@@ -14,8 +14,8 @@ constexpr int kMaxN = (LABS_MAX_L + 1) / 2;  // 256 free variables
 constexpr int kBitWords = kMaxN / 32;        // 8 words of free-variable bits
 // Long sequences (LABS_MAX_L < L <= LABS_MAX_L_LONG) run one walker per CTA of
 // kLongThreads threads; their free-variable bits live beside the walker states.
-constexpr int kMaxNLong = (LABS_MAX_L_LONG + 1) / 2;  // 4096 free variables
-constexpr int kBitWordsLong = kMaxNLong / 32;          // 128 words
+constexpr int kMaxNLong = (LABS_MAX_L_LONG + 1) / 2;  // 5632 free variables
+constexpr int kBitWordsLong = kMaxNLong / 32;          // 176 words
 constexpr int kLongThreads = 512;       // threads of a long walker's CTA, n > kLongSmallMaxN
 constexpr int kLongThreadsSmall = 256;  // ... for n <= kLongSmallMaxN (two CTAs per SM)
 constexpr int kLongSmallMaxN = 2304;    // lane block <= 9 with 256 threads

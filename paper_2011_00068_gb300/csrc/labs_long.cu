@@ -414,7 +414,7 @@ __device__ void long_walk_psl(const LongWalk& lw, Walker& w, PslTrack& ps, int64
 }
 
 // Best-first search for a long walker (the rules of walk_bestfirst, Algorithm 1 as
-// printed): the queue's 32 keys ISL << 34 | (steps before the producing step) << 12 | i
+// printed): the queue's 32 keys ISL << 34 | (steps before the producing step) << 13 | i
 // (ISL < 2^30 under the exact-range bound, at most LABS_BEST_FIRST_MAX_STEPS_LONG steps)
 // sit in shared memory, where every thread reads them, so every decision below is taken
 // identically by the whole CTA; the entries' bits (kBitWordsLong words each) are in
@@ -486,7 +486,7 @@ __device__ void long_walk_bestfirst(const LongWalk& lw, Walker& w, int64_t until
         for (int r = 0; r < R; ++r) {
             key[r] = kLongEmpty;
             if (dl[r] != INT_MAX) {
-                const uint64_t ck = ((uint64_t)(uint32_t)(w.isl + dl[r]) << 34) | (e << 12) |
+                const uint64_t ck = ((uint64_t)(uint32_t)(w.isl + dl[r]) << 34) | (e << 13) |
                                     (uint64_t)(2 * (o.v0 + r) + o.p);
                 if (ck < last0) key[r] = ck;
             }
@@ -532,7 +532,7 @@ __device__ void long_walk_bestfirst(const LongWalk& lw, Walker& w, int64_t until
                 }
                 bool vis = false;
                 if (lane < cnt) {
-                    const uint64_t f = w.fp ^ __ldg(env.zk + (int)(mine & 0xFFFu));
+                    const uint64_t f = w.fp ^ __ldg(env.zk + (int)(mine & 0x1FFFu));
                     const uint64_t tag = (f & ~kGenMask) | w.gen;
                     for (int s = 0; s < p.probe_cap; ++s) {
                         const uint64_t x = env.T[(f + (uint64_t)s) & env.tmask];
@@ -579,13 +579,13 @@ __device__ void long_walk_bestfirst(const LongWalk& lw, Walker& w, int64_t until
             t.sync();
             const int m0 = (int)meta[0], nins = m0 & 0xFF;
             for (int j = 0; j < nins; ++j) {
-                const int i = (int)(IK[j] & 0xFFFu);
+                const int i = (int)(IK[j] & 0x1FFFu);
                 if (lane < lw.nw)
                     qbits[ID[j] * kBitWordsLong + lane] = w.word ^ (lane == (i >> 5) ? 1u << (i & 31) : 0u);
             }
             if (nins > 0) {  // the round's first entry has the lowest ISL entered so far
                 const uint64_t ck = IK[0];
-                const int i = (int)(ck & 0xFFFu), isl_f = (int)(ck >> 34);
+                const int i = (int)(ck & 0x1FFFu), isl_f = (int)(ck >> 34);
                 if (isl_f < w.best_isl) {
                     w.best_isl = isl_f;
                     w.best_step = (int64_t)e + 1;
@@ -612,8 +612,8 @@ __device__ void long_walk_bestfirst(const LongWalk& lw, Walker& w, int64_t until
             if (lane == 0) Q[src] = kLongEmpty;
             if (lane < lw.nw) lw.bits[lane] = word;
             t.sync();
-            const int i = (int)(first & 0xFFFu);
-            const bool nb = ((first >> 12) & 0x3FFFFFull) == e;  // a neighbour of S
+            const int i = (int)(first & 0x1FFFu);
+            const bool nb = ((first >> 13) & 0x1FFFFFull) == e;  // a neighbour of S
             const uint64_t f = nb ? (w.fp ^ __ldg(env.zk + i)) : long_fingerprint(lw, t);
             const Probe pr = long_probe(lw, f, w.gen, t);
             if (pr.visited) continue;
@@ -862,15 +862,25 @@ __global__ void __launch_bounds__(NT, kLongThreads / NT) long_delta_kernel(const
 using LongFn = void (*)(KParams, int);
 using LongDeltaFn = void (*)(const int8_t*, int64_t, int, int32_t*, DevStatus*);
 
+// Lane blocks in use: 3..9 with 256 threads (257 <= n <= 2304), 5..11 with 512
+// (2304 < n <= 5632).
 template <int NT, int MODE>
 LongFn long_fn_nt(int R)
 {
-    switch (R) {
-        case 1: return long_walk_kernel<NT, 1, MODE>;
-        case 3: return long_walk_kernel<NT, 3, MODE>;
-        case 5: return long_walk_kernel<NT, 5, MODE>;
-        case 7: return long_walk_kernel<NT, 7, MODE>;
-        default: return long_walk_kernel<NT, 9, MODE>;
+    if constexpr (NT == kLongThreadsSmall) {
+        switch (R) {
+            case 3: return long_walk_kernel<NT, 3, MODE>;
+            case 5: return long_walk_kernel<NT, 5, MODE>;
+            case 7: return long_walk_kernel<NT, 7, MODE>;
+            default: return long_walk_kernel<NT, 9, MODE>;
+        }
+    } else {
+        switch (R) {
+            case 5: return long_walk_kernel<NT, 5, MODE>;
+            case 7: return long_walk_kernel<NT, 7, MODE>;
+            case 9: return long_walk_kernel<NT, 9, MODE>;
+            default: return long_walk_kernel<NT, 11, MODE>;
+        }
     }
 }
 
@@ -883,12 +893,20 @@ LongFn long_fn_mode(int NT, int R)
 template <int NT>
 LongDeltaFn long_delta_fn_nt(int R)
 {
-    switch (R) {
-        case 1: return long_delta_kernel<NT, 1>;
-        case 3: return long_delta_kernel<NT, 3>;
-        case 5: return long_delta_kernel<NT, 5>;
-        case 7: return long_delta_kernel<NT, 7>;
-        default: return long_delta_kernel<NT, 9>;
+    if constexpr (NT == kLongThreadsSmall) {
+        switch (R) {
+            case 3: return long_delta_kernel<NT, 3>;
+            case 5: return long_delta_kernel<NT, 5>;
+            case 7: return long_delta_kernel<NT, 7>;
+            default: return long_delta_kernel<NT, 9>;
+        }
+    } else {
+        switch (R) {
+            case 5: return long_delta_kernel<NT, 5>;
+            case 7: return long_delta_kernel<NT, 7>;
+            case 9: return long_delta_kernel<NT, 9>;
+            default: return long_delta_kernel<NT, 11>;
+        }
     }
 }
 

@@ -32,6 +32,7 @@ def traced(L, walkers, steps, seed, **cfg):
     (2047, 3, 120, {}),
     (4095, 2, 60, {}),
     (8191, 2, 16, {}),
+    (11263, 1, 4, {}),
 ])
 def test_long_trajectory_parity(L, walkers, steps, kw):
     seed = 6
@@ -95,7 +96,7 @@ def exact_limit(L):
     return int(min(room * room / (n - 1), 2 ** 29)) - 1
 
 
-@pytest.mark.parametrize("L", [513, 1025, 4095, 8191])
+@pytest.mark.parametrize("L", [513, 1025, 4095, 8191, 11263])
 def test_long_rows(L):
     n = (L + 1) // 2
     xs = labs_inputs.random_free_vars(5, L, seed=L)
@@ -151,7 +152,7 @@ def test_long_refusals():
     with pytest.raises(labs.LabsError):
         labs.Search([201, 1025], [2, 2], 1)  # short and long lengths in one context
     with pytest.raises(labs.LabsError):
-        labs.Search(8193, 2, 1)
+        labs.Search(_native.LABS_MAX_L_LONG + 2, 2, 1)
     BF = _native.LABS_FLAG_BEST_FIRST
     for f in (_native.LABS_FLAG_LEARNED, BF | _native.LABS_FLAG_SECOND_HASH):
         with pytest.raises(labs.LabsError):
@@ -173,8 +174,9 @@ def test_long_walker_outside_exact_range_stops_with_erange():
     """A walker put (through a checkpoint) on a state whose ISL is above the exact-range
     bound stops before evaluating it and labs_sync reports LABS_ERANGE; the other walker
     is unaffected.  Checkpoint layout: 64-byte header, then the walker states (160 bytes
-    each, ISL at byte 96), then the rows of current and best bits (128 words per walker,
-    each array 256-byte aligned)."""
+    each, ISL at byte 96), then the rows of current and best bits (176 words per walker,
+    each array 256-byte aligned; n = 2048 here, so walker 0's bits are the row's first
+    64 words)."""
     import struct
 
     L, W, seed = 4095, 2, 5
@@ -182,7 +184,7 @@ def test_long_walker_outside_exact_range_stops_with_erange():
     buf = s.checkpoint(with_tabu=False)
     hdr, state_bytes = 64, 160
     cur = hdr + ((W * state_bytes + 255) // 256) * 256
-    buf[cur:cur + 512] = bytes(512)                       # walker 0: every free variable +1
+    buf[cur:cur + 256] = bytes(256)                       # walker 0: every free variable +1
     struct.pack_into("<i", buf, hdr + 96, 2 ** 31 - 1)    # its ISL as the kernel finds it (saturated)
     assert oracle.isl(oracle.skew_expand(np.ones((L + 1) // 2, np.int8), L)) > 2 ** 31 - 1
     s.restore(buf)
@@ -245,10 +247,11 @@ def test_long_psl_chunking_and_mixed_lengths():
     (1025, 2, 40, {}),
     (2049, 1, 20, {}),
     (4801, 1, 6, {}),
+    (11263, 1, 3, {}),
 ])
 def test_long_bestfirst_parity(L, walkers, steps, kw):
     """The best-first search (Algorithm 1 as printed) for long sequences, one walker per
-    CTA of 256 threads (512 at L = 4801), against the oracle: per-step trace codes and
+    CTA of 256 threads (512 at L = 4801 and 11263), against the oracle: per-step trace codes and
     ISLs, best and final sequences, counters."""
     seed = 3
     s, code, isl = traced(L, walkers, steps, seed, flags=_native.LABS_FLAG_BEST_FIRST, **kw)
@@ -284,4 +287,39 @@ def test_long_bestfirst_chunking_and_mixed_lengths():
         assert np.array_equal(code[first:first + cnt], o["trace_code"]), Lg
         assert np.array_equal(isl[first:first + cnt], o["trace_isl"]), Lg
         first += cnt
+    s.close()
+
+
+@pytest.mark.parametrize("mode", ["walk", "psl", "bestfirst"])
+def test_long_lane_block_11_on_short_walkers(mode):
+    """The kernels of lane block 11 (compiled for 5120 < n <= 5632) run every walker of a
+    context whose longest length is 11263, so the L = 601 walkers of such a context
+    exercise them at lengths where the oracle is fast (under the PSL objective it
+    rebuilds every neighbour in O(L^2)): their traces against the oracle, and the
+    L = 11263 walker's final and best values against the oracle's Eq. 2 and PSL of its
+    sequences."""
+    Ls, counts, seed, steps = [601, 11263], [2, 1], 12, 16
+    cfg = {"objective": "psl"} if mode == "psl" else {}
+    if mode == "bestfirst":
+        cfg["flags"] = _native.LABS_FLAG_BEST_FIRST
+    s = labs.Search(Ls, counts, seed, **cfg)
+    assert s.stats()["lane_block"] == 11
+    code, isl = s.trace([0, 1], steps)
+    s.walk(steps)
+    s.sync()
+    code, isl = code.cpu().numpy(), isl.cpu().numpy()
+    if mode == "bestfirst":
+        o = oracle.bestfirst(601, seed, 2, steps, pq_size=_native.LABS_QUEUE_SIZE, trace=True)
+    else:
+        o = oracle.walk(601, seed, 2, steps, trace=True, objective="psl" if mode == "psl" else "isl")
+    assert np.array_equal(code, o["trace_code"]) and np.array_equal(isl, o["trace_isl"])
+    r = s.results(0, 2, seqs=True)
+    assert np.array_equal(r["seq"], o["final_seq"]) and np.array_equal(r["best_isl"], o["best_isl"])
+    r = s.results(2, 1, seqs=True)
+    assert r["isl"][0] == oracle.isl(r["seq"][0]) and r["best_isl"][0] == oracle.isl(r["best_seq"][0])
+    if mode == "psl":
+        assert r["psl"][0] == oracle.psl(r["seq"][0]) and r["best_psl"][0] == oracle.psl(r["best_seq"][0])
+        assert (r["best_psl"][0], r["best_isl"][0]) <= (r["psl"][0], r["isl"][0])
+    else:
+        assert r["best_isl"][0] <= r["isl"][0]
     s.close()

@@ -217,7 +217,7 @@ def test_bad_arguments_raise():
     with pytest.raises(labs.LabsError):
         labs.Search(200, 4, 1)
     with pytest.raises(labs.LabsError):
-        labs.Search(8193, 4, 1)
+        labs.Search(_native.LABS_MAX_L_LONG + 2, 4, 1)
     with pytest.raises(labs.LabsError):
         labs.Search(41, 4, 1, tabu_log2=21)
     with pytest.raises(labs.LabsError):
