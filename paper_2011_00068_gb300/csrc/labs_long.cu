@@ -1,7 +1,8 @@
-// labs_long.cu -- the walk for long sequences (LABS_MAX_L < L <= LABS_MAX_L_LONG): one
-// CTA of 256 or 512 threads runs one walker (long_threads).  The step is the walk's (Algorithm 1 in
-// its self-avoiding form): all n flips evaluated by the Toeplitz form of dISL, the
-// lowest (dISL, i) whose result is not in HT taken, C_k and P updated in O(n) per move.
+// labs_long.cu -- long sequences (LABS_MAX_L < L <= LABS_MAX_L_LONG): one CTA of 256 or
+// 512 threads runs one walker (long_threads).  The walk's step (Algorithm 1 in its
+// self-avoiding form): all n flips evaluated by the Toeplitz form of dISL, the lowest
+// (dISL, i) whose result is not in HT taken, C_k and P updated in O(n) per move; the same
+// under the PSL objective, and the best-first search (Algorithm 1 as printed).
 // The per-lane arithmetic is the warp kernels' (labs_device.cuh), run by a lane group
 // that spans the CTA; the collectives go through shared memory.
 #include "labs_device.cuh"
@@ -416,10 +417,12 @@ __device__ void long_walk_psl(const LongWalk& lw, Walker& w, PslTrack& ps, int64
 // Best-first search for a long walker (the rules of walk_bestfirst, Algorithm 1 as
 // printed): the queue's 32 keys ISL << 34 | (steps before the producing step) << 13 | i
 // (ISL < 2^30 under the exact-range bound, at most LABS_BEST_FIRST_MAX_STEPS_LONG steps)
-// sit in shared memory, where every thread reads them, so every decision below is taken
-// identically by the whole CTA; the entries' bits (kBitWordsLong words each) are in
-// global memory.  An entry that differs from S in at most kBestFirstMaxFlips free
-// variables is reached by that many incremental flips, any other by a rebuild.
+// sit in shared memory: the first warp updates them during the insertion, and every
+// thread reads them when S moves, so each decision is taken identically by the whole
+// CTA; the entries' bits (kBitWordsLong words each) are in global memory, each word
+// written and read by the same thread.  An entry that differs from S in at most
+// kBestFirstMaxFlips free variables is reached by that many incremental flips, any other
+// by a rebuild.
 constexpr uint64_t kLongEmpty = ~0ull;
 
 __device__ __forceinline__ int long_queue_min(const uint64_t* Q, uint64_t& v)
@@ -733,7 +736,9 @@ __global__ void __launch_bounds__(NT, kLongThreads / NT) long_reset_kernel(KPara
     }
 }
 
-// One chunk of steps for every long walker; walkers are taken from a counter.
+// One chunk of steps for every long walker; walkers are taken from a counter.  MODE: 0
+// the walk, 1 the walk under the PSL objective, 2 the best-first search (its queue keys
+// are copied into shared memory for the chunk and back at its end).
 template <int NT, int R, int MODE>
 __global__ void __launch_bounds__(NT, kLongThreads / NT) long_walk_kernel(KParams p, int chunk_index)
 {
