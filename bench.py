@@ -550,7 +550,7 @@ def run_long(args):
     line = {"metric": "exact flip evaluations/sec, long sequences" + what,
             "value": total, "unit": "flip evaluations/s",
             "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic", "vs_baseline": None,
-            "config": {"workload": "L=2047, 4095, 8191 and 11263, %d walkers each (one per CTA of 256 or 512 threads), %d steps, "
+            "config": {"workload": "L=2047, 4095, 8191 and 11263, %d walkers each (one per CTA of 128, 256 or 512 threads), %d steps, "
                                    "seed 42, uniform random +-1 Philox starts, HT 2^16 slots/walker"
                                    % (args.long_walkers, args.long_steps),
                        "kernel": "long_walk_kernel",

@@ -26,10 +26,10 @@
  *     detected on the device are reported by the next synchronising call
  *     (labs_sync, labs_best, labs_walker_results, labs_stats, labs_checkpoint).
  *   - Lengths: odd L with 3 <= L <= LABS_MAX_L (walkers run one, two or four per warp),
- *     or LABS_MAX_L < L <= LABS_MAX_L_LONG (long sequences: one walker per CTA of 256
- *     or 512 threads, the same step rules: the walk under the ISL or the PSL objective,
- *     or the best-first search without the second table); a context holds lengths of one
- *     kind only.
+ *     or LABS_MAX_L < L <= LABS_MAX_L_LONG (long sequences: one walker per CTA of 128,
+ *     256 or 512 threads, the same step rules: the walk under the ISL or the PSL
+ *     objective, or the best-first search without the second table); a context holds
+ *     lengths of one kind only.
  *   - A context is not thread-safe; use one per host thread.
  */
 #ifndef LABS_H

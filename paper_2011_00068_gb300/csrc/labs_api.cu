@@ -302,7 +302,7 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     // mode runs one walker per warp)
     if (c->long_mode) {
         // one walker per CTA of 256 or 512 threads
-        c->tile = long_threads(c->n_max);
+        c->tile = long_threads(c->n_max, (k.flags & LABS_FLAG_PSL) != 0);
         c->smem_bytes = (size_t)long_smem(c->n_max, c->tile).words * sizeof(int);
         int occ = 0;
         const int mode = (k.flags & LABS_FLAG_PSL) ? 1 : (k.flags & LABS_FLAG_BEST_FIRST) ? 2 : 0;

@@ -16,9 +16,11 @@ constexpr int kBitWords = kMaxN / 32;        // 8 words of free-variable bits
 // kLongThreads threads; their free-variable bits live beside the walker states.
 constexpr int kMaxNLong = (LABS_MAX_L_LONG + 1) / 2;  // 5632 free variables
 constexpr int kBitWordsLong = kMaxNLong / 32;          // 176 words
-constexpr int kLongThreads = 512;       // threads of a long walker's CTA, n > kLongSmallMaxN
-constexpr int kLongThreadsSmall = 256;  // ... for n <= kLongSmallMaxN (two CTAs per SM)
-constexpr int kLongSmallMaxN = 2304;    // lane block <= 9 with 256 threads
+constexpr int kLongThreads = 512;       // threads of a long walker's CTA, n > kLongMidMaxN
+constexpr int kLongThreadsMid = 256;    // ... for kLongSmallMaxN < n <= kLongMidMaxN (two CTAs per SM)
+constexpr int kLongThreadsSmall = 128;  // ... for n <= kLongSmallMaxN (four CTAs per SM)
+constexpr int kLongSmallMaxN = 1152;    // lane block <= 9 with 128 threads
+constexpr int kLongMidMaxN = 2304;      // lane block <= 9 with 256 threads
 constexpr int kQuadMaxR = 10;                // largest lane block of four walkers per warp (n <= 80)
 constexpr int kMaxChunksPerCall = 4096;      // chunk launches per labs_walk call
 constexpr int kMaxTrace = 4096;              // traced walkers
@@ -236,10 +238,14 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
     return w;
 }
 
-// Threads of a long walker's CTA for n_max free variables.
-__host__ __device__ inline int long_threads(int n_max)
+// Threads of a long walker's CTA for n_max free variables: 128 (four walkers per SM) up
+// to n = 1152, 256 (two) up to 2304, else 512.  The walk under the PSL objective keeps
+// 256 threads below n = 1152, where its lane block stays at most 5 and psl_eval uses
+// its ring form (faster there than lane block 9 with 128 threads).
+__host__ __device__ inline int long_threads(int n_max, bool psl = false)
 {
-    return n_max <= kLongSmallMaxN ? kLongThreadsSmall : kLongThreads;
+    if (n_max <= kLongSmallMaxN && !psl) return kLongThreadsSmall;
+    return n_max <= kLongMidMaxN ? kLongThreadsMid : kLongThreads;
 }
 
 // Lane block of the long layout: ceil(ceil(n/2) / (threads/2)) raised to odd, so that the

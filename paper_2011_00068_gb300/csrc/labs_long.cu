@@ -867,12 +867,12 @@ __global__ void __launch_bounds__(NT, kLongThreads / NT) long_delta_kernel(const
 using LongFn = void (*)(KParams, int);
 using LongDeltaFn = void (*)(const int8_t*, int64_t, int, int32_t*, DevStatus*);
 
-// Lane blocks in use: 3..9 with 256 threads (257 <= n <= 2304), 5..11 with 512
-// (2304 < n <= 5632).
+// Lane blocks in use (long_R): 3..9 with 128 or 256 threads (257 <= n <= 2304), 5..11
+// with 512 (2304 < n <= 5632).
 template <int NT, int MODE>
 LongFn long_fn_nt(int R)
 {
-    if constexpr (NT == kLongThreadsSmall) {
+    if constexpr (NT != kLongThreads) {
         switch (R) {
             case 3: return long_walk_kernel<NT, 3, MODE>;
             case 5: return long_walk_kernel<NT, 5, MODE>;
@@ -892,13 +892,15 @@ LongFn long_fn_nt(int R)
 template <int MODE>
 LongFn long_fn_mode(int NT, int R)
 {
-    return NT == kLongThreadsSmall ? long_fn_nt<kLongThreadsSmall, MODE>(R) : long_fn_nt<kLongThreads, MODE>(R);
+    return NT == kLongThreadsSmall ? long_fn_nt<kLongThreadsSmall, MODE>(R)
+           : NT == kLongThreadsMid ? long_fn_nt<kLongThreadsMid, MODE>(R)
+                                   : long_fn_nt<kLongThreads, MODE>(R);
 }
 
 template <int NT>
 LongDeltaFn long_delta_fn_nt(int R)
 {
-    if constexpr (NT == kLongThreadsSmall) {
+    if constexpr (NT != kLongThreads) {
         switch (R) {
             case 3: return long_delta_kernel<NT, 3>;
             case 5: return long_delta_kernel<NT, 5>;
@@ -919,21 +921,25 @@ LongDeltaFn long_delta_fn_nt(int R)
 // mode 0 the walk, 1 the walk under the PSL objective, 2 the best-first search
 LongFn long_fn(int n_max, int mode)
 {
-    const int NT = long_threads(n_max), R = long_R(n_max, NT);
+    const int NT = long_threads(n_max, mode == 1), R = long_R(n_max, NT);
     return mode == 1 ? long_fn_mode<1>(NT, R) : mode == 2 ? long_fn_mode<2>(NT, R) : long_fn_mode<0>(NT, R);
 }
 
 LongDeltaFn long_delta_fn(int n)
 {
     const int NT = long_threads(n), R = long_R(n, NT);
-    return NT == kLongThreadsSmall ? long_delta_fn_nt<kLongThreadsSmall>(R) : long_delta_fn_nt<kLongThreads>(R);
+    return NT == kLongThreadsSmall ? long_delta_fn_nt<kLongThreadsSmall>(R)
+           : NT == kLongThreadsMid ? long_delta_fn_nt<kLongThreadsMid>(R)
+                                   : long_delta_fn_nt<kLongThreads>(R);
 }
 
 using ResetFn = void (*)(KParams);
-ResetFn long_reset_fn(int n_max)
+ResetFn long_reset_fn(int n_max, bool psl)
 {
-    return long_threads(n_max) == kLongThreadsSmall ? long_reset_kernel<kLongThreadsSmall>
-                                                    : long_reset_kernel<kLongThreads>;
+    const int NT = long_threads(n_max, psl);
+    return NT == kLongThreadsSmall ? long_reset_kernel<kLongThreadsSmall>
+           : NT == kLongThreadsMid ? long_reset_kernel<kLongThreadsMid>
+                                   : long_reset_kernel<kLongThreads>;
 }
 
 }  // namespace
@@ -943,13 +949,14 @@ int long_kernel_config(int n_max, int mode, size_t smem_bytes, int* ctas_per_sm,
     const LongFn fn = long_fn(n_max, mode);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return LABS_ECUDA;
-    e = cudaFuncSetAttribute(long_reset_fn(n_max), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    e = cudaFuncSetAttribute(long_reset_fn(n_max, mode == 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes);
     if (e != cudaSuccess) return LABS_ECUDA;
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return LABS_ECUDA;
     if (regs) *regs = fa.numRegs;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, long_threads(n_max), smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, long_threads(n_max, mode == 1), smem_bytes);
     return e == cudaSuccess ? LABS_OK : LABS_ECUDA;
 }
 
@@ -959,14 +966,16 @@ int launch_long_reset(const KParams& p, size_t smem_bytes, void* stream)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t grid = p.W < sms ? (p.W > 0 ? p.W : 1) : sms;
-    long_reset_fn(p.n_max)<<<(int)grid, long_threads(p.n_max), smem_bytes, (cudaStream_t)stream>>>(p);
+    const bool psl = p.mode == 3;
+    long_reset_fn(p.n_max, psl)<<<(int)grid, long_threads(p.n_max, psl), smem_bytes, (cudaStream_t)stream>>>(p);
     return cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ECUDA;
 }
 
 int launch_long_walk_chunk(const KParams& p, int chunk_index, int grid, size_t smem_bytes, void* stream)
 {
     const int mode = p.mode == 3 ? 1 : p.mode == 2 ? 2 : 0;
-    long_fn(p.n_max, mode)<<<grid, long_threads(p.n_max), smem_bytes, (cudaStream_t)stream>>>(p, chunk_index);
+    long_fn(p.n_max, mode)<<<grid, long_threads(p.n_max, mode == 1), smem_bytes, (cudaStream_t)stream>>>(p,
+                                                                                                    chunk_index);
     return cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ECUDA;
 }
 

@@ -17,11 +17,13 @@ int main()
             std::printf("warp %d %d %d %d %d %d %d %d %d %d\n", tiles[ti], n, w.apad, w.alen, w.gpad, w.glen, w.bvec,
                         w.xoff, w.words, block_R(n, tiles[ti]));
         }
-    for (int n = kMaxN + 1; n <= kMaxNLong; ++n) {
-        const int nt = long_threads(n);
-        const WarpSmem w = long_smem(n, nt);
-        std::printf("long %d %d %d %d %d %d %d %d %d %d %d\n", nt, n, w.apad, w.alen, w.gpad, w.glen, w.bvec, w.xoff,
-                    w.words, long_R(n, nt), long_isl_limit(2 * n - 1, n));
-    }
+    for (int n = kMaxN + 1; n <= kMaxNLong; ++n)
+        for (int psl = 0; psl < 2; ++psl) {  // the CTA width of the walk and of the PSL walk
+            const int nt = long_threads(n, psl != 0);
+            if (psl && nt == long_threads(n, false)) continue;
+            const WarpSmem w = long_smem(n, nt);
+            std::printf("long %d %d %d %d %d %d %d %d %d %d %d %d\n", nt, n, w.apad, w.alen, w.gpad, w.glen, w.bvec,
+                        w.xoff, w.words, long_R(n, nt), long_isl_limit(2 * n - 1, n), psl);
+        }
     return 0;
 }

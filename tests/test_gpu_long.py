@@ -246,13 +246,14 @@ def test_long_psl_chunking_and_mixed_lengths():
     (601, 2, 60, {"tabu_log2": 4, "probe_cap": 3}),
     (1025, 2, 40, {}),
     (2049, 1, 20, {}),
+    (3001, 1, 12, {}),
     (4801, 1, 6, {}),
     (11263, 1, 3, {}),
 ])
 def test_long_bestfirst_parity(L, walkers, steps, kw):
     """The best-first search (Algorithm 1 as printed) for long sequences, one walker per
-    CTA of 256 threads (512 at L = 4801 and 11263), against the oracle: per-step trace codes and
-    ISLs, best and final sequences, counters."""
+    CTA (128 threads up to L = 2303, 256 at L = 3001, 512 at 4801 and 11263), against the
+    oracle: per-step trace codes and ISLs, best and final sequences, counters."""
     seed = 3
     s, code, isl = traced(L, walkers, steps, seed, flags=_native.LABS_FLAG_BEST_FIRST, **kw)
     o = oracle.bestfirst(L, seed, walkers, steps, pq_size=_native.LABS_QUEUE_SIZE, trace=True, **kw)
@@ -291,19 +292,20 @@ def test_long_bestfirst_chunking_and_mixed_lengths():
 
 
 @pytest.mark.parametrize("mode", ["walk", "psl", "bestfirst"])
-def test_long_lane_block_11_on_short_walkers(mode):
-    """The kernels of lane block 11 (compiled for 5120 < n <= 5632) run every walker of a
-    context whose longest length is 11263, so the L = 601 walkers of such a context
-    exercise them at lengths where the oracle is fast (under the PSL objective it
-    rebuilds every neighbour in O(L^2)): their traces against the oracle, and the
-    L = 11263 walker's final and best values against the oracle's Eq. 2 and PSL of its
-    sequences."""
-    Ls, counts, seed, steps = [601, 11263], [2, 1], 12, 16
+@pytest.mark.parametrize("L_long,R", [(2311, 5), (11263, 11)])
+def test_long_kernels_on_short_walkers(mode, L_long, R):
+    """The kernels chosen for a context's longest length run all its walkers, so the
+    L = 601 walkers of a context whose longest length is 2311 (256-thread CTAs, lane
+    block 5) or 11263 (512 threads, lane block 11) exercise those kernels at a length
+    where the oracle is fast (under the PSL objective it rebuilds every neighbour in
+    O(L^2)): their traces against the oracle, and the long walker's final and best
+    values against the oracle's Eq. 2 and PSL of its sequences."""
+    Ls, counts, seed, steps = [601, L_long], [2, 1], 12, 16
     cfg = {"objective": "psl"} if mode == "psl" else {}
     if mode == "bestfirst":
         cfg["flags"] = _native.LABS_FLAG_BEST_FIRST
     s = labs.Search(Ls, counts, seed, **cfg)
-    assert s.stats()["lane_block"] == 11
+    assert s.stats()["lane_block"] == R
     code, isl = s.trace([0, 1], steps)
     s.walk(steps)
     s.sync()

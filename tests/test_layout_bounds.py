@@ -35,8 +35,8 @@ def layouts(tmp_path_factory):
             warp[(tile, n)] = dict(apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], R=v[9])
         else:
             nt, n = v[0], v[1]
-            long_[n] = dict(nt=nt, apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], xoff=v[7],
-                            words=v[8], R=v[9], limit=v[10])
+            long_[(nt, n)] = dict(nt=nt, apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], xoff=v[7],
+                                  words=v[8], R=v[9], limit=v[10], psl_only=v[11])
     return warp, long_
 
 
@@ -174,16 +174,19 @@ def test_warp_layouts(layouts):
 def test_long_layouts(layouts):
     _, long_ = layouts
     bad = []
-    for n_max in range(257, 5633):
-        S = long_[n_max]
-        nt, R = S["nt"], S["R"]
-        # scratch (nt words), bits (128 words), then the best-first search's 32 queue keys,
-        # nt / 32 warps x 32 candidate keys, 32 entered keys (all 64-bit, so 8-byte aligned),
-        # two words of round state and 32 places
-        q = S["xoff"] + nt + 128
+    # lane blocks compiled for each CTA width (the dispatch in labs_long.cu)
+    compiled = {128: {3, 5, 7, 9}, 256: {3, 5, 7, 9}, 512: {5, 7, 9, 11}}
+    assert {n for _, n in long_} == set(range(257, 5633))
+    for (nt, n_max), S in sorted(long_.items(), key=lambda kv: kv[0][1]):
+        R = S["R"]
+        assert R in compiled[nt], (nt, n_max, R)
+        # scratch (nt words), bits (kBitWordsLong = 176 words), then the best-first search's
+        # 32 queue keys, nt / 32 warps x 32 candidate keys, 32 entered keys (all 64-bit, so
+        # 8-byte aligned), two words of round state and 32 places
+        q = S["xoff"] + nt + 176
         assert nt * R >= n_max and S["words"] >= q + 2 * 32 + 2 * nt + 2 * 32 + 4 + 32
         assert q % 2 == 0
-        assert S["words"] * 4 <= (227 * 1024 if nt == 512 else 113 * 1024)  # one / two CTAs per SM
+        assert S["words"] * 4 <= {512: 227, 256: 113, 128: 56}[nt] * 1024  # one, two or four CTAs per SM
         for n in sorted({257, (257 + n_max) // 2, n_max}):
             reg = Region(S)
             common(reg, n, nt, R, valid_only=True)
@@ -217,9 +220,10 @@ def test_long_exact_range_bound(layouts):
     on sum |C_2m|), the condition for the long kernels' fp32 arithmetic to be exact, and
     stays above the ISL of random starts (about L^2/2) by a factor of at least 2."""
     _, long_ = layouts
+    limit = {n: S["limit"] for (_, n), S in long_.items()}
     for n in (257, 1024, 2048, 4096, 5632):
         L = 2 * n - 1
-        lim = long_[n]["limit"]
+        lim = limit[n]
         assert 16 * ((n - 1) * lim) ** 0.5 + 8 * L + 32 * n + 32 < 2 ** 24
         assert lim > L * L  # twice the mean ISL of random starts
         assert lim < 2 ** 29
