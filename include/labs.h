@@ -365,8 +365,10 @@ int labs_trace_learned(labs_ctx *ctx, int32_t capacity, float *dev_scores, int64
 /* Checkpoint of every walker's state (sequence, ISL, best, counters, random-stream
  * position) and, with with_tabu != 0, its HT.  With the HT included a restored run
  * continues bit-identically; without it the HT restarts empty.  host_buf NULL queries
- * the size; a checkpoint restores only into a context with the same LABS_FLAG_PSL.  Synchronising.  LABS_EINVAL for a context with LABS_FLAG_BEST_FIRST (its
- * queues are not part of the checkpoint). */
+ * the size; a checkpoint restores only into a context with the same walker count,
+ * lengths' kind (short or long; for long ones the same LABS_MAX_L_LONG), HT size,
+ * seed and LABS_FLAG_PSL (LABS_EINVAL otherwise).  Synchronising.  LABS_EINVAL for a
+ * context with LABS_FLAG_BEST_FIRST (its queues are not part of the checkpoint). */
 int labs_checkpoint(labs_ctx *ctx, int with_tabu, void *host_buf, size_t *bytes);
 int labs_restore(labs_ctx *ctx, const void *host_buf, size_t bytes);
 

@@ -968,6 +968,13 @@ int labs_enumerate(int32_t L, void* dev_scratch, size_t scratch_bytes, int64_t* 
     return LABS_OK;
 }
 
+// Header word 7 of a checkpoint: the objective, and for long sequences the long flag and
+// the words per bit row (the rows' stride in the checkpoint).
+static uint64_t ckpt_kind(const labs_ctx* c)
+{
+    return (uint64_t)(c->cfg.flags & LABS_FLAG_PSL) | (c->long_mode ? 0x100u | ((uint64_t)kBitWordsLong << 16) : 0u);
+}
+
 int labs_checkpoint(labs_ctx* c, int with_tabu, void* host_buf, size_t* bytes)
 {
     int rc = need_ws(c);
@@ -991,8 +998,7 @@ int labs_checkpoint(labs_ctx* c, int with_tabu, void* host_buf, size_t* bytes)
     rc = sync_status(c);
     if (rc) return rc;
     uint64_t h[8] = {kCkptMagic, (uint64_t)c->W, (uint64_t)c->nG, (uint64_t)c->cfg.tabu_log2,
-                     (uint64_t)(with_tabu ? 1 : 0), (uint64_t)c->planned, c->seed,
-                     (uint64_t)(c->cfg.flags & LABS_FLAG_PSL) | (c->long_mode ? 0x100u : 0u)};
+                     (uint64_t)(with_tabu ? 1 : 0), (uint64_t)c->planned, c->seed, ckpt_kind(c)};
     memcpy(host_buf, h, sizeof(h));
     char* dst = (char*)host_buf + hdr;
     cudaError_t e = cudaMemcpy(dst, c->ws + c->off_states, sbytes, cudaMemcpyDeviceToHost);
@@ -1011,7 +1017,7 @@ int labs_restore(labs_ctx* c, const void* host_buf, size_t bytes)
     uint64_t h[8];
     memcpy(h, host_buf, sizeof(h));
     if (h[0] != kCkptMagic || h[1] != (uint64_t)c->W || h[2] != (uint64_t)c->nG ||
-        h[3] != (uint64_t)c->cfg.tabu_log2 || h[6] != c->seed || h[7] != ((uint64_t)(c->cfg.flags & LABS_FLAG_PSL) | (c->long_mode ? 0x100u : 0u)))
+        h[3] != (uint64_t)c->cfg.tabu_log2 || h[6] != c->seed || h[7] != ckpt_kind(c))
         return fail(c, LABS_EINVAL, "checkpoint does not match this context");
     const size_t sbytes = c->long_mode ? c->off_best_bits + sizeof(uint32_t) * kBitWordsLong * (size_t)c->W -
                                              c->off_states
