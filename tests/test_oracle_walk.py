@@ -98,7 +98,7 @@ def test_stagnation_restart_interval():
 # ------------------------------------------------------ best-first search (Alg. 1)
 
 @pytest.mark.parametrize("L,steps,K,log2,cap", [(13, 300, 3, 16, 32), (21, 300, 32, 16, 32), (21, 400, 5, 4, 3),
-                                                (41, 200, 32, 16, 32), (5, 80, 2, 16, 32)])
+                                                (41, 200, 32, 16, 32), (5, 80, 2, 16, 32), (601, 25, 32, 16, 32)])
 def test_bestfirst_matches_python_statement(L, steps, K, log2, cap):
     """The queue rules (order, eviction of the last entry, discarding entries that
     became S, restarts) against the Python statement, whose dISL is flip-and-recompute."""
