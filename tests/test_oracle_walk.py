@@ -157,7 +157,7 @@ def test_bestfirst_invariants_L201():
 
 @pytest.mark.parametrize("L,steps,log2,cap,patience",
                          [(13, 200, 16, 32, 0), (21, 250, 16, 32, 0), (21, 300, 4, 3, 7),
-                          (5, 60, 16, 32, 0), (3, 20, 16, 32, 0), (41, 150, 16, 32, 0)])
+                          (5, 60, 16, 32, 0), (3, 20, 16, 32, 0), (41, 150, 16, 32, 0), (601, 12, 16, 32, 0)])
 def test_psl_walk_matches_python_statement(L, steps, log2, cap, patience):
     """Candidate order (PSL, ISL, i), best and stagnation on (PSL, ISL) pairs, against
     the Python statement, whose PSL and ISL come from numpy's correlate."""
