@@ -52,6 +52,8 @@ extern "C" {
 #define LABS_ERANGE (-7)     /* a long sequence left the range in which the library's fp32
                                 neighbourhood is exact (ISL above the bound stated at
                                 labs_walk); random starts and walks stay far below it */
+#define LABS_ETABU_FULL (-8) /* with LABS_FLAG_STRICT_HT: an HT insertion found no free
+                                slot within probe_cap (that walker restarted) */
 
 #define LABS_MAX_L 511       /* n = (L+1)/2 <= 256 free variables */
 #define LABS_MAX_L_LONG 11263 /* long sequences: n <= 5632 free variables */
@@ -90,6 +92,10 @@ typedef struct labs_config {
                                        neighbours per walker (see labs_walk); one walker per
                                        warp (per CTA for long sequences); not with
                                        LABS_FLAG_LEARNED, no checkpoints */
+#define LABS_FLAG_STRICT_HT 256     /* labs_sync returns LABS_ETABU_FULL once any HT insertion
+                                       of the context found no free slot within probe_cap
+                                       (the overflows counter of labs_stats is nonzero); the
+                                       walk itself is unchanged (the walker restarts) */
 #define LABS_FLAG_SECOND_HASH 128   /* with LABS_FLAG_BEST_FIRST: xLastovka's second table of
                                        evaluated neighbours (Section 3), one per walker with
                                        as many slots as HT; neighbours it holds are skipped

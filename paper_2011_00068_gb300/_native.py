@@ -19,6 +19,7 @@ LABS_ETIMEOUT = -4
 LABS_ECANCELLED = -5
 LABS_ESTATE = -6
 LABS_ERANGE = -7
+LABS_ETABU_FULL = -8
 LABS_MAX_L = 511
 LABS_MAX_L_LONG = 11263
 LABS_MAX_GROUPS = 64
@@ -32,13 +33,15 @@ LABS_FLAG_TWO_PER_WARP = 16
 LABS_FLAG_BEST_FIRST = 32
 LABS_FLAG_PSL = 64
 LABS_FLAG_SECOND_HASH = 128
+LABS_FLAG_STRICT_HT = 256
 LABS_QUEUE_SIZE = 32
 LABS_BEST_FIRST_MAX_STEPS = 1 << 28
 LABS_BEST_FIRST_MAX_STEPS_LONG = 1 << 21
 LOG_RECORD_BYTES = 64
 
 ERRORS = {LABS_EINVAL: "EINVAL", LABS_ENOMEM: "ENOMEM", LABS_ECUDA: "ECUDA", LABS_ETIMEOUT: "ETIMEOUT",
-          LABS_ECANCELLED: "ECANCELLED", LABS_ESTATE: "ESTATE", LABS_ERANGE: "ERANGE"}
+          LABS_ECANCELLED: "ECANCELLED", LABS_ESTATE: "ESTATE", LABS_ERANGE: "ERANGE",
+          LABS_ETABU_FULL: "ETABU_FULL"}
 
 # Every exported symbol of include/labs.h, in declaration order.
 EXPORTS = [

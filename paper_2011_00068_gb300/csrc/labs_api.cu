@@ -658,7 +658,15 @@ int labs_sync(labs_ctx* c)
         return e == cudaSuccess ? LABS_OK : cuda_fail(c, e, "stream synchronise");
     }
     cudaSetDevice(c->device);
-    return sync_status(c);
+    rc = sync_status(c);
+    if (rc || !(c->cfg.flags & LABS_FLAG_STRICT_HT)) return rc;
+    labs_counters cnt;
+    rc = labs_stats(c, 0, &cnt);
+    if (rc) return rc;
+    if (cnt.overflows > 0)
+        return fail(c, LABS_ETABU_FULL, "%lld HT insertions found no free slot within probe_cap = %d",
+                    (long long)cnt.overflows, c->cfg.probe_cap);
+    return LABS_OK;
 }
 
 // The walker with the best sequence among walkers of length L (0: all): lowest best

@@ -227,3 +227,25 @@ def test_bad_arguments_raise():
         s.walk(-1)
     with pytest.raises(labs.LabsError):
         s.results(3, 5)
+
+
+def test_strict_ht_reports_overflows():
+    """LABS_FLAG_STRICT_HT: labs_sync returns LABS_ETABU_FULL once an HT insertion found
+    no free slot (a 16-slot table with 3 probes at L = 21 overflows within 400 steps, as
+    the oracle shows); the walk itself is unchanged.  With the default table no error."""
+    o = oracle.walk(21, 9, 2, 400, tabu_log2=4, probe_cap=3, trace=True)
+    assert o["overflows"].sum() > 0
+    s = labs.Search(21, 2, 9, tabu_log2=4, probe_cap=3, flags=_native.LABS_FLAG_STRICT_HT)
+    code, isl = s.trace([0, 1], 400)
+    s.walk(400)
+    with pytest.raises(labs.LabsError) as err:
+        s.sync()
+    assert err.value.code == _native.LABS_ETABU_FULL
+    assert np.array_equal(code.cpu().numpy(), o["trace_code"])
+    assert s.stats()["overflows"] == int(o["overflows"].sum())
+    s.close()
+    s = labs.Search(21, 2, 9, flags=_native.LABS_FLAG_STRICT_HT)
+    s.walk(400)
+    s.sync()
+    assert s.stats()["overflows"] == 0
+    s.close()
