@@ -160,6 +160,28 @@ def test_neighbor_delta_equals_flip_and_recompute(L):
             assert d[i] == pyref.isl_np(t) - e
 
 
+@pytest.mark.parametrize("L", [1025, 4095, 11263])
+def test_neighbor_delta_long_lengths_sampled(L):
+    """At the long lengths the library serves, sampled neighbours (first, centre, last and
+    random free variables) of a random and of the all-+1 row equal Eq. 2 recomputed by
+    numpy after the flip, and ISL = n-1 mod 8 holds as at short lengths."""
+    n = (L + 1) // 2
+    rng = np.random.default_rng(L)
+    rows = [oracle.skew_expand(labs_inputs.random_free_vars(1, L, seed=L)[0], L),
+            oracle.skew_expand(np.ones(n, np.int8), L)]
+    for s in rows:
+        e = pyref.isl_np(s)
+        assert oracle.isl(s) == e and e % 8 == (n - 1) % 8
+        d = oracle.neighbor_delta(s)
+        assert d.shape == (n,)
+        for i in sorted({0, n // 2, n - 1} | set(int(k) for k in rng.integers(0, n, 3))):
+            t = s.astype(np.int64).copy()
+            t[i] = -t[i]
+            if L - 1 - i != i:
+                t[L - 1 - i] = -t[L - 1 - i]
+            assert d[i] == pyref.isl_np(t) - e, i
+
+
 def test_neighbor_delta_on_table1_and_degenerate():
     for L, F, _, hexs, p in table1()[::13]:
         s = oracle.hex_decode(hexs, L)
