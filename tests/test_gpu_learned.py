@@ -13,6 +13,7 @@ import paper_2011_00068_gb300 as labs
 from oracle import learned as ln
 from paper_2011_00068_gb300 import _native
 from paper_2011_00068_gb300 import learned as lrn
+from tests.nettol import assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -28,6 +29,38 @@ def seq_of_bits(bits, L):
     n = (L + 1) // 2
     x = np.array([-1 if (bits[i // 32] >> (i % 32)) & 1 else 1 for i in range(n)], np.int8)
     return oracle.skew_expand(x, L)
+
+
+def states_before_steps(L, seed, w, code, restart_idx, restart_bits):
+    """Free variables of walker w before every step, rebuilt from its trace codes (the
+    flipped free variable, TRACE_RESTART or -1 for a restart) and its starts: the
+    recorded restart state where one was used for that restart index (the last one
+    recorded wins, as in the oracle's replay), else the random start."""
+    n = (L + 1) // 2
+
+    def start_of(r):
+        x = None
+        for j, ri in enumerate(restart_idx):
+            if int(ri) == r:
+                bits = restart_bits[j]
+                x = np.array([-1 if (int(bits[i // 32]) >> (i % 32)) & 1 else 1 for i in range(n)], np.int8)
+        return x if x is not None else oracle.random_start(seed, w, r, L)
+
+    ridx = 0
+    x = start_of(0)
+    out = []
+    for c in code:
+        out.append(x.copy())
+        c = int(c)
+        if c == -1:
+            ridx += 1
+            x = start_of(ridx)
+            continue
+        x[c & 0xFFFF] = -x[c & 0xFFFF]
+        if c & oracle.TRACE_RESTART:
+            ridx += 1
+            x = start_of(ridx)
+    return out
 
 
 def test_log_records_follow_the_trajectory():
@@ -99,7 +132,10 @@ def test_learned_walk_replays_bit_exactly(L, W, steps, chunk, tau, cands):
     code, isl = code.cpu().numpy(), isl.cpu().numpy()
     res = s.results(seqs=True)
     dd = {k: v.cpu().numpy() for k, v in d.items()}
+    host_params = ln.unflatten(params.cpu().numpy())
+    net = ln.Net(True)
     used_restarts = 0
+    worst = 0.0
     for w in range(W):
         ns, nr = int(dd["score_count"][w]), int(dd["restart_count"][w])
         assert ns >= steps // chunk - 1 and ns <= cap
@@ -110,7 +146,18 @@ def test_learned_walk_replays_bit_exactly(L, W, steps, chunk, tau, cands):
         assert np.array_equal(code[w], o["trace_code"]), w
         assert np.array_equal(isl[w], o["trace_isl"]), w
         assert np.array_equal(res["best_seq"][w], o["best_seq"])
+        # every recorded score vector is the oracle network's output on the walker's
+        # state at that step (features from Eq. 1 and the neighbourhood, then the net)
+        before = states_before_steps(L, seed, w, code[w], dd["restart_idx"][w, :nr],
+                                     dd["restart"][w, :nr].view(np.uint32))
+        for k in range(ns):
+            seq = oracle.skew_expand(before[int(dd["score_step"][w, k])], L)
+            C_even = np.array([oracle.ck(seq, 2 * m) for m in range(1, n)])
+            fw = net.forward(host_params, ln.features(seq, C_even, oracle.neighbor_delta(seq)))
+            worst = max(worst, assert_close(dd["scores"][w, k, :n], fw["score"],
+                                            "walker %d, score vector %d" % (w, k)))
     assert used_restarts > 0  # restart proposals were taken
+    print("recorded scores: worst error / bound %.3f" % worst)
 
 
 def test_training_on_the_walk_log_lowers_the_loss():

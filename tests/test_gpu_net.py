@@ -1,6 +1,7 @@
 """GPU parity of the learned-proposal network kernels against oracle/learned.py, which
-rounds to bfloat16 at the same points: outputs within 2e-2 relative, gradients with
-cosine similarity >= 0.999 per parameter tensor, AdamW to float32 rounding."""
+rounds to bfloat16 at the same points, element by element.
+
+The per-element bound is stated in tests/nettol.py.  AdamW agrees to float32 rounding."""
 from __future__ import annotations
 
 import ctypes
@@ -11,6 +12,7 @@ import torch
 
 import paper_2011_00068_gb300 as labs
 from oracle import learned as ln
+from tests.nettol import assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -64,11 +66,14 @@ def test_forward_matches_oracle(n, B):
     sc, rs = gpu_forward(ln.flatten(params), x)
     net = ln.Net(True)
     xo = oracle_x(x)
+    worst = 0.0
     for b in range(B):
         fw = net.forward(params, xo[b])
-        rel = np.linalg.norm(sc[b] - fw["score"]) / max(np.linalg.norm(fw["score"]), 1e-6)
-        assert rel < 2e-2, (b, rel)
-        assert abs(rs[b] - fw["restart"]) <= 2e-2 * max(abs(fw["restart"]), 1e-2) + 1e-3
+        worst = max(worst, assert_close(sc[b], fw["score"], "score of sample %d" % b))
+        # the restart score is one dot product: its scale is the sum of its terms' sizes
+        terms = float(np.abs(fw["W"]["w6"] * fw["pooled"]).sum() + abs(params["b6"][0]))
+        worst = max(worst, assert_close(rs[b], fw["restart"], "restart score of sample %d" % b, scale=terms))
+    print("n=%d: worst error / bound %.3f" % (n, worst))
 
 
 @pytest.mark.parametrize("n,B", [(13, 4), (101, 6), (128, 5)])
@@ -93,14 +98,14 @@ def test_gradients_match_oracle(n, B):
     gpu = ln.unflatten(g.cpu().numpy())
     net = ln.Net(True)
     oloss, og = net.batch_loss_and_grads(params, list(oracle_x(x)), target, y, wf)
-    assert abs(loss.item() - oloss) <= 1e-2 * abs(oloss) + 1e-4
+    assert_close(loss.item(), oloss, "loss", scale=0.0)
+    worst = 0.0
     for name, _ in ln.PARAM_SHAPES:
-        a, b = gpu[name].ravel().astype(np.float64), og[name].ravel().astype(np.float64)
-        if np.linalg.norm(b) < 1e-7:
-            assert np.linalg.norm(a) < 1e-5, name
-            continue
-        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
-        assert cos >= 0.999, (name, cos)
+        # b5's exact gradient is zero (each sample's softmax gradient sums to zero): both
+        # sides hold float32 residue of n terms of size <= 1/B, below n * 2^-23
+        scale = 1e-3 if name == "b5" else None
+        worst = max(worst, assert_close(gpu[name], og[name], "gradient of " + name, scale=scale))
+    print("n=%d: worst gradient error / bound %.3f" % (n, worst))
 
 
 def test_adamw_matches_oracle():
