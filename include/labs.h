@@ -83,7 +83,11 @@ typedef struct labs_config {
 } labs_config;
 
 #define LABS_FLAG_NO_GRAPH 1     /* launch chunks one by one instead of a CUDA graph */
-#define LABS_FLAG_CHECK_STATE 2  /* re-derive ISL from scratch at each chunk end */
+#define LABS_FLAG_CHECK_STATE 2  /* accepted, no further effect: the check is always on.
+                                    Every chunk start rebuilds a walker's rows and C_k table
+                                    from its stored bits and compares the ISL (and, under the
+                                    PSL objective, the PSL) with the stored value; a mismatch
+                                    stops that walker and labs_sync returns LABS_ESTATE */
 #define LABS_FLAG_LEARNED 4      /* reserve workspace for the learned mode (labs_learned) */
 #define LABS_FLAG_WARP_PER_WALKER 8 /* one walker per warp even where two per warp fit */
 #define LABS_FLAG_TWO_PER_WARP 16   /* at most two walkers per warp even where four fit */
@@ -95,7 +99,9 @@ typedef struct labs_config {
 #define LABS_FLAG_STRICT_HT 256     /* labs_sync returns LABS_ETABU_FULL once any HT insertion
                                        of the context found no free slot within probe_cap
                                        (the overflows counter of labs_stats is nonzero); the
-                                       walk itself is unchanged (the walker restarts) */
+                                       walk itself is unchanged (the walker restarts).  Each
+                                       labs_sync then runs labs_stats (a reduction kernel and
+                                       three blocking copies); labs_reset clears the count */
 #define LABS_FLAG_SECOND_HASH 128   /* with LABS_FLAG_BEST_FIRST: xLastovka's second table of
                                        evaluated neighbours (Section 3), one per walker with
                                        as many slots as HT; neighbours it holds are skipped
@@ -151,7 +157,7 @@ void labs_default_config(labs_config *cfg);
 /* Creates a context for `walkers` independent walkers of one odd length L
  * (Algorithm 1: input L; every walker is one run of the search).  Walker w starts
  * from the random skew-symmetric sequence drawn by Philox4x32-10 under key `seed`
- * (Algorithm 1, "initialize a starting skew-symmetric sequence").  cfg may be NULL
+ * (Algorithm 1, start: a random skew-symmetric first sequence).  cfg may be NULL
  * (defaults).  No device work happens until a workspace is bound. */
 int labs_init(labs_ctx **ctx, int32_t L, int64_t walkers, uint64_t seed,
               const labs_config *cfg, void *cuda_stream);
@@ -179,7 +185,8 @@ int labs_reset(labs_ctx *ctx);
  * batch may be 0. */
 int labs_isl(labs_ctx *ctx, const int8_t *dev_seqs, int64_t batch, int32_t *dev_isl_out);
 
-/* The neighbourhood of Algorithm 1 ("fast calculate merit factor of S_f") for a
+/* The neighbourhood of Algorithm 1 (neighbourhood evaluation: the ISL of every
+ * one-flip neighbour S_f, from the current C_k in O(L) per flip) for a
  * batch of skew-symmetric rows: dev_delta_out is int32 [batch][n], entry i = ISL after
  * flipping free variable i (and its mirror) minus ISL before, i = 0..n-1.  A row that
  * is not +-1 or breaks Eq. 4 gets INT32_MIN in every entry (and labs_sync reports
@@ -288,7 +295,9 @@ int labs_enumerate(int32_t L, void *dev_scratch, size_t scratch_bytes, int64_t *
  * nothing (no cudaMalloc / cudaFree / allocating library routine); it clears the part
  * of the array it uses, then runs on cuda_stream and synchronises it.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current, so make that first call before any stream capture.  All calls share
+ * device current, so make that first call before any stream capture.  A device reset
+ * (cudaDeviceReset) invalidates the looked-up address: a call whose CUDA work fails
+ * forgets it, and the next call on that device looks it up again.  All calls share
  * the one array: calls that overlap on the GPU (from several host threads or streams)
  * race and give wrong results. */
 int labs_enumerate_noalloc(int32_t L, int64_t *min_isl, uint64_t *count,

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "labs_internal.cuh"
+#include "labs_nvtx.h"
 
 using namespace labsgpu;
 
@@ -507,12 +508,14 @@ void labs_default_config(labs_config* cfg)
 int labs_init(labs_ctx** ctx, int32_t L, int64_t walkers, uint64_t seed, const labs_config* cfg,
               void* cuda_stream)
 {
+    LABS_API_RANGE();
     return create(ctx, &L, &walkers, 1, seed, cfg, cuda_stream);
 }
 
 int labs_init_multi(labs_ctx** ctx, const int32_t* Ls, const int64_t* walkers_per_L, int32_t nL,
                     uint64_t seed, const labs_config* cfg, void* cuda_stream)
 {
+    LABS_API_RANGE();
     return create(ctx, Ls, walkers_per_L, nL, seed, cfg, cuda_stream);
 }
 
@@ -525,6 +528,7 @@ int labs_workspace_bytes(const labs_ctx* ctx, size_t* bytes)
 
 int labs_reset(labs_ctx* c)
 {
+    LABS_API_RANGE();
     int rc = need_ws(c);
     if (rc) return rc;
     cudaSetDevice(c->device);
@@ -558,6 +562,7 @@ int labs_reset(labs_ctx* c)
 
 int labs_bind_workspace(labs_ctx* c, void* dev_workspace, size_t bytes)
 {
+    LABS_API_RANGE();
     if (!c || !dev_workspace) return LABS_EINVAL;
     if (bytes < c->total) return fail(c, LABS_ENOMEM, "workspace has %zu bytes, needs %zu", bytes, c->total);
     if (((uintptr_t)dev_workspace & 255) != 0) return fail(c, LABS_EINVAL, "workspace must be 256-byte aligned");
@@ -585,6 +590,7 @@ int labs_bind_workspace(labs_ctx* c, void* dev_workspace, size_t bytes)
 
 int labs_isl(labs_ctx* c, const int8_t* dev_seqs, int64_t batch, int32_t* dev_isl_out)
 {
+    LABS_API_RANGE();
     if (!c) return LABS_EINVAL;
     if (c->nG != 1) return fail(c, LABS_EINVAL, "labs_isl needs a single-length context");
     if (batch < 0 || (batch > 0 && (!dev_seqs || !dev_isl_out))) return fail(c, LABS_EINVAL, "bad batch");
@@ -596,6 +602,7 @@ int labs_isl(labs_ctx* c, const int8_t* dev_seqs, int64_t batch, int32_t* dev_is
 
 int labs_neighbor_delta(labs_ctx* c, const int8_t* dev_seqs, int64_t batch, int32_t* dev_delta_out)
 {
+    LABS_API_RANGE();
     if (!c) return LABS_EINVAL;
     if (c->nG != 1) return fail(c, LABS_EINVAL, "labs_neighbor_delta needs a single-length context");
     if (batch < 0 || (batch > 0 && (!dev_seqs || !dev_delta_out))) return fail(c, LABS_EINVAL, "bad batch");
@@ -608,6 +615,7 @@ int labs_neighbor_delta(labs_ctx* c, const int8_t* dev_seqs, int64_t batch, int3
 
 int labs_walk(labs_ctx* c, int64_t steps)
 {
+    LABS_API_RANGE();
     int rc = need_ws(c);
     if (rc) return rc;
     if (steps < 0) return fail(c, LABS_EINVAL, "negative steps");
@@ -651,6 +659,7 @@ int labs_walk(labs_ctx* c, int64_t steps)
 
 int labs_sync(labs_ctx* c)
 {
+    LABS_API_RANGE();
     int rc = need_ws(c);
     if (rc) {
         if (!c) return rc;
@@ -712,6 +721,7 @@ static int best_outputs(labs_ctx* c, int64_t w, const WalkerState& ws, int8_t* h
 int labs_best(labs_ctx* c, int32_t L, int8_t* host_seq_out, int32_t* isl, double* F, int32_t* L_out,
               char* hex_out)
 {
+    LABS_API_RANGE();
     WalkerState ws;
     int64_t w = 0;
     int rc = best_state(c, L, &ws, &w);
@@ -727,6 +737,7 @@ int labs_best(labs_ctx* c, int32_t L, int8_t* host_seq_out, int32_t* isl, double
 int labs_best_psl(labs_ctx* c, int32_t L, int8_t* host_seq_out, int32_t* psl, int32_t* isl, int32_t* L_out,
                   char* hex_out)
 {
+    LABS_API_RANGE();
     if (c && !(c->cfg.flags & LABS_FLAG_PSL)) return fail(c, LABS_EINVAL, "context created without LABS_FLAG_PSL");
     WalkerState ws;
     int64_t w = 0;
@@ -741,6 +752,7 @@ int labs_best_psl(labs_ctx* c, int32_t L, int8_t* host_seq_out, int32_t* psl, in
 
 int labs_walker_psl(labs_ctx* c, int64_t first, int64_t count, int32_t* host_psl, int32_t* host_best_psl)
 {
+    LABS_API_RANGE();
     int rc = need_ws(c);
     if (rc) return rc;
     if (!(c->cfg.flags & LABS_FLAG_PSL)) return fail(c, LABS_EINVAL, "context created without LABS_FLAG_PSL");
@@ -764,6 +776,7 @@ int labs_walker_psl(labs_ctx* c, int64_t first, int64_t count, int32_t* host_psl
 int labs_walker_results(labs_ctx* c, int64_t first, int64_t count, int32_t* host_isl, int32_t* host_best_isl,
                         int8_t* host_seq, int8_t* host_best_seq, int64_t* host_target_step)
 {
+    LABS_API_RANGE();
     int rc = need_ws(c);
     if (rc) return rc;
     if (first < 0 || count < 0 || first + count > c->W) return fail(c, LABS_EINVAL, "walker range out of bounds");
@@ -806,6 +819,7 @@ int labs_walker_results(labs_ctx* c, int64_t first, int64_t count, int32_t* host
 
 int labs_stats(labs_ctx* c, int32_t L, labs_counters* out)
 {
+    LABS_API_RANGE();
     int rc = need_ws(c);
     if (rc) return rc;
     if (!out) return fail(c, LABS_EINVAL, "null output");
@@ -857,6 +871,7 @@ int labs_stats(labs_ctx* c, int32_t L, labs_counters* out)
 int labs_trace(labs_ctx* c, const int64_t* host_walker_ids, int32_t k, int64_t capacity, int32_t* dev_code_log,
                int32_t* dev_isl_log)
 {
+    LABS_API_RANGE();
     int rc = need_ws(c);
     if (rc) return rc;
     if (k < 0 || k > kMaxTrace) return fail(c, LABS_EINVAL, "0 <= k <= %d", kMaxTrace);
@@ -879,6 +894,7 @@ int labs_trace(labs_ctx* c, const int64_t* host_walker_ids, int32_t k, int64_t c
 
 int labs_log(labs_ctx* c, labs_log_record* dev_records, int64_t capacity)
 {
+    LABS_API_RANGE();
     int rc = need_ws(c);
     if (rc) return rc;
     if (capacity < 0 || (capacity > 0 && !dev_records)) return fail(c, LABS_EINVAL, "bad log buffer");
@@ -894,6 +910,7 @@ int labs_log(labs_ctx* c, labs_log_record* dev_records, int64_t capacity)
 int labs_log_labels(const labs_log_record* dev_records, int64_t count, int32_t* dev_target, float* dev_y,
                     float* dev_wf, void* cuda_stream)
 {
+    LABS_API_RANGE();
     if (count < 0 || (count > 0 && (!dev_records || !dev_target || !dev_y || !dev_wf))) return LABS_EINVAL;
     if (count == 0) return LABS_OK;
     return launch_labels(dev_records, count, dev_target, dev_y, dev_wf, cuda_stream);
@@ -902,6 +919,7 @@ int labs_log_labels(const labs_log_record* dev_records, int64_t count, int32_t* 
 int labs_features(int32_t L, const uint32_t* dev_bits, int64_t stride_words, int64_t count, float* dev_x,
                   void* cuda_stream)
 {
+    LABS_API_RANGE();
     if (!valid_L(L) || count < 0 || stride_words < kBitWords || (count > 0 && (!dev_bits || !dev_x)))
         return LABS_EINVAL;
     return launch_features(dev_bits, stride_words, count, L, dev_x, cuda_stream);
@@ -916,6 +934,7 @@ int labs_learned_workspace_bytes(const labs_ctx* c, int32_t candidates, size_t* 
 
 int labs_learned(labs_ctx* c, const float* dev_params, int32_t tau, int32_t candidates, void* dev_ws, size_t ws_bytes)
 {
+    LABS_API_RANGE();
     int rc = need_ws(c);
     if (rc) return rc;
     if (dev_params) {
@@ -937,6 +956,7 @@ int labs_trace_learned(labs_ctx* c, int32_t capacity, float* dev_scores, int64_t
                        int32_t* dev_score_count, uint32_t* dev_restart, int64_t* dev_restart_idx,
                        int32_t* dev_restart_count)
 {
+    LABS_API_RANGE();
     int rc = need_ws(c);
     if (rc) return rc;
     if (capacity < 0 || (capacity > 0 && (!dev_scores || !dev_score_step || !dev_score_count || !dev_restart ||
@@ -964,6 +984,7 @@ int labs_enumerate_scratch_bytes(int32_t L, size_t* bytes)
 int labs_enumerate(int32_t L, void* dev_scratch, size_t scratch_bytes, int64_t* min_isl, uint64_t* count,
                    uint64_t* first_assignment, void* cuda_stream)
 {
+    LABS_API_RANGE();
     if (L < 3 || L > 63 || (L & 1) == 0 || !dev_scratch) return LABS_EINVAL;
     if (scratch_bytes < enum_scratch_bytes(L)) return LABS_ENOMEM;
     if (((uintptr_t)dev_scratch & 15) != 0) return LABS_EINVAL;
@@ -985,6 +1006,7 @@ static uint64_t ckpt_kind(const labs_ctx* c)
 
 int labs_checkpoint(labs_ctx* c, int with_tabu, void* host_buf, size_t* bytes)
 {
+    LABS_API_RANGE();
     int rc = need_ws(c);
     if (rc) return rc;
     if (c->cfg.flags & LABS_FLAG_BEST_FIRST) return fail(c, LABS_EINVAL, "no checkpoints of a best-first search");
@@ -1018,6 +1040,7 @@ int labs_checkpoint(labs_ctx* c, int with_tabu, void* host_buf, size_t* bytes)
 
 int labs_restore(labs_ctx* c, const void* host_buf, size_t bytes)
 {
+    LABS_API_RANGE();
     int rc = need_ws(c);
     if (rc) return rc;
     if (c->cfg.flags & LABS_FLAG_BEST_FIRST) return fail(c, LABS_EINVAL, "no checkpoints of a best-first search");

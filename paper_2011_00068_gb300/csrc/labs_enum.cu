@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "labs_internal.cuh"
+#include "labs_nvtx.h"
 
 namespace labsgpu {
 
@@ -182,7 +183,9 @@ int enum_run(int L, EnumPart* scratch, void* stream, EnumPart* host_out)
 // library holds its kNoAllocParts * 32 bytes (33,280 bytes) until the process exits.
 // Host code cannot use the array's name as a device address, so the first call on
 // each device looks the address up with cudaGetSymbolAddress (with that device
-// current) and keeps it per device.
+// current) and keeps it per device.  A device reset (cudaDeviceReset) unloads the
+// module and invalidates a kept address: a call whose CUDA work fails drops the kept
+// address of its device, and the next call looks it up again.
 constexpr int kNoAllocParts = 1040;  // enum_blocks(63) + 1 = 1025 fit
 constexpr int kNoAllocDevices = 64;
 static __device__ __align__(256) EnumPart g_noalloc_scratch[kNoAllocParts];
@@ -197,6 +200,7 @@ EnumPart* g_noalloc_addr[kNoAllocDevices] = {};
 extern "C" int labs_enumerate_noalloc(int32_t L, int64_t* min_isl, uint64_t* count, uint64_t* first_assignment,
                                       void* cuda_stream)
 {
+    LABS_API_RANGE();
     using namespace labsgpu;
     if (L < 3 || L > 63 || (L & 1) == 0) return LABS_EINVAL;
     const int blocks = enum_blocks(L);
@@ -214,12 +218,22 @@ extern "C" int labs_enumerate_noalloc(int32_t L, int64_t* min_isl, uint64_t* cou
         }
         scratch = g_noalloc_addr[dev];
     }
+    auto forget = [dev]() {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        g_noalloc_addr[dev] = nullptr;
+    };
     // The array keeps the previous call's contents; clear the part this call uses.
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    if (cudaMemsetAsync(scratch, 0, sizeof(EnumPart) * (size_t)(blocks + 1), s) != cudaSuccess) return LABS_ECUDA;
+    if (cudaMemsetAsync(scratch, 0, sizeof(EnumPart) * (size_t)(blocks + 1), s) != cudaSuccess) {
+        forget();
+        return LABS_ECUDA;
+    }
     EnumPart r;
     const int rc = enum_run(L, scratch, cuda_stream, &r);
-    if (rc) return rc;
+    if (rc) {
+        if (rc == LABS_ECUDA) forget();
+        return rc;
+    }
     if (min_isl) *min_isl = r.min_isl;
     if (count) *count = r.count;
     if (first_assignment) *first_assignment = r.first;

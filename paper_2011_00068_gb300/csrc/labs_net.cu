@@ -22,6 +22,7 @@
 #include <cstdint>
 
 #include "labs_internal.cuh"
+#include "labs_nvtx.h"
 
 namespace labsgpu {
 namespace net {
@@ -608,6 +609,7 @@ int labs_net_sizes(int32_t n, int64_t batch, size_t* param_count, size_t* worksp
 
 int labs_net_init(float* dev_params, uint64_t seed, void* cuda_stream)
 {
+    LABS_API_RANGE();
     if (!dev_params) return LABS_EINVAL;
     return net::init_params(dev_params, seed, (cudaStream_t)cuda_stream);
 }
@@ -615,6 +617,7 @@ int labs_net_init(float* dev_params, uint64_t seed, void* cuda_stream)
 int labs_net_forward(const float* dev_params, const float* dev_x, int64_t batch, int32_t n, float* dev_scores,
                      float* dev_restart, void* dev_ws, size_t ws_bytes, void* cuda_stream)
 {
+    LABS_API_RANGE();
     if (!dev_params || !dev_x || n < 2 || n > kMaxN || batch < 0 || batch > INT32_MAX) return LABS_EINVAL;
     if (batch == 0) return LABS_OK;
     const net::NetWs w = net::carve(dev_ws, batch, n);
@@ -634,6 +637,7 @@ int labs_net_gradients(const float* dev_params, const float* dev_x, const int32_
                        const float* dev_wf, int64_t batch, int32_t n, float* dev_grads, float* dev_loss, void* dev_ws,
                        size_t ws_bytes, void* cuda_stream)
 {
+    LABS_API_RANGE();
     if (!dev_params || !dev_x || !dev_target || !dev_y || !dev_wf || !dev_grads || n < 2 || n > kMaxN || batch < 1 ||
         batch > INT32_MAX)
         return LABS_EINVAL;
@@ -651,6 +655,7 @@ int labs_net_gradients(const float* dev_params, const float* dev_x, const int32_
 int labs_net_adamw(float* dev_params, const float* dev_grads, float* dev_m, float* dev_v, int64_t t, float lr,
                    float weight_decay, void* cuda_stream)
 {
+    LABS_API_RANGE();
     if (!dev_params || !dev_grads || !dev_m || !dev_v || t < 1) return LABS_EINVAL;
     return net::adamw(dev_params, dev_grads, dev_m, dev_v, t, lr, weight_decay, (cudaStream_t)cuda_stream);
 }

@@ -243,6 +243,15 @@ def test_strict_ht_reports_overflows():
     assert err.value.code == _native.LABS_ETABU_FULL
     assert np.array_equal(code.cpu().numpy(), o["trace_code"])
     assert s.stats()["overflows"] == int(o["overflows"].sum())
+    # labs_reset empties HT and the counters: the error is gone, and a walk shorter than
+    # the first overflow (the oracle's walkers first overflow within 10 steps) syncs
+    s.reset()
+    assert s.stats()["overflows"] == 0
+    s.sync()
+    assert oracle.walk(21, 9, 2, 9, tabu_log2=4, probe_cap=3)["overflows"].sum() == 0
+    s.walk(9)
+    s.sync()
+    assert s.stats()["overflows"] == 0
     s.close()
     s = labs.Search(21, 2, 9, flags=_native.LABS_FLAG_STRICT_HT)
     s.walk(400)
