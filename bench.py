@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-delta", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-length line (52 odd lengths 201..303 x 2048 walkers in one launch)")
+    ap.add_argument("--mixed-walkers", type=int, default=2048)
+    ap.add_argument("--mixed-steps", type=int, default=5000)
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--config", choices=["walk", "learned", "scaleup", "long", "secondhash"], default="walk")
     ap.add_argument("--long-walkers", type=int, default=608)
@@ -272,6 +276,52 @@ def delta_kernel_line(args, dev, stream, labs):
             "int32_equivalent": int32_equivalent((n - 1) * flips, sms, sm_mhz)}
 
 
+def mixed_line(args, dev, labs):
+    """All 52 odd lengths L = 201..303 as walkers of one context (one persistent,
+    graph-captured chunk chain; launch shape from the tuner), mixed_walkers walkers per
+    length x mixed_steps steps, seed 7: flips/s timed with CUDA events on the
+    library's stream around labs_walk, after an untimed run of the same length."""
+    import torch
+
+    from paper_2011_00068_gb300 import tune
+
+    Ls = list(range(201, 304, 2))
+    counts = [args.mixed_walkers] * len(Ls)
+    best = tune.tune(Ls, counts, tabu_log2=args.tabu_log2, device=dev, steps=256)
+    s = labs.Search(Ls, counts, 7, device=dev, tabu_log2=args.tabu_log2, warps_per_cta=best["warps_per_cta"],
+                    chunk_steps=best["chunk_steps"])
+    s.walk(args.mixed_steps)  # untimed: graph capture and first touch of the tables
+    s.sync()
+    s.reset()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s.stream)
+    s.walk(args.mixed_steps)
+    b.record(s.stream)
+    s.sync()
+    ms = a.elapsed_time(b)
+    st = s.stats()
+    assert st["steps"] == sum(counts) * args.mixed_steps, st
+    peaks = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    lag_terms = sum(c * args.mixed_steps * ((L + 1) // 2) * ((L + 1) // 2 - 1) for L, c in zip(Ls, counts))
+    peak = FP32_LANES_PER_SM * 2 * sms * sm_mhz * 1e6
+    b = s.best()
+    out = {"workload": "52 odd L = 201..303, %d walkers each (%d walkers), %d steps, one context, seed 7, "
+                       "HT 2^%d slots/walker (%.1f GB)" % (args.mixed_walkers, sum(counts), args.mixed_steps,
+                                                         args.tabu_log2,
+                                                         (sum(counts) << args.tabu_log2) * 8 / 1e9),
+           "value": st["flip_evaluations"] / (ms / 1e3), "unit": UNIT, "ms": ms,
+           "launch": {"warps_per_cta": best["warps_per_cta"], "chunk_steps": best["chunk_steps"]},
+           "roofline_frac": ALGO_FLOP_PER_LAG_TERM * lag_terms / (ms / 1e3) / peak,
+           "best": {"isl": b["isl"], "F": b["F"], "L": b["L"]}}
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -387,6 +437,11 @@ def run_ours(args):
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h)}
 
     delta = None if args.no_delta else delta_kernel_line(args, dev, stream, labs)
+    mixed = None
+    if not args.no_mixed and world == 1 and args.search == "walk":
+        s.close()
+        torch.cuda.empty_cache()
+        mixed = mixed_line(args, dev, labs)
     if args.search == "psl":
         # lowest (PSL, ISL) pair over ranks: PSL < 2^9 above ISL < 2^26 in one key
         obj, best_rank = replicas.best_over_ranks((st["best_psl"] << 26) | st["best_isl"], device=dev)
@@ -409,6 +464,7 @@ def run_ours(args):
                 "best": dict({"isl": best_isl, "F": args.L ** 2 / (2 * best_isl), "L": st["best_L"],
                               "rank": best_rank}, **({"psl": best_psl} if args.search == "psl" else {})),
                 "delta_kernel": delta,
+                "mixed_201_303": mixed,
                 "restarts": st["restarts"]}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)

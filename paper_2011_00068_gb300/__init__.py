@@ -17,6 +17,7 @@ when the library cannot be loaded every call raises.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 from typing import Sequence
 
@@ -27,7 +28,7 @@ from . import _native
 from ._native import LabsConfig, LabsCounters, LabsError  # noqa: F401
 
 __all__ = ["Search", "isl", "neighbor_delta", "enumerate_skew", "config", "LabsError", "library", "features",
-           "log_labels"]
+           "log_labels", "close_rows"]
 
 LOG_RECORD_WORDS = 16  # a labs_log_record is 16 32-bit words
 
@@ -257,6 +258,19 @@ class Search:
 
 
 _row_ctx: dict = {}
+
+
+def close_rows():
+    """Destroys the contexts that isl() and neighbor_delta() keep per (length, device,
+    stream); the next call creates them again.  Runs at interpreter exit."""
+    lib = _native._lib
+    while _row_ctx:
+        _, ctx = _row_ctx.popitem()
+        if lib is not None:
+            lib.labs_destroy(ctx)
+
+
+atexit.register(close_rows)
 
 
 def _rows_ctx(L: int, device: torch.device, stream):

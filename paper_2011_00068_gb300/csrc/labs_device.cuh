@@ -1,6 +1,7 @@
 // labs_device.cuh -- device code of the walk shared by the kernel translation units
-// (included by labs_kernels.cu and the walk-instantiation units labs_walk16.cu and
-// labs_walk32.cu).  Not part of the public ABI.
+// (included by labs_kernels.cu, labs_long.cu and the walk-instantiation units
+// labs_walk8a/8b.cu, labs_walk16a/16b.cu and labs_walk32*.cu).  Not part of the
+// public ABI.
 //
 // A tile of lanes owns one walker (or one input row): the whole warp, or half of it when
 // two walkers share a warp.  A walker's sequence is kept in shared

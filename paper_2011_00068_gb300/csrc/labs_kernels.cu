@@ -1,8 +1,7 @@
 // labs_kernels.cu -- sm_103a kernels of the skew-symmetric LABS search
 // (Brest & Boskovic, arXiv 2011.00068): walker starts, the stateless row kernels
 // (ISL, neighbourhood), learned-proposal support, reductions and the launchers.
-// The walk itself is in labs_device.cuh, instantiated by labs_walk16.cu and
-// labs_walk32.cu.
+// The walk itself is in labs_device.cuh, instantiated by the labs_walk*.cu units.
 #include <algorithm>
 
 #include "labs_device.cuh"

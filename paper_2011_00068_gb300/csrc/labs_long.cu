@@ -987,10 +987,14 @@ int launch_long_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out
     const LongDeltaFn fn = long_delta_fn(n);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LABS_ECUDA;
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = (int)(batch < 2 * sms ? batch : 2 * sms);
+    // as many resident CTAs as fit (four per SM with 128 threads, two with 256, one with 512)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, long_threads(n), smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int64_t slots = (int64_t)per_sm * sms;
+    const int grid = (int)(batch < slots ? batch : slots);
     fn<<<grid, long_threads(n), smem, (cudaStream_t)stream>>>(seqs, batch, L, out, status);
     return cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ECUDA;
 }

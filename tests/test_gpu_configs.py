@@ -5,8 +5,8 @@ config 1: L=41, 64 walkers x 1e5 steps, seed 1: every step of every walker.
 config 2: L=201, 16384 walkers x 1e4 steps, seed 7 (the bench step): 48 walkers
           spread over the batch, final/best ISL, best sequence, time-to-target step.
 config 3: the 52 odd lengths 201..303, 2048 walkers each, 5e3 steps, one launch:
-          LABS_PARITY_PER_L walkers per length (default 3; 64 is the full sample,
-          about five minutes of oracle time on 16 cores).
+          64 walkers per length (3,328 oracle walkers; LABS_PARITY_PER_L sets
+          another count).
 largest length: L=501 (the largest length of the scale-up configuration), 8192
           walkers x 2000 steps.
 best-first search: the config-2 workload with LABS_FLAG_BEST_FIRST (bench.py
@@ -81,7 +81,7 @@ def test_config3_mixed_lengths_one_launch():
     s = labs.Search(Ls, [per] * len(Ls), seed)
     s.walk(steps)
     s.sync()
-    k = int(os.environ.get("LABS_PARITY_PER_L", "3"))
+    k = int(os.environ.get("LABS_PARITY_PER_L", "64"))
     rng = np.random.default_rng(3)
     jobs = []
     for g, L in enumerate(Ls):
