@@ -166,6 +166,7 @@ struct WarpSmem {
     int bvec;   // words per bit vector of B
     int xoff;   // long layout: word offset of the CTA scratch (kLongThreads words) and the
                 // free-variable bits (kBitWordsLong words)
+    int poff;   // row layout: word offset of the per-lag P values Q[0 .. n_max) (0: none)
     int words;  // total words per walker (multiple of 4: walkers stay 16-byte aligned)
 };
 // Outputs per lane (the lane block R) for n free variables and `tile` lanes per walker
@@ -234,7 +235,48 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
     w.boff = w.goff + 2 * w.glen;
     w.bvec = kBitVec;
     w.xoff = 0;
+    w.poff = 0;
     w.words = (w.boff + 4 * kBitVec + 3) & ~3;
+    return w;
+}
+
+// Layout of one row of the stateless row kernels (labs_neighbor_delta), `tile` lanes per
+// row with lane block R = block_R(n_max, tile) (v0 <= (tile/2 - 1) R):
+//   A rows: the Toeplitz loop reads A_p[0 .. round8(n)) (zero beyond the class), the
+//     assembly A_p[v], A_p[n-1-p-v] and A_p[3v+p-n+1] for every lane output v (down to
+//     -(n-1), below 3 (tile/2) R - n);
+//   G: the table writes E[m] and its mirror for 1 <= m < n (pairs -n .. n-1), the
+//     window reads pairs -(tile/2) R .. round8(n), the assembly C_{q-i} at pairs above
+//     c - 2 (tile/2) R;
+//   Q[0 .. n_max): the per-lag P values (see the row kernels); no bit vectors (the
+//     classes stay in registers).
+__host__ __device__ inline WarpSmem row_smem(int n_max, int tile)
+{
+    WarpSmem w;
+    const int R = block_R(n_max, tile);
+    const int vtop = (tile / 2) * R;             // one past the largest lane output
+    const int nu = (n_max + 7) & ~7;
+    int lo = n_max, hi = nu;
+    if (vtop > hi) hi = vtop;                    // A_p[v] with v < vtop
+    if (3 * vtop - n_max > hi) hi = 3 * vtop - n_max;  // A_p[3v+p-n+1] <= 3 vtop - n - 1
+    if (n_max + 2 > lo) lo = n_max + 2;          // A_p[n-1-p-v] down to n - 1 - vtop
+    if (vtop - n_max + 2 > lo) lo = vtop - n_max + 2;
+    w.apad = (lo + 3) & ~3;
+    w.alen = w.apad + ((hi + 7) & ~7);
+    // one row per warp: the halves read A0 and A1 at equal offsets, on disjoint banks
+    // when alen = 16 (mod 32)
+    if (tile == 32) w.alen += (48 - (w.alen & 31)) & 31;
+    int gl = n_max + 1;                          // mirror of E down to pair -n
+    if (vtop + R > gl) gl = vtop + R;            // the window's first pairs
+    if (2 * vtop - n_max + 2 > gl) gl = 2 * vtop - n_max + 2;  // C_{q-i} below 0
+    w.gpad = gl;
+    w.glen = w.gpad + nu + 2;
+    w.goff = 2 * w.alen;
+    w.boff = w.goff + 2 * w.glen;
+    w.bvec = 0;
+    w.xoff = 0;
+    w.poff = (w.boff + 3) & ~3;
+    w.words = w.poff + ((n_max + 3) & ~3);
     return w;
 }
 
@@ -282,6 +324,7 @@ __host__ __device__ inline WarpSmem long_smem(int n_max, int tile)
     w.boff = w.goff + 2 * w.glen;
     w.bvec = (n_max + 31) / 32 + 2;
     w.xoff = (w.boff + 4 * w.bvec + 3) & ~3;
+    w.poff = 0;
     // scratch, bits, then the best-first search's queue keys (LABS_QUEUE_SIZE 64-bit
     // words), each warp's lowest candidate keys (32 per warp), the keys entered in a
     // round, two words of round state and the entered keys' places (LABS_QUEUE_SIZE ints)

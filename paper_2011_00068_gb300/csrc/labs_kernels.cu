@@ -4,6 +4,7 @@
 // The walk itself is in labs_device.cuh, instantiated by the labs_walk*.cu units.
 #include <algorithm>
 
+#include "labs_async.cuh"
 #include "labs_device.cuh"
 
 namespace labsgpu {
@@ -123,118 +124,388 @@ __global__ void __launch_bounds__(256) isl_kernel(const int8_t* __restrict__ seq
     }
 }
 
-template <int R>
-__device__ void delta_row(const View& V, int n, const Tile<32>& t, int32_t* dst)
+// ------------------------------------------ stateless rows (labs_neighbor_delta)
+//
+// A row kernel sees each input row once, so it builds everything from the row itself:
+//   - the two parity classes as bit vectors held in registers (NW words each, bit u of
+//     class p set <=> A_p[u] = -1), from warp ballots of the row's bytes, while the
+//     bytes also go to the float rows A0/A1 that the Toeplitz product reads;
+//   - the Eq. 4 check on those words: class p of a skew-symmetric row is a palindrome
+//     when c + p is even and an antipalindrome when it is odd (entries u and n_p-1-u are
+//     positions c-j and c+j of the sequence), so its bit vector reversed over its n_p
+//     bits equals itself, or itself with every bit inverted;
+//   - the even-lag table C_{2m} = C0_m + C1_m, C^{(p)}_m = (n_p - m) - 2 #{u : a_u !=
+//     a_{u+m}}, from popcounts of class words against the class shifted by m;
+//   - P without a pass of its own: with a_{n_p-1-u} = s_p a_u (s_p = +-1 as above), the
+//     pairs (v+m, v-m), m = 1..v, of P_v are the upper half of the pairs of the class's
+//     lag d = n_p-1-2v, whose lower half repeats them term by term and whose middle pair
+//     (v, n_p-1-v) has product s_p; so C^{(p)}_d = 2 s_p P_v + s_p, i.e.
+//     P_v = (s_p C^{(p)}_d - 1) / 2.  Lag m serves the class with n_p - 1 = m (mod 2),
+//     p = (c - m) & 1, whose sign is then s_p = (-1)^m; the lane that counts lag m
+//     stores that class's P value in Q[m], and the lane of output v reads Q[n_p-1-2v].
+// Then the Toeplitz product and the assembly as in the walk.
+
+// Row `src` (has = false: no row for this lane group) into A_p[u] (floats) and the
+// class words x0/x1.  TILE lanes per row (16: two rows per warp; 32: one); lane l reads
+// class l / (TILE/2), entries u = (TILE/2) it + l % (TILE/2).  With STAGED, bytes j <
+// lim of the row are read from its staged copy stg (shared memory), the rest from src.
+// Returns true when a byte of this lane is not +-1.
+template <int TILE, int NW, bool STAGED>
+__device__ __forceinline__ bool row_load(const View& V, const int8_t* __restrict__ src, const int8_t* stg,
+                                         int64_t lim, bool has, int L, int lane, int h, uint32_t (&x0)[NW],
+                                         uint32_t (&x1)[NW])
 {
-    const Outs<Tile<32>, R> o(t);
-    int dl[R];
-    {
-        float X[R], P[R];
-        toeplitz(V, n, o, X);
-        p_direct(V, n, o, P);
-        assemble(V, n, o, X, P, dl);
-    }
+    constexpr int G = TILE / 2;               // lanes per class
+    constexpr int IT = 32 / G;                // ballots per class word
+    const int p = lane / G, e = lane % G;
+    float* A = p ? V.A1 : V.A0;
+    uint32_t bad = 0u;  // v in {1, -1} <=> (v + 1) & ~2 == 0
+    // rows held whole by the staging buffer (all but the input's last few bytes) read
+    // shared memory only; the choice is the same for the whole warp
+    const bool whole = STAGED && __all_sync(kFull, has && lim >= L);
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-        if (dl[r] != INT_MAX) dst[2 * (o.v0 + r) + o.p] = dl[r];
+    for (int k = 0; k < NW; ++k) {
+        uint32_t bl[IT];
+#pragma unroll
+        for (int tt = 0; tt < IT; ++tt) {
+            bl[tt] = 0u;
+            // only the last word's rounds can lie wholly past the row (n > 32 (NW - 1))
+            if (k == NW - 1 && 2 * G * (IT * k + tt) >= L) continue;  // uniform
+            const int u = G * (IT * k + tt) + e, j = 2 * u + p;
+            int v = 1;
+            if (whole) {
+                // every row exists, and rounds below the last word lie inside the row
+                if (k < NW - 1 || j < L) {
+                    v = stg[j];
+                    A[u] = (float)v;
+                }
+            } else if (has && j < L) {
+                v = (STAGED && j < lim) ? stg[j] : src[j];
+                A[u] = (float)v;
+            }
+            bad |= (uint32_t)(v + 1) & ~2u;
+            bl[tt] = __ballot_sync(kFull, v < 0);
+        }
+        if constexpr (TILE == 16) {
+            // ballot bit 16h + 8p + e: byte 2h + p of the four ballots, in order
+            const uint32_t s0 = (uint32_t)(((4 + 2 * h) << 4) | (2 * h)), s1 = s0 + 0x11u;
+            x0[k] = __byte_perm(__byte_perm(bl[0], bl[1], s0), __byte_perm(bl[2], bl[3], s0), 0x5410);
+            x1[k] = __byte_perm(__byte_perm(bl[0], bl[1], s1), __byte_perm(bl[2], bl[3], s1), 0x5410);
+        } else {
+            // ballot bit 16p + e: half p of the two ballots
+            x0[k] = __byte_perm(bl[0], bl[1], 0x5410);
+            x1[k] = __byte_perm(bl[0], bl[1], 0x7632);
+        }
+    }
+    return bad != 0u;
 }
 
-// The neighbourhood of Algorithm 1 for skew-symmetric rows, one warp per row, R
-// outputs per lane (R = block_R(n, 32), odd, chosen by the host).
-template <int R>
+// Bits of class entries below np in word k.
+__device__ __forceinline__ uint32_t class_mask(int np, int k)
+{
+    const int w = np - 32 * k;
+    return w >= 32 ? ~0u : (w <= 0 ? 0u : (1u << w) - 1u);
+}
+
+// xr = x reversed over its np bits (bit t of xr = bit np-1-t of x), np >= 32 (NW-1).
+template <int NW>
+__device__ __forceinline__ void reverse_class(const uint32_t (&x)[NW], int np, uint32_t (&xr)[NW])
+{
+    uint32_t rv[NW + 1];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) rv[k] = __brev(x[NW - 1 - k]);
+    rv[NW] = 0u;
+    const int sh = 32 * NW - np;  // 0 .. 32
+#pragma unroll
+    for (int k = 0; k < NW; ++k) xr[k] = __funnelshift_rc(rv[k], rv[k + 1], sh);
+}
+
+// The table E (set_E) and Q from the class words; lane `lane` of TILE counts the lags
+// m = 32q + lane + TILE j (q < NW, j < 32/TILE) of both classes.  Mismatches of lag m
+// over the valid pairs u < n_p - m: over the first NW - q words against the class
+// shifted by m, plus the set bits of the words beyond (positions whose partner lies
+// past the vector), minus the set bits of the top m entries (partners past the class,
+// counted as mismatches by the shifted words) = the reversed class's first m bits.
+template <int TILE, int NW>
+__device__ __forceinline__ void row_table(const View& V, float* __restrict__ Q, int n, int lane,
+                                          const uint32_t (&x0)[NW], const uint32_t (&x1)[NW],
+                                          const uint32_t (&xr0)[NW], const uint32_t (&xr1)[NW])
+{
+    const int n1 = n - 1;
+    int pre0[NW], pre1[NW], suf0[NW + 1], suf1[NW + 1];
+    pre0[0] = pre1[0] = 0;
+#pragma unroll
+    for (int k = 1; k < NW; ++k) {
+        pre0[k] = pre0[k - 1] + __popc(xr0[k - 1]);
+        pre1[k] = pre1[k - 1] + __popc(xr1[k - 1]);
+    }
+    suf0[NW] = suf1[NW] = 0;
+#pragma unroll
+    for (int k = NW - 1; k >= 0; --k) {
+        suf0[k] = suf0[k + 1] + __popc(x0[k]);
+        suf1[k] = suf1[k + 1] + __popc(x1[k]);
+    }
+    // mismatch counts of lag 32q + r start from the words beyond the shift and the
+    // top-entry correction; those parts not depending on r are shared by both j
+    int base0[NW], base1[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        base0[q] = suf0[NW - q] - pre0[q];
+        base1[q] = suf1[NW - q] - pre1[q];
+    }
+#pragma unroll
+    for (int j = 0; j < 32 / TILE; ++j) {
+        const int r = lane + TILE * j;  // < 32
+        const uint32_t low = (1u << r) - 1u;
+        // lag m = 32q + r has the parity of r: Q[m] belongs to class (n1 - r) & 1, sign (-1)^r
+        const bool use1 = ((n1 - r) & 1) != 0;
+        const float half = (r & 1) ? -0.5f : 0.5f;
+        uint32_t s0[NW], s1[NW];
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            s0[k] = __funnelshift_r(x0[k], k + 1 < NW ? x0[k + 1] : 0u, r);
+            s1[k] = __funnelshift_r(x1[k], k + 1 < NW ? x1[k + 1] : 0u, r);
+        }
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+            const int m = 32 * q + r;
+            int t0 = base0[q] - __popc(xr0[q] & low);
+            int t1 = base1[q] - __popc(xr1[q] & low);
+#pragma unroll
+            for (int k = 0; k + q < NW; ++k) {
+                t0 += __popc(x0[k] ^ s0[k + q]);
+                t1 += __popc(x1[k] ^ s1[k + q]);
+            }
+            // lags below the last word group exist in both classes (n1 >= 32 (NW - 1))
+            if (q < NW - 1 || m < n) {
+                const int c0 = (n - m) - 2 * t0;
+                // class 1 has n1 = n - 1 entries: no pair at lag n - 1
+                const int c1 = (q < NW - 1 || m < n1) ? (n1 - m) - 2 * t1 : 0;
+                if (q > 0 || m > 0) {
+                    // E[m] in both pairs that hold it and in the mirror half (the row
+                    // layouts keep gpad >= n, so every mirror entry exists)
+                    const float e = (float)(c0 + c1);
+                    V.G[m].x = e;
+                    V.G[m - 1].y = e;
+                    V.G[-m].x = e;
+                    V.G[-m - 1].y = e;
+                }
+                // Q[0] belongs to the centre, whose dISL has no P term
+                Q[m] = fmaf(half, (float)(use1 ? c1 : c0), -0.5f);
+            }
+        }
+    }
+}
+
+// P of the lane's R outputs from Q.
+template <class TL, int R>
+__device__ __forceinline__ void row_p(const float* __restrict__ Q, int n, const Outs<TL, R>& o, float (&P)[R])
+{
+    const int top = (o.p ? n - 2 : n - 1) - 2 * o.v0;  // n_p - 1 - 2 v0
+#pragma unroll
+    for (int r = 0; r < R; ++r) P[r] = Q[max(top - 2 * r, 0)];
+}
+
+// Staging of input rows: each warp copies the bytes of its next rows (rows r0 .. r0+k-1,
+// global bytes [r0 L, (r0+k) L)) into one of two shared-memory buffers with one bulk
+// copy while it evaluates the current rows from the other buffer.  A bulk copy moves
+// 16-byte aligned blocks, so the copy covers [floor16(r0 L), ceil16((r0+k) L)), cut at
+// the last 16-byte boundary of the input (the few bytes past it, and every byte when the
+// input is not 16-byte aligned, are read from global memory directly).
+__host__ __device__ inline int stage_bytes(int L, int rows)
+{
+    return (rows * L + 32 + 15) & ~15;
+}
+
+struct StageRange {
+    int64_t a0, a1;  // staged global bytes [a0, a1); a1 <= a0: none
+};
+
+__device__ __forceinline__ StageRange stage_range(int64_t r0, int rows, int L, int64_t total)
+{
+    const int64_t e = min((r0 + rows) * (int64_t)L, total);
+    StageRange g;
+    g.a0 = (r0 * L) & ~(int64_t)15;
+    g.a1 = min((e + 15) & ~(int64_t)15, total & ~(int64_t)15);
+    return g;
+}
+
+// Issued by one lane: the copy of rows r0 .. r0+rows-1 into the buffer at shared address
+// dst, counted on barrier bar (an arrival without bytes when nothing is staged).
+__device__ __forceinline__ void stage_rows(const int8_t* seqs, int64_t r0, int rows, int L, int64_t total,
+                                           uint32_t dst, uint32_t bar)
+{
+    const StageRange g = stage_range(r0, rows, L, total);
+    fence_async_shared();  // earlier reads of the buffer come before the copy's writes
+    if (g.a1 > g.a0) {
+        const uint32_t bytes = (uint32_t)(g.a1 - g.a0);
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_copy_g2s(dst, seqs + g.a0, bytes, bar);
+    } else {
+        mbar_arrive(bar);
+    }
+}
+
+// The neighbourhood of Algorithm 1 for skew-symmetric rows, one warp per row (n > 160),
+// R outputs per lane (R = block_R(n, 32)), NW = ceil(n/32) words per class; with
+// STAGED, rows come through the staging buffers after the rows' shared memory.
+template <int R, int NW, bool STAGED>
 __global__ void __launch_bounds__(256) delta_kernel(const int8_t* __restrict__ seqs, int64_t batch, int L,
                                                     int32_t* __restrict__ out, DevStatus* status)
 {
     extern __shared__ __align__(16) int smem[];
     const int n = (L + 1) / 2, c = n - 1;
-    const WarpSmem SL = warp_smem(n, 32);
+    const WarpSmem SL = row_smem(n, 32);
     const Tile<32> t(threadIdx.x & 31);
     const int lane = t.lane, warp = threadIdx.x >> 5;
     int* base = smem + warp * SL.words;
     const View V = make_view(base, SL);
+    float* Q = reinterpret_cast<float*>(base + SL.poff);
+    const Outs<Tile<32>, R> o(t);
+    // every row writes the same entries of the rows and the table: clear them once
+    clear_rows(base, SL, t);
+    const int SB = stage_bytes(L, 1);
+    const int8_t* stg = reinterpret_cast<const int8_t*>(smem + (blockDim.x >> 5) * SL.words) + warp * (2 * SB + 16);
+    const uint32_t sdst = smem_addr(stg), bar = sdst + 2 * SB;  // two buffers, then two barriers
+    const int64_t total = batch * (int64_t)L;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < batch; row += nwarps) {
-        clear_rows(base, SL, t);
-        const int8_t* src = seqs + row * (int64_t)L;
-        bool ok = true;
-        for (int j = lane; j < L; j += kWarp) {
-            const int v = src[j];
-            ok = ok && (v == 1 || v == -1);
-            if (j & 1) V.A1[j >> 1] = (float)v;
-            else V.A0[j >> 1] = (float)v;
+    const int64_t first = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (STAGED) {
+        if (lane == 0) {
+            mbar_init(bar, 1);
+            mbar_init(bar + 8, 1);
+            mbar_init_fence();
         }
-        t.sync();
-        for (int j = 1 + lane; j <= c; j += kWarp) {  // Eq. 4
-            const int hi = c + j, lo = c - j;
-            const float shi = (hi & 1) ? V.A1[hi >> 1] : V.A0[hi >> 1];
-            const float slo = (lo & 1) ? V.A1[lo >> 1] : V.A0[lo >> 1];
-            ok = ok && (shi == ((j & 1) ? -slo : slo));
+        __syncwarp();
+        if (lane == 0 && first < batch) stage_rows(seqs, first, 1, L, total, sdst, bar);
+    }
+    int it = 0;
+    for (int64_t row = first; row < batch; row += nwarps, ++it) {
+        const int b = it & 1;
+        StageRange g{0, 0};
+        if (STAGED) {
+            const int64_t next = row + nwarps;
+            const bool more = next < batch;
+            if (lane == 0 && more) stage_rows(seqs, next, 1, L, total, sdst + (b ^ 1) * SB, bar + 8 * (b ^ 1));
+            if (!__all_sync(kFull, mbar_wait(bar + 8 * b, (it >> 1) & 1))) {
+                if (lane == 0 && status) raise_error(status, LABS_ECUDA, (int)row);
+                if (more) mbar_wait(bar + 8 * (b ^ 1), ((it + 1) >> 1) & 1);  // the copy in flight
+                return;
+            }
+            g = stage_range(row, 1, L, total);
         }
+        const int64_t rs = row * (int64_t)L;
+        uint32_t x0[NW], x1[NW], xr0[NW], xr1[NW];
+        bool bad = row_load<32, NW, STAGED>(V, seqs + rs, stg + b * SB + (rs - g.a0), g.a1 - rs, true, L, lane, 0,
+                                            x0, x1);
+        reverse_class(x0, n, xr0);
+        reverse_class(x1, n - 1, xr1);
+        const uint32_t f0 = (c & 1) ? ~0u : 0u, f1 = ~f0;  // antipalindromic class: all bits inverted
+        uint32_t diff = 0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k)
+            diff |= (xr0[k] ^ x0[k] ^ (f0 & class_mask(n, k))) | (xr1[k] ^ x1[k] ^ (f1 & class_mask(n - 1, k)));
+        bad |= diff != 0;
         int32_t* dst = out + row * (int64_t)n;
-        if (!__all_sync(kFull, ok)) {
+        if (__any_sync(kFull, bad)) {
             for (int i = lane; i < n; i += kWarp) dst[i] = INT_MIN;
             if (lane == 0 && status) atomicAdd(&status->invalid_rows, 1);
             t.sync();
             continue;
         }
-        build_table(V, n, t);
-        delta_row<R>(V, n, t, dst);
-        t.sync();
+        row_table<32, NW>(V, Q, n, lane, x0, x1, xr0, xr1);
+        t.sync();  // rows, table and Q written
+        int dl[R];
+        {
+            float X[R], P[R];
+            row_p(Q, n, o, P);
+            toeplitz(V, n, o, X);
+            assemble(V, n, o, X, P, dl);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (dl[r] != INT_MAX) dst[2 * (o.v0 + r) + o.p] = dl[r];
+        t.sync();  // the next row overwrites the rows, the table, Q and this staging buffer
     }
 }
 
 // The same for two rows per warp (n <= 160), 16 lanes per row in lockstep: rows r0, r0+1
 // of each warp; R = block_R(n, 16).  The rows' shared memory is cleared once, each row
 // overwrites every entry the previous one set.
-template <int R>
-__global__ void __launch_bounds__(256) delta_pair_kernel(const int8_t* __restrict__ seqs, int64_t batch, int L,
+template <int R, int NW, bool STAGED>
+__global__ void __launch_bounds__(256, R <= 7 ? 3 : 2) delta_pair_kernel(const int8_t* __restrict__ seqs, int64_t batch, int L,
                                                          int32_t* __restrict__ out, DevStatus* status)
 {
     extern __shared__ __align__(16) int smem[];
     const int n = (L + 1) / 2, c = n - 1;
-    const WarpSmem SL = warp_smem(n, 16);
+    const WarpSmem SL = row_smem(n, 16);
     const Pair t(threadIdx.x & 31);
-    const int lane = t.lane;
+    const int lane = t.lane, wl = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* base = smem + (threadIdx.x / 16) * SL.words;
     const View V = make_view(base, SL);
+    float* Q = reinterpret_cast<float*>(base + SL.poff);
     const Outs<Pair, R> o(t);
     clear_rows(base, SL, t);
+    const int SB = stage_bytes(L, 2);
+    const int8_t* stg = reinterpret_cast<const int8_t*>(smem + (blockDim.x >> 4) * SL.words) + warp * (2 * SB + 16);
+    const uint32_t sdst = smem_addr(stg), bar = sdst + 2 * SB;
+    const int64_t total = batch * (int64_t)L;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t r0 = 2 * ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); r0 < batch;
-         r0 += 2 * nwarps) {
+    const int64_t first = 2 * ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp);
+    if (STAGED) {
+        if (wl == 0) {
+            mbar_init(bar, 1);
+            mbar_init(bar + 8, 1);
+            mbar_init_fence();
+        }
+        __syncwarp();
+        if (wl == 0 && first < batch) stage_rows(seqs, first, 2, L, total, sdst, bar);
+    }
+    int it = 0;
+    for (int64_t r0 = first; r0 < batch; r0 += 2 * nwarps, ++it) {
+        const int b = it & 1;
+        StageRange g{0, 0};
+        if (STAGED) {
+            const int64_t next = r0 + 2 * nwarps;
+            const bool more = next < batch;
+            if (wl == 0 && more) stage_rows(seqs, next, 2, L, total, sdst + (b ^ 1) * SB, bar + 8 * (b ^ 1));
+            if (!__all_sync(kFull, mbar_wait(bar + 8 * b, (it >> 1) & 1))) {
+                if (wl == 0 && status) raise_error(status, LABS_ECUDA, (int)r0);
+                if (more) mbar_wait(bar + 8 * (b ^ 1), ((it + 1) >> 1) & 1);  // the copy in flight
+                return;
+            }
+            g = stage_range(r0, 2, L, total);
+        }
         const int64_t row = r0 + t.h;
         const bool has = row < batch;
-        const int8_t* src = seqs + row * (int64_t)L;
-        bool ok = true;
-        if (has) {
-            for (int j = lane; j < L; j += 16) {
-                const int v = src[j];
-                ok = ok && (v == 1 || v == -1);
-                ((j & 1) ? V.A1 : V.A0)[j >> 1] = (float)v;
-            }
-        }
-        t.sync();
-        if (has) {
-            for (int j = 1 + lane; j <= c; j += 16) {  // Eq. 4
-                const int hi = c + j, lo = c - j;
-                const float shi = (hi & 1) ? V.A1[hi >> 1] : V.A0[hi >> 1];
-                const float slo = (lo & 1) ? V.A1[lo >> 1] : V.A0[lo >> 1];
-                ok = ok && (shi == ((j & 1) ? -slo : slo));
-            }
-        }
-        const bool valid = has && t.ballot(!ok) == 0u;
+        const int64_t rs = row * (int64_t)L;
+        uint32_t x0[NW], x1[NW], xr0[NW], xr1[NW];
+        bool bad = row_load<16, NW, STAGED>(V, seqs + rs, stg + b * SB + (rs - g.a0), g.a1 - rs, has, L, lane, t.h,
+                                            x0, x1);
+        reverse_class(x0, n, xr0);
+        reverse_class(x1, n - 1, xr1);
+        const uint32_t f0 = (c & 1) ? ~0u : 0u, f1 = ~f0;
+        uint32_t diff = 0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k)
+            diff |= (xr0[k] ^ x0[k] ^ (f0 & class_mask(n, k))) | (xr1[k] ^ x1[k] ^ (f1 & class_mask(n - 1, k)));
+        bad |= diff != 0;
+        // the ballot is a full-warp collective: both halves take it, with or without a row
+        const unsigned any_bad = t.ballot(bad);
+        const bool valid = has && any_bad == 0u;
         int32_t* dst = out + row * (int64_t)n;
         if (has && !valid) {
             for (int i = lane; i < n; i += 16) dst[i] = INT_MIN;
             if (lane == 0 && status) atomicAdd(&status->invalid_rows, 1);
         }
-        build_table(V, n, t);
+        row_table<16, NW>(V, Q, n, lane, x0, x1, xr0, xr1);
+        t.sync();  // rows, table and Q written
         int dl[R];
         int rv;
         {
             float X[R], P[R];
+            row_p(Q, n, o, P);
             toeplitz(V, n, o, X);
-            p_direct(V, n, o, P);
             rv = lane_dl(V, n, o, X, P, dl);
         }
         if (valid) {
@@ -242,7 +513,7 @@ __global__ void __launch_bounds__(256) delta_pair_kernel(const int8_t* __restric
             for (int r = 0; r < R; ++r)
                 if (r < rv) dst[2 * (o.v0 + r) + o.p] = dl[r];
         }
-        t.sync();
+        t.sync();  // the next rows overwrite the rows, the table, Q and this staging buffer
     }
 }
 
@@ -576,36 +847,54 @@ int launch_isl(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevSt
 int launch_delta(const int8_t* seqs, int64_t batch, int32_t L, int32_t* out, DevStatus* status, void* stream)
 {
     if (batch == 0) return LABS_OK;
-    const int warps = 8, n = (L + 1) / 2;
+    const int warps = 8, n = (L + 1) / 2, nw = (n + 31) / 32;
     using DeltaFn = void (*)(const int8_t*, int64_t, int, int32_t*, DevStatus*);
-    DeltaFn fn;
-    if (block_R(n, 16) <= 10) {  // two rows per warp
-        const size_t smem = (size_t)2 * warps * warp_smem(n, 16).words * sizeof(int);
-        switch (block_R(n, 16)) {
-            case 1: fn = delta_pair_kernel<1>; break;
-            case 2: fn = delta_pair_kernel<2>; break;
-            case 3: fn = delta_pair_kernel<3>; break;
-            case 5: fn = delta_pair_kernel<5>; break;
-            case 6: fn = delta_pair_kernel<6>; break;
-            case 7: fn = delta_pair_kernel<7>; break;
-            case 9: fn = delta_pair_kernel<9>; break;
-            default: fn = delta_pair_kernel<10>; break;
+    const bool pair = n <= 160;
+    const int rows = pair ? 2 : 1;
+    const size_t rows_bytes = (size_t)rows * warps * row_smem(n, pair ? 16 : 32).words * sizeof(int);
+    const size_t stage = (size_t)warps * (2 * stage_bytes(L, rows) + 16);
+    // staged rows need a 16-byte aligned input, and are used where they keep as many CTAs
+    // on an SM as the rows alone (three two-row CTAs of 8 warps, two one-row CTAs)
+    const size_t sm_bytes = 226 * 1024;
+    const size_t cap = pair && block_R(n, 16) <= 7 ? 3 : 2;  // the kernels' launch bounds
+    const size_t ctas_plain = std::min(cap, sm_bytes / rows_bytes);
+    const size_t ctas_staged = std::min(cap, sm_bytes / (rows_bytes + stage));
+    const bool staged = ((uintptr_t)seqs & 15) == 0 && ctas_staged >= ctas_plain;
+    // (lane block, words per class) of every length: block_R(n, 16) and ceil(n/32)
+    // for n <= 160 (two rows per warp), block_R(n, 32) above
+    const int key = 16 * (pair ? block_R(n, 16) : block_R(n, 32)) + nw;
+#define LABS_DELTA_CASE(KIND, R, W)                                         \
+    case 16 * R + W:                                                        \
+        fn = staged ? KIND<R, W, true> : KIND<R, W, false>;                 \
+        break;
+    DeltaFn fn = nullptr;
+    if (pair) {
+        switch (key) {
+            LABS_DELTA_CASE(delta_pair_kernel, 1, 1)
+            LABS_DELTA_CASE(delta_pair_kernel, 2, 1)
+            LABS_DELTA_CASE(delta_pair_kernel, 3, 2)
+            LABS_DELTA_CASE(delta_pair_kernel, 5, 2)
+            LABS_DELTA_CASE(delta_pair_kernel, 5, 3)
+            LABS_DELTA_CASE(delta_pair_kernel, 6, 3)
+            LABS_DELTA_CASE(delta_pair_kernel, 7, 4)
+            LABS_DELTA_CASE(delta_pair_kernel, 9, 4)
+            LABS_DELTA_CASE(delta_pair_kernel, 9, 5)
+            LABS_DELTA_CASE(delta_pair_kernel, 10, 5)
+            default: return LABS_EINVAL;
         }
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        fn<<<row_grid((batch + 1) / 2, warps), warps * kWarp, smem, (cudaStream_t)stream>>>(seqs, batch, L, out,
-                                                                                           status);
-        return status_of(cudaGetLastError());
+    } else {
+        switch (key) {
+            LABS_DELTA_CASE(delta_kernel, 7, 6)
+            LABS_DELTA_CASE(delta_kernel, 7, 7)
+            LABS_DELTA_CASE(delta_kernel, 9, 8)
+            default: return LABS_EINVAL;
+        }
     }
-    const size_t smem = (size_t)warps * warp_smem(n, 32).words * sizeof(int);
-    switch (lanes_for(n, 32)) {
-        case 1: fn = delta_kernel<1>; break;
-        case 3: fn = delta_kernel<3>; break;
-        case 5: fn = delta_kernel<5>; break;
-        case 7: fn = delta_kernel<7>; break;
-        default: fn = delta_kernel<9>; break;
-    }
+#undef LABS_DELTA_CASE
+    const size_t smem = rows_bytes + (staged ? stage : 0);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    fn<<<row_grid(batch, warps), warps * kWarp, smem, (cudaStream_t)stream>>>(seqs, batch, L, out, status);
+    const int64_t units = pair ? (batch + 1) / 2 : batch;
+    fn<<<row_grid(units, warps), warps * kWarp, smem, (cudaStream_t)stream>>>(seqs, batch, L, out, status);
     return status_of(cudaGetLastError());
 }
 

@@ -1,5 +1,6 @@
 // Prints the shared-memory layouts the kernels use (labs_internal.cuh, compiled for the
-// host): one line per (kind, tile, n_max): apad alen gpad glen bvec xoff words R.
+// host): one line per (kind, tile, n_max): apad alen gpad glen bvec xoff words R (the
+// row layout: apad alen gpad glen bvec boff poff words R).
 #define __host__
 #define __device__
 #include <cstdio>
@@ -17,6 +18,12 @@ int main()
             std::printf("warp %d %d %d %d %d %d %d %d %d %d\n", tiles[ti], n, w.apad, w.alen, w.gpad, w.glen, w.bvec,
                         w.xoff, w.words, block_R(n, tiles[ti]));
         }
+    for (int n = 2; n <= kMaxN; ++n) {  // the row kernels: two rows per warp up to n = 160
+        const int tile = n <= 160 ? 16 : 32;
+        const WarpSmem w = row_smem(n, tile);
+        std::printf("row %d %d %d %d %d %d %d %d %d %d %d\n", tile, n, w.apad, w.alen, w.gpad, w.glen, w.bvec,
+                    w.boff, w.poff, w.words, block_R(n, tile));
+    }
     for (int n = kMaxN + 1; n <= kMaxNLong; ++n)
         for (int psl = 0; psl < 2; ++psl) {  // the CTA width of the walk and of the PSL walk
             const int nt = long_threads(n, psl != 0);

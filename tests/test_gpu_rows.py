@@ -81,6 +81,59 @@ def test_neighbor_delta_rejects_bad_rows():
     assert np.array_equal(got[2], oracle.neighbor_delta(rows[2]))
 
 
+def test_neighbor_delta_every_length():
+    """Every odd L = 3..511 (every lane block and word count the row kernels
+    instantiate): two random skew rows, a row with one entry negated (breaks Eq. 4 unless
+    it is the centre) and, at odd batch sizes, the two-rows-per-warp tail."""
+    rng = np.random.default_rng(21)
+    for L in range(3, 512, 2):
+        n = (L + 1) // 2
+        rows = skew_rows(3, L, seed=L)
+        j = int(rng.integers(0, L - 1))
+        j = j if j < n - 1 else j + 1  # any position but the centre
+        rows[2, j] = -rows[2, j]
+        got = labs.neighbor_delta(dev(rows)).cpu().numpy()
+        for b in (0, 1):
+            assert np.array_equal(got[b], oracle.neighbor_delta(rows[b])), (L, b)
+        assert (got[2] == INT32_MIN).all(), (L, j)
+
+
+@pytest.mark.parametrize("L,offset", [(41, 1), (201, 3), (401, 5), (201, 16)])
+def test_neighbor_delta_unaligned_input(L, offset):
+    """Rows starting off a 16-byte boundary are read from global memory directly (no
+    staging copy); offset 16 keeps the staged path with a shifted base."""
+    B = 37
+    rows = skew_rows(B, L, seed=50 + L)
+    buf = torch.zeros(B * L + offset, dtype=torch.int8, device="cuda")
+    buf[offset:] = dev(rows.reshape(-1))
+    view = buf[offset:].view(B, L)
+    assert (view.data_ptr() % 16 == 0) == (offset % 16 == 0)
+    got = labs.neighbor_delta(view).cpu().numpy()
+    for r, g in zip(rows, got):
+        assert np.array_equal(g, oracle.neighbor_delta(r))
+
+
+@pytest.mark.parametrize("L,B", [(3, 1), (3, 2), (5, 3), (41, 1), (201, 1), (401, 1)])
+def test_neighbor_delta_tiny_batches(L, B):
+    """Inputs shorter than one 16-byte block (nothing staged) and single rows."""
+    rows = skew_rows(B, L, seed=7 + L + B)
+    got = labs.neighbor_delta(dev(rows)).cpu().numpy()
+    for r, g in zip(rows, got):
+        assert np.array_equal(g, oracle.neighbor_delta(r))
+
+
+def test_neighbor_delta_many_rows_per_warp():
+    """About ten row pairs per warp (both staging buffers in turn), an odd batch whose
+    byte count is not a multiple of 16 (the last bytes come from global memory), every
+    row checked."""
+    L, B = 41, 150001
+    rows = skew_rows(B, L, seed=77)
+    assert (B * L) % 16 != 0
+    got = labs.neighbor_delta(dev(rows)).cpu().numpy()
+    bad = [b for b in range(B) if not np.array_equal(got[b], oracle.neighbor_delta(rows[b]))]
+    assert not bad, bad[:10]
+
+
 def test_neighbor_delta_large_batch_sampled():
     """The launch shape used for throughput (many rows per warp slot): sampled rows."""
     L, B = 201, 20000

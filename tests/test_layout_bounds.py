@@ -26,18 +26,21 @@ def layouts(tmp_path_factory):
     subprocess.run(["g++", "-std=c++17", "-O1", "-I", os.path.join(ROOT, "include"), "-I",
                     os.path.join(ROOT, "paper_2011_00068_gb300", "csrc"), src, "-o", exe], check=True)
     out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
-    warp, long_ = {}, {}
+    warp, long_, row = {}, {}, {}
     for line in out.splitlines():
         f = line.split()
         v = list(map(int, f[1:]))
-        if f[0] == "warp":
+        if f[0] == "row":
+            row[(v[0], v[1])] = dict(apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], boff=v[7], poff=v[8],
+                                     words=v[9], R=v[10])
+        elif f[0] == "warp":
             tile, n = v[0], v[1]
             warp[(tile, n)] = dict(apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], R=v[9])
         else:
             nt, n = v[0], v[1]
             long_[(nt, n)] = dict(nt=nt, apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], xoff=v[7],
                                   words=v[8], R=v[9], limit=v[10], psl_only=v[11])
-    return warp, long_
+    return warp, long_, row
 
 
 def conflict_free_R(R, tile):
@@ -63,8 +66,8 @@ class Region:
             self.bad.append(("B", what, word))
 
 
-def common(reg, n, tile, R, valid_only):
-    """Rows, Toeplitz window, assembly, table and bit vectors (all layouts)."""
+def common(reg, n, tile, R, valid_only, bits=True):
+    """Rows, Toeplitz window, assembly, table and (bits) bit vectors."""
     c = n - 1
     half = tile // 2
     v0max = (half - 1) * R
@@ -91,6 +94,8 @@ def common(reg, n, tile, R, valid_only):
             reg.g(-m, "mirror E")
         if m < reg.S["gpad"]:
             reg.g(-m - 1, "mirror E.y")
+    if not bits:
+        return
     for p in (0, 1):                        # shifted mismatch counts (table) and P
         np_ = n - 1 if p else n
         for m in (1, 2, 31, 32, 33, n - 2, n - 1):
@@ -105,7 +110,7 @@ def common(reg, n, tile, R, valid_only):
 
 
 def test_warp_layouts(layouts):
-    warp, _ = layouts
+    warp, _, _ = layouts
     bad = []
     for tile in (8, 16, 32):
         for n_max in range(2, 257):
@@ -172,7 +177,7 @@ def test_warp_layouts(layouts):
 
 
 def test_long_layouts(layouts):
-    _, long_ = layouts
+    _, long_, _ = layouts
     bad = []
     # lane blocks compiled for each CTA width (the dispatch in labs_long.cu)
     compiled = {128: {3, 5, 7, 9}, 256: {3, 5, 7, 9}, 512: {5, 7, 9, 11}}
@@ -219,7 +224,7 @@ def test_long_exact_range_bound(layouts):
     """The bound on ISL keeps 16 sqrt((n-1) ISL) + 8L + 32n + 32 below 2^24 (Cauchy-Schwarz
     on sum |C_2m|), the condition for the long kernels' fp32 arithmetic to be exact, and
     stays above the ISL of random starts (about L^2/2) by a factor of at least 2."""
-    _, long_ = layouts
+    _, long_, _ = layouts
     limit = {n: S["limit"] for (_, n), S in long_.items()}
     for n in (257, 1024, 2048, 4096, 5632):
         L = 2 * n - 1
@@ -227,3 +232,42 @@ def test_long_exact_range_bound(layouts):
         assert 16 * ((n - 1) * lim) ** 0.5 + 8 * L + 32 * n + 32 < 2 ** 24
         assert lim > L * L  # twice the mean ISL of random starts
         assert lim < 2 ** 29
+
+
+def test_row_layouts(layouts):
+    """The row kernels (labs_neighbor_delta): two rows per warp (16 lanes) up to n = 160,
+    one per warp above; rows, Toeplitz window, assembly and table as in the walk, and the
+    per-lag P values Q[m], written for m < n and read at max(n_p - 1 - 2v, 0), inside
+    their own region after the bit vectors."""
+    _, _, row = layouts
+    bad = []
+    assert {n for _, n in row} == set(range(2, 257))
+    for (tile, n), S in sorted(row.items()):
+        R = S["R"]
+        reg = Region(S)
+        # the two-row kernel assembles every lane output; the one-row kernel existing ones
+        common(reg, n, tile, R, valid_only=(tile == 32), bits=False)
+        for m in (1, n - 1):                    # the table's mirror writes, unconditional
+            reg.g(-m, "mirror E (row)")
+            reg.g(-m - 1, "mirror E.y (row)")
+        for p in (0, 1):                        # row_load writes entries below the class length
+            reg.a((n - 1 - p), "row load")
+        if S["alen"] - S["apad"] < ((n + 7) & ~7):
+            reg.bad.append(("zero padding to round8(n)", S["alen"] - S["apad"]))
+        if S["gpad"] < n:                       # the table's mirror writes are unconditional
+            reg.bad.append(("gpad below n", S["gpad"]))
+        q_words = (n + 3) & ~3
+        if not (S["poff"] >= S["boff"] and S["poff"] + q_words <= S["words"]):
+            reg.bad.append(("Q region", S["poff"], S["words"]))
+        half = tile // 2
+        for p in (0, 1):
+            np_ = n - p
+            for v in (0, (half - 1) * R + R - 1):       # every lane output, existing or not
+                idx = max(np_ - 1 - 2 * v, 0)
+                if not 0 <= idx < n:
+                    reg.bad.append(("Q read", p, v, idx))
+        if S["words"] % 4:
+            reg.bad.append(("alignment", S["words"]))
+        if reg.bad:
+            bad.append((tile, n, R, reg.bad[:3]))
+    assert not bad, bad[:5]
