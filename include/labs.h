@@ -111,6 +111,12 @@ typedef struct labs_config {
                                        labs_walk); one walker per warp (per CTA for long
                                        sequences); not with LABS_FLAG_BEST_FIRST or
                                        LABS_FLAG_LEARNED */
+#define LABS_FLAG_LEARNED_RESTARTS 512 /* reserve workspace for the restart-only learned mode:
+                                       labs_learned then runs only the restart half of the
+                                       proposal pass (see labs_learned) and the walk keeps its
+                                       plain kernels (two or four walkers per warp); lengths
+                                       up to LABS_MAX_L; not with LABS_FLAG_LEARNED,
+                                       LABS_FLAG_BEST_FIRST or LABS_FLAG_PSL */
 #define LABS_QUEUE_SIZE 32           /* entries of a walker's best-first queue */
 #define LABS_BEST_FIRST_MAX_STEPS (1ll << 28) /* steps per walker the queue order can number */
 #define LABS_BEST_FIRST_MAX_STEPS_LONG (1ll << 21) /* the same for lengths above LABS_MAX_L */
@@ -353,8 +359,10 @@ int labs_log_labels(const labs_log_record *dev_records, int64_t count, int32_t *
 int labs_features(int32_t L, const uint32_t *dev_bits, int64_t stride_words, int64_t count,
                   float *dev_x, void *cuda_stream);
 
-/* Turns the learned mode on (dev_params != NULL) or off.  Needs LABS_FLAG_LEARNED at
- * init.  Before every chunk launch of labs_walk the library then runs a proposal pass:
+/* Turns the learned mode on (dev_params != NULL) or off.  Needs LABS_FLAG_LEARNED (or
+ * LABS_FLAG_LEARNED_RESTARTS) at init.  Before every chunk launch of labs_walk the
+ * library then runs a proposal pass (with LABS_FLAG_LEARNED_RESTARTS only its restart
+ * half, and tau is ignored):
  *   - flip scores of every walker's current state; at the chunk's first step the walker
  *     tries, among the flips with dISL <= (lowest dISL) + tau, the highest-scored
  *     (ties: lowest i) first, and continues in the plain order when none is admissible;

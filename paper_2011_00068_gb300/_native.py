@@ -34,6 +34,7 @@ LABS_FLAG_BEST_FIRST = 32
 LABS_FLAG_PSL = 64
 LABS_FLAG_SECOND_HASH = 128
 LABS_FLAG_STRICT_HT = 256
+LABS_FLAG_LEARNED_RESTARTS = 512
 LABS_QUEUE_SIZE = 32
 LABS_BEST_FIRST_MAX_STEPS = 1 << 28
 LABS_BEST_FIRST_MAX_STEPS_LONG = 1 << 21

@@ -29,7 +29,7 @@ def nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, h) for h in ("labs_internal.cuh", "labs_device.cuh", "labs_nvtx.h", "labs_async.cuh")]
+    files += [os.path.join(CSRC, h) for h in ("labs_internal.cuh", "labs_device.cuh", "labs_nvtx.h", "labs_async.cuh", "labs_tc.cuh")]
     files += [os.path.join(ROOT, "include", "labs.h"), __file__]
     return files
 

@@ -213,15 +213,17 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     if (k.patience < 0 || k.chunk_steps < 0 || k.warps_per_cta < 0 || k.warps_per_cta > 8)
         return fail(c, LABS_EINVAL, "bad patience / chunk_steps / warps_per_cta (0..8)");
     if (nL < 1 || nL > LABS_MAX_GROUPS) return fail(c, LABS_EINVAL, "need 1..%d lengths", LABS_MAX_GROUPS);
-    if ((k.flags & LABS_FLAG_BEST_FIRST) && (k.flags & LABS_FLAG_LEARNED))
-        return fail(c, LABS_EINVAL, "LABS_FLAG_BEST_FIRST and LABS_FLAG_LEARNED do not combine");
+    if ((k.flags & LABS_FLAG_LEARNED) && (k.flags & LABS_FLAG_LEARNED_RESTARTS))
+        return fail(c, LABS_EINVAL, "LABS_FLAG_LEARNED and LABS_FLAG_LEARNED_RESTARTS do not combine");
+    if ((k.flags & LABS_FLAG_BEST_FIRST) && (k.flags & kLearnedAny))
+        return fail(c, LABS_EINVAL, "LABS_FLAG_BEST_FIRST and the learned modes do not combine");
     if ((k.flags & LABS_FLAG_SECOND_HASH) && !(k.flags & LABS_FLAG_BEST_FIRST))
         return fail(c, LABS_EINVAL, "LABS_FLAG_SECOND_HASH needs LABS_FLAG_BEST_FIRST");
-    if ((k.flags & LABS_FLAG_PSL) && (k.flags & (LABS_FLAG_BEST_FIRST | LABS_FLAG_LEARNED)))
-        return fail(c, LABS_EINVAL, "LABS_FLAG_PSL combines with neither LABS_FLAG_BEST_FIRST nor LABS_FLAG_LEARNED");
+    if ((k.flags & LABS_FLAG_PSL) && (k.flags & (LABS_FLAG_BEST_FIRST | kLearnedAny)))
+        return fail(c, LABS_EINVAL, "LABS_FLAG_PSL combines with neither LABS_FLAG_BEST_FIRST nor the learned modes");
     if (nL >= 1 && Ls && valid_long_L(Ls[0])) {
         c->long_mode = true;
-        if (k.flags & (LABS_FLAG_LEARNED | LABS_FLAG_SECOND_HASH))
+        if (k.flags & (kLearnedAny | LABS_FLAG_SECOND_HASH))
             return fail(c, LABS_EINVAL, "lengths above %d run the walk (plain or PSL objective) or the best-first "
                         "search without the second table", LABS_MAX_L);
     }
@@ -272,7 +274,7 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     off = align_up(off + sizeof(int64_t) * kMaxTrace, 256);
     c->off_queue = off;
     off = align_up(off + sizeof(uint32_t) * kMaxChunksPerCall, 256);
-    if (k.flags & LABS_FLAG_LEARNED) {
+    if (k.flags & kLearnedAny) {
         c->off_l_scores = off;
         off = align_up(off + sizeof(float) * (size_t)c->W * c->n_max, 256);
         c->off_l_step = off;
@@ -396,7 +398,7 @@ int push_status(labs_ctx* c)
     h.log = c->log;
     h.log_capacity = c->log_capacity;
     h.log_start = c->log_start;
-    const bool lw = (c->cfg.flags & LABS_FLAG_LEARNED) != 0;
+    const bool lw = (c->cfg.flags & kLearnedAny) != 0;
     h.l_scores = lw ? at<float>(c, c->off_l_scores) : nullptr;
     h.l_score_step = lw ? at<int64_t>(c, c->off_l_step) : nullptr;
     h.l_slot = lw ? at<uint32_t>(c, c->off_l_slot) : nullptr;
@@ -443,10 +445,13 @@ int proposal_pass(labs_ctx* c)
         for (int64_t s0 = G.first; s0 < G.first + G.count; s0 += S) {
             const int64_t cnt = std::min<int64_t>(S, G.first + G.count - s0);
             const float *sc = nullptr, *rs = nullptr;
-            int rc = launch_features(reinterpret_cast<const uint32_t*>(states + s0), sizeof(WalkerState) / 4, cnt,
+            int rc = LABS_OK;
+            if (!(c->cfg.flags & LABS_FLAG_LEARNED_RESTARTS)) {  // flip scores: the full learned mode
+                rc = launch_features(reinterpret_cast<const uint32_t*>(states + s0), sizeof(WalkerState) / 4, cnt,
                                      G.L, x, c->stream);
-            if (!rc) rc = net_forward_ws(c->l_params, x, cnt, G.n, nws, &sc, &rs, c->stream);
-            if (!rc) rc = launch_scores(p, s0, cnt, G.n, sc, c->stream);
+                if (!rc) rc = net_forward_ws(c->l_params, x, cnt, G.n, nws, &sc, &rs, c->stream);
+                if (!rc) rc = launch_scores(p, s0, cnt, G.n, sc, c->stream);
+            }
             if (!rc) rc = launch_candidates(p, s0, cnt, G.n, P, cand, c->stream);
             if (!rc) rc = launch_features(cand, kBitWords, cnt * P, G.L, x, c->stream);
             if (!rc) rc = net_forward_ws(c->l_params, x, cnt * P, G.n, nws, &sc, &rs, c->stream);
@@ -549,7 +554,7 @@ int labs_reset(labs_ctx* c)
         rc = launch_reset(p, grid, block, c->stream);
         if (rc) return fail(c, rc, "reset launch: %s", cudaGetErrorString(cudaGetLastError()));
     }
-    if (c->cfg.flags & LABS_FLAG_LEARNED) {
+    if (c->cfg.flags & kLearnedAny) {
         e = cudaMemsetAsync(c->ws + c->off_l_step, 0xFF, sizeof(int64_t) * (size_t)c->W, c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + c->off_l_valid, 0, sizeof(int32_t) * (size_t)c->W, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "learned state clear");
@@ -938,7 +943,8 @@ int labs_learned(labs_ctx* c, const float* dev_params, int32_t tau, int32_t cand
     int rc = need_ws(c);
     if (rc) return rc;
     if (dev_params) {
-        if (!(c->cfg.flags & LABS_FLAG_LEARNED)) return fail(c, LABS_EINVAL, "context created without LABS_FLAG_LEARNED");
+        if (!(c->cfg.flags & kLearnedAny))
+            return fail(c, LABS_EINVAL, "context created without LABS_FLAG_LEARNED or LABS_FLAG_LEARNED_RESTARTS");
         if (tau < 0 || candidates < 1 || candidates > 64) return fail(c, LABS_EINVAL, "bad tau / candidates");
         if (!dev_ws || ws_bytes < learned_ws_bytes(c, candidates))
             return fail(c, LABS_ENOMEM, "learned workspace needs %zu bytes", learned_ws_bytes(c, candidates));

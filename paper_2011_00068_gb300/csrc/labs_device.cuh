@@ -1934,6 +1934,18 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(K
         env.rdump_count = nullptr;
         env.dump_cap = 0;
         DevStatus* S = p.status;
+        if (MODE == 0 && S->learned) {
+            // restart-only learned mode: the proposed restart state, and its record for
+            // a traced walker
+            env.slot = S->l_slot + wi * kBitWords;
+            env.slot_valid = S->l_slot_valid + wi;
+            if (trace_slot >= 0 && S->d_restart != nullptr) {
+                env.rdump = S->d_restart + (int64_t)trace_slot * S->d_cap * kBitWords;
+                env.rdump_idx = S->d_restart_idx + (int64_t)trace_slot * S->d_cap;
+                env.rdump_count = S->d_restart_count + trace_slot;
+                env.dump_cap = S->d_cap;
+            }
+        }
         if (MODE == 1 && S->learned) {
             env.slot = S->l_slot + wi * kBitWords;
             env.slot_valid = S->l_slot_valid + wi;
@@ -2062,6 +2074,18 @@ __device__ __forceinline__ void walk_group(const KParams& p, int chunk_index)
             int64_t until = min(target, steps_done + (int64_t)p.chunk_steps);
             bool real = real0 && steps_done < until;
             const int trace_slot = real ? env.st->trace_slot : -1;
+            if (real && S->learned) {
+                // restart-only learned mode: the proposed restart state (and its record
+                // for a traced walker)
+                env.slot = S->l_slot + mine_w * kBitWords;
+                env.slot_valid = S->l_slot_valid + mine_w;
+                if (trace_slot >= 0 && S->d_restart != nullptr) {
+                    env.rdump = S->d_restart + (int64_t)trace_slot * S->d_cap * kBitWords;
+                    env.rdump_idx = S->d_restart_idx + (int64_t)trace_slot * S->d_cap;
+                    env.rdump_count = S->d_restart_count + trace_slot;
+                    env.dump_cap = S->d_cap;
+                }
+            }
             const int64_t trace_start = trace_slot >= 0 ? p.trace_start[trace_slot] : 0;
             const int isl = load_rows(base, SL, V, w.word, G.L, G.n, t);
             if (real && isl != w.isl) {

@@ -29,6 +29,9 @@ constexpr uint64_t kGenMask = 0xFFFFFull;    // HT generation field (low 20 bits
 constexpr uint32_t kZobristKey0 = 0x1BADB002u;  // Philox key of the HT fingerprint keys
 constexpr uint32_t kZobristKey1 = 0x2011A068u;
 
+// Either learned mode (full: flip scores and restart proposals; restarts only).
+constexpr int kLearnedAny = LABS_FLAG_LEARNED | LABS_FLAG_LEARNED_RESTARTS;
+
 // One length group: walkers [first, first+count) of length L, n = (L+1)/2 free vars.
 struct DevGroup {
     int32_t L;

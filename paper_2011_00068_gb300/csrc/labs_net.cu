@@ -20,8 +20,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "labs_internal.cuh"
+#include "labs_tc.cuh"
 #include "labs_nvtx.h"
 
 namespace labsgpu {
@@ -55,95 +57,165 @@ __device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ uint32_t ld32(const bf16* p)
-{
-    return *reinterpret_cast<const uint32_t*>(p);
-}
-
 __device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi)
 {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-__device__ __forceinline__ void st2(bf16* p, float a, float b)
-{
-    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
-}
-
 enum { EPI_BIAS_RELU = 0, EPI_MASK = 1, EPI_MASK_POOL = 2 };
 
-// out[b][3+p][o] = epi(sum_{k<TAPS, c<CIN} in[b][p+k+RO][c] * Wt[o][k*CIN+c]) for p < n.
-// One warp computes 16 positions x 64 outputs; the CTA (4 warps) keeps Wt in shared
-// memory with a padded row stride (conflict-free fragment loads).
+// out[b][3+p][o] = epi(sum_{k<TAPS, c<CIN} in[b][p+k+RO][c] * Wt[o][k*CIN+c]) for p < n, on
+// the 5th-generation tensor cores.  The B*P activation rows form
+// one long sequence (the zero rows around each sample keep the samples apart), so output
+// row G (sample b = G / P, position G % P - 3) takes input rows G - 3 + RO + k, k < TAPS:
+// a tile of 128 output rows reads 128 + TAPS - 1 consecutive input rows.  TMA stages them
+// once, in the K-major layout without swizzling (16-byte rows back to back, one column
+// of rows per 8 input channels, kRowsPad rows apart), and tap k is the same operand with
+// its start address 16 k bytes further.  The weights (64 outputs x TAPS CIN) are staged
+// once per CTA in the same layout (64 rows per column of 8 K values).  One thread issues
+// TAPS * CIN/16 MMAs of M = 128, N = 64, K = 16 into 64 TMEM columns; every warp reads
+// its 32 rows back (tcgen05.ld) for the epilogue, which writes only rows of real
+// positions (the zero rows stay zero).
+constexpr int kTcThreads = 128;
+constexpr int kTcTile = 128;  // output rows per tile (the MMA's M)
+
+template <int CIN, int TAPS>
+struct TcShape {
+    static constexpr int KK = TAPS * CIN;
+    static constexpr int RO = 3 - (TAPS - 1) / 2;
+    static constexpr int ROWS = kTcTile + TAPS - 1;              // input rows per tile
+    static constexpr int ROWS_PAD = (ROWS + 7) & ~7;              // 128-byte aligned columns
+    static constexpr int A_COL = ROWS_PAD * 16;                   // bytes per 8-channel column
+    static constexpr int A_BYTES = (CIN / 8) * A_COL;
+    static constexpr int W_BYTES = (KK / 8) * 1024;               // 64 rows x 16 bytes per column
+    static constexpr int BAR_OFF = W_BYTES + A_BYTES;             // three barriers, the TMEM slot
+    static constexpr int BIAS_OFF = BAR_OFF + 32;
+    static constexpr int SMEM = BIAS_OFF + 2 * kC * 4 + 128;       // + alignment slack
+};
+
 template <int CIN, int TAPS, int EPI>
-__global__ void __launch_bounds__(128) rows_gemm_kernel(const bf16* __restrict__ in, const bf16* __restrict__ Wt,
-                                                        const float* __restrict__ bias,
-                                                        const bf16* __restrict__ mask,
-                                                        const float* __restrict__ pool_dr,
-                                                        const bf16* __restrict__ pool_w, bf16* __restrict__ out,
-                                                        int B, int n)
+__global__ void __launch_bounds__(kTcThreads) rows_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                             const __grid_constant__ CUtensorMap tmW,
+                                                             const float* __restrict__ bias,
+                                                             const bf16* __restrict__ mask,
+                                                             const float* __restrict__ pool_dr,
+                                                             const bf16* __restrict__ pool_w, bf16* __restrict__ out,
+                                                             int n, int64_t rows_total, int* __restrict__ err)
 {
-    constexpr int KK = TAPS * CIN;
-    constexpr int KS = KK + 8;  // padded smem row stride (elements)
-    constexpr int RO = 3 - (TAPS - 1) / 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    bf16* ws = reinterpret_cast<bf16*>(smem_raw);
-    for (int t = threadIdx.x; t < kC * KK / 2; t += blockDim.x) {
-        const int o = (2 * t) / KK, kk = (2 * t) % KK;
-        *reinterpret_cast<uint32_t*>(ws + o * KS + kk) = ld32(Wt + 2 * t);
-    }
-    __syncthreads();
+    using S = TcShape<CIN, TAPS>;
+    extern __shared__ unsigned char tc_smem_raw[];
+    // 128-byte aligned base for the TMA destinations
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 127) & ~uintptr_t(127));
+    const uint32_t sW = smem_addr(sm), sA = sW + S::W_BYTES;
+    const uint32_t bar_w = sW + S::BAR_OFF, bar_a = bar_w + 8, bar_m = bar_w + 16, slot = bar_w + 24;
+    float* sbias = reinterpret_cast<float*>(sm + S::BIAS_OFF);
+    float* spool = sbias + kC;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int P = rows_per_sample(n);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
-    const int mtiles = (n + 15) >> 4;
-    const int64_t total = (int64_t)B * mtiles;
-    for (int64_t tile = (int64_t)blockIdx.x * 4 + warp; tile < total; tile += (int64_t)gridDim.x * 4) {
-        const int b = (int)(tile / mtiles), p0 = (int)(tile % mtiles) * 16;
-        const bf16* src = in + (int64_t)b * P * CIN;
-        float acc[8][4];
+    const int64_t tiles = (rows_total + kTcTile - 1) / kTcTile;
+    if (threadIdx.x < kC) {
+        sbias[threadIdx.x] = (EPI == EPI_BIAS_RELU) ? bias[threadIdx.x] : 0.f;
+        spool[threadIdx.x] = (EPI == EPI_MASK_POOL) ? __bfloat162float(pool_w[threadIdx.x]) / (float)n : 0.f;
+    }
+    if (warp == 0) tmem_alloc(slot, 64);
+    if (threadIdx.x == 0) {
+        mbar_init(bar_w, 1);
+        mbar_init(bar_a, 1);
+        mbar_init(bar_m, 1);
+        mbar_init_fence();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + S::BAR_OFF + 24);
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(bar_w, S::W_BYTES);
+        for (int j = 0; j < S::KK / 8; ++j) tma_load_2d(sW + 1024 * j, &tmW, 8 * j, 0, bar_w);
+        ok = mbar_wait(bar_w, 0);
+    }
+    constexpr uint32_t idesc = idesc_bf16_f32(kTcTile, kC);
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+        const int64_t G0 = tile * kTcTile;
+        if (threadIdx.x == 0 && ok) {
+            mbar_arrive_expect_tx(bar_a, S::A_BYTES / S::ROWS_PAD * S::ROWS);
+            for (int j = 0; j < CIN / 8; ++j)
+                tma_load_2d(sA + S::A_COL * j, &tmA, 8 * j, (int)(G0 - 3 + S::RO), bar_a);
+            ok = mbar_wait(bar_a, it & 1);
+            if (ok) {
+                tc_fence_after();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+                for (int k = 0; k < TAPS; ++k)
 #pragma unroll
-        for (int k = 0; k < TAPS; ++k) {
-            const bf16* r0 = src + (int64_t)(p0 + g + k + RO) * CIN + tig * 2;
-            const bf16* r1 = r0 + 8 * CIN;
-#pragma unroll
-            for (int c0 = 0; c0 < CIN; c0 += 16) {
-                const uint32_t a0 = ld32(r0 + c0), a1 = ld32(r1 + c0), a2 = ld32(r0 + c0 + 8), a3 = ld32(r1 + c0 + 8);
-                const bf16* wb = ws + g * KS + k * CIN + c0 + tig * 2;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const bf16* w = wb + j * 8 * KS;
-                    mma16816(acc[j], a0, a1, a2, a3, ld32(w), ld32(w + 8));
-                }
-            }
-        }
-        bf16* dst = out + (int64_t)b * P * kC;
-        const bf16* msk = mask ? mask + (int64_t)b * P * kC : nullptr;
-        const float pdr = (EPI == EPI_MASK_POOL) ? pool_dr[b] : 0.f;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int p = p0 + g + 8 * h;
-            if (p >= n) continue;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int o = 8 * j + tig * 2;
-                float v0 = acc[j][2 * h], v1 = acc[j][2 * h + 1];
-                if (EPI == EPI_BIAS_RELU) {
-                    v0 = fmaxf(v0 + bias[o], 0.f);
-                    v1 = fmaxf(v1 + bias[o + 1], 0.f);
-                } else {
-                    if (EPI == EPI_MASK_POOL) {
-                        v0 += __bfloat162float(pool_w[o]) * pdr / (float)n;
-                        v1 += __bfloat162float(pool_w[o + 1]) * pdr / (float)n;
+                    for (int s2 = 0; s2 < CIN / 16; ++s2) {
+                        const uint64_t ad = smem_desc(sA + 16 * k + 2 * s2 * S::A_COL, S::A_COL, 128);
+                        const uint64_t bd = smem_desc(sW + (k * (CIN / 8) + 2 * s2) * 1024, 1024, 128);
+                        tc_mma_bf16(tmem, ad, bd, idesc, (k | s2) != 0);
                     }
-                    const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(msk + (int64_t)(p + 3) * kC + o);
-                    if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
-                    if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
-                }
-                st2(dst + (int64_t)(p + 3) * kC + o, v0, v1);
+                tc_commit(bar_m);
             }
         }
+        // every thread waits for the accumulator (a failed copy or wait skips the tile)
+        ok = __syncthreads_and(ok) && mbar_wait(bar_m, it & 1);
+        ok = __syncthreads_and(ok);
+        if (!ok) {
+            if (threadIdx.x == 0) atomicExch(err, 1);
+            break;
+        }
+        tc_fence_after();
+        float acc[64];
+        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float v[16];
+            tmem_ld16(trow + 16 * q, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[16 * q + i] = v[i];
+        }
+        tc_wait_ld();
+        const int64_t G = G0 + 32 * warp + lane;
+        const int b = (int)(G / P), p = (int)(G % P) - 3;
+        if (G < rows_total && p >= 0 && p < n) {
+            bf16* dst = out + G * kC;
+            const float pdr = (EPI == EPI_MASK_POOL) ? pool_dr[b] : 0.f;
+#pragma unroll
+            for (int c8 = 0; c8 < kC / 8; ++c8) {
+                uint4 mk = make_uint4(0u, 0u, 0u, 0u);
+                if (EPI != EPI_BIAS_RELU) mk = *reinterpret_cast<const uint4*>(mask + G * kC + 8 * c8);
+                const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
+                uint32_t pk[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int o = 8 * c8 + 2 * h;
+                    float v0 = acc[o], v1 = acc[o + 1];
+                    if (EPI == EPI_BIAS_RELU) {
+                        v0 = fmaxf(v0 + sbias[o], 0.f);
+                        v1 = fmaxf(v1 + sbias[o + 1], 0.f);
+                    } else {
+                        if (EPI == EPI_MASK_POOL) {
+                            v0 += spool[o] * pdr;
+                            v1 += spool[o + 1] * pdr;
+                        }
+                        const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162*>(&mw[h]);
+                        if (!(__bfloat162float(m2.x) > 0.f)) v0 = 0.f;
+                        if (!(__bfloat162float(m2.y) > 0.f)) v1 = 0.f;
+                    }
+                    const __nv_bfloat162 r2 = __floats2bfloat162_rn(v0, v1);
+                    pk[h] = *reinterpret_cast<const uint32_t*>(&r2);
+                }
+                *reinterpret_cast<uint4*>(dst + 8 * c8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+        }
+        // the next tile's copy overwrites the operand and its MMAs the accumulator
+        tc_fence_before();
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 64);
     }
 }
 
@@ -418,17 +490,61 @@ __global__ void init_kernel(float* __restrict__ prm, uint64_t seed)
     }
 }
 
-template <int CIN, int TAPS, int EPI>
-int launch_rows(const bf16* in, const bf16* Wt, const float* bias, const bf16* mask, const float* pdr,
-                const bf16* pw, bf16* out, int B, int n, int sms, cudaStream_t s)
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (the
+// library links no driver library of its own).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled()
 {
-    const size_t smem = (size_t)kC * (TAPS * CIN + 8) * sizeof(bf16);
-    auto fn = rows_gemm_kernel<CIN, TAPS, EPI>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    });
+    return fn;
+}
+
+// Row-major BF16 matrix [outer][inner] (rows 2 inner bytes apart, a multiple of 16), read
+// in boxes of box_outer rows x box_inner values; reads outside the matrix give zeros.
+bool map_rows(CUtensorMap* m, const bf16* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+              uint32_t box_outer)
+{
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {inner * sizeof(bf16)};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int CIN, int TAPS, int EPI>
+int launch_rows_tc(const bf16* in, const bf16* Wt, const float* bias, const bf16* mask, const float* pdr,
+                   const bf16* pw, bf16* out, int B, int n, int sms, int* err, cudaStream_t s)
+{
+    using S = TcShape<CIN, TAPS>;
+    const int64_t rows = (int64_t)B * rows_per_sample(n);
+    CUtensorMap ma, mw;
+    if (!map_rows(&ma, in, CIN, (uint64_t)rows, 8, S::ROWS) || !map_rows(&mw, Wt, S::KK, kC, 8, kC))
         return LABS_ECUDA;
-    const int64_t tiles = (int64_t)B * ((n + 15) >> 4);
-    const int grid = (int)std::min<int64_t>((tiles + 3) / 4, (int64_t)sms * 8);
-    fn<<<grid, 128, smem, s>>>(in, Wt, bias, mask, pdr, pw, out, B, n);
+    auto fn = rows_tc_kernel<CIN, TAPS, EPI>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) != cudaSuccess)
+        return LABS_ECUDA;
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTcThreads, S::SMEM) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int64_t tiles = (rows + kTcTile - 1) / kTcTile;
+    const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * per_sm);
+    fn<<<grid, kTcThreads, S::SMEM, s>>>(ma, mw, bias, mask, pdr, pw, out, n, rows, err);
     return cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ECUDA;
 }
 
@@ -447,6 +563,7 @@ int launch_wgrad(const bf16* G, const bf16* IN, float* dW, int B, int n, int sms
 struct NetWs {
     bf16 *X0, *A1, *A2, *A3, *H, *dH, *dA3, *dA2, *dA1, *wpk;
     float *score, *restart, *pooled, *ds, *dr, *loss;
+    int* err;  // set by a tensor-core kernel whose copy or MMA wait gave up
     size_t bytes;
 };
 
@@ -483,6 +600,7 @@ NetWs carve(void* base, int64_t B, int n)
     w.dr = (float*)take((size_t)B * 4);
     w.pooled = (float*)take((size_t)B * kC * 4);
     w.loss = (float*)take(4);
+    w.err = (int*)take(4);
     w.bytes = off;
     return w;
 }
@@ -500,14 +618,14 @@ int forward(const float* prm, const NetWs& w, int B, int n, cudaStream_t s)
 {
     const int sms = sm_count();
     pack_kernel<<<64, 256, 0, s>>>(prm, w.wpk);
-    int rc = launch_rows<kCin, kTaps, EPI_BIAS_RELU>(w.X0, w.wpk + pWf1, prm + oB1, nullptr, nullptr, nullptr, w.A1, B,
-                                                     n, sms, s);
-    if (!rc) rc = launch_rows<kC, kTaps, EPI_BIAS_RELU>(w.A1, w.wpk + pWf2, prm + oB2, nullptr, nullptr, nullptr, w.A2,
-                                                        B, n, sms, s);
-    if (!rc) rc = launch_rows<kC, kTaps, EPI_BIAS_RELU>(w.A2, w.wpk + pWf3, prm + oB3, nullptr, nullptr, nullptr, w.A3,
-                                                        B, n, sms, s);
-    if (!rc) rc = launch_rows<kC, 1, EPI_BIAS_RELU>(w.A3, w.wpk + pWf4, prm + oB4, nullptr, nullptr, nullptr, w.H, B, n,
-                                                    sms, s);
+    int rc = launch_rows_tc<kCin, kTaps, EPI_BIAS_RELU>(w.X0, w.wpk + pWf1, prm + oB1, nullptr, nullptr, nullptr, w.A1,
+                                                        B, n, sms, w.err, s);
+    if (!rc) rc = launch_rows_tc<kC, kTaps, EPI_BIAS_RELU>(w.A1, w.wpk + pWf2, prm + oB2, nullptr, nullptr, nullptr,
+                                                           w.A2, B, n, sms, w.err, s);
+    if (!rc) rc = launch_rows_tc<kC, kTaps, EPI_BIAS_RELU>(w.A2, w.wpk + pWf3, prm + oB3, nullptr, nullptr, nullptr,
+                                                           w.A3, B, n, sms, w.err, s);
+    if (!rc) rc = launch_rows_tc<kC, 1, EPI_BIAS_RELU>(w.A3, w.wpk + pWf4, prm + oB4, nullptr, nullptr, nullptr, w.H,
+                                                       B, n, sms, w.err, s);
     if (rc) return rc;
     head_kernel<<<std::min(B, sms * 8), 128, 0, s>>>(w.H, w.A3, w.wpk, prm, w.score, w.pooled, w.restart, B, n);
     return cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ECUDA;
@@ -532,18 +650,18 @@ int backward(const float* prm, const NetWs& w, const int32_t* target, const floa
     // h = relu(W4 a3 + b4): dW4, db4, then da3 = (W4^T dh + w6 dr / n) * (a3 > 0)
     if (!rc) rc = launch_wgrad<kC, 1>(w.dH, w.A3, grad + oW4, B, n, sms, s);
     colsum_kernel<<<sms * 4, 256, 0, s>>>(w.dH, grad + oB4, B, n);
-    if (!rc) rc = launch_rows<kC, 1, EPI_MASK_POOL>(w.dH, w.wpk + pWb4, nullptr, w.A3, w.dr, w.wpk + pW6, w.dA3, B, n,
-                                                    sms, s);
+    if (!rc) rc = launch_rows_tc<kC, 1, EPI_MASK_POOL>(w.dH, w.wpk + pWb4, nullptr, w.A3, w.dr, w.wpk + pW6, w.dA3,
+                                                       B, n, sms, w.err, s);
     // conv3
     if (!rc) rc = launch_wgrad<kC, kTaps>(w.dA3, w.A2, grad + oW3, B, n, sms, s);
     colsum_kernel<<<sms * 4, 256, 0, s>>>(w.dA3, grad + oB3, B, n);
-    if (!rc) rc = launch_rows<kC, kTaps, EPI_MASK>(w.dA3, w.wpk + pWb3, nullptr, w.A2, nullptr, nullptr, w.dA2, B, n,
-                                                   sms, s);
+    if (!rc) rc = launch_rows_tc<kC, kTaps, EPI_MASK>(w.dA3, w.wpk + pWb3, nullptr, w.A2, nullptr, nullptr, w.dA2, B,
+                                                      n, sms, w.err, s);
     // conv2
     if (!rc) rc = launch_wgrad<kC, kTaps>(w.dA2, w.A1, grad + oW2, B, n, sms, s);
     colsum_kernel<<<sms * 4, 256, 0, s>>>(w.dA2, grad + oB2, B, n);
-    if (!rc) rc = launch_rows<kC, kTaps, EPI_MASK>(w.dA2, w.wpk + pWb2, nullptr, w.A1, nullptr, nullptr, w.dA1, B, n,
-                                                   sms, s);
+    if (!rc) rc = launch_rows_tc<kC, kTaps, EPI_MASK>(w.dA2, w.wpk + pWb2, nullptr, w.A1, nullptr, nullptr, w.dA1, B,
+                                                      n, sms, w.err, s);
     // conv1
     if (!rc) rc = launch_wgrad<kCin, kTaps>(w.dA1, w.X0, grad + oW1, B, n, sms, s);
     colsum_kernel<<<sms * 4, 256, 0, s>>>(w.dA1, grad + oB1, B, n);

@@ -116,3 +116,20 @@ def test_missing_or_short_workspace_is_enomem():
         assert lib.labs_sync(ctx) == 0
     finally:
         lib.labs_destroy(ctx)
+
+
+def test_learned_flags_reject_bad_combinations():
+    lib = labs.library()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for flags in (_native.LABS_FLAG_LEARNED | _native.LABS_FLAG_LEARNED_RESTARTS,
+                  _native.LABS_FLAG_LEARNED_RESTARTS | _native.LABS_FLAG_BEST_FIRST,
+                  _native.LABS_FLAG_LEARNED_RESTARTS | _native.LABS_FLAG_PSL):
+        cfg = labs.config(tabu_log2=8, flags=flags)
+        ctx = ctypes.c_void_p()
+        rc = lib.labs_init(ctypes.byref(ctx), 41, 4, 1, ctypes.byref(cfg), stream)
+        assert rc == _native.LABS_EINVAL, flags
+        lib.labs_destroy(ctx)
+    cfg = labs.config(tabu_log2=8, flags=_native.LABS_FLAG_LEARNED_RESTARTS)
+    ctx = ctypes.c_void_p()
+    assert lib.labs_init(ctypes.byref(ctx), 1025, 4, 1, ctypes.byref(cfg), stream) == _native.LABS_EINVAL
+    lib.labs_destroy(ctx)

@@ -160,6 +160,69 @@ def test_learned_walk_replays_bit_exactly(L, W, steps, chunk, tau, cands):
     print("recorded scores: worst error / bound %.3f" % worst)
 
 
+@pytest.mark.parametrize("L,W,chunk,cands", [(61, 16, 64, 4), (101, 8, 50, 3), (41, 12, 40, 2)])
+def test_restart_only_learned_walk_replays_bit_exactly(L, W, chunk, cands):
+    """LABS_FLAG_LEARNED_RESTARTS: the walk keeps its plain kernels (four walkers per
+    warp at L = 41 and 61, two at L = 101) and takes the network's restart proposals;
+    replayed by the oracle from the recorded restart states, bit for bit, and every
+    recorded restart state is one of the walker's candidates (its own next random start
+    or a further Philox start)."""
+    seed, steps = 5, 10 * chunk
+    s = labs.Search(L, W, seed, chunk_steps=chunk, flags=_native.LABS_FLAG_LEARNED_RESTARTS, patience=30)
+    assert s.stats()["walkers_per_warp"] in (2, 4)
+    params = lrn.init_params(9)
+    s.learned(params, candidates=cands)
+    code, isl = s.trace(list(range(W)), steps)
+    cap = steps // 4 + 64
+    d = s.trace_learned(W, cap, (L + 1) // 2)
+    s.walk(steps)
+    s.sync()
+    code, isl = code.cpu().numpy(), isl.cpu().numpy()
+    res = s.results(seqs=True)
+    dd = {k: v.cpu().numpy() for k, v in d.items()}
+    used = 0
+    for w in range(W):
+        assert int(dd["score_count"][w]) == 0  # no flip scores in this mode
+        nr = int(dd["restart_count"][w])
+        used += nr
+        o = oracle.walk_replay(L, seed, w, steps, tau=0, score_steps=[], scores=np.zeros((0, 1), np.float32),
+                               restart_idx=dd["restart_idx"][w, :nr],
+                               restart_bits=dd["restart"][w, :nr].view(np.uint32), patience=30)
+        assert np.array_equal(code[w], o["trace_code"]), w
+        assert np.array_equal(isl[w], o["trace_isl"]), w
+        assert np.array_equal(res["best_seq"][w], o["best_seq"])
+        for k in range(nr):
+            ridx = int(dd["restart_idx"][w, k])
+            got = dd["restart"][w, k].view(np.uint32)
+            assert any(np.array_equal(got, cand) for cand in restart_candidates(seed, w, ridx, L, cands)), (w, k)
+    assert used > 0
+    s.close()
+
+
+def restart_candidates(seed, w, ridx, L, cands):
+    """Free-variable words of walker w's restart candidates at restart index ridx:
+    candidate 0 its own random start, candidate c >= 1 the Philox4x32-10 blocks with
+    key (seed lo, seed hi) and counter (w, ridx, block, c), word j = word j % 4 of block
+    j / 4, bits at or above n cleared."""
+    n = (L + 1) // 2
+    out = []
+    x = oracle.random_start(seed, w, ridx, L)
+    words = np.zeros(8, np.uint32)
+    for i in range(n):
+        if x[i] < 0:
+            words[i // 32] |= np.uint32(1 << (i % 32))
+    out.append(words)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for c in range(1, cands):
+        words = np.zeros(8, np.uint32)
+        for j in range(8):
+            v = int(oracle.philox4x32_10([w, ridx, j >> 2, c], key)[j & 3])
+            lo = 32 * j
+            words[j] = 0 if n <= lo else (v if n - lo >= 32 else v & ((1 << (n - lo)) - 1))
+        out.append(words)
+    return out
+
+
 def test_training_on_the_walk_log_lowers_the_loss():
     L = 61
     recs = lrn.collect(L, walkers=512, chunks=16, seed=7, chunk_steps=64)
