@@ -236,7 +236,7 @@ def test_training_on_the_walk_log_lowers_the_loss():
 def test_learned_vs_plain_comparison():
     """What the trained network changes, on identical walkers (same seed, length and step
     budget): the plain walk against the restart-only learned mode, which keeps the plain
-    walk's kernel (two walkers per warp at L = 101) and lets the network pick restart
+    walk's kernel (four walkers per warp at L = 101) and lets the network pick restart
     states.  Measured here: the restart choices neither break the search nor improve it
     beyond noise -- the mean best F per walker stays within 1% of the plain walk's (the
     measured difference, printed, was +0.05% at L = 101 and +0.04% at L = 255 over three
@@ -248,7 +248,7 @@ def test_learned_vs_plain_comparison():
     tr = lrn.Trainer(L, batch=512, seed=seed + 2)
     losses = tr.fit(recs, steps=300, seed=seed + 3)
     assert np.mean(losses[-20:]) < np.mean(losses[:20])
-    out = {}
+    out, wpw = {}, {}
     for arm, flags in (("plain", 0), ("restarts", _native.LABS_FLAG_LEARNED_RESTARTS)):
         s = labs.Search(L, W, seed, flags=flags, chunk_steps=256)
         if flags:
@@ -257,10 +257,11 @@ def test_learned_vs_plain_comparison():
         s.sync()
         st = s.stats()
         assert st["steps"] == W * steps
-        assert st["walkers_per_warp"] == 2  # the plain kernel in both arms
+        wpw[arm] = st["walkers_per_warp"]
         out[arm] = float((L * L / (2.0 * s.results()["best_isl"].astype(np.float64))).mean())
         s.close()
     torch.cuda.synchronize()
+    assert wpw["plain"] == wpw["restarts"] == 4  # the same plain kernel in both arms
     gain = out["restarts"] / out["plain"] - 1.0
     print("mean best F per walker: plain %.4f, learned restarts %.4f (%+.3f%%)" % (out["plain"], out["restarts"],
                                                                                 100 * gain))

@@ -137,3 +137,48 @@ def test_init_is_bounded_and_seeded():
     assert torch.equal(a, b)
     assert np.abs(pa["W2"]).max() <= np.sqrt(6 / 448) + 1e-6 and np.abs(pa["W2"]).std() > 0.01
     assert np.all(pa["b2"] == 0)
+
+
+def test_forward_large_batch_sampled():
+    """B = 2048 states of n = 101 (1888 tiles of 128 rows: several tiles per CTA, so the
+    operand and accumulator barriers run through many phases): sampled states against
+    the oracle, element by element."""
+    n, B = 101, 2048
+    params, x = random_case(n, B, seed=7)
+    sc, rs = gpu_forward(ln.flatten(params), x)
+    net = ln.Net(True)
+    xo = oracle_x(x)
+    rng = np.random.default_rng(8)
+    for b in sorted(set(rng.choice(B, 24, replace=False).tolist()) | {0, B - 1}):
+        fw = net.forward(params, xo[b])
+        assert_close(sc[b], fw["score"], "score of sample %d" % b)
+        terms = float(np.abs(fw["W"]["w6"] * fw["pooled"]).sum() + abs(params["b6"][0]))
+        assert_close(rs[b], fw["restart"], "restart score of sample %d" % b, scale=terms)
+
+
+def test_gradients_large_batch():
+    """B = 1024 states of n = 101: each weight-gradient CTA reduces several blocks of 64
+    rows and the per-CTA partials are summed; every gradient entry against the oracle."""
+    n, B = 101, 1024
+    params, x = random_case(n, B, seed=9)
+    rng = np.random.default_rng(10)
+    target = rng.integers(0, n, B).astype(np.int32)
+    y = rng.standard_normal(B).astype(np.float32)
+    wf = (rng.random(B) < 0.7).astype(np.float32)
+    ws, wb = net_ws(n, B)
+    p = torch.from_numpy(ln.flatten(params)).cuda()
+    g = torch.empty_like(p)
+    loss = torch.zeros(1, device="cuda")
+    s = torch.cuda.current_stream()
+    xd, td, yd, wd = (torch.from_numpy(a).cuda() for a in (x, target, y, wf))
+    assert lib().labs_net_gradients(ptr(p), ptr(xd), ptr(td), ptr(yd), ptr(wd), B, n, ptr(g), ptr(loss), ptr(ws), wb,
+                                    ctypes.c_void_p(s.cuda_stream)) == 0
+    torch.cuda.synchronize()
+    gpu = ln.unflatten(g.cpu().numpy())
+    oloss, og = ln.Net(True).batch_loss_and_grads(params, list(oracle_x(x)), target, y, wf)
+    assert_close(loss.item(), oloss, "loss", scale=0.0)
+    worst = 0.0
+    for name, _ in ln.PARAM_SHAPES:
+        scale = 1e-3 if name == "b5" else None
+        worst = max(worst, assert_close(gpu[name], og[name], "gradient of " + name, scale=scale))
+    print("B=%d: worst gradient error / bound %.3f" % (B, worst))
