@@ -29,6 +29,7 @@
 // along u.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -418,6 +419,100 @@ __device__ __forceinline__ void toeplitz(const View& V, int n, const Outs<TL, R>
     toeplitz_part<R, 0, R>(A, V.G - o.v0, (n + 7) & ~7, X);
 }
 
+// The Toeplitz products of both walkers of a warp (two walkers per warp) on the tensor
+// cores, for n <= 128.  In blocks of 16, u = 16 s + j and v = 16 t + i, the product is
+//   X_t = sum_d T_d A_{t+d},   T_d[i][j] = E[16 d + j - i],   A_s[j] = A_p[16 s + j],
+// a sum over the block diagonals d of a 16 x 16 Toeplitz block of the table times the
+// row blocks d further.  One mma.sync.m16n8k16 per diagonal takes T_d (rows i, columns
+// j) and, as its 8 columns, the row blocks of output blocks t = 0..3 of both classes
+// (columns 0-3 class 0, 4-7 class 1); d runs from -(T-1) to S-1 for the T output and S
+// row blocks.  The table's entries are rounded to FP16 as they are loaded (|E| < 2^11
+// is exact), the rows come from their FP16 copies (A = 0, +-1), and the products
+// accumulate in FP32: every partial sum is an integer below 2^24, so the result equals
+// the FP32 product's.  Reads outside the class meet the rows' zero padding, and E is
+// finite (zero) beyond the table.  The warp writes each walker's results to its
+// scratch X[2][xp], and every lane then reads its R outputs.
+__device__ __forceinline__ uint32_t half2_bits(float2 v)
+{
+    const __half2 h = __float22half2_rn(v);  // .x in the low half
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__device__ __forceinline__ void mma_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                          uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// One block diagonal of one walker: T_d from the table pairs at gy (and the pair 8 below,
+// carried in am8), the row blocks' FP16 pairs at ab.
+__device__ __forceinline__ void tc_diag(float (&d)[4], const float2* gy, const uint32_t* ab, uint32_t& am8)
+{
+    const uint32_t a0 = half2_bits(gy[0]), a2 = half2_bits(gy[8]);
+    mma_16816(d, a0, am8, a2, a0, ab[0], ab[4]);
+    am8 = a2;
+}
+
+// The FP16 copies of the rows, from the FP32 rows (their padding is zero already).
+template <class TL>
+__device__ __forceinline__ void half_rows(int* base, const WarpSmem& SL, const View& V, int n, const TL& t)
+{
+    __half* H = reinterpret_cast<__half*>(base + SL.hoff) + kTcPad;
+    for (int j = t.lane; j < 2 * n; j += TL::kSize) {
+        const int p = j >= n, u = p ? j - n : j;
+        if (u < n - p) H[p * 2 * SL.hlen + u] = __float2half_rn((p ? V.A1 : V.A0)[u]);
+    }
+    t.sync();
+}
+
+template <int R>
+__device__ __forceinline__ void toeplitz_tc(const View& V, const WarpSmem& SL, int n, const Outs<Pair, R>& o, int h,
+                                            float (&X)[R])
+{
+    const int l = threadIdx.x & 31, g = l >> 2, tq = l & 3;
+    const int S = (n + 15) >> 4;               // row blocks
+    const int T = (((n + 1) >> 1) + 15) >> 4;  // output blocks per class (<= 4)
+    const int pb = g >> 2, tb = g & 3;         // this lane's operand column: class, block
+    const int px = tq >> 1, tx = 2 * (tq & 1); // its accumulator columns: class, first block
+    int* const own = reinterpret_cast<int*>(V.A0) - SL.apad;
+    int* const base0 = own - h * SL.words;     // walker 0 of the warp; walker 1 follows
+    const float2* gy = reinterpret_cast<const float2*>(base0 + SL.goff) + SL.gpad + (2 * tq - g - 16 * (T - 1));
+    const uint32_t* ab = reinterpret_cast<const uint32_t*>(base0 + SL.hoff + pb * SL.hlen) + (kTcPad >> 1) +
+                         8 * (tb - (T - 1)) + tq;
+    const int nd = S + T - 1, w1 = SL.words, g1 = SL.words >> 1;
+    // two independent accumulator chains, one per walker
+    float d0[4] = {0.f, 0.f, 0.f, 0.f}, e0[4] = {0.f, 0.f, 0.f, 0.f};
+    uint32_t am0 = half2_bits(gy[-8]), am1 = half2_bits(gy[g1 - 8]);
+    for (int k = 0; k < nd; ++k) {
+        tc_diag(d0, gy, ab, am0);
+        tc_diag(e0, gy + g1, ab + w1, am1);
+        gy += 16;
+        ab += 8;
+    }
+    float* xp = reinterpret_cast<float*>(base0 + SL.xoff) + px * SL.xp + 16 * tx + g;
+    float* xq = xp + w1;
+    if (tx < T) {
+        xp[0] = d0[0];
+        xp[8] = d0[2];
+        xq[0] = e0[0];
+        xq[8] = e0[2];
+    }
+    if (tx + 1 < T) {
+        xp[16] = d0[1];
+        xp[24] = d0[3];
+        xq[16] = e0[1];
+        xq[24] = e0[3];
+    }
+    __syncwarp();
+    const float* xr = reinterpret_cast<const float*>(own + SL.xoff) + o.p * SL.xp + o.v0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) X[r] = xr[r];
+}
+
 // P_v = sum_{m=1}^{v} A_p[v+m] A_p[v-m] from scratch for the lane's outputs, from the
 // bit-packed classes (built by build_table): the pairs compare bits v+1.. of the
 // class with bits n_p-v.. of the reversed class, P_v = v - 2 #{mismatches}.
@@ -520,6 +615,7 @@ __device__ __forceinline__ int load_rows(int* base, const WarpSmem& SL, const Vi
 {
     clear_rows(base, SL, t);
     rows_from_bits(V, word, L, n, t);
+    if (SL.hoff) half_rows(base, SL, V, n, t);
     return build_table(V, n, t);
 }
 
@@ -1249,7 +1345,9 @@ __device__ __forceinline__ int target_isl(const KParams& p, int L)
 // Outcome of probing HT for a candidate.
 enum : int { kProbeFree = 0, kProbeVisited = 1, kProbeUnknown = 2, kProbeNone = 3 };
 
-template <class LG, class RT, int R>
+// TC: the Toeplitz product on the tensor cores (two walkers per warp): 0 never, 1 always,
+// 2 when the layout holds the FP16 rows (n_max <= 128).
+template <class LG, class RT, int R, int TC = 0>
 __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool real, int* base, const WarpSmem& SL,
                               const View& V, int trace_slot, int64_t trace_start, labs_log_record* rec, const LG& t,
                               const RT& tt)
@@ -1292,7 +1390,16 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
         unsigned key[R];
         {
             float X[R];
-            toeplitz(V, n, o, X);
+            if constexpr (TC == 1) {
+                toeplitz_tc(V, SL, n, o, t.h, X);
+            } else if constexpr (TC == 2) {
+                if (SL.hoff)
+                    toeplitz_tc(V, SL, n, o, t.h, X);
+                else
+                    toeplitz(V, n, o, X);
+            } else {
+                toeplitz(V, n, o, X);
+            }
             lane_keys(V, n, o, X, P, key);
         }
 
@@ -1367,6 +1474,15 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
         const bool moves = act && kc != 0xFFFFFFFFu;
         const int best_i = moves ? (int)(kc & 0xFFu) : 0, best_d = (int)(kc >> 8) - kKeyBias;
         apply_flip<LG, R>(V, n, o, lane, moves, best_i, P);
+        if constexpr (TC != 0) {
+            if (moves && lane == 0 && SL.hoff) {  // the FP16 copies of the flipped entries
+                const int pb = best_i & 1, vb = best_i >> 1, vq = best_i == n - 1 ? vb : n - 1 - vb - pb;
+                const float* Ab = pb ? V.A1 : V.A0;
+                __half* H = reinterpret_cast<__half*>(base + SL.hoff + pb * SL.hlen) + kTcPad;
+                H[vb] = __float2half_rn(Ab[vb]);
+                H[vq] = __float2half_rn(Ab[vq]);
+            }
+        }
         const bool stored = slot >= 0;
         if (moves && lane == 0 && stored) env.T[slot] = (fnew & ~kGenMask) | w.gen;
         if (moves && lane == (best_i >> 5)) w.word ^= 1u << (best_i & 31);
@@ -2124,19 +2240,22 @@ __device__ __forceinline__ void walk_group(const KParams& p, int chunk_index)
                 }
             }
             // lane block: block_R(n) when it is one of RMAX .. RMAX-3, else the smallest
-            // bank-conflict-free one of those
+            // bank-conflict-free one of those.  Two walkers per warp take the Toeplitz
+            // product to the tensor cores while n_max <= 128 (lane blocks up to 9; the
+            // second product for n > 128 would be mostly padding)
+            constexpr int TC = LG::kSize != 16 ? 0 : RMAX <= 8 ? 1 : RMAX == 9 ? 2 : 0;
             int R = block_R(G.n, LG::kSize);
             if (R < RMAX - 3) R = conflict_free_R(RMAX - 3, LG::kSize);
             if (R >= RMAX)
-                walk_lockstep<LG, RT, RMAX>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec, t, tt);
+                walk_lockstep<LG, RT, RMAX, TC>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec, t, tt);
             else if (R == RMAX - 1)
-                walk_lockstep<LG, RT, (RMAX > 1 ? RMAX - 1 : 1)>(env, w, until, real, base, SL, V, trace_slot,
+                walk_lockstep<LG, RT, (RMAX > 1 ? RMAX - 1 : 1), TC>(env, w, until, real, base, SL, V, trace_slot,
                                                                  trace_start, rec, t, tt);
             else if (R == RMAX - 2)
-                walk_lockstep<LG, RT, (RMAX > 2 ? RMAX - 2 : 1)>(env, w, until, real, base, SL, V, trace_slot,
+                walk_lockstep<LG, RT, (RMAX > 2 ? RMAX - 2 : 1), TC>(env, w, until, real, base, SL, V, trace_slot,
                                                                  trace_start, rec, t, tt);
             else
-                walk_lockstep<LG, RT, (RMAX > 3 ? RMAX - 3 : 1)>(env, w, until, real, base, SL, V, trace_slot,
+                walk_lockstep<LG, RT, (RMAX > 3 ? RMAX - 3 : 1), TC>(env, w, until, real, base, SL, V, trace_slot,
                                                                  trace_start, rec, t, tt);
             if (real) save_walker(env.st, w, t.lane);
             __syncwarp();

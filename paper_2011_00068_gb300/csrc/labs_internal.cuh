@@ -148,7 +148,8 @@ struct KParams {
 // Shared-memory layout of one walker, in 32-bit words.  Rows and table hold small
 // integers as floats (exact: every value and every partial sum of the neighbourhood
 // stays below 2^24 in magnitude for L <= 511), so that the Toeplitz product runs on
-// the FP32 pipes.
+// the FP32 pipes (or, two walkers per warp, on the tensor cores from FP16 copies of the
+// same integers, |C_k| < 2^11).
 //   A0: even positions s_0, s_2, .. (n values) as +-1.0f; zero from -apad up to the
 //       row end (indices [-apad, alen - apad)); the padding covers every index the
 //       walk reads without a bounds test
@@ -158,6 +159,7 @@ struct KParams {
 //   B : bit-packed classes (bit u set <=> A_p[u] = -1) and their reversals,
 //       4 vectors x bvec words (kBitVec in the warp layouts), zero beyond the class
 //       length
+constexpr int kTcPad = 48;  // FP16 row entries below u = 0 (three blocks of 16)
 constexpr int kBitVec = 9;  // 256 bits per class plus one zero word read by the shifts
 struct WarpSmem {
     int apad;   // zero words below index 0 of each row (multiple of 4)
@@ -168,8 +170,15 @@ struct WarpSmem {
     int boff;   // word offset of B
     int bvec;   // words per bit vector of B
     int xoff;   // long layout: word offset of the CTA scratch (kLongThreads words) and the
-                // free-variable bits (kBitWordsLong words)
+                // free-variable bits (kBitWordsLong words); two walkers per warp: word
+                // offset of the Toeplitz results
     int poff;   // row layout: word offset of the per-lag P values Q[0 .. n_max) (0: none)
+    int xp;     // two walkers per warp: floats per class of the walker's Toeplitz results
+                // X[2][xp] at word offset xoff (0: none)
+    int hoff;   // two walkers per warp: word offset of FP16 copies of the rows, class p at
+                // hoff + p hlen, entry u at half index kTcPad + u, zero around the class
+    int hlen;   // words per FP16 row (4 mod 8: the two classes' operand loads use
+                // different banks; 0: no FP16 rows)
     int words;  // total words per walker (multiple of 4: walkers stay 16-byte aligned)
 };
 // Outputs per lane (the lane block R) for n free variables and `tile` lanes per walker
@@ -217,6 +226,15 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
         if (3 * (tile / 2) * R > hi) hi = 3 * (tile / 2) * R;
         int lo = n_max > span ? n_max : span;
         int gtop = top > span ? top : span;
+        int gdeep = 0;
+        if (tile == 16 && n_max <= 128) {
+            // the Toeplitz product on the tensor cores (both walkers of a warp) reads the
+            // table from y = -(16 T - 1) up to 16 S, with S = ceil(n/16) row blocks and
+            // T = ceil(ceil(n/2) / 16) output blocks
+            const int S = (n_max + 15) >> 4, T = (((n_max + 1) >> 1) + 15) >> 4;
+            if (gtop < 16 * S) gtop = 16 * S;
+            gdeep = 16 * T - 1;
+        }
         if (tile == 32) {
             // the PSL neighbourhood (one walker per warp) runs its lags 2R - 2 past n - 1:
             // class entries from v0 - n - 2R up to v0 + n + 2R (v0 <= (tile/2 - 1) R) and
@@ -232,6 +250,7 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
         // the two sets are disjoint (no conflicts) when alen = 16 (mod 32)
         if (tile == 32) w.alen += (48 - (w.alen & 31)) & 31;
         w.gpad = (tile / 2) * R > span ? (tile / 2) * R : span;
+        if (w.gpad < gdeep) w.gpad = gdeep;
         w.glen = w.gpad + gtop;
     }
     w.goff = 2 * w.alen;
@@ -239,7 +258,23 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
     w.bvec = kBitVec;
     w.xoff = 0;
     w.poff = 0;
+    w.xp = 0;
+    w.hoff = 0;
+    w.hlen = 0;
     w.words = (w.boff + 4 * kBitVec + 3) & ~3;
+    if (tile == 16 && n_max <= 128) {
+        // the tensor-core Toeplitz product (n_max <= 128: one product per diagonal
+        // covers the outputs).  Its results: 16 T outputs per class written, (tile/2) R
+        // read; xp = 16 (mod 32) puts the two classes' entries in different banks
+        const int T = (((n_max + 1) >> 1) + 15) >> 4, S = (n_max + 15) >> 4;
+        const int need = 16 * T > (tile / 2) * R ? 16 * T : (tile / 2) * R;
+        w.xoff = w.words;
+        w.xp = ((need + 15) & ~31) + 16;
+        // FP16 rows: u from -kTcPad up to 16 S + kTcPad (16 S + 96 halves)
+        w.hoff = w.xoff + 2 * w.xp;
+        w.hlen = ((8 * S + kTcPad + 3) & ~7) + 4;
+        w.words = w.hoff + 2 * w.hlen;
+    }
     return w;
 }
 
@@ -278,6 +313,9 @@ __host__ __device__ inline WarpSmem row_smem(int n_max, int tile)
     w.boff = w.goff + 2 * w.glen;
     w.bvec = 0;
     w.xoff = 0;
+    w.xp = 0;
+    w.hoff = 0;
+    w.hlen = 0;
     w.poff = (w.boff + 3) & ~3;
     w.words = w.poff + ((n_max + 3) & ~3);
     return w;
@@ -328,6 +366,9 @@ __host__ __device__ inline WarpSmem long_smem(int n_max, int tile)
     w.bvec = (n_max + 31) / 32 + 2;
     w.xoff = (w.boff + 4 * w.bvec + 3) & ~3;
     w.poff = 0;
+    w.xp = 0;
+    w.hoff = 0;
+    w.hlen = 0;
     // scratch, bits, then the best-first search's queue keys (LABS_QUEUE_SIZE 64-bit
     // words), each warp's lowest candidate keys (32 per warp), the keys entered in a
     // round, two words of round state and the entered keys' places (LABS_QUEUE_SIZE ints)

@@ -1,5 +1,5 @@
 // Prints the shared-memory layouts the kernels use (labs_internal.cuh, compiled for the
-// host): one line per (kind, tile, n_max): apad alen gpad glen bvec xoff words R (the
+// host): one line per (kind, tile, n_max): apad alen gpad glen bvec xoff words R xp hoff hlen (the
 // row layout: apad alen gpad glen bvec boff poff words R).
 #define __host__
 #define __device__
@@ -15,8 +15,8 @@ int main()
     for (int ti = 0; ti < 3; ++ti)
         for (int n = 2; n <= kMaxN; ++n) {
             const WarpSmem w = warp_smem(n, tiles[ti]);
-            std::printf("warp %d %d %d %d %d %d %d %d %d %d\n", tiles[ti], n, w.apad, w.alen, w.gpad, w.glen, w.bvec,
-                        w.xoff, w.words, block_R(n, tiles[ti]));
+            std::printf("warp %d %d %d %d %d %d %d %d %d %d %d %d %d\n", tiles[ti], n, w.apad, w.alen, w.gpad,
+                        w.glen, w.bvec, w.xoff, w.words, block_R(n, tiles[ti]), w.xp, w.hoff, w.hlen);
         }
     for (int n = 2; n <= kMaxN; ++n) {  // the row kernels: two rows per warp up to n = 160
         const int tile = n <= 160 ? 16 : 32;

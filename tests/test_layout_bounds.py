@@ -35,7 +35,8 @@ def layouts(tmp_path_factory):
                                      words=v[9], R=v[10])
         elif f[0] == "warp":
             tile, n = v[0], v[1]
-            warp[(tile, n)] = dict(apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], R=v[9])
+            warp[(tile, n)] = dict(apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], xoff=v[7], words=v[8],
+                                   R=v[9], xp=v[10], hoff=v[11], hlen=v[12])
         else:
             nt, n = v[0], v[1]
             long_[(nt, n)] = dict(nt=nt, apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], xoff=v[7],
@@ -109,6 +110,36 @@ def common(reg, n, tile, R, valid_only, bits=True):
     reg.b(((n + 31) // 32), "bits zero word")
 
 
+def tensor_core_reads(reg, S, n, R):
+    """Every table, FP16-row and scratch index of toeplitz_tc (two walkers per warp,
+    n <= 128: one product per diagonal, d = -(T-1) .. S-1)."""
+    nS = (n + 15) >> 4
+    nT = (((n + 1) >> 1) + 15) >> 4
+    assert nT <= 4
+    nd = nS + nT - 1
+    ys = [-16 * (nT - 1) + 2 * tq - g for tq in range(4) for g in range(8)]
+    reg.g(min(ys) - 8, "tc table first")
+    hrow = 2 * S["hlen"]                    # halves per FP16 row
+    for k in (0, nd - 1):
+        reg.g(min(ys) + 16 * k, "tc table")
+        reg.g(max(ys) + 16 * k + 8 + 1, "tc table + 8")
+        for tb in range(4):
+            for tq in (0, 3):
+                u = 16 * (tb - (nT - 1) + k) + 2 * tq
+                if not (0 <= 48 + u and 48 + u + 9 < hrow):
+                    reg.bad.append(("FP16 row", u))
+    for tx in (0, 2):
+        for t in (tx, tx + 1):
+            if t < nT and not 16 * t + 15 < S["xp"]:
+                reg.bad.append(("X write", t))
+    if not ((S["xp"] & 31) == 16 and 8 * R <= S["xp"]):
+        reg.bad.append(("X scratch", S["xoff"], S["xp"]))
+    if not ((S["hlen"] & 7) == 4 and 2 * S["hlen"] >= 16 * nS + 96):
+        reg.bad.append(("FP16 rows", S["hlen"]))
+    if not (S["xoff"] + 2 * S["xp"] <= S["hoff"] and S["hoff"] + 2 * S["hlen"] <= S["words"]):
+        reg.bad.append(("regions", S["xoff"], S["hoff"], S["words"]))
+
+
 def test_warp_layouts(layouts):
     warp, _, _ = layouts
     bad = []
@@ -157,6 +188,8 @@ def test_warp_layouts(layouts):
                             covered.update(range(m0, m0 + R))
                     if not set(range(1, min(n, 4 * R))) <= covered:
                         reg.bad.append(("mirror coverage", n, R))
+                if tile == 16 and n_max <= 128:   # the Toeplitz product on the tensor cores
+                    tensor_core_reads(reg, S, n, R)
                 if tile == 32:          # the PSL neighbourhood
                     if R <= 5:
                         P = 3 * R - 2
