@@ -49,9 +49,9 @@ PSL_LANE_OPS_PER_LAG_TERM = 4
 WALK_KERNELS = {4: "walk_quad_kernel", 2: "walk_pair_kernel", 1: "walk_chunk_kernel"}  # by walkers per warp
 # DRAM bytes per walker step of the L=201 walk kernel (ncu: dram__bytes_read.sum +
 # dram__bytes_write.sum of a 4864-walker x 256-step launch of the current kernel,
-# 288.5 + 30.3 MB over 1,245,184 walker steps, profiles/walk_pair_kernel_L201_16384w.md);
+# 288.8 + 31.3 MB over 1,245,184 walker steps, profiles/walk_pair_kernel_L201_16384w.md);
 # None when not captured for the current kernel
-DRAM_BYTES_PER_WALKER_STEP = 256.0
+DRAM_BYTES_PER_WALKER_STEP = 257.0
 
 
 def parse():
@@ -423,7 +423,11 @@ def run_ours(args):
                                  else "not captured for this kernel and workload"),
                 "kernel": kernel, "lane_block": st["lane_block"],
                 "peak_source": "derived: %d SMs x %d FP32 lanes x %s x %.0f MHz (FMA pipe)" % (
-                    sms, FP32_LANES_PER_SM, "1 op" if args.search == "psl" else "2 FLOP", sm_mhz)}
+                    sms, FP32_LANES_PER_SM, "1 op" if args.search == "psl" else "2 FLOP", sm_mhz),
+                "toeplitz": ("tensor cores: mma.sync.m16n8k16, FP16 operands (exact small integers), FP32 "
+                             "accumulation; lag terms counted against the FP32 FMA peak"
+                             if st["walkers_per_warp"] == 2 and n <= 128 and args.search == "walk"
+                             else "FP32 FMA pipe")}
 
     e2e = None
     if not args.no_e2e:
