@@ -461,7 +461,7 @@ __device__ __forceinline__ void tc_diag(float (&d)[4], const float2* gy, const u
 template <class TL>
 __device__ __forceinline__ void half_rows(int* base, const WarpSmem& SL, const View& V, int n, const TL& t)
 {
-    __half* H = reinterpret_cast<__half*>(base + SL.hoff) + kTcPad;
+    __half* H = reinterpret_cast<__half*>(base + SL.hoff) + SL.hpad;
     for (int j = t.lane; j < 2 * n; j += TL::kSize) {
         const int p = j >= n, u = p ? j - n : j;
         if (u < n - p) H[p * 2 * SL.hlen + u] = __float2half_rn((p ? V.A1 : V.A0)[u]);
@@ -481,7 +481,7 @@ __device__ __forceinline__ void toeplitz_tc(const View& V, const WarpSmem& SL, i
     int* const own = reinterpret_cast<int*>(V.A0) - SL.apad;
     int* const base0 = own - h * SL.words;     // walker 0 of the warp; walker 1 follows
     const float2* gy = reinterpret_cast<const float2*>(base0 + SL.goff) + SL.gpad + (2 * tq - g - 16 * (T - 1));
-    const uint32_t* ab = reinterpret_cast<const uint32_t*>(base0 + SL.hoff + pb * SL.hlen) + (kTcPad >> 1) +
+    const uint32_t* ab = reinterpret_cast<const uint32_t*>(base0 + SL.hoff + pb * SL.hlen) + (SL.hpad >> 1) +
                          8 * (tb - (T - 1)) + tq;
     const int nd = S + T - 1, w1 = SL.words, g1 = SL.words >> 1;
     // two independent accumulator chains, one per walker
@@ -1170,26 +1170,35 @@ constexpr float kIntBias = 12582912.f;  // 1.5 * 2^23
 constexpr int kIntBiasBits = 0x4B400000;
 constexpr int kKeyBias = 1 << 22;       // dISL = (key >> 8) - kKeyBias
 
-template <class LG, int R>
-__device__ __forceinline__ int lane_dlb(const View& V, int n, const Outs<LG, R>& o, const float (&X)[R],
-                                        const float (&P)[R], uint32_t (&db)[R])
+__device__ __forceinline__ float row_value(float a)
+{
+    return a;
+}
+__device__ __forceinline__ float row_value(__half a)
+{
+    return __half2float(a);
+}
+
+// A: the lane's class row (FP32, or FP16 in the row kernels' tensor-core layout).
+template <class LG, int R, class E>
+__device__ __forceinline__ int lane_dlb_rows(const E* A, const View& V, int n, const Outs<LG, R>& o,
+                                             const float (&X)[R], const float (&P)[R], uint32_t (&db)[R])
 {
     // four walkers per warp: the rows are not padded for the missing outputs' reads
     constexpr bool kGuard = LG::kSize == 8;
     const int p = o.p, c = n - 1;
     const int rv = (p ? (n >> 1) : ((n + 1) >> 1)) - o.v0;
-    const float* A = p ? V.A1 : V.A0;
     const int rc = (c & 1) == p ? ((c - p) >> 1) - o.v0 : -1;  // the centre's r, if this lane has it
     const float base = (float)(16 * ((p ? n - 2 : n - 1) - 1)) + kIntBias, cbase = (float)(16 * (c >> 1)) + kIntBias;
-    const float* Av = A + o.v0;                    // s_i          = Av[r]
-    const float* Aq = A + (n - 1 - p - o.v0);      // s_q          = Aq[-r]
-    const float* At = A + (3 * o.v0 + p - n + 1);  // s_{3i-L+1}   = At[3r]
+    const E* Av = A + o.v0;                        // s_i          = Av[r]
+    const E* Aq = A + (n - 1 - p - o.v0);          // s_q          = Aq[-r]
+    const E* At = A + (3 * o.v0 + p - n + 1);      // s_{3i-L+1}   = At[3r]
     const float2* Gc = V.G + (c - p - 2 * o.v0);   // C_{q-i}      = Gc[-2r].x
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const bool ok = !kGuard || r < rv;
-        const float av = Av[r], sq = Aq[-r];
-        const float ck0 = ok ? Gc[-2 * r].x : 0.f, st = ok ? At[3 * r] : 0.f;
+        const float av = row_value(Av[r]), sq = row_value(Aq[-r]);
+        const float ck0 = ok ? Gc[-2 * r].x : 0.f, st = ok ? row_value(At[3 * r]) : 0.f;
         const bool ctr = r == rc;
         // every partial sum is an integer of magnitude below 2^24: exact
         const float add = ctr ? cbase : fmaf(32.f, fmaf(-sq, st, P[r]), base);
@@ -1200,14 +1209,28 @@ __device__ __forceinline__ int lane_dlb(const View& V, int n, const Outs<LG, R>&
 }
 
 template <class LG, int R>
-__device__ __forceinline__ int lane_dl(const View& V, int n, const Outs<LG, R>& o, const float (&X)[R],
-                                       const float (&P)[R], int (&dl)[R])
+__device__ __forceinline__ int lane_dlb(const View& V, int n, const Outs<LG, R>& o, const float (&X)[R],
+                                        const float (&P)[R], uint32_t (&db)[R])
+{
+    return lane_dlb_rows(o.p ? V.A1 : V.A0, V, n, o, X, P, db);
+}
+
+template <class LG, int R, class E>
+__device__ __forceinline__ int lane_dl_rows(const E* A, const View& V, int n, const Outs<LG, R>& o,
+                                            const float (&X)[R], const float (&P)[R], int (&dl)[R])
 {
     uint32_t db[R];
-    const int rv = lane_dlb(V, n, o, X, P, db);
+    const int rv = lane_dlb_rows(A, V, n, o, X, P, db);
 #pragma unroll
     for (int r = 0; r < R; ++r) dl[r] = (int)db[r] - kIntBiasBits;
     return rv;
+}
+
+template <class LG, int R>
+__device__ __forceinline__ int lane_dl(const View& V, int n, const Outs<LG, R>& o, const float (&X)[R],
+                                       const float (&P)[R], int (&dl)[R])
+{
+    return lane_dl_rows(o.p ? V.A1 : V.A0, V, n, o, X, P, dl);
 }
 
 template <class LG, int R>
@@ -1478,7 +1501,7 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
             if (moves && lane == 0 && SL.hoff) {  // the FP16 copies of the flipped entries
                 const int pb = best_i & 1, vb = best_i >> 1, vq = best_i == n - 1 ? vb : n - 1 - vb - pb;
                 const float* Ab = pb ? V.A1 : V.A0;
-                __half* H = reinterpret_cast<__half*>(base + SL.hoff + pb * SL.hlen) + kTcPad;
+                __half* H = reinterpret_cast<__half*>(base + SL.hoff + pb * SL.hlen) + SL.hpad;
                 H[vb] = __float2half_rn(Ab[vb]);
                 H[vq] = __float2half_rn(Ab[vq]);
             }

@@ -159,7 +159,7 @@ struct KParams {
 //   B : bit-packed classes (bit u set <=> A_p[u] = -1) and their reversals,
 //       4 vectors x bvec words (kBitVec in the warp layouts), zero beyond the class
 //       length
-constexpr int kTcPad = 48;  // FP16 row entries below u = 0 (three blocks of 16)
+constexpr int kTcPad = 48;  // FP16 row entries the tensor-core product reads below u = 0
 constexpr int kBitVec = 9;  // 256 bits per class plus one zero word read by the shifts
 struct WarpSmem {
     int apad;   // zero words below index 0 of each row (multiple of 4)
@@ -175,10 +175,12 @@ struct WarpSmem {
     int poff;   // row layout: word offset of the per-lag P values Q[0 .. n_max) (0: none)
     int xp;     // two walkers per warp: floats per class of the walker's Toeplitz results
                 // X[2][xp] at word offset xoff (0: none)
-    int hoff;   // two walkers per warp: word offset of FP16 copies of the rows, class p at
-                // hoff + p hlen, entry u at half index kTcPad + u, zero around the class
+    int hoff;   // tensor-core layouts: word offset of FP16 rows (copies of the rows in the
+                // walk, the only rows in the row kernels), class p at hoff + p hlen, entry
+                // u at half index hpad + u, zero around the class
     int hlen;   // words per FP16 row (4 mod 8: the two classes' operand loads use
                 // different banks; 0: no FP16 rows)
+    int hpad;   // FP16 entries below u = 0 (even)
     int words;  // total words per walker (multiple of 4: walkers stay 16-byte aligned)
 };
 // Outputs per lane (the lane block R) for n free variables and `tile` lanes per walker
@@ -261,6 +263,7 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
     w.xp = 0;
     w.hoff = 0;
     w.hlen = 0;
+    w.hpad = 0;
     w.words = (w.boff + 4 * kBitVec + 3) & ~3;
     if (tile == 16 && n_max <= 128) {
         // the tensor-core Toeplitz product (n_max <= 128: one product per diagonal
@@ -272,6 +275,7 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
         w.xp = ((need + 15) & ~31) + 16;
         // FP16 rows: u from -kTcPad up to 16 S + kTcPad (16 S + 96 halves)
         w.hoff = w.xoff + 2 * w.xp;
+        w.hpad = kTcPad;
         w.hlen = ((8 * S + kTcPad + 3) & ~7) + 4;
         w.words = w.hoff + 2 * w.hlen;
     }
@@ -293,6 +297,39 @@ __host__ __device__ inline WarpSmem row_smem(int n_max, int tile)
     WarpSmem w;
     const int R = block_R(n_max, tile);
     const int vtop = (tile / 2) * R;             // one past the largest lane output
+    if (tile == 16 && n_max <= 128) {
+        // two rows per warp with the Toeplitz product on the tensor cores: FP16 rows only
+        // (the product's operand blocks u = -kTcPad .. 16 S + kTcPad and the assembly's
+        // reads, down to -(n-1)), the table for the product (pairs -(16 T - 1) .. 16 S)
+        // and the assembly, then Q, which the product's results X[2][xp] overwrite
+        const int S = (n_max + 15) >> 4, T = (((n_max + 1) >> 1) + 15) >> 4;
+        int hlo = kTcPad > n_max - 1 ? kTcPad : n_max - 1;
+        if (vtop - n_max + 1 > hlo) hlo = vtop - n_max + 1;
+        int hhi = 16 * S + kTcPad;               // A_p[v] (v < vtop), A_p[3v+p-n+1], A_p[n-1]
+        if (vtop > hhi) hhi = vtop;
+        if (3 * vtop - n_max > hhi) hhi = 3 * vtop - n_max;
+        if (n_max > hhi) hhi = n_max;
+        w.apad = 0;
+        w.alen = 0;
+        w.hoff = 0;
+        w.hpad = (hlo + 1) & ~1;
+        w.hlen = (((w.hpad + hhi + 1) / 2 + 3) & ~7) + 4;
+        int gl = n_max + 1;                      // mirror of E down to pair -n
+        if (16 * T - 1 > gl) gl = 16 * T - 1;    // the product's first pairs
+        if (2 * vtop - n_max + 2 > gl) gl = 2 * vtop - n_max + 2;  // C_{q-i} below 0
+        w.gpad = gl;
+        w.glen = w.gpad + (16 * S > n_max + 2 ? 16 * S : n_max + 2);
+        w.goff = 2 * w.hlen;
+        w.boff = w.goff + 2 * w.glen;
+        w.bvec = 0;
+        const int need = 16 * T > vtop ? 16 * T : vtop;
+        w.xp = ((need + 15) & ~31) + 16;
+        w.poff = (w.boff + 3) & ~3;
+        w.xoff = w.poff;
+        const int q = 2 * w.xp > n_max ? 2 * w.xp : n_max;
+        w.words = w.poff + ((q + 3) & ~3);
+        return w;
+    }
     const int nu = (n_max + 7) & ~7;
     int lo = n_max, hi = nu;
     if (vtop > hi) hi = vtop;                    // A_p[v] with v < vtop
@@ -316,6 +353,7 @@ __host__ __device__ inline WarpSmem row_smem(int n_max, int tile)
     w.xp = 0;
     w.hoff = 0;
     w.hlen = 0;
+    w.hpad = 0;
     w.poff = (w.boff + 3) & ~3;
     w.words = w.poff + ((n_max + 3) & ~3);
     return w;
@@ -369,6 +407,7 @@ __host__ __device__ inline WarpSmem long_smem(int n_max, int tile)
     w.xp = 0;
     w.hoff = 0;
     w.hlen = 0;
+    w.hpad = 0;
     // scratch, bits, then the best-first search's queue keys (LABS_QUEUE_SIZE 64-bit
     // words), each warp's lowest candidate keys (32 per warp), the keys entered in a
     // round, two words of round state and the entered keys' places (LABS_QUEUE_SIZE ints)

@@ -150,15 +150,17 @@ __global__ void __launch_bounds__(256) isl_kernel(const int8_t* __restrict__ seq
 // class l / (TILE/2), entries u = (TILE/2) it + l % (TILE/2).  With STAGED, bytes j <
 // lim of the row are read from its staged copy stg (shared memory), the rest from src.
 // Returns true when a byte of this lane is not +-1.
-template <int TILE, int NW, bool STAGED>
+// HALF: the rows are FP16 (hrow: class 0's entry 0; class 1 lies hstride halves further).
+template <int TILE, int NW, bool STAGED, bool HALF = false>
 __device__ __forceinline__ bool row_load(const View& V, const int8_t* __restrict__ src, const int8_t* stg,
                                          int64_t lim, bool has, int L, int lane, int h, uint32_t (&x0)[NW],
-                                         uint32_t (&x1)[NW])
+                                         uint32_t (&x1)[NW], __half* hrow = nullptr, int hstride = 0)
 {
     constexpr int G = TILE / 2;               // lanes per class
     constexpr int IT = 32 / G;                // ballots per class word
     const int p = lane / G, e = lane % G;
     float* A = p ? V.A1 : V.A0;
+    __half* H = hrow + p * hstride;
     uint32_t bad = 0u;  // v in {1, -1} <=> (v + 1) & ~2 == 0
     // rows held whole by the staging buffer (all but the input's last few bytes) read
     // shared memory only; the choice is the same for the whole warp
@@ -177,11 +179,17 @@ __device__ __forceinline__ bool row_load(const View& V, const int8_t* __restrict
                 // every row exists, and rounds below the last word lie inside the row
                 if (k < NW - 1 || j < L) {
                     v = stg[j];
-                    A[u] = (float)v;
+                    if constexpr (HALF)
+                        H[u] = __int2half_rn(v);
+                    else
+                        A[u] = (float)v;
                 }
             } else if (has && j < L) {
                 v = (STAGED && j < lim) ? stg[j] : src[j];
-                A[u] = (float)v;
+                if constexpr (HALF)
+                    H[u] = __int2half_rn(v);
+                else
+                    A[u] = (float)v;
             }
             bad |= (uint32_t)(v + 1) & ~2u;
             bl[tt] = __ballot_sync(kFull, v < 0);
@@ -436,6 +444,9 @@ template <int R, int NW, bool STAGED>
 __global__ void __launch_bounds__(256, R <= 7 ? 3 : 2) delta_pair_kernel(const int8_t* __restrict__ seqs, int64_t batch, int L,
                                                          int32_t* __restrict__ out, DevStatus* status)
 {
+    // n <= 128 (at most four class words): the Toeplitz product on the tensor cores over
+    // FP16 rows (row_smem's tensor-core layout); above, the FP32 product
+    constexpr bool TC = NW <= 4;
     extern __shared__ __align__(16) int smem[];
     const int n = (L + 1) / 2, c = n - 1;
     const WarpSmem SL = row_smem(n, 16);
@@ -480,8 +491,9 @@ __global__ void __launch_bounds__(256, R <= 7 ? 3 : 2) delta_pair_kernel(const i
         const bool has = row < batch;
         const int64_t rs = row * (int64_t)L;
         uint32_t x0[NW], x1[NW], xr0[NW], xr1[NW];
-        bool bad = row_load<16, NW, STAGED>(V, seqs + rs, stg + b * SB + (rs - g.a0), g.a1 - rs, has, L, lane, t.h,
-                                            x0, x1);
+        bool bad = row_load<16, NW, STAGED, TC>(V, seqs + rs, stg + b * SB + (rs - g.a0), g.a1 - rs, has, L, lane,
+                                                t.h, x0, x1, reinterpret_cast<__half*>(base + SL.hoff) + SL.hpad,
+                                                2 * SL.hlen);
         reverse_class(x0, n, xr0);
         reverse_class(x1, n - 1, xr1);
         const uint32_t f0 = (c & 1) ? ~0u : 0u, f1 = ~f0;
@@ -505,8 +517,15 @@ __global__ void __launch_bounds__(256, R <= 7 ? 3 : 2) delta_pair_kernel(const i
         {
             float X[R], P[R];
             row_p(Q, n, o, P);
-            toeplitz(V, n, o, X);
-            rv = lane_dl(V, n, o, X, P, dl);
+            if constexpr (TC) {
+                __syncwarp();  // the product's results overwrite Q
+                toeplitz_tc(V, SL, n, o, t.h, X);
+                const __half* H = reinterpret_cast<const __half*>(base + SL.hoff + o.p * SL.hlen) + SL.hpad;
+                rv = lane_dl_rows(H, V, n, o, X, P, dl);
+            } else {
+                toeplitz(V, n, o, X);
+                rv = lane_dl(V, n, o, X, P, dl);
+            }
         }
         if (valid) {
 #pragma unroll

@@ -32,11 +32,11 @@ def layouts(tmp_path_factory):
         v = list(map(int, f[1:]))
         if f[0] == "row":
             row[(v[0], v[1])] = dict(apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], boff=v[7], poff=v[8],
-                                     words=v[9], R=v[10])
+                                     words=v[9], R=v[10], xoff=v[11], xp=v[12], hoff=v[13], hlen=v[14], hpad=v[15])
         elif f[0] == "warp":
             tile, n = v[0], v[1]
             warp[(tile, n)] = dict(apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], xoff=v[7], words=v[8],
-                                   R=v[9], xp=v[10], hoff=v[11], hlen=v[12])
+                                   R=v[9], xp=v[10], hoff=v[11], hlen=v[12], hpad=v[13])
         else:
             nt, n = v[0], v[1]
             long_[(nt, n)] = dict(nt=nt, apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], xoff=v[7],
@@ -61,6 +61,10 @@ class Region:
     def g(self, y, what):
         if not (-self.S["gpad"] <= y < self.S["glen"] - self.S["gpad"]):
             self.bad.append(("G", what, y))
+
+    def h(self, idx, what):                 # FP16 rows (tensor-core layouts)
+        if not (-self.S["hpad"] <= idx < 2 * self.S["hlen"] - self.S["hpad"]):
+            self.bad.append(("H", what, idx))
 
     def b(self, word, what):
         if not (0 <= word < self.S["bvec"]):
@@ -119,25 +123,22 @@ def tensor_core_reads(reg, S, n, R):
     nd = nS + nT - 1
     ys = [-16 * (nT - 1) + 2 * tq - g for tq in range(4) for g in range(8)]
     reg.g(min(ys) - 8, "tc table first")
-    hrow = 2 * S["hlen"]                    # halves per FP16 row
     for k in (0, nd - 1):
         reg.g(min(ys) + 16 * k, "tc table")
         reg.g(max(ys) + 16 * k + 8 + 1, "tc table + 8")
         for tb in range(4):
             for tq in (0, 3):
                 u = 16 * (tb - (nT - 1) + k) + 2 * tq
-                if not (0 <= 48 + u and 48 + u + 9 < hrow):
-                    reg.bad.append(("FP16 row", u))
+                reg.h(u, "tc rows")
+                reg.h(u + 9, "tc rows + 9")
     for tx in (0, 2):
         for t in (tx, tx + 1):
             if t < nT and not 16 * t + 15 < S["xp"]:
                 reg.bad.append(("X write", t))
     if not ((S["xp"] & 31) == 16 and 8 * R <= S["xp"]):
         reg.bad.append(("X scratch", S["xoff"], S["xp"]))
-    if not ((S["hlen"] & 7) == 4 and 2 * S["hlen"] >= 16 * nS + 96):
-        reg.bad.append(("FP16 rows", S["hlen"]))
-    if not (S["xoff"] + 2 * S["xp"] <= S["hoff"] and S["hoff"] + 2 * S["hlen"] <= S["words"]):
-        reg.bad.append(("regions", S["xoff"], S["hoff"], S["words"]))
+    if not ((S["hlen"] & 7) == 4 and (S["hpad"] & 1) == 0):
+        reg.bad.append(("FP16 rows", S["hlen"], S["hpad"]))
 
 
 def test_warp_layouts(layouts):
@@ -190,6 +191,10 @@ def test_warp_layouts(layouts):
                         reg.bad.append(("mirror coverage", n, R))
                 if tile == 16 and n_max <= 128:   # the Toeplitz product on the tensor cores
                     tensor_core_reads(reg, S, n, R)
+                    if not (S["xoff"] + 2 * S["xp"] <= S["hoff"] and S["hoff"] + 2 * S["hlen"] <= S["words"]):
+                        reg.bad.append(("regions", S["xoff"], S["hoff"], S["words"]))
+                    reg.h(-48, "tc rows low")
+                    reg.h(n - 1, "tc row copy")
                 if tile == 32:          # the PSL neighbourhood
                     if R <= 5:
                         P = 3 * R - 2
@@ -267,6 +272,36 @@ def test_long_exact_range_bound(layouts):
         assert lim < 2 ** 29
 
 
+def row_tensor_core(reg, S, n, R):
+    """The two-row kernel for n <= 128: FP16 rows only, the tensor-core product, the
+    assembly on the FP16 rows and the table, Q overwritten by the product's results."""
+    c = n - 1
+    vtop = 8 * R
+    tensor_core_reads(reg, S, n, R)
+    for p in (0, 1):
+        reg.h(n - 1 - p, "row load")
+        for v in (0, vtop - 1):             # every lane output, existing or not
+            reg.h(v, "asm v")
+            reg.h(n - 1 - p - v, "asm q")
+            reg.h(3 * v + p - n + 1, "asm t")
+            reg.g(c - p - 2 * v, "asm G")
+    for m in (1, n - 1):                    # the table's writes and mirror writes
+        reg.g(m, "E")
+        reg.g(m - 1, "E.y")
+        reg.g(-m, "mirror E")
+        reg.g(-m - 1, "mirror E.y")
+    nS = (n + 15) >> 4
+    if S["glen"] - S["gpad"] < 16 * nS:     # E is zero from n up to what the product reads
+        reg.bad.append(("table top", S["glen"] - S["gpad"]))
+    q = max(n, 2 * S["xp"])
+    if not (S["xoff"] == S["poff"] >= S["boff"] and S["poff"] + q <= S["words"]):
+        reg.bad.append(("Q / X region", S["poff"], S["xp"], S["words"]))
+    if not (S["hoff"] + 2 * S["hlen"] <= S["boff"] - 2 * S["glen"]):   # rows, then the table
+        reg.bad.append(("FP16 rows overlap the table", S["hoff"], S["hlen"]))
+    if S["apad"] or S["alen"]:
+        reg.bad.append(("FP32 rows", S["apad"], S["alen"]))
+
+
 def test_row_layouts(layouts):
     """The row kernels (labs_neighbor_delta): two rows per warp (16 lanes) up to n = 160,
     one per warp above; rows, Toeplitz window, assembly and table as in the walk, and the
@@ -278,6 +313,11 @@ def test_row_layouts(layouts):
     for (tile, n), S in sorted(row.items()):
         R = S["R"]
         reg = Region(S)
+        if tile == 16 and n <= 128:
+            row_tensor_core(reg, S, n, R)
+            if reg.bad:
+                bad.append((tile, n, R, reg.bad[:3]))
+            continue
         # the two-row kernel assembles every lane output; the one-row kernel existing ones
         common(reg, n, tile, R, valid_only=(tile == 32), bits=False)
         for m in (1, n - 1):                    # the table's mirror writes, unconditional
