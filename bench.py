@@ -169,6 +169,24 @@ def measured_peaks():
         return {}
 
 
+def tensor_peak():
+    """Dense FP16 tensor rate (FLOP/s): the measured sustained BF16 GEMM rate (FP16 and
+    BF16 share the nominal dense rate), else the fallback 1.7 PFLOP/s."""
+    return float(measured_peaks().get("bf16_tflops_sustained", 1700.0)) * 1e12
+
+
+def lag_roofline(n, flips, st, fma_peak):
+    """Lag-term FLOP/s (one multiply-add per lag term, n - 1 per flip evaluation) against
+    the FP32 FMA peak and the FP16 tensor peak; `roofline_frac` takes the pipe that runs
+    the Toeplitz product (labs_counters.tensor_cores)."""
+    flops = ALGO_FLOP_PER_LAG_TERM * (n - 1) * flips
+    tc = bool(st.get("tensor_cores"))
+    d = {"toeplitz": "tensor cores" if tc else "fp32", "fma_frac": flops / fma_peak,
+         "tensor_frac": flops / tensor_peak()}
+    d["roofline_frac"] = d["tensor_frac"] if tc else d["fma_frac"]
+    return d
+
+
 def cpu_baseline(args):
     """The oracle as it stands, all host cores, on a bounded sample of the workload."""
     import oracle
@@ -425,9 +443,10 @@ def run_ours(args):
                 "peak_source": "derived: %d SMs x %d FP32 lanes x %s x %.0f MHz (FMA pipe)" % (
                     sms, FP32_LANES_PER_SM, "1 op" if args.search == "psl" else "2 FLOP", sm_mhz),
                 "toeplitz": ("tensor cores: mma.sync.m16n8k16, FP16 operands (exact small integers), FP32 "
-                             "accumulation; lag terms counted against the FP32 FMA peak"
-                             if st["walkers_per_warp"] == 2 and n <= 128 and args.search == "walk"
-                             else "FP32 FMA pipe")}
+                             "accumulation; the step around it is issue- and latency-bound on the FP32, integer "
+                             "and load/store pipes, so lag terms are counted against the FP32 FMA peak"
+                             if st.get("tensor_cores") else "FP32 FMA pipe"),
+                "tensor_frac": (ops_per_launch / avg_launch_s / tensor_peak() if args.search != "psl" else None)}
 
     e2e = None
     if not args.no_e2e:
@@ -561,7 +580,7 @@ def run_scaleup(args):
         out[str(L)] = {"flips_per_s": flips, "seconds": dt, "steps": done, "walkers": args.scaleup_walkers,
                        "best_isl": b["isl"], "best_F": b["F"], "best_hex": b["hex"], "time_to_F8": t8,
                        "kernel": WALK_KERNELS[st["walkers_per_warp"]],
-                       "roofline_frac": ALGO_FLOP_PER_LAG_TERM * (n - 1) * flips / peak,
+                       **lag_roofline(n, flips, st, peak),
                        "tabu_bytes": (args.scaleup_walkers << 16) * 8}
         s.close()
         del s
@@ -572,8 +591,9 @@ def run_scaleup(args):
             "data": "synthetic", "vs_baseline": None,
             "config": {"workload": "L=303 and L=501, %d walkers each, %d steps, seed 42, uniform random +-1 Philox "
                                    "starts, HT 2^16 slots/walker" % (args.scaleup_walkers, args.scaleup_steps),
-                       "peak_source": "derived: %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz (FMA pipe)" % (
-                           sms, FP32_LANES_PER_SM, sm_mhz)},
+                       "peak_source": "fma_frac: derived, %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz (FMA pipe); "
+                                      "tensor_frac: of measured sustained BF16 GEMM rate %.1f TFLOP/s (FP16 shares "
+                                      "the dense rate)" % (sms, FP32_LANES_PER_SM, sm_mhz, tensor_peak() / 1e12)},
             "per_L": out}
     print(json.dumps(line))
     return 0
@@ -615,9 +635,10 @@ def run_long(args):
         best = s.best()
         out[str(L)] = {"flips_per_s": flips, "ms": ms, "steps": args.long_steps, "walkers": args.long_walkers,
                        "walker_steps_per_s": st["steps"] / (ms / 1e3), "best_isl": best["isl"],
-                       "best_F": best["F"], "lane_block": st["lane_block"],
-                       "roofline_frac": (PSL_LANE_OPS_PER_LAG_TERM * (n - 1) * flips / (peak / 2) if objective == "psl"
-                                         else ALGO_FLOP_PER_LAG_TERM * (n - 1) * flips / peak)}
+                       "best_F": best["F"], "lane_block": st["lane_block"], **lag_roofline(n, flips, st, peak)}
+        if objective == "psl":
+            # FP32 lane operations of the PSL terms: PSL_LANE_OPS_PER_LAG_TERM per lag term
+            out[str(L)]["psl_lane_op_frac"] = PSL_LANE_OPS_PER_LAG_TERM * (n - 1) * flips / (peak / 2)
         if objective == "psl":
             out[str(L)]["best_psl"] = best["psl"]
         s.close()
@@ -632,8 +653,9 @@ def run_long(args):
                                    "seed 42, uniform random +-1 Philox starts, HT 2^16 slots/walker"
                                    % (args.long_walkers, args.long_steps),
                        "kernel": "long_walk_kernel",
-                       "peak_source": "derived: %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz (FMA pipe)" % (
-                           sms, FP32_LANES_PER_SM, sm_mhz)},
+                       "peak_source": "fma_frac: derived, %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz (FMA pipe); "
+                                      "tensor_frac: of measured sustained BF16 GEMM rate %.1f TFLOP/s (FP16 shares "
+                                      "the dense rate)" % (sms, FP32_LANES_PER_SM, sm_mhz, tensor_peak() / 1e12)},
             "per_L": out}
     print(json.dumps(line))
     return 0

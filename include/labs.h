@@ -139,7 +139,9 @@ typedef struct labs_counters {
     int32_t lane_block;        /* outputs per lane of the widest walker (R) */
     int32_t best_psl;          /* LABS_FLAG_PSL: PSL of the best sequence (whose ISL is
                                   best_isl; best in the (PSL, ISL) order); else -1 */
-    int32_t pad_;
+    int32_t tensor_cores;      /* 1: the walk's Toeplitz product (the neighbourhood's
+                                  O(n^2) part) runs on the tensor cores as exact FP16 x FP16
+                                  -> FP32 block products; 0: on the FP32 pipes */
     int64_t cache_hits;        /* LABS_FLAG_SECOND_HASH: neighbours skipped because the
                                   second table held them (flip_evaluations counts all n
                                   per step: the GPU evaluates them anyway) */

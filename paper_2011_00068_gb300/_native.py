@@ -67,7 +67,7 @@ class LabsCounters(ctypes.Structure):
                 ("overflows", ctypes.c_int64), ("blocked", ctypes.c_int64), ("best_isl", ctypes.c_int32),
                 ("best_L", ctypes.c_int32), ("best_walker", ctypes.c_int64), ("target_step", ctypes.c_int64),
                 ("walkers_at_target", ctypes.c_int64), ("walkers_per_warp", ctypes.c_int32),
-                ("lane_block", ctypes.c_int32), ("best_psl", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("lane_block", ctypes.c_int32), ("best_psl", ctypes.c_int32), ("tensor_cores", ctypes.c_int32),
                 ("cache_hits", ctypes.c_int64)]
 
 

@@ -856,6 +856,7 @@ int labs_stats(labs_ctx* c, int32_t L, labs_counters* out)
     out->walkers_at_target = (int64_t)h.st_at_target;
     out->walkers_per_warp = kWarp / c->tile;  // 0 for long sequences: one walker per CTA
     out->lane_block = c->long_mode ? long_R(c->n_max, c->tile) : lanes_for(c->n_max, c->tile);
+    out->tensor_cores = (c->long_mode ? long_smem(c->n_max, c->tile).xp : warp_smem(c->n_max, c->tile).xp) != 0;
     out->target_step = h.st_target_step == LLONG_MAX ? -1 : (int64_t)h.st_target_step;
     out->best_psl = -1;
     if (h.best_key == ~0ull) {

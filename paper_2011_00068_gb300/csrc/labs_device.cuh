@@ -221,6 +221,8 @@ struct View {
     float* A1;
     float2* G;    // G[y] = (E[y], E[y+1]), y in [-gpad, glen-gpad)
     uint32_t* B;  // bit-packed classes and reversals, 4 x bvec words
+    __half* H0;   // FP16 copies of A0 and A1 for the tensor-core Toeplitz product (null:
+    __half* H1;   // none); every write of a row entry writes its copy too
     int gpad;
     int bvec;
 };
@@ -232,9 +234,18 @@ __device__ __forceinline__ View make_view(int* base, const WarpSmem& L)
     v.A1 = reinterpret_cast<float*>(base) + L.alen + L.apad;
     v.G = reinterpret_cast<float2*>(base + L.goff) + L.gpad;
     v.B = reinterpret_cast<uint32_t*>(base + L.boff);
+    v.H0 = L.hlen ? reinterpret_cast<__half*>(base + L.hoff) + L.hpad : nullptr;
+    v.H1 = L.hlen ? reinterpret_cast<__half*>(base + L.hoff + L.hlen) + L.hpad : nullptr;
     v.gpad = L.gpad;
     v.bvec = L.bvec;
     return v;
+}
+
+// Row entry u of class p (and its FP16 copy, when the layout keeps one).
+__device__ __forceinline__ void set_row(const View& V, int p, int u, float s)
+{
+    (p ? V.A1 : V.A0)[u] = s;
+    if (V.H0 != nullptr) (p ? V.H1 : V.H0)[u] = __float2half_rn(s);
 }
 
 // E[m] = e (m >= 1) in every pair of G that holds it, mirrored to E[-m].
@@ -269,8 +280,7 @@ __device__ __forceinline__ void rows_from_bits(const View& V, uint32_t word, int
         if (j < L) {
             const int x = ((w >> (f & 31)) & 1u) ? -1 : 1;
             const int s = (j > c && ((j - c) & 1)) ? -x : x;
-            if (j & 1) V.A1[j >> 1] = (float)s;
-            else V.A0[j >> 1] = (float)s;
+            set_row(V, j & 1, j >> 1, (float)s);
         }
     }
     t.sync();
@@ -457,18 +467,6 @@ __device__ __forceinline__ void tc_diag(float (&d)[4], const float2* gy, const u
     am8 = a2;
 }
 
-// The FP16 copies of the rows, from the FP32 rows (their padding is zero already).
-template <class TL>
-__device__ __forceinline__ void half_rows(int* base, const WarpSmem& SL, const View& V, int n, const TL& t)
-{
-    __half* H = reinterpret_cast<__half*>(base + SL.hoff) + SL.hpad;
-    for (int j = t.lane; j < 2 * n; j += TL::kSize) {
-        const int p = j >= n, u = p ? j - n : j;
-        if (u < n - p) H[p * 2 * SL.hlen + u] = __float2half_rn((p ? V.A1 : V.A0)[u]);
-    }
-    t.sync();
-}
-
 template <int R>
 __device__ __forceinline__ void toeplitz_tc(const View& V, const WarpSmem& SL, int n, const Outs<Pair, R>& o, int h,
                                             float (&X)[R])
@@ -493,7 +491,7 @@ __device__ __forceinline__ void toeplitz_tc(const View& V, const WarpSmem& SL, i
         gy += 16;
         ab += 8;
     }
-    float* xp = reinterpret_cast<float*>(base0 + SL.xoff) + px * SL.xp + 16 * tx + g;
+    float* xp = reinterpret_cast<float*>(base0 + SL.roff) + px * SL.xp + 16 * tx + g;
     float* xq = xp + w1;
     if (tx < T) {
         xp[0] = d0[0];
@@ -508,9 +506,73 @@ __device__ __forceinline__ void toeplitz_tc(const View& V, const WarpSmem& SL, i
         xq[24] = e0[3];
     }
     __syncwarp();
-    const float* xr = reinterpret_cast<const float*>(own + SL.xoff) + o.p * SL.xp + o.v0;
+    const float* xr = reinterpret_cast<const float*>(own + SL.roff) + o.p * SL.xp + o.v0;
 #pragma unroll
     for (int r = 0; r < R; ++r) X[r] = xr[r];
+}
+
+// The same product for one walker whose lane group spans W whole warps (one walker per
+// warp, W = 1, or per CTA): the output blocks form ceil(T/4) column groups of 4 blocks
+// per class, warp w takes groups w, w + W, ..., and for group m the block diagonals run
+// from -(4m+3) (or -(T-1)) up to S-1-4m.  Two accumulator chains per group (even and odd
+// diagonals; integer partial sums, so the split does not change the result).  The
+// results go through the walker's scratch X[2][xp] to the lanes' R outputs; the group's
+// barrier orders them.
+template <class LG, int R>
+__device__ __forceinline__ void toeplitz_tc1(const View& V, const WarpSmem& SL, int n, const Outs<LG, R>& o,
+                                             const LG& t, float (&X)[R])
+{
+    constexpr int W = LG::kSize / 32;
+    const int warp = W == 1 ? 0 : (int)(threadIdx.x >> 5), l = threadIdx.x & 31, g = l >> 2, tq = l & 3;
+    const int S = (n + 15) >> 4, T = (((n + 1) >> 1) + 15) >> 4, M = (T + 3) >> 2;
+    const int pb = g >> 2, tb = g & 3, px = tq >> 1, tx = 2 * (tq & 1);
+    int* const base = reinterpret_cast<int*>(V.A0) - SL.apad;
+    const float2* G = reinterpret_cast<const float2*>(base + SL.goff) + SL.gpad + (2 * tq - g);
+    const uint32_t* H = reinterpret_cast<const uint32_t*>(base + SL.hoff + pb * SL.hlen) + (SL.hpad >> 1) + 8 * tb + tq;
+    float* xs = reinterpret_cast<float*>(base + SL.roff) + px * SL.xp + g;
+    for (int m = warp; m < M; m += W) {
+        const int dlo = -min(4 * m + 3, T - 1), nd = S - 4 * m - dlo;  // d = dlo .. S-1-4m
+        const float2* gy = G + 16 * dlo;
+        const uint32_t* ab = H + 8 * (4 * m + dlo);
+        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+        uint32_t am = half2_bits(gy[-8]);
+        int k = 0;
+        for (; k + 1 < nd; k += 2) {
+            tc_diag(d0, gy, ab, am);
+            tc_diag(d1, gy + 16, ab + 8, am);
+            gy += 32;
+            ab += 16;
+        }
+        if (k < nd) tc_diag(d0, gy, ab, am);
+        const int t0 = tx + 4 * m;
+        if (t0 < T) {
+            xs[16 * t0] = d0[0] + d1[0];
+            xs[16 * t0 + 8] = d0[2] + d1[2];
+        }
+        if (t0 + 1 < T) {
+            xs[16 * t0 + 16] = d0[1] + d1[1];
+            xs[16 * t0 + 24] = d0[3] + d1[3];
+        }
+    }
+    t.sync();
+    const float* xr = reinterpret_cast<const float*>(base + SL.roff) + o.p * SL.xp + o.v0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) X[r] = xr[r];
+}
+
+// The Toeplitz product of a lane group that owns one walker: on the tensor cores when
+// the layout holds the FP16 rows and the results' scratch, else on the FP32 pipes.
+template <class LG, int R>
+__device__ __forceinline__ void toeplitz_one(const View& V, const WarpSmem& SL, int n, const Outs<LG, R>& o,
+                                             const LG& t, float (&X)[R])
+{
+    if constexpr (LG::kSize >= 32) {
+        if (SL.xp != 0) {
+            toeplitz_tc1(V, SL, n, o, t, X);
+            return;
+        }
+    }
+    toeplitz(V, n, o, X);
 }
 
 // P_v = sum_{m=1}^{v} A_p[v+m] A_p[v-m] from scratch for the lane's outputs, from the
@@ -615,7 +677,6 @@ __device__ __forceinline__ int load_rows(int* base, const WarpSmem& SL, const Vi
 {
     clear_rows(base, SL, t);
     rows_from_bits(V, word, L, n, t);
-    if (SL.hoff) half_rows(base, SL, V, n, t);
     return build_table(V, n, t);
 }
 
@@ -882,8 +943,8 @@ __device__ __forceinline__ void flip_rows_table(const View& V, int n, const Outs
         if (m < n) set_E(V, m, V.G[m].x + dd[k]);
     }
     if (lane == 0) {
-        Ab[vb] = -as;
-        if (!centre) Ab[vq] = -Ab[vq];
+        set_row(V, pb, vb, -as);
+        if (!centre) set_row(V, pb, vq, -Ab[vq]);
     }
 }
 
@@ -935,7 +996,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
         int dl[R];
         {
             float X[R];
-            toeplitz(V, n, o, X);
+            toeplitz_one(V, SL, n, o, t, X);
             assemble(V, n, o, X, P, dl);
         }
 
@@ -1353,8 +1414,8 @@ __device__ __forceinline__ void apply_flip(const View& V, int n, const Outs<LG, 
     }
     __syncwarp();
     if (moves && lane == 0) {
-        Ab[vb] = -as;
-        if (!centre) Ab[vq] = -aq;
+        set_row(V, pb, vb, -as);
+        if (!centre) set_row(V, pb, vq, -aq);
     }
 }
 
@@ -1416,12 +1477,12 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
             if constexpr (TC == 1) {
                 toeplitz_tc(V, SL, n, o, t.h, X);
             } else if constexpr (TC == 2) {
-                if (SL.hoff)
+                if (SL.xp)
                     toeplitz_tc(V, SL, n, o, t.h, X);
                 else
-                    toeplitz(V, n, o, X);
+                    toeplitz_one(V, SL, n, o, t, X);
             } else {
-                toeplitz(V, n, o, X);
+                toeplitz_one(V, SL, n, o, t, X);
             }
             lane_keys(V, n, o, X, P, key);
         }
@@ -1497,15 +1558,6 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
         const bool moves = act && kc != 0xFFFFFFFFu;
         const int best_i = moves ? (int)(kc & 0xFFu) : 0, best_d = (int)(kc >> 8) - kKeyBias;
         apply_flip<LG, R>(V, n, o, lane, moves, best_i, P);
-        if constexpr (TC != 0) {
-            if (moves && lane == 0 && SL.hoff) {  // the FP16 copies of the flipped entries
-                const int pb = best_i & 1, vb = best_i >> 1, vq = best_i == n - 1 ? vb : n - 1 - vb - pb;
-                const float* Ab = pb ? V.A1 : V.A0;
-                __half* H = reinterpret_cast<__half*>(base + SL.hoff + pb * SL.hlen) + SL.hpad;
-                H[vb] = __float2half_rn(Ab[vb]);
-                H[vq] = __float2half_rn(Ab[vq]);
-            }
-        }
         const bool stored = slot >= 0;
         if (moves && lane == 0 && stored) env.T[slot] = (fnew & ~kGenMask) | w.gen;
         if (moves && lane == (best_i >> 5)) w.word ^= 1u << (best_i & 31);
@@ -1631,7 +1683,7 @@ __device__ void walk_bestfirst(const WalkEnv& env, Walker& w, int64_t until, int
         unsigned key[R];
         {
             float X[R];
-            toeplitz(V, n, o, X);
+            toeplitz_one(V, SL, n, o, t, X);
             lane_keys(V, n, o, X, P, key);
         }
         if (T2 != nullptr) {
@@ -1969,7 +2021,7 @@ __device__ void walk_psl(const WalkEnv& env, Walker& w, PslTrack& ps, int64_t un
         int dl[R], pl[R];
         {
             float X[R];
-            toeplitz(V, n, o, X);
+            toeplitz_one(V, SL, n, o, t, X);
             assemble(V, n, o, X, P, dl);
         }
         psl_eval(V, n, o, pl);

@@ -170,11 +170,10 @@ struct WarpSmem {
     int boff;   // word offset of B
     int bvec;   // words per bit vector of B
     int xoff;   // long layout: word offset of the CTA scratch (kLongThreads words) and the
-                // free-variable bits (kBitWordsLong words); two walkers per warp: word
-                // offset of the Toeplitz results
+                // free-variable bits (kBitWordsLong words)
     int poff;   // row layout: word offset of the per-lag P values Q[0 .. n_max) (0: none)
-    int xp;     // two walkers per warp: floats per class of the walker's Toeplitz results
-                // X[2][xp] at word offset xoff (0: none)
+    int roff;   // tensor-core layouts: word offset of the Toeplitz results X[2][xp]
+    int xp;     // floats per class of the Toeplitz results (0: no tensor-core product)
     int hoff;   // tensor-core layouts: word offset of FP16 rows (copies of the rows in the
                 // walk, the only rows in the row kernels), class p at hoff + p hlen, entry
                 // u at half index hpad + u, zero around the class
@@ -201,8 +200,12 @@ __host__ __device__ inline int block_R(int n, int tile)
     return conflict_free_R((((n + 1) >> 1) + h - 1) / h, tile);
 }
 
-// n_max: largest number of free variables served; tile: lanes per walker (32, 16 or 8).
-__host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
+// Shared memory of one SM that the walk layouts may fill (of 228 KB, 1 KB per CTA kept).
+constexpr int kSmemBudget = 226 * 1024;
+
+// n_max: largest number of free variables served; tile: lanes per walker (32, 16 or 8);
+// tc: with the regions of the tensor-core Toeplitz product (FP16 rows, results).
+__host__ __device__ inline WarpSmem warp_layout(int n_max, int tile, bool tc)
 {
     WarpSmem w;
     const int R = block_R(n_max, tile);
@@ -229,9 +232,9 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
         int lo = n_max > span ? n_max : span;
         int gtop = top > span ? top : span;
         int gdeep = 0;
-        if (tile == 16 && n_max <= 128) {
-            // the Toeplitz product on the tensor cores (both walkers of a warp) reads the
-            // table from y = -(16 T - 1) up to 16 S, with S = ceil(n/16) row blocks and
+        if (tc) {
+            // the Toeplitz product on the tensor cores reads the table from
+            // y = -(16 T - 1) up to 16 S, with S = ceil(n/16) row blocks and
             // T = ceil(ceil(n/2) / 16) output blocks
             const int S = (n_max + 15) >> 4, T = (((n_max + 1) >> 1) + 15) >> 4;
             if (gtop < 16 * S) gtop = 16 * S;
@@ -261,25 +264,41 @@ __host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
     w.xoff = 0;
     w.poff = 0;
     w.xp = 0;
+    w.roff = 0;
     w.hoff = 0;
     w.hlen = 0;
     w.hpad = 0;
     w.words = (w.boff + 4 * kBitVec + 3) & ~3;
-    if (tile == 16 && n_max <= 128) {
-        // the tensor-core Toeplitz product (n_max <= 128: one product per diagonal
-        // covers the outputs).  Its results: 16 T outputs per class written, (tile/2) R
-        // read; xp = 16 (mod 32) puts the two classes' entries in different banks
+    if (tc) {
+        // the tensor-core Toeplitz product.  Its results: 16 T outputs per class written,
+        // (tile/2) R read; xp = 16 (mod 32) puts the two classes' entries in different
+        // banks
         const int T = (((n_max + 1) >> 1) + 15) >> 4, S = (n_max + 15) >> 4;
         const int need = 16 * T > (tile / 2) * R ? 16 * T : (tile / 2) * R;
-        w.xoff = w.words;
+        w.roff = w.words;
         w.xp = ((need + 15) & ~31) + 16;
         // FP16 rows: u from -kTcPad up to 16 S + kTcPad (16 S + 96 halves)
-        w.hoff = w.xoff + 2 * w.xp;
+        w.hoff = w.roff + 2 * w.xp;
         w.hpad = kTcPad;
         w.hlen = ((8 * S + kTcPad + 3) & ~7) + 4;
         w.words = w.hoff + 2 * w.hlen;
     }
     return w;
+}
+
+// The walk layout of n_max free variables with `tile` lanes per walker.  Two walkers per
+// warp take the tensor-core Toeplitz product up to n_max = 128 (one product per block
+// diagonal covers the outputs); one walker per warp takes it when its regions keep the
+// 16 walkers of two 8-warp CTAs within an SM's shared memory; four walkers per warp keep
+// the FP32 product.
+__host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
+{
+    if (tile == 16) return warp_layout(n_max, tile, n_max <= 128);
+    if (tile == 32) {
+        const WarpSmem w = warp_layout(n_max, tile, true);
+        if (w.words * 4 * 16 <= kSmemBudget) return w;
+    }
+    return warp_layout(n_max, tile, false);
 }
 
 // Layout of one row of the stateless row kernels (labs_neighbor_delta), `tile` lanes per
@@ -325,7 +344,8 @@ __host__ __device__ inline WarpSmem row_smem(int n_max, int tile)
         const int need = 16 * T > vtop ? 16 * T : vtop;
         w.xp = ((need + 15) & ~31) + 16;
         w.poff = (w.boff + 3) & ~3;
-        w.xoff = w.poff;
+        w.xoff = 0;
+        w.roff = w.poff;
         const int q = 2 * w.xp > n_max ? 2 * w.xp : n_max;
         w.words = w.poff + ((q + 3) & ~3);
         return w;
@@ -351,6 +371,7 @@ __host__ __device__ inline WarpSmem row_smem(int n_max, int tile)
     w.bvec = 0;
     w.xoff = 0;
     w.xp = 0;
+    w.roff = 0;
     w.hoff = 0;
     w.hlen = 0;
     w.hpad = 0;
@@ -381,7 +402,7 @@ __host__ __device__ inline int long_R(int n, int threads)
 // Shared-memory layout of one long walker (one CTA): the rows and the table as in the
 // warp layout (bounds from the tile code with tile = the CTA width), bit vectors sized
 // for n_max, then the CTA scratch, the bits and the best-first queue's keys.
-__host__ __device__ inline WarpSmem long_smem(int n_max, int tile)
+__host__ __device__ inline WarpSmem long_layout(int n_max, int tile, bool tc)
 {
     WarpSmem w;
     const int R = long_R(n_max, tile);
@@ -395,25 +416,53 @@ __host__ __device__ inline WarpSmem long_smem(int n_max, int tile)
     if (n_max + (tile / 2 + 2) * R > hi) hi = n_max + (tile / 2 + 2) * R;
     if (n_max + 2 * R > lo) lo = n_max + 2 * R;
     if (n_max + 2 * R > gtop) gtop = n_max + 2 * R;
+    const int S = (n_max + 15) >> 4, T = (((n_max + 1) >> 1) + 15) >> 4;
+    if (tc && gtop < 16 * S) gtop = 16 * S;  // the tensor-core product's table reads
     w.apad = (lo + 3) & ~3;
     w.alen = w.apad + ((hi + 7) & ~7);
     w.gpad = (tile / 2) * R > span ? (tile / 2) * R : span;
+    if (tc && w.gpad < 16 * T - 1) w.gpad = 16 * T - 1;
     w.glen = w.gpad + gtop;
     w.goff = 2 * w.alen;
     w.boff = w.goff + 2 * w.glen;
     w.bvec = (n_max + 31) / 32 + 2;
-    w.xoff = (w.boff + 4 * w.bvec + 3) & ~3;
     w.poff = 0;
     w.xp = 0;
+    w.roff = 0;
     w.hoff = 0;
     w.hlen = 0;
     w.hpad = 0;
+    w.xoff = (w.boff + 4 * w.bvec + 3) & ~3;
+    if (tc) {
+        // FP16 rows (cleared with the rows, below xoff): u from -kTcPad up to 16 S + kTcPad
+        w.hoff = w.xoff;
+        w.hpad = kTcPad;
+        w.hlen = ((8 * S + kTcPad + 3) & ~7) + 4;
+        w.xoff = w.hoff + 2 * w.hlen;
+    }
     // scratch, bits, then the best-first search's queue keys (LABS_QUEUE_SIZE 64-bit
     // words), each warp's lowest candidate keys (32 per warp), the keys entered in a
     // round, two words of round state and the entered keys' places (LABS_QUEUE_SIZE ints)
     w.words = w.xoff + tile + kBitWordsLong + 2 * LABS_QUEUE_SIZE + 2 * tile + 2 * LABS_QUEUE_SIZE + 4 +
               LABS_QUEUE_SIZE;
+    if (tc) {
+        // the tensor-core product's results X[2][xp] (16 T written, (tile/2) R read per class)
+        const int need = 16 * T > (tile / 2) * R ? 16 * T : (tile / 2) * R;
+        w.xp = ((need + 15) & ~31) + 16;
+        w.roff = (w.words + 3) & ~3;
+        w.words = w.roff + 2 * w.xp;
+    }
     return w;
+}
+
+// The long layout (one walker per CTA of `tile` threads) takes the tensor-core Toeplitz
+// product when its regions keep the kLongThreads / tile CTAs of an SM within its shared
+// memory.
+__host__ __device__ inline WarpSmem long_smem(int n_max, int tile)
+{
+    const WarpSmem w = long_layout(n_max, tile, true);
+    if ((int64_t)w.words * 4 * (kLongThreads / tile) <= kSmemBudget) return w;
+    return long_layout(n_max, tile, false);
 }
 
 // Largest ISL for which the long walk's fp32 neighbourhood stays exact.  Every value in

@@ -129,8 +129,7 @@ __device__ int long_load_rows(const LongWalk& lw, const WarpSmem& SL, int* base,
         const int f = j <= c ? j : 2 * c - j;
         const int x = ((lw.bits[f >> 5] >> (f & 31)) & 1u) ? -1 : 1;
         const int s = (j > c && ((j - c) & 1)) ? -x : x;
-        if (j & 1) V.A1[j >> 1] = (float)s;
-        else V.A0[j >> 1] = (float)s;
+        set_row(V, j & 1, j >> 1, (float)s);
     }
     t.sync();
     return build_table(V, n, t);
@@ -248,7 +247,7 @@ __device__ void long_walk(const LongWalk& lw, Walker& w, int64_t until, const Wa
         int dl[R];
         {
             float X[R];
-            toeplitz(V, n, o, X);
+            toeplitz_one(V, SL, n, o, t, X);
             assemble(V, n, o, X, P, dl);
         }
         // lowest (dISL, i) whose result is not in HT
@@ -341,7 +340,7 @@ __device__ void long_walk_psl(const LongWalk& lw, Walker& w, PslTrack& ps, int64
         int dl[R], pl[R];
         {
             float X[R];
-            toeplitz(V, n, o, X);
+            toeplitz_one(V, SL, n, o, t, X);
             assemble(V, n, o, X, P, dl);
         }
         psl_eval(V, n, o, pl);
@@ -472,7 +471,7 @@ __device__ void long_walk_bestfirst(const LongWalk& lw, Walker& w, int64_t until
         int dl[R];
         {
             float X[R];
-            toeplitz(V, n, o, X);
+            toeplitz_one(V, SL, n, o, t, X);
             assemble(V, n, o, X, P, dl);
         }
         // the queue's last entry at the start of the step (empty place: no bound)
@@ -829,8 +828,7 @@ __global__ void __launch_bounds__(NT, kLongThreads / NT) long_delta_kernel(const
                 const int m = src[2 * c - j];
                 ok = ok && (v == ((((j - c) & 1) ? -m : m)));
             }
-            if (j & 1) V.A1[j >> 1] = (float)v;
-            else V.A0[j >> 1] = (float)v;
+            set_row(V, j & 1, j >> 1, (float)v);
         }
         const bool all_ok = t.rmin(ok ? 1 : 0) != 0;
         int32_t* dst = out + row * (int64_t)n;
@@ -853,7 +851,7 @@ __global__ void __launch_bounds__(NT, kLongThreads / NT) long_delta_kernel(const
         int dl[R];
         {
             float X[R], P[R];
-            toeplitz(V, n, o, X);
+            toeplitz_one(V, SL, n, o, t, X);
             p_direct(V, n, o, P);
             assemble(V, n, o, X, P, dl);
         }

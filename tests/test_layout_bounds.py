@@ -32,15 +32,16 @@ def layouts(tmp_path_factory):
         v = list(map(int, f[1:]))
         if f[0] == "row":
             row[(v[0], v[1])] = dict(apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], boff=v[7], poff=v[8],
-                                     words=v[9], R=v[10], xoff=v[11], xp=v[12], hoff=v[13], hlen=v[14], hpad=v[15])
+                                     words=v[9], R=v[10], roff=v[11], xp=v[12], hoff=v[13], hlen=v[14], hpad=v[15])
         elif f[0] == "warp":
             tile, n = v[0], v[1]
             warp[(tile, n)] = dict(apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], xoff=v[7], words=v[8],
-                                   R=v[9], xp=v[10], hoff=v[11], hlen=v[12], hpad=v[13])
+                                   R=v[9], xp=v[10], hoff=v[11], hlen=v[12], hpad=v[13], roff=v[14])
         else:
             nt, n = v[0], v[1]
             long_[(nt, n)] = dict(nt=nt, apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], xoff=v[7],
-                                  words=v[8], R=v[9], limit=v[10], psl_only=v[11])
+                                  words=v[8], R=v[9], limit=v[10], psl_only=v[11], xp=v[12], hoff=v[13],
+                                  hlen=v[14], hpad=v[15], roff=v[16])
     return warp, long_, row
 
 
@@ -114,29 +115,31 @@ def common(reg, n, tile, R, valid_only, bits=True):
     reg.b(((n + 31) // 32), "bits zero word")
 
 
-def tensor_core_reads(reg, S, n, R):
-    """Every table, FP16-row and scratch index of toeplitz_tc (two walkers per warp,
-    n <= 128: one product per diagonal, d = -(T-1) .. S-1)."""
+def tensor_core_reads(reg, S, n, R, half=8):
+    """Every table, FP16-row and scratch index of the tensor-core Toeplitz product
+    (toeplitz_tc, toeplitz_tc1): column groups m of 4 output blocks per class, block
+    diagonals d = -min(4m+3, T-1) .. S-1-4m; `half` lanes per class read R outputs each."""
     nS = (n + 15) >> 4
     nT = (((n + 1) >> 1) + 15) >> 4
-    assert nT <= 4
-    nd = nS + nT - 1
-    ys = [-16 * (nT - 1) + 2 * tq - g for tq in range(4) for g in range(8)]
-    reg.g(min(ys) - 8, "tc table first")
-    for k in (0, nd - 1):
-        reg.g(min(ys) + 16 * k, "tc table")
-        reg.g(max(ys) + 16 * k + 8 + 1, "tc table + 8")
-        for tb in range(4):
-            for tq in (0, 3):
-                u = 16 * (tb - (nT - 1) + k) + 2 * tq
-                reg.h(u, "tc rows")
-                reg.h(u + 9, "tc rows + 9")
-    for tx in (0, 2):
-        for t in (tx, tx + 1):
-            if t < nT and not 16 * t + 15 < S["xp"]:
-                reg.bad.append(("X write", t))
-    if not ((S["xp"] & 31) == 16 and 8 * R <= S["xp"]):
-        reg.bad.append(("X scratch", S["xoff"], S["xp"]))
+    for m in range((nT + 3) // 4):
+        dlo = -min(4 * m + 3, nT - 1)
+        nd = nS - 4 * m - dlo
+        ys = [16 * dlo + 2 * tq - g for tq in range(4) for g in range(8)]
+        reg.g(min(ys) - 8, "tc table first")
+        for k in (0, nd - 1):
+            reg.g(min(ys) + 16 * k, "tc table")
+            reg.g(max(ys) + 16 * k + 8 + 1, "tc table + 8")
+            for tb in range(4):
+                for tq in (0, 3):
+                    u = 16 * (tb + 4 * m + dlo + k) + 2 * tq
+                    reg.h(u, "tc rows")
+                    reg.h(u + 9, "tc rows + 9")
+        for tx in (0, 2):
+            for t in (tx + 4 * m, tx + 4 * m + 1):
+                if t < nT and not 16 * t + 15 < S["xp"]:
+                    reg.bad.append(("X write", t))
+    if not ((S["xp"] & 31) == 16 and half * R <= S["xp"]):
+        reg.bad.append(("X scratch", S["roff"], S["xp"]))
     if not ((S["hlen"] & 7) == 4 and (S["hpad"] & 1) == 0):
         reg.bad.append(("FP16 rows", S["hlen"], S["hpad"]))
 
@@ -189,12 +192,17 @@ def test_warp_layouts(layouts):
                             covered.update(range(m0, m0 + R))
                     if not set(range(1, min(n, 4 * R))) <= covered:
                         reg.bad.append(("mirror coverage", n, R))
-                if tile == 16 and n_max <= 128:   # the Toeplitz product on the tensor cores
-                    tensor_core_reads(reg, S, n, R)
-                    if not (S["xoff"] + 2 * S["xp"] <= S["hoff"] and S["hoff"] + 2 * S["hlen"] <= S["words"]):
-                        reg.bad.append(("regions", S["xoff"], S["hoff"], S["words"]))
-                    reg.h(-48, "tc rows low")
-                    reg.h(n - 1, "tc row copy")
+                if tile == 16 and n_max <= 128 and not S["xp"]:
+                    reg.bad.append(("no tensor-core regions", n_max))
+                if S["xp"]:             # the Toeplitz product on the tensor cores
+                    if tile == 8:
+                        reg.bad.append(("tensor-core regions with four walkers per warp", n_max))
+                    tensor_core_reads(reg, S, n, R, tile // 2)
+                    if not (S["roff"] + 2 * S["xp"] <= S["hoff"] and S["hoff"] + 2 * S["hlen"] <= S["words"]):
+                        reg.bad.append(("regions", S["roff"], S["hoff"], S["words"]))
+                    reg.h(n - 1, "row copy")
+                    if tile == 32 and S["words"] * 4 * 16 > 226 * 1024:
+                        reg.bad.append(("two 8-warp CTAs do not fit", S["words"]))
                 if tile == 32:          # the PSL neighbourhood
                     if R <= 5:
                         P = 3 * R - 2
@@ -227,12 +235,21 @@ def test_long_layouts(layouts):
         # 32 queue keys, nt / 32 warps x 32 candidate keys, 32 entered keys (all 64-bit, so
         # 8-byte aligned), two words of round state and 32 places
         q = S["xoff"] + nt + 176
-        assert nt * R >= n_max and S["words"] >= q + 2 * 32 + 2 * nt + 2 * 32 + 4 + 32
+        end = q + 2 * 32 + 2 * nt + 2 * 32 + 4 + 32
+        assert nt * R >= n_max and S["words"] >= end
         assert q % 2 == 0
         assert S["words"] * 4 <= {512: 227, 256: 113, 128: 56}[nt] * 1024  # one, two or four CTAs per SM
+        if S["xp"]:
+            # FP16 rows between the bit vectors and the scratch (cleared with the rows), the
+            # product's results after everything else
+            assert S["hoff"] + 2 * S["hlen"] <= S["xoff"], (nt, n_max)
+            assert S["roff"] >= end and S["roff"] + 2 * S["xp"] <= S["words"], (nt, n_max)
         for n in sorted({257, (257 + n_max) // 2, n_max}):
             reg = Region(S)
             common(reg, n, nt, R, valid_only=True)
+            if S["xp"]:
+                tensor_core_reads(reg, S, n, R, nt // 2)
+                reg.h(n - 1, "row copy")
             c = n - 1
             for vb in (0, c >> 1):
                 reg.a(vb + n - 1, "flip up")
@@ -294,7 +311,7 @@ def row_tensor_core(reg, S, n, R):
     if S["glen"] - S["gpad"] < 16 * nS:     # E is zero from n up to what the product reads
         reg.bad.append(("table top", S["glen"] - S["gpad"]))
     q = max(n, 2 * S["xp"])
-    if not (S["xoff"] == S["poff"] >= S["boff"] and S["poff"] + q <= S["words"]):
+    if not (S["roff"] == S["poff"] >= S["boff"] and S["poff"] + q <= S["words"]):
         reg.bad.append(("Q / X region", S["poff"], S["xp"], S["words"]))
     if not (S["hoff"] + 2 * S["hlen"] <= S["boff"] - 2 * S["glen"]):   # rows, then the table
         reg.bad.append(("FP16 rows overlap the table", S["hoff"], S["hlen"]))
