@@ -90,7 +90,9 @@ typedef struct labs_config {
                                     stops that walker and labs_sync returns LABS_ESTATE */
 #define LABS_FLAG_LEARNED 4      /* reserve workspace for the learned mode (labs_learned) */
 #define LABS_FLAG_WARP_PER_WALKER 8 /* one walker per warp even where two per warp fit */
-#define LABS_FLAG_TWO_PER_WARP 16   /* at most two walkers per warp even where four fit */
+#define LABS_FLAG_TWO_PER_WARP 16   /* at most two walkers per warp even where four fit,
+                                       and two (FP32 Toeplitz product) where one per warp
+                                       would run (n = 129..160) */
 #define LABS_FLAG_BEST_FIRST 32     /* labs_walk runs Algorithm 1 as printed: best-first
                                        search with a queue of LABS_QUEUE_SIZE evaluated
                                        neighbours per walker (see labs_walk); one walker per

@@ -301,7 +301,9 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     // launch shape of the walk kernel: four walkers per warp (8 lanes each) while 8
     // lanes cover n with at most kQuadMaxR outputs per lane (n <= 80; measured faster
     // than two per warp there, equal from n = 88 to 104), two walkers per warp (16 lanes
-    // each) up to 10 outputs per lane (n <= 160), else one walker per warp (the learned
+    // each, the Toeplitz product on the tensor cores) up to n = 128, else one walker per
+    // warp (tensor-core product; measured 7-12% faster than two walkers per warp with the
+    // FP32 product from n = 129 to 160, which LABS_FLAG_TWO_PER_WARP keeps; the learned
     // mode runs one walker per warp)
     if (c->long_mode) {
         // one walker per CTA of 256 or 512 threads
@@ -319,7 +321,7 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
         c->chunk = k.chunk_steps ? k.chunk_steps : 64;
     } else {
         if ((k.flags & (LABS_FLAG_WARP_PER_WALKER | LABS_FLAG_LEARNED | LABS_FLAG_BEST_FIRST | LABS_FLAG_PSL)) ||
-            lanes_for(c->n_max, 16) > 10)
+            lanes_for(c->n_max, 16) > 10 || (c->n_max > 128 && !(k.flags & LABS_FLAG_TWO_PER_WARP)))
             c->tile = 32;
         else if (!(k.flags & LABS_FLAG_TWO_PER_WARP) && lanes_for(c->n_max, 8) <= kQuadMaxR)
             c->tile = 8;
