@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--no-delta", action="store_true")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-length line (52 odd lengths 201..303 x 2048 walkers in one launch)")
+    ap.add_argument("--no-scaleup", action="store_true",
+                    help="skip the scale-up key (L=303 and 501, 131072 walkers x 2e4 steps each)")
     ap.add_argument("--mixed-walkers", type=int, default=2048)
     ap.add_argument("--mixed-steps", type=int, default=5000)
     ap.add_argument("--no-tune", action="store_true")
@@ -466,11 +468,16 @@ def run_ours(args):
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h)}
 
     delta = None if args.no_delta else delta_kernel_line(args, dev, stream, labs)
-    mixed = None
-    if not args.no_mixed and world == 1 and args.search == "walk":
+    mixed = scaleup = None
+    if world == 1 and args.search == "walk" and not (args.no_mixed and args.no_scaleup):
         s.close()
         torch.cuda.empty_cache()
-        mixed = mixed_line(args, dev, labs)
+        if not args.no_mixed:
+            mixed = mixed_line(args, dev, labs)
+        if not args.no_scaleup:
+            # config 5 (the walks; its learned arm is --config learned's measurement)
+            total, per_L, workload, _ = scaleup_measure(args, dev, labs)
+            scaleup = {"workload": workload, "value": total, "unit": UNIT, "per_L": per_L}
     if args.search == "psl":
         # lowest (PSL, ISL) pair over ranks: PSL < 2^9 above ISL < 2^26 in one key
         obj, best_rank = replicas.best_over_ranks((st["best_psl"] << 26) | st["best_isl"], device=dev)
@@ -494,6 +501,7 @@ def run_ours(args):
                               "rank": best_rank}, **({"psl": best_psl} if args.search == "psl" else {})),
                 "delta_kernel": delta,
                 "mixed_201_303": mixed,
+                "scaleup_303_501": scaleup,
                 "restarts": st["restarts"]}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)
@@ -541,17 +549,12 @@ def run_learned(args):
     return 0
 
 
-def run_scaleup(args):
-    """Config 5: L=303 and L=501, 131072 walkers each, 2e4 steps of the plain walk (the
-    learned proposal is measured by --config learned): flips/s, the walk kernel's
-    roofline fraction, best F and the time to F >= 8 (sampled every 1000 steps); one
-    JSON line."""
+def scaleup_measure(args, dev, labs):
+    """Config 5's walks: L=303 and L=501, scaleup_walkers walkers each, scaleup_steps
+    steps (segments of 1000, best ISL read after each): per-length flips/s, roofline
+    fractions, best F and the time to F >= 8; and the time-weighted aggregate."""
     import torch
 
-    import paper_2011_00068_gb300 as labs
-
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = float(measured_peaks().get("sm_max_mhz", 2070.0))
     peak = FP32_LANES_PER_SM * 2 * sms * sm_mhz * 1e6
@@ -586,14 +589,30 @@ def run_scaleup(args):
         del s
         torch.cuda.empty_cache()
     total = sum(v["flips_per_s"] * v["seconds"] for v in out.values()) / sum(v["seconds"] for v in out.values())
+    workload = ("L=303 and L=501, %d walkers each, %d steps, seed 42, uniform random +-1 Philox starts, HT 2^16 "
+                "slots/walker" % (args.scaleup_walkers, args.scaleup_steps))
+    peak_source = ("fma_frac: derived, %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz (FMA pipe); tensor_frac: of "
+                   "measured sustained BF16 GEMM rate %.1f TFLOP/s (FP16 shares the dense rate)"
+                   % (sms, FP32_LANES_PER_SM, sm_mhz, tensor_peak() / 1e12))
+    return total, out, workload, peak_source
+
+
+def run_scaleup(args):
+    """Config 5: L=303 and L=501, 131072 walkers each, 2e4 steps of the plain walk (the
+    learned proposal is measured by --config learned): flips/s, the walk kernel's
+    roofline fraction, best F and the time to F >= 8 (sampled every 1000 steps); one
+    JSON line."""
+    import torch
+
+    import paper_2011_00068_gb300 as labs
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    total, out, workload, peak_source = scaleup_measure(args, dev, labs)
     line = {"metric": "exact flip evaluations/sec, L=303 and L=501 scale-up", "value": total,
             "unit": "flip evaluations/s", "higher_is_better": True, "n_gpus": 1, "dtype": "f32",
             "data": "synthetic", "vs_baseline": None,
-            "config": {"workload": "L=303 and L=501, %d walkers each, %d steps, seed 42, uniform random +-1 Philox "
-                                   "starts, HT 2^16 slots/walker" % (args.scaleup_walkers, args.scaleup_steps),
-                       "peak_source": "fma_frac: derived, %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz (FMA pipe); "
-                                      "tensor_frac: of measured sustained BF16 GEMM rate %.1f TFLOP/s (FP16 shares "
-                                      "the dense rate)" % (sms, FP32_LANES_PER_SM, sm_mhz, tensor_peak() / 1e12)},
+            "config": {"workload": workload, "peak_source": peak_source},
             "per_L": out}
     print(json.dumps(line))
     return 0

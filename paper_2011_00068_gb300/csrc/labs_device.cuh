@@ -514,10 +514,10 @@ __device__ __forceinline__ void toeplitz_tc(const View& V, const WarpSmem& SL, i
 // The same product for one walker whose lane group spans W whole warps (one walker per
 // warp, W = 1, or per CTA): the output blocks form ceil(T/4) column groups of 4 blocks
 // per class, warp w takes groups w, w + W, ..., and for group m the block diagonals run
-// from -(4m+3) (or -(T-1)) up to S-1-4m.  Two accumulator chains per group (even and odd
-// diagonals; integer partial sums, so the split does not change the result).  The
-// results go through the walker's scratch X[2][xp] to the lanes' R outputs; the group's
-// barrier orders them.
+// from -(4m+3) (or -(T-1)) up to S-1-4m.  Two accumulator chains per warp (two groups,
+// or the even and odd diagonals of a lone group; integer partial sums, so the split does
+// not change the result).  The results go through the walker's scratch X[2][xp] to the
+// lanes' R outputs; the group's barrier orders them.
 template <class LG, int R>
 __device__ __forceinline__ void toeplitz_tc1(const View& V, const WarpSmem& SL, int n, const Outs<LG, R>& o,
                                              const LG& t, float (&X)[R])
@@ -530,28 +530,66 @@ __device__ __forceinline__ void toeplitz_tc1(const View& V, const WarpSmem& SL, 
     const float2* G = reinterpret_cast<const float2*>(base + SL.goff) + SL.gpad + (2 * tq - g);
     const uint32_t* H = reinterpret_cast<const uint32_t*>(base + SL.hoff + pb * SL.hlen) + (SL.hpad >> 1) + 8 * tb + tq;
     float* xs = reinterpret_cast<float*>(base + SL.roff) + px * SL.xp + g;
-    for (int m = warp; m < M; m += W) {
-        const int dlo = -min(4 * m + 3, T - 1), nd = S - 4 * m - dlo;  // d = dlo .. S-1-4m
-        const float2* gy = G + 16 * dlo;
-        const uint32_t* ab = H + 8 * (4 * m + dlo);
-        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
-        uint32_t am = half2_bits(gy[-8]);
-        int k = 0;
-        for (; k + 1 < nd; k += 2) {
-            tc_diag(d0, gy, ab, am);
-            tc_diag(d1, gy + 16, ab + 8, am);
-            gy += 32;
-            ab += 16;
-        }
-        if (k < nd) tc_diag(d0, gy, ab, am);
-        const int t0 = tx + 4 * m;
-        if (t0 < T) {
-            xs[16 * t0] = d0[0] + d1[0];
-            xs[16 * t0 + 8] = d0[2] + d1[2];
-        }
-        if (t0 + 1 < T) {
-            xs[16 * t0 + 16] = d0[1] + d1[1];
-            xs[16 * t0 + 24] = d0[3] + d1[3];
+    // warp w takes groups m and m + W together: a diagonal's table fragment is loaded
+    // once for both (their diagonal ranges are shifted by 4W); a group without a partner
+    // runs alone with two chains (even and odd diagonals)
+    for (int m = warp; m < M; m += 2 * W) {
+        const int mb = m + W;
+        const int dloA = -min(4 * m + 3, T - 1), dhi = S - 1 - 4 * m;  // group m: d = dloA .. dhi
+        if (mb < M) {
+            const int dlo = -min(4 * mb + 3, T - 1), dhiB = dhi - 4 * W;  // group mb: d = dlo .. dhiB
+            const float2* gy = G + 16 * dlo;
+            const uint32_t* ab = H + 8 * (4 * m + dlo);  // group m's operand; mb's is 32 W words further
+            float dA[4] = {0.f, 0.f, 0.f, 0.f}, dB[4] = {0.f, 0.f, 0.f, 0.f};
+            uint32_t am = half2_bits(gy[-8]);
+            for (int d = dlo; d <= dhi; ++d) {
+                const uint32_t a0 = half2_bits(gy[0]), a2 = half2_bits(gy[8]);
+                if (d >= dloA) mma_16816(dA, a0, am, a2, a0, ab[0], ab[4]);
+                if (d <= dhiB) mma_16816(dB, a0, am, a2, a0, ab[32 * W], ab[32 * W + 4]);
+                am = a2;
+                gy += 16;
+                ab += 8;
+            }
+            const int tA = tx + 4 * m, tB = tx + 4 * mb;
+            if (tA < T) {
+                xs[16 * tA] = dA[0];
+                xs[16 * tA + 8] = dA[2];
+            }
+            if (tA + 1 < T) {
+                xs[16 * tA + 16] = dA[1];
+                xs[16 * tA + 24] = dA[3];
+            }
+            if (tB < T) {
+                xs[16 * tB] = dB[0];
+                xs[16 * tB + 8] = dB[2];
+            }
+            if (tB + 1 < T) {
+                xs[16 * tB + 16] = dB[1];
+                xs[16 * tB + 24] = dB[3];
+            }
+        } else {
+            const int nd = dhi - dloA + 1;
+            const float2* gy = G + 16 * dloA;
+            const uint32_t* ab = H + 8 * (4 * m + dloA);
+            float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+            uint32_t am = half2_bits(gy[-8]);
+            int k = 0;
+            for (; k + 1 < nd; k += 2) {
+                tc_diag(d0, gy, ab, am);
+                tc_diag(d1, gy + 16, ab + 8, am);
+                gy += 32;
+                ab += 16;
+            }
+            if (k < nd) tc_diag(d0, gy, ab, am);
+            const int t0 = tx + 4 * m;
+            if (t0 < T) {
+                xs[16 * t0] = d0[0] + d1[0];
+                xs[16 * t0 + 8] = d0[2] + d1[2];
+            }
+            if (t0 + 1 < T) {
+                xs[16 * t0 + 16] = d0[1] + d1[1];
+                xs[16 * t0 + 24] = d0[3] + d1[3];
+            }
         }
     }
     t.sync();
