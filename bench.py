@@ -431,7 +431,8 @@ def run_ours(args):
         achieved *= PSL_LANE_OPS_PER_LAG_TERM / ALGO_FLOP_PER_LAG_TERM
         peak /= 2
         unit = "Tops/s (FP32 lane operations)"
-    kernel = WALK_KERNELS[st["walkers_per_warp"]]
+    kernel = ("walk_psl_pair_kernel" if args.search == "psl" and st["walkers_per_warp"] == 2
+              else WALK_KERNELS[st["walkers_per_warp"]])
     steps_per_launch = args.walkers * args.walk_steps / nchunks
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": unit,
                 "frac": achieved / peak,

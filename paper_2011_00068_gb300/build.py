@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblabs.so")
-SOURCES = ["labs_walk8a.cu", "labs_walk8b.cu", "labs_walk16a.cu", "labs_walk16b.cu", "labs_walk32.cu", "labs_walk32l.cu", "labs_walk32b.cu", "labs_walk32p.cu", "labs_long.cu", "labs_kernels.cu", "labs_enum.cu", "labs_net.cu", "labs_api.cu"]
+SOURCES = ["labs_walk8a.cu", "labs_walk8b.cu", "labs_walk16a.cu", "labs_walk16b.cu", "labs_walk16p.cu", "labs_walk16q.cu", "labs_walk32.cu", "labs_walk32l.cu", "labs_walk32b.cu", "labs_walk32p.cu", "labs_long.cu", "labs_kernels.cu", "labs_enum.cu", "labs_net.cu", "labs_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

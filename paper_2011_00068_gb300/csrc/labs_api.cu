@@ -304,7 +304,9 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
     // each, the Toeplitz product on the tensor cores) up to n = 128, else one walker per
     // warp (tensor-core product; measured 7-12% faster than two walkers per warp with the
     // FP32 product from n = 129 to 160, which LABS_FLAG_TWO_PER_WARP keeps; the learned
-    // mode runs one walker per warp)
+    // mode and the best-first search run one walker per warp).  The PSL objective runs
+    // two walkers per warp up to n = 128 (LABS_FLAG_WARP_PER_WALKER: one per warp), one
+    // above.
     if (c->long_mode) {
         // one walker per CTA of 256 or 512 threads
         c->tile = long_threads(c->n_max, (k.flags & LABS_FLAG_PSL) != 0);
@@ -320,14 +322,17 @@ int setup(labs_ctx* c, const int32_t* Ls, const int64_t* counts, int32_t nL, uin
         c->grid = c->sms * c->ctas_per_sm;
         c->chunk = k.chunk_steps ? k.chunk_steps : 64;
     } else {
-        if ((k.flags & (LABS_FLAG_WARP_PER_WALKER | LABS_FLAG_LEARNED | LABS_FLAG_BEST_FIRST | LABS_FLAG_PSL)) ||
-            lanes_for(c->n_max, 16) > 10 || (c->n_max > 128 && !(k.flags & LABS_FLAG_TWO_PER_WARP)))
+        const bool psl = (k.flags & LABS_FLAG_PSL) != 0;
+        if (psl)
+            c->tile = c->n_max <= 128 && !(k.flags & LABS_FLAG_WARP_PER_WALKER) ? 16 : 32;
+        else if ((k.flags & (LABS_FLAG_WARP_PER_WALKER | LABS_FLAG_LEARNED | LABS_FLAG_BEST_FIRST)) ||
+                 lanes_for(c->n_max, 16) > 10 || (c->n_max > 128 && !(k.flags & LABS_FLAG_TWO_PER_WARP)))
             c->tile = 32;
         else if (!(k.flags & LABS_FLAG_TWO_PER_WARP) && lanes_for(c->n_max, 8) <= kQuadMaxR)
             c->tile = 8;
         else
             c->tile = 16;
-        const size_t per_warp = (size_t)warp_smem(c->n_max, c->tile).words * sizeof(int) * (kWarp / c->tile);
+        const size_t per_warp = (size_t)warp_smem(c->n_max, c->tile, psl).words * sizeof(int) * (kWarp / c->tile);
         int warps = k.warps_per_cta ? k.warps_per_cta : 8;
         for (;;) {
             c->smem_bytes = per_warp * (size_t)warps;
@@ -858,7 +863,8 @@ int labs_stats(labs_ctx* c, int32_t L, labs_counters* out)
     out->walkers_at_target = (int64_t)h.st_at_target;
     out->walkers_per_warp = kWarp / c->tile;  // 0 for long sequences: one walker per CTA
     out->lane_block = c->long_mode ? long_R(c->n_max, c->tile) : lanes_for(c->n_max, c->tile);
-    out->tensor_cores = (c->long_mode ? long_smem(c->n_max, c->tile).xp : warp_smem(c->n_max, c->tile).xp) != 0;
+    out->tensor_cores = (c->long_mode ? long_smem(c->n_max, c->tile).xp
+                                      : warp_smem(c->n_max, c->tile, (c->cfg.flags & LABS_FLAG_PSL) != 0).xp) != 0;
     out->target_step = h.st_target_step == LLONG_MAX ? -1 : (int64_t)h.st_target_step;
     out->best_psl = -1;
     if (h.best_key == ~0ull) {

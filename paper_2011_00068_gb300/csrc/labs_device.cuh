@@ -2133,6 +2133,201 @@ __device__ void walk_psl(const WalkEnv& env, Walker& w, PslTrack& ps, int64_t un
     }
 }
 
+// The lane's two lowest 64-bit keys above `floor` (~0 where there are fewer).
+template <int R>
+__device__ __forceinline__ void top2_above64(const uint64_t (&key)[R], uint64_t floor, uint64_t& b1, uint64_t& b2)
+{
+    b1 = ~0ull;
+    b2 = ~0ull;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint64_t k = key[r] > floor ? key[r] : ~0ull;
+        b2 = min(b2, max(b1, k));
+        b1 = min(b1, k);
+    }
+}
+
+// Lowest 64-bit value of the lane group: the lowest high word, then the lowest low word
+// among the lanes that hold it.
+template <class LG>
+__device__ __forceinline__ uint64_t group_min64(uint64_t v, const LG& t)
+{
+    const uint32_t hi = t.rminu((uint32_t)(v >> 32));
+    const uint32_t lo = t.rminu((uint32_t)(v >> 32) == hi ? (uint32_t)v : 0xFFFFFFFFu);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// The walk under the PSL objective with two walkers per warp in lockstep (Pair): the
+// dISL of every flip from the lockstep Toeplitz step (on the tensor cores when TC says
+// so, as in walk_lockstep), the PSL of every neighbour from psl_eval, and the candidate
+// rounds of walk_lockstep on the (PSL', ISL', i) keys: two candidates per round, the
+// first S HT slots of each probed by half of the walker's lanes, full probes for longer
+// chains.  The trajectory of each walker is exactly that of walk_psl: the lowest key
+// whose state is not in HT is taken, and the best, stagnation and restart rules are the
+// same.  Restarts run divergently per half (RT = Tile<16>).
+template <class LG, class RT, int R, int TC>
+__device__ void walk_psl_lockstep(const WalkEnv& env, Walker& w, PslTrack& ps, int64_t until, bool real, int* base,
+                                  const WarpSmem& SL, const View& V, int trace_slot, int64_t trace_start,
+                                  const LG& t, const RT& tt)
+{
+    constexpr int S = LG::kSize / 2;  // HT slots probed per candidate in a round
+    constexpr unsigned SM = (1u << S) - 1u;
+    const KParams& p = *env.p;
+    const int lane = t.lane, n = env.n;
+    const Outs<LG, R> o(t);
+    const int cap = p.probe_cap;
+    const uint32_t tmask = (uint32_t)env.tmask;  // HT slots <= 2^20
+    float P[R];
+    p_direct(V, n, o, P);
+    StopCheck stop;
+    stop.start(p, (threadIdx.x & 31) == 0);
+    for (;;) {
+        const bool act = real && w.steps < until;
+        if (!__any_sync(kFull, act)) break;
+        if (__any_sync(kFull, act && (w.steps & (kCheckEvery - 1)) == 0)) {
+            const int why = __shfl_sync(kFull, stop.poll(p, (threadIdx.x & 31) == 0), 0);
+            if (why) {
+                if (act && lane == 0) raise_error(p.status, why, (int)env.g);
+                break;
+            }
+        }
+        uint64_t key[R];
+        {
+            int dl[R], pl[R];
+            int rv;
+            {
+                float X[R];
+                if constexpr (TC == 1) {
+                    toeplitz_tc(V, SL, n, o, t.h, X);
+                } else if constexpr (TC == 2) {
+                    if (SL.xp)
+                        toeplitz_tc(V, SL, n, o, t.h, X);
+                    else
+                        toeplitz(V, n, o, X);
+                } else {
+                    toeplitz(V, n, o, X);
+                }
+                rv = lane_dl(V, n, o, X, P, dl);
+            }
+            psl_eval<LG, R>(V, n, o, pl);
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                key[r] = r < rv ? psl_key(pl[r], w.isl + dl[r], 2 * (o.v0 + r) + o.p) : ~0ull;
+        }
+
+        // Best admissible flip: candidates in ascending key order, two per round; keys
+        // <= floor are known to lead to visited states.
+        uint64_t floor = 0ull, kc = ~0ull;
+        int slot = -1;
+        uint64_t fnew = 0;
+        bool done = !act;
+        do {
+            uint64_t b1, b2;
+            top2_above64(key, floor, b1, b2);
+            const uint64_t k0 = group_min64(done ? ~0ull : b1, t);
+            const uint64_t k1 = group_min64(done ? ~0ull : (b1 == k0 ? b2 : b1), t);
+            const bool has0 = k0 != ~0ull, has1 = k1 != ~0ull;
+            const uint64_t f0 = w.fp ^ (has0 ? __ldg(env.zk + psl_key_i(k0)) : 0ull);
+            const uint64_t f1 = w.fp ^ (has1 ? __ldg(env.zk + psl_key_i(k1)) : 0ull);
+            const int hs = lane & (S - 1);
+            const bool second = lane >= S;
+            const uint64_t f = second ? f1 : f0;
+            const bool live = !done && (second ? has1 : has0) && hs < cap;
+            uint64_t e = 0;
+            if (live) e = env.T[((uint32_t)f + (uint32_t)hs) & tmask];
+            const bool match = live && e == ((f & ~kGenMask) | w.gen);
+            const bool hit = live && ((((uint32_t)e & (uint32_t)kGenMask) != w.gen) || match);
+            const unsigned hb = t.ballot(hit), mb = t.ballot(match);
+            const unsigned h0 = hb & SM, h1 = (hb >> S) & SM;
+            int st0 = !has0 ? kProbeNone
+                            : h0 ? ((mb & h0 & (0u - h0)) ? kProbeVisited : kProbeFree)
+                                 : (cap > S ? kProbeUnknown : kProbeFree);
+            int st1 = !has1 ? kProbeNone
+                            : h1 ? (((mb >> S) & h1 & (0u - h1)) ? kProbeVisited : kProbeFree)
+                                 : (cap > S ? kProbeUnknown : kProbeFree);
+            int s0 = -2, s1 = -2;
+            const bool need0 = !done && st0 == kProbeUnknown;
+            if (__any_sync(kFull, need0)) {
+                const Probe pf = lockstep_probe_full(env, f0, w.gen, cap, need0, t);
+                if (need0) {
+                    st0 = pf.visited ? kProbeVisited : kProbeFree;
+                    s0 = (int)pf.slot;
+                }
+            }
+            const bool need1 = !done && st0 == kProbeVisited && st1 == kProbeUnknown;
+            if (__any_sync(kFull, need1)) {
+                const Probe pf = lockstep_probe_full(env, f1, w.gen, cap, need1, t);
+                if (need1) {
+                    st1 = pf.visited ? kProbeVisited : kProbeFree;
+                    s1 = (int)pf.slot;
+                }
+            }
+            if (!done) {
+                if (st0 == kProbeFree) {
+                    kc = k0, fnew = f0, done = true;
+                    slot = s0 != -2 ? s0 : (h0 ? (int)(((uint32_t)f0 + (uint32_t)(__ffs(h0) - 1)) & tmask) : -1);
+                } else if (st0 == kProbeNone || st1 == kProbeNone) {
+                    done = true;  // every neighbour is in HT
+                } else if (st1 == kProbeFree) {
+                    kc = k1, fnew = f1, done = true;
+                    slot = s1 != -2 ? s1 : (h1 ? (int)(((uint32_t)f1 + (uint32_t)(__ffs(h1) - 1)) & tmask) : -1);
+                } else {
+                    floor = k1;
+                }
+            }
+        } while (__any_sync(kFull, !done));
+
+        // Apply the move (walkers that have one), from the values before the flip.
+        const bool moves = act && kc != ~0ull;
+        const int best_i = moves ? psl_key_i(kc) : 0;
+        apply_flip<LG, R>(V, n, o, lane, moves, best_i, P);
+        const bool stored = slot >= 0;
+        if (moves && lane == 0 && stored) env.T[slot] = (fnew & ~kGenMask) | w.gen;
+        if (moves && lane == (best_i >> 5)) w.word ^= 1u << (best_i & 31);
+        __syncwarp();
+        int code = 0;
+        bool again = false;
+        if (act) {
+            w.steps += 1;
+            if (!moves) {
+                w.blocked += 1;
+                again = true;
+                code = LABS_TRACE_BLOCKED;
+            } else {
+                w.fp = fnew;
+                w.isl = psl_key_isl(kc);
+                ps.psl = psl_key_psl(kc);
+                if (!stored) w.overflows += 1;
+                note_best(env, w, t, &ps);
+                if (psl_better(ps.psl, w.isl, ps.since_psl, w.since)) {
+                    w.since = w.isl;
+                    ps.since_psl = ps.psl;
+                    w.stag = 0;
+                } else {
+                    w.stag += 1;
+                }
+                code = best_i;
+                if (w.stag >= env.patience || !stored) {
+                    again = true;
+                    code |= LABS_TRACE_RESTART;
+                }
+            }
+        }
+        if (again) {  // divergent: only this half restarts
+            restart_walker(env, w, base, SL, V, tt, &ps);
+            p_direct(V, n, o, P);
+        }
+        __syncwarp();
+        if (act && trace_slot >= 0 && lane == 0) {
+            const int64_t s = w.steps - 1 - trace_start;
+            if (s >= 0 && s < p.status->trace_capacity) {
+                p.status->trace_code[trace_slot * p.status->trace_capacity + s] = code;
+                p.status->trace_isl[trace_slot * p.status->trace_capacity + s] = w.isl;
+            }
+        }
+    }
+}
+
 template <int TILE, int RMAX, int MODE>
 __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(KParams p, int chunk_index)
 {
@@ -2275,12 +2470,13 @@ __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_chunk_kernel(K
 // short sequences): the warp takes WPW consecutive walkers; when their lengths differ
 // (a group boundary) or fewer are left, it runs them one after the other with the other
 // lane groups idle.  RT is the tile type a lane group restarts with (divergently).
-template <class LG, class RT, int RMAX>
+// MODE 0: the plain walk; 3: the walk under the PSL objective (two walkers per warp).
+template <class LG, class RT, int RMAX, int MODE = 0>
 __device__ __forceinline__ void walk_group(const KParams& p, int chunk_index)
 {
     constexpr int WPW = 32 / LG::kSize;
     extern __shared__ __align__(16) int smem[];
-    const WarpSmem SL = warp_smem(p.n_max, LG::kSize);
+    const WarpSmem SL = warp_smem(p.n_max, LG::kSize, MODE == 3);
     const LG t(threadIdx.x & 31);
     const RT tt(threadIdx.x & 31);
     int* base = smem + (threadIdx.x / LG::kSize) * SL.words;
@@ -2326,7 +2522,7 @@ __device__ __forceinline__ void walk_group(const KParams& p, int chunk_index)
             int64_t until = min(target, steps_done + (int64_t)p.chunk_steps);
             bool real = real0 && steps_done < until;
             const int trace_slot = real ? env.st->trace_slot : -1;
-            if (real && S->learned) {
+            if (MODE == 0 && real && S->learned) {
                 // restart-only learned mode: the proposed restart state (and its record
                 // for a traced walker)
                 env.slot = S->l_slot + mine_w * kBitWords;
@@ -2344,8 +2540,18 @@ __device__ __forceinline__ void walk_group(const KParams& p, int chunk_index)
                 if (t.lane == 0) raise_error(p.status, LABS_ESTATE, (int)mine_w);
                 real = false;
             }
+            PslTrack ps;
+            if constexpr (MODE == 3) {
+                ps.psl = table_psl(V, G.n, t);
+                ps.best_psl = env.st->best_psl;
+                ps.since_psl = env.st->since_psl;
+                if (real && ps.psl != env.st->psl) {
+                    if (t.lane == 0) raise_error(p.status, LABS_ESTATE, (int)mine_w);
+                    real = false;
+                }
+            }
             labs_log_record* rec = nullptr;
-            if (real && S->log != nullptr && p.chunk_steps > 0) {
+            if (MODE == 0 && real && S->log != nullptr && p.chunk_steps > 0) {
                 const int64_t since = steps_done - S->log_start;
                 if (since >= 0 && since % p.chunk_steps == 0) {
                     const int64_t idx = (since / p.chunk_steps) * p.W + mine_w;
@@ -2359,18 +2565,41 @@ __device__ __forceinline__ void walk_group(const KParams& p, int chunk_index)
             constexpr int TC = LG::kSize != 16 ? 0 : RMAX <= 8 ? 1 : RMAX == 9 ? 2 : 0;
             int R = block_R(G.n, LG::kSize);
             if (R < RMAX - 3) R = conflict_free_R(RMAX - 3, LG::kSize);
-            if (R >= RMAX)
-                walk_lockstep<LG, RT, RMAX, TC>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec, t, tt);
-            else if (R == RMAX - 1)
-                walk_lockstep<LG, RT, (RMAX > 1 ? RMAX - 1 : 1), TC>(env, w, until, real, base, SL, V, trace_slot,
-                                                                 trace_start, rec, t, tt);
-            else if (R == RMAX - 2)
-                walk_lockstep<LG, RT, (RMAX > 2 ? RMAX - 2 : 1), TC>(env, w, until, real, base, SL, V, trace_slot,
-                                                                 trace_start, rec, t, tt);
-            else
-                walk_lockstep<LG, RT, (RMAX > 3 ? RMAX - 3 : 1), TC>(env, w, until, real, base, SL, V, trace_slot,
-                                                                 trace_start, rec, t, tt);
-            if (real) save_walker(env.st, w, t.lane);
+            if constexpr (MODE == 3) {
+                if (R >= RMAX)
+                    walk_psl_lockstep<LG, RT, RMAX, TC>(env, w, ps, until, real, base, SL, V, trace_slot, trace_start,
+                                                        t, tt);
+                else if (R == RMAX - 1)
+                    walk_psl_lockstep<LG, RT, (RMAX > 1 ? RMAX - 1 : 1), TC>(env, w, ps, until, real, base, SL, V,
+                                                                         trace_slot, trace_start, t, tt);
+                else if (R == RMAX - 2)
+                    walk_psl_lockstep<LG, RT, (RMAX > 2 ? RMAX - 2 : 1), TC>(env, w, ps, until, real, base, SL, V,
+                                                                         trace_slot, trace_start, t, tt);
+                else
+                    walk_psl_lockstep<LG, RT, (RMAX > 3 ? RMAX - 3 : 1), TC>(env, w, ps, until, real, base, SL, V,
+                                                                         trace_slot, trace_start, t, tt);
+            } else {
+                if (R >= RMAX)
+                    walk_lockstep<LG, RT, RMAX, TC>(env, w, until, real, base, SL, V, trace_slot, trace_start, rec, t,
+                                                    tt);
+                else if (R == RMAX - 1)
+                    walk_lockstep<LG, RT, (RMAX > 1 ? RMAX - 1 : 1), TC>(env, w, until, real, base, SL, V, trace_slot,
+                                                                     trace_start, rec, t, tt);
+                else if (R == RMAX - 2)
+                    walk_lockstep<LG, RT, (RMAX > 2 ? RMAX - 2 : 1), TC>(env, w, until, real, base, SL, V, trace_slot,
+                                                                     trace_start, rec, t, tt);
+                else
+                    walk_lockstep<LG, RT, (RMAX > 3 ? RMAX - 3 : 1), TC>(env, w, until, real, base, SL, V, trace_slot,
+                                                                     trace_start, rec, t, tt);
+            }
+            if (real) {
+                save_walker(env.st, w, t.lane);
+                if (MODE == 3 && t.lane == 0) {
+                    env.st->psl = ps.psl;
+                    env.st->best_psl = ps.best_psl;
+                    env.st->since_psl = ps.since_psl;
+                }
+            }
             __syncwarp();
         }
     }
@@ -2380,6 +2609,12 @@ template <int RMAX>
 __global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_pair_kernel(KParams p, int chunk_index)
 {
     walk_group<Pair, Tile<16>, RMAX>(p, chunk_index);
+}
+
+template <int RMAX>
+__global__ void __launch_bounds__(256, LABS_WALK_MIN_BLOCKS) walk_psl_pair_kernel(KParams p, int chunk_index)
+{
+    walk_group<Pair, Tile<16>, RMAX, 3>(p, chunk_index);
 }
 
 template <int RMAX>

@@ -204,8 +204,10 @@ __host__ __device__ inline int block_R(int n, int tile)
 constexpr int kSmemBudget = 226 * 1024;
 
 // n_max: largest number of free variables served; tile: lanes per walker (32, 16 or 8);
-// tc: with the regions of the tensor-core Toeplitz product (FP16 rows, results).
-__host__ __device__ inline WarpSmem warp_layout(int n_max, int tile, bool tc)
+// tc: with the regions of the tensor-core Toeplitz product (FP16 rows, results); psl:
+// two walkers per warp under the PSL objective (the rows and the table padded for the
+// PSL neighbourhood's reads, as every one-walker-per-warp layout is).
+__host__ __device__ inline WarpSmem warp_layout(int n_max, int tile, bool tc, bool psl = false)
 {
     WarpSmem w;
     const int R = block_R(n_max, tile);
@@ -240,10 +242,9 @@ __host__ __device__ inline WarpSmem warp_layout(int n_max, int tile, bool tc)
             if (gtop < 16 * S) gtop = 16 * S;
             gdeep = 16 * T - 1;
         }
-        if (tile == 32) {
-            // the PSL neighbourhood (one walker per warp) runs its lags 2R - 2 past n - 1:
-            // class entries from v0 - n - 2R up to v0 + n + 2R (v0 <= (tile/2 - 1) R) and
-            // the table up to n + 2R
+        if (tile == 32 || (psl && tile == 16)) {
+            // the PSL neighbourhood runs its lags 2R - 2 past n - 1: class entries from
+            // v0 - n - 2R up to v0 + n + 2R (v0 <= (tile/2 - 1) R) and the table up to n + 2R
             if (n_max + (tile / 2 + 2) * R > hi) hi = n_max + (tile / 2 + 2) * R;
             if (n_max + 2 * R > lo) lo = n_max + 2 * R;
             if (n_max + 2 * R > gtop) gtop = n_max + 2 * R;
@@ -290,10 +291,10 @@ __host__ __device__ inline WarpSmem warp_layout(int n_max, int tile, bool tc)
 // warp take the tensor-core Toeplitz product up to n_max = 128 (one product per block
 // diagonal covers the outputs); one walker per warp takes it when its regions keep the
 // 16 walkers of two 8-warp CTAs within an SM's shared memory; four walkers per warp keep
-// the FP32 product.
-__host__ __device__ inline WarpSmem warp_smem(int n_max, int tile)
+// the FP32 product.  psl: the layout of the PSL walk with two walkers per warp (tile 16).
+__host__ __device__ inline WarpSmem warp_smem(int n_max, int tile, bool psl = false)
 {
-    if (tile == 16) return warp_layout(n_max, tile, n_max <= 128);
+    if (tile == 16) return warp_layout(n_max, tile, n_max <= 128, psl);
     if (tile == 32) {
         const WarpSmem w = warp_layout(n_max, tile, true);
         if (w.words * 4 * 16 <= kSmemBudget) return w;
@@ -486,6 +487,8 @@ WalkFn walk_fn8a(int rmax);
 WalkFn walk_fn8b(int rmax);
 WalkFn walk_fn16a(int rmax);
 WalkFn walk_fn16b(int rmax);
+WalkFn walk_fn16p(int rmax);  // two walkers per warp, PSL objective, lane blocks 1-5 (labs_walk16p.cu)
+WalkFn walk_fn16q(int rmax);  // the same, lane blocks 6-9 (labs_walk16q.cu)
 WalkFn walk_fn32(int rmax);   // one walker per warp: plain walk
 WalkFn walk_fn32l(int rmax);  // learned mode (labs_walk32l.cu)
 WalkFn walk_fn32b(int rmax);  // best-first search (labs_walk32b.cu)

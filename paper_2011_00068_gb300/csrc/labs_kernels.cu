@@ -794,6 +794,7 @@ int launch_prep_walk(const KParams& p, int64_t steps, int nchunks, void* stream)
 static WalkFn walk_fn(int tile, int rmax, int mode)
 {
     if (tile == 8) return rmax <= 6 ? walk_fn8a(rmax) : walk_fn8b(rmax);
+    if (tile == 16 && mode == 3) return rmax <= 5 ? walk_fn16p(rmax) : walk_fn16q(rmax);
     if (tile == 16) return rmax <= 5 ? walk_fn16a(rmax) : walk_fn16b(rmax);
     switch (mode) {
         case 1: return walk_fn32l(rmax);

@@ -1,5 +1,6 @@
 // Prints the shared-memory layouts the kernels use (labs_internal.cuh, compiled for the
 // host): one line per (kind, tile, n_max): apad alen gpad glen bvec xoff words R xp hoff hlen hpad roff (the
+// walk, and as "warpp" the PSL walk with two walkers per warp; the
 // row layout: apad alen gpad glen bvec boff poff words R roff xp hoff hlen hpad; the long
 // layout: apad alen gpad glen bvec xoff words R limit psl xp hoff hlen hpad roff).
 #define __host__
@@ -19,6 +20,11 @@ int main()
             std::printf("warp %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d\n", tiles[ti], n, w.apad, w.alen, w.gpad,
                         w.glen, w.bvec, w.xoff, w.words, block_R(n, tiles[ti]), w.xp, w.hoff, w.hlen, w.hpad, w.roff);
         }
+    for (int n = 2; n <= 128; ++n) {  // the PSL walk with two walkers per warp
+        const WarpSmem w = warp_smem(n, 16, true);
+        std::printf("warpp 16 %d %d %d %d %d %d %d %d %d %d %d %d %d %d\n", n, w.apad, w.alen, w.gpad, w.glen, w.bvec,
+                    w.xoff, w.words, block_R(n, 16), w.xp, w.hoff, w.hlen, w.hpad, w.roff);
+    }
     for (int n = 2; n <= kMaxN; ++n) {  // the row kernels: two rows per warp up to n = 160
         const int tile = n <= 160 ? 16 : 32;
         const WarpSmem w = row_smem(n, tile);

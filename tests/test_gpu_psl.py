@@ -23,7 +23,7 @@ def traced(L, walkers, steps, seed, **cfg):
     return s, code.cpu().numpy(), isl.cpu().numpy()
 
 
-def check_results(s, o, walkers, steps, L):
+def check_results(s, o, walkers, steps, L, flags=0):
     res = s.results(seqs=True)
     for k in ("best_isl", "best_psl", "target_step"):
         assert np.array_equal(res[k], o[k]), k
@@ -32,7 +32,9 @@ def check_results(s, o, walkers, steps, L):
     assert np.array_equal(res["seq"], o["final_seq"])
     assert np.array_equal(res["best_seq"], o["best_seq"])
     st = s.stats()
-    assert st["steps"] == walkers * steps and st["walkers_per_warp"] == 1
+    # two walkers per warp up to n = 128 unless LABS_FLAG_WARP_PER_WALKER asks for one
+    pair = (L + 1) // 2 <= 128 and not flags & _native.LABS_FLAG_WARP_PER_WALKER
+    assert st["steps"] == walkers * steps and st["walkers_per_warp"] == (2 if pair else 1)
     assert st["flip_evaluations"] == walkers * steps * ((L + 1) // 2)
     assert st["restarts"] == int(o["restarts"].sum())
     assert st["overflows"] == int(o["overflows"].sum())
@@ -68,6 +70,27 @@ def test_psl_trajectory_parity(L, walkers, steps, kw):
     assert np.array_equal(isl, o["trace_isl"])
     check_results(s, o, walkers, steps, L)
     s.close()
+
+
+@pytest.mark.parametrize("L,walkers,steps,kw", [
+    (41, 7, 400, {}),
+    (101, 5, 300, {"tabu_log2": 5, "probe_cap": 9}),
+    (201, 9, 250, {}),
+    (255, 4, 200, {"patience": 40}),
+])
+def test_psl_two_walkers_per_warp_matches_one(L, walkers, steps, kw):
+    """Two walkers per warp (lockstep PSL step) and one walker per warp
+    (LABS_FLAG_WARP_PER_WALKER) give the same trajectories, results and counters, and
+    both match the oracle; odd walker counts leave a lone walker in the last warp, and a
+    small table with a probe cap above the 8 slots of a round takes the full probes."""
+    seed = 13
+    o = oracle.walk(L, seed, walkers, steps, trace=True, objective="psl", **kw)
+    for flags in (0, _native.LABS_FLAG_WARP_PER_WALKER):
+        s, code, isl = traced(L, walkers, steps, seed, flags=flags, **kw)
+        assert np.array_equal(code, o["trace_code"]), flags
+        assert np.array_equal(isl, o["trace_isl"]), flags
+        check_results(s, o, walkers, steps, L, flags)
+        s.close()
 
 
 def test_psl_chunking_graphs_and_mixed_lengths():

@@ -33,9 +33,9 @@ def layouts(tmp_path_factory):
         if f[0] == "row":
             row[(v[0], v[1])] = dict(apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], boff=v[7], poff=v[8],
                                      words=v[9], R=v[10], roff=v[11], xp=v[12], hoff=v[13], hlen=v[14], hpad=v[15])
-        elif f[0] == "warp":
+        elif f[0] in ("warp", "warpp"):
             tile, n = v[0], v[1]
-            warp[(tile, n)] = dict(apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], xoff=v[7], words=v[8],
+            warp[(tile if f[0] == "warp" else "psl16", n)] = dict(apad=v[2], alen=v[3], gpad=v[4], glen=v[5], bvec=v[6], xoff=v[7], words=v[8],
                                    R=v[9], xp=v[10], hoff=v[11], hlen=v[12], hpad=v[13], roff=v[14])
         else:
             nt, n = v[0], v[1]
@@ -219,6 +219,71 @@ def test_warp_layouts(layouts):
                         reg.a(v0max + R - 1, "psl sel init")
                 if reg.bad:
                     bad.append((tile, n_max, n, R, reg.bad[:3]))
+    assert not bad, bad[:5]
+
+
+def psl_reads(reg, n, R, v0max):
+    """The PSL neighbourhood (psl_eval): the ring form for lane blocks up to 5 (its lags
+    run 2R - 2 past n - 1), the select form above."""
+    if R <= 5:
+        P = 3 * R - 2
+        tend = n - 1 + 2 * (R - 1)
+        reg.a(v0max + P - 1, "psl ring init hi")
+        reg.a(1 - P, "psl ring init lo")
+        reg.g(1 - P, "psl ring init G")
+        reg.a(-tend, "psl a")
+        reg.a(v0max + tend, "psl b")
+        reg.g(tend, "psl C")
+    else:
+        reg.a(-(n - 1), "psl sel a")
+        reg.a(v0max + n + R - 2, "psl sel b")
+        reg.a(v0max + R - 1, "psl sel init")
+
+
+def test_psl_pair_layouts(layouts):
+    """The PSL walk with two walkers per warp (n_max <= 128): every access of the plain
+    lockstep step with two walkers per warp (rows, table, bit vectors, lag update, the
+    tensor-core product) and the PSL neighbourhood's reads for the lane blocks that
+    walk_group picks, inside the layout warp_smem(n_max, 16, psl)."""
+    warp, _, _ = layouts
+    bad = []
+    for n_max in range(2, 129):
+        S = warp[("psl16", n_max)]
+        plain = warp[(16, n_max)]
+        RMAX = S["R"]
+        if RMAX != plain["R"] or not S["xp"] or S["words"] < plain["words"]:
+            bad.append((n_max, "layout", RMAX, S["xp"], S["words"]))
+        for n in range(2, n_max + 1):
+            need = warp[(16, n)]["R"]
+            R = need if need >= RMAX - 3 else conflict_free_R(RMAX - 3, 16)
+            R = min(R, RMAX)
+            assert R >= need
+            reg = Region(S)
+            c = n - 1
+            common(reg, n, 16, R, valid_only=False)
+            v0max = 7 * R
+            for i in (0, 1, c - 1, c):
+                if i < 0:
+                    continue
+                vb, pb = i >> 1, i & 1
+                vq = vb if i == c else n - 1 - vb - pb
+                reg.a(vq, "vq")
+                reg.a(vb + 16 * R, "up")
+                reg.a(vb - 16 * R, "dn")
+                reg.a(2 * v0max + 2 * (R - 1) - vb, "p1")
+                reg.a(-vq, "p2")
+            reg.g(16 * R, "E load")
+            reg.g(-(1 + 15 * R) - R, "mirror E load")
+            tensor_core_reads(reg, S, n, R, 8)
+            if not (S["roff"] + 2 * S["xp"] <= S["hoff"] and S["hoff"] + 2 * S["hlen"] <= S["words"]):
+                reg.bad.append(("regions", S["roff"], S["hoff"], S["words"]))
+            reg.h(n - 1, "row copy")
+            psl_reads(reg, n, R, v0max)
+            if reg.bad:
+                bad.append((n_max, n, R, reg.bad[:3]))
+        # two 8-warp CTAs of 16 walkers each fit on an SM
+        if S["words"] * 4 * 16 * 2 > 226 * 1024:
+            bad.append((n_max, "two CTAs", S["words"]))
     assert not bad, bad[:5]
 
 
