@@ -110,9 +110,10 @@ typedef struct labs_config {
                                        (see labs_walk); lengths up to LABS_MAX_L */
 #define LABS_FLAG_PSL 64            /* labs_walk minimises PSL (Section 1) instead of ISL: the
                                        walk's rules with (PSL, ISL) pairs as the objective (see
-                                       labs_walk); one walker per warp (per CTA for long
-                                       sequences); not with LABS_FLAG_BEST_FIRST or
-                                       LABS_FLAG_LEARNED */
+                                       labs_walk); two walkers per warp up to L = 255 (one
+                                       with LABS_FLAG_WARP_PER_WALKER, the same trajectories),
+                                       one per warp above, one per CTA for long sequences;
+                                       not with LABS_FLAG_BEST_FIRST or LABS_FLAG_LEARNED */
 #define LABS_FLAG_LEARNED_RESTARTS 512 /* reserve workspace for the restart-only learned mode:
                                        labs_learned then runs only the restart half of the
                                        proposal pass (see labs_learned) and the walk keeps its
