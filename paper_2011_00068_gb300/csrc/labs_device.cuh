@@ -1358,6 +1358,21 @@ __device__ __forceinline__ void top2_above(const unsigned (&key)[R], unsigned fl
     }
 }
 
+// Removes free variable j from the lane's candidates (key `none`) when it is one of the
+// lane's outputs; j < 0: none.  The lockstep steps drop the move back to the previous
+// state this way: that state is in HT (every state of the walk since the last start
+// was inserted, and a failed insertion restarts the walker), so the probe would find
+// it visited, and leaving it out changes no choice while it saves most second rounds.
+template <class LG, int R, class K>
+__device__ __forceinline__ void drop_candidate(K (&key)[R], int j, const Outs<LG, R>& o, K none)
+{
+    const int d = (j >> 1) - o.v0;
+    const bool mine = j >= 0 && (j & 1) == o.p;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (mine && d == r) key[r] = none;
+}
+
 // Full probe of f for the walkers (halves) with need set: every lane runs the same rounds.
 template <class LG>
 __device__ __forceinline__ Probe lockstep_probe_full(const WalkEnv& env, uint64_t f, uint32_t gen, int cap, bool need,
@@ -1488,6 +1503,7 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
     const int64_t first_step = w.steps;
     int log_first = 0, log_min = w.isl;
     bool log_live = true;
+    int prev = -1;  // the last flip since the walker's (re)start in this call, or -1
     StopCheck stop;
     stop.start(p, (threadIdx.x & 31) == 0);
     if (real && rec != nullptr) {
@@ -1523,6 +1539,7 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
                 toeplitz_one(V, SL, n, o, t, X);
             }
             lane_keys(V, n, o, X, P, key);
+            drop_candidate(key, prev, o, 0xFFFFFFFFu);
         }
 
         // Best admissible flip, as in walk_steps: candidates in ascending key order, two
@@ -1631,9 +1648,11 @@ __device__ void walk_lockstep(const WalkEnv& env, Walker& w, int64_t until, bool
                 }
             }
         }
+        if (moves) prev = best_i;
         if (again) {  // two walkers per warp: divergent, only this half restarts
             restart_walker(env, w, base, SL, V, tt);
             p_direct(V, n, o, P);
+            prev = -1;
         }
         __syncwarp();
         if (act) {
@@ -2179,6 +2198,7 @@ __device__ void walk_psl_lockstep(const WalkEnv& env, Walker& w, PslTrack& ps, i
     const uint32_t tmask = (uint32_t)env.tmask;  // HT slots <= 2^20
     float P[R];
     p_direct(V, n, o, P);
+    int prev = -1;  // the last flip since the walker's (re)start in this call, or -1
     StopCheck stop;
     stop.start(p, (threadIdx.x & 31) == 0);
     for (;;) {
@@ -2213,6 +2233,7 @@ __device__ void walk_psl_lockstep(const WalkEnv& env, Walker& w, PslTrack& ps, i
 #pragma unroll
             for (int r = 0; r < R; ++r)
                 key[r] = r < rv ? psl_key(pl[r], w.isl + dl[r], 2 * (o.v0 + r) + o.p) : ~0ull;
+            drop_candidate(key, prev, o, ~(uint64_t)0);
         }
 
         // Best admissible flip: candidates in ascending key order, two per round; keys
@@ -2313,9 +2334,11 @@ __device__ void walk_psl_lockstep(const WalkEnv& env, Walker& w, PslTrack& ps, i
                 }
             }
         }
+        if (moves) prev = best_i;
         if (again) {  // divergent: only this half restarts
             restart_walker(env, w, base, SL, V, tt, &ps);
             p_direct(V, n, o, P);
+            prev = -1;
         }
         __syncwarp();
         if (act && trace_slot >= 0 && lane == 0) {
