@@ -49,9 +49,9 @@ PSL_LANE_OPS_PER_LAG_TERM = 4
 WALK_KERNELS = {4: "walk_quad_kernel", 2: "walk_pair_kernel", 1: "walk_chunk_kernel"}  # by walkers per warp
 # DRAM bytes per walker step of the L=201 walk kernel (ncu: dram__bytes_read.sum +
 # dram__bytes_write.sum of a 4864-walker x 256-step launch of the current kernel,
-# 288.8 + 31.3 MB over 1,245,184 walker steps, profiles/walk_pair_kernel_L201_16384w.md);
+# 373.1 + 33.6 MB over 1,245,184 walker steps, profiles/walk_pair_kernel_L201_16384w.md);
 # None when not captured for the current kernel
-DRAM_BYTES_PER_WALKER_STEP = 257.0
+DRAM_BYTES_PER_WALKER_STEP = 326.7
 
 
 def parse():

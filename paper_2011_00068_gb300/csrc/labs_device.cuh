@@ -1927,10 +1927,9 @@ __device__ __forceinline__ int psl_key_i(uint64_t k) { return (int)(k & 0x1FFFu)
 __device__ __forceinline__ int psl_key_isl(uint64_t k) { return (int)((k >> 13) & 0x3FFFFFFFull); }
 __device__ __forceinline__ int psl_key_psl(uint64_t k) { return (int)(k >> 43); }
 
-// The same PSL values for wide lane blocks (R >= 7), where the three rings of psl_eval
-// would not fit the registers: s_{i-2m} and s_{i+2m} of the R outputs in two windows of
-// R values that slide one class entry per lag (three shared loads per lag), and the
-// mirror's term dropped by a compare and select per lag term.
+// The same PSL values for the lane block R = 7 in one pass: s_{i-2m} and s_{i+2m} of the
+// R outputs in two windows of R values that slide one class entry per lag (three shared
+// loads per lag), and the mirror's term dropped by a compare and select per lag term.
 template <class TL, int R>
 __device__ __forceinline__ void psl_eval_select(const View& V, int n, const Outs<TL, R>& o, int (&pl)[R])
 {
@@ -1976,31 +1975,29 @@ __device__ __forceinline__ void psl_eval_select(const View& V, int n, const Outs
 // term (i+2m = L-1-i, i.e. m = c-i) left out, or by -2 s_c (s_{c-2m} + s_{c+2m}) at the
 // centre; the odd-lag C_k stay zero.  pl[r] = max_m |C_{2m} + dC_{2m}(i)| over
 // m = 1..n-1 (Section 1's PSL).
-// Output r takes lag m = t - 2r at iteration t, so that every output of the lane meets
-// its mirror at the same iteration t* = c - p - 2 v0 (where m = c - i): there one
+// psl_ring takes the outputs C0 .. C0+RC-1 of the lane (block start w0 = v0 + C0).
+// Output r takes lag m = t - 2r at iteration t, so that every output of the pass meets
+// its mirror at the same iteration t* = c - p - 2 w0 (where m = c - i): there one
 // multiplier z = 0 drops the mirror term of all of them, and a lag term costs three
-// instructions (FMA, FMA, max of the absolute value).  s_{i-2m} = A_p[v0 + 3r - t],
-// C_{2m} = E[t - 2r] and s_{i+2m} = A_p[v0 + t - r] come from three register rings of
-// P = 3R - 2 entries indexed by t mod P (one new shared load each per iteration, the
+// instructions (FMA, FMA, max of the absolute value).  s_{i-2m} = A_p[w0 + 3r - t],
+// C_{2m} = E[t - 2r] and s_{i+2m} = A_p[w0 + t - r] come from three register rings of
+// P = 3 RC - 2 entries indexed by t mod P (one new shared load each per iteration, the
 // loop unrolled by P so that the ring indices are constants).  Lags outside 1..n-1 (the
-// first 2R - 2 and the last iterations) are masked in the blocks that hold them.  Exact
-// in fp32: every value is an integer of magnitude below 2^10.
-template <class TL, int R>
-__device__ __forceinline__ void psl_eval(const View& V, int n, const Outs<TL, R>& o, int (&pl)[R])
+// first 2 RC - 2 and the last iterations) are masked in the blocks that hold them.
+// Exact in fp32: every value is an integer of magnitude below 2^10.
+template <class TL, int R, int C0, int RC>
+__device__ __forceinline__ void psl_ring(const View& V, int n, const Outs<TL, R>& o, int (&pl)[R])
 {
-    if constexpr (R >= 7) {
-        psl_eval_select<TL, R>(V, n, o, pl);
-        return;
-    }
-    constexpr int P = 3 * R - 2;
-    const float* A = (o.p ? V.A1 : V.A0) + o.v0;
+    constexpr int P = 3 * RC - 2;
+    const int w0 = o.v0 + C0;
+    const float* A = (o.p ? V.A1 : V.A0) + w0;
     const int c = n - 1;
-    const int tstar = c - o.p - 2 * o.v0;
-    const int tend = n - 1 + 2 * (R - 1);
-    float cs[R], mx[R], ra[P], rc[P], rb[P];
+    const int tstar = c - o.p - 2 * w0;
+    const int tend = n - 1 + 2 * (RC - 1);
+    float cs[RC], mx[RC], ra[P], rc[P], rb[P];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int i = 2 * (o.v0 + r) + o.p;
+    for (int r = 0; r < RC; ++r) {
+        const int i = 2 * (w0 + r) + o.p;
         cs[r] = (i == c ? -2.f : -4.f) * A[r];
         mx[r] = 0.f;
     }
@@ -2012,7 +2009,7 @@ __device__ __forceinline__ void psl_eval(const View& V, int n, const Outs<TL, R>
         rb[k] = A[k - P];
     }
     for (int t0 = 0; t0 <= tend; t0 += P) {
-        if (t0 >= 2 * R - 1 && t0 + P - 1 <= c) {
+        if (t0 >= 2 * RC - 1 && t0 + P - 1 <= c) {
 #pragma unroll
             for (int j = 0; j < P; ++j) {
                 const int t = t0 + j;
@@ -2021,7 +2018,7 @@ __device__ __forceinline__ void psl_eval(const View& V, int n, const Outs<TL, R>
                 rb[j] = A[t];
                 const float z = t == tstar ? 0.f : 1.f;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
+                for (int r = 0; r < RC; ++r) {
                     const float cp = fmaf(cs[r], fmaf(rb[(j - r + P) % P], z, ra[(j - 3 * r + 3 * P) % P]),
                                           rc[(j - 2 * r + 2 * P) % P]);
                     mx[r] = fmaxf(mx[r], fabsf(cp));
@@ -2037,7 +2034,7 @@ __device__ __forceinline__ void psl_eval(const View& V, int n, const Outs<TL, R>
                 rb[j] = A[t];
                 const float z = t == tstar ? 0.f : 1.f;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
+                for (int r = 0; r < RC; ++r) {
                     const float cp = fmaf(cs[r], fmaf(rb[(j - r + P) % P], z, ra[(j - 3 * r + 3 * P) % P]),
                                           rc[(j - 2 * r + 2 * P) % P]);
                     const int m = t - 2 * r;
@@ -2047,7 +2044,27 @@ __device__ __forceinline__ void psl_eval(const View& V, int n, const Outs<TL, R>
         }
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) pl[r] = (int)mx[r];
+    for (int r = 0; r < RC; ++r) pl[C0 + r] = (int)mx[r];
+}
+
+// All R outputs of the lane: one ring pass up to R = 6; wider lane blocks, whose three
+// rings of 3R - 2 entries would not fit the registers, take the compare-and-select form
+// at R = 7 (measured 2% faster there, two walkers per warp at L = 201) and two ring
+// passes of (R+1)/2 and R - (R+1)/2 outputs from R = 9 (each pass reloads its rings:
+// about twice the shared loads of one pass, but three instructions per lag term instead
+// of a compare and select per term; 21-40% faster for the long lane blocks 9 and 11).
+template <class TL, int R>
+__device__ __forceinline__ void psl_eval(const View& V, int n, const Outs<TL, R>& o, int (&pl)[R])
+{
+    if constexpr (R == 7) {
+        psl_eval_select<TL, R>(V, n, o, pl);
+    } else if constexpr (R >= 8) {
+        constexpr int H = (R + 1) / 2;
+        psl_ring<TL, R, 0, H>(V, n, o, pl);
+        psl_ring<TL, R, H, R - H>(V, n, o, pl);
+    } else {
+        psl_ring<TL, R, 0, R>(V, n, o, pl);
+    }
 }
 
 // The walk under the PSL objective, one walker per warp: evaluate all n flips (dISL by

@@ -204,40 +204,41 @@ def test_warp_layouts(layouts):
                     if tile == 32 and S["words"] * 4 * 16 > 226 * 1024:
                         reg.bad.append(("two 8-warp CTAs do not fit", S["words"]))
                 if tile == 32:          # the PSL neighbourhood
-                    if R <= 5:
-                        P = 3 * R - 2
-                        tend = n - 1 + 2 * (R - 1)
-                        reg.a(v0max + P - 1, "psl ring init hi")
-                        reg.a(1 - P, "psl ring init lo")
-                        reg.g(1 - P, "psl ring init G")
-                        reg.a(-tend, "psl a")
-                        reg.a(v0max + tend, "psl b")
-                        reg.g(tend, "psl C")
-                    else:
-                        reg.a(-(n - 1), "psl sel a")
-                        reg.a(v0max + n + R - 2, "psl sel b")
-                        reg.a(v0max + R - 1, "psl sel init")
+                    psl_reads(reg, n, R, v0max)
                 if reg.bad:
                     bad.append((tile, n_max, n, R, reg.bad[:3]))
     assert not bad, bad[:5]
 
 
+def psl_passes(R):
+    """The ring passes of psl_eval: one up to R = 6, two from R = 8 (R = 7 takes the
+    compare-and-select form)."""
+    if R >= 8:
+        h = (R + 1) // 2
+        return [(0, h), (h, R - h)]
+    return [(0, R)]
+
+
 def psl_reads(reg, n, R, v0max):
-    """The PSL neighbourhood (psl_eval): the ring form for lane blocks up to 5 (its lags
-    run 2R - 2 past n - 1), the select form above."""
-    if R <= 5:
-        P = 3 * R - 2
-        tend = n - 1 + 2 * (R - 1)
-        reg.a(v0max + P - 1, "psl ring init hi")
-        reg.a(1 - P, "psl ring init lo")
-        reg.g(1 - P, "psl ring init G")
-        reg.a(-tend, "psl a")
-        reg.a(v0max + tend, "psl b")
-        reg.g(tend, "psl C")
-    else:
+    """The PSL neighbourhood (psl_eval): each ring pass over outputs C0 .. C0+RC-1 of a
+    lane (block start w0 = v0 + C0) runs its lags 2 RC - 2 past n - 1; the select form
+    reads the class from -(n-1) up to v0 + n + R - 2."""
+    if R == 7:
         reg.a(-(n - 1), "psl sel a")
         reg.a(v0max + n + R - 2, "psl sel b")
         reg.a(v0max + R - 1, "psl sel init")
+        return
+    for C0, RC in psl_passes(R):
+        P = 3 * RC - 2
+        tend = n - 1 + 2 * (RC - 1)
+        for w0 in (C0, v0max + C0):
+            reg.a(w0 + RC - 1, "psl cs")
+            reg.a(w0 + P - 1, "psl ring init hi")
+            reg.a(w0 + 1 - P, "psl ring init lo")
+            reg.a(w0 - tend, "psl a")
+            reg.a(w0 + tend, "psl b")
+        reg.g(1 - P, "psl ring init G")
+        reg.g(tend, "psl C")
 
 
 def test_psl_pair_layouts(layouts):
@@ -322,19 +323,7 @@ def test_long_layouts(layouts):
             reg.a(-(n - 1), "p")
             reg.a(2 * ((n + 1) >> 1), "p hi")
             v0max = (nt // 2 - 1) * R        # the PSL neighbourhood (long PSL walk)
-            if R <= 5:
-                P = 3 * R - 2
-                tend = n - 1 + 2 * (R - 1)
-                reg.a(v0max + P - 1, "psl ring init hi")
-                reg.a(1 - P, "psl ring init lo")
-                reg.g(1 - P, "psl ring init G")
-                reg.a(-tend, "psl a")
-                reg.a(v0max + tend, "psl b")
-                reg.g(tend, "psl C")
-            else:
-                reg.a(-(n - 1), "psl sel a")
-                reg.a(v0max + n + R - 2, "psl sel b")
-                reg.a(v0max + R - 1, "psl sel init")
+            psl_reads(reg, n, R, v0max)
             if reg.bad:
                 bad.append((n_max, n, R, reg.bad[:3]))
     assert not bad, bad[:5]
