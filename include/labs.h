@@ -392,7 +392,10 @@ int labs_trace_learned(labs_ctx *ctx, int32_t capacity, float *dev_scores, int64
 
 /* Checkpoint of every walker's state (sequence, ISL, best, counters, random-stream
  * position) and, with with_tabu != 0, its HT.  With the HT included a restored run
- * continues bit-identically; without it the HT restarts empty.  host_buf NULL queries
+ * continues bit-identically; without it the HT restarts empty (the walks with two or
+ * four walkers per warp, and the plain walk with one, still never move straight back to
+ * the state a walker has just left, which they leave out without probing: the same
+ * choice as the probe's wherever HT holds the walker's states).  host_buf NULL queries
  * the size; a checkpoint restores only into a context with the same walker count,
  * lengths' kind (short or long; for long ones the same LABS_MAX_L_LONG), HT size,
  * seed and LABS_FLAG_PSL (LABS_EINVAL otherwise).  Synchronising.  LABS_EINVAL for a
