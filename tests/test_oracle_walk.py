@@ -244,3 +244,27 @@ def test_bestfirst_second_table_without_hits_is_the_search():
         assert np.array_equal(a[k], b[k])
     c = oracle.bestfirst(L, 5, 4, 400, second_hash=True)
     assert (c["cache_hits"] > 0).all()
+
+
+@pytest.mark.parametrize("objective", ["isl", "psl"])
+@pytest.mark.parametrize("L,walkers,steps,log2,cap", [(21, 4, 600, 4, 3), (41, 4, 800, 16, 32),
+                                                       (101, 3, 600, 6, 9), (201, 2, 500, 16, 32)])
+def test_walk_never_moves_straight_back(objective, L, walkers, steps, log2, cap):
+    """The state a walker has just left is in HT (every state since the walker's start is
+    inserted, and a failed insertion restarts it), so the walk never flips the same free
+    variable twice in a row within one run between restarts: the fact that lets the GPU's
+    lockstep steps leave that move out without probing it.  Small tables, whose
+    insertions overflow and whose neighbourhoods fill, keep it too."""
+    out = oracle.walk(L, 5, walkers, steps, tabu_log2=log2, probe_cap=cap, trace=True, nthreads=2,
+                      objective=objective)
+    codes = out["trace_code"]
+    moves_back = 0
+    pairs = 0
+    for g in range(walkers):
+        for t in range(1, steps):
+            a, b = int(codes[g, t - 1]), int(codes[g, t])
+            if a < 0 or (a & oracle.TRACE_RESTART) or b < 0:
+                continue  # the step before ended in a restart: a fresh state, no move to undo
+            pairs += 1
+            moves_back += (a & 0xFFFF) == (b & 0xFFFF)
+    assert pairs > steps // 2 and moves_back == 0
