@@ -1003,7 +1003,7 @@ __device__ void walk_steps(const WalkEnv& env, Walker& w, int64_t until, int* ba
                            const TL& t)
 {
     const KParams& p = *env.p;
-    const int lane = t.lane, n = env.n, c = n - 1;
+    const int lane = t.lane, n = env.n;
     const Outs<TL, R> o(t);
     const int cap = p.probe_cap;
     constexpr int S = TL::kSize / 2;  // probe slots per candidate in the two-candidate round
@@ -2634,10 +2634,12 @@ __device__ __forceinline__ void walk_group(const KParams& p, int chunk_index)
             }
             if (real) {
                 save_walker(env.st, w, t.lane);
-                if (MODE == 3 && t.lane == 0) {
-                    env.st->psl = ps.psl;
-                    env.st->best_psl = ps.best_psl;
-                    env.st->since_psl = ps.since_psl;
+                if constexpr (MODE == 3) {
+                    if (t.lane == 0) {
+                        env.st->psl = ps.psl;
+                        env.st->best_psl = ps.best_psl;
+                        env.st->since_psl = ps.since_psl;
+                    }
                 }
             }
             __syncwarp();
